@@ -1,0 +1,342 @@
+"""Pins for the CPU oracle: closed forms, brute force, invariants and published values.
+
+Each test fixes a property that the paper or the mathematics determines
+independently of the oracle's own code, chosen so that a plausible slip in the
+oracle (a dropped 1/s scale, a transposed operand, a wrong sign, a wrong index
+set) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import philox, offline
+from oracle.gradient import grid_gradient_operator
+from oracle.rid import (RIDConfig, OnlineRID, coeff_alg4, coeff_alg5, coeff_alg6,
+                        coeff_alg7, css_update, na_hutchpp_sq_error, refill_scale,
+                        sketched_ridge_scores, streaming_lambda)
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    """Published Philox4x32-10 known-answer vectors (Salmon et al., SC'11)."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox.philox4x32(*v[:4], v[4], v[5])
+        assert [int(o) for o in out] == v[6:]
+
+
+def test_rademacher_bit_layout_and_moments():
+    seed = 12345
+    blk = philox.rademacher_block(seed, [3, 7], 0, 512)
+    k0, k1 = philox.seed_key(seed)
+    # entry (row 7, coordinate 300): block 2, position 44 -> word 1, bit 12
+    w = philox.philox4x32(2, 7, philox.TAG_RADEMACHER, 0, k0, k1)
+    bit = (int(w[1]) >> 12) & 1
+    assert blk[1, 300] == (-1.0 if bit else 1.0)
+    big = philox.rademacher_block(seed, np.arange(64), 0, 4096)
+    assert set(np.unique(big)) == {-1.0, 1.0}
+    assert abs(big.mean()) < 4 / math.sqrt(big.size)
+    # distinct rows are uncorrelated: E[w_r w_q] = delta_rq
+    C = big @ big.T / big.shape[1]
+    off = C - np.diag(np.diag(C))
+    assert np.abs(off).max() < 5 / math.sqrt(big.shape[1])
+
+
+def test_gaussian_moments():
+    g = philox.gauss_block(7, np.arange(16), 0, 8192)
+    x = g.ravel()
+    n = x.size
+    assert abs(x.mean()) < 4 / math.sqrt(n)
+    assert abs(x.var() - 1.0) < 4 * math.sqrt(2.0 / n)
+    assert abs(np.mean(x ** 4) - 3.0) < 0.1
+
+
+def test_uniform53_exact_and_range():
+    u = philox.uniform(99, np.arange(4), np.arange(1000)[:, None], 0)
+    assert (u >= 0).all() and (u < 1).all()
+    k0, k1 = philox.seed_key(99)
+    w = philox.philox4x32(5, 3, philox.TAG_UNIFORM, 2, k0, k1)
+    ref = ((int(w[0]) >> 5) * 2 ** 26 + (int(w[1]) >> 6)) / 2 ** 53
+    assert float(philox.uniform(99, 2, 5, 3)) == ref
+
+
+# ---------------------------------------------------------------- ridge leverage (Eqs. 16, 23)
+def test_ridge_scores_orthogonal_closed_form():
+    """For orthogonal columns with norms sigma_j, Eq. 16 gives sigma_j^2/(sigma_j^2 + lambda)."""
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 6)))
+    sig = np.array([3.0, 2.0, 1.0, 0.5, 0.1, 0.01])
+    A = Q * sig
+    lam = 0.3
+    ref = sig ** 2 / (sig ** 2 + lam)
+    np.testing.assert_allclose(offline.ridge_leverage_scores(A, lam), ref, rtol=1e-12)
+    # Eq. 23 with the identity as the (scaled) sketch reduces to Eq. 16
+    np.testing.assert_allclose(sketched_ridge_scores(A @ A.T, lam, A), ref, rtol=1e-12)
+
+
+def test_ridge_score_trace_identity_and_monotonicity():
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((10, 7)) @ np.diag([5, 3, 2, 1, .5, .2, .1])
+    lam = 0.4
+    tau = offline.ridge_leverage_scores(A, lam)
+    mu = np.linalg.eigvalsh(A @ A.T)
+    assert abs(tau.sum() - np.sum(mu / (mu + lam))) < 1e-12
+    b = rng.standard_normal(10)
+    tau2 = offline.ridge_leverage_scores(np.column_stack([A, b]), lam)
+    assert (tau2[:7] <= tau + 1e-15).all()      # Lemma 1 (monotonicity)
+
+
+def test_streaming_lambda_identity_sketch_is_tail_over_k():
+    """With the identity sketch, (||A||^2 - ||S_k||^2)/k equals ||A - A_k||_F^2/k (Eckart-Young)."""
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((15, 9))
+    k = 4
+    lam = streaming_lambda(A @ A.T, float(np.sum(A * A)), k)
+    assert abs(lam - offline.tail_energy(A, k) / k) < 1e-12 * np.sum(A * A)
+
+
+# ---------------------------------------------------------------- CPQR ID (Eqs. 5-11) and coefficient updates
+def test_cpqr_id_is_least_squares_and_exact_for_rank_k():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((40, 5)) @ rng.standard_normal((5, 30))
+    J, P = offline.cpqr_id(A, 5)
+    np.testing.assert_allclose(P[:, J], np.eye(5), atol=1e-12)
+    assert offline.id_error(A, J, P) < 1e-12 * np.linalg.norm(A)
+    B = A + 1e-3 * rng.standard_normal(A.shape)
+    J, P = offline.cpqr_id(B, 5)
+    Pls = np.linalg.lstsq(B[:, J], B, rcond=None)[0]
+    np.testing.assert_allclose(P, Pls, atol=1e-9)
+
+
+def test_coefficient_updates_with_identity_sketch_equal_exact_least_squares():
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((30, 20))
+    J = np.array([3, 9, 11, 17])
+    Pls = np.linalg.lstsq(A[:, J], A, rcond=None)[0]
+    G = A[:, J].T @ A[:, J]
+    np.testing.assert_allclose(coeff_alg4(A[:, J], A), Pls, atol=1e-12)
+    np.testing.assert_allclose(coeff_alg5(G, A[:, J], A), Pls, atol=1e-11)
+    # Algorithm 6 with every row replaced is Algorithm 4; with none replaced it keeps P_prev
+    Pprev = rng.standard_normal((4, 20))
+    np.testing.assert_allclose(coeff_alg6(A[:, J], A, Pprev, np.zeros(4, bool)), Pls, atol=1e-12)
+    np.testing.assert_array_equal(coeff_alg6(A[:, J], A, Pprev, np.ones(4, bool)), Pprev)
+    # mixed case: kept rows are unchanged; the new rows satisfy the normal equations of the residual
+    kept = np.array([True, False, True, False])
+    P6 = coeff_alg6(A[:, J], A, Pprev, kept)
+    np.testing.assert_array_equal(P6[kept], Pprev[kept])
+    Anew = A[:, J[~kept]]
+    np.testing.assert_allclose(Anew.T @ (A - A[:, J] @ P6), 0, atol=1e-10)
+    # Algorithm 7: T = A_J^+ A_Jprev; same basis gives T = I
+    np.testing.assert_allclose(coeff_alg7(A[:, J], A[:, J], Pprev), Pprev, atol=1e-12)
+    # a permuted previous basis is mapped back by the permutation
+    perm = np.array([2, 0, 3, 1])
+    np.testing.assert_allclose(coeff_alg7(A[:, J], A[:, J[perm]], Pprev), np.eye(4)[:, perm] @ Pprev, atol=1e-12)
+
+
+# ---------------------------------------------------------------- NA-Hutch++ (Eqs. 33-37)
+def _hutch_fixture(seed=5, m=60, n=25, t=4, h=36):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, 6)) @ rng.standard_normal((6, n)) + 0.1 * rng.standard_normal((m, n))
+    J = np.array([1, 7, 12, n - 2])
+    P = np.linalg.lstsq(A[:, J], A, rcond=None)[0] + 0.05 * rng.standard_normal((t, n))
+    Om = rng.standard_normal((h, m))
+    return A, J, P, Om
+
+
+def test_hutchpp_sketch_form_equals_dense_form():
+    """Eq. 37 (sketches only) equals Eqs. 34-35 applied to the explicit B = A (A_J P)^T."""
+    A, J, P, Om = _hutch_fixture()
+    AJ = A[:, J]
+    G = AJ.T @ AJ
+    split = ((0, 6), (6, 18), (18, 36))
+    H = Om @ A
+    fro2 = float(np.sum(A * A))
+    e2 = na_hutchpp_sq_error(H, H[:, J], P, G, fro2, split)
+    B = A @ (AJ @ P).T
+    cross = offline.na_hutchpp_trace(B, Om[0:6], Om[6:18], Om[18:36])
+    ref = fro2 - 2 * cross + np.trace(G @ P @ P.T)
+    assert abs(e2 - ref) < 1e-10 * fro2
+    # Eq. 36 itself: the expansion is an identity for the exact trace
+    exact = np.linalg.norm(A - AJ @ P) ** 2
+    assert abs(fro2 - 2 * np.trace(B) + np.trace(G @ P @ P.T) - exact) < 1e-10 * fro2
+
+
+def test_hutchpp_reduces_to_hutchinson_without_control_variate():
+    A, J, P, Om = _hutch_fixture()
+    AJ = A[:, J]
+    G = AJ.T @ AJ
+    fro2 = float(np.sum(A * A))
+    e2 = na_hutchpp_sq_error(Om @ A, (Om @ A)[:, J], P, G, fro2, ((0, 0), (0, 0), (0, 36)))
+    B = A @ (AJ @ P).T
+    ref = fro2 - 2 * offline.hutchinson_trace(B, Om) + np.trace(G @ P @ P.T)
+    assert abs(e2 - ref) < 1e-10 * fro2
+
+
+def test_hutchpp_exact_when_reconstruction_is_exact_and_rank_small():
+    """A = A_J P of rank r <= c1 h: B is symmetric of rank r, B~ = B and the estimate is exact (0)."""
+    rng = np.random.default_rng(6)
+    m, n, r = 80, 30, 4
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    J = np.array([0, 5, 9, 14])
+    P = np.linalg.lstsq(A[:, J], A, rcond=None)[0]
+    G = A[:, J].T @ A[:, J]
+    Om = rng.standard_normal((48, m))
+    H = Om @ A
+    e2 = na_hutchpp_sq_error(H, H[:, J], P, G, float(np.sum(A * A)), ((0, 8), (8, 24), (24, 48)))
+    assert abs(e2) < 1e-9 * np.sum(A * A)
+
+
+def test_hutchpp_unbiased_over_probe_draws():
+    """E[e2] = ||A - A_J P||_F^2 for fixed (A, J, P) over independent probe rows."""
+    A, J, P, _ = _hutch_fixture(seed=8, m=40, n=20, h=30)
+    AJ = A[:, J]
+    G = AJ.T @ AJ
+    fro2 = float(np.sum(A * A))
+    exact = np.linalg.norm(A - AJ @ P) ** 2
+    split = ((0, 5), (5, 15), (15, 30))
+    vals = []
+    for seed in range(3000):
+        Om = philox.rademacher_block(seed, np.arange(30), 0, A.shape[0])
+        H = Om @ A
+        vals.append(na_hutchpp_sq_error(H, H[:, J], P, G, fro2, split))
+    vals = np.array(vals)
+    se = vals.std() / math.sqrt(len(vals))
+    assert abs(vals.mean() - exact) < 4 * se
+
+
+# ---------------------------------------------------------------- column subset selection
+def test_css_update_probabilities():
+    """Drop with probability 1 - tau/tau_old; refill with probability tau^D * scale (clipped)."""
+    cfg = RIDConfig(m=10, k=4, s=7, seed=0)
+    scale = refill_scale(cfg)
+    JC = np.array([10, 11, 12, 13])
+    tau_old = np.array([0.5, 0.5, 0.5, 0.5])
+    tau_C = np.array([0.5, 0.4, 0.25, 0.1])          # drop probabilities 0, .2, .5, .8
+    JD = [20, 21, 22, 23]
+    tau_D = np.array([0.3, 0.3, 0.3, 0.3]) / scale    # refill probability 0.3 per candidate
+    drops = np.zeros(4)
+    first = np.zeros(4)
+    N = 4000
+    for seed in range(N):
+        cfg.seed = seed
+        newJ, newtau = css_update(cfg, 0, JC, tau_old, tau_C, JD, tau_D)
+        dropped = newJ != JC
+        drops += dropped
+        if newJ[3] == 20:
+            first[3] += 1
+        assert len(set(int(j) for j in newJ if j >= 0)) == int((newJ >= 0).sum())
+        kept = ~dropped
+        np.testing.assert_array_equal(newtau[kept], tau_C[kept])
+    p = np.array([0.0, 0.2, 0.5, 0.8])
+    assert drops[0] == 0
+    se = np.sqrt(p * (1 - p) / N) + 1e-9
+    assert (np.abs(drops / N - p) < 4 * se + 1e-12).all()
+    # slot 3 is dropped w.p. 0.8 and then takes candidate 20 w.p. 0.3, unless slot 1 or 2
+    # (dropped w.p. 0.2 and 0.5) took it first: candidates already in C are skipped
+    q = 0.8 * 0.3 * (1 - 0.2 * 0.3) * (1 - 0.5 * 0.3)
+    assert abs(first[3] / N - q) < 4 * math.sqrt(q * (1 - q) / N)
+
+
+def test_refill_scale_formula():
+    cfg = RIDConfig(m=10, k=20, s=83, eps=0.5, delta=0.05)
+    assert abs(refill_scale(cfg) - (20 * math.log(20) + 20 * math.log(20.0) / 0.5) / 20) < 1e-12
+
+
+# ---------------------------------------------------------------- whole stream (Algorithm 3)
+def test_stream_exact_rank_r_reconstruction():
+    """Rank r < t data: Algorithms 4 and 7 reproduce A; the chosen error estimate is ~0 with c1 h >= r."""
+    rng = np.random.default_rng(9)
+    m, n, r, k = 400, 70, 5, 8
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    cfg = RIDConfig(m=m, k=k, s=4 * k + 3, h=60, seed=2)
+    o = OnlineRID(cfg)
+    o.ingest(A)
+    J, P = o.finalize()
+    act = o._last_active
+    assert np.linalg.norm(A - A[:, J[act]] @ o._last_candidates[0]) < 1e-11 * np.linalg.norm(A)
+    assert np.linalg.norm(A - A[:, J[act]] @ o._last_candidates[3]) < 1e-10 * np.linalg.norm(A)
+    est, q = o.error_estimates()
+    assert abs(est[0]) < 1e-9 * np.sum(A * A)
+    assert offline.id_error(A, J, P) < 1e-6 * np.linalg.norm(A) or q in (5, 6)
+
+
+def test_stream_large_sketch_approaches_unsketched_quantities():
+    """s >> t: the scaled sketch Gram matches A A^T in trace and top-k energy, and Algorithm 5
+    approaches exact least squares (both fail by a factor ~s if the 1/s scale of R1 is dropped)."""
+    rng = np.random.default_rng(10)
+    m, n, k = 300, 24, 6
+    A = rng.standard_normal((m, 10)) @ np.diag(2.0 ** -np.arange(10)) @ rng.standard_normal((10, n))
+    A += 0.01 * rng.standard_normal((m, n))
+    s = 3000
+    cfg = RIDConfig(m=m, k=k, s=s, h=0, seed=1)
+    o = OnlineRID(cfg)
+    o.ingest(A[:, :k * 3])
+    A18 = A[:, :18]
+    fro2 = float(np.sum(A18 ** 2))
+    M = o.SSt / s
+    assert abs(np.trace(M) - fro2) < 4 * math.sqrt(2.0 / s) * fro2
+    mu = np.linalg.eigvalsh(M)[::-1]
+    topk = fro2 - offline.tail_energy(A18, k)
+    assert abs(mu[:k].sum() - topk) < 0.1 * topk
+    rec = o.history[-1]
+    assert abs(rec.lam - max((fro2 - mu[:k].sum()) / k, 1e-12 * fro2 / k)) < 1e-9 * fro2
+    act = o._last_active
+    J = o.JC[act]
+    P5 = o._last_candidates[1]
+    Pls = np.linalg.lstsq(A[:, J], A18, rcond=None)[0]
+    assert np.linalg.norm(A[:, J] @ (P5 - Pls)) < 0.1 * np.linalg.norm(A18)
+
+
+def test_stream_first_batch_fills_slots_in_order_when_probabilities_saturate():
+    rng = np.random.default_rng(11)
+    m, k = 200, 5
+    A = rng.standard_normal((m, 5))
+    cfg = RIDConfig(m=m, k=k, s=23, h=12, c_const=1e6, seed=4)
+    o = OnlineRID(cfg)
+    o.ingest(A)
+    np.testing.assert_array_equal(o.JC, np.arange(5))
+
+
+def test_stream_tail_batch_and_p_width():
+    rng = np.random.default_rng(12)
+    m, k, n = 150, 4, 23
+    A = rng.standard_normal((m, n))
+    cfg = RIDConfig(m=m, k=k, s=19, h=12, seed=3)
+    o = OnlineRID(cfg)
+    o.ingest(A)
+    assert len(o.history) == n // k
+    J, P = o.finalize()
+    assert len(o.history) == n // k + 1
+    assert P.shape == (k, n)
+    assert ((J >= -1) & (J < n)).all()
+    assert (P[J < 0] == 0).all()
+
+
+# ---------------------------------------------------------------- simplex gradient (Eqs. 38-43)
+def test_gradient_interior_is_central_difference_and_linear_exact():
+    nx, ny = 7, 5
+    G = grid_gradient_operator((nx, ny))
+    x = np.arange(nx)[None, :].repeat(ny, 0).ravel()    # x fastest
+    y = np.arange(ny)[:, None].repeat(nx, 1).ravel()
+    f = np.sin(0.7 * x) + np.cos(0.3 * y) * x
+    g = G @ f
+    gx, gy = g[: nx * ny].reshape(ny, nx), g[nx * ny:].reshape(ny, nx)
+    F = f.reshape(ny, nx)
+    np.testing.assert_allclose(gx[:, 1:-1], (F[:, 2:] - F[:, :-2]) / 2, atol=1e-12)
+    np.testing.assert_allclose(gy[1:-1, :], (F[2:, :] - F[:-2, :]) / 2, atol=1e-12)
+    np.testing.assert_allclose(gx[:, 0], F[:, 1] - F[:, 0], atol=1e-12)       # one-sided at the boundary
+    lin = 2.0 * x - 3.0 * y + 1.0
+    gl = G @ lin
+    np.testing.assert_allclose(gl[: nx * ny], 2.0, atol=1e-12)
+    np.testing.assert_allclose(gl[nx * ny:], -3.0, atol=1e-12)
+    G2 = grid_gradient_operator((nx, ny), nfields=2)
+    assert G2.shape == (2 * 2 * nx * ny, 2 * nx * ny)
+    np.testing.assert_allclose(G2 @ np.concatenate([f, lin]),
+                               np.concatenate([gx.ravel(), lin * 0 + 2.0, gy.ravel(), lin * 0 - 3.0]), atol=1e-12)
