@@ -1,0 +1,281 @@
+"""Benchmark of the single-pass online randomized ID ingest path on GB300.
+
+Workload (default): the channel-flow-shaped stream -- three velocity
+components on a 192 x 129 x 192 grid (m = 14,266,368 FP32 values per
+snapshot), n = 1000 snapshots streamed in blocks of 8, k = t = 100,
+s = 403 left-sketch rows, h = 50 NA-Hutch++ probe rows, Rademacher test
+matrix, streaming lambda.  One step = one whole stream through the C ABI
+(reset, 125 ingest calls with the batch step every 100 snapshots, finalize).
+
+Prints one JSON line.  ``value`` is snapshots/s over all ranks with the
+inputs resident in HBM; ``e2e`` is the same metric through rid_ingest with
+pinned host buffers (host->device copies inside the timed region) and the
+coefficients read back to the host.  ``roofline`` reports the fused
+ingest/sketch kernel (the dominant kernel), timed live with CUDA events on
+its stream.  ``--impl reference`` times the CPU oracle on a bounded sample of
+the same workload.  Under torchrun every rank runs its own independent stream
+(weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    "channel": dict(workload="channel-flow-shaped stream, 3 x 192 x 129 x 192 FP32, n=1000, blocks of 8",
+                    nx=192, ny=129, nz=192, n=1000, b=8, k=100, s=403, h=50),
+    "channel_small": dict(workload="channel-flow-shaped stream, 3 x 48 x 33 x 48 FP32, n=200, blocks of 8",
+                          nx=48, ny=33, nz=48, n=200, b=8, k=20, s=83, h=30),
+}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(cfg, seconds_target=15.0, m_sample=1 << 17):
+    """The oracle as it stands on a bounded sample: the first m_sample coordinates of one block of
+    b snapshots of the same stream; throughput extrapolated linearly in m (ingest is linear in m)."""
+    import torch
+    from oracle.rid import OnlineRID as Oracle, RIDConfig
+    from workloads import ChannelFlowStream
+    st = ChannelFlowStream(seed=0, nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=cfg["n"], device="cpu")
+    m = st.m
+    ms = min(m_sample, m)
+    blk = st.block(0, cfg["b"]).double().numpy()[:, :ms]
+    o = Oracle(RIDConfig(m=ms, k=cfg["k"], s=cfg["s"], h=cfg["h"], seed=0))
+    t0 = time.perf_counter()
+    o.ingest(blk.T)
+    dt = time.perf_counter() - t0
+    cores = torch.get_num_threads()
+    per_snap_full = dt / cfg["b"] * (m / ms)
+    return {"value": 1.0 / per_snap_full, "unit": "snapshots/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle ingest of {cfg['b']} snapshots restricted to the first {ms} of m={m} coordinates "
+                      f"({dt:.1f} s), extrapolated linearly in m; batch steps not included"}
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(cfg, m_sample=1 << 15)
+        if i >= args.warmup:
+            steps.append(cb)
+    v = float(np.mean([c["value"] for c in steps]))
+    line = {"metric": "snapshots/s", "value": v, "unit": "snapshots/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "impl": "reference", "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["workload"]},
+            "cpu_baseline": {"kind": "oracle", "cores": steps[0]["cores"], "sample": steps[0]["sample"], "value": v},
+            "e2e": {"value": v, "unit": "snapshots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="channel", choices=sorted(CONFIGS))
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2405_16076_gb300 import rid
+    from workloads import ChannelFlowStream
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    n, b = cfg["n"], cfg["b"]
+    gen = ChannelFlowStream(seed=1000 + rank, nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=n, device=dev)
+    m = gen.m
+    X = torch.empty((n, m), dtype=torch.float32, device=dev)     # row j = snapshot j, resident in HBM
+    for j0 in range(0, n, 50):
+        gen.block(j0, min(50, n - j0), out=X[j0:j0 + 50])
+    torch.cuda.synchronize()
+
+    st = torch.cuda.Stream(device=dev)
+    h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", n_max=n, seed=7 + rank, stream=st)
+    Jd = torch.empty(cfg["k"], dtype=torch.int64, device=dev)
+    Pd = torch.empty((n, cfg["k"]), dtype=torch.float64, device=dev)
+
+    def step():
+        h.reset()
+        for j0 in range(0, n, b):
+            h.ingest(X[j0:j0 + b])
+        h.finalize_device(Jd, Pd)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    h.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    prof_ms, prof_kern, prof_grp = h.profile_read()
+    h.profile(False)
+    t_max = ms_total
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n * args.steps / (t_max / 1e3)
+
+    # e2e: same metric through rid_ingest with pinned host buffers and a host read of P
+    ring = 32
+    Xh = torch.empty((ring * b, m), dtype=torch.float32, pin_memory=True)
+    Xh.copy_(X[: ring * b].cpu())
+    J_h = np.empty(cfg["k"], dtype=np.int64)
+    P_h = np.empty((n, cfg["k"]))
+
+    def step_e2e():
+        h.reset()
+        for q, j0 in enumerate(range(0, n, b)):
+            r0 = (q % ring) * b
+            h.ingest(Xh[r0:r0 + b])
+        J, P = h.finalize()
+        return P
+
+    step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step_e2e()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_val = world * n / e2e_s
+
+    pk = peaks()
+    groups = max(int(prof_grp[0]), 1)
+    avg_ms = prof_ms[0] / groups
+    bytes_per_launch = 2.0 * b * m * 4          # read each column once + write it to its D slot
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "ingest_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            traffic = json.load(open(tr_path)).get(args.config)
+        except Exception:
+            traffic = None
+    line = {
+        "metric": "snapshots/s", "value": value, "unit": "snapshots/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": cfg["workload"], "m": m, "n": n, "block": b, "k": cfg["k"], "s": cfg["s"],
+                   "h": cfg["h"], "omega": "rademacher", "lambda": "streaming",
+                   "l2": "inputs larger than L2 (57 MB per snapshot, whole stream resident in HBM)",
+                   "parallelism": f"{world} independent streams"},
+        "e2e": {"value": e2e_val, "unit": "snapshots/s", "h2d_bytes_per_step": int(n * m * 4),
+                "d2h_bytes_per_step": int(cfg["k"] * n * 8 + cfg["k"] * 8)},
+        "gpu_launches": int(prof_kern.sum()),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": achieved / pk.get("hbm_gbs"), "traffic": traffic,
+                     "kernel": "ingest_sketch_kernel", "avg_launch_ms": avg_ms,
+                     "phase_ms_per_step": {"ingest_sketch": prof_ms[0] / args.steps,
+                                           "ingest_reduce": prof_ms[1] / args.steps,
+                                           "batch_step": prof_ms[2] / args.steps},
+                     "peak_source": "measured (MEASURED_PEAKS.json)" if "fallback" not in pk else "fallback"},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

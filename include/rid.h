@@ -1,0 +1,173 @@
+/*
+ * rid.h -- C ABI of the GB300 single-pass online randomized interpolative
+ * decomposition (Li, Becker & Doostan, arXiv 2405.16076).
+ *
+ * Problem (Sec. 1 and Algorithm 3): the columns a_1..a_n of an m x n matrix A
+ * arrive once, in order.  After the stream ends the library returns an index
+ * set J of t = k columns and a t x n coefficient matrix P with A ~ A(:,J) P
+ * (the column ID of Eq. 2), together with single-pass NA-Hutch++ estimates of
+ * ||A - A(:,J) P||_F for the four coefficient updates (Algorithm 8).
+ *
+ * Conventions shared by every entry point:
+ *  - Return RID_OK (0) on success, a negative RID_E* code otherwise; the text
+ *    of the last error is available from rid_last_error().  No C++ exception
+ *    crosses this boundary.
+ *  - All compute runs asynchronously on the handle's CUDA stream
+ *    (rid_config.cuda_stream, NULL = the legacy default stream).  Entry points
+ *    that return data to the host synchronize that stream.
+ *  - Matrices are column-major.  A "column" of the stream is m contiguous
+ *    elements of the configured data type; ld is the element distance
+ *    between consecutive columns (ld >= m).
+ *  - The handle owns all device state.  Output buffers are owned by the
+ *    caller.  One handle must not be used by two host threads at once.
+ *  - Indices are 0-based; -1 marks an empty basis slot.
+ */
+#ifndef RID_H
+#define RID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum rid_status {
+  RID_OK = 0,
+  RID_EINVAL = -1,      /* bad argument or configuration */
+  RID_ENOMEM = -2,      /* device or host allocation failed */
+  RID_ECUDA = -3,       /* a CUDA runtime call failed */
+  RID_ESTATE = -4,      /* call not allowed in the current state (e.g. ingest after finalize) */
+  RID_ENONFINITE = -5,  /* a NaN/Inf snapshot was ingested (detected from its squared norm) */
+  RID_ENOLIB = -6       /* the CUDA library is missing or no device is present */
+};
+
+enum rid_lambda_mode {
+  RID_LAMBDA_STREAMING = 0,  /* lambda = (||A_obs||_F^2 - ||S_k||_F^2)/k, Eq. 23 */
+  RID_LAMBDA_FIXED = 1       /* lambda = lambda_fixed, e.g. ||A - A_k||_F^2/k (Eq. 17 with Eq. 16) */
+};
+
+enum rid_omega_kind {
+  RID_OMEGA_GAUSSIAN = 0,    /* i.i.d. N(0,1) entries (Algorithm 3, randn) */
+  RID_OMEGA_RADEMACHER = 1   /* i.i.d. +-1 entries (sub-Gaussian, Sec. 3.3) */
+};
+
+enum rid_dtype { RID_F64 = 0, RID_F32 = 1 };
+
+enum rid_sketch_prec {
+  RID_SKETCH_NATIVE = 0,     /* sketch accumulated in the data type (FP64 or FP32) */
+  RID_SKETCH_BF16 = 1,       /* data rounded to BF16, tensor cores, FP32 accumulation */
+  RID_SKETCH_BF16X2 = 2      /* data split hi+lo in BF16, tensor cores, FP32 accumulation */
+};
+
+typedef struct rid_config {
+  int64_t m;             /* snapshot length */
+  int32_t k;             /* target rank; basis size t = k (Sec. 2.2.2) */
+  int32_t s;             /* left-sketch rows (ell of Algorithm 3) */
+  int32_t h;             /* independent Hutch++ probe rows; 0 = shared rows of the left sketch */
+  int32_t lambda_mode;   /* enum rid_lambda_mode */
+  double c1, c2;         /* NA-Hutch++ split, c1 < c2, c3 = 1 - c1 - c2 (Algorithm 8) */
+  double eps, delta;     /* accuracy and failure probability of the refill rule (Algorithm 3) */
+  double c_const;        /* constant c of the refill probability (Algorithm 3) */
+  double lambda_fixed;   /* used when lambda_mode == RID_LAMBDA_FIXED */
+  int32_t omega_kind;    /* enum rid_omega_kind */
+  int32_t data_dtype;    /* enum rid_dtype */
+  int32_t sketch_prec;   /* enum rid_sketch_prec */
+  int32_t grad_dims;     /* 0 = off; 2 = 2-D grid gradient in the leverage sketch (Sec. 3.4) */
+  int32_t nx, ny;        /* grid of one field when grad_dims = 2 (x fastest) */
+  int32_t nfields;       /* fields stacked in one snapshot when grad_dims = 2 */
+  int64_t n_max;         /* initial capacity in columns (grows by doubling) */
+  uint64_t seed;         /* key of the Philox4x32-10 streams */
+  void* cuda_stream;     /* cudaStream_t to run on; NULL = default stream */
+} rid_config;
+
+typedef struct rid_handle rid_handle;
+
+/* Fill *cfg with defaults: c1 = 1/6, c2 = 1/3, eps = 0.5, delta = 0.05,
+ * c_const = 1, streaming lambda, Rademacher Omega, FP32 data, native sketch,
+ * n_max = 1024.  m, k, s, h must still be set.  Returns RID_EINVAL on NULL. */
+int rid_config_default(rid_config* cfg);
+
+/* Validate *cfg and allocate the device state (Algorithm 3, initialisation).
+ * On success *out receives a new handle.  Errors: RID_EINVAL (sizes: m >= 1,
+ * 1 <= k <= 1024, k < s <= 4096, 0 <= h <= 1024, h == 0 or h >= 3,
+ * 0 < c1 < c2, c1 + c2 < 1, unknown enum values), RID_ENOMEM, RID_ENOLIB. */
+int rid_init(rid_handle** out, const rid_config* cfg);
+
+/* Ingest ncols >= 0 columns (Algorithm 3, the loop body for each column):
+ * column q starts at cols + q*ld elements of the configured dtype.
+ * on_device != 0: cols is a device pointer, read in place; otherwise a host
+ * pointer (preferably pinned), copied to the device first.  The library copies
+ * what it keeps; the caller may reuse the buffer once the handle's stream has
+ * passed this call.  Whenever t = k columns have been buffered the batch step
+ * (ridge scores, prune/refill, Algorithms 4-8) runs on the device without a
+ * host round trip.  Errors: RID_EINVAL (ld < m, NULL cols with ncols > 0),
+ * RID_ESTATE (after rid_finalize), RID_ECUDA. */
+int rid_ingest(rid_handle* h, const void* cols, int64_t ld, int32_t ncols, int32_t on_device);
+
+/* End the stream: run the batch step over the count < t buffered columns, if
+ * any (tail batch).  Then, if J_out != NULL, write the t basis indices
+ * (int64, -1 = empty slot) and, if P_out != NULL, the t x n coefficient matrix
+ * (double, column-major, ldp >= t).  on_device selects device or host output
+ * pointers.  Synchronizes the stream.  May be called again to re-read the
+ * result.  Errors: RID_EINVAL (ldp < t), RID_ENONFINITE, RID_ECUDA. */
+int rid_finalize(rid_handle* h, int64_t* J_out, double* P_out, int64_t ldp, int32_t on_device);
+
+/* Estimates from the last batch step (Algorithm 8): est_sq[0] = chosen
+ * candidate, est_sq[1..4] = Algorithms 4..7, signed estimates of
+ * ||A_obs - A_J P||_F^2; est_fro = sqrt(max(est_sq, 0)); *q_star in 4..7.
+ * Any output pointer may be NULL.  Synchronizes.  RID_ESTATE before the first
+ * batch step. */
+int rid_error_estimate(rid_handle* h, double est_sq[5], double est_fro[5], int32_t* q_star);
+
+/* Number of columns ingested so far. */
+int64_t rid_n_obs(const rid_handle* h);
+
+/* Copy the current basis columns A(:,J) (m x t, data dtype, ld >= m; empty
+ * slots are written as zeros) to out (device or host).  Synchronizes. */
+int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device);
+
+/* Internal state for tests (host output, synchronizes):
+ *  RID_STATE_SKETCH   : (s+h) x n_obs doubles, Omega A_obs (unit-variance rows)
+ *  RID_STATE_SKETCH_LEV: s x n_obs doubles, the sketch used by the ridge scores
+ *  RID_STATE_SST      : s x s doubles
+ *  RID_STATE_FRO2     : 2 doubles, ||A_obs||^2 and the leverage-sketch norm
+ *  RID_STATE_JC       : t int64 basis indices
+ *  RID_STATE_TAU_OLD  : t doubles
+ *  RID_STATE_LAMBDA   : 1 double, lambda of the last batch step
+ *  RID_STATE_CAND     : 4 x t x n_obs doubles, candidates P_4..P_7 of the last
+ *                       batch step (rows of empty slots are 0)
+ *  RID_STATE_BATCHES  : 1 int64, number of batch steps run
+ * count is the number of elements the caller's buffer holds. */
+enum rid_state_item {
+  RID_STATE_SKETCH = 0, RID_STATE_SKETCH_LEV = 1, RID_STATE_SST = 2, RID_STATE_FRO2 = 3,
+  RID_STATE_JC = 4, RID_STATE_TAU_OLD = 5, RID_STATE_LAMBDA = 6, RID_STATE_CAND = 7,
+  RID_STATE_BATCHES = 8
+};
+int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count);
+
+/* Measurement hooks (used by the benchmark).  While enabled, the library
+ * brackets its launches with CUDA events on the handle's stream, per phase:
+ * [0] the fused ingest/sketch kernel, [1] the ingest reductions (sketch
+ * append, SS^T, ||A_obs||^2), [2] the batch step; and counts its kernel
+ * launches.  rid_profile(h, 1) clears the counters; rid_profile_read
+ * synchronizes and returns total milliseconds, kernel launches and bracketed
+ * launch groups per phase since then (any pointer may be NULL). */
+int rid_profile(rid_handle* h, int32_t enable);
+int rid_profile_read(rid_handle* h, double ms[3], int64_t kernels[3], int64_t groups[3]);
+
+/* Wait for the handle's stream; report deferred device errors. */
+int rid_sync(rid_handle* h);
+
+/* Forget the stream (keep allocations): the handle is as after rid_init. */
+int rid_reset(rid_handle* h);
+
+/* Text of the last error on h (or of the last failed rid_init when h is NULL). */
+const char* rid_last_error(const rid_handle* h);
+
+/* Free everything.  NULL is ignored. */
+void rid_destroy(rid_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RID_H */

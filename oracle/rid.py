@@ -116,11 +116,13 @@ def sketched_ridge_scores(SSt_scaled, lam, V):
     return np.einsum("ij,ij->j", V, X)
 
 
-def css_update(cfg, batch, JC, tau_old, tau_C, JD, tau_D):
+def css_update(cfg, batch, JC, tau_old, tau_C, JD, tau_D, margins=None):
     """Prune and refill the basis slots (Algorithm 3, following Cohen et al.; R7, R8).
 
     JC, tau_old are updated copies; tau_C are min(tau_old, scores of C) for the
-    occupied slots; JD, tau_D the buffered columns and their scores.
+    occupied slots; JD, tau_D the buffered columns and their scores.  If
+    ``margins`` is a list, the relative distance of every decision's score
+    from the score at which that decision would flip is appended to it.
     """
     JC = JC.copy()
     tau_old = tau_old.copy()
@@ -128,6 +130,8 @@ def css_update(cfg, batch, JC, tau_old, tau_C, JD, tau_D):
     for i in range(cfg.t):
         if JC[i] >= 0:
             u = float(philox.uniform(cfg.seed, batch, i, 0))
+            if margins is not None and tau_C[i] > 0:
+                margins.append(abs(u - (1.0 - tau_C[i] / tau_old[i])) * tau_old[i] / tau_C[i])
             if u < 1.0 - tau_C[i] / tau_old[i]:
                 JC[i] = -1
                 tau_old[i] = 1.0
@@ -137,6 +141,8 @@ def css_update(cfg, batch, JC, tau_old, tau_C, JD, tau_D):
             for r in range(len(JD)):
                 p = min(max(tau_D[r] * scale, 0.0), 1.0)
                 u = float(philox.uniform(cfg.seed, batch, i, 1 + r))
+                if margins is not None and p < 1.0 and tau_D[r] > 0:
+                    margins.append(abs(u - p) / p)
                 if u < p and JD[r] not in JC:
                     JC[i] = JD[r]
                     tau_old[i] = tau_D[r]
@@ -239,6 +245,7 @@ class OnlineRID:
         self.history = []
         self._omega = None
         self._omega_g = None
+        self.margins = []
 
     # Omega is materialized once: this is the slow, obviously correct form.
     def omega(self):
@@ -310,7 +317,7 @@ class OnlineRID:
         JD = list(self.JD)
         tau_D = sketched_ridge_scores(SSt_scaled, lam, Vlev[:, JD])
         JC_prev = self.JC.copy()
-        JC, tau_old = css_update(c, self.batch, self.JC, self.tau_old, tau_C, JD, tau_D)
+        JC, tau_old = css_update(c, self.batch, self.JC, self.tau_old, tau_C, JD, tau_D, self.margins)
 
         # Coefficient candidates over the active slots (R11)
         act = np.nonzero(JC >= 0)[0]

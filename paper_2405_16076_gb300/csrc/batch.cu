@@ -1,0 +1,685 @@
+// Batch step of Algorithm 3, run on the device whenever t columns are
+// buffered (and once more for the tail): lambda (Eq. 23), sketched ridge
+// scores of C and D (Eq. 23), prune/refill of the basis slots, the basis Gram
+// G = A_J^T A_J and A_J^T A_Jprev, the coefficient candidates of Algorithms
+// 4-7, the NA-Hutch++ estimate of each (Algorithm 8, Eqs. 36-37) and the
+// commit of P = P_{q*}.  Every decision stays on the device, so the whole
+// ingest loop needs no host round trip.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "linalg.cuh"
+#include "philox.cuh"
+#include "rid_internal.cuh"
+
+namespace rid {
+
+// ---------------------------------------------------------------- work layout
+struct WorkLayout {
+  int64_t eigA, eigD, eigE, eigV, eigP;   // lambda
+  int64_t cholM;                          // s x s
+  int64_t vec;                            // per-warp vectors (scores / applies)
+  int64_t SJ, HJ, G, Gq, Gc, T;           // gathered sketch data and Grams
+  int64_t QR4, b4, h4, QR6, b6, h6;       // Householder factors
+  int64_t Z, trgpp, hut, hut_stride;      // Hutch++
+  int64_t total;
+};
+
+static constexpr int kApplyBlocks = 2 * 152;
+static constexpr int kApplyThreads = 256;
+static constexpr int kHutChunk = 32;
+
+// per-candidate scratch of hutch_finish_kernel: X, W (h1 x h2), ZG (h1 x t), J (h1 x h1),
+// Xp (h2 x h1), M1 (h1 x h3), F (h3 x h2), E (h2 x h3)
+static int64_t hut_stride(const Dev& d) {
+  const int64_t h1 = d.h1, h2 = d.h2, h3 = d.h3, t = d.t;
+  return 3 * h1 * h2 + h1 * t + h1 * h1 + 2 * h1 * h3 + 2 * h2 * h3 + 64;
+}
+
+static WorkLayout layout(const Dev& d) {
+  WorkLayout w{};
+  const int64_t s = d.s, t = d.t, hh = d.h1 + d.h2 + d.h3;
+  const int64_t nw = (int64_t)kApplyBlocks * (kApplyThreads / 32);
+  int64_t o = 0;
+  auto take = [&](int64_t n) { int64_t r = o; o += (n + 31) / 32 * 32; return r; };
+  w.eigA = take(s * s); w.eigD = take(s); w.eigE = take(s); w.eigV = take(s); w.eigP = take(s);
+  w.cholM = take(s * s);
+  w.vec = take(nw * (s > t ? s : t));
+  w.SJ = take(s * t); w.HJ = take(hh * t); w.G = take(t * t); w.Gq = take(t * t);
+  w.Gc = take(t * t); w.T = take(t * t);
+  w.QR4 = take(s * t); w.b4 = take(t); w.h4 = take(t);
+  w.QR6 = take(s * t); w.b6 = take(t); w.h6 = take(t);
+  w.Z = take(4 * hh * t); w.trgpp = take(4);
+  w.hut_stride = hut_stride(d);
+  w.hut = take(4 * w.hut_stride);
+  w.total = o;
+  return w;
+}
+
+int64_t work_doubles(const Dev& d) { return layout(d).total; }
+
+// ---------------------------------------------------------------- lambda and scores
+__global__ void __launch_bounds__(512) lambda_chol_kernel(Dev d, WorkLayout w) {
+  __shared__ double sh[33];
+  __shared__ int fail;
+  const int s = d.s, tid = threadIdx.x;
+  const double inv_s = 1.0 / (double)s;
+  if (tid == 0) fail = 0;
+  double lam;
+  if (d.lambda_mode == 1) {
+    lam = d.lambda_fixed;
+  } else {
+    double* A = d.work + w.eigA;
+    for (int64_t i = tid; i < (int64_t)s * s; i += blockDim.x) A[i] = d.SSt[i] / (double)s;
+    __syncthreads();
+    cta_tridiagonalize(A, s, s, d.work + w.eigD, d.work + w.eigE, d.work + w.eigV, d.work + w.eigP, sh);
+    // top-k eigenvalues: indices s-1 .. s-k in ascending order
+    const int k = d.t;
+    double part = 0.0;
+    for (int j = tid; j < k && j < s; j += blockDim.x)
+      part += tridiag_eig_bisect(d.work + w.eigD, d.work + w.eigE, s, s - 1 - j);
+    const double topk = block_sum(part, sh);
+    const double fro = d.fro2[1];
+    lam = (fro - topk) / (double)k;
+    lam = fmax(lam, 1e-12 * fro / (double)k);
+  }
+  if (tid == 0) d.scal[SCAL_LAMBDA] = lam;
+  double* M = d.work + w.cholM;
+  for (int64_t idx = tid; idx < (int64_t)s * s; idx += blockDim.x) {
+    const int i = (int)(idx % s), j = (int)(idx / s);
+    M[idx] = d.SSt[idx] * inv_s + ((i == j) ? lam : 0.0);
+  }
+  // tolerance: pivots below 1e-300 are treated as zero (semi-definite M when lambda == 0)
+  cta_cholesky(M, s, s, 1e-300, &fail);
+  if (tid == 0 && fail && lam > 0.0) atomicOr(d.err, ERR_CHOL);
+}
+
+// One warp per vector: occupied C slots (i < t) and buffered D columns (t <= i < t+count).
+__global__ void __launch_bounds__(kApplyThreads) scores_kernel(Dev d, WorkLayout w, int count) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int s = d.s;
+  const double rs = 1.0 / sqrt((double)s);
+  const double* L = d.work + w.cholM;
+  double* b = d.work + w.vec + (size_t)gw * (s > d.t ? s : d.t);
+  for (int v = gw; v < d.t + count; v += nwarps) {
+    int64_t col;
+    if (v < d.t) { col = d.JC[v]; if (col < 0) { if (lane == 0) d.tauC[v] = 1.0; continue; } }
+    else col = d.JD[v - d.t];
+    const double* l = d.Slev + (size_t)col * d.lev_ld;
+    for (int i = lane; i < s; i += 32) b[i] = l[i] * rs;
+    __syncwarp();
+    warp_trsv_lower(L, s, s, b);
+    double acc = 0.0;
+    for (int i = lane; i < s; i += 32) acc += b[i] * b[i];
+    acc = warp_sum(acc);
+    if (lane == 0) { if (v < d.t) d.tauC[v] = acc; else d.tauD[v - d.t] = acc; }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- prune / refill (one thread)
+__global__ void select_kernel(Dev d, int count, int batch) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int t = d.t, two_t = 2 * t;
+  for (int i = 0; i < t; ++i) {
+    if (d.JC[i] >= 0) {
+      const double tc = fmin(d.tau_old[i], d.tauC[i]);
+      const double u = sample_uniform(d.seed, (uint32_t)batch, (uint32_t)i, 0u);
+      if (u < 1.0 - tc / d.tau_old[i]) { d.JC[i] = -1; d.slotC[i] = -1; d.tau_old[i] = 1.0; }
+      else d.tau_old[i] = tc;
+    }
+    if (d.JC[i] < 0) {
+      for (int r = 0; r < count; ++r) {
+        const double p = fmin(fmax(d.tauD[r] * d.refill_scale, 0.0), 1.0);
+        const double u = sample_uniform(d.seed, (uint32_t)batch, (uint32_t)i, (uint32_t)(1 + r));
+        if (u < p) {
+          bool inC = false;
+          for (int x = 0; x < t; ++x) inC |= (d.JC[x] == d.JD[r]);
+          if (!inC) { d.JC[i] = d.JD[r]; d.slotC[i] = d.dslot[r]; d.tau_old[i] = d.tauD[r]; break; }
+        }
+      }
+    }
+  }
+  int na = 0, nn = 0, nk = 0;
+  for (int i = 0; i < t; ++i) {
+    d.posof[i] = -1;
+    if (d.JC[i] >= 0) {
+      const int is_new = !(d.JC[i] == d.JC_prev[i]);
+      d.act[na] = i;
+      d.posof[i] = na;
+      d.isnew[na] = is_new;
+      if (is_new) { d.newpos[nn] = na; d.gnew[nn++] = d.slotC[i]; } else ++nk;
+      ++na;
+    }
+  }
+  int npa = 0;
+  for (int i = 0; i < t; ++i) if (d.JC_prev[i] >= 0) d.pact[npa++] = i;
+  // Gram targets: pool slots of the current and the previous basis (distinct)
+  int nt = 0;
+  for (int a = 0; a < na; ++a) d.gtgt[nt++] = d.slotC[d.act[a]];
+  for (int b = 0; b < npa; ++b) {
+    const int ps = d.slotC_prev[d.pact[b]];
+    bool dup = false;
+    for (int x = 0; x < nt; ++x) dup |= (d.gtgt[x] == ps);
+    if (!dup) d.gtgt[nt++] = ps;
+  }
+  d.meta[META_NACT] = na; d.meta[META_NPACT] = npa; d.meta[META_NNEW] = nn;
+  d.meta[META_NTGT] = nt; d.meta[META_NKEPT] = nk;
+  // buffer slots for the next batch: the first t pool slots not used by the new basis
+  int q = 0;
+  for (int ps = 0; ps < two_t && q < t; ++ps) {
+    bool used = false;
+    for (int i = 0; i < t; ++i) used |= (d.slotC[i] == ps);
+    if (!used) d.dslot[q++] = ps;
+  }
+}
+
+// ---------------------------------------------------------------- basis Gram
+// C[x][y] = <pool[gnew[x]], pool[gtgt[y]]> over one K-range, 64x64 tile per CTA, 4x4 per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) basis_gram_kernel(Dev d) {
+  __shared__ T As[16][64 + 1];
+  __shared__ T Bs[16][64 + 1];
+  const int nnew = d.meta[META_NNEW], ntgt = d.meta[META_NTGT];
+  const int x0 = blockIdx.x * 64, y0 = blockIdx.y * 64;
+  if (x0 >= nnew || y0 >= ntgt) return;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t per = (d.m + gridDim.z - 1) / gridDim.z;
+  const int64_t k0 = (int64_t)blockIdx.z * per;
+  const int64_t k1 = (k0 + per < d.m) ? k0 + per : d.m;
+  const T* pool = (const T*)d.pool;
+  double acc64[4][4];
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc64[a][b] = 0.0; acc[a][b] = T(0); }
+  int since = 0;
+  for (int64_t kk = k0; kk < k1; kk += 16) {
+    // load 16 coordinates of 64 columns each: thread -> (coord = tid % 16, col = tid / 16 + 16 c)
+    const int kc = threadIdx.x & 15, cc = threadIdx.x >> 4;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int col = cc + 16 * c;
+      const int64_t i = kk + kc;
+      T va = T(0), vb = T(0);
+      if (i < k1) {
+        if (x0 + col < nnew) va = pool[(int64_t)d.gnew[x0 + col] * d.m_pad + i];
+        if (y0 + col < ntgt) vb = pool[(int64_t)d.gtgt[y0 + col] * d.m_pad + i];
+      }
+      As[kc][col] = va;
+      Bs[kc][col] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      T ra[4], rb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) { ra[a] = As[k][tx + 16 * a]; rb[a] = Bs[k][ty + 16 * a]; }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += ra[a] * rb[b];
+    }
+    __syncthreads();
+    if (++since == 4) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { acc64[a][b] += (double)acc[a][b]; acc[a][b] = T(0); }
+      since = 0;
+    }
+  }
+  const int two_t = 2 * d.t;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int x = x0 + tx + 16 * a, y = y0 + ty + 16 * b;
+      if (x < nnew && y < ntgt)
+        d.gpart[((size_t)blockIdx.z * d.t + x) * two_t + y] = acc64[a][b] + (double)acc[a][b];
+    }
+}
+
+__global__ void gram_reduce_kernel(Dev d, int nsplit) {
+  const int nnew = d.meta[META_NNEW], ntgt = d.meta[META_NTGT];
+  const int two_t = 2 * d.t;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.t * two_t) return;
+  const int x = idx / two_t, y = idx % two_t;
+  if (x >= nnew || y >= ntgt) return;
+  double v = 0.0;
+  for (int z = 0; z < nsplit; ++z) v += d.gpart[((size_t)z * d.t + x) * two_t + y];
+  const int a = d.gnew[x], b = d.gtgt[y];
+  d.Gp[a + (size_t)b * two_t] = v;
+  d.Gp[b + (size_t)a * two_t] = v;
+}
+
+// ---------------------------------------------------------------- gather + factorizations (one CTA)
+__global__ void __launch_bounds__(512) factor_kernel(Dev d, WorkLayout w) {
+  __shared__ double sh[33];
+  __shared__ int fail;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int s = d.s, t = d.t, two_t = 2 * t, hh = d.h1 + d.h2 + d.h3;
+  const int na = d.meta[META_NACT], npa = d.meta[META_NPACT];
+  const double rs = 1.0 / sqrt((double)s);
+  double* SJ = d.work + w.SJ;
+  double* HJ = d.work + w.HJ;
+  double* G = d.work + w.G;
+  double* Gq = d.work + w.Gq;
+  double* Gc = d.work + w.Gc;
+  double* QR4 = d.work + w.QR4;
+  double* QR6 = d.work + w.QR6;
+  if (tid == 0) fail = 0;
+  for (int64_t idx = tid; idx < (int64_t)s * na; idx += nt) {
+    const int i = (int)(idx % s), a = (int)(idx / s);
+    const double v = d.S[(size_t)d.JC[d.act[a]] * d.rows + i] * rs;
+    SJ[i + (size_t)a * s] = v;
+    QR4[i + (size_t)a * s] = v;
+  }
+  for (int64_t idx = tid; idx < (int64_t)hh * na; idx += nt) {
+    const int r = (int)(idx % hh), a = (int)(idx / hh);
+    HJ[r + (size_t)a * hh] = d.S[(size_t)d.JC[d.act[a]] * d.rows + d.hbase + r];
+  }
+  for (int64_t idx = tid; idx < (int64_t)na * na; idx += nt) {
+    const int a = (int)(idx % na), b = (int)(idx / na);
+    const double g = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC[d.act[b]] * two_t];
+    G[a + (size_t)b * na] = g;
+    Gc[a + (size_t)b * na] = g;
+  }
+  for (int64_t idx = tid; idx < (int64_t)na * npa; idx += nt) {
+    const int a = (int)(idx % na), b = (int)(idx / na);
+    Gq[a + (size_t)b * na] = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC_prev[d.pact[b]] * two_t];
+  }
+  __syncthreads();
+  // columns of the new basis elements, for Algorithm 6
+  const int nn = d.meta[META_NNEW];
+  for (int64_t idx = tid; idx < (int64_t)s * nn; idx += nt) {
+    const int i = (int)(idx % s), c = (int)(idx / s);
+    QR6[i + (size_t)c * s] = SJ[i + (size_t)d.newpos[c] * s];
+  }
+  __syncthreads();
+  cta_householder_qr(QR4, s, na, s, d.work + w.b4, d.work + w.h4, sh);
+  cta_householder_qr(QR6, s, nn, s, d.work + w.b6, d.work + w.h6, sh);
+  __shared__ double gm;
+  if (tid == 0) { double m = 0.0; for (int a = 0; a < na; ++a) m = fmax(m, Gc[a + (size_t)a * na]); gm = m; }
+  __syncthreads();
+  cta_cholesky(Gc, na, na, 1e-13 * gm, &fail);
+  // T = G^{-1} Gq (Algorithm 7 through the Gram: R^+ Q^T A_Jprev = (A_J^T A_J)^{-1} A_J^T A_Jprev)
+  double* T = d.work + w.T;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int b = wid; b < npa; b += nw) {
+    double* x = T + (size_t)b * na;
+    for (int a = lane; a < na; a += 32) x[a] = Gq[a + (size_t)b * na];
+    __syncwarp();
+    warp_trsv_lower(Gc, na, na, x);
+    warp_trsv_lower_t(Gc, na, na, x);
+  }
+}
+
+// ---------------------------------------------------------------- Algorithms 4-7, one warp per column
+__global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout w, int64_t n_obs,
+                                                              int64_t n_prev) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int s = d.s, t = d.t;
+  const int na = d.meta[META_NACT], npa = d.meta[META_NPACT];
+  const double rs = 1.0 / sqrt((double)s);
+  const double* SJ = d.work + w.SJ;
+  const double* QR4 = d.work + w.QR4;
+  const double* QR6 = d.work + w.QR6;
+  const double* Gc = d.work + w.Gc;
+  const double* T = d.work + w.T;
+  double* b = d.work + w.vec + (size_t)gw * (s > t ? s : t);
+  double* P4 = d.cand;
+  double* P5 = d.cand + (size_t)t * d.n_cap;
+  double* P6 = d.cand + 2 * (size_t)t * d.n_cap;
+  double* P7 = d.cand + 3 * (size_t)t * d.n_cap;
+  // rank tolerance of R: max(s, na) * eps * |largest diagonal|
+  double rmax = 0.0;
+  for (int a = 0; a < na; ++a) rmax = fmax(rmax, fabs(QR4[a + (size_t)a * s]));
+  const double tol4 = (double)(s > na ? s : na) * 2.220446049250313e-16 * rmax;
+  const int nn = d.meta[META_NNEW];
+  double rmax6 = 0.0;
+  for (int c = 0; c < nn; ++c) rmax6 = fmax(rmax6, fabs(QR6[c + (size_t)c * s]));
+  const double tol6 = (double)(s > nn ? s : nn) * 2.220446049250313e-16 * rmax6;
+  for (int64_t j = gw; j < n_obs; j += nwarps) {
+    const double* sa = d.S + (size_t)j * d.rows;
+    // Algorithm 4 (Eq. 24): P4(:, j) = (Omega A_J)^+ Omega a_j via Householder QR
+    for (int i = lane; i < s; i += 32) b[i] = sa[i] * rs;
+    __syncwarp();
+    warp_apply_qt(QR4, s, na, s, d.work + w.b4, d.work + w.h4, b);
+    warp_trsv_upper(QR4, na, s, b, tol4);
+    for (int a = lane; a < na; a += 32) P4[a + (size_t)j * t] = b[a];
+    __syncwarp();
+    // Algorithm 5: P5(:, j) = G^{-1} (Omega A_J)^T Omega a_j
+    for (int a = 0; a < na; ++a) {
+      double acc = 0.0;
+      for (int i = lane; i < s; i += 32) acc += SJ[i + (size_t)a * s] * sa[i] * rs;
+      acc = warp_sum(acc);
+      if (lane == 0) b[a] = acc;
+    }
+    __syncwarp();
+    warp_trsv_lower(Gc, na, na, b);
+    warp_trsv_lower_t(Gc, na, na, b);
+    for (int a = lane; a < na; a += 32) P5[a + (size_t)j * t] = b[a];
+    __syncwarp();
+    // Algorithm 6 (Eqs. 27-30): keep the rows of unchanged basis elements, refit the new
+    // ones on the sketched residual.  Previous coefficients of columns observed since the
+    // last batch step are the preliminary estimate P4.
+    for (int i = lane; i < s; i += 32) {
+      double r = sa[i] * rs;
+      for (int a = 0; a < na; ++a) {
+        if (d.isnew[a]) continue;
+        const double pp = (j < n_prev) ? d.P[d.act[a] + (size_t)j * t] : P4[a + (size_t)j * t];
+        r -= SJ[i + (size_t)a * s] * pp;
+      }
+      b[i] = r;
+    }
+    __syncwarp();
+    warp_apply_qt(QR6, s, nn, s, d.work + w.b6, d.work + w.h6, b);
+    warp_trsv_upper(QR6, nn, s, b, tol6);
+    if (lane == 0) {
+      int c = 0;
+      for (int a = 0; a < na; ++a) {
+        double v;
+        if (d.isnew[a]) v = b[c++];
+        else v = (j < n_prev) ? d.P[d.act[a] + (size_t)j * t] : P4[a + (size_t)j * t];
+        P6[a + (size_t)j * t] = v;
+      }
+    }
+    __syncwarp();
+    // Algorithm 7 (Eqs. 31-32): P7 = T P_prev on the previous columns, P4 on the new ones
+    for (int a = lane; a < na; a += 32) {
+      double v;
+      if (j < n_prev) {
+        v = 0.0;
+        for (int c = 0; c < npa; ++c) v += T[a + (size_t)c * na] * d.P[d.pact[c] + (size_t)j * t];
+      } else {
+        v = P4[a + (size_t)j * t];
+      }
+      P7[a + (size_t)j * t] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- NA-Hutch++ (Algorithm 8)
+// grid (ceil(n_obs / kHutChunk), 4): partial Z_q = H P_q^T over a column chunk, and tr(G P P^T).
+__global__ void __launch_bounds__(256) hutch_partial_kernel(Dev d, WorkLayout w, int64_t n_obs) {
+  __shared__ double sh[33];
+  const int q = blockIdx.y;
+  const int na = d.meta[META_NACT];
+  const int hh = d.h1 + d.h2 + d.h3;
+  const int t = d.t;
+  const double* Pq = d.cand + (size_t)q * t * d.n_cap;
+  const int64_t j0 = (int64_t)blockIdx.x * kHutChunk;
+  const int64_t j1 = (j0 + kHutChunk < n_obs) ? j0 + kHutChunk : n_obs;
+  double* out = d.hpart + ((size_t)q * gridDim.x + blockIdx.x) * ((size_t)hh * t + 1);
+  for (int idx = threadIdx.x; idx < hh * na; idx += blockDim.x) {
+    const int r = idx % hh, a = idx / hh;
+    double acc = 0.0;
+    for (int64_t j = j0; j < j1; ++j) acc += d.S[(size_t)j * d.rows + d.hbase + r] * Pq[a + (size_t)j * t];
+    out[idx] = acc;
+  }
+  const double* G = d.work + w.G;
+  double part = 0.0;
+  for (int idx = threadIdx.x; idx < na * (int)(j1 - j0); idx += blockDim.x) {
+    const int a = idx % na;
+    const int64_t j = j0 + idx / na;
+    double gp = 0.0;
+    for (int c = 0; c < na; ++c) gp += G[a + (size_t)c * na] * Pq[c + (size_t)j * t];
+    part += gp * Pq[a + (size_t)j * t];
+  }
+  const double tot = block_sum(part, sh);
+  if (threadIdx.x == 0) out[(size_t)hh * t] = tot;
+}
+
+// Pseudo-inverse of the small p x q matrix X (p <= q, row-major in Y) by one-sided Jacobi
+// on its rows; writes Xp (q x p, row-major).  Single warp.
+__device__ void warp_pinv_rows(double* Y, double* J, int p, int q, double* Xp, double rcond) {
+  const int lane = threadIdx.x & 31;
+  for (int idx = lane; idx < p * p; idx += 32) J[idx] = (idx % (p + 1) == 0) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int a = 0; a < p; ++a)
+      for (int c = a + 1; c < p; ++c) {
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int k = lane; k < q; k += 32) {
+          const double ya = Y[a * q + k], yc = Y[c * q + k];
+          al += ya * ya; be += yc * yc; ga += ya * yc;
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (al == 0.0 || be == 0.0) continue;
+        const double rel = fabs(ga) / sqrt(al * be);
+        off = fmax(off, rel);
+        if (rel < 1e-15) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double tt = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        __syncwarp();
+        for (int k = lane; k < q; k += 32) {
+          const double ya = Y[a * q + k], yc = Y[c * q + k];
+          Y[a * q + k] = cs * ya - sn * yc;
+          Y[c * q + k] = sn * ya + cs * yc;
+        }
+        for (int k = lane; k < p; k += 32) {
+          const double ja = J[k * p + a], jc = J[k * p + c];
+          J[k * p + a] = cs * ja - sn * jc;
+          J[k * p + c] = sn * ja + cs * jc;
+        }
+        __syncwarp();
+      }
+    if (off < 1e-15) break;
+  }
+  // sigma_i = ||Y_i||; X^+ = Y^T diag(1/sigma^2) J^T for sigma_i > rcond * sigma_max
+  double smax = 0.0;
+  for (int a = 0; a < p; ++a) {
+    double nr = 0.0;
+    for (int k = lane; k < q; k += 32) nr += Y[a * q + k] * Y[a * q + k];
+    nr = warp_sum(nr);
+    smax = fmax(smax, sqrt(nr));
+  }
+  for (int idx = lane; idx < q * p; idx += 32) Xp[idx] = 0.0;
+  __syncwarp();
+  for (int a = 0; a < p; ++a) {
+    double nr = 0.0;
+    for (int k = lane; k < q; k += 32) nr += Y[a * q + k] * Y[a * q + k];
+    nr = warp_sum(nr);
+    const double sg = sqrt(nr);
+    if (!(sg > rcond * smax) || sg == 0.0) continue;
+    const double inv = 1.0 / nr;
+    for (int idx = lane; idx < q * p; idx += 32) {
+      const int k = idx / p, c = idx % p;      // Xp[k][c] += Y[a][k] / sigma^2 * J[c][a]
+      Xp[idx] += Y[a * q + k] * inv * J[c * p + a];
+    }
+    __syncwarp();
+  }
+}
+
+// One CTA per candidate: reduce the partials and evaluate Eqs. 36-37.
+__global__ void __launch_bounds__(256) hutch_finish_kernel(Dev d, WorkLayout w, int nchunk) {
+  __shared__ double sh[33];
+  const int q = blockIdx.x;
+  const int na = d.meta[META_NACT];
+  const int h1 = d.h1, h2 = d.h2, h3 = d.h3, hh = h1 + h2 + h3;
+  const int t = d.t;
+  double* Z = d.work + w.Z + (size_t)q * hh * t;
+  const double* HJ = d.work + w.HJ;
+  const double* G = d.work + w.G;
+  double* hut = d.work + w.hut + (size_t)q * w.hut_stride;
+  for (int idx = threadIdx.x; idx < hh * na; idx += blockDim.x) {
+    double v = 0.0;
+    for (int c = 0; c < nchunk; ++c) v += d.hpart[((size_t)q * nchunk + c) * ((size_t)hh * t + 1) + idx];
+    Z[idx] = v;                                   // Z[r + a*hh] = (Omega A_obs P^T)[r][a]
+  }
+  double trg = 0.0;
+  if (threadIdx.x == 0)
+    for (int c = 0; c < nchunk; ++c) trg += d.hpart[((size_t)q * nchunk + c) * ((size_t)hh * t + 1) + (size_t)hh * t];
+  __syncthreads();
+  // views: Zi rows [o_i, o_i + h_i) of Z and HJ
+  const int o1 = 0, o2 = h1, o3 = h1 + h2;
+  double* X = hut;                    // h1 x h2 row-major
+  double* W = X + h1 * h2;            // h1 x h2 row-major: Z1 G Z2^T
+  double* ZG = W + h1 * h2;           // h1 x na row-major
+  double* Jm = ZG + (size_t)h1 * t;   // h1 x h1
+  double* Xp = Jm + h1 * h1;          // h2 x h1 row-major
+  double* M1 = Xp + h2 * h1;          // h1 x h3 row-major: Z1 K3^T
+  double* F = M1 + h1 * h3;           // h3 x h2 row-major: K3 Z2^T
+  double* E = F + h3 * h2;            // h2 x h3 row-major: Xp M1
+  double term1 = 0.0, corr = 0.0;
+  if (h1 > 0 && h2 > 0) {
+    for (int idx = threadIdx.x; idx < h1 * h2; idx += blockDim.x) {
+      const int a = idx / h2, b = idx % h2;
+      double acc = 0.0;
+      for (int c = 0; c < na; ++c) acc += Z[(o1 + a) + (size_t)c * hh] * HJ[(o2 + b) + (size_t)c * hh];
+      X[idx] = acc;
+    }
+    for (int idx = threadIdx.x; idx < h1 * na; idx += blockDim.x) {
+      const int a = idx / na, c = idx % na;
+      double acc = 0.0;
+      for (int e = 0; e < na; ++e) acc += Z[(o1 + a) + (size_t)e * hh] * G[e + (size_t)c * na];
+      ZG[idx] = acc;
+    }
+    for (int idx = threadIdx.x; idx < h1 * h3; idx += blockDim.x) {
+      const int a = idx / h3, r = idx % h3;
+      double acc = 0.0;
+      for (int c = 0; c < na; ++c) acc += Z[(o1 + a) + (size_t)c * hh] * HJ[(o3 + r) + (size_t)c * hh];
+      M1[idx] = acc;
+    }
+    for (int idx = threadIdx.x; idx < h3 * h2; idx += blockDim.x) {
+      const int r = idx / h2, b = idx % h2;
+      double acc = 0.0;
+      for (int c = 0; c < na; ++c) acc += HJ[(o3 + r) + (size_t)c * hh] * Z[(o2 + b) + (size_t)c * hh];
+      F[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < h1 * h2; idx += blockDim.x) {
+      const int a = idx / h2, b = idx % h2;
+      double acc = 0.0;
+      for (int c = 0; c < na; ++c) acc += ZG[a * na + c] * Z[(o2 + b) + (size_t)c * hh];
+      W[idx] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int mx = (h1 > h2) ? h1 : h2;
+      warp_pinv_rows(X, Jm, h1, h2, Xp, (double)mx * 2.220446049250313e-16);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < h2 * h3; idx += blockDim.x) {
+      const int a = idx / h3, r = idx % h3;
+      double acc = 0.0;
+      for (int b = 0; b < h1; ++b) acc += Xp[a * h1 + b] * M1[b * h3 + r];
+      E[idx] = acc;
+    }
+    __syncthreads();
+    double p1 = 0.0;
+    for (int idx = threadIdx.x; idx < h2 * h1; idx += blockDim.x) {
+      const int a = idx / h1, b = idx % h1;
+      p1 += Xp[idx] * W[b * h2 + a];
+    }
+    term1 = block_sum(p1, sh);
+    double p2 = 0.0;
+    for (int idx = threadIdx.x; idx < h3 * h2; idx += blockDim.x) {
+      const int r = idx / h2, a = idx % h2;
+      p2 += F[idx] * E[a * h3 + r];
+    }
+    corr = block_sum(p2, sh);
+  }
+  double p3 = 0.0;
+  for (int idx = threadIdx.x; idx < h3 * na; idx += blockDim.x) {
+    const int r = idx % h3, c = idx / h3;
+    p3 += Z[(o3 + r) + (size_t)c * hh] * HJ[(o3 + r) + (size_t)c * hh];
+  }
+  const double direct = block_sum(p3, sh);
+  if (threadIdx.x == 0) {
+    const double cross = term1 + (direct - corr) / (double)h3;
+    d.scal[SCAL_EST + q] = d.fro2[0] - 2.0 * cross + trg;
+  }
+}
+
+// ---------------------------------------------------------------- commit P = P_{q*}
+__device__ __forceinline__ int argmin4(const double* e) {
+  int q = 0;
+  for (int i = 1; i < 4; ++i) if (e[i] < e[q]) q = i;
+  return q;
+}
+
+__global__ void commit_kernel(Dev d, int64_t n_obs) {
+  const int t = d.t;
+  const int q = argmin4(d.scal + SCAL_EST);
+  const double* Pq = d.cand + (size_t)q * t * d.n_cap;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)t * n_obs;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % t);
+    const int64_t j = idx / t;
+    const int a = d.posof[i];
+    d.P[i + (size_t)j * t] = (a >= 0) ? Pq[a + (size_t)j * t] : 0.0;
+  }
+}
+
+__global__ void finish_kernel(Dev d, int batch, int64_t n_obs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  d.meta[META_QSTAR] = 4 + argmin4(d.scal + SCAL_EST);
+  for (int i = 0; i < d.t; ++i) { d.JC_prev[i] = d.JC[i]; d.slotC_prev[i] = d.slotC[i]; }
+  d.meta[META_BATCH] = batch + 1;
+  d.meta[META_NPREV] = (int)n_obs;
+}
+
+__global__ void reset_kernel(Dev d) {
+  const int t = d.t;
+  for (int i = threadIdx.x; i < t; i += blockDim.x) {
+    d.JC[i] = -1; d.JC_prev[i] = -1; d.slotC[i] = -1; d.slotC_prev[i] = -1;
+    d.dslot[i] = i; d.tau_old[i] = 1.0; d.JD[i] = -1;
+  }
+  if (threadIdx.x == 0) {
+    d.fro2[0] = 0.0; d.fro2[1] = 0.0;
+    for (int i = 0; i < META_LEN; ++i) d.meta[i] = 0;
+    for (int i = 0; i < SCAL_LEN; ++i) d.scal[i] = 0.0;
+    *d.err = 0;
+  }
+}
+
+__global__ void set_jd_kernel(Dev d, int count, int nb, int64_t n_obs) {
+  const int q = threadIdx.x;
+  if (q < nb) d.JD[count + q] = n_obs + q;
+}
+
+int launch_set_jd(const Dev& d, int count, int nb, int64_t n_obs, cudaStream_t st) {
+  set_jd_kernel<<<1, 32, 0, st>>>(d, count, nb, n_obs);
+  return 1;
+}
+
+int launch_reset_state(const Dev& d, cudaStream_t st) {
+  reset_kernel<<<1, 256, 0, st>>>(d);
+  cudaMemsetAsync(d.SSt, 0, sizeof(double) * (size_t)d.s * d.s, st);
+  cudaMemsetAsync(d.Gp, 0, sizeof(double) * (size_t)4 * d.t * d.t, st);
+  return 1;
+}
+
+int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
+                      cudaStream_t st) {
+  const WorkLayout w = layout(d);
+  lambda_chol_kernel<<<1, 512, 0, st>>>(d, w);
+  const int nvec = d.t + count;
+  scores_kernel<<<(nvec + 7) / 8, kApplyThreads, 0, st>>>(d, w, count);
+  select_kernel<<<1, 32, 0, st>>>(d, count, batch);
+  dim3 gg((d.t + 63) / 64, (2 * d.t + 63) / 64, d.gram_split);
+  if (d.dtype == 0) basis_gram_kernel<double><<<gg, 256, 0, st>>>(d);
+  else basis_gram_kernel<float><<<gg, 256, 0, st>>>(d);
+  gram_reduce_kernel<<<(d.t * 2 * d.t + 255) / 256, 256, 0, st>>>(d, d.gram_split);
+  factor_kernel<<<1, 512, 0, st>>>(d, w);
+  coeff_kernel<<<kApplyBlocks, kApplyThreads, 0, st>>>(d, w, n_obs, n_prev);
+  const int nchunk = (int)((n_obs + kHutChunk - 1) / kHutChunk);
+  hutch_partial_kernel<<<dim3(nchunk, 4), 256, 0, st>>>(d, w, n_obs);
+  hutch_finish_kernel<<<4, 256, 0, st>>>(d, w, nchunk);
+  commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
+  finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
+  return 12;
+}
+
+}  // namespace rid

@@ -1,0 +1,204 @@
+// Ingest path of Algorithm 3: for a block of nb columns, one read of each
+// column produces (i) the copy into its buffer slot d_count, (ii) the squared
+// norms for ||A_obs||_F^2 and (iii) the sketch s_j = Omega a_j for all s left
+// rows and h probe rows, with Omega generated on chip from the counter-based
+// generator (Rademacher) or read from its materialized transpose (Gaussian).
+// A deterministic split-K reduction then appends the sketches to S and
+// updates SS^T and ||A_obs||^2 in column order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "philox.cuh"
+#include "rid_internal.cuh"
+
+namespace rid {
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { using type = double; };
+template <> struct Acc<float> { using type = float; };
+
+__device__ __forceinline__ double flip_sign(double x, uint32_t bit) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((unsigned long long)bit << 63));
+}
+__device__ __forceinline__ float flip_sign(float x, uint32_t bit) {
+  return __int_as_float(__float_as_int(x) ^ (bit << 31));
+}
+
+// grid: (n_sketch_blocks, ceil(rows/256)); block: 256 threads.
+// Thread tid of row-group y owns sketch row r = 256*y + tid.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kSketchThreads)
+ingest_sketch_kernel(Dev d, const T* __restrict__ src, int64_t ld, int nb, int count) {
+  __shared__ T X[NB][kChunk];
+  __shared__ int dst[NB];
+  __shared__ double red[kSketchThreads / 32][NB];
+  const int tid = threadIdx.x;
+  const int r = blockIdx.y * kSketchThreads + tid;
+  const bool row_ok = r < d.rows;
+  const bool lead = blockIdx.y == 0;
+  if (tid < NB) dst[tid] = (tid < nb) ? d.dslot[count + tid] : 0;
+  __syncthreads();
+  T* pool = (T*)d.pool;
+  const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+
+  double acc64[NB];
+  T acc[NB];
+  double nrm[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) { acc64[q] = 0.0; acc[q] = T(0); nrm[q] = 0.0; }
+
+  const int64_t nchunks = (d.m + kChunk - 1) / kChunk;
+  int since_flush = 0;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int64_t i0 = c * kChunk;
+    const int64_t i = i0 + tid;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      if (q < nb) {
+        T v = T(0);
+        if (i < d.m) {
+          v = src[(int64_t)q * ld + i];
+          if (lead) pool[(int64_t)dst[q] * d.m_pad + i] = v;
+        }
+        X[q][tid] = v;
+        nrm[q] += (double)v * (double)v;
+      }
+    }
+    __syncthreads();
+    if (row_ok) {
+      if (d.omega_kind == 1) {
+        // Rademacher: 2 Philox calls cover the 256 coordinates of the chunk
+#pragma unroll 1
+        for (int half = 0; half < kChunk / 128; ++half) {
+          const uint32_t blk = (uint32_t)((i0 >> 7) + half);
+          const u32x4 w = philox4x32_10(blk, (uint32_t)r, kTagRademacher, 0, k0, k1);
+          const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int wi = 0; wi < 4; ++wi) {
+            const uint32_t bits = words[wi];
+#pragma unroll 8
+            for (int b = 0; b < 32; ++b) {
+              const uint32_t bit = (bits >> b) & 1u;
+              const int ii = half * 128 + wi * 32 + b;
+#pragma unroll
+              for (int q = 0; q < NB; ++q)
+                if (q < nb) acc[q] += flip_sign(X[q][ii], bit);
+            }
+          }
+        }
+      } else {
+        const double* om = d.omegaT + (size_t)i0 * d.rows + r;
+#pragma unroll 4
+        for (int ii = 0; ii < kChunk; ++ii) {
+          if (i0 + ii >= d.m) break;
+          const T w = (T)om[(size_t)ii * d.rows];
+#pragma unroll
+          for (int q = 0; q < NB; ++q)
+            if (q < nb) acc[q] += w * X[q][ii];
+        }
+      }
+    }
+    if (++since_flush == 4) {
+#pragma unroll
+      for (int q = 0; q < NB; ++q) { acc64[q] += (double)acc[q]; acc[q] = T(0); }
+      since_flush = 0;
+    }
+    __syncthreads();
+  }
+  if (row_ok) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (q < nb)
+        d.spart[((size_t)blockIdx.x * nb + q) * d.rows + r] = acc64[q] + (double)acc[q];
+  }
+  if (lead) {
+    // deterministic block reduction of the squared norms
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      double v = nrm[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][q] = v;
+    }
+    __syncthreads();
+    if (tid < nb) {
+      double v = 0.0;
+      for (int w = 0; w < kSketchThreads / 32; ++w) v += red[w][tid];
+      d.npart[(size_t)blockIdx.x * nb + tid] = v;
+    }
+  }
+}
+
+// One thread per (q, r): sum the split-K partials in block order, append S(:, n_obs+q).
+__global__ void sketch_reduce_kernel(Dev d, int nb, int64_t n_obs, int nblk) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < nb * d.rows) {
+    const int q = idx / d.rows, r = idx % d.rows;
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += d.spart[((size_t)b * nb + q) * d.rows + r];
+    d.S[(size_t)(n_obs + q) * d.rows + r] = v;
+  }
+  if (idx == 0) {
+    for (int q = 0; q < nb; ++q) {
+      double v = 0.0;
+      for (int b = 0; b < nblk; ++b) v += d.npart[(size_t)b * nb + q];
+      if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
+      d.fro2[0] += v;
+      d.fro2[1] += v;
+    }
+  }
+}
+
+// SS^T += sum_q l_q l_q^T over the new leverage-sketch columns, in column order.
+__global__ void gram_update_kernel(Dev d, int nb, int64_t n_obs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = d.s;
+  if (idx >= (int64_t)s * s) return;
+  const int i = (int)(idx % s), j = (int)(idx / s);
+  double v = d.SSt[idx];
+  for (int q = 0; q < nb; ++q) {
+    const double* l = d.Slev + (size_t)(n_obs + q) * d.lev_ld;
+    v += l[i] * l[j];
+  }
+  d.SSt[idx] = v;
+}
+
+__global__ void materialize_omega_kernel(Dev d) {
+  const int64_t n = d.m_pad * d.rows;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / d.rows;
+    const int r = (int)(idx % d.rows);
+    d.omegaT[idx] = (i < d.m) ? gauss_entry(d.seed, kTagGauss, (uint32_t)r, (uint64_t)i) : 0.0;
+  }
+}
+
+void launch_materialize_omega(const Dev& d, cudaStream_t st) {
+  materialize_omega_kernel<<<4 * 152, 256, 0, st>>>(d);
+}
+
+int launch_ingest(const Dev& d, const void* src, int64_t ld, int nb, int count, int64_t n_obs,
+                  cudaStream_t st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  dim3 grid(d.n_sketch_blocks, (d.rows + kSketchThreads - 1) / kSketchThreads);
+  if (d.dtype == 0) {
+    if (nb == 1)
+      ingest_sketch_kernel<double, 1><<<grid, kSketchThreads, 0, st>>>(d, (const double*)src, ld, nb, count);
+    else
+      ingest_sketch_kernel<double, kMaxB><<<grid, kSketchThreads, 0, st>>>(d, (const double*)src, ld, nb, count);
+  } else {
+    if (nb == 1)
+      ingest_sketch_kernel<float, 1><<<grid, kSketchThreads, 0, st>>>(d, (const float*)src, ld, nb, count);
+    else
+      ingest_sketch_kernel<float, kMaxB><<<grid, kSketchThreads, 0, st>>>(d, (const float*)src, ld, nb, count);
+  }
+  if (ev) cudaEventRecord(ev[1], st);
+  const int n = nb * d.rows;
+  sketch_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, nb, n_obs, d.n_sketch_blocks);
+  const int64_t ns = (int64_t)d.s * d.s;
+  gram_update_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(d, nb, n_obs);
+  if (ev) cudaEventRecord(ev[2], st);
+  return 3;
+}
+
+}  // namespace rid

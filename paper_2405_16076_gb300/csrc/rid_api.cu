@@ -1,0 +1,493 @@
+// Host side of the C ABI declared in include/rid.h: validation, device
+// allocation, and the column-counting state machine of Algorithm 3 that
+// issues the ingest launches and, every t columns, the device batch step.
+// The host never reads device state while ingesting, so a whole stream can
+// be enqueued (or captured) without synchronization.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rid.h"
+#include "rid_internal.cuh"
+
+using rid::Dev;
+
+struct rid_handle {
+  rid_config cfg;
+  Dev d;
+  cudaStream_t st;
+  int count;          // columns buffered since the last batch step
+  int64_t n_obs;      // columns ingested
+  int64_t n_prev;     // columns covered by the last batch step
+  int batch;          // batch steps run
+  bool finalized;
+  size_t esize;
+  void* staging;
+  std::string err;
+  int n_sm;
+  // measurement (rid_profile)
+  bool prof;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[3];
+  int64_t kernels[3];
+};
+
+static thread_local std::string g_init_err;
+
+namespace {
+
+int fail(rid_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_init_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? RID_ENOMEM : RID_ECUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+void free_all(Dev& d, void* staging) {
+  void* ptrs[] = {d.pool, d.omegaT, d.omegagT, d.S, d.SSt, d.fro2, d.JC, d.JC_prev, d.slotC,
+                  d.slotC_prev, d.dslot, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
+                  d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
+                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, staging};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
+}
+
+int64_t hpart_len(const Dev& d, int64_t ncap) {
+  const int64_t hh = d.h1 + d.h2 + d.h3;
+  return 4 * ((ncap + 31) / 32) * (hh * d.t + 1);
+}
+
+// (Re)allocate the arrays whose size follows the column capacity, keeping S, Slev and P.
+int grow(rid_handle* h, int64_t need) {
+  Dev& d = h->d;
+  if (need <= d.n_cap && d.S) return RID_OK;
+  int64_t cap = d.n_cap > 0 ? d.n_cap : 1;
+  while (cap < need) cap *= 2;
+  CK(cudaStreamSynchronize(h->st));
+  double *S, *Slev = nullptr, *P, *cand, *hpart;
+  CK(dalloc(&S, (size_t)d.rows * cap));
+  if (d.grad) CK(dalloc(&Slev, (size_t)d.s * cap));
+  CK(dalloc(&P, (size_t)d.t * cap));
+  CK(dalloc(&cand, (size_t)4 * d.t * cap));
+  CK(dalloc(&hpart, (size_t)hpart_len(d, cap)));
+  CK(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)d.t * cap, h->st));
+  CK(cudaMemsetAsync(cand, 0, sizeof(double) * (size_t)4 * d.t * cap, h->st));
+  if (d.S) {
+    CK(cudaMemcpyAsync(S, d.S, sizeof(double) * (size_t)d.rows * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
+    if (d.grad) CK(cudaMemcpyAsync(Slev, d.Slev, sizeof(double) * (size_t)d.s * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(P, d.P, sizeof(double) * (size_t)d.t * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    cudaFree(d.S);
+    if (d.grad) cudaFree(d.Slev);
+    cudaFree(d.P);
+    cudaFree(d.cand);
+    cudaFree(d.hpart);
+  }
+  d.S = S;
+  d.Slev = d.grad ? Slev : S;
+  d.P = P;
+  d.cand = cand;
+  d.hpart = hpart;
+  d.n_cap = cap;
+  return RID_OK;
+}
+
+cudaEvent_t next_event(rid_handle* h) {
+  if (h->evused == h->evpool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->evpool.push_back(e);
+  }
+  return h->evpool[h->evused++];
+}
+
+int run_batch(rid_handle* h) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->prof) { e0 = next_event(h); e1 = next_event(h); cudaEventRecord(e0, h->st); }
+  const int nk = rid::launch_batch_step(h->d, h->count, h->n_obs, h->n_prev, h->batch, h->st);
+  if (h->prof) {
+    cudaEventRecord(e1, h->st);
+    h->spans[2].push_back({e0, e1});
+    h->kernels[2] += nk;
+  }
+  h->n_prev = h->n_obs;
+  h->batch += 1;
+  h->count = 0;
+  CK(cudaGetLastError());
+  return RID_OK;
+}
+
+int check_device_error(rid_handle* h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (e & rid::ERR_NONFINITE) return fail(h, RID_ENONFINITE, "a non-finite snapshot was ingested");
+  return RID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rid_config_default(rid_config* cfg) {
+  if (!cfg) return RID_EINVAL;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->c1 = 1.0 / 6.0;
+  cfg->c2 = 1.0 / 3.0;
+  cfg->eps = 0.5;
+  cfg->delta = 0.05;
+  cfg->c_const = 1.0;
+  cfg->lambda_mode = RID_LAMBDA_STREAMING;
+  cfg->omega_kind = RID_OMEGA_RADEMACHER;
+  cfg->data_dtype = RID_F32;
+  cfg->sketch_prec = RID_SKETCH_NATIVE;
+  cfg->n_max = 1024;
+  return RID_OK;
+}
+
+int rid_init(rid_handle** out, const rid_config* c) {
+  rid_handle* h = nullptr;
+  if (!out || !c) return fail(h, RID_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (c->m < 1) return fail(h, RID_EINVAL, "m must be >= 1");
+  if (c->k < 1 || c->k > 1024) return fail(h, RID_EINVAL, "k must be in [1, 1024]");
+  if (c->s <= c->k || c->s > 4096) return fail(h, RID_EINVAL, "s must satisfy k < s <= 4096");
+  if (c->h < 0 || c->h > 1024 || (c->h > 0 && c->h < 3)) return fail(h, RID_EINVAL, "h must be 0 or in [3, 1024]");
+  if (!(c->c1 > 0.0) || !(c->c2 > c->c1) || !(c->c1 + c->c2 < 1.0))
+    return fail(h, RID_EINVAL, "need 0 < c1 < c2 and c1 + c2 < 1");
+  if (!(c->eps > 0.0) || !(c->delta > 0.0 && c->delta < 1.0) || !(c->c_const > 0.0))
+    return fail(h, RID_EINVAL, "need eps > 0, 0 < delta < 1, c_const > 0");
+  if (c->lambda_mode != RID_LAMBDA_STREAMING && c->lambda_mode != RID_LAMBDA_FIXED)
+    return fail(h, RID_EINVAL, "unknown lambda_mode");
+  if (c->lambda_mode == RID_LAMBDA_FIXED && !(c->lambda_fixed >= 0.0))
+    return fail(h, RID_EINVAL, "lambda_fixed must be >= 0");
+  if (c->omega_kind != RID_OMEGA_GAUSSIAN && c->omega_kind != RID_OMEGA_RADEMACHER)
+    return fail(h, RID_EINVAL, "unknown omega_kind");
+  if (c->data_dtype != RID_F64 && c->data_dtype != RID_F32) return fail(h, RID_EINVAL, "unknown data_dtype");
+  if (c->sketch_prec != RID_SKETCH_NATIVE) return fail(h, RID_EINVAL, "this build supports sketch_prec = NATIVE");
+  if (c->grad_dims != 0) return fail(h, RID_EINVAL, "this build supports grad_dims = 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(h, RID_ENOLIB, "no CUDA device");
+  }
+  h = new (std::nothrow) rid_handle();
+  if (!h) return fail(nullptr, RID_ENOMEM, "host allocation failed");
+  h->cfg = *c;
+  h->st = (cudaStream_t)c->cuda_stream;
+  h->esize = c->data_dtype == RID_F64 ? 8 : 4;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  Dev& d = h->d;
+  memset(&d, 0, sizeof(d));
+  d.m = c->m;
+  d.m_pad = (c->m + 63) / 64 * 64;
+  d.t = c->k;
+  d.s = c->s;
+  d.h = c->h;
+  d.rows = c->s + c->h;
+  const int nprobe = c->h > 0 ? c->h : c->s;
+  d.hbase = c->h > 0 ? c->s : 0;
+  d.h1 = (int)floor(c->c1 * nprobe);
+  d.h2 = (int)floor(c->c2 * nprobe);
+  d.h3 = nprobe - d.h1 - d.h2;
+  if (d.h3 < 1) { delete h; return fail(nullptr, RID_EINVAL, "empty Omega_3 split"); }
+  d.dtype = c->data_dtype == RID_F64 ? 0 : 1;
+  d.omega_kind = c->omega_kind == RID_OMEGA_RADEMACHER ? 1 : 0;
+  d.lambda_mode = c->lambda_mode == RID_LAMBDA_FIXED ? 1 : 0;
+  d.lambda_fixed = c->lambda_fixed;
+  const double k = (double)c->k;
+  d.refill_scale = c->c_const * (k * log(k) + k * log(1.0 / c->delta) / c->eps) / (double)c->k;
+  d.seed = c->seed;
+  d.grad = 0;
+  d.lev_ld = d.rows;
+  const int64_t nchunks = (d.m + rid::kChunk - 1) / rid::kChunk;
+  d.n_sketch_blocks = (int)(nchunks < 4 * h->n_sm ? nchunks : 4 * h->n_sm);
+  int64_t gs = (d.m + 16383) / 16384;
+  d.gram_split = (int)(gs < 1 ? 1 : (gs > 256 ? 256 : gs));
+  const int t = d.t;
+  int rc = RID_OK;
+#define AL(ptr, n) do { if (dalloc(&(ptr), (size_t)(n)) != cudaSuccess) { rc = RID_ENOMEM; goto fail_alloc; } } while (0)
+  {
+    char* pool = nullptr;
+    AL(pool, (size_t)2 * t * d.m_pad * h->esize);
+    d.pool = pool;
+    if (cudaMemset(d.pool, 0, (size_t)2 * t * d.m_pad * h->esize) != cudaSuccess) { rc = RID_ECUDA; goto fail_alloc; }
+  }
+  if (d.omega_kind == 0) AL(d.omegaT, (size_t)d.m_pad * d.rows);
+  AL(d.SSt, (size_t)d.s * d.s);
+  AL(d.fro2, 2);
+  AL(d.JC, t); AL(d.JC_prev, t); AL(d.JD, t);
+  AL(d.slotC, t); AL(d.slotC_prev, t); AL(d.dslot, t);
+  AL(d.tau_old, t); AL(d.tauC, t); AL(d.tauD, t);
+  AL(d.meta, rid::META_LEN); AL(d.scal, rid::SCAL_LEN);
+  AL(d.act, t); AL(d.pact, t); AL(d.isnew, t); AL(d.posof, t); AL(d.newpos, t);
+  AL(d.gnew, t); AL(d.gtgt, 2 * t);
+  AL(d.Gp, (size_t)4 * t * t);
+  AL(d.gpart, (size_t)d.gram_split * t * 2 * t);
+  AL(d.spart, (size_t)d.n_sketch_blocks * rid::kMaxB * d.rows);
+  AL(d.npart, (size_t)d.n_sketch_blocks * rid::kMaxB);
+  AL(d.err, 1);
+  d.work_len = rid::work_doubles(d);
+  AL(d.work, d.work_len);
+  {
+    char* stg = nullptr;
+    AL(stg, (size_t)rid::kMaxB * d.m_pad * h->esize);
+    h->staging = stg;
+  }
+#undef AL
+  {
+    int64_t want = c->n_max > 0 ? c->n_max : 1024;
+    rc = grow(h, want);
+    if (rc != RID_OK) goto fail_alloc;
+  }
+  if (d.omega_kind == 0) rid::launch_materialize_omega(d, h->st);
+  rid::launch_reset_state(d, h->st);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->st) != cudaSuccess) {
+    rc = RID_ECUDA;
+    goto fail_alloc;
+  }
+  *out = h;
+  return RID_OK;
+fail_alloc:
+  {
+    std::string msg = rc == RID_ENOMEM ? "device allocation failed" : (h->err.empty() ? "CUDA error during init" : h->err);
+    free_all(h->d, h->staging);
+    delete h;
+    return fail(nullptr, rc, msg);
+  }
+}
+
+int rid_ingest(rid_handle* h, const void* cols, int64_t ld, int32_t ncols, int32_t on_device) {
+  if (!h) return RID_EINVAL;
+  if (h->finalized) return fail(h, RID_ESTATE, "rid_ingest after rid_finalize (call rid_reset first)");
+  if (ncols < 0) return fail(h, RID_EINVAL, "ncols < 0");
+  if (ncols == 0) return RID_OK;
+  if (!cols) return fail(h, RID_EINVAL, "cols is NULL");
+  if (ld < h->d.m) return fail(h, RID_EINVAL, "ld < m");
+  int32_t q = 0;
+  while (q < ncols) {
+    int nb = ncols - q;
+    if (nb > rid::kMaxB) nb = rid::kMaxB;
+    if (nb > h->d.t - h->count) nb = h->d.t - h->count;
+    int rc = grow(h, h->n_obs + nb);
+    if (rc != RID_OK) return rc;
+    const char* src = (const char*)cols + (size_t)q * ld * h->esize;
+    int64_t use_ld = ld;
+    if (!on_device) {
+      CK(cudaMemcpy2DAsync(h->staging, (size_t)h->d.m_pad * h->esize, src, (size_t)ld * h->esize,
+                           (size_t)h->d.m * h->esize, (size_t)nb, cudaMemcpyHostToDevice, h->st));
+      src = (const char*)h->staging;
+      use_ld = h->d.m_pad;
+    }
+    const int nj = rid::launch_set_jd(h->d, h->count, nb, h->n_obs, h->st);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (h->prof) for (auto& e : ev) e = next_event(h);
+    const int ni = rid::launch_ingest(h->d, src, use_ld, nb, h->count, h->n_obs, h->st, h->prof ? ev : nullptr);
+    if (h->prof) {
+      h->spans[0].push_back({ev[0], ev[1]});
+      h->spans[1].push_back({ev[1], ev[2]});
+      h->kernels[0] += 1;
+      h->kernels[1] += ni - 1 + nj;
+    }
+    CK(cudaGetLastError());
+    h->count += nb;
+    h->n_obs += nb;
+    q += nb;
+    if (h->count == h->d.t) {
+      rc = run_batch(h);
+      if (rc != RID_OK) return rc;
+    }
+  }
+  return RID_OK;
+}
+
+int rid_finalize(rid_handle* h, int64_t* J_out, double* P_out, int64_t ldp, int32_t on_device) {
+  if (!h) return RID_EINVAL;
+  const int t = h->d.t;
+  if (P_out && ldp < t) return fail(h, RID_EINVAL, "ldp < t");
+  if (!h->finalized && h->count > 0) {
+    int rc = run_batch(h);
+    if (rc != RID_OK) return rc;
+  }
+  h->finalized = true;
+  int rc = check_device_error(h);
+  if (rc != RID_OK) return rc;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (J_out) CK(cudaMemcpyAsync(J_out, h->d.JC, sizeof(int64_t) * t, kind, h->st));
+  if (P_out && h->n_obs > 0)
+    CK(cudaMemcpy2DAsync(P_out, sizeof(double) * ldp, h->d.P, sizeof(double) * t, sizeof(double) * t,
+                         (size_t)h->n_obs, kind, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RID_OK;
+}
+
+int rid_error_estimate(rid_handle* h, double est_sq[5], double est_fro[5], int32_t* q_star) {
+  if (!h) return RID_EINVAL;
+  if (h->batch == 0) return fail(h, RID_ESTATE, "no batch step has run yet");
+  double e[4];
+  int meta[rid::META_LEN];
+  CK(cudaMemcpyAsync(e, h->d.scal + rid::SCAL_EST, sizeof(e), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(meta, h->d.meta, sizeof(meta), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const int q = meta[rid::META_QSTAR];
+  double out[5] = {e[q - 4], e[0], e[1], e[2], e[3]};
+  for (int i = 0; i < 5; ++i) {
+    if (est_sq) est_sq[i] = out[i];
+    if (est_fro) est_fro[i] = sqrt(out[i] > 0.0 ? out[i] : 0.0);
+  }
+  if (q_star) *q_star = q;
+  return RID_OK;
+}
+
+int64_t rid_n_obs(const rid_handle* h) { return h ? h->n_obs : -1; }
+
+int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device) {
+  if (!h || !out) return RID_EINVAL;
+  if (ld < h->d.m) return fail(h, RID_EINVAL, "ld < m");
+  const int t = h->d.t;
+  std::vector<int> slot(t);
+  std::vector<int64_t> jc(t);
+  CK(cudaMemcpyAsync(slot.data(), h->d.slotC, sizeof(int) * t, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int i = 0; i < t; ++i) {
+    char* dst = (char*)out + (size_t)i * ld * h->esize;
+    if (slot[i] >= 0) {
+      CK(cudaMemcpyAsync(dst, (const char*)h->d.pool + (size_t)slot[i] * h->d.m_pad * h->esize,
+                         (size_t)h->d.m * h->esize, kind, h->st));
+    } else if (on_device) {
+      CK(cudaMemsetAsync(dst, 0, (size_t)h->d.m * h->esize, h->st));
+    } else {
+      CK(cudaStreamSynchronize(h->st));
+      memset(dst, 0, (size_t)h->d.m * h->esize);
+    }
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return RID_OK;
+}
+
+int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
+  if (!h || !out) return RID_EINVAL;
+  const Dev& d = h->d;
+  const int64_t n = h->n_obs;
+  const void* src = nullptr;
+  size_t bytes = 0;
+  std::vector<double> tmp;
+  switch (item) {
+    case RID_STATE_SKETCH: src = d.S; bytes = sizeof(double) * d.rows * n; break;
+    case RID_STATE_SKETCH_LEV:
+      if (d.lev_ld == d.s) { src = d.Slev; bytes = sizeof(double) * d.s * n; }
+      else {
+        if (count < (int64_t)d.s * n) return fail(h, RID_EINVAL, "buffer too small");
+        CK(cudaMemcpy2DAsync(out, sizeof(double) * d.s, d.Slev, sizeof(double) * d.lev_ld,
+                             sizeof(double) * d.s, (size_t)n, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        return RID_OK;
+      }
+      break;
+    case RID_STATE_SST: src = d.SSt; bytes = sizeof(double) * d.s * d.s; break;
+    case RID_STATE_FRO2: src = d.fro2; bytes = sizeof(double) * 2; break;
+    case RID_STATE_JC: src = d.JC; bytes = sizeof(int64_t) * d.t; break;
+    case RID_STATE_TAU_OLD: src = d.tau_old; bytes = sizeof(double) * d.t; break;
+    case RID_STATE_LAMBDA: src = d.scal + rid::SCAL_LAMBDA; bytes = sizeof(double); break;
+    case RID_STATE_CAND: {
+      if (count < 4 * (int64_t)d.t * h->n_prev) return fail(h, RID_EINVAL, "buffer too small");
+      for (int q = 0; q < 4; ++q)
+        CK(cudaMemcpyAsync((double*)out + (size_t)q * d.t * h->n_prev, d.cand + (size_t)q * d.t * d.n_cap,
+                           sizeof(double) * d.t * h->n_prev, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      return RID_OK;
+    }
+    case RID_STATE_BATCHES: {
+      if (count < 1) return fail(h, RID_EINVAL, "buffer too small");
+      *(int64_t*)out = h->batch;
+      return RID_OK;
+    }
+    default: return fail(h, RID_EINVAL, "unknown state item");
+  }
+  const size_t esz = (item == RID_STATE_JC) ? sizeof(int64_t) : sizeof(double);
+  if ((size_t)count * esz < bytes) return fail(h, RID_EINVAL, "buffer too small");
+  if (bytes) CK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RID_OK;
+}
+
+int rid_profile(rid_handle* h, int32_t enable) {
+  if (!h) return RID_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  h->prof = enable != 0;
+  h->evused = 0;
+  for (auto& v : h->spans) v.clear();
+  for (auto& k : h->kernels) k = 0;
+  return RID_OK;
+}
+
+int rid_profile_read(rid_handle* h, double ms[3], int64_t kernels[3], int64_t groups[3]) {
+  if (!h) return RID_EINVAL;
+  CK(cudaStreamSynchronize(h->st));
+  for (int p = 0; p < 3; ++p) {
+    double tot = 0.0;
+    for (auto& sp : h->spans[p]) {
+      float e = 0.f;
+      CK(cudaEventElapsedTime(&e, sp.first, sp.second));
+      tot += e;
+    }
+    if (ms) ms[p] = tot;
+    if (kernels) kernels[p] = h->kernels[p];
+    if (groups) groups[p] = (int64_t)h->spans[p].size();
+  }
+  return RID_OK;
+}
+
+int rid_sync(rid_handle* h) {
+  if (!h) return RID_EINVAL;
+  return check_device_error(h);
+}
+
+int rid_reset(rid_handle* h) {
+  if (!h) return RID_EINVAL;
+  const int nk = rid::launch_reset_state(h->d, h->st);
+  if (h->prof) h->kernels[1] += nk;
+  CK(cudaGetLastError());
+  h->count = 0;
+  h->n_obs = 0;
+  h->n_prev = 0;
+  h->batch = 0;
+  h->finalized = false;
+  return RID_OK;
+}
+
+const char* rid_last_error(const rid_handle* h) {
+  return h ? h->err.c_str() : g_init_err.c_str();
+}
+
+void rid_destroy(rid_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  for (auto e : h->evpool) cudaEventDestroy(e);
+  free_all(h->d, h->staging);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Device-state layout and kernel launchers shared by the CUDA translation units.
+//
+// HBM layout (all column-major):
+//   pool   : 2t slots of m_pad elements (data dtype).  Basis columns C and
+//            buffered columns D both live here; a selection only moves slot
+//            indices, never data.
+//   S      : (s+h) x n_cap doubles, S(:, j) = Omega a_j (unit-variance rows;
+//            rows [0, s) are the left sketch, [s, s+h) the Hutch++ probes).
+//   Slev   : sketch used by the ridge scores (= S rows [0,s) with stride s+h,
+//            or an s x n_cap buffer of Omega a + Omega_g G a in gradient mode).
+//   SSt    : s x s doubles, Slev Slev^T.
+//   P      : t x n_cap doubles (slot rows); cand: 4 candidates t x n_cap
+//            (active-slot rows).
+//   Gp     : 2t x 2t doubles, Gram of pool slots (entries are valid for pairs
+//            whose slots have not been overwritten since they were computed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rid {
+
+constexpr int kMaxB = 16;          // columns per ingest launch
+constexpr int kSketchThreads = 256;
+constexpr int kChunk = 256;        // coordinates staged per CTA iteration
+
+struct Dev {
+  // sizes
+  int64_t m, m_pad;
+  int t, s, h, rows;              // rows = s + h
+  int hbase, h1, h2, h3;          // probe rows [hbase, hbase+h1+h2+h3) split into Omega_1/2/3
+  int64_t n_cap;
+  int dtype;                      // 0 f64, 1 f32
+  int omega_kind;                 // 0 gaussian, 1 rademacher
+  int lambda_mode;
+  double lambda_fixed;
+  double refill_scale;            // c (k ln k + k ln(1/delta)/eps) / t
+  uint64_t seed;
+  int grad;                       // gradient mode
+  int nx, ny, nfields;
+  int lev_ld;                     // leading dimension of Slev
+  // data
+  void* pool;
+  double* omegaT;                 // Gaussian mode: m_pad x rows (entry (i, r) at i*rows + r)
+  double* omegagT;                // Gaussian gradient sketch: (2 m_pad) x s
+  double* S;
+  double* Slev;
+  double* SSt;
+  double* fro2;                   // [0] ||A_obs||^2, [1] leverage norm
+  // selection state (device)
+  int64_t* JC; int64_t* JC_prev;  // t
+  int* slotC; int* slotC_prev;    // t, pool slot of each basis slot (-1 empty)
+  int* dslot;                     // t, pool slot receiving the q-th buffered column
+  int64_t* JD;                    // t, global index of the q-th buffered column
+  double* tau_old;                // t
+  double* tauC; double* tauD;     // t each
+  int* meta;                      // small ints, see META_*
+  int* act; int* pact;            // active slots now / before (ordered by slot)
+  int* isnew;                     // per active position: 1 if new basis element
+  int* posof;                     // per slot: active position or -1
+  int* newpos;                    // active positions of the new basis elements
+  int* gnew; int* gtgt;           // pool slots: new entries, Gram targets
+  double* scal;                   // small doubles, see SCAL_*
+  // batch-step work
+  double* Gp;                     // 2t x 2t
+  double* gpart;                  // gram split-K partials
+  double* P;                      // t x n_cap
+  double* cand;                   // 4 x t x n_cap
+  double* work;                   // linear-algebra scratch
+  double* hpart;                  // Hutch++ partials
+  double* spart;                  // sketch partials
+  double* npart;                  // norm partials
+  int* err;                       // device error word
+  int n_sketch_blocks;
+  int gram_split;
+  int64_t work_len;
+};
+
+// meta[] indices
+enum {
+  META_NACT = 0, META_NPACT = 1, META_NNEW = 2, META_NTGT = 3, META_COUNT = 4,
+  META_NOBS = 5, META_NPREV = 6, META_BATCH = 7, META_QSTAR = 8, META_NKEPT = 9, META_LEN = 16
+};
+// scal[] indices
+enum { SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_LEN = 8 };
+
+// device error bits
+enum { ERR_NONFINITE = 1, ERR_CHOL = 2, ERR_EIG = 4 };
+
+// ingest.cu
+// Returns the number of kernels launched; ev[0..2] (may be null) are recorded before the
+// sketch kernel, after it, and after the reductions.
+int launch_ingest(const Dev& d, const void* src, int64_t ld, int nb, int count, int64_t n_obs,
+                  cudaStream_t st, cudaEvent_t* ev);
+void launch_materialize_omega(const Dev& d, cudaStream_t st);
+
+// batch.cu
+int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
+                      cudaStream_t st);
+int launch_reset_state(const Dev& d, cudaStream_t st);
+int launch_set_jd(const Dev& d, int count, int nb, int64_t n_obs, cudaStream_t st);
+int64_t work_doubles(const Dev& d);
+
+}  // namespace rid

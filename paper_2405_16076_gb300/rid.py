@@ -1,0 +1,250 @@
+"""ctypes binding of the C ABI in include/rid.h (argument marshalling only).
+
+Every function of the header is exposed under the same name; ``OnlineRID``
+is a small convenience wrapper that owns one handle.  Device memory and
+streams come from PyTorch; every step of the method runs in librid.so.
+There is no CPU fallback: importing this module fails if the library has
+not been built, and ``rid_init`` fails with RID_ENOLIB without a GPU.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librid.so")
+
+RID_OK, RID_EINVAL, RID_ENOMEM, RID_ECUDA, RID_ESTATE, RID_ENONFINITE, RID_ENOLIB = 0, -1, -2, -3, -4, -5, -6
+RID_LAMBDA_STREAMING, RID_LAMBDA_FIXED = 0, 1
+RID_OMEGA_GAUSSIAN, RID_OMEGA_RADEMACHER = 0, 1
+RID_F64, RID_F32 = 0, 1
+RID_SKETCH_NATIVE, RID_SKETCH_BF16, RID_SKETCH_BF16X2 = 0, 1, 2
+(RID_STATE_SKETCH, RID_STATE_SKETCH_LEV, RID_STATE_SST, RID_STATE_FRO2, RID_STATE_JC,
+ RID_STATE_TAU_OLD, RID_STATE_LAMBDA, RID_STATE_CAND, RID_STATE_BATCHES) = range(9)
+
+
+class rid_config(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64), ("k", ctypes.c_int32), ("s", ctypes.c_int32), ("h", ctypes.c_int32),
+        ("lambda_mode", ctypes.c_int32), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
+        ("eps", ctypes.c_double), ("delta", ctypes.c_double), ("c_const", ctypes.c_double),
+        ("lambda_fixed", ctypes.c_double), ("omega_kind", ctypes.c_int32), ("data_dtype", ctypes.c_int32),
+        ("sketch_prec", ctypes.c_int32), ("grad_dims", ctypes.c_int32), ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32), ("nfields", ctypes.c_int32), ("n_max", ctypes.c_int64),
+        ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class RIDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rid error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"librid.so is not built ({LIB_PATH}); run paper_2405_16076_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    P = ctypes.c_void_p
+    sig = {
+        "rid_config_default": (ctypes.c_int, [ctypes.POINTER(rid_config)]),
+        "rid_init": (ctypes.c_int, [ctypes.POINTER(H), ctypes.POINTER(rid_config)]),
+        "rid_ingest": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
+        "rid_finalize": (ctypes.c_int, [H, P, P, ctypes.c_int64, ctypes.c_int32]),
+        "rid_error_estimate": (ctypes.c_int, [H, P, P, P]),
+        "rid_n_obs": (ctypes.c_int64, [H]),
+        "rid_get_basis": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32]),
+        "rid_get_state": (ctypes.c_int, [H, ctypes.c_int32, P, ctypes.c_int64]),
+        "rid_sync": (ctypes.c_int, [H]),
+        "rid_profile": (ctypes.c_int, [H, ctypes.c_int32]),
+        "rid_profile_read": (ctypes.c_int, [H, P, P, P]),
+        "rid_reset": (ctypes.c_int, [H]),
+        "rid_last_error": (ctypes.c_char_p, [H]),
+        "rid_destroy": (None, [H]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+rid_config_default = lib.rid_config_default
+rid_init = lib.rid_init
+rid_ingest = lib.rid_ingest
+rid_finalize = lib.rid_finalize
+rid_error_estimate = lib.rid_error_estimate
+rid_n_obs = lib.rid_n_obs
+rid_get_basis = lib.rid_get_basis
+rid_get_state = lib.rid_get_state
+rid_sync = lib.rid_sync
+rid_profile = lib.rid_profile
+rid_profile_read = lib.rid_profile_read
+rid_reset = lib.rid_reset
+rid_last_error = lib.rid_last_error
+rid_destroy = lib.rid_destroy
+
+
+def _check(rc, h=None):
+    if rc != RID_OK:
+        msg = rid_last_error(h)
+        raise RIDError(rc, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr()), bool(x.is_cuda)
+    arr = np.asarray(x)
+    return ctypes.c_void_p(arr.ctypes.data), False
+
+
+class OnlineRID:
+    """One streaming decomposition handle (see include/rid.h)."""
+
+    def __init__(self, m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
+                 lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
+                 sketch="native", n_max=1024, seed=0, stream=None):
+        cfg = rid_config()
+        _check(rid_config_default(ctypes.byref(cfg)))
+        cfg.m, cfg.k, cfg.s, cfg.h = int(m), int(k), int(s), int(h)
+        cfg.c1, cfg.c2, cfg.eps, cfg.delta, cfg.c_const = c1, c2, eps, delta, c_const
+        cfg.lambda_mode = RID_LAMBDA_FIXED if lambda_mode == "fixed" else RID_LAMBDA_STREAMING
+        cfg.lambda_fixed = float(lambda_fixed)
+        cfg.omega_kind = RID_OMEGA_GAUSSIAN if omega == "gaussian" else RID_OMEGA_RADEMACHER
+        cfg.data_dtype = RID_F64 if dtype == "f64" else RID_F32
+        cfg.sketch_prec = {"native": RID_SKETCH_NATIVE, "bf16": RID_SKETCH_BF16, "bf16x2": RID_SKETCH_BF16X2}[sketch]
+        cfg.n_max = int(n_max)
+        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        self.cfg = cfg
+        self.t = int(k)
+        self.m = int(m)
+        self.rows = int(s) + int(h)
+        self.s = int(s)
+        self.esize = 8 if dtype == "f64" else 4
+        self.np_dtype = np.float64 if dtype == "f64" else np.float32
+        hnd = ctypes.c_void_p()
+        _check(rid_init(ctypes.byref(hnd), ctypes.byref(cfg)))
+        self.h = hnd
+
+    def close(self):
+        if self.h:
+            rid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ingest(self, cols, ld=None, ncols=None):
+        """cols: m x b column-major block (torch tensor on the GPU, or numpy array on the host).
+
+        A torch tensor of shape (b, m) (row q = snapshot q) is accepted as well."""
+        p, on_dev = _ptr(cols)
+        if ncols is None or ld is None:
+            shp = tuple(cols.shape)
+            if len(shp) == 1:
+                ncols, ld = 1, shp[0]
+            elif hasattr(cols, "stride") and not isinstance(cols, np.ndarray):
+                st = cols.stride()
+                if shp[0] == self.m and st[0] == 1:
+                    ncols, ld = shp[1], st[1]
+                elif shp[1] == self.m and st[1] == 1:
+                    ncols, ld = shp[0], st[0]
+                else:
+                    raise ValueError("tensor must hold contiguous m-long columns")
+            else:
+                a = np.asarray(cols)
+                if a.flags.f_contiguous and a.shape[0] == self.m:
+                    ncols, ld = a.shape[1], a.shape[0]
+                elif a.flags.c_contiguous and a.shape[1] == self.m:
+                    ncols, ld = a.shape[0], a.shape[1]
+                else:
+                    raise ValueError("array must hold contiguous m-long columns")
+        _check(rid_ingest(self.h, p, int(ld), int(ncols), int(on_dev)), self.h)
+
+    def finalize(self):
+        t = self.t
+        n = int(rid_n_obs(self.h))
+        J = np.empty(t, dtype=np.int64)
+        P = np.empty((n, t), dtype=np.float64)     # row j = column j of the t x n matrix
+        _check(rid_finalize(self.h, ctypes.c_void_p(J.ctypes.data), ctypes.c_void_p(P.ctypes.data), t, 0), self.h)
+        return J, P.T.copy()
+
+    def error_estimate(self):
+        sq = np.empty(5)
+        fro = np.empty(5)
+        q = ctypes.c_int32()
+        _check(rid_error_estimate(self.h, ctypes.c_void_p(sq.ctypes.data), ctypes.c_void_p(fro.ctypes.data),
+                                  ctypes.byref(q)), self.h)
+        return sq, fro, int(q.value)
+
+    def n_obs(self):
+        return int(rid_n_obs(self.h))
+
+    def state(self, item):
+        n = self.n_obs()
+        t, s, rows = self.t, self.s, self.rows
+        if item == RID_STATE_SKETCH:
+            out = np.empty((n, rows))
+        elif item == RID_STATE_SKETCH_LEV:
+            out = np.empty((n, s))
+        elif item == RID_STATE_SST:
+            out = np.empty((s, s))
+        elif item == RID_STATE_FRO2:
+            out = np.empty(2)
+        elif item == RID_STATE_JC:
+            out = np.empty(t, dtype=np.int64)
+        elif item == RID_STATE_TAU_OLD:
+            out = np.empty(t)
+        elif item == RID_STATE_LAMBDA:
+            out = np.empty(1)
+        elif item == RID_STATE_BATCHES:
+            out = np.empty(1, dtype=np.int64)
+        elif item == RID_STATE_CAND:
+            raise ValueError("use candidates()")
+        else:
+            raise ValueError(item)
+        _check(rid_get_state(self.h, item, ctypes.c_void_p(out.ctypes.data), out.size), self.h)
+        if item in (RID_STATE_SKETCH, RID_STATE_SKETCH_LEV):
+            return out.T.copy()
+        if item == RID_STATE_SST:
+            return out.T.copy()
+        return out
+
+    def candidates(self, n_prev):
+        out = np.empty((4, n_prev, self.t))
+        _check(rid_get_state(self.h, RID_STATE_CAND, ctypes.c_void_p(out.ctypes.data), out.size), self.h)
+        return out.transpose(0, 2, 1).copy()    # (4, t, n_prev), rows = active positions
+
+    def basis(self):
+        out = np.zeros((self.t, self.m), dtype=self.np_dtype)
+        _check(rid_get_basis(self.h, ctypes.c_void_p(out.ctypes.data), self.m, 0), self.h)
+        return out.T.copy()
+
+    def finalize_device(self, J, P):
+        """Finalize into device tensors: J (t,) int64 and P (n, t) float64 (row j = column j)."""
+        _check(rid_finalize(self.h, ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(P.data_ptr()), self.t, 1), self.h)
+
+    def profile(self, enable=True):
+        _check(rid_profile(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self):
+        ms = np.zeros(3)
+        kern = np.zeros(3, dtype=np.int64)
+        grp = np.zeros(3, dtype=np.int64)
+        _check(rid_profile_read(self.h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(kern.ctypes.data),
+                                ctypes.c_void_p(grp.ctypes.data)), self.h)
+        return ms, kern, grp
+
+    def sync(self):
+        _check(rid_sync(self.h), self.h)
+
+    def reset(self):
+        _check(rid_reset(self.h), self.h)

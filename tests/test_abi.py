@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads, exports what include/rid.h declares, and the
+ctypes structure matches the C layout.  No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rid.h")
+LIB = os.path.join(ROOT, "paper_2405_16076_gb300", "librid.so")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        from paper_2405_16076_gb300.build import build
+        build()
+    return ctypes.CDLL(LIB)
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rid_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["rid_init", "rid_ingest", "rid_finalize", "rid_error_estimate", "rid_destroy",
+                 "rid_config_default", "rid_last_error", "rid_get_basis", "rid_get_state",
+                 "rid_reset", "rid_sync", "rid_n_obs"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (rid_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_ctypes_layout_matches_c(lib):
+    from paper_2405_16076_gb300.rid import rid_config
+    fields = [f for f, _ in rid_config._fields_]
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"rid.h\"\nint main(void){\n"
+    src += 'printf("%zu\\n", sizeof(rid_config));\n'
+    for f in fields:
+        src += f'printf("%zu\\n", offsetof(rid_config, {f}));\n'
+    src += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(rid_config)
+    for f, off in zip(fields, vals[1:]):
+        assert getattr(rid_config, f).offset == off, f
+
+
+def test_defaults_and_validation_without_device(lib):
+    from paper_2405_16076_gb300 import rid
+    cfg = rid.rid_config()
+    assert rid.rid_config_default(ctypes.byref(cfg)) == rid.RID_OK
+    assert abs(cfg.c1 - 1 / 6) < 1e-15 and abs(cfg.c2 - 1 / 3) < 1e-15
+    assert cfg.eps == 0.5 and cfg.delta == 0.05 and cfg.omega_kind == rid.RID_OMEGA_RADEMACHER
+    h = ctypes.c_void_p()
+    cfg.m, cfg.k, cfg.s, cfg.h = 100, 10, 5, 0          # s <= k is rejected before any device call
+    assert rid.rid_init(ctypes.byref(h), ctypes.byref(cfg)) == rid.RID_EINVAL
+    assert b"s must" in rid.rid_last_error(None)
+    cfg.s, cfg.c1, cfg.c2 = 43, 0.4, 0.3                 # c1 < c2 required (Algorithm 8)
+    assert rid.rid_init(ctypes.byref(h), ctypes.byref(cfg)) == rid.RID_EINVAL
+
+
+def test_no_cpu_fallback_without_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_2405_16076_gb300 import rid
+    with pytest.raises(rid.RIDError) as e:
+        rid.OnlineRID(m=1000, k=5, s=23, h=12)
+    assert e.value.code == rid.RID_ENOLIB
