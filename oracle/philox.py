@@ -17,8 +17,9 @@ behind every "with probability p" decision of the column subset selection.
 Their counter layout is fixed here and restated independently by the CUDA
 library:
 
-* Rademacher Omega[r, i]:   bit (i mod 128) of Philox((i // 128, r, TAG_RADEMACHER, 0)),
-  bit b of word w at position 32*w + b; a set bit means -1.
+* Rademacher Omega[r, i]:   one bit of Philox((i // 128, r, TAG_RADEMACHER, 0)); with
+  j = i mod 128, word w = j // 32 and e = j mod 32, coordinate pair p = e // 2 takes
+  bit 15 - p of word w for even e and bit 31 - p for odd e; a set bit means -1.
 * Gaussian Omega[r, i]:     Box-Muller pair from Philox((i // 2, r, TAG_GAUSS, 0));
   even i takes the cosine branch, odd i the sine branch.
 * Uniform u(batch, i, r):   53-bit uniform in [0, 1) from words 0, 1 of
@@ -97,7 +98,8 @@ def rademacher_block(seed, rows, i0, i1, tag=TAG_RADEMACHER):
     w = philox4x32(blk[None, :], rows[:, None], tag, 0, k0, k1)
     pos = (i % 128)[None, :]
     word = pos // 32
-    bit = (pos % 32).astype(np.uint64)
+    e = pos % 32
+    bit = np.where(e % 2 == 0, 15 - e // 2, 31 - e // 2).astype(np.uint64)
     words = np.stack([x.astype(np.uint64) for x in w], axis=0)  # (4, R, N)
     sel = np.take_along_axis(words, np.broadcast_to(word, w[0].shape)[None], axis=0)[0]
     b = (sel >> bit) & np.uint64(1)

@@ -77,9 +77,11 @@ ingest_sketch_kernel(Dev d, const T* __restrict__ src, int64_t ld, int nb, int c
           for (int wi = 0; wi < 4; ++wi) {
             const uint32_t bits = words[wi];
 #pragma unroll 8
-            for (int b = 0; b < 32; ++b) {
-              const uint32_t bit = (bits >> b) & 1u;
-              const int ii = half * 128 + wi * 32 + b;
+            for (int e = 0; e < 32; ++e) {
+              // coordinate pair p = e/2 takes bit 15-p (even e) or 31-p (odd e) of the word
+              const int bpos = (e & 1) ? 31 - (e >> 1) : 15 - (e >> 1);
+              const uint32_t bit = (bits >> bpos) & 1u;
+              const int ii = half * 128 + wi * 32 + e;
 #pragma unroll
               for (int q = 0; q < NB; ++q)
                 if (q < nb) acc[q] += flip_sign(X[q][ii], bit);

@@ -8,7 +8,10 @@
 // 0xBB67AE85).
 //
 // Stream layout (counter = (c0, c1, tag, c3), key = (seed_lo, seed_hi)):
-//   Rademacher Omega[r][i]: bit (i mod 128) of Philox(i/128, r, RAD, 0), set bit = -1
+//   Rademacher Omega[r][i]: with j = i mod 128, word w = j/32, e = j mod 32, pair p = e/2:
+//                           bit 15-p (even e) or 31-p (odd e) of word w of
+//                           Philox(i/128, r, RAD, 0); set bit = -1.  A pair of
+//                           coordinates is then one AND/OR of a shifted word.
 //   Gaussian   Omega[r][i]: Box-Muller from Philox(i/2, r, GAU, 0); even i cosine, odd i sine
 //   uniform u(batch, i, r): 53-bit uniform from words 0,1 of Philox(i, r, UNI, batch)
 #pragma once

@@ -36,10 +36,15 @@ def test_rademacher_bit_layout_and_moments():
     seed = 12345
     blk = philox.rademacher_block(seed, [3, 7], 0, 512)
     k0, k1 = philox.seed_key(seed)
-    # entry (row 7, coordinate 300): block 2, position 44 -> word 1, bit 12
+    # entry (row 7, coordinate 300): block 2, position 44 -> word 1, e = 12 (even, pair 6) -> bit 9;
+    # coordinate 301 (e = 13, odd, pair 6) -> bit 25
     w = philox.philox4x32(2, 7, philox.TAG_RADEMACHER, 0, k0, k1)
-    bit = (int(w[1]) >> 12) & 1
-    assert blk[1, 300] == (-1.0 if bit else 1.0)
+    assert blk[1, 300] == (-1.0 if (int(w[1]) >> 9) & 1 else 1.0)
+    assert blk[1, 301] == (-1.0 if (int(w[1]) >> 25) & 1 else 1.0)
+    # every bit of the 128-bit block is used exactly once per 128 coordinates
+    one = philox.rademacher_block(seed, [7], 256, 384)[0]
+    bits = [(int(w[q]) >> b) & 1 for q in range(4) for b in range(32)]
+    assert sorted((one < 0).astype(int).tolist()) == sorted(bits)
     big = philox.rademacher_block(seed, np.arange(64), 0, 4096)
     assert set(np.unique(big)) == {-1.0, 1.0}
     assert abs(big.mean()) < 4 / math.sqrt(big.size)
