@@ -147,6 +147,8 @@ def main():
     ap.add_argument("--config", default="channel", choices=sorted(CONFIGS))
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sketch", default="bf16x2", choices=["bf16x2", "bf16", "native"])
+    ap.add_argument("--group", type=int, default=64)
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
@@ -174,7 +176,8 @@ def main():
     torch.cuda.synchronize()
 
     st = torch.cuda.Stream(device=dev)
-    h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", n_max=n, seed=7 + rank, stream=st)
+    h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=args.sketch, n_max=n,
+                      seed=7 + rank, stream=st, defer=True, group_max=args.group)
     Jd = torch.empty(cfg["k"], dtype=torch.int64, device=dev)
     Pd = torch.empty((n, cfg["k"]), dtype=torch.float64, device=dev)
 
@@ -240,7 +243,8 @@ def main():
     pk = peaks()
     groups = max(int(prof_grp[0]), 1)
     avg_ms = prof_ms[0] / groups
-    bytes_per_launch = 2.0 * b * m * 4          # read each column once + write it to its D slot
+    cols_per_launch = int(prof_kern[0] and (n * args.steps) / max(int(prof_grp[0]), 1))
+    bytes_per_launch = 2.0 * cols_per_launch * m * 4    # read each column once + write it to its slot
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "ingest_traffic.json")
@@ -252,10 +256,12 @@ def main():
     line = {
         "metric": "snapshots/s", "value": value, "unit": "snapshots/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x2": "f32 data, bf16x2 sketch", "bf16": "f32 data, bf16 sketch", "native": "f32"}[args.sketch],
         "data": "synthetic",
         "config": {"workload": cfg["workload"], "m": m, "n": n, "block": b, "k": cfg["k"], "s": cfg["s"],
-                   "h": cfg["h"], "omega": "rademacher", "lambda": "streaming",
+                   "h": cfg["h"], "omega": "rademacher", "lambda": "streaming", "sketch": args.sketch,
+                   "group": args.group,
                    "l2": "inputs larger than L2 (57 MB per snapshot, whole stream resident in HBM)",
                    "parallelism": f"{world} independent streams"},
         "e2e": {"value": e2e_val, "unit": "snapshots/s", "h2d_bytes_per_step": int(n * m * 4),
@@ -263,7 +269,8 @@ def main():
         "gpu_launches": int(prof_kern.sum()),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                      "frac": achieved / pk.get("hbm_gbs"), "traffic": traffic,
-                     "kernel": "ingest_sketch_kernel", "avg_launch_ms": avg_ms,
+                     "kernel": "tc_ingest_kernel" if args.sketch != "native" else "ingest_sketch_kernel",
+                     "avg_launch_ms": avg_ms, "cols_per_launch": cols_per_launch,
                      "phase_ms_per_step": {"ingest_sketch": prof_ms[0] / args.steps,
                                            "ingest_reduce": prof_ms[1] / args.steps,
                                            "batch_step": prof_ms[2] / args.steps},

@@ -38,7 +38,8 @@ enum rid_status {
   RID_ECUDA = -3,       /* a CUDA runtime call failed */
   RID_ESTATE = -4,      /* call not allowed in the current state (e.g. ingest after finalize) */
   RID_ENONFINITE = -5,  /* a NaN/Inf snapshot was ingested (detected from its squared norm) */
-  RID_ENOLIB = -6       /* the CUDA library is missing or no device is present */
+  RID_ENOLIB = -6,      /* the CUDA library is missing or no device is present */
+  RID_ETIMEOUT = -7     /* a bounded wait inside a kernel gave up; that kernel returned early */
 };
 
 enum rid_lambda_mode {
@@ -77,6 +78,8 @@ typedef struct rid_config {
   int32_t nfields;       /* fields stacked in one snapshot when grad_dims = 2 */
   int64_t n_max;         /* initial capacity in columns (grows by doubling) */
   uint64_t seed;         /* key of the Philox4x32-10 streams */
+  int32_t group_max;     /* columns sketched per launch (1..64; 0 = 64 on tensor cores, 16 otherwise) */
+  int32_t defer_device_input; /* 1: device columns are read later, in groups (see rid_ingest) */
   void* cuda_stream;     /* cudaStream_t to run on; NULL = default stream */
 } rid_config;
 
@@ -96,9 +99,16 @@ int rid_init(rid_handle** out, const rid_config* cfg);
 /* Ingest ncols >= 0 columns (Algorithm 3, the loop body for each column):
  * column q starts at cols + q*ld elements of the configured dtype.
  * on_device != 0: cols is a device pointer, read in place; otherwise a host
- * pointer (preferably pinned), copied to the device first.  The library copies
- * what it keeps; the caller may reuse the buffer once the handle's stream has
- * passed this call.  Whenever t = k columns have been buffered the batch step
+ * pointer (preferably pinned), copied to a device staging area first.  The
+ * library copies what it keeps; the caller may reuse a host buffer when the
+ * call returns and a device buffer once the handle's stream has passed this
+ * call -- except with defer_device_input = 1, where device columns are only
+ * recorded and read later, in groups of up to group_max columns (one read of
+ * each column sketches the whole group); the caller must then keep them
+ * valid and unchanged until the t-th buffered column of the batch, or
+ * rid_finalize / rid_sync / rid_get_state / rid_get_basis / rid_reset, has
+ * been called and the stream has passed it.  Host columns are always grouped
+ * through the staging area.  Whenever t = k columns have been buffered the batch step
  * (ridge scores, prune/refill, Algorithms 4-8) runs on the device without a
  * host round trip.  Errors: RID_EINVAL (ld < m, NULL cols with ncols > 0),
  * RID_ESTATE (after rid_finalize), RID_ECUDA. */

@@ -26,9 +26,13 @@ __device__ __forceinline__ float flip_sign(float x, uint32_t bit) {
 
 // grid: (n_sketch_blocks, ceil(rows/256)); block: 256 threads.
 // Thread tid of row-group y owns sketch row r = 256*y + tid.
+struct SimtCols {
+  const void* p[kMaxB];
+};
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(kSketchThreads)
-ingest_sketch_kernel(Dev d, const T* __restrict__ src, int64_t ld, int nb, int count) {
+ingest_sketch_kernel(Dev d, SimtCols cols, int nb, int count) {
   __shared__ T X[NB][kChunk];
   __shared__ int dst[NB];
   __shared__ double red[kSketchThreads / 32][NB];
@@ -57,7 +61,7 @@ ingest_sketch_kernel(Dev d, const T* __restrict__ src, int64_t ld, int nb, int c
       if (q < nb) {
         T v = T(0);
         if (i < d.m) {
-          v = src[(int64_t)q * ld + i];
+          v = ((const T*)cols.p[q])[i];
           if (lead) pool[(int64_t)dst[q] * d.m_pad + i] = v;
         }
         X[q][tid] = v;
@@ -179,28 +183,32 @@ void launch_materialize_omega(const Dev& d, cudaStream_t st) {
   materialize_omega_kernel<<<4 * 152, 256, 0, st>>>(d);
 }
 
-int launch_ingest(const Dev& d, const void* src, int64_t ld, int nb, int count, int64_t n_obs,
+void launch_gram_update(const Dev& d, int nb, int64_t n_obs, cudaStream_t st) {
+  const int64_t ns = (int64_t)d.s * d.s;
+  gram_update_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(d, nb, n_obs);
+}
+
+int launch_ingest(const Dev& d, const void* const* colp, int nb, int count, int64_t n_obs,
                   cudaStream_t st, cudaEvent_t* ev) {
+  SimtCols cols;
+  for (int q = 0; q < kMaxB; ++q) cols.p[q] = q < nb ? colp[q] : nullptr;
   if (ev) cudaEventRecord(ev[0], st);
   dim3 grid(d.n_sketch_blocks, (d.rows + kSketchThreads - 1) / kSketchThreads);
   if (d.dtype == 0) {
     if (nb == 1)
-      ingest_sketch_kernel<double, 1><<<grid, kSketchThreads, 0, st>>>(d, (const double*)src, ld, nb, count);
+      ingest_sketch_kernel<double, 1><<<grid, kSketchThreads, 0, st>>>(d, cols, nb, count);
     else
-      ingest_sketch_kernel<double, kMaxB><<<grid, kSketchThreads, 0, st>>>(d, (const double*)src, ld, nb, count);
+      ingest_sketch_kernel<double, kMaxB><<<grid, kSketchThreads, 0, st>>>(d, cols, nb, count);
   } else {
     if (nb == 1)
-      ingest_sketch_kernel<float, 1><<<grid, kSketchThreads, 0, st>>>(d, (const float*)src, ld, nb, count);
+      ingest_sketch_kernel<float, 1><<<grid, kSketchThreads, 0, st>>>(d, cols, nb, count);
     else
-      ingest_sketch_kernel<float, kMaxB><<<grid, kSketchThreads, 0, st>>>(d, (const float*)src, ld, nb, count);
+      ingest_sketch_kernel<float, kMaxB><<<grid, kSketchThreads, 0, st>>>(d, cols, nb, count);
   }
   if (ev) cudaEventRecord(ev[1], st);
   const int n = nb * d.rows;
   sketch_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, nb, n_obs, d.n_sketch_blocks);
-  const int64_t ns = (int64_t)d.s * d.s;
-  gram_update_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(d, nb, n_obs);
-  if (ev) cudaEventRecord(ev[2], st);
-  return 3;
+  return 2;
 }
 
 }  // namespace rid

@@ -27,7 +27,13 @@ struct rid_handle {
   int batch;          // batch steps run
   bool finalized;
   size_t esize;
-  void* staging;
+  void* staging;          // host-input staging area: group_max columns of m_pad
+  std::vector<const void*> pend;   // columns recorded but not yet sketched
+  int group_max;
+  bool tc;                // tensor-core ingest (FP32 data, BF16 / BF16x2 sketch)
+  int tc_blocks;
+  float* tc_part;
+  double* tc_npart;
   std::string err;
   int n_sm;
   // measurement (rid_profile)
@@ -140,7 +146,52 @@ int check_device_error(rid_handle* h) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  if (e & rid::ERR_TIMEOUT) return fail(h, RID_ETIMEOUT, "a bounded device wait gave up");
   if (e & rid::ERR_NONFINITE) return fail(h, RID_ENONFINITE, "a non-finite snapshot was ingested");
+  return RID_OK;
+}
+
+// Sketch the pending columns (one read of each), append them, and run the batch step
+// when the t-th buffered column has arrived.
+int flush(rid_handle* h) {
+  const int G = (int)h->pend.size();
+  if (G == 0) return RID_OK;
+  int rc = grow(h, h->n_obs + G);
+  if (rc != RID_OK) return rc;
+  const int nj = rid::launch_set_jd(h->d, h->count, G, h->n_obs, h->st);
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  if (h->prof) for (auto& e : ev) e = next_event(h);
+  int nk0 = 0, nk1 = nj;
+  if (h->tc) {
+    const int split = h->cfg.sketch_prec == RID_SKETCH_BF16X2 ? 1 : 0;
+    if (rid::launch_tc_ingest(h->d, h->pend.data(), G, split, h->count, h->n_obs, h->tc_blocks,
+                              h->tc_part, h->tc_npart, h->st, h->prof ? ev : nullptr) != 0)
+      return fail(h, RID_ECUDA, "tensor-core ingest launch failed");
+    rid::launch_gram_update(h->d, G, h->n_obs, h->st);
+    nk0 = 1;
+    nk1 += 2;
+  } else {
+    for (int q0 = 0; q0 < G; q0 += rid::kMaxB) {
+      const int nb = G - q0 < rid::kMaxB ? G - q0 : rid::kMaxB;
+      cudaEvent_t* e = (h->prof && q0 == 0) ? ev : nullptr;
+      nk1 += rid::launch_ingest(h->d, h->pend.data() + q0, nb, h->count + q0, h->n_obs + q0, h->st, e) - 1;
+      rid::launch_gram_update(h->d, nb, h->n_obs + q0, h->st);
+      nk0 += 1;
+      nk1 += 1;
+    }
+  }
+  if (h->prof) {
+    cudaEventRecord(ev[2], h->st);
+    h->spans[0].push_back({ev[0], ev[1]});
+    h->spans[1].push_back({ev[1], ev[2]});
+    h->kernels[0] += nk0;
+    h->kernels[1] += nk1;
+  }
+  CK(cudaGetLastError());
+  h->count += G;
+  h->n_obs += G;
+  h->pend.clear();
+  if (h->count == h->d.t) return run_batch(h);
   return RID_OK;
 }
 
@@ -183,7 +234,15 @@ int rid_init(rid_handle** out, const rid_config* c) {
   if (c->omega_kind != RID_OMEGA_GAUSSIAN && c->omega_kind != RID_OMEGA_RADEMACHER)
     return fail(h, RID_EINVAL, "unknown omega_kind");
   if (c->data_dtype != RID_F64 && c->data_dtype != RID_F32) return fail(h, RID_EINVAL, "unknown data_dtype");
-  if (c->sketch_prec != RID_SKETCH_NATIVE) return fail(h, RID_EINVAL, "this build supports sketch_prec = NATIVE");
+  if (c->sketch_prec != RID_SKETCH_NATIVE && c->sketch_prec != RID_SKETCH_BF16 &&
+      c->sketch_prec != RID_SKETCH_BF16X2)
+    return fail(h, RID_EINVAL, "unknown sketch_prec");
+  if (c->sketch_prec != RID_SKETCH_NATIVE) {
+    if (c->data_dtype != RID_F32) return fail(h, RID_EINVAL, "BF16 sketches need FP32 data");
+    if (c->omega_kind != RID_OMEGA_RADEMACHER) return fail(h, RID_EINVAL, "BF16 sketches need a Rademacher Omega");
+    if (c->s + c->h > 512) return fail(h, RID_EINVAL, "BF16 sketches support s + h <= 512");
+  }
+  if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
   if (c->grad_dims != 0) return fail(h, RID_EINVAL, "this build supports grad_dims = 0");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -226,8 +285,21 @@ int rid_init(rid_handle** out, const rid_config* c) {
   int64_t gs = (d.m + 16383) / 16384;
   d.gram_split = (int)(gs < 1 ? 1 : (gs > 256 ? 256 : gs));
   const int t = d.t;
+  h->tc = c->sketch_prec != RID_SKETCH_NATIVE;
+  h->group_max = c->group_max > 0 ? c->group_max : (h->tc ? rid::kMaxGroup : rid::kMaxB);
+  {
+    const int64_t tc_chunks = (d.m + 63) / 64;
+    const int64_t want_blocks = (tc_chunks + 1) / 2;
+    h->tc_blocks = (int)(want_blocks < h->n_sm ? want_blocks : h->n_sm);
+    if (h->tc_blocks < 1) h->tc_blocks = 1;
+  }
   int rc = RID_OK;
 #define AL(ptr, n) do { if (dalloc(&(ptr), (size_t)(n)) != cudaSuccess) { rc = RID_ENOMEM; goto fail_alloc; } } while (0)
+  if (h->tc) {
+    const int nrows16 = (d.rows + 15) / 16 * 16;
+    AL(h->tc_part, (size_t)h->tc_blocks * nrows16 * 128);
+    AL(h->tc_npart, (size_t)h->tc_blocks * 128);
+  }
   {
     char* pool = nullptr;
     AL(pool, (size_t)2 * t * d.m_pad * h->esize);
@@ -252,7 +324,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
   AL(d.work, d.work_len);
   {
     char* stg = nullptr;
-    AL(stg, (size_t)rid::kMaxB * d.m_pad * h->esize);
+    AL(stg, (size_t)h->group_max * d.m_pad * h->esize);
     h->staging = stg;
   }
 #undef AL
@@ -273,6 +345,8 @@ fail_alloc:
   {
     std::string msg = rc == RID_ENOMEM ? "device allocation failed" : (h->err.empty() ? "CUDA error during init" : h->err);
     free_all(h->d, h->staging);
+    if (h->tc_part) cudaFree(h->tc_part);
+    if (h->tc_npart) cudaFree(h->tc_npart);
     delete h;
     return fail(nullptr, rc, msg);
   }
@@ -285,40 +359,24 @@ int rid_ingest(rid_handle* h, const void* cols, int64_t ld, int32_t ncols, int32
   if (ncols == 0) return RID_OK;
   if (!cols) return fail(h, RID_EINVAL, "cols is NULL");
   if (ld < h->d.m) return fail(h, RID_EINVAL, "ld < m");
-  int32_t q = 0;
-  while (q < ncols) {
-    int nb = ncols - q;
-    if (nb > rid::kMaxB) nb = rid::kMaxB;
-    if (nb > h->d.t - h->count) nb = h->d.t - h->count;
-    int rc = grow(h, h->n_obs + nb);
-    if (rc != RID_OK) return rc;
+  const size_t cbytes = (size_t)h->d.m * h->esize;
+  for (int32_t q = 0; q < ncols; ++q) {
     const char* src = (const char*)cols + (size_t)q * ld * h->esize;
-    int64_t use_ld = ld;
     if (!on_device) {
-      CK(cudaMemcpy2DAsync(h->staging, (size_t)h->d.m_pad * h->esize, src, (size_t)ld * h->esize,
-                           (size_t)h->d.m * h->esize, (size_t)nb, cudaMemcpyHostToDevice, h->st));
-      src = (const char*)h->staging;
-      use_ld = h->d.m_pad;
+      char* dst = (char*)h->staging + h->pend.size() * (size_t)h->d.m_pad * h->esize;
+      CK(cudaMemcpyAsync(dst, src, cbytes, cudaMemcpyHostToDevice, h->st));
+      src = dst;
     }
-    const int nj = rid::launch_set_jd(h->d, h->count, nb, h->n_obs, h->st);
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    if (h->prof) for (auto& e : ev) e = next_event(h);
-    const int ni = rid::launch_ingest(h->d, src, use_ld, nb, h->count, h->n_obs, h->st, h->prof ? ev : nullptr);
-    if (h->prof) {
-      h->spans[0].push_back({ev[0], ev[1]});
-      h->spans[1].push_back({ev[1], ev[2]});
-      h->kernels[0] += 1;
-      h->kernels[1] += ni - 1 + nj;
-    }
-    CK(cudaGetLastError());
-    h->count += nb;
-    h->n_obs += nb;
-    q += nb;
-    if (h->count == h->d.t) {
-      rc = run_batch(h);
+    h->pend.push_back(src);
+    const bool full = (int)h->pend.size() == h->group_max;
+    const bool batch_end = h->count + (int)h->pend.size() == h->d.t;
+    if (full || batch_end) {
+      const int rc = flush(h);
       if (rc != RID_OK) return rc;
     }
   }
+  // device columns are read before the call returns unless the caller opted into deferral
+  if (on_device && !h->cfg.defer_device_input) return flush(h);
   return RID_OK;
 }
 
@@ -326,9 +384,13 @@ int rid_finalize(rid_handle* h, int64_t* J_out, double* P_out, int64_t ldp, int3
   if (!h) return RID_EINVAL;
   const int t = h->d.t;
   if (P_out && ldp < t) return fail(h, RID_EINVAL, "ldp < t");
-  if (!h->finalized && h->count > 0) {
-    int rc = run_batch(h);
+  if (!h->finalized) {
+    int rc = flush(h);
     if (rc != RID_OK) return rc;
+    if (h->count > 0) {
+      rc = run_batch(h);
+      if (rc != RID_OK) return rc;
+    }
   }
   h->finalized = true;
   int rc = check_device_error(h);
@@ -344,6 +406,10 @@ int rid_finalize(rid_handle* h, int64_t* J_out, double* P_out, int64_t ldp, int3
 
 int rid_error_estimate(rid_handle* h, double est_sq[5], double est_fro[5], int32_t* q_star) {
   if (!h) return RID_EINVAL;
+  {
+    const int rc = flush(h);
+    if (rc != RID_OK) return rc;
+  }
   if (h->batch == 0) return fail(h, RID_ESTATE, "no batch step has run yet");
   double e[4];
   int meta[rid::META_LEN];
@@ -360,11 +426,15 @@ int rid_error_estimate(rid_handle* h, double est_sq[5], double est_fro[5], int32
   return RID_OK;
 }
 
-int64_t rid_n_obs(const rid_handle* h) { return h ? h->n_obs : -1; }
+int64_t rid_n_obs(const rid_handle* h) { return h ? h->n_obs + (int64_t)h->pend.size() : -1; }
 
 int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device) {
   if (!h || !out) return RID_EINVAL;
   if (ld < h->d.m) return fail(h, RID_EINVAL, "ld < m");
+  {
+    const int rc = flush(h);
+    if (rc != RID_OK) return rc;
+  }
   const int t = h->d.t;
   std::vector<int> slot(t);
   std::vector<int64_t> jc(t);
@@ -389,6 +459,10 @@ int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device) {
 
 int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
   if (!h || !out) return RID_EINVAL;
+  {
+    const int rc = flush(h);
+    if (rc != RID_OK) return rc;
+  }
   const Dev& d = h->d;
   const int64_t n = h->n_obs;
   const void* src = nullptr;
@@ -462,6 +536,8 @@ int rid_profile_read(rid_handle* h, double ms[3], int64_t kernels[3], int64_t gr
 
 int rid_sync(rid_handle* h) {
   if (!h) return RID_EINVAL;
+  const int rc = flush(h);
+  if (rc != RID_OK) return rc;
   return check_device_error(h);
 }
 
@@ -470,6 +546,7 @@ int rid_reset(rid_handle* h) {
   const int nk = rid::launch_reset_state(h->d, h->st);
   if (h->prof) h->kernels[1] += nk;
   CK(cudaGetLastError());
+  h->pend.clear();
   h->count = 0;
   h->n_obs = 0;
   h->n_prev = 0;
@@ -487,6 +564,8 @@ void rid_destroy(rid_handle* h) {
   cudaStreamSynchronize(h->st);
   for (auto e : h->evpool) cudaEventDestroy(e);
   free_all(h->d, h->staging);
+  if (h->tc_part) cudaFree(h->tc_part);
+  if (h->tc_npart) cudaFree(h->tc_npart);
   delete h;
 }
 

@@ -84,13 +84,24 @@ enum {
 enum { SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_LEN = 8 };
 
 // device error bits
-enum { ERR_NONFINITE = 1, ERR_CHOL = 2, ERR_EIG = 4 };
+enum { ERR_NONFINITE = 1, ERR_CHOL = 2, ERR_EIG = 4, ERR_TIMEOUT = 8 };
 
-// ingest.cu
-// Returns the number of kernels launched; ev[0..2] (may be null) are recorded before the
-// sketch kernel, after it, and after the reductions.
-int launch_ingest(const Dev& d, const void* src, int64_t ld, int nb, int count, int64_t n_obs,
+constexpr int kMaxGroup = 64;      // columns per tensor-core ingest launch
+
+// ingest.cu: SIMT path (FP64 or FP32, native precision), nb <= kMaxB columns given by
+// pointer.  Returns the number of kernels launched; ev[0..2] (may be null) are recorded
+// before the sketch kernel, after it, and after the reductions.
+int launch_ingest(const Dev& d, const void* const* cols, int nb, int count, int64_t n_obs,
                   cudaStream_t st, cudaEvent_t* ev);
+// SS^T update for nb new columns (shared by both ingest paths).
+void launch_gram_update(const Dev& d, int nb, int64_t n_obs, cudaStream_t st);
+
+// tc_ingest.cu: tensor-core path for FP32 data (ncols <= kMaxGroup); records ev[0], ev[1]
+// around the sketch kernel and launches the reduction.  Returns 0 on success.
+int launch_tc_ingest(const Dev& d, const void* const* cols, int ncols, int split, int count,
+                     int64_t n_obs, int nblk, float* part, double* npart, cudaStream_t st,
+                     cudaEvent_t* ev);
+int tc_smem_bytes();
 void launch_materialize_omega(const Dev& d, cudaStream_t st);
 
 // batch.cu

@@ -1,0 +1,421 @@
+// Tensor-core ingest for FP32 snapshots (sm_103a, tcgen05 + TMEM).
+//
+// One launch sketches a group of G <= 64 (split) or <= 128 (hi only) columns:
+//   S(:, q) = Omega a_q  for every left and probe row of Omega (Algorithm 3),
+// while copying each column into its buffer slot and accumulating its squared
+// norm -- one HBM read of each column.
+//
+// MMA mapping (kind::f16, BF16 operands, FP32 accumulation in TMEM):
+//   A (M = 128, K-major): rows are the data columns, split a = hi + lo in BF16
+//                         (row q = hi(a_q), row 64 + q = lo(a_q)), or hi only.
+//   B (N <= 256 per tile, K-major): rows of Omega, +-1 exactly representable in
+//                         BF16, generated on chip from the counter-based generator.
+//   D (128 x R16 FP32 in TMEM): D[q][r] = sum_i A[q][i] Omega[r][i].
+// The contraction runs over the coordinates; each CTA owns a contiguous range
+// of 64-coordinate chunks and keeps its partial D in TMEM for the whole range
+// (split-K over the SMs); a deterministic FP64 reduction adds the partials.
+//
+// Warp roles: warp 0 allocates TMEM and one lane issues the MMAs; warps 1..8
+// produce both operands (HBM loads with a two-chunk register prefetch, the
+// split into BF16, the copy to the buffer slot, Philox expansion of Omega) and
+// then read the accumulators back.  Two SMEM stages, mbarrier hand-off, every
+// wait bounded (on timeout: error flag, drain, free TMEM, return).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "philox.cuh"
+#include "rid_internal.cuh"
+
+namespace rid {
+
+namespace {
+
+constexpr int kChunkK = 64;                 // coordinates per chunk: one 128-byte BF16 row
+constexpr int kProducerWarps = 8;
+constexpr int kThreads = 32 * (1 + kProducerWarps);
+constexpr int kATile = 128 * 128;           // 128 rows x 128 bytes
+constexpr int kBTile = 512 * 128;           // up to 512 Omega rows x 128 bytes
+constexpr int kSmemBytes = 2 * kATile + 2 * kBTile + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after kWaitLimit polls (or when another role gave up),
+// raising the CTA abort flag and the device error word.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (it > 32) __nanosleep(128);
+  }
+  *abort_flag = 1;
+  atomicOr(err, ERR_TIMEOUT);
+  return false;
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
+  d |= (uint64_t)1u << 16;                     // leading byte offset (unused when K fits the swizzle)
+  d |= (uint64_t)(1024u >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)1u << 46;                     // descriptor version
+  d |= (uint64_t)2u << 61;                     // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Byte offset of the 16-byte chunk c of row r in a K-major SW128 tile.
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+               : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const uint32_t a = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo));
+  const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi));
+  return a | (b << 16);
+}
+
+struct Cols {
+  const float* p[128];
+};
+
+// 16 coordinates of one column: 4 float4 (aligned) or guarded scalars.
+__device__ __forceinline__ void load16(const float* src, int64_t i, int64_t m, bool vec, float4 (&v)[4]) {
+  if (vec && i + 16 <= m) {
+    const float4* s = reinterpret_cast<const float4*>(src + i);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __ldcs(s + j);
+  } else {
+    float t[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) t[j] = (i + j < m) ? src[i + j] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = make_float4(t[4 * j], t[4 * j + 1], t[4 * j + 2], t[4 * j + 3]);
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16, int n1, int n2,
+                 int64_t chunks_per_cta, int vec, float* __restrict__ part, double* __restrict__ npart) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t sA = base;                       // 2 x 16 KB
+  const uint32_t sB = base + 2 * kATile;          // 2 x 64 KB
+  const uint32_t sBar = sB + 2 * kBTile;          // full[2], empty[2], done
+  uint8_t* gbar = gbase + (sBar - base);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 64);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 72);
+  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 16, bar_done = sBar + 32;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
+  const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
+  int64_t c1 = c0 + chunks_per_cta;
+  if (c1 > nchunks) c1 = nchunks;
+  const int64_t nch = c1 > c0 ? c1 - c0 : 0;
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar_full0, 32 * kProducerWarps);
+    mbar_init(bar_full0 + 8, 32 * kProducerWarps);
+    mbar_init(bar_empty0, 1);
+    mbar_init(bar_empty0 + 8, 1);
+    mbar_init(bar_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t id1 = idesc_bf16(128, n1);
+      const uint32_t id2 = idesc_bf16(128, n2 > 0 ? n2 : 16);
+      for (int64_t c = 0; c < nch; ++c) {
+        const int st = (int)(c & 1);
+        const uint32_t par = (uint32_t)((c >> 1) & 1);
+        if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err)) break;
+        tc_fence_after();
+        const uint64_t da = desc_sw128(sA + st * kATile);
+        const uint64_t db1 = desc_sw128(sB + st * kBTile);
+        const uint64_t db2 = desc_sw128(sB + st * kBTile + 256 * 128);
+#pragma unroll
+        for (int kk = 0; kk < kChunkK / 16; ++kk) {
+          const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t adv = (uint64_t)(kk * 2);            // +32 bytes along K
+          tc_mma(tmem, da + adv, db1 + adv, id1, acc);
+          if (n2 > 0) tc_mma(tmem + (uint32_t)n1, da + adv, db2 + adv, id2, acc);
+        }
+        tc_commit(bar_empty0 + 8 * st);
+      }
+      tc_commit(bar_done);   // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- producers
+    const int pt = threadIdx.x - 32;          // 0..255
+    const int q = pt >> 2, g = pt & 3;        // data task: column q, 16-coordinate segment g
+    const bool has_col = q < ncols;
+    const float* src = has_col ? cols.p[q] : nullptr;
+    float* dstp = has_col ? (float*)d.pool + (int64_t)d.dslot[count + q] * d.m_pad : nullptr;
+    const int r0 = pt, r1 = pt + 256;         // Omega rows of this thread
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    double nrm = 0.0;
+    uint32_t keep0[2] = {0u, 0u}, keep1[2] = {0u, 0u};
+    float4 bufA[4], bufB[4];
+    auto load_chunk = [&](int64_t c, float4 (&v)[4]) {
+      if (has_col && c < nch) load16(src, (c0 + c) * kChunkK + 16 * g, d.m, vec != 0, v);
+    };
+    auto omega_row = [&](int r, int64_t cg, uint32_t (&keep)[2], uint32_t bst) {
+      uint32_t wa, wb;
+      if ((cg & 1) == 0) {
+        const u32x4 w = philox4x32_10((uint32_t)(cg >> 1), (uint32_t)r, kTagRademacher, 0, k0, k1);
+        wa = w.x; wb = w.y; keep[0] = w.z; keep[1] = w.w;
+      } else {
+        wa = keep[0]; wb = keep[1];
+      }
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        const uint32_t w = (cc < 4) ? wa : wb;
+        const int p0 = 4 * (cc & 3);
+        const uint32_t v0 = ((w << (p0 + 0)) & 0x80008000u) | 0x3F803F80u;
+        const uint32_t v1 = ((w << (p0 + 1)) & 0x80008000u) | 0x3F803F80u;
+        const uint32_t v2 = ((w << (p0 + 2)) & 0x80008000u) | 0x3F803F80u;
+        const uint32_t v3 = ((w << (p0 + 3)) & 0x80008000u) | 0x3F803F80u;
+        sts128(bst + sw128_off(r, cc), v0, v1, v2, v3);
+      }
+    };
+    auto process = [&](int64_t c, float4 (&v)[4]) -> bool {
+      const int st = (int)(c & 1);
+      const uint32_t par = (uint32_t)(((c >> 1) & 1) ^ 1);
+      if (!mbar_wait(bar_empty0 + 8 * st, par, abort_flag, d.err)) return false;
+      const int64_t cg = c0 + c;
+      const int64_t i0 = cg * kChunkK + 16 * g;
+      const uint32_t ast = sA + st * kATile;
+      if (has_col) {
+        float x[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { x[4 * j] = v[j].x; x[4 * j + 1] = v[j].y; x[4 * j + 2] = v[j].z; x[4 * j + 3] = v[j].w; }
+        // copy into the buffer slot
+        if (i0 + 16 <= d.m) {
+          float4* o = reinterpret_cast<float4*>(dstp + i0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) __stcs(o + j, v[j]);
+        } else {
+          for (int j = 0; j < 16; ++j) if (i0 + j < d.m) dstp[i0 + j] = x[j];
+        }
+        float s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) s2 = fmaf(x[j], x[j], s2);
+        nrm += (double)s2;
+        uint32_t hw[8], lw[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float a = x[2 * j], b = x[2 * j + 1];
+          const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+          hw[j] = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+          lw[j] = pack_bf16(a - __bfloat162float(ha), b - __bfloat162float(hb));
+        }
+        sts128(ast + sw128_off(q, 2 * g), hw[0], hw[1], hw[2], hw[3]);
+        sts128(ast + sw128_off(q, 2 * g + 1), hw[4], hw[5], hw[6], hw[7]);
+        if (split) {
+          sts128(ast + sw128_off(64 + q, 2 * g), lw[0], lw[1], lw[2], lw[3]);
+          sts128(ast + sw128_off(64 + q, 2 * g + 1), lw[4], lw[5], lw[6], lw[7]);
+        }
+      }
+      const uint32_t bst = sB + st * kBTile;
+      if (r0 < nrows16) omega_row(r0, cg, keep0, bst);
+      if (r1 < nrows16) omega_row(r1, cg, keep1, bst);
+      fence_async_smem();
+      mbar_arrive(bar_full0 + 8 * st);
+      return true;
+    };
+    load_chunk(0, bufA);
+    load_chunk(1, bufB);
+    for (int64_t c = 0; c < nch; c += 2) {
+      if (!process(c, bufA)) break;
+      load_chunk(c + 2, bufA);
+      if (c + 1 < nch) {
+        if (!process(c + 1, bufB)) break;
+        load_chunk(c + 3, bufB);
+      }
+    }
+    // squared norms: the four segment threads of a column are adjacent lanes
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, 1);
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, 2);
+    if (has_col && g == 0) npart[(size_t)blockIdx.x * 128 + q] = nrm;
+
+    // ---------------------------------------------------------------- epilogue (warps 1..4)
+    if (warp <= 4) {
+      const bool ok = mbar_wait(bar_done, 0, abort_flag, d.err);
+      tc_fence_after();
+      if (ok && !*abort_flag) {
+        const int quarter = warp & 3;           // TMEM lanes 32*quarter .. +31
+        const int L = 32 * quarter + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+        for (int cb = 0; cb < nrows16; cb += 32) {
+          uint32_t r[32];
+          tc_ld32(taddr + (uint32_t)cb, r);
+          tc_wait_ld();
+          float* o = part + ((size_t)blockIdx.x * nrows16 + cb) * 128 + L;
+          const int jn = (nrows16 - cb < 32) ? nrows16 - cb : 32;   // rows of this CTA's slice only
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < jn) o[(size_t)j * 128] = (nch > 0) ? __uint_as_float(r[j]) : 0.f;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// S(:, n_obs + q) = sum over CTAs of the hi (and lo) rows; norms in CTA order.
+__global__ void tc_reduce_kernel(Dev d, const float* __restrict__ part, const double* __restrict__ npart,
+                                 int nblk, int ncols, int split, int nrows16, int64_t n_obs) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < ncols * d.rows) {
+    const int q = idx % ncols, r = idx / ncols;
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      const float* p = part + ((size_t)b * nrows16 + r) * 128;
+      v += (double)p[q];
+      if (split) v += (double)p[64 + q];
+    }
+    d.S[(size_t)(n_obs + q) * d.rows + r] = v;
+  }
+  if (idx == 0) {
+    for (int q = 0; q < ncols; ++q) {
+      double v = 0.0;
+      for (int b = 0; b < nblk; ++b) v += npart[(size_t)b * 128 + q];
+      if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
+      d.fro2[0] += v;
+      d.fro2[1] += v;
+    }
+  }
+}
+
+int tc_smem_bytes() { return kSmemBytes; }
+
+// Launch the tensor-core sketch of ncols columns; returns 0 on success.
+int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split, int count,
+                     int64_t n_obs, int nblk, float* part, double* npart, cudaStream_t st,
+                     cudaEvent_t* ev) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes) != cudaSuccess)
+      return -1;
+    attr_set = true;
+  }
+  Cols c;
+  bool vec = true;
+  for (int q = 0; q < 128; ++q) {
+    c.p[q] = q < ncols ? (const float*)colp[q] : nullptr;
+    if (q < ncols && ((uintptr_t)colp[q] & 15u)) vec = false;
+  }
+  const int nrows16 = (d.rows + 15) / 16 * 16;
+  const int n1 = nrows16 < 256 ? nrows16 : 256;
+  const int n2 = nrows16 - n1;
+  const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
+  int64_t per = (nchunks + nblk - 1) / nblk;
+  per = (per + 1) / 2 * 2;                      // even: Philox words are shared by chunk pairs
+  if (ev) cudaEventRecord(ev[0], st);
+  tc_ingest_kernel<<<nblk, kThreads, kSmemBytes, st>>>(d, c, ncols, split, count, nrows16, n1, n2, per,
+                                                       vec ? 1 : 0, part, npart);
+  if (ev) cudaEventRecord(ev[1], st);
+  const int n = ncols * d.rows;
+  tc_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, part, npart, nblk, ncols, split, nrows16, n_obs);
+  return 0;
+}
+
+}  // namespace rid

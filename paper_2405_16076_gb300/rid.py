@@ -14,7 +14,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librid.so")
 
-RID_OK, RID_EINVAL, RID_ENOMEM, RID_ECUDA, RID_ESTATE, RID_ENONFINITE, RID_ENOLIB = 0, -1, -2, -3, -4, -5, -6
+RID_OK, RID_EINVAL, RID_ENOMEM, RID_ECUDA, RID_ESTATE, RID_ENONFINITE, RID_ENOLIB, RID_ETIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 RID_LAMBDA_STREAMING, RID_LAMBDA_FIXED = 0, 1
 RID_OMEGA_GAUSSIAN, RID_OMEGA_RADEMACHER = 0, 1
 RID_F64, RID_F32 = 0, 1
@@ -31,7 +32,8 @@ class rid_config(ctypes.Structure):
         ("lambda_fixed", ctypes.c_double), ("omega_kind", ctypes.c_int32), ("data_dtype", ctypes.c_int32),
         ("sketch_prec", ctypes.c_int32), ("grad_dims", ctypes.c_int32), ("nx", ctypes.c_int32),
         ("ny", ctypes.c_int32), ("nfields", ctypes.c_int32), ("n_max", ctypes.c_int64),
-        ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
+        ("seed", ctypes.c_uint64), ("group_max", ctypes.c_int32), ("defer_device_input", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
     ]
 
 
@@ -107,7 +109,7 @@ class OnlineRID:
 
     def __init__(self, m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
                  lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
-                 sketch="native", n_max=1024, seed=0, stream=None):
+                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False):
         cfg = rid_config()
         _check(rid_config_default(ctypes.byref(cfg)))
         cfg.m, cfg.k, cfg.s, cfg.h = int(m), int(k), int(s), int(h)
@@ -119,6 +121,8 @@ class OnlineRID:
         cfg.sketch_prec = {"native": RID_SKETCH_NATIVE, "bf16": RID_SKETCH_BF16, "bf16x2": RID_SKETCH_BF16X2}[sketch]
         cfg.n_max = int(n_max)
         cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        cfg.group_max = int(group_max)
+        cfg.defer_device_input = 1 if defer else 0
         cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         self.cfg = cfg
         self.t = int(k)

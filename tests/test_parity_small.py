@@ -61,13 +61,20 @@ def assert_parity(o, Jo, Po, g, Jg, Pg, A):
     if not np.array_equal(Jg, Jo):
         assert min(o.margins) <= MARGIN, (Jg, Jo, min(o.margins))
         return False
+    # Algorithms 5 and 7 solve through the Gram matrix A_J^T A_J, so two correct FP64
+    # implementations agree to ~kappa(A_J)^2 * eps; the bar is 1e-10 unless the basis is
+    # ill-conditioned enough for that bound to exceed it.
+    act = Jo >= 0
+    kappa = np.linalg.cond(A[:, Jo[act]]) if act.any() else 1.0
+    tol = max(P_TOL, 10.0 * kappa ** 2 * np.finfo(np.float64).eps)
     err = np.linalg.norm(Pg - Po) / max(np.linalg.norm(Po), 1e-300)
-    assert err <= P_TOL, err
+    assert err <= tol, (err, tol, kappa)
     sq, fro_est, q = g.error_estimate()
     est_o, q_o = o.error_estimates()
-    assert np.abs(sq[1:] - est_o).max() <= 1e-9 * o.fro2, (sq[1:], est_o)
+    etol = max(1e-9, 10.0 * kappa ** 2 * np.finfo(np.float64).eps) * o.fro2
+    assert np.abs(sq[1:] - est_o).max() <= etol, (sq[1:], est_o)
     srt = np.sort(est_o)
-    if srt[1] - srt[0] > 1e-9 * o.fro2:
+    if srt[1] - srt[0] > 2 * etol:
         assert q == q_o
     return True
 
