@@ -16,8 +16,9 @@ namespace rid {
 
 // ---------------------------------------------------------------- work layout
 struct WorkLayout {
-  int64_t eigA, eigD, eigE, eigV, eigP;   // lambda
-  int64_t cholM;                          // s x s
+  int64_t eigA, eigD, eigE, eigV, eigP;   // tridiagonalization of the sketch Gram
+  int64_t beta, vhead, mu, ldld, ldll;    // reflectors, top-k eigenvalues, LDL^T of T + lambda I
+  int64_t unif;                           // uniforms of the prune/refill decisions
   int64_t vec;                            // per-warp vectors (scores / applies)
   int64_t SJ, HJ, G, Gq, Gc, T;           // gathered sketch data and Grams
   int64_t QR4, b4, h4, QR6, b6, h6;       // Householder factors
@@ -43,7 +44,8 @@ static WorkLayout layout(const Dev& d) {
   int64_t o = 0;
   auto take = [&](int64_t n) { int64_t r = o; o += (n + 31) / 32 * 32; return r; };
   w.eigA = take(s * s); w.eigD = take(s); w.eigE = take(s); w.eigV = take(s); w.eigP = take(s);
-  w.cholM = take(s * s);
+  w.beta = take(s); w.vhead = take(s); w.mu = take(t); w.ldld = take(s); w.ldll = take(s);
+  w.unif = take(t * (t + 1));
   w.vec = take(nw * (s > t ? s : t));
   w.SJ = take(s * t); w.HJ = take(hh * t); w.G = take(t * t); w.Gq = take(t * t);
   w.Gc = take(t * t); w.T = take(t * t);
@@ -58,86 +60,38 @@ static WorkLayout layout(const Dev& d) {
 
 int64_t work_doubles(const Dev& d) { return layout(d).total; }
 
-// ---------------------------------------------------------------- lambda and scores
-__global__ void __launch_bounds__(512) lambda_chol_kernel(Dev d, WorkLayout w) {
-  __shared__ double sh[33];
-  __shared__ int fail;
-  const int s = d.s, tid = threadIdx.x;
-  const double inv_s = 1.0 / (double)s;
-  if (tid == 0) fail = 0;
-  double lam;
-  if (d.lambda_mode == 1) {
-    lam = d.lambda_fixed;
-  } else {
-    double* A = d.work + w.eigA;
-    for (int64_t i = tid; i < (int64_t)s * s; i += blockDim.x) A[i] = d.SSt[i] / (double)s;
-    __syncthreads();
-    cta_tridiagonalize(A, s, s, d.work + w.eigD, d.work + w.eigE, d.work + w.eigV, d.work + w.eigP, sh);
-    // top-k eigenvalues: indices s-1 .. s-k in ascending order
-    const int k = d.t;
-    double part = 0.0;
-    for (int j = tid; j < k && j < s; j += blockDim.x)
-      part += tridiag_eig_bisect(d.work + w.eigD, d.work + w.eigE, s, s - 1 - j);
-    const double topk = block_sum(part, sh);
-    const double fro = d.fro2[1];
-    lam = (fro - topk) / (double)k;
-    lam = fmax(lam, 1e-12 * fro / (double)k);
-  }
-  if (tid == 0) d.scal[SCAL_LAMBDA] = lam;
-  double* M = d.work + w.cholM;
-  for (int64_t idx = tid; idx < (int64_t)s * s; idx += blockDim.x) {
-    const int i = (int)(idx % s), j = (int)(idx / s);
-    M[idx] = d.SSt[idx] * inv_s + ((i == j) ? lam : 0.0);
-  }
-  // tolerance: pivots below 1e-300 are treated as zero (semi-definite M when lambda == 0)
-  cta_cholesky(M, s, s, 1e-300, &fail);
-  if (tid == 0 && fail && lam > 0.0) atomicOr(d.err, ERR_CHOL);
+// ---------------------------------------------------------------- prune / refill
+// The uniforms of every possible decision, u(batch, i, r), drawn in parallel.
+__global__ void uniforms_kernel(Dev d, double* unif, int count, int batch) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = count + 1;
+  if (idx >= d.t * per) return;
+  const int i = idx / per, r = idx % per;
+  unif[idx] = sample_uniform(d.seed, (uint32_t)batch, (uint32_t)i, (uint32_t)r);
 }
 
-// One warp per vector: occupied C slots (i < t) and buffered D columns (t <= i < t+count).
-__global__ void __launch_bounds__(kApplyThreads) scores_kernel(Dev d, WorkLayout w, int count) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int s = d.s;
-  const double rs = 1.0 / sqrt((double)s);
-  const double* L = d.work + w.cholM;
-  double* b = d.work + w.vec + (size_t)gw * (s > d.t ? s : d.t);
-  for (int v = gw; v < d.t + count; v += nwarps) {
-    int64_t col;
-    if (v < d.t) { col = d.JC[v]; if (col < 0) { if (lane == 0) d.tauC[v] = 1.0; continue; } }
-    else col = d.JD[v - d.t];
-    const double* l = d.Slev + (size_t)col * d.lev_ld;
-    for (int i = lane; i < s; i += 32) b[i] = l[i] * rs;
-    __syncwarp();
-    warp_trsv_lower(L, s, s, b);
-    double acc = 0.0;
-    for (int i = lane; i < s; i += 32) acc += b[i] * b[i];
-    acc = warp_sum(acc);
-    if (lane == 0) { if (v < d.t) d.tauC[v] = acc; else d.tauD[v - d.t] = acc; }
-    __syncwarp();
-  }
-}
-
-// ---------------------------------------------------------------- prune / refill (one thread)
-__global__ void select_kernel(Dev d, int count, int batch) {
+// The sequential scan of Algorithm 3 over the slots (one thread).  A buffered column
+// has a larger index than every column of the previous basis, so it can only be in C
+// already if an earlier slot of this scan took it (the taken[] flags).
+__global__ void select_kernel(Dev d, const double* unif, int count) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int t = d.t, two_t = 2 * t;
+  const int t = d.t, two_t = 2 * t, per = count + 1;
+  int* taken = d.isnew;            // scratch flags over the buffered columns; rewritten below
+  for (int r = 0; r < count; ++r) taken[r] = 0;
   for (int i = 0; i < t; ++i) {
+    const double* u = unif + (size_t)i * per;
     if (d.JC[i] >= 0) {
       const double tc = fmin(d.tau_old[i], d.tauC[i]);
-      const double u = sample_uniform(d.seed, (uint32_t)batch, (uint32_t)i, 0u);
-      if (u < 1.0 - tc / d.tau_old[i]) { d.JC[i] = -1; d.slotC[i] = -1; d.tau_old[i] = 1.0; }
+      if (u[0] < 1.0 - tc / d.tau_old[i]) { d.JC[i] = -1; d.slotC[i] = -1; d.tau_old[i] = 1.0; }
       else d.tau_old[i] = tc;
     }
     if (d.JC[i] < 0) {
       for (int r = 0; r < count; ++r) {
         const double p = fmin(fmax(d.tauD[r] * d.refill_scale, 0.0), 1.0);
-        const double u = sample_uniform(d.seed, (uint32_t)batch, (uint32_t)i, (uint32_t)(1 + r));
-        if (u < p) {
-          bool inC = false;
-          for (int x = 0; x < t; ++x) inC |= (d.JC[x] == d.JD[r]);
-          if (!inC) { d.JC[i] = d.JD[r]; d.slotC[i] = d.dslot[r]; d.tau_old[i] = d.tauD[r]; break; }
+        if (u[1 + r] < p && !taken[r]) {
+          taken[r] = 1;
+          d.JC[i] = d.JD[r]; d.slotC[i] = d.dslot[r]; d.tau_old[i] = d.tauD[r];
+          break;
         }
       }
     }
@@ -156,24 +110,22 @@ __global__ void select_kernel(Dev d, int count, int batch) {
   }
   int npa = 0;
   for (int i = 0; i < t; ++i) if (d.JC_prev[i] >= 0) d.pact[npa++] = i;
-  // Gram targets: pool slots of the current and the previous basis (distinct)
+  // Gram targets: pool slots of the current and the previous basis (distinct); the
+  // flags over the 2t pool slots live in tauD's storage after its last use above
+  int* used = (int*)d.tauD;
+  for (int ps = 0; ps < two_t; ++ps) used[ps] = 0;
   int nt = 0;
-  for (int a = 0; a < na; ++a) d.gtgt[nt++] = d.slotC[d.act[a]];
+  for (int a = 0; a < na; ++a) { const int ps = d.slotC[d.act[a]]; d.gtgt[nt++] = ps; used[ps] = 1; }
   for (int b = 0; b < npa; ++b) {
     const int ps = d.slotC_prev[d.pact[b]];
-    bool dup = false;
-    for (int x = 0; x < nt; ++x) dup |= (d.gtgt[x] == ps);
-    if (!dup) d.gtgt[nt++] = ps;
+    if (!used[ps]) { d.gtgt[nt++] = ps; used[ps] = 2; }
   }
   d.meta[META_NACT] = na; d.meta[META_NPACT] = npa; d.meta[META_NNEW] = nn;
   d.meta[META_NTGT] = nt; d.meta[META_NKEPT] = nk;
   // buffer slots for the next batch: the first t pool slots not used by the new basis
   int q = 0;
-  for (int ps = 0; ps < two_t && q < t; ++ps) {
-    bool used = false;
-    for (int i = 0; i < t; ++i) used |= (d.slotC[i] == ps);
-    if (!used) d.dslot[q++] = ps;
-  }
+  for (int ps = 0; ps < two_t && q < t; ++ps)
+    if (used[ps] != 1) d.dslot[q++] = ps;
 }
 
 // ---------------------------------------------------------------- basis Gram
@@ -664,10 +616,12 @@ int launch_reset_state(const Dev& d, cudaStream_t st) {
 int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
                       cudaStream_t st) {
   const WorkLayout w = layout(d);
-  lambda_chol_kernel<<<1, 512, 0, st>>>(d, w);
-  const int nvec = d.t + count;
-  scores_kernel<<<(nvec + 7) / 8, kApplyThreads, 0, st>>>(d, w, count);
-  select_kernel<<<1, 32, 0, st>>>(d, count, batch);
+  int nk = launch_lambda_scores(d, count, d.work, w.eigA, w.eigD, w.eigE, w.beta, w.vhead, w.eigP,
+                                w.mu, w.ldld, w.ldll, w.vec, (d.s > d.t ? d.s : d.t), d.gbar, d.n_sm, st);
+  if (nk == 0) return 0;
+  const int nu = d.t * (count + 1);
+  uniforms_kernel<<<(nu + 255) / 256, 256, 0, st>>>(d, d.work + w.unif, count, batch);
+  select_kernel<<<1, 32, 0, st>>>(d, d.work + w.unif, count);
   dim3 gg((d.t + 63) / 64, (2 * d.t + 63) / 64, d.gram_split);
   if (d.dtype == 0) basis_gram_kernel<double><<<gg, 256, 0, st>>>(d);
   else basis_gram_kernel<float><<<gg, 256, 0, st>>>(d);
@@ -679,7 +633,7 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   hutch_finish_kernel<<<4, 256, 0, st>>>(d, w, nchunk);
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
-  return 12;
+  return nk + 11;
 }
 
 }  // namespace rid

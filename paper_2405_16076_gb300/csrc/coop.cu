@@ -1,0 +1,292 @@
+// Multi-SM FP64 kernels for the sketch Gram M = S_lev S_lev^T / s of the batch step.
+//
+// GB300's FP64 rate is ~2 FMA/clk per SM, so the O(s^3) reduction is spread
+// over every SM with a grid barrier between the dependent phases:
+//   * tridiag_coop_kernel: Householder reduction M = Q T Q^T (T tridiagonal),
+//     reflectors kept in place for later use;
+//   * topk_eig_kernel: the k largest eigenvalues of T by 32-way multisection of
+//     Sturm counts (one warp per eigenvalue), then
+//     lambda = (||A_obs||^2 - sum of the k largest) / k  (Eq. 23, floored);
+//   * tri_scores_kernel: sketched ridge scores (Eq. 23)
+//     tau = v^T (M + lambda I)^{-1} v = y^T (T + lambda I)^{-1} y with y = Q^T v,
+//     using the stored reflectors and one LDL^T of the SPD tridiagonal T + lambda I.
+// The grid barrier is a counter/generation pair with a bounded spin; on timeout
+// the kernel raises ERR_TIMEOUT and every block stops at its next barrier.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "linalg.cuh"
+#include "rid_internal.cuh"
+
+namespace rid {
+
+namespace {
+
+constexpr int kCoopThreads = 256;
+constexpr uint32_t kBarrierSpin = 1u << 24;
+
+struct GridBar {
+  unsigned int* count;
+  unsigned int* gen;
+  int* err;
+  int* stop;   // set when any barrier timed out
+};
+
+// Returns false if the barrier timed out (or another block's did).
+__device__ bool grid_barrier(const GridBar& b) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* vgen = b.gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(b.count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      uint32_t it = 0;
+      while (*vgen == g) {
+        if (++it > kBarrierSpin || *(volatile int*)b.stop) { ok = 0; break; }
+        if (it > 64) __nanosleep(64);
+      }
+      if (!ok) {
+        atomicExch(b.stop, 1);
+        atomicOr(b.err, ERR_TIMEOUT);
+      }
+    }
+    __threadfence();
+    ok_s = ok && !*(volatile int*)b.stop;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+}  // namespace
+
+// A (s x s, column-major) <- M, then reduced in place.  On exit: d[0..s), e[0..s-1),
+// reflector k = [vhead[k]; A(k+2:s, k)] acting on rows k+1..s-1 with coefficient beta[k].
+__global__ void __launch_bounds__(kCoopThreads)
+tridiag_coop_kernel(Dev d, double* A, double* dvec, double* evec, double* beta, double* vhead,
+                    double* pglob, GridBar bar) {
+  extern __shared__ double sm[];
+  const int n = d.s;
+  double* v = sm;            // n
+  double* w = sm + n;        // n
+  __shared__ double sh[33];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const double inv_s = 1.0 / (double)n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < (int64_t)n * n; i += (int64_t)gridDim.x * blockDim.x)
+    A[i] = d.SSt[i] * inv_s;
+  if (!grid_barrier(bar)) return;
+  for (int k = 0; k + 2 < n; ++k) {
+    const int nn = n - k - 1;
+    const double* x = A + (k + 1) + (size_t)k * n;
+    double part = 0.0;
+    for (int i = tid; i < nn; i += blockDim.x) { const double xi = x[i]; v[i] = xi; part += xi * xi; }
+    const double nrm2 = block_sum(part, sh);
+    const double x0 = v[0];
+    const double tail = nrm2 - x0 * x0;
+    const double nrm = sqrt(nrm2);
+    const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    const double vtv = tail + v0 * v0;
+    const double bt = (tail > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
+    __syncthreads();
+    if (tid == 0) v[0] = v0;
+    if (blockIdx.x == 0 && tid == 0) {
+      dvec[k] = A[k + (size_t)k * n];
+      evec[k] = (bt > 0.0) ? alpha : x0;
+      beta[k] = bt;
+      vhead[k] = v0;
+    }
+    __syncthreads();
+    if (bt == 0.0) continue;                   // uniform over the grid: same data, same arithmetic
+    double* Ab = A + (k + 1) + (size_t)(k + 1) * n;
+    // p = beta * A' v (A' symmetric: row i read as column i); rows split over blocks, warp per row
+    for (int i = blockIdx.x * nw + wid; i < nn; i += gridDim.x * nw) {
+      const double* col = Ab + (size_t)i * n;
+      double acc = 0.0;
+      for (int j = lane; j < nn; j += 32) acc += col[j] * v[j];
+      acc = warp_sum(acc);
+      if (lane == 0) pglob[i] = bt * acc;
+    }
+    if (!grid_barrier(bar)) return;
+    part = 0.0;
+    for (int i = tid; i < nn; i += blockDim.x) { const double pi = pglob[i]; w[i] = pi; part += pi * v[i]; }
+    const double ptv = block_sum(part, sh);
+    const double kc = 0.5 * bt * ptv;
+    for (int i = tid; i < nn; i += blockDim.x) w[i] -= kc * v[i];
+    __syncthreads();
+    // A' -= v w^T + w v^T on the columns of this block
+    for (int j = blockIdx.x * nw + wid; j < nn; j += gridDim.x * nw) {
+      double* col = Ab + (size_t)j * n;
+      const double wj = w[j], vj = v[j];
+      for (int i = lane; i < nn; i += 32) col[i] -= v[i] * wj + w[i] * vj;
+    }
+    if (!grid_barrier(bar)) return;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (n >= 2) {
+      dvec[n - 2] = A[(n - 2) + (size_t)(n - 2) * n];
+      evec[n - 2] = A[(n - 1) + (size_t)(n - 2) * n];
+      beta[n - 2] = 0.0;
+    }
+    dvec[n - 1] = A[(n - 1) + (size_t)(n - 1) * n];
+  }
+}
+
+// One warp per requested eigenvalue index j (ascending order): 32-point multisection
+// of the Sturm count until the bracket stops shrinking.
+__global__ void topk_eig_kernel(Dev d, const double* dvec, const double* evec, int k, double* mu) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n = d.s;
+  if (gw >= k || gw >= n) return;
+  const int j = n - 1 - gw;                    // the gw-th largest
+  double lo = dvec[0], hi = dvec[0], emax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = ((i > 0) ? fabs(evec[i - 1]) : 0.0) + ((i + 1 < n) ? fabs(evec[i]) : 0.0);
+    lo = fmin(lo, dvec[i] - r);
+    hi = fmax(hi, dvec[i] + r);
+    if (i + 1 < n) emax = fmax(emax, fabs(evec[i]));
+  }
+  const double scale = fmax(fabs(lo), fabs(hi));
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax * emax) + 1e-300;
+  lo -= 4.440892098500626e-16 * scale + pivmin;
+  hi += 4.440892098500626e-16 * scale + pivmin;
+  for (int it = 0; it < 64; ++it) {
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const bool above = sturm_count(dvec, evec, n, x, pivmin) > j;   // eigenvalue j < x
+    const unsigned msk = __ballot_sync(0xffffffffu, above);
+    // first lane whose point lies above eigenvalue j
+    const int a = msk ? __ffs(msk) - 1 : 32;
+    const double nlo = (a == 0) ? lo : lo + (hi - lo) * (double)a / 33.0;
+    const double nhi = (a == 32) ? hi : lo + (hi - lo) * (double)(a + 1) / 33.0;
+    if (!(nhi - nlo < hi - lo)) break;
+    lo = nlo;
+    hi = nhi;
+    if (hi - lo <= 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+  }
+  if (lane == 0) mu[gw] = 0.5 * (lo + hi);
+}
+
+// lambda from the k largest eigenvalues (summed largest first), the LDL^T of T + lambda I.
+__global__ void lambda_ldl_kernel(Dev d, const double* mu, int k, const double* dvec,
+                                  const double* evec, double* ldl_d, double* ldl_l) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double lam;
+  if (d.lambda_mode == 1) {
+    lam = d.lambda_fixed;
+  } else {
+    double top = 0.0;
+    const int kk = k < d.s ? k : d.s;
+    for (int i = 0; i < kk; ++i) top += mu[i];
+    const double fro = d.fro2[1];
+    lam = (fro - top) / (double)k;
+    lam = fmax(lam, 1e-12 * fro / (double)k);
+  }
+  d.scal[SCAL_LAMBDA] = lam;
+  const int n = d.s;
+  double del = dvec[0] + lam;
+  ldl_d[0] = del;
+  for (int i = 1; i < n; ++i) {
+    const double l = (del != 0.0) ? evec[i - 1] / del : 0.0;
+    ldl_l[i - 1] = l;
+    del = dvec[i] + lam - l * evec[i - 1];
+    ldl_d[i] = del;
+  }
+}
+
+// One warp per vector: occupied C slots (v < t) and buffered D columns (t <= v < t + count).
+__global__ void __launch_bounds__(256)
+tri_scores_kernel(Dev d, const double* A, const double* beta, const double* vhead,
+                  const double* ldl_d, const double* ldl_l, double* vecbuf, int vstride, int count) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int n = d.s;
+  const double rs = 1.0 / sqrt((double)n);
+  double* y = vecbuf + (size_t)gw * vstride;
+  for (int vi = gw; vi < d.t + count; vi += nwarps) {
+    int64_t col;
+    if (vi < d.t) { col = d.JC[vi]; if (col < 0) { if (lane == 0) d.tauC[vi] = 1.0; continue; } }
+    else col = d.JD[vi - d.t];
+    const double* l = d.Slev + (size_t)col * d.lev_ld;
+    for (int i = lane; i < n; i += 32) y[i] = l[i] * rs;
+    __syncwarp();
+    for (int k = 0; k + 2 < n; ++k) {          // y <- H_{n-3} ... H_0 y
+      const double bt = beta[k];
+      if (bt == 0.0) continue;
+      const double* u = A + (size_t)k * n;       // u[k+1] = vhead[k], u[i] = A(i, k) for i >= k+2
+      const double vh = vhead[k];
+      double dot = (lane == 0) ? vh * y[k + 1] : 0.0;
+      for (int i = k + 2 + lane; i < n; i += 32) dot += u[i] * y[i];
+      dot = warp_sum(dot);
+      const double f = bt * dot;
+      __syncwarp();
+      if (lane == 0) y[k + 1] -= f * vh;
+      for (int i = k + 2 + lane; i < n; i += 32) y[i] -= f * u[i];
+      __syncwarp();
+    }
+    if (lane == 0) {
+      // tau = y^T (L D L^T)^{-1} y = sum_i z_i^2 / D_i with L z = y
+      double z = y[0];
+      double tau = (ldl_d[0] > 0.0) ? z * z / ldl_d[0] : 0.0;
+      for (int i = 1; i < n; ++i) {
+        z = y[i] - ldl_l[i - 1] * z;
+        if (ldl_d[i] > 0.0) tau += z * z / ldl_d[i];
+      }
+      if (vi < d.t) d.tauC[vi] = tau; else d.tauD[vi - d.t] = tau;
+    }
+    __syncwarp();
+  }
+}
+
+// Launch the three phases; returns the number of kernels launched (0 on failure).
+int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_d,
+                         int64_t off_e, int64_t off_beta, int64_t off_vhead, int64_t off_p,
+                         int64_t off_mu, int64_t off_ldld, int64_t off_ldll, int64_t off_vec,
+                         int vstride, unsigned int* bar_mem, int n_sm, cudaStream_t st) {
+  double* A = work_base + off_A;
+  double* dv = work_base + off_d;
+  double* ev = work_base + off_e;
+  double* bt = work_base + off_beta;
+  double* vh = work_base + off_vhead;
+  double* pg = work_base + off_p;
+  double* mu = work_base + off_mu;
+  double* ld = work_base + off_ldld;
+  double* ll = work_base + off_ldll;
+  const size_t shm = (size_t)2 * d.s * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tridiag_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8);
+    attr = true;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_coop_kernel, kCoopThreads, shm);
+  int grid = n_sm * (per_sm > 0 ? 1 : 0);
+  const int want = (d.s + 7) / 8;               // at least ~8 rows per warp-group of a block
+  if (grid > want) grid = want;
+  if (grid < 1) grid = 1;
+  cudaMemsetAsync(bar_mem, 0, 4 * sizeof(unsigned int), st);
+  GridBar gb{bar_mem, bar_mem + 1, d.err, (int*)(bar_mem + 2)};
+  Dev dd = d;
+  void* args[] = {&dd, &A, &dv, &ev, &bt, &vh, &pg, &gb};
+  if (cudaLaunchCooperativeKernel((void*)tridiag_coop_kernel, grid, kCoopThreads, args, shm, st) != cudaSuccess)
+    return 0;
+  int nk = 2;
+  const int k = d.t;
+  if (d.lambda_mode == 0) {
+    topk_eig_kernel<<<(k * 32 + 255) / 256, 256, 0, st>>>(d, dv, ev, k, mu);
+    ++nk;
+  }
+  lambda_ldl_kernel<<<1, 32, 0, st>>>(d, mu, k, dv, ev, ld, ll);
+  const int nvec = d.t + count;
+  tri_scores_kernel<<<(nvec + 7) / 8, 256, 0, st>>>(d, A, bt, vh, ld, ll, work_base + off_vec, vstride, count);
+  return nk + 2;
+}
+
+}  // namespace rid

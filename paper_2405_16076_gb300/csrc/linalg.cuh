@@ -33,7 +33,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // In-place lower Cholesky of the n x n SPD matrix A (lower triangle used).
 // A non-positive pivot (relative to tol) zeroes its column; returns via *fail.
-__device__ void cta_cholesky(double* A, int n, int lda, double tol, int* fail) {
+static __device__ void cta_cholesky(double* A, int n, int lda, double tol, int* fail) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int j = 0; j < n; ++j) {
     __syncthreads();
@@ -59,7 +59,7 @@ __device__ void cta_cholesky(double* A, int n, int lda, double tol, int* fail) {
 }
 
 // Solve L y = b in place (L lower from cta_cholesky); warp cooperative.
-__device__ void warp_trsv_lower(const double* L, int n, int lda, double* b) {
+static __device__ void warp_trsv_lower(const double* L, int n, int lda, double* b) {
   const int lane = threadIdx.x & 31;
   for (int j = 0; j < n; ++j) {
     const double ljj = L[j + (size_t)j * lda];
@@ -72,7 +72,7 @@ __device__ void warp_trsv_lower(const double* L, int n, int lda, double* b) {
 }
 
 // Solve L^T x = y in place; warp cooperative.
-__device__ void warp_trsv_lower_t(const double* L, int n, int lda, double* b) {
+static __device__ void warp_trsv_lower_t(const double* L, int n, int lda, double* b) {
   const int lane = threadIdx.x & 31;
   for (int j = n - 1; j >= 0; --j) {
     const double ljj = L[j + (size_t)j * lda];
@@ -86,7 +86,7 @@ __device__ void warp_trsv_lower_t(const double* L, int n, int lda, double* b) {
 
 // Householder QR of the m x n matrix A (m >= n) in place.  R is the upper
 // triangle of A; reflector j is v = [vhead[j]; A(j+1:m, j)], H_j = I - beta[j] v v^T.
-__device__ void cta_householder_qr(double* A, int m, int n, int lda, double* beta, double* vhead,
+static __device__ void cta_householder_qr(double* A, int m, int n, int lda, double* beta, double* vhead,
                                    double* sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -119,7 +119,7 @@ __device__ void cta_householder_qr(double* A, int m, int n, int lda, double* bet
 }
 
 // b <- Q^T b for the reflectors of cta_householder_qr; warp cooperative.
-__device__ void warp_apply_qt(const double* QR, int m, int n, int lda, const double* beta,
+static __device__ void warp_apply_qt(const double* QR, int m, int n, int lda, const double* beta,
                               const double* vhead, double* b) {
   const int lane = threadIdx.x & 31;
   for (int j = 0; j < n; ++j) {
@@ -139,7 +139,7 @@ __device__ void warp_apply_qt(const double* QR, int m, int n, int lda, const dou
 }
 
 // Solve R x = c in place (R = upper triangle of QR, n x n); |r_jj| <= tol gives x_j = 0.
-__device__ void warp_trsv_upper(const double* R, int n, int lda, double* c, double tol) {
+static __device__ void warp_trsv_upper(const double* R, int n, int lda, double* c, double tol) {
   const int lane = threadIdx.x & 31;
   for (int j = n - 1; j >= 0; --j) {
     const double rjj = R[j + (size_t)j * lda];
@@ -153,7 +153,7 @@ __device__ void warp_trsv_upper(const double* R, int n, int lda, double* c, doub
 
 // Householder tridiagonalization of the symmetric n x n matrix A (full
 // storage, destroyed); diagonal to dvec, off-diagonal to evec.  v, p: n doubles each.
-__device__ void cta_tridiagonalize(double* A, int n, int lda, double* dvec, double* evec,
+static __device__ void cta_tridiagonalize(double* A, int n, int lda, double* dvec, double* evec,
                                    double* v, double* p, double* sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int k = 0; k + 2 < n; ++k) {
@@ -206,7 +206,7 @@ __device__ void cta_tridiagonalize(double* A, int n, int lda, double* dvec, doub
 }
 
 // Number of eigenvalues of the symmetric tridiagonal (d, e) smaller than x (Sturm count).
-__device__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
+static __device__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
   int cnt = 0;
   double q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
@@ -220,7 +220,7 @@ __device__ int sturm_count(const double* d, const double* e, int n, double x, do
 }
 
 // j-th smallest eigenvalue (0-based) of the tridiagonal (d, e) by bisection.
-__device__ double tridiag_eig_bisect(const double* d, const double* e, int n, int j) {
+static __device__ double tridiag_eig_bisect(const double* d, const double* e, int n, int j) {
   double lo = d[0], hi = d[0], emax = 0.0;
   for (int i = 0; i < n; ++i) {
     const double r = ((i > 0) ? fabs(e[i - 1]) : 0.0) + ((i + 1 < n) ? fabs(e[i]) : 0.0);

@@ -72,7 +72,7 @@ void free_all(Dev& d, void* staging) {
   void* ptrs[] = {d.pool, d.omegaT, d.omegagT, d.S, d.SSt, d.fro2, d.JC, d.JC_prev, d.slotC,
                   d.slotC_prev, d.dslot, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
                   d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
-                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, staging};
+                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, staging};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
 }
@@ -130,6 +130,10 @@ int run_batch(rid_handle* h) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->prof) { e0 = next_event(h); e1 = next_event(h); cudaEventRecord(e0, h->st); }
   const int nk = rid::launch_batch_step(h->d, h->count, h->n_obs, h->n_prev, h->batch, h->st);
+  if (nk == 0) {
+    cudaGetLastError();
+    return fail(h, RID_ECUDA, "batch step launch failed (cooperative launch refused)");
+  }
   if (h->prof) {
     cudaEventRecord(e1, h->st);
     h->spans[2].push_back({e0, e1});
@@ -320,6 +324,8 @@ int rid_init(rid_handle** out, const rid_config* c) {
   AL(d.spart, (size_t)d.n_sketch_blocks * rid::kMaxB * d.rows);
   AL(d.npart, (size_t)d.n_sketch_blocks * rid::kMaxB);
   AL(d.err, 1);
+  AL(d.gbar, 4);
+  d.n_sm = h->n_sm;
   d.work_len = rid::work_doubles(d);
   AL(d.work, d.work_len);
   {

@@ -70,6 +70,8 @@ struct Dev {
   double* spart;                  // sketch partials
   double* npart;                  // norm partials
   int* err;                       // device error word
+  unsigned int* gbar;             // grid-barrier words of the cooperative kernels
+  int n_sm;
   int n_sketch_blocks;
   int gram_split;
   int64_t work_len;
@@ -109,6 +111,13 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
                       cudaStream_t st);
 int launch_reset_state(const Dev& d, cudaStream_t st);
 int launch_set_jd(const Dev& d, int count, int nb, int64_t n_obs, cudaStream_t st);
+
+// coop.cu: lambda (Eq. 23) and the sketched ridge scores of C and D through a
+// multi-SM tridiagonalization; returns the number of kernels launched (0 on failure).
+int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_d,
+                         int64_t off_e, int64_t off_beta, int64_t off_vhead, int64_t off_p,
+                         int64_t off_mu, int64_t off_ldld, int64_t off_ldll, int64_t off_vec,
+                         int vstride, unsigned int* bar_mem, int n_sm, cudaStream_t st);
 int64_t work_doubles(const Dev& d);
 
 }  // namespace rid
