@@ -16,7 +16,7 @@ namespace rid {
 
 // ---------------------------------------------------------------- work layout
 struct WorkLayout {
-  int64_t eigA, eigD, eigE, eigV, eigP;   // tridiagonalization of the sketch Gram
+  int64_t eigA, eigR, eigD, eigE, eigV, eigP;   // tridiagonalization of the sketch Gram
   int64_t beta, vhead, mu, ldld, ldll;    // reflectors, top-k eigenvalues, LDL^T of T + lambda I
   int64_t unif;                           // uniforms of the prune/refill decisions
   int64_t vec;                            // per-warp vectors (scores / applies)
@@ -43,7 +43,8 @@ static WorkLayout layout(const Dev& d) {
   const int64_t nw = (int64_t)kApplyBlocks * (kApplyThreads / 32);
   int64_t o = 0;
   auto take = [&](int64_t n) { int64_t r = o; o += (n + 31) / 32 * 32; return r; };
-  w.eigA = take(s * s); w.eigD = take(s); w.eigE = take(s); w.eigV = take(s); w.eigP = take(s);
+  w.eigA = take(s * s); w.eigR = take(s * s); w.eigD = take(s); w.eigE = take(s); w.eigV = take(s);
+  w.eigP = take(2 * s);
   w.beta = take(s); w.vhead = take(s); w.mu = take(t); w.ldld = take(s); w.ldll = take(s);
   w.unif = take(t * (t + 1));
   w.vec = take(nw * (s > t ? s : t));
@@ -616,16 +617,22 @@ int launch_reset_state(const Dev& d, cudaStream_t st) {
 int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
                       cudaStream_t st) {
   const WorkLayout w = layout(d);
-  int nk = launch_lambda_scores(d, count, d.work, w.eigA, w.eigD, w.eigE, w.beta, w.vhead, w.eigP,
+  int nk = launch_lambda_scores(d, count, d.work, w.eigA, w.eigR, w.eigD, w.eigE, w.beta, w.vhead, w.eigP,
                                 w.mu, w.ldld, w.ldll, w.vec, (d.s > d.t ? d.s : d.t), d.gbar, d.n_sm, st);
   if (nk == 0) return 0;
   const int nu = d.t * (count + 1);
   uniforms_kernel<<<(nu + 255) / 256, 256, 0, st>>>(d, d.work + w.unif, count, batch);
   select_kernel<<<1, 32, 0, st>>>(d, d.work + w.unif, count);
-  dim3 gg((d.t + 63) / 64, (2 * d.t + 63) / 64, d.gram_split);
-  if (d.dtype == 0) basis_gram_kernel<double><<<gg, 256, 0, st>>>(d);
-  else basis_gram_kernel<float><<<gg, 256, 0, st>>>(d);
-  gram_reduce_kernel<<<(d.t * 2 * d.t + 255) / 256, 256, 0, st>>>(d, d.gram_split);
+  int ngk = 2;
+  if (d.dtype == 1 && d.tc_part) {
+    ngk = launch_tc_gram(d, d.tc_blocks, d.tc_part, st);
+    if (ngk < 0) return 0;
+  } else {
+    dim3 gg((d.t + 63) / 64, (2 * d.t + 63) / 64, d.gram_split);
+    if (d.dtype == 0) basis_gram_kernel<double><<<gg, 256, 0, st>>>(d);
+    else basis_gram_kernel<float><<<gg, 256, 0, st>>>(d);
+    gram_reduce_kernel<<<(d.t * 2 * d.t + 255) / 256, 256, 0, st>>>(d, d.gram_split);
+  }
   factor_kernel<<<1, 512, 0, st>>>(d, w);
   coeff_kernel<<<kApplyBlocks, kApplyThreads, 0, st>>>(d, w, n_obs, n_prev);
   const int nchunk = (int)((n_obs + kHutChunk - 1) / kHutChunk);
@@ -633,7 +640,7 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   hutch_finish_kernel<<<4, 256, 0, st>>>(d, w, nchunk);
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
-  return nk + 11;
+  return nk + 9 + ngk;
 }
 
 }  // namespace rid

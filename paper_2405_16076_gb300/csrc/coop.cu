@@ -66,75 +66,97 @@ __device__ bool grid_barrier(const GridBar& b) {
 
 }  // namespace
 
-// A (s x s, column-major) <- M, then reduced in place.  On exit: d[0..s), e[0..s-1),
-// reflector k = [vhead[k]; A(k+2:s, k)] acting on rows k+1..s-1 with coefficient beta[k].
+// Householder reduction M = Q T Q^T on every SM with one grid barrier per step.
+// Block b owns the trailing columns j with j % gridDim.x == b.  At step k every
+// block holds the (updated) column k locally, forms reflector k from it, computes
+// p = beta A' v on its own columns, and after the barrier forms w, updates its
+// own columns except column k+1, and recomputes the updated column k+1 -- the
+// next reflector column -- itself from A, v and w.  Column k+1 is therefore never
+// written back, and p is double-buffered by step parity.
+// On exit: d[0..n), e[0..n-1), reflector k = [vhead[k]; R(k+2:n, k)] acting on
+// rows k+1..n-1 with coefficient beta[k].
 __global__ void __launch_bounds__(kCoopThreads)
-tridiag_coop_kernel(Dev d, double* A, double* dvec, double* evec, double* beta, double* vhead,
-                    double* pglob, GridBar bar) {
+tridiag_coop_kernel(Dev d, double* A, double* R, double* dvec, double* evec, double* beta,
+                    double* vhead, double* pbuf, GridBar bar) {
   extern __shared__ double sm[];
   const int n = d.s;
-  double* v = sm;            // n
-  double* w = sm + n;        // n
+  double* v = sm;            // reflector of the current step, trailing-relative index
+  double* w = sm + n;
+  double* x = sm + 2 * n;    // current column below the diagonal, trailing-relative index
   __shared__ double sh[33];
+  __shared__ double diag_s;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int G = gridDim.x, b = blockIdx.x;
   const double inv_s = 1.0 / (double)n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < (int64_t)n * n; i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = (int64_t)b * blockDim.x + tid; i < (int64_t)n * n; i += (int64_t)G * blockDim.x)
     A[i] = d.SSt[i] * inv_s;
   if (!grid_barrier(bar)) return;
+  for (int i = tid; i + 1 < n; i += blockDim.x) x[i] = A[(i + 1)];
+  if (tid == 0) diag_s = A[0];
+  __syncthreads();
   for (int k = 0; k + 2 < n; ++k) {
-    const int nn = n - k - 1;
-    const double* x = A + (k + 1) + (size_t)k * n;
+    const int nn = n - k - 1;                   // trailing rows/columns k+1 .. n-1
     double part = 0.0;
-    for (int i = tid; i < nn; i += blockDim.x) { const double xi = x[i]; v[i] = xi; part += xi * xi; }
+    for (int i = tid; i < nn; i += blockDim.x) part += x[i] * x[i];
     const double nrm2 = block_sum(part, sh);
-    const double x0 = v[0];
+    const double x0 = x[0];
     const double tail = nrm2 - x0 * x0;
     const double nrm = sqrt(nrm2);
     const double alpha = (x0 >= 0.0) ? -nrm : nrm;
     const double v0 = x0 - alpha;
     const double vtv = tail + v0 * v0;
     const double bt = (tail > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
-    __syncthreads();
-    if (tid == 0) v[0] = v0;
-    if (blockIdx.x == 0 && tid == 0) {
-      dvec[k] = A[k + (size_t)k * n];
-      evec[k] = (bt > 0.0) ? alpha : x0;
-      beta[k] = bt;
-      vhead[k] = v0;
+    for (int i = tid; i < nn; i += blockDim.x) v[i] = (i == 0) ? v0 : x[i];
+    if (b == 0) {
+      if (tid == 0) {
+        dvec[k] = diag_s;
+        evec[k] = (bt > 0.0) ? alpha : x0;
+        beta[k] = bt;
+        vhead[k] = v0;
+      }
+      for (int i = 1 + tid; i < nn; i += blockDim.x) R[(k + 1 + i) + (size_t)k * n] = x[i];
     }
     __syncthreads();
-    if (bt == 0.0) continue;                   // uniform over the grid: same data, same arithmetic
-    double* Ab = A + (k + 1) + (size_t)(k + 1) * n;
-    // p = beta * A' v (A' symmetric: row i read as column i); rows split over blocks, warp per row
-    for (int i = blockIdx.x * nw + wid; i < nn; i += gridDim.x * nw) {
-      const double* col = Ab + (size_t)i * n;
+    // p_j = beta * (A' v)_j on the owned trailing columns (A' symmetric: row j read as column j)
+    double* pk = pbuf + (size_t)(k & 1) * n;
+    const int j0 = ((b - (k + 1)) % G + G) % G;   // first owned trailing column
+    for (int jl = j0 + wid * G; jl < nn; jl += nw * G) {
+      const double* col = A + (k + 1) + (size_t)(k + 1 + jl) * n;
       double acc = 0.0;
-      for (int j = lane; j < nn; j += 32) acc += col[j] * v[j];
+      for (int i = lane; i < nn; i += 32) acc += col[i] * v[i];
       acc = warp_sum(acc);
-      if (lane == 0) pglob[i] = bt * acc;
+      if (lane == 0) pk[jl] = bt * acc;
     }
     if (!grid_barrier(bar)) return;
     part = 0.0;
-    for (int i = tid; i < nn; i += blockDim.x) { const double pi = pglob[i]; w[i] = pi; part += pi * v[i]; }
+    for (int i = tid; i < nn; i += blockDim.x) { const double pi = pk[i]; w[i] = pi; part += pi * v[i]; }
     const double ptv = block_sum(part, sh);
     const double kc = 0.5 * bt * ptv;
     for (int i = tid; i < nn; i += blockDim.x) w[i] -= kc * v[i];
     __syncthreads();
-    // A' -= v w^T + w v^T on the columns of this block
-    for (int j = blockIdx.x * nw + wid; j < nn; j += gridDim.x * nw) {
-      double* col = Ab + (size_t)j * n;
-      const double wj = w[j], vj = v[j];
+    // owned columns except the next one: A' -= v w^T + w v^T
+    for (int jl = j0 + wid * G; jl < nn; jl += nw * G) {
+      if (jl == 0) continue;
+      double* col = A + (k + 1) + (size_t)(k + 1 + jl) * n;
+      const double wj = w[jl], vj = v[jl];
       for (int i = lane; i < nn; i += 32) col[i] -= v[i] * wj + w[i] * vj;
     }
-    if (!grid_barrier(bar)) return;
+    // the updated next column (trailing column 0), recomputed by every block
+    const double* c0 = A + (k + 1) + (size_t)(k + 1) * n;
+    for (int i = 1 + tid; i < nn; i += blockDim.x) x[i - 1] = c0[i] - v[i] * w[0] - w[i] * v[0];
+    if (tid == 0) diag_s = c0[0] - 2.0 * v[0] * w[0];
+    __syncthreads();
   }
-  if (blockIdx.x == 0 && tid == 0) {
+  if (!grid_barrier(bar)) return;
+  if (b == 0 && tid == 0) {
     if (n >= 2) {
-      dvec[n - 2] = A[(n - 2) + (size_t)(n - 2) * n];
-      evec[n - 2] = A[(n - 1) + (size_t)(n - 2) * n];
+      dvec[n - 2] = diag_s;
+      evec[n - 2] = x[0];
       beta[n - 2] = 0.0;
+      dvec[n - 1] = A[(n - 1) + (size_t)(n - 1) * n];
+    } else {
+      dvec[0] = A[0];
     }
-    dvec[n - 1] = A[(n - 1) + (size_t)(n - 1) * n];
   }
 }
 
@@ -201,8 +223,8 @@ __global__ void lambda_ldl_kernel(Dev d, const double* mu, int k, const double* 
 }
 
 // One warp per vector: occupied C slots (v < t) and buffered D columns (t <= v < t + count).
-__global__ void __launch_bounds__(256)
-tri_scores_kernel(Dev d, const double* A, const double* beta, const double* vhead,
+__global__ void __launch_bounds__(32)
+tri_scores_kernel(Dev d, const double* R, const double* beta, const double* vhead,
                   const double* ldl_d, const double* ldl_l, double* vecbuf, int vstride, int count) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -220,7 +242,7 @@ tri_scores_kernel(Dev d, const double* A, const double* beta, const double* vhea
     for (int k = 0; k + 2 < n; ++k) {          // y <- H_{n-3} ... H_0 y
       const double bt = beta[k];
       if (bt == 0.0) continue;
-      const double* u = A + (size_t)k * n;       // u[k+1] = vhead[k], u[i] = A(i, k) for i >= k+2
+      const double* u = R + (size_t)k * n;       // u[k+1] = vhead[k], u[i] = R(i, k) for i >= k+2
       const double vh = vhead[k];
       double dot = (lane == 0) ? vh * y[k + 1] : 0.0;
       for (int i = k + 2 + lane; i < n; i += 32) dot += u[i] * y[i];
@@ -246,11 +268,13 @@ tri_scores_kernel(Dev d, const double* A, const double* beta, const double* vhea
 }
 
 // Launch the three phases; returns the number of kernels launched (0 on failure).
-int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_d,
-                         int64_t off_e, int64_t off_beta, int64_t off_vhead, int64_t off_p,
-                         int64_t off_mu, int64_t off_ldld, int64_t off_ldll, int64_t off_vec,
-                         int vstride, unsigned int* bar_mem, int n_sm, cudaStream_t st) {
+int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_R,
+                         int64_t off_d, int64_t off_e, int64_t off_beta, int64_t off_vhead,
+                         int64_t off_p, int64_t off_mu, int64_t off_ldld, int64_t off_ldll,
+                         int64_t off_vec, int vstride, unsigned int* bar_mem, int n_sm,
+                         cudaStream_t st) {
   double* A = work_base + off_A;
+  double* R = work_base + off_R;
   double* dv = work_base + off_d;
   double* ev = work_base + off_e;
   double* bt = work_base + off_beta;
@@ -259,33 +283,33 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
   double* mu = work_base + off_mu;
   double* ld = work_base + off_ldld;
   double* ll = work_base + off_ldll;
-  const size_t shm = (size_t)2 * d.s * sizeof(double);
+  const size_t shm = (size_t)3 * d.s * sizeof(double);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(tridiag_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8);
+    cudaFuncSetAttribute(tridiag_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 8);
     attr = true;
   }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_coop_kernel, kCoopThreads, shm);
   int grid = n_sm * (per_sm > 0 ? 1 : 0);
-  const int want = (d.s + 7) / 8;               // at least ~8 rows per warp-group of a block
+  const int want = d.s - 1;                     // at least one trailing column per block
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
   cudaMemsetAsync(bar_mem, 0, 4 * sizeof(unsigned int), st);
   GridBar gb{bar_mem, bar_mem + 1, d.err, (int*)(bar_mem + 2)};
   Dev dd = d;
-  void* args[] = {&dd, &A, &dv, &ev, &bt, &vh, &pg, &gb};
+  void* args[] = {&dd, &A, &R, &dv, &ev, &bt, &vh, &pg, &gb};
   if (cudaLaunchCooperativeKernel((void*)tridiag_coop_kernel, grid, kCoopThreads, args, shm, st) != cudaSuccess)
     return 0;
   int nk = 2;
   const int k = d.t;
   if (d.lambda_mode == 0) {
-    topk_eig_kernel<<<(k * 32 + 255) / 256, 256, 0, st>>>(d, dv, ev, k, mu);
+    topk_eig_kernel<<<k, 32, 0, st>>>(d, dv, ev, k, mu);        // one warp per SM slot: FP64-bound
     ++nk;
   }
   lambda_ldl_kernel<<<1, 32, 0, st>>>(d, mu, k, dv, ev, ld, ll);
   const int nvec = d.t + count;
-  tri_scores_kernel<<<(nvec + 7) / 8, 256, 0, st>>>(d, A, bt, vh, ld, ll, work_base + off_vec, vstride, count);
+  tri_scores_kernel<<<nvec, 32, 0, st>>>(d, R, bt, vh, ld, ll, work_base + off_vec, vstride, count);
   return nk + 2;
 }
 

@@ -301,8 +301,11 @@ int rid_init(rid_handle** out, const rid_config* c) {
 #define AL(ptr, n) do { if (dalloc(&(ptr), (size_t)(n)) != cudaSuccess) { rc = RID_ENOMEM; goto fail_alloc; } } while (0)
   if (h->tc) {
     const int nrows16 = (d.rows + 15) / 16 * 16;
-    AL(h->tc_part, (size_t)h->tc_blocks * nrows16 * 128);
+    const int prow = nrows16 > 256 ? nrows16 : 256;     // ingest partials or Gram partials
+    AL(h->tc_part, (size_t)h->tc_blocks * prow * 128);
     AL(h->tc_npart, (size_t)h->tc_blocks * 128);
+    d.tc_blocks = h->tc_blocks;
+    d.tc_part = h->tc_part;
   }
   {
     char* pool = nullptr;

@@ -72,6 +72,8 @@ struct Dev {
   int* err;                       // device error word
   unsigned int* gbar;             // grid-barrier words of the cooperative kernels
   int n_sm;
+  int tc_blocks;                  // CTAs of the tensor-core kernels
+  float* tc_part;                 // their partial accumulators (>= tc_blocks x 512 x 128 floats)
   int n_sketch_blocks;
   int gram_split;
   int64_t work_len;
@@ -104,6 +106,9 @@ int launch_tc_ingest(const Dev& d, const void* const* cols, int ncols, int split
                      int64_t n_obs, int nblk, float* part, double* npart, cudaStream_t st,
                      cudaEvent_t* ev);
 int tc_smem_bytes();
+// Basis Gram of the new x target pool slots on tensor cores (FP32 pool); returns the
+// number of kernels launched, or -1.  part holds nblk x 256 x 128 floats.
+int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st);
 void launch_materialize_omega(const Dev& d, cudaStream_t st);
 
 // batch.cu
@@ -114,10 +119,11 @@ int launch_set_jd(const Dev& d, int count, int nb, int64_t n_obs, cudaStream_t s
 
 // coop.cu: lambda (Eq. 23) and the sketched ridge scores of C and D through a
 // multi-SM tridiagonalization; returns the number of kernels launched (0 on failure).
-int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_d,
-                         int64_t off_e, int64_t off_beta, int64_t off_vhead, int64_t off_p,
-                         int64_t off_mu, int64_t off_ldld, int64_t off_ldll, int64_t off_vec,
-                         int vstride, unsigned int* bar_mem, int n_sm, cudaStream_t st);
+int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_R,
+                         int64_t off_d, int64_t off_e, int64_t off_beta, int64_t off_vhead,
+                         int64_t off_p, int64_t off_mu, int64_t off_ldld, int64_t off_ldll,
+                         int64_t off_vec, int vstride, unsigned int* bar_mem, int n_sm,
+                         cudaStream_t st);
 int64_t work_doubles(const Dev& d);
 
 }  // namespace rid

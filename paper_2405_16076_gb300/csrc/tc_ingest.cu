@@ -384,6 +384,189 @@ __global__ void tc_reduce_kernel(Dev d, const float* __restrict__ part, const do
   }
 }
 
+// ---------------------------------------------------------------- basis Gram on tensor cores
+// G(x, y) = <pool[gnew[x0 + x]], pool[gtgt[y0 + y]]> for x < nx <= 64, y < ny <= 128, over
+// all m coordinates: A rows are the new columns split hi/lo (rows x, 64 + x), B rows the
+// target columns split hi/lo (rows y, 128 + y), so that the four BF16 cross products of
+// (hi + lo)(hi + lo) land in D(x | 64 + x, y | 128 + y); the split leaves an error of
+// at most ~2^-16 |a_i b_i| per term.  Same pipeline as the ingest kernel, no Omega.
+constexpr int kGramN = 256;
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gram_kernel(Dev d, int x0, int y0, int64_t chunks_per_cta, float* __restrict__ part) {
+  extern __shared__ uint8_t smem_raw[];
+  const int nx = min(64, d.meta[META_NNEW] - x0);     // counts are decided on the device
+  const int ny = min(128, d.meta[META_NTGT] - y0);
+  if (nx <= 0 || ny <= 0) return;                     // uniform over the CTA, before any TMEM use
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t sA = base;
+  const uint32_t sB = base + 2 * kATile;
+  const uint32_t sBar = sB + 2 * kBTile;
+  uint8_t* gbar = gbase + (sBar - base);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 64);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 72);
+  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 16, bar_done = sBar + 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
+  const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
+  int64_t c1 = c0 + chunks_per_cta;
+  if (c1 > nchunks) c1 = nchunks;
+  const int64_t nch = c1 > c0 ? c1 - c0 : 0;
+  if (threadIdx.x == 0) {
+    mbar_init(bar_full0, 32 * kProducerWarps);
+    mbar_init(bar_full0 + 8, 32 * kProducerWarps);
+    mbar_init(bar_empty0, 1);
+    mbar_init(bar_empty0 + 8, 1);
+    mbar_init(bar_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t id = idesc_bf16(128, kGramN);
+      for (int64_t c = 0; c < nch; ++c) {
+        const int st = (int)(c & 1);
+        if (!mbar_wait(bar_full0 + 8 * st, (uint32_t)((c >> 1) & 1), abort_flag, d.err)) break;
+        tc_fence_after();
+        const uint64_t da = desc_sw128(sA + st * kATile);
+        const uint64_t db = desc_sw128(sB + st * kBTile);
+#pragma unroll
+        for (int kk = 0; kk < kChunkK / 16; ++kk)
+          tc_mma(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), id, (c > 0 || kk > 0) ? 1u : 0u);
+        tc_commit(bar_empty0 + 8 * st);
+      }
+      tc_commit(bar_done);
+    }
+    __syncwarp();
+  } else {
+    const int pt = threadIdx.x - 32;
+    const float* pool = (const float*)d.pool;
+    // task 0: new column qa (A rows qa, 64 + qa); tasks 1, 2: target columns (B rows)
+    const int qa = pt >> 2, g = pt & 3;
+    const bool hasA = qa < nx;
+    const float* srcA = hasA ? pool + (int64_t)d.gnew[x0 + qa] * d.m_pad : nullptr;
+    const int qb0 = pt >> 2, qb1 = 64 + (pt >> 2);
+    const bool hasB0 = qb0 < ny, hasB1 = qb1 < ny;
+    const float* srcB0 = hasB0 ? pool + (int64_t)d.gtgt[y0 + qb0] * d.m_pad : nullptr;
+    const float* srcB1 = hasB1 ? pool + (int64_t)d.gtgt[y0 + qb1] * d.m_pad : nullptr;
+    float4 a0[4], a1[4], b00[4], b01[4], b10[4], b11[4];
+    auto ld = [&](const float* src, bool has, int64_t c, float4 (&v)[4]) {
+      if (has && c < nch) load16(src, (c0 + c) * kChunkK + 16 * g, d.m, true, v);
+    };
+    auto put = [&](uint32_t tile, int row_hi, int row_lo, const float4 (&v)[4]) {
+      float xv[16];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { xv[4 * j] = v[j].x; xv[4 * j + 1] = v[j].y; xv[4 * j + 2] = v[j].z; xv[4 * j + 3] = v[j].w; }
+      uint32_t hw[8], lw[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float a = xv[2 * j], bb = xv[2 * j + 1];
+        const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(bb);
+        hw[j] = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+        lw[j] = pack_bf16(a - __bfloat162float(ha), bb - __bfloat162float(hb));
+      }
+      sts128(tile + sw128_off(row_hi, 2 * g), hw[0], hw[1], hw[2], hw[3]);
+      sts128(tile + sw128_off(row_hi, 2 * g + 1), hw[4], hw[5], hw[6], hw[7]);
+      sts128(tile + sw128_off(row_lo, 2 * g), lw[0], lw[1], lw[2], lw[3]);
+      sts128(tile + sw128_off(row_lo, 2 * g + 1), lw[4], lw[5], lw[6], lw[7]);
+    };
+    auto process = [&](int64_t c, const float4 (&va)[4], const float4 (&vb0)[4], const float4 (&vb1)[4]) -> bool {
+      const int st = (int)(c & 1);
+      if (!mbar_wait(bar_empty0 + 8 * st, (uint32_t)(((c >> 1) & 1) ^ 1), abort_flag, d.err)) return false;
+      const uint32_t ast = sA + st * kATile, bst = sB + st * kBTile;
+      if (hasA) put(ast, qa, 64 + qa, va);
+      if (hasB0) put(bst, qb0, 128 + qb0, vb0);
+      if (hasB1) put(bst, qb1, 128 + qb1, vb1);
+      fence_async_smem();
+      mbar_arrive(bar_full0 + 8 * st);
+      return true;
+    };
+    ld(srcA, hasA, 0, a0); ld(srcB0, hasB0, 0, b00); ld(srcB1, hasB1, 0, b10);
+    ld(srcA, hasA, 1, a1); ld(srcB0, hasB0, 1, b01); ld(srcB1, hasB1, 1, b11);
+    for (int64_t c = 0; c < nch; c += 2) {
+      if (!process(c, a0, b00, b10)) break;
+      ld(srcA, hasA, c + 2, a0); ld(srcB0, hasB0, c + 2, b00); ld(srcB1, hasB1, c + 2, b10);
+      if (c + 1 < nch) {
+        if (!process(c + 1, a1, b01, b11)) break;
+        ld(srcA, hasA, c + 3, a1); ld(srcB0, hasB0, c + 3, b01); ld(srcB1, hasB1, c + 3, b11);
+      }
+    }
+    if (warp <= 4) {
+      const bool ok = mbar_wait(bar_done, 0, abort_flag, d.err);
+      tc_fence_after();
+      if (ok && !*abort_flag) {
+        const int quarter = warp & 3;
+        const int L = 32 * quarter + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+        for (int cb = 0; cb < kGramN; cb += 32) {
+          uint32_t r[32];
+          tc_ld32(taddr + (uint32_t)cb, r);
+          tc_wait_ld();
+          float* o = part + ((size_t)blockIdx.x * kGramN + cb) * 128 + L;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) o[(size_t)j * 128] = (nch > 0) ? __uint_as_float(r[j]) : 0.f;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+__global__ void tc_gram_reduce_kernel(Dev d, const float* __restrict__ part, int nblk, int x0, int y0) {
+  const int nx = min(64, d.meta[META_NNEW] - x0);
+  const int ny = min(128, d.meta[META_NTGT] - y0);
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (nx <= 0 || ny <= 0 || idx >= nx * ny) return;
+  const int x = idx % nx, y = idx / nx;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    const float* p = part + (size_t)b * kGramN * 128;
+    v += (double)p[(size_t)y * 128 + x] + (double)p[(size_t)y * 128 + 64 + x] +
+         (double)p[(size_t)(128 + y) * 128 + x] + (double)p[(size_t)(128 + y) * 128 + 64 + x];
+  }
+  const int two_t = 2 * d.t;
+  const int a = d.gnew[x0 + x], bb = d.gtgt[y0 + y];
+  d.Gp[a + (size_t)bb * two_t] = v;
+  d.Gp[bb + (size_t)a * two_t] = v;
+}
+
+// Gram of every (new, target) pool-slot pair, in tiles of 64 x 128.  The counts live on the
+// device, so every tile is launched for the largest possible counts and exits early.
+int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+        cudaSuccess)
+      return -1;
+    attr_set = true;
+  }
+  const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
+  int64_t per = (nchunks + nblk - 1) / nblk;
+  int nk = 0;
+  for (int x0 = 0; x0 < d.t; x0 += 64)
+    for (int y0 = 0; y0 < 2 * d.t; y0 += 128) {
+      tc_gram_kernel<<<nblk, kThreads, kSmemBytes, st>>>(d, x0, y0, per, part);
+      tc_gram_reduce_kernel<<<(64 * 128 + 255) / 256, 256, 0, st>>>(d, part, nblk, x0, y0);
+      nk += 2;
+    }
+  return nk;
+}
+
 int tc_smem_bytes() { return kSmemBytes; }
 
 // Launch the tensor-core sketch of ncols columns; returns 0 on success.

@@ -104,3 +104,31 @@ def test_tc_small_m_single_column_groups():
     g, J, P, _ = _run_gpu(A, k, s, h, "bf16x2", block=1)
     err = np.abs(g.state(0) - o.S) / np.linalg.norm(A.astype(np.float64), axis=0)[None, :]
     assert err.max() <= 2e-5
+
+
+def test_tc_batch_step_candidates_on_gpu_sketch():
+    """Batch-step parity on identical inputs: the oracle's Algorithms 4 and 5 evaluated on the
+    GPU's own sketch and basis.  Algorithm 4 uses only the FP64 sketch (bar 1e-10 x kappa);
+    Algorithm 5 also uses the basis Gram, computed on tensor cores from the BF16x2 split
+    (per-term error <= ~2^-16 |a_i b_i|, FP32 accumulation): bar 1e-5 x kappa(G)."""
+    import math
+    from oracle.rid import coeff_alg4, coeff_alg5
+    A = _mats(50000, 64, 21)
+    k, s, h = 16, 67, 30
+    g, J, P, _ = _run_gpu(A, k, s, h, "bf16x2", defer=True)
+    n = A.shape[1]
+    cand = g.candidates(n)
+    S = g.state(0)
+    act = J >= 0
+    Ja = J[act]
+    SA = S[:s] / math.sqrt(s)
+    SJ = SA[:, Ja]
+    A64 = A.astype(np.float64)
+    G = A64[:, Ja].T @ A64[:, Ja]
+    na = int(act.sum())
+    P4 = coeff_alg4(SJ, SA)
+    P5 = coeff_alg5(G, SJ, SA)
+    kap = np.linalg.cond(SJ)
+    assert np.linalg.norm(cand[0][:na] - P4) <= 1e-10 * max(1.0, kap) * np.linalg.norm(P4)
+    kapG = np.linalg.cond(G)
+    assert np.linalg.norm(cand[1][:na] - P5) <= 1e-5 * max(1.0, kapG) * np.linalg.norm(P5)
