@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 CONFIGS = {
     "channel": dict(workload="channel-flow-shaped stream, 3 x 192 x 129 x 192 FP32, n=1000, blocks of 8",
                     nx=192, ny=129, nz=192, n=1000, b=8, k=100, s=403, h=50),
+    "channel_mid": dict(workload="channel-flow-shaped stream, 3 x 96 x 65 x 96 FP32, n=200, blocks of 8",
+                        nx=96, ny=65, nz=96, n=200, b=8, k=100, s=403, h=50),
     "channel_small": dict(workload="channel-flow-shaped stream, 3 x 48 x 33 x 48 FP32, n=200, blocks of 8",
                           nx=48, ny=33, nz=48, n=200, b=8, k=20, s=83, h=30),
 }

@@ -21,7 +21,7 @@ struct WorkLayout {
   int64_t unif;                           // uniforms of the prune/refill decisions
   int64_t vec;                            // per-warp vectors (scores / applies)
   int64_t SJ, HJ, G, Gq, Gc, T;           // gathered sketch data and Grams
-  int64_t QR4, b4, h4, QR6, b6, h6;       // Householder factors
+  int64_t QR4, b4, h4, r4, QR6, b6, h6, r6;   // Householder factors (r: diagonal of R)
   int64_t Z, trgpp, hut, hut_stride;      // Hutch++
   int64_t total;
 };
@@ -50,8 +50,8 @@ static WorkLayout layout(const Dev& d) {
   w.vec = take(nw * (s > t ? s : t));
   w.SJ = take(s * t); w.HJ = take(hh * t); w.G = take(t * t); w.Gq = take(t * t);
   w.Gc = take(t * t); w.T = take(t * t);
-  w.QR4 = take(s * t); w.b4 = take(t); w.h4 = take(t);
-  w.QR6 = take(s * t); w.b6 = take(t); w.h6 = take(t);
+  w.QR4 = take(s * t); w.b4 = take(t); w.h4 = take(t); w.r4 = take(t);
+  w.QR6 = take(s * t); w.b6 = take(t); w.h6 = take(t); w.r6 = take(t);
   w.Z = take(4 * hh * t); w.trgpp = take(4);
   w.hut_stride = hut_stride(d);
   w.hut = take(4 * w.hut_stride);
@@ -210,13 +210,12 @@ __global__ void gram_reduce_kernel(Dev d, int nsplit) {
   d.Gp[b + (size_t)a * two_t] = v;
 }
 
-// ---------------------------------------------------------------- gather + factorizations (one CTA)
-__global__ void __launch_bounds__(512) factor_kernel(Dev d, WorkLayout w) {
-  __shared__ double sh[33];
-  __shared__ int fail;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int s = d.s, t = d.t, two_t = 2 * t, hh = d.h1 + d.h2 + d.h3;
-  const int na = d.meta[META_NACT], npa = d.meta[META_NPACT];
+// ---------------------------------------------------------------- gather + factorizations
+// Gather Omega A_J (scaled), the probe rows of the basis, G = A_J^T A_J and A_J^T A_Jprev from
+// the pool Gram, and the new-element columns for Algorithm 6 (grid-stride, many blocks).
+__global__ void gather_kernel(Dev d, WorkLayout w) {
+  const int s = d.s, two_t = 2 * d.t, hh = d.h1 + d.h2 + d.h3;
+  const int na = d.meta[META_NACT], npa = d.meta[META_NPACT], nn = d.meta[META_NNEW];
   const double rs = 1.0 / sqrt((double)s);
   double* SJ = d.work + w.SJ;
   double* HJ = d.work + w.HJ;
@@ -225,45 +224,60 @@ __global__ void __launch_bounds__(512) factor_kernel(Dev d, WorkLayout w) {
   double* Gc = d.work + w.Gc;
   double* QR4 = d.work + w.QR4;
   double* QR6 = d.work + w.QR6;
-  if (tid == 0) fail = 0;
-  for (int64_t idx = tid; idx < (int64_t)s * na; idx += nt) {
+  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = g0; idx < (int64_t)s * na; idx += gs) {
     const int i = (int)(idx % s), a = (int)(idx / s);
     const double v = d.S[(size_t)d.JC[d.act[a]] * d.rows + i] * rs;
     SJ[i + (size_t)a * s] = v;
     QR4[i + (size_t)a * s] = v;
   }
-  for (int64_t idx = tid; idx < (int64_t)hh * na; idx += nt) {
+  for (int64_t idx = g0; idx < (int64_t)s * nn; idx += gs) {
+    const int i = (int)(idx % s), c = (int)(idx / s);
+    QR6[i + (size_t)c * s] = d.S[(size_t)d.JC[d.act[d.newpos[c]]] * d.rows + i] * rs;
+  }
+  for (int64_t idx = g0; idx < (int64_t)hh * na; idx += gs) {
     const int r = (int)(idx % hh), a = (int)(idx / hh);
     HJ[r + (size_t)a * hh] = d.S[(size_t)d.JC[d.act[a]] * d.rows + d.hbase + r];
   }
-  for (int64_t idx = tid; idx < (int64_t)na * na; idx += nt) {
+  for (int64_t idx = g0; idx < (int64_t)na * na; idx += gs) {
     const int a = (int)(idx % na), b = (int)(idx / na);
     const double g = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC[d.act[b]] * two_t];
     G[a + (size_t)b * na] = g;
     Gc[a + (size_t)b * na] = g;
   }
-  for (int64_t idx = tid; idx < (int64_t)na * npa; idx += nt) {
+  for (int64_t idx = g0; idx < (int64_t)na * npa; idx += gs) {
     const int a = (int)(idx % na), b = (int)(idx / na);
     Gq[a + (size_t)b * na] = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC_prev[d.pact[b]] * two_t];
   }
-  __syncthreads();
-  // columns of the new basis elements, for Algorithm 6
-  const int nn = d.meta[META_NNEW];
-  for (int64_t idx = tid; idx < (int64_t)s * nn; idx += nt) {
-    const int i = (int)(idx % s), c = (int)(idx / s);
-    QR6[i + (size_t)c * s] = SJ[i + (size_t)d.newpos[c] * s];
+}
+
+// Cholesky of G (t x t at most; FP64, one CTA).
+__global__ void __launch_bounds__(1024) gram_chol_kernel(Dev d, WorkLayout w) {
+  __shared__ int fail;
+  __shared__ double gm;
+  const int na = d.meta[META_NACT];
+  double* Gc = d.work + w.Gc;
+  if (threadIdx.x == 0) {
+    fail = 0;
+    double m = 0.0;
+    for (int a = 0; a < na; ++a) m = fmax(m, Gc[a + (size_t)a * na]);
+    gm = m;
   }
   __syncthreads();
-  cta_householder_qr(QR4, s, na, s, d.work + w.b4, d.work + w.h4, sh);
-  cta_householder_qr(QR6, s, nn, s, d.work + w.b6, d.work + w.h6, sh);
-  __shared__ double gm;
-  if (tid == 0) { double m = 0.0; for (int a = 0; a < na; ++a) m = fmax(m, Gc[a + (size_t)a * na]); gm = m; }
-  __syncthreads();
   cta_cholesky(Gc, na, na, 1e-13 * gm, &fail);
-  // T = G^{-1} Gq (Algorithm 7 through the Gram: R^+ Q^T A_Jprev = (A_J^T A_J)^{-1} A_J^T A_Jprev)
+}
+
+// T = G^{-1} Gq, one warp per column (Algorithm 7 through the Gram:
+// R^+ Q^T A_Jprev = (A_J^T A_J)^{-1} A_J^T A_Jprev).
+__global__ void tsolve_kernel(Dev d, WorkLayout w) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int na = d.meta[META_NACT], npa = d.meta[META_NPACT];
+  const double* Gc = d.work + w.Gc;
+  const double* Gq = d.work + w.Gq;
   double* T = d.work + w.T;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  for (int b = wid; b < npa; b += nw) {
+  for (int b = gw; b < npa; b += nwarps) {
     double* x = T + (size_t)b * na;
     for (int a = lane; a < na; a += 32) x[a] = Gq[a + (size_t)b * na];
     __syncwarp();
@@ -293,11 +307,13 @@ __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout 
   double* P7 = d.cand + 3 * (size_t)t * d.n_cap;
   // rank tolerance of R: max(s, na) * eps * |largest diagonal|
   double rmax = 0.0;
-  for (int a = 0; a < na; ++a) rmax = fmax(rmax, fabs(QR4[a + (size_t)a * s]));
+  const double* r4 = d.work + w.r4;
+  const double* r6 = d.work + w.r6;
+  for (int a = 0; a < na; ++a) rmax = fmax(rmax, fabs(r4[a]));
   const double tol4 = (double)(s > na ? s : na) * 2.220446049250313e-16 * rmax;
   const int nn = d.meta[META_NNEW];
   double rmax6 = 0.0;
-  for (int c = 0; c < nn; ++c) rmax6 = fmax(rmax6, fabs(QR6[c + (size_t)c * s]));
+  for (int c = 0; c < nn; ++c) rmax6 = fmax(rmax6, fabs(r6[c]));
   const double tol6 = (double)(s > nn ? s : nn) * 2.220446049250313e-16 * rmax6;
   for (int64_t j = gw; j < n_obs; j += nwarps) {
     const double* sa = d.S + (size_t)j * d.rows;
@@ -305,7 +321,7 @@ __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout 
     for (int i = lane; i < s; i += 32) b[i] = sa[i] * rs;
     __syncwarp();
     warp_apply_qt(QR4, s, na, s, d.work + w.b4, d.work + w.h4, b);
-    warp_trsv_upper(QR4, na, s, b, tol4);
+    warp_trsv_upper_d(QR4, r4, na, s, b, tol4);
     for (int a = lane; a < na; a += 32) P4[a + (size_t)j * t] = b[a];
     __syncwarp();
     // Algorithm 5: P5(:, j) = G^{-1} (Omega A_J)^T Omega a_j
@@ -334,7 +350,7 @@ __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout 
     }
     __syncwarp();
     warp_apply_qt(QR6, s, nn, s, d.work + w.b6, d.work + w.h6, b);
-    warp_trsv_upper(QR6, nn, s, b, tol6);
+    warp_trsv_upper_d(QR6, r6, nn, s, b, tol6);
     if (lane == 0) {
       int c = 0;
       for (int a = 0; a < na; ++a) {
@@ -633,14 +649,19 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
     else basis_gram_kernel<float><<<gg, 256, 0, st>>>(d);
     gram_reduce_kernel<<<(d.t * 2 * d.t + 255) / 256, 256, 0, st>>>(d, d.gram_split);
   }
-  factor_kernel<<<1, 512, 0, st>>>(d, w);
+  gather_kernel<<<d.n_sm, 256, 0, st>>>(d, w);
+  if (!launch_qr_coop(d, d.work + w.QR4, d.work + w.b4, d.work + w.h4, d.work + w.r4, d.work + w.QR6,
+                      d.work + w.b6, d.work + w.h6, d.work + w.r6, d.gbar, st))
+    return 0;
+  gram_chol_kernel<<<1, 1024, 0, st>>>(d, w);
+  tsolve_kernel<<<(d.t + 7) / 8, 256, 0, st>>>(d, w);
   coeff_kernel<<<kApplyBlocks, kApplyThreads, 0, st>>>(d, w, n_obs, n_prev);
   const int nchunk = (int)((n_obs + kHutChunk - 1) / kHutChunk);
   hutch_partial_kernel<<<dim3(nchunk, 4), 256, 0, st>>>(d, w, n_obs);
   hutch_finish_kernel<<<4, 256, 0, st>>>(d, w, nchunk);
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
-  return nk + 9 + ngk;
+  return nk + 12 + ngk;
 }
 
 }  // namespace rid

@@ -26,11 +26,17 @@ constexpr int kCoopThreads = 256;
 constexpr uint32_t kBarrierSpin = 1u << 24;
 
 struct GridBar {
-  unsigned int* count;
-  unsigned int* gen;
+  unsigned int* count;   // monotonic ticket counter: barrier i completes at (i + 1) * gridDim.x
+  unsigned int* unused;
   int* err;
-  int* stop;   // set when any barrier timed out
+  int* stop;             // set when any barrier timed out
 };
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 
 // Returns false if the barrier timed out (or another block's did).
 __device__ bool grid_barrier(const GridBar& b) {
@@ -38,24 +44,18 @@ __device__ bool grid_barrier(const GridBar& b) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned int* vgen = b.gen;
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(b.count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(b.count, 0u);
-      __threadfence();
-      atomicAdd(b.gen, 1u);
-    } else {
-      uint32_t it = 0;
-      while (*vgen == g) {
-        if (++it > kBarrierSpin || *(volatile int*)b.stop) { ok = 0; break; }
-        if (it > 64) __nanosleep(64);
-      }
-      if (!ok) {
-        atomicExch(b.stop, 1);
-        atomicOr(b.err, ERR_TIMEOUT);
-      }
+    __threadfence();                                   // release this block's writes
+    const unsigned int ticket = atomicAdd(b.count, 1u);
+    const unsigned int target = (ticket / gridDim.x + 1u) * gridDim.x;
+    uint32_t it = 0;
+    while ((int)(ld_acquire(b.count) - target) < 0) {
+      if (++it > kBarrierSpin) { ok = 0; break; }
+      if ((it & 1023u) == 0u && *(volatile int*)b.stop) { ok = 0; break; }
+      if (it > 4096) __nanosleep(32);
+    }
+    if (!ok) {
+      atomicExch(b.stop, 1);
+      atomicOr(b.err, ERR_TIMEOUT);
     }
     __threadfence();
     ok_s = ok && !*(volatile int*)b.stop;
@@ -190,7 +190,8 @@ __global__ void topk_eig_kernel(Dev d, const double* dvec, const double* evec, i
     if (!(nhi - nlo < hi - lo)) break;
     lo = nlo;
     hi = nhi;
-    if (hi - lo <= 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    // the Sturm count's backward error is ~eps * ||T||: narrower brackets carry no information
+    if (hi - lo <= 4.440892098500626e-16 * scale + pivmin) break;
   }
   if (lane == 0) mu[gw] = 0.5 * (lo + hi);
 }
@@ -311,6 +312,70 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
   const int nvec = d.t + count;
   tri_scores_kernel<<<nvec, 32, 0, st>>>(d, R, bt, vh, ld, ll, work_base + off_vec, vstride, count);
   return nk + 2;
+}
+
+}  // namespace rid
+
+namespace rid {
+
+// Householder QR of the m x n matrix A (column-major, lda = m) on every SM, one grid
+// barrier per column: all blocks form reflector j from column j, each block applies it
+// to the columns it owns (l % gridDim.x == blockIdx.x, l > j).  Column j is never
+// rewritten: reflector j = [vhead[j]; A(j+1:m, j)], R(j, j) = rdiag[j], R(i, j) = A(i, j)
+// for i < j.
+__device__ bool qr_coop(double* A, int m, int n, double* beta, double* vhead, double* rdiag,
+                        const GridBar& bar, double* sh) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int G = gridDim.x, b = blockIdx.x;
+  for (int j = 0; j < n; ++j) {
+    const double* col = A + (size_t)j * m;
+    double part = 0.0;
+    for (int i = j + tid; i < m; i += blockDim.x) part += col[i] * col[i];
+    const double nrm2 = block_sum(part, sh);
+    const double x0 = col[j];
+    const double nrm = sqrt(nrm2);
+    const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    const double vtv = nrm2 - x0 * x0 + v0 * v0;
+    const double bt = (nrm2 > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
+    if (b == 0 && tid == 0) { beta[j] = bt; vhead[j] = v0; rdiag[j] = (bt > 0.0) ? alpha : x0; }
+    if (bt > 0.0) {
+      const int l0 = j + 1 + ((b - (j + 1)) % G + G) % G;   // first owned column after j
+      for (int l = l0 + wid * G; l < n; l += nw * G) {
+        double* a = A + (size_t)l * m;
+        double dot = (lane == 0) ? v0 * a[j] : 0.0;
+        for (int i = j + 1 + lane; i < m; i += 32) dot += col[i] * a[i];
+        dot = warp_sum(dot);
+        const double f = bt * dot;
+        if (lane == 0) a[j] -= f * v0;
+        for (int i = j + 1 + lane; i < m; i += 32) a[i] -= f * col[i];
+      }
+    }
+    if (!grid_barrier(bar)) return false;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kCoopThreads)
+qr_coop_kernel(Dev d, double* Q4, double* b4, double* h4, double* r4, double* Q6, double* b6,
+               double* h6, double* r6, GridBar bar) {
+  __shared__ double sh[33];
+  const int na = d.meta[META_NACT], nn = d.meta[META_NNEW];
+  if (!qr_coop(Q4, d.s, na, b4, h4, r4, bar, sh)) return;
+  qr_coop(Q6, d.s, nn, b6, h6, r6, bar, sh);
+}
+
+int launch_qr_coop(const Dev& d, double* Q4, double* b4, double* h4, double* r4, double* Q6,
+                   double* b6, double* h6, double* r6, unsigned int* bar_mem, cudaStream_t st) {
+  int grid = d.n_sm < d.t ? d.n_sm : d.t;
+  if (grid < 1) grid = 1;
+  cudaMemsetAsync(bar_mem, 0, 4 * sizeof(unsigned int), st);
+  GridBar gb{bar_mem, bar_mem + 1, d.err, (int*)(bar_mem + 2)};
+  Dev dd = d;
+  void* args[] = {&dd, &Q4, &b4, &h4, &r4, &Q6, &b6, &h6, &r6, &gb};
+  if (cudaLaunchCooperativeKernel((void*)qr_coop_kernel, grid, kCoopThreads, args, 0, st) != cudaSuccess)
+    return 0;
+  return 1;
 }
 
 }  // namespace rid

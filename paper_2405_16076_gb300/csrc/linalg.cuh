@@ -151,6 +151,20 @@ static __device__ void warp_trsv_upper(const double* R, int n, int lda, double* 
   }
 }
 
+// Solve R x = c in place with R's diagonal held apart in rdiag (the QR of qr_coop).
+static __device__ void warp_trsv_upper_d(const double* R, const double* rdiag, int n, int lda, double* c,
+                                         double tol) {
+  const int lane = threadIdx.x & 31;
+  for (int j = n - 1; j >= 0; --j) {
+    const double rjj = rdiag[j];
+    const double xj = (fabs(rjj) > tol) ? c[j] / rjj : 0.0;
+    __syncwarp();
+    for (int i = lane; i < j; i += 32) c[i] -= R[i + (size_t)j * lda] * xj;
+    if (lane == 0) c[j] = xj;
+    __syncwarp();
+  }
+}
+
 // Householder tridiagonalization of the symmetric n x n matrix A (full
 // storage, destroyed); diagonal to dvec, off-diagonal to evec.  v, p: n doubles each.
 static __device__ void cta_tridiagonalize(double* A, int n, int lda, double* dvec, double* evec,

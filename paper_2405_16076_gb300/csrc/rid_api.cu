@@ -12,7 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/rid.h"
+#include "rid.h"
 #include "rid_internal.cuh"
 
 using rid::Dev;

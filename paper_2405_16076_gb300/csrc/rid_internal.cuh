@@ -124,6 +124,10 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
                          int64_t off_p, int64_t off_mu, int64_t off_ldld, int64_t off_ldll,
                          int64_t off_vec, int vstride, unsigned int* bar_mem, int n_sm,
                          cudaStream_t st);
+// coop.cu: Householder QR of Omega A_J (s x n_act) and of its new-element columns
+// (s x n_new) on every SM; R's diagonal goes to r4 / r6.  Returns 1, or 0 on failure.
+int launch_qr_coop(const Dev& d, double* Q4, double* b4, double* h4, double* r4, double* Q6,
+                   double* b6, double* h6, double* r6, unsigned int* bar_mem, cudaStream_t st);
 int64_t work_doubles(const Dev& d);
 
 }  // namespace rid

@@ -453,10 +453,11 @@ tc_gram_kernel(Dev d, int x0, int y0, int64_t chunks_per_cta, float* __restrict_
     const float* pool = (const float*)d.pool;
     // task 0: new column qa (A rows qa, 64 + qa); tasks 1, 2: target columns (B rows)
     const int qa = pt >> 2, g = pt & 3;
-    const bool hasA = qa < nx;
+    const bool tasks = pt < 256;               // 64 A columns and 2 x 64 B columns, 4 segments each
+    const bool hasA = tasks && qa < nx;
     const float* srcA = hasA ? pool + (int64_t)d.gnew[x0 + qa] * d.m_pad : nullptr;
     const int qb0 = pt >> 2, qb1 = 64 + (pt >> 2);
-    const bool hasB0 = qb0 < ny, hasB1 = qb1 < ny;
+    const bool hasB0 = tasks && qb0 < ny, hasB1 = tasks && qb1 < ny;
     const float* srcB0 = hasB0 ? pool + (int64_t)d.gtgt[y0 + qb0] * d.m_pad : nullptr;
     const float* srcB1 = hasB1 ? pool + (int64_t)d.gtgt[y0 + qb1] * d.m_pad : nullptr;
     float4 a0[4], a1[4], b00[4], b01[4], b10[4], b11[4];
