@@ -171,8 +171,42 @@ int rid_sync(rid_handle* h);
 /* Forget the stream (keep allocations): the handle is as after rid_init. */
 int rid_reset(rid_handle* h);
 
-/* Text of the last error on h (or of the last failed rid_init when h is NULL). */
+/* Text of the last error on h (or, when h is NULL, of the last failed
+ * rid_init or rid_sketch_noalloc of the calling thread). */
 const char* rid_last_error(const rid_handle* h);
+
+/* Sketch of a block of columns that allocates nothing.  The paper has no
+ * counterpart: this is a library service for callers that cannot allocate
+ * device memory per call -- typically a simulation compressing its snapshots
+ * in situ, which reserves nearly all of HBM for its own fields and whose time
+ * loop must not be stalled by the device-wide synchronisation of cudaMalloc /
+ * cudaFree.  It calls no cudaMalloc, cudaFree or other allocating routine;
+ * its split-K partial sums live in one fixed file-scope device array of
+ * 8 MiB + 16 KiB per GPU, present from the library's first use on that GPU
+ * until the process exits.
+ *
+ * Computes, on cfg->cuda_stream (asynchronous; nothing is synchronized):
+ *   S_out(r, q) = (Omega a_q)_r for r < s + h   (the rows and scaling of
+ *                 RID_STATE_SKETCH of a handle with the same m, s, h, seed)
+ *   norms_out[q] = ||a_q||^2                      for q < ncols.
+ * Reads from cfg: m, s, h, omega_kind (must be RID_OMEGA_RADEMACHER),
+ * data_dtype (RID_F64 / RID_F32), seed, cuda_stream; ignores the rest.
+ *   cols      : device, column q at cols + q*ld elements of data_dtype, ld >= m
+ *   S_out     : device doubles, column q at S_out + q*lds, lds >= s + h
+ *   norms_out : device, ncols doubles
+ * The caller owns all three buffers.  Limits, fixed by the scratch size:
+ * 1 <= ncols <= 16 and s + h <= 512; a call beyond them returns RID_EINVAL
+ * with a message in rid_last_error(NULL) and launches nothing.
+ * Set-up: the first call on a device, with that device current, looks up the
+ * scratch array's address (cudaGetSymbolAddress) and keeps it; make that
+ * first call before any stream capture.  Every later call on the device
+ * shares the array, which keeps the last call's contents (nothing in it has
+ * to start at zero).  Calls whose kernels overlap on the GPU (streams with no
+ * ordering between them) race on the scratch; calls on one stream are safe.
+ * Errors: RID_EINVAL (NULL or non-device pointer, sizes, Gaussian Omega),
+ * RID_ENOLIB (no GPU), RID_ECUDA (set-up or launch failure). */
+int rid_sketch_noalloc(const rid_config* cfg, const void* cols, int64_t ld, int32_t ncols,
+                       double* S_out, int64_t lds, double* norms_out);
 
 /* Free everything.  NULL is ignored. */
 void rid_destroy(rid_handle* h);

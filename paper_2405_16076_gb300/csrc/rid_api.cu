@@ -46,6 +46,10 @@ struct rid_handle {
 
 static thread_local std::string g_init_err;
 
+namespace rid {
+void set_global_error(const char* msg) { g_init_err = msg ? msg : ""; }
+}  // namespace rid
+
 namespace {
 
 int fail(rid_handle* h, int code, const std::string& msg) {

@@ -130,4 +130,7 @@ int launch_qr_coop(const Dev& d, double* Q4, double* b4, double* h4, double* r4,
                    double* b6, double* h6, double* r6, unsigned int* bar_mem, cudaStream_t st);
 int64_t work_doubles(const Dev& d);
 
+// Message returned by rid_last_error(NULL) for failures outside a handle.
+void set_global_error(const char* msg);
+
 }  // namespace rid

@@ -64,6 +64,8 @@ def _load():
         "rid_reset": (ctypes.c_int, [H]),
         "rid_last_error": (ctypes.c_char_p, [H]),
         "rid_destroy": (None, [H]),
+        "rid_sketch_noalloc": (ctypes.c_int, [ctypes.POINTER(rid_config), P, ctypes.c_int64, ctypes.c_int32,
+                                              P, ctypes.c_int64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -88,6 +90,7 @@ rid_profile_read = lib.rid_profile_read
 rid_reset = lib.rid_reset
 rid_last_error = lib.rid_last_error
 rid_destroy = lib.rid_destroy
+rid_sketch_noalloc = lib.rid_sketch_noalloc
 
 
 def _check(rc, h=None):
