@@ -160,28 +160,73 @@ tridiag_coop_kernel(Dev d, double* A, double* R, double* dvec, double* evec, dou
   }
 }
 
+// Number of eigenvalues of the tridiagonal T below x, from the signs of the
+// leading principal minors p_i = det(T_i - x I): p_0 = 1, p_1 = d_0 - x,
+// p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1}; the count is the number of sign
+// changes along p_0 .. p_n (Sturm's theorem).  Division-free (GB300's FP64 pipe
+// is the bottleneck, and a divide costs several FMA-equivalents).  T is scaled
+// so that ||T|| <= 1 (ds = d / sc, e2s = (e / sc)^2); every 4 steps both carried
+// minors are multiplied by the same power of two (exact), which keeps them in
+// range.  An exactly zero minor takes the sign opposite to its predecessor,
+// like a zero pivot -pivmin in the LDL^T form of the count.
+__device__ __forceinline__ int sign_flip(double a, double b) {
+  return (int)(((uint32_t)__double2hiint(a) ^ (uint32_t)__double2hiint(b)) >> 31);
+}
+__device__ __forceinline__ bool is_zero(double a) {
+  return ((__double2hiint(a) & 0x7FFFFFFF) | __double2loint(a)) == 0;
+}
+__device__ int sturm_count_minors(const double* ds, const double* e2s, int n, double x) {
+  double pm = 1.0, p = ds[0] - x;
+  if (is_zero(p)) p = -0x1p-600;
+  int cnt = sign_flip(p, pm);
+  for (int i = 1; i < n; ++i) {
+    double pn = fma(ds[i] - x, p, -e2s[i - 1] * pm);
+    if (is_zero(pn)) pn = -p * 0x1p-600;
+    cnt += sign_flip(pn, p);
+    pm = p;
+    p = pn;
+    if ((i & 3) == 0) {
+      const int ea = (__double2hiint(p) >> 20) & 0x7FF, eb = (__double2hiint(pm) >> 20) & 0x7FF;
+      const int em = ea > eb ? ea : eb;
+      const double f = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em)
+      p *= f;
+      pm *= f;
+    }
+  }
+  return cnt;
+}
+
 // One warp per requested eigenvalue index j (ascending order): 32-point multisection
-// of the Sturm count until the bracket stops shrinking.
-__global__ void topk_eig_kernel(Dev d, const double* dvec, const double* evec, int k, double* mu) {
+// of the Sturm count until the bracket reaches the count's resolution eps * ||T||.
+__global__ void __launch_bounds__(32) topk_eig_kernel(Dev d, const double* dvec, const double* evec, int k,
+                                                      double* mu) {
+  extern __shared__ double tsm[];
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int gw = blockIdx.x;
   const int n = d.s;
   if (gw >= k || gw >= n) return;
   const int j = n - 1 - gw;                    // the gw-th largest
-  double lo = dvec[0], hi = dvec[0], emax = 0.0;
+  double lo = dvec[0], hi = dvec[0];
   for (int i = 0; i < n; ++i) {
     const double r = ((i > 0) ? fabs(evec[i - 1]) : 0.0) + ((i + 1 < n) ? fabs(evec[i]) : 0.0);
     lo = fmin(lo, dvec[i] - r);
     hi = fmax(hi, dvec[i] + r);
-    if (i + 1 < n) emax = fmax(emax, fabs(evec[i]));
   }
-  const double scale = fmax(fabs(lo), fabs(hi));
-  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax * emax) + 1e-300;
-  lo -= 4.440892098500626e-16 * scale + pivmin;
-  hi += 4.440892098500626e-16 * scale + pivmin;
+  const double sc = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
+  const double inv = 1.0 / sc;
+  double* ds = tsm;
+  double* e2s = tsm + n;
+  for (int i = lane; i < n; i += 32) {
+    ds[i] = dvec[i] * inv;
+    if (i + 1 < n) { const double e = evec[i] * inv; e2s[i] = e * e; }
+  }
+  __syncwarp();
+  const double tol = 4.440892098500626e-16;    // in units of sc
+  lo = lo * inv - 2.0 * tol;
+  hi = hi * inv + 2.0 * tol;
   for (int it = 0; it < 64; ++it) {
     const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const bool above = sturm_count(dvec, evec, n, x, pivmin) > j;   // eigenvalue j < x
+    const bool above = sturm_count_minors(ds, e2s, n, x) > j;   // eigenvalue j < x
     const unsigned msk = __ballot_sync(0xffffffffu, above);
     // first lane whose point lies above eigenvalue j
     const int a = msk ? __ffs(msk) - 1 : 32;
@@ -191,9 +236,9 @@ __global__ void topk_eig_kernel(Dev d, const double* dvec, const double* evec, i
     lo = nlo;
     hi = nhi;
     // the Sturm count's backward error is ~eps * ||T||: narrower brackets carry no information
-    if (hi - lo <= 4.440892098500626e-16 * scale + pivmin) break;
+    if (hi - lo <= tol) break;
   }
-  if (lane == 0) mu[gw] = 0.5 * (lo + hi);
+  if (lane == 0) mu[gw] = 0.5 * (lo + hi) * sc;
 }
 
 // lambda from the k largest eigenvalues (summed largest first), the LDL^T of T + lambda I.
@@ -288,6 +333,7 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tridiag_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 8);
+    cudaFuncSetAttribute(topk_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8);
     attr = true;
   }
   int per_sm = 0;
@@ -305,7 +351,7 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
   int nk = 2;
   const int k = d.t;
   if (d.lambda_mode == 0) {
-    topk_eig_kernel<<<k, 32, 0, st>>>(d, dv, ev, k, mu);        // one warp per SM slot: FP64-bound
+    topk_eig_kernel<<<k, 32, (size_t)2 * d.s * sizeof(double), st>>>(d, dv, ev, k, mu);   // FP64-bound
     ++nk;
   }
   lambda_ldl_kernel<<<1, 32, 0, st>>>(d, mu, k, dv, ev, ld, ll);

@@ -32,12 +32,16 @@ namespace rid {
 namespace {
 
 constexpr int kChunkK = 64;                 // coordinates per chunk: one 128-byte BF16 row
-constexpr int kProducerWarps = 8;
+constexpr int kProducerWarps = 16;           // ingest: 4 producer warps per SM sub-partition
 constexpr int kThreads = 32 * (1 + kProducerWarps);
+constexpr int kGramProducerWarps = 8;        // basis Gram: 4 column segments x 64 tasks
+constexpr int kGramThreads = 32 * (1 + kGramProducerWarps);
 constexpr int kATile = 128 * 128;           // 128 rows x 128 bytes
 constexpr int kBTile = 512 * 128;           // up to 512 Omega rows x 128 bytes
 constexpr int kSmemBytes = 2 * kATile + 2 * kBTile + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr int kL2Ahead = 6;                 // L2 prefetch distance of the ingest, in chunks
+constexpr int kMaxStages = 4;               // ingest ring stages (barrier slots)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -118,6 +122,10 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 }
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void tc_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -173,18 +181,20 @@ __device__ __forceinline__ void load16(const float* src, int64_t i, int64_t m, b
 
 __global__ void __launch_bounds__(kThreads, 1)
 tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16, int n1, int n2,
-                 int64_t chunks_per_cta, int vec, float* __restrict__ part, double* __restrict__ npart) {
+                 int64_t chunks_per_cta, int vec, float* __restrict__ part, double* __restrict__ npart,
+                 int nstage, uint32_t btile) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
-  const uint32_t sA = base;                       // 2 x 16 KB
-  const uint32_t sB = base + 2 * kATile;          // 2 x 64 KB
-  const uint32_t sBar = sB + 2 * kBTile;          // full[2], empty[2], done
+  // nstage ring stages of one A tile (16 KB) and one B tile (btile = nrows16 x 128 bytes)
+  const uint32_t sA = base;
+  const uint32_t sB = base + (uint32_t)nstage * kATile;
+  const uint32_t sBar = sB + (uint32_t)nstage * btile;   // full[4], empty[4], done
   uint8_t* gbar = gbase + (sBar - base);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 64);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 72);
-  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 16, bar_done = sBar + 32;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 96);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 104);
+  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 32, bar_done = sBar + 64;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
@@ -194,10 +204,10 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
   const int64_t nch = c1 > c0 ? c1 - c0 : 0;
 
   if (threadIdx.x == 0) {
-    mbar_init(bar_full0, 32 * kProducerWarps);
-    mbar_init(bar_full0 + 8, 32 * kProducerWarps);
-    mbar_init(bar_empty0, 1);
-    mbar_init(bar_empty0 + 8, 1);
+    for (int i = 0; i < nstage; ++i) {
+      mbar_init(bar_full0 + 8 * i, 32 * kProducerWarps);
+      mbar_init(bar_empty0 + 8 * i, 1);
+    }
     mbar_init(bar_done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -216,14 +226,14 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
     if (lane == 0) {
       const uint32_t id1 = idesc_bf16(128, n1);
       const uint32_t id2 = idesc_bf16(128, n2 > 0 ? n2 : 16);
+      int st = 0;
+      uint32_t par = 0;
       for (int64_t c = 0; c < nch; ++c) {
-        const int st = (int)(c & 1);
-        const uint32_t par = (uint32_t)((c >> 1) & 1);
         if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err)) break;
         tc_fence_after();
         const uint64_t da = desc_sw128(sA + st * kATile);
-        const uint64_t db1 = desc_sw128(sB + st * kBTile);
-        const uint64_t db2 = desc_sw128(sB + st * kBTile + 256 * 128);
+        const uint64_t db1 = desc_sw128(sB + st * btile);
+        const uint64_t db2 = desc_sw128(sB + st * btile + 256 * 128);
 #pragma unroll
         for (int kk = 0; kk < kChunkK / 16; ++kk) {
           const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
@@ -232,89 +242,111 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
           if (n2 > 0) tc_mma(tmem + (uint32_t)n1, da + adv, db2 + adv, id2, acc);
         }
         tc_commit(bar_empty0 + 8 * st);
+        if (++st == nstage) { st = 0; par ^= 1u; }
       }
       tc_commit(bar_done);   // arrives once every MMA issued above has completed
     }
     __syncwarp();
   } else {
     // ---------------------------------------------------------------- producers
-    const int pt = threadIdx.x - 32;          // 0..255
-    const int q = pt >> 2, g = pt & 3;        // data task: column q, 16-coordinate segment g
+    // 512 producer threads: thread pt moves coordinates 8g..8g+7 of every chunk of column
+    // q = pt / 8 (g = pt % 8: one 16-byte BF16 unit of the 128-byte A row) and expands
+    // Omega row pt.  Every producer thread arrives once per chunk.
+    const int pt = threadIdx.x - 32;          // 0..511
+    const int q = pt >> 3, g = pt & 7;
     const bool has_col = q < ncols;
     const float* src = has_col ? cols.p[q] : nullptr;
     float* dstp = has_col ? (float*)d.pool + (int64_t)d.dslot[count + q] * d.m_pad : nullptr;
-    const int r0 = pt, r1 = pt + 256;         // Omega rows of this thread
+    const int r0 = pt;                        // Omega row of this thread
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     double nrm = 0.0;
-    uint32_t keep0[2] = {0u, 0u}, keep1[2] = {0u, 0u};
-    float4 bufA[4], bufB[4];
-    auto load_chunk = [&](int64_t c, float4 (&v)[4]) {
-      if (has_col && c < nch) load16(src, (c0 + c) * kChunkK + 16 * g, d.m, vec != 0, v);
-    };
-    auto omega_row = [&](int r, int64_t cg, uint32_t (&keep)[2], uint32_t bst) {
-      uint32_t wa, wb;
-      if ((cg & 1) == 0) {
-        const u32x4 w = philox4x32_10((uint32_t)(cg >> 1), (uint32_t)r, kTagRademacher, 0, k0, k1);
-        wa = w.x; wb = w.y; keep[0] = w.z; keep[1] = w.w;
-      } else {
-        wa = keep[0]; wb = keep[1];
-      }
+    uint32_t keep[2] = {0u, 0u};
+    float4 bufA[2], bufB[2];
+    // Loads run two chunks ahead in registers; one lane per column also asks L2 for the
+    // column's chunk kL2Ahead chunks ahead (a bulk prefetch), so that those loads hit L2.
+    auto load_chunk = [&](int64_t c, float4 (&v)[2]) {
+      if (has_col && c < nch) {
+        const int64_t i = (c0 + c) * kChunkK + 8 * g;
+        if (vec && i + 8 <= d.m) {
+          const float4* s4 = reinterpret_cast<const float4*>(src + i);
+          v[0] = __ldcs(s4);
+          v[1] = __ldcs(s4 + 1);
+        } else {
+          float t[8];
 #pragma unroll
-      for (int cc = 0; cc < 8; ++cc) {
-        const uint32_t w = (cc < 4) ? wa : wb;
-        const int p0 = 4 * (cc & 3);
-        const uint32_t v0 = ((w << (p0 + 0)) & 0x80008000u) | 0x3F803F80u;
-        const uint32_t v1 = ((w << (p0 + 1)) & 0x80008000u) | 0x3F803F80u;
-        const uint32_t v2 = ((w << (p0 + 2)) & 0x80008000u) | 0x3F803F80u;
-        const uint32_t v3 = ((w << (p0 + 3)) & 0x80008000u) | 0x3F803F80u;
-        sts128(bst + sw128_off(r, cc), v0, v1, v2, v3);
+          for (int j = 0; j < 8; ++j) t[j] = (i + j < d.m) ? src[i + j] : 0.f;
+          v[0] = make_float4(t[0], t[1], t[2], t[3]);
+          v[1] = make_float4(t[4], t[5], t[6], t[7]);
+        }
       }
+      if (has_col && g == 0 && vec && c + kL2Ahead < nch && (c0 + c + kL2Ahead + 1) * kChunkK <= d.m)
+        prefetch_l2(src + (c0 + c + kL2Ahead) * kChunkK, kChunkK * 4);
     };
-    auto process = [&](int64_t c, float4 (&v)[4]) -> bool {
-      const int st = (int)(c & 1);
-      const uint32_t par = (uint32_t)(((c >> 1) & 1) ^ 1);
-      if (!mbar_wait(bar_empty0 + 8 * st, par, abort_flag, d.err)) return false;
+    int pst = 0;
+    uint32_t ppar = 1u;                       // first pass over the ring: stages start empty
+    auto process = [&](int64_t c, const float4 (&v)[2]) -> bool {
+      const int st = pst;
+      if (!mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err)) return false;
+      if (++pst == nstage) { pst = 0; ppar ^= 1u; }
       const int64_t cg = c0 + c;
-      const int64_t i0 = cg * kChunkK + 16 * g;
       const uint32_t ast = sA + st * kATile;
       if (has_col) {
-        float x[16];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) { x[4 * j] = v[j].x; x[4 * j + 1] = v[j].y; x[4 * j + 2] = v[j].z; x[4 * j + 3] = v[j].w; }
+        const int64_t i0 = cg * kChunkK + 8 * g;
+        const float x[8] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w};
         // copy into the buffer slot
-        if (i0 + 16 <= d.m) {
+        if (i0 + 8 <= d.m) {
           float4* o = reinterpret_cast<float4*>(dstp + i0);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) __stcs(o + j, v[j]);
+          __stcs(o, v[0]);
+          __stcs(o + 1, v[1]);
         } else {
-          for (int j = 0; j < 16; ++j) if (i0 + j < d.m) dstp[i0 + j] = x[j];
+          for (int j = 0; j < 8; ++j) if (i0 + j < d.m) dstp[i0 + j] = x[j];
         }
         float s2 = 0.f;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) s2 = fmaf(x[j], x[j], s2);
+        for (int j = 0; j < 8; ++j) s2 = fmaf(x[j], x[j], s2);
         nrm += (double)s2;
-        uint32_t hw[8], lw[8];
+        // a = hi + lo with hi = bf16(a) and lo = bf16(a - hi), two coordinates per 32-bit word
+        uint32_t hw[4], lw[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float a = x[2 * j], b = x[2 * j + 1];
-          const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-          hw[j] = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-          lw[j] = pack_bf16(a - __bfloat162float(ha), b - __bfloat162float(hb));
+        for (int j = 0; j < 4; ++j) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+          const uint32_t hv = *reinterpret_cast<const uint32_t*>(&h2);
+          hw[j] = hv;
+          const float ra = x[2 * j] - __uint_as_float(hv << 16);
+          const float rb = x[2 * j + 1] - __uint_as_float(hv & 0xFFFF0000u);
+          const __nv_bfloat162 l2 = __floats2bfloat162_rn(ra, rb);
+          lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
         }
-        sts128(ast + sw128_off(q, 2 * g), hw[0], hw[1], hw[2], hw[3]);
-        sts128(ast + sw128_off(q, 2 * g + 1), hw[4], hw[5], hw[6], hw[7]);
-        if (split) {
-          sts128(ast + sw128_off(64 + q, 2 * g), lw[0], lw[1], lw[2], lw[3]);
-          sts128(ast + sw128_off(64 + q, 2 * g + 1), lw[4], lw[5], lw[6], lw[7]);
+        sts128(ast + sw128_off(q, g), hw[0], hw[1], hw[2], hw[3]);
+        if (split) sts128(ast + sw128_off(64 + q, g), lw[0], lw[1], lw[2], lw[3]);
+      }
+      if (r0 < nrows16) {
+        const uint32_t bst = sB + st * btile;
+        uint32_t wa, wb;
+        if ((cg & 1) == 0) {
+          const u32x4 w = philox4x32_10((uint32_t)(cg >> 1), (uint32_t)r0, kTagRademacher, 0, k0, k1);
+          wa = w.x; wb = w.y; keep[0] = w.z; keep[1] = w.w;
+        } else {
+          wa = keep[0]; wb = keep[1];
+        }
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          const uint32_t w = (cc < 4) ? wa : wb;
+          const int p0 = 4 * (cc & 3);
+          const uint32_t v0 = ((w << (p0 + 0)) & 0x80008000u) | 0x3F803F80u;
+          const uint32_t v1 = ((w << (p0 + 1)) & 0x80008000u) | 0x3F803F80u;
+          const uint32_t v2 = ((w << (p0 + 2)) & 0x80008000u) | 0x3F803F80u;
+          const uint32_t v3 = ((w << (p0 + 3)) & 0x80008000u) | 0x3F803F80u;
+          sts128(bst + sw128_off(r0, cc), v0, v1, v2, v3);
         }
       }
-      const uint32_t bst = sB + st * kBTile;
-      if (r0 < nrows16) omega_row(r0, cg, keep0, bst);
-      if (r1 < nrows16) omega_row(r1, cg, keep1, bst);
       fence_async_smem();
       mbar_arrive(bar_full0 + 8 * st);
       return true;
     };
+    if (has_col && g == 0 && vec)
+      for (int64_t c = 2; c < kL2Ahead && c < nch; ++c)
+        if ((c0 + c + 1) * kChunkK <= d.m) prefetch_l2(src + (c0 + c) * kChunkK, kChunkK * 4);
     load_chunk(0, bufA);
     load_chunk(1, bufB);
     for (int64_t c = 0; c < nch; c += 2) {
@@ -325,9 +357,10 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
         load_chunk(c + 3, bufB);
       }
     }
-    // squared norms: the four segment threads of a column are adjacent lanes
+    // squared norms: the eight segment threads of a column are adjacent lanes
     nrm += __shfl_xor_sync(0xffffffffu, nrm, 1);
     nrm += __shfl_xor_sync(0xffffffffu, nrm, 2);
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, 4);
     if (has_col && g == 0) npart[(size_t)blockIdx.x * 128 + q] = nrm;
 
     // ---------------------------------------------------------------- epilogue (warps 1..4)
@@ -392,7 +425,7 @@ __global__ void tc_reduce_kernel(Dev d, const float* __restrict__ part, const do
 // at most ~2^-16 |a_i b_i| per term.  Same pipeline as the ingest kernel, no Omega.
 constexpr int kGramN = 256;
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kGramThreads, 1)
 tc_gram_kernel(Dev d, int x0, int y0, int64_t chunks_per_cta, float* __restrict__ part) {
   extern __shared__ uint8_t smem_raw[];
   const int nx = min(64, d.meta[META_NNEW] - x0);     // counts are decided on the device
@@ -415,8 +448,8 @@ tc_gram_kernel(Dev d, int x0, int y0, int64_t chunks_per_cta, float* __restrict_
   if (c1 > nchunks) c1 = nchunks;
   const int64_t nch = c1 > c0 ? c1 - c0 : 0;
   if (threadIdx.x == 0) {
-    mbar_init(bar_full0, 32 * kProducerWarps);
-    mbar_init(bar_full0 + 8, 32 * kProducerWarps);
+    mbar_init(bar_full0, 32 * kGramProducerWarps);
+    mbar_init(bar_full0 + 8, 32 * kGramProducerWarps);
     mbar_init(bar_empty0, 1);
     mbar_init(bar_empty0 + 8, 1);
     mbar_init(bar_done, 1);
@@ -561,7 +594,7 @@ int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st) {
   int nk = 0;
   for (int x0 = 0; x0 < d.t; x0 += 64)
     for (int y0 = 0; y0 < 2 * d.t; y0 += 128) {
-      tc_gram_kernel<<<nblk, kThreads, kSmemBytes, st>>>(d, x0, y0, per, part);
+      tc_gram_kernel<<<nblk, kGramThreads, kSmemBytes, st>>>(d, x0, y0, per, part);
       tc_gram_reduce_kernel<<<(64 * 128 + 255) / 256, 256, 0, st>>>(d, part, nblk, x0, y0);
       nk += 2;
     }
@@ -574,12 +607,15 @@ int tc_smem_bytes() { return kSmemBytes; }
 int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split, int count,
                      int64_t n_obs, int nblk, float* part, double* npart, cudaStream_t st,
                      cudaEvent_t* ev) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmemBytes) != cudaSuccess)
+  static int max_smem = 0;
+  if (max_smem == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       return -1;
-    attr_set = true;
+    if (cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, v) != cudaSuccess)
+      return -1;
+    max_smem = v;
   }
   Cols c;
   bool vec = true;
@@ -593,9 +629,16 @@ int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split
   const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
   int64_t per = (nchunks + nblk - 1) / nblk;
   per = (per + 1) / 2 * 2;                      // even: Philox words are shared by chunk pairs
+  // as many ring stages as fit (align slack + barrier block + stages)
+  const uint32_t btile = (uint32_t)nrows16 * 128u;
+  const int stage_bytes = kATile + (int)btile;
+  int nstage = (max_smem - 1024 - 128) / stage_bytes;
+  if (nstage > kMaxStages) nstage = kMaxStages;
+  if (nstage < 2) return -1;
+  const size_t smem = 1024 + 128 + (size_t)nstage * stage_bytes;
   if (ev) cudaEventRecord(ev[0], st);
-  tc_ingest_kernel<<<nblk, kThreads, kSmemBytes, st>>>(d, c, ncols, split, count, nrows16, n1, n2, per,
-                                                       vec ? 1 : 0, part, npart);
+  tc_ingest_kernel<<<nblk, kThreads, smem, st>>>(d, c, ncols, split, count, nrows16, n1, n2, per,
+                                                 vec ? 1 : 0, part, npart, nstage, btile);
   if (ev) cudaEventRecord(ev[1], st);
   const int n = ncols * d.rows;
   tc_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, part, npart, nblk, ncols, split, nrows16, n_obs);
