@@ -74,59 +74,107 @@ __global__ void uniforms_kernel(Dev d, double* unif, int count, int batch) {
 // The sequential scan of Algorithm 3 over the slots (one thread).  A buffered column
 // has a larger index than every column of the previous basis, so it can only be in C
 // already if an earlier slot of this scan took it (the taken[] flags).
-__global__ void select_kernel(Dev d, const double* unif, int count) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Prune / refill of the basis slots (Algorithm 3) and the bookkeeping of the later kernels.
+// One CTA: the slot state, the refill probabilities and (when they fit) the uniforms are
+// staged in shared memory by all threads; warp 0 then takes the decisions slot by slot in
+// slot order (a refill tests 32 buffered columns at a time and takes the first success in
+// column order), and thread 0 writes the index lists.
+__global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, int count, int stage_u) {
+  extern __shared__ double ssm[];
   const int t = d.t, two_t = 2 * t, per = count + 1;
-  int* taken = d.isnew;            // scratch flags over the buffered columns; rewritten below
-  for (int r = 0; r < count; ++r) taken[r] = 0;
-  for (int i = 0; i < t; ++i) {
-    const double* u = unif + (size_t)i * per;
-    if (d.JC[i] >= 0) {
-      const double tc = fmin(d.tau_old[i], d.tauC[i]);
-      if (u[0] < 1.0 - tc / d.tau_old[i]) { d.JC[i] = -1; d.slotC[i] = -1; d.tau_old[i] = 1.0; }
-      else d.tau_old[i] = tc;
-    }
-    if (d.JC[i] < 0) {
-      for (int r = 0; r < count; ++r) {
-        const double p = fmin(fmax(d.tauD[r] * d.refill_scale, 0.0), 1.0);
-        if (u[1 + r] < p && !taken[r]) {
-          taken[r] = 1;
-          d.JC[i] = d.JD[r]; d.slotC[i] = d.dslot[r]; d.tau_old[i] = d.tauD[r];
-          break;
+  const int tid = threadIdx.x, lane = tid & 31;
+  double* s_told = ssm;                                  // t
+  double* s_tauC = s_told + t;                           // t
+  double* s_p = s_tauC + t;                              // count: refill probabilities
+  double* s_tauD = s_p + count;                          // count
+  double* s_u = s_tauD + count;                          // t x per when staged
+  int64_t* s_JC = reinterpret_cast<int64_t*>(s_u + (stage_u ? (size_t)t * per : 0));
+  int64_t* s_JCp = s_JC + t;
+  int64_t* s_JD = s_JCp + t;                             // count
+  int* s_slot = reinterpret_cast<int*>(s_JD + count);    // t
+  int* s_slotp = s_slot + t;                             // t
+  int* s_dslot = s_slotp + t;                            // count
+  int* s_taken = s_dslot + count;                        // count
+  int* s_used = s_taken + count;                         // 2t
+  for (int i = tid; i < t; i += blockDim.x) {
+    s_told[i] = d.tau_old[i]; s_tauC[i] = d.tauC[i];
+    s_JC[i] = d.JC[i]; s_JCp[i] = d.JC_prev[i];
+    s_slot[i] = d.slotC[i]; s_slotp[i] = d.slotC_prev[i];
+  }
+  for (int r = tid; r < count; r += blockDim.x) {
+    const double td = d.tauD[r];
+    s_tauD[r] = td;
+    s_p[r] = fmin(fmax(td * d.refill_scale, 0.0), 1.0);
+    s_JD[r] = d.JD[r]; s_dslot[r] = d.dslot[r]; s_taken[r] = 0;
+  }
+  for (int i = tid; i < two_t; i += blockDim.x) s_used[i] = 0;
+  if (stage_u)
+    for (int i = tid; i < t * per; i += blockDim.x) s_u[i] = unif[i];
+  __syncthreads();
+  if (tid < 32) {
+    for (int i = 0; i < t; ++i) {
+      const double* u = stage_u ? s_u + (size_t)i * per : unif + (size_t)i * per;
+      if (lane == 0 && s_JC[i] >= 0) {
+        const double tc = fmin(s_told[i], s_tauC[i]);
+        if (u[0] < 1.0 - tc / s_told[i]) { s_JC[i] = -1; s_slot[i] = -1; s_told[i] = 1.0; }
+        else s_told[i] = tc;
+      }
+      __syncwarp();
+      if (s_JC[i] < 0) {
+        for (int r0 = 0; r0 < count; r0 += 32) {
+          const int r = r0 + lane;
+          const bool ok = r < count && u[1 + r] < s_p[r] && !s_taken[r];
+          const unsigned msk = __ballot_sync(0xffffffffu, ok);
+          if (msk) {
+            const int rr = r0 + __ffs(msk) - 1;
+            if (lane == 0) { s_taken[rr] = 1; s_JC[i] = s_JD[rr]; s_slot[i] = s_dslot[rr]; s_told[i] = s_tauD[rr]; }
+            break;
+          }
         }
       }
+      __syncwarp();
     }
   }
-  int na = 0, nn = 0, nk = 0;
-  for (int i = 0; i < t; ++i) {
-    d.posof[i] = -1;
-    if (d.JC[i] >= 0) {
-      const int is_new = !(d.JC[i] == d.JC_prev[i]);
-      d.act[na] = i;
-      d.posof[i] = na;
-      d.isnew[na] = is_new;
-      if (is_new) { d.newpos[nn] = na; d.gnew[nn++] = d.slotC[i]; } else ++nk;
-      ++na;
+  __syncthreads();
+  if (tid == 0) {
+    int na = 0, nn = 0, nk = 0;
+    for (int i = 0; i < t; ++i) {
+      d.posof[i] = -1;
+      if (s_JC[i] >= 0) {
+        const int is_new = !(s_JC[i] == s_JCp[i]);
+        d.act[na] = i;
+        d.posof[i] = na;
+        d.isnew[na] = is_new;
+        if (is_new) { d.newpos[nn] = na; d.gnew[nn++] = s_slot[i]; } else ++nk;
+        ++na;
+      }
     }
+    int npa = 0;
+    for (int i = 0; i < t; ++i) if (s_JCp[i] >= 0) d.pact[npa++] = i;
+    // Gram targets: pool slots of the current and the previous basis (distinct)
+    int nt = 0;
+    for (int i = 0; i < t; ++i)
+      if (s_JC[i] >= 0) { const int ps = s_slot[i]; d.gtgt[nt++] = ps; s_used[ps] = 1; }
+    for (int i = 0; i < t; ++i) {
+      if (s_JCp[i] < 0) continue;
+      const int ps = s_slotp[i];
+      if (!s_used[ps]) { d.gtgt[nt++] = ps; s_used[ps] = 2; }
+    }
+    d.meta[META_NACT] = na; d.meta[META_NPACT] = npa; d.meta[META_NNEW] = nn;
+    d.meta[META_NTGT] = nt; d.meta[META_NKEPT] = nk;
+    // buffer slots for the next batch: the first t pool slots not used by the new basis
+    int q = 0;
+    for (int ps = 0; ps < two_t && q < t; ++ps)
+      if (s_used[ps] != 1) d.dslot[q++] = ps;
   }
-  int npa = 0;
-  for (int i = 0; i < t; ++i) if (d.JC_prev[i] >= 0) d.pact[npa++] = i;
-  // Gram targets: pool slots of the current and the previous basis (distinct); the
-  // flags over the 2t pool slots live in tauD's storage after its last use above
-  int* used = (int*)d.tauD;
-  for (int ps = 0; ps < two_t; ++ps) used[ps] = 0;
-  int nt = 0;
-  for (int a = 0; a < na; ++a) { const int ps = d.slotC[d.act[a]]; d.gtgt[nt++] = ps; used[ps] = 1; }
-  for (int b = 0; b < npa; ++b) {
-    const int ps = d.slotC_prev[d.pact[b]];
-    if (!used[ps]) { d.gtgt[nt++] = ps; used[ps] = 2; }
+  for (int i = tid; i < t; i += blockDim.x) {
+    d.JC[i] = s_JC[i]; d.slotC[i] = s_slot[i]; d.tau_old[i] = s_told[i];
   }
-  d.meta[META_NACT] = na; d.meta[META_NPACT] = npa; d.meta[META_NNEW] = nn;
-  d.meta[META_NTGT] = nt; d.meta[META_NKEPT] = nk;
-  // buffer slots for the next batch: the first t pool slots not used by the new basis
-  int q = 0;
-  for (int ps = 0; ps < two_t && q < t; ++ps)
-    if (used[ps] != 1) d.dslot[q++] = ps;
+}
+
+size_t select_smem_bytes(int t, int count, bool stage_u) {
+  return (size_t)8 * (2 * t + 2 * count + (stage_u ? (size_t)t * (count + 1) : 0)) + (size_t)8 * (2 * t + count) +
+         (size_t)4 * (2 * t + 2 * count + 2 * t);
 }
 
 // ---------------------------------------------------------------- basis Gram
@@ -206,6 +254,11 @@ __global__ void gram_reduce_kernel(Dev d, int nsplit) {
   double v = 0.0;
   for (int z = 0; z < nsplit; ++z) v += d.gpart[((size_t)z * d.t + x) * two_t + y];
   const int a = d.gnew[x], b = d.gtgt[y];
+  // a pair of two new columns is computed twice; only the one with a <= b writes it, so
+  // that the stored Gram is symmetric and independent of the order of the writes
+  bool b_new = false;
+  for (int z = 0; z < nnew; ++z) b_new |= d.gnew[z] == b;
+  if (b_new && a > b) return;
   d.Gp[a + (size_t)b * two_t] = v;
   d.Gp[b + (size_t)a * two_t] = v;
 }
@@ -252,19 +305,31 @@ __global__ void gather_kernel(Dev d, WorkLayout w) {
 }
 
 // Cholesky of G (t x t at most; FP64, one CTA).
-__global__ void __launch_bounds__(1024) gram_chol_kernel(Dev d, WorkLayout w) {
+constexpr size_t kCholSmemBytes = 160 * 1024;
+constexpr size_t kHutchSmemBytes = 160 * 1024;
+
+// Cholesky factor of the basis Gram (in place in Gc); staged in shared memory when it fits.
+__global__ void __launch_bounds__(1024) gram_chol_kernel(Dev d, WorkLayout w, int staged) {
+  extern __shared__ double gsm[];
   __shared__ int fail;
   __shared__ double gm;
   const int na = d.meta[META_NACT];
   double* Gc = d.work + w.Gc;
+  const bool use_smem = staged && (size_t)na * na * sizeof(double) <= kCholSmemBytes;
+  double* A = use_smem ? gsm : Gc;
+  if (use_smem)
+    for (int i = threadIdx.x; i < na * na; i += blockDim.x) gsm[i] = Gc[i];
+  __syncthreads();
   if (threadIdx.x == 0) {
     fail = 0;
     double m = 0.0;
-    for (int a = 0; a < na; ++a) m = fmax(m, Gc[a + (size_t)a * na]);
+    for (int a = 0; a < na; ++a) m = fmax(m, A[a + (size_t)a * na]);
     gm = m;
   }
   __syncthreads();
-  cta_cholesky(Gc, na, na, 1e-13 * gm, &fail);
+  cta_cholesky(A, na, na, 1e-13 * gm, &fail);
+  if (use_smem)
+    for (int i = threadIdx.x; i < na * na; i += blockDim.x) Gc[i] = gsm[i];
 }
 
 // T = G^{-1} Gq, one warp per column (Algorithm 7 through the Gram:
@@ -471,7 +536,8 @@ __device__ void warp_pinv_rows(double* Y, double* J, int p, int q, double* Xp, d
 }
 
 // One CTA per candidate: reduce the partials and evaluate Eqs. 36-37.
-__global__ void __launch_bounds__(256) hutch_finish_kernel(Dev d, WorkLayout w, int nchunk) {
+__global__ void __launch_bounds__(512) hutch_finish_kernel(Dev d, WorkLayout w, int nchunk, int staged) {
+  extern __shared__ double hsm[];
   __shared__ double sh[33];
   const int q = blockIdx.x;
   const int na = d.meta[META_NACT];
@@ -481,11 +547,18 @@ __global__ void __launch_bounds__(256) hutch_finish_kernel(Dev d, WorkLayout w, 
   const double* HJ = d.work + w.HJ;
   const double* G = d.work + w.G;
   double* hut = d.work + w.hut + (size_t)q * w.hut_stride;
+  // Z and HJ are read many times below: staged in shared memory when they fit
+  const bool use_smem = staged && (size_t)2 * hh * na * sizeof(double) <= kHutchSmemBytes;
+  double* Zs = use_smem ? hsm : Z;
+  const double* HJs = use_smem ? hsm + (size_t)hh * na : HJ;
   for (int idx = threadIdx.x; idx < hh * na; idx += blockDim.x) {
     double v = 0.0;
     for (int c = 0; c < nchunk; ++c) v += d.hpart[((size_t)q * nchunk + c) * ((size_t)hh * t + 1) + idx];
     Z[idx] = v;                                   // Z[r + a*hh] = (Omega A_obs P^T)[r][a]
+    if (use_smem) Zs[idx] = v;
   }
+  if (use_smem)
+    for (int idx = threadIdx.x; idx < hh * na; idx += blockDim.x) hsm[(size_t)hh * na + idx] = HJ[idx];
   double trg = 0.0;
   if (threadIdx.x == 0)
     for (int c = 0; c < nchunk; ++c) trg += d.hpart[((size_t)q * nchunk + c) * ((size_t)hh * t + 1) + (size_t)hh * t];
@@ -505,32 +578,33 @@ __global__ void __launch_bounds__(256) hutch_finish_kernel(Dev d, WorkLayout w, 
     for (int idx = threadIdx.x; idx < h1 * h2; idx += blockDim.x) {
       const int a = idx / h2, b = idx % h2;
       double acc = 0.0;
-      for (int c = 0; c < na; ++c) acc += Z[(o1 + a) + (size_t)c * hh] * HJ[(o2 + b) + (size_t)c * hh];
+      for (int c = 0; c < na; ++c) acc += Zs[(o1 + a) + (size_t)c * hh] * HJs[(o2 + b) + (size_t)c * hh];
       X[idx] = acc;
     }
     for (int idx = threadIdx.x; idx < h1 * na; idx += blockDim.x) {
       const int a = idx / na, c = idx % na;
       double acc = 0.0;
-      for (int e = 0; e < na; ++e) acc += Z[(o1 + a) + (size_t)e * hh] * G[e + (size_t)c * na];
+      // G is symmetric: G[e][c] read as G[c][e], consecutive c at consecutive addresses
+      for (int e = 0; e < na; ++e) acc += Zs[(o1 + a) + (size_t)e * hh] * G[c + (size_t)e * na];
       ZG[idx] = acc;
     }
     for (int idx = threadIdx.x; idx < h1 * h3; idx += blockDim.x) {
       const int a = idx / h3, r = idx % h3;
       double acc = 0.0;
-      for (int c = 0; c < na; ++c) acc += Z[(o1 + a) + (size_t)c * hh] * HJ[(o3 + r) + (size_t)c * hh];
+      for (int c = 0; c < na; ++c) acc += Zs[(o1 + a) + (size_t)c * hh] * HJs[(o3 + r) + (size_t)c * hh];
       M1[idx] = acc;
     }
     for (int idx = threadIdx.x; idx < h3 * h2; idx += blockDim.x) {
       const int r = idx / h2, b = idx % h2;
       double acc = 0.0;
-      for (int c = 0; c < na; ++c) acc += HJ[(o3 + r) + (size_t)c * hh] * Z[(o2 + b) + (size_t)c * hh];
+      for (int c = 0; c < na; ++c) acc += HJs[(o3 + r) + (size_t)c * hh] * Zs[(o2 + b) + (size_t)c * hh];
       F[idx] = acc;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < h1 * h2; idx += blockDim.x) {
       const int a = idx / h2, b = idx % h2;
       double acc = 0.0;
-      for (int c = 0; c < na; ++c) acc += ZG[a * na + c] * Z[(o2 + b) + (size_t)c * hh];
+      for (int c = 0; c < na; ++c) acc += ZG[a * na + c] * Zs[(o2 + b) + (size_t)c * hh];
       W[idx] = acc;
     }
     __syncthreads();
@@ -562,7 +636,7 @@ __global__ void __launch_bounds__(256) hutch_finish_kernel(Dev d, WorkLayout w, 
   double p3 = 0.0;
   for (int idx = threadIdx.x; idx < h3 * na; idx += blockDim.x) {
     const int r = idx % h3, c = idx / h3;
-    p3 += Z[(o3 + r) + (size_t)c * hh] * HJ[(o3 + r) + (size_t)c * hh];
+    p3 += Zs[(o3 + r) + (size_t)c * hh] * HJs[(o3 + r) + (size_t)c * hh];
   }
   const double direct = block_sum(p3, sh);
   if (threadIdx.x == 0) {
@@ -638,7 +712,16 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   if (nk == 0) return 0;
   const int nu = d.t * (count + 1);
   uniforms_kernel<<<(nu + 255) / 256, 256, 0, st>>>(d, d.work + w.unif, count, batch);
-  select_kernel<<<1, 32, 0, st>>>(d, d.work + w.unif, count);
+  {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+      attr = true;
+    }
+    const bool stage_u = select_smem_bytes(d.t, count, true) <= 160 * 1024;
+    select_kernel<<<1, 256, select_smem_bytes(d.t, count, stage_u), st>>>(d, d.work + w.unif, count,
+                                                                         stage_u ? 1 : 0);
+  }
   int ngk = 2;
   if (d.dtype == 1 && d.tc_part) {
     ngk = launch_tc_gram(d, d.tc_blocks, d.tc_part, st);
@@ -653,12 +736,24 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   if (!launch_qr_coop(d, d.work + w.QR4, d.work + w.b4, d.work + w.h4, d.work + w.r4, d.work + w.QR6,
                       d.work + w.b6, d.work + w.h6, d.work + w.r6, d.gbar, st))
     return 0;
-  gram_chol_kernel<<<1, 1024, 0, st>>>(d, w);
+  {
+    static int staged = -1;
+    if (staged < 0)
+      staged = cudaFuncSetAttribute(gram_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kCholSmemBytes) == cudaSuccess ? 1 : 0;
+    gram_chol_kernel<<<1, 1024, staged ? kCholSmemBytes : 0, st>>>(d, w, staged);
+  }
   tsolve_kernel<<<(d.t + 7) / 8, 256, 0, st>>>(d, w);
   coeff_kernel<<<kApplyBlocks, kApplyThreads, 0, st>>>(d, w, n_obs, n_prev);
   const int nchunk = (int)((n_obs + kHutChunk - 1) / kHutChunk);
   hutch_partial_kernel<<<dim3(nchunk, 4), 256, 0, st>>>(d, w, n_obs);
-  hutch_finish_kernel<<<4, 256, 0, st>>>(d, w, nchunk);
+  {
+    static int staged = -1;
+    if (staged < 0)
+      staged = cudaFuncSetAttribute(hutch_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kHutchSmemBytes) == cudaSuccess ? 1 : 0;
+    hutch_finish_kernel<<<4, 512, staged ? kHutchSmemBytes : 0, st>>>(d, w, nchunk, staged);
+  }
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
   return nk + 12 + ngk;

@@ -242,28 +242,38 @@ __global__ void __launch_bounds__(32) topk_eig_kernel(Dev d, const double* dvec,
 }
 
 // lambda from the k largest eigenvalues (summed largest first), the LDL^T of T + lambda I.
-__global__ void lambda_ldl_kernel(Dev d, const double* mu, int k, const double* dvec,
-                                  const double* evec, double* ldl_d, double* ldl_l) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One warp stages the tridiagonal and the eigenvalues in shared memory; lane 0 then runs
+// the two sequential recurrences.
+__global__ void __launch_bounds__(32) lambda_ldl_kernel(Dev d, const double* mu, int k, const double* dvec,
+                                                        const double* evec, double* ldl_d, double* ldl_l) {
+  extern __shared__ double lsm[];
+  const int n = d.s, lane = threadIdx.x;
+  const int kk = k < n ? k : n;
+  double* sd = lsm;            // n
+  double* se = sd + n;         // n - 1
+  double* smu = se + n;        // kk
+  for (int i = lane; i < n; i += 32) { sd[i] = dvec[i]; if (i + 1 < n) se[i] = evec[i]; }
+  if (d.lambda_mode != 1)
+    for (int i = lane; i < kk; i += 32) smu[i] = mu[i];
+  __syncwarp();
+  if (lane != 0) return;
   double lam;
   if (d.lambda_mode == 1) {
     lam = d.lambda_fixed;
   } else {
     double top = 0.0;
-    const int kk = k < d.s ? k : d.s;
-    for (int i = 0; i < kk; ++i) top += mu[i];
+    for (int i = 0; i < kk; ++i) top += smu[i];
     const double fro = d.fro2[1];
     lam = (fro - top) / (double)k;
     lam = fmax(lam, 1e-12 * fro / (double)k);
   }
   d.scal[SCAL_LAMBDA] = lam;
-  const int n = d.s;
-  double del = dvec[0] + lam;
+  double del = sd[0] + lam;
   ldl_d[0] = del;
   for (int i = 1; i < n; ++i) {
-    const double l = (del != 0.0) ? evec[i - 1] / del : 0.0;
+    const double l = (del != 0.0) ? se[i - 1] / del : 0.0;
     ldl_l[i - 1] = l;
-    del = dvec[i] + lam - l * evec[i - 1];
+    del = sd[i] + lam - l * se[i - 1];
     ldl_d[i] = del;
   }
 }
@@ -334,6 +344,7 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
   if (!attr) {
     cudaFuncSetAttribute(tridiag_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 8);
     cudaFuncSetAttribute(topk_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8);
+    cudaFuncSetAttribute(lambda_ldl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 4096 * 8);
     attr = true;
   }
   int per_sm = 0;
@@ -354,7 +365,8 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
     topk_eig_kernel<<<k, 32, (size_t)2 * d.s * sizeof(double), st>>>(d, dv, ev, k, mu);   // FP64-bound
     ++nk;
   }
-  lambda_ldl_kernel<<<1, 32, 0, st>>>(d, mu, k, dv, ev, ld, ll);
+  lambda_ldl_kernel<<<1, 32, (size_t)(2 * d.s + (k < d.s ? k : d.s)) * sizeof(double), st>>>(d, mu, k, dv, ev,
+                                                                                            ld, ll);
   const int nvec = d.t + count;
   tri_scores_kernel<<<nvec, 32, 0, st>>>(d, R, bt, vh, ld, ll, work_base + off_vec, vstride, count);
   return nk + 2;

@@ -46,13 +46,11 @@ static __device__ void cta_cholesky(double* A, int n, int lda, double tol, int* 
     const double inv = ok ? 1.0 / djj : 0.0;
     for (int i = j + 1 + tid; i < n; i += nt) A[i + (size_t)j * lda] *= inv;
     __syncthreads();
-    const int nn = n - j - 1;
-    for (long long p = tid; p < (long long)nn * nn; p += nt) {
-      const int ii = (int)(p % nn), ll = (int)(p / nn);
-      if (ii >= ll) {
-        const int i = j + 1 + ii, l = j + 1 + ll;
-        A[i + (size_t)l * lda] -= A[i + (size_t)j * lda] * A[l + (size_t)j * lda];
-      }
+    // trailing lower triangle, one warp per column
+    const int lane = tid & 31, nw = nt >> 5;
+    for (int l = j + 1 + (tid >> 5); l < n; l += nw) {
+      const double alj = A[l + (size_t)j * lda];
+      for (int i = l + lane; i < n; i += 32) A[i + (size_t)l * lda] -= A[i + (size_t)j * lda] * alj;
     }
   }
   __syncthreads();

@@ -393,26 +393,44 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
 }
 
 // S(:, n_obs + q) = sum over CTAs of the hi (and lo) rows; norms in CTA order.
-__global__ void tc_reduce_kernel(Dev d, const float* __restrict__ part, const double* __restrict__ npart,
-                                 int nblk, int ncols, int split, int nrows16, int64_t n_obs) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < ncols * d.rows) {
-    const int q = idx % ncols, r = idx / ncols;
+// grid: d.rows + 1 CTAs of 256 threads.  CTA r < rows: S(r, n_obs + q) = sum over the split-K
+// blocks of the hi and lo partials of column q; thread (j, q) sums the blocks b = j (mod 4) in
+// order, and the four partial sums are added in the fixed order j = 0..3 (deterministic).
+// CTA rows: the squared norms, added to ||A_obs||^2 in column order.
+__global__ void __launch_bounds__(256) tc_reduce_kernel(Dev d, const float* __restrict__ part,
+                                                        const double* __restrict__ npart, int nblk,
+                                                        int ncols, int split, int nrows16, int64_t n_obs) {
+  __shared__ double red[4][64];
+  const int q = threadIdx.x & 63, j = threadIdx.x >> 6;
+  if ((int)blockIdx.x < d.rows) {
+    const int r = blockIdx.x;
     double v = 0.0;
-    for (int b = 0; b < nblk; ++b) {
-      const float* p = part + ((size_t)b * nrows16 + r) * 128;
-      v += (double)p[q];
-      if (split) v += (double)p[64 + q];
+    if (q < ncols) {
+      for (int b = j; b < nblk; b += 4) {
+        const float* p = part + ((size_t)b * nrows16 + r) * 128;
+        v += (double)p[q];
+        if (split) v += (double)p[64 + q];
+      }
     }
-    d.S[(size_t)(n_obs + q) * d.rows + r] = v;
-  }
-  if (idx == 0) {
-    for (int q = 0; q < ncols; ++q) {
+    red[j][q] = v;
+    __syncthreads();
+    if (j == 0 && q < ncols)
+      d.S[(size_t)(n_obs + q) * d.rows + r] = ((red[0][q] + red[1][q]) + red[2][q]) + red[3][q];
+  } else {
+    if (j == 0) {
       double v = 0.0;
-      for (int b = 0; b < nblk; ++b) v += npart[(size_t)b * 128 + q];
-      if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
-      d.fro2[0] += v;
-      d.fro2[1] += v;
+      if (q < ncols)
+        for (int b = 0; b < nblk; ++b) v += npart[(size_t)b * 128 + q];
+      red[0][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < ncols; ++c) {
+        const double v = red[0][c];
+        if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
+        d.fro2[0] += v;
+        d.fro2[1] += v;
+      }
     }
   }
 }
@@ -575,6 +593,12 @@ __global__ void tc_gram_reduce_kernel(Dev d, const float* __restrict__ part, int
   }
   const int two_t = 2 * d.t;
   const int a = d.gnew[x0 + x], bb = d.gtgt[y0 + y];
+  // a pair of two new columns is computed twice; only the one with a <= bb writes it, so
+  // that the stored Gram is symmetric and independent of the order of the writes
+  const int nnew = d.meta[META_NNEW];
+  bool b_new = false;
+  for (int z = 0; z < nnew; ++z) b_new |= d.gnew[z] == bb;
+  if (b_new && a > bb) return;
   d.Gp[a + (size_t)bb * two_t] = v;
   d.Gp[bb + (size_t)a * two_t] = v;
 }
@@ -640,8 +664,7 @@ int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split
   tc_ingest_kernel<<<nblk, kThreads, smem, st>>>(d, c, ncols, split, count, nrows16, n1, n2, per,
                                                  vec ? 1 : 0, part, npart, nstage, btile);
   if (ev) cudaEventRecord(ev[1], st);
-  const int n = ncols * d.rows;
-  tc_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, part, npart, nblk, ncols, split, nrows16, n_obs);
+  tc_reduce_kernel<<<d.rows + 1, 256, 0, st>>>(d, part, npart, nblk, ncols, split, nrows16, n_obs);
   return 0;
 }
 
