@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cooperative_groups.h>
+
 #include "linalg.cuh"
 #include "rid_internal.cuh"
 
@@ -23,6 +25,9 @@ namespace rid {
 namespace {
 
 constexpr int kCoopThreads = 256;
+constexpr int kTriThreads = 512;
+constexpr int kRedWarps = 4;             // warps that take part in the vector reductions
+namespace cg = cooperative_groups;
 constexpr uint32_t kBarrierSpin = 1u << 24;
 
 struct GridBar {
@@ -158,6 +163,141 @@ tridiag_coop_kernel(Dev d, double* A, double* R, double* dvec, double* evec, dou
       dvec[0] = A[0];
     }
   }
+}
+
+// The same reduction M = Q T Q^T with the same outputs, on one thread-block cluster: the
+// trailing columns live in the shared memory of the cluster's CTAs (CTA r owns the columns
+// j with j % C == r), and one cluster barrier per step replaces the grid barrier.  At step
+// k every CTA holds column k below the diagonal, forms the reflector, computes p on its
+// own columns and stores each p_j into every CTA's p buffer (distributed shared memory,
+// double-buffered by step parity); after the barrier it forms w, reads the next column
+// k+1 from its owner, updates its own columns except column k+1 (never written again, so
+// the owner's copy is stable while others read it), and forms the updated column k+1.
+// Control flow is uniform over the cluster, so every CTA meets every barrier.
+__global__ void __launch_bounds__(kTriThreads, 1)
+tridiag_cluster_kernel(Dev d, double* R, double* dvec, double* evec, double* beta, double* vhead, int ncl) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int n = d.s;
+  extern __shared__ double tsm2[];
+  double* cols = tsm2;                     // ncl x n: local column lc is global column lc * C + rank
+  double* x = cols + (size_t)ncl * n;      // column k below the diagonal (trailing-relative)
+  double* y = x + n;                       // column k+1 rows k+1.. as read from its owner
+  double* v = y + n;
+  double* w = v + n;
+  double* pb = w + n;                      // 2 x n, p of the step, by step parity
+  __shared__ double sh[33];
+  __shared__ double diag_s;
+  __shared__ double scal[4];               // beta, v0 of the step; kc
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const double inv_s = 1.0 / (double)n;
+  for (int lc = wid; lc * C + rank < n; lc += nw) {
+    const double* src = d.SSt + (size_t)(lc * C + rank) * n;
+    for (int i = lane; i < n; i += 32) cols[(size_t)lc * n + i] = src[i] * inv_s;
+  }
+  for (int i = tid; i + 1 < n; i += blockDim.x) x[i] = d.SSt[i + 1] * inv_s;
+  if (tid == 0) diag_s = d.SSt[0] * inv_s;
+  cl.sync();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int nn = n - k - 1;
+    // GB300's FP64 pipe is narrow: reductions run on kRedWarps warps and the scalar
+    // arithmetic (square root, division) on one thread
+    if (wid < kRedWarps) {
+      double part = 0.0;
+      for (int i = tid; i < nn; i += 32 * kRedWarps) part += x[i] * x[i];
+      part = warp_sum(part);
+      if (lane == 0) sh[wid] = part;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double nrm2 = 0.0;
+      for (int i = 0; i < kRedWarps; ++i) nrm2 += sh[i];
+      const double x0 = x[0];
+      const double tail = nrm2 - x0 * x0;
+      const double nrm = sqrt(nrm2);
+      const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = tail + v0 * v0;
+      const double bt = (tail > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
+      scal[0] = bt;
+      scal[1] = v0;
+      if (rank == 0) {
+        dvec[k] = diag_s;
+        evec[k] = (bt > 0.0) ? alpha : x0;
+        beta[k] = bt;
+        vhead[k] = v0;
+      }
+    }
+    __syncthreads();
+    const double bt = scal[0];
+    for (int i = tid; i < nn; i += blockDim.x) v[i] = (i == 0) ? scal[1] : x[i];
+    if (rank == 0)
+      for (int i = 1 + tid; i < nn; i += blockDim.x) R[(k + 1 + i) + (size_t)k * n] = x[i];
+    __syncthreads();
+    // p_j = beta (A' v)_j on the owned trailing columns, stored into every CTA's buffer
+    const int par = k & 1;
+    const int lc0 = (k + 1 - rank + C - 1) / C;   // first owned column >= k+1
+    for (int lc = lc0 + wid; lc * C + rank < n; lc += nw) {
+      const int jl = lc * C + rank - (k + 1);
+      const double* col = cols + (size_t)lc * n + (k + 1);
+      double acc = 0.0;
+      for (int i = lane; i < nn; i += 32) acc += col[i] * v[i];
+      acc = warp_sum(acc);
+      if (lane < C) {
+        double* rp = cl.map_shared_rank(pb, lane);
+        rp[(size_t)par * n + jl] = bt * acc;
+      }
+    }
+    cl.sync();
+    const double* pk = pb + (size_t)par * n;
+    if (wid < kRedWarps) {
+      double part = 0.0;
+      for (int i = tid; i < nn; i += 32 * kRedWarps) part += pk[i] * v[i];
+      part = warp_sum(part);
+      if (lane == 0) sh[wid] = part;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double ptv = 0.0;
+      for (int i = 0; i < kRedWarps; ++i) ptv += sh[i];
+      scal[2] = 0.5 * bt * ptv;
+    }
+    __syncthreads();
+    const double kc = scal[2];
+    for (int i = tid; i < nn; i += blockDim.x) w[i] = pk[i] - kc * v[i];
+    // column k+1 (rows k+1 ..) from its owner; it is not modified at this step
+    {
+      const int o = (k + 1) % C, lco = (k + 1) / C;
+      const double* yc = cl.map_shared_rank(cols, o) + (size_t)lco * n + (k + 1);
+      for (int i = tid; i < nn; i += blockDim.x) y[i] = yc[i];
+    }
+    __syncthreads();
+    // owned columns except the next one: A' -= v w^T + w v^T
+    for (int lc = lc0 + wid; lc * C + rank < n; lc += nw) {
+      const int jl = lc * C + rank - (k + 1);
+      if (jl == 0) continue;
+      double* col = cols + (size_t)lc * n + (k + 1);
+      const double wj = w[jl], vj = v[jl];
+      for (int i = lane; i < nn; i += 32) col[i] -= v[i] * wj + w[i] * vj;
+    }
+    // the updated next column (trailing column 0)
+    for (int i = 1 + tid; i < nn; i += blockDim.x) x[i - 1] = y[i] - v[i] * w[0] - w[i] * v[0];
+    if (tid == 0) diag_s = y[0] - 2.0 * v[0] * w[0];
+    __syncthreads();
+  }
+  cl.sync();
+  if (rank == 0 && tid == 0) {
+    if (n >= 2) {
+      dvec[n - 2] = diag_s;
+      evec[n - 2] = x[0];
+      beta[n - 2] = 0.0;
+      const double* last = cl.map_shared_rank(cols, (n - 1) % C) + (size_t)((n - 1) / C) * n;
+      dvec[n - 1] = last[n - 1];
+    } else {
+      dvec[0] = diag_s;
+    }
+  }
+  cl.sync();                               // no CTA leaves while its shared memory may be read
 }
 
 // Number of eigenvalues of the tridiagonal T below x, from the signs of the
@@ -323,6 +463,54 @@ tri_scores_kernel(Dev d, const double* R, const double* beta, const double* vhea
   }
 }
 
+size_t tri_cluster_smem(int n, int C) {
+  const int ncl = (n + C - 1) / C;
+  return ((size_t)ncl * n + 6 * (size_t)n) * sizeof(double);
+}
+
+// Cluster size for the shared-memory tridiagonalization of an n x n matrix: 16 (non-portable)
+// or 8 CTAs when the columns fit and the device can co-schedule the cluster, else 0.
+int tri_cluster_size(int n) {
+  static int cached_n = -1, cached_c = 0;
+  if (n == cached_n) return cached_c;
+  int dev = 0, max_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int best = 0;
+  cudaFuncAttributes fa;
+  const bool have_fa = cudaFuncGetAttributes(&fa, tridiag_cluster_kernel) == cudaSuccess;
+  max_smem -= have_fa ? (int)fa.sharedSizeBytes : 0;          // static shared memory comes first
+  if (have_fa &&
+      cudaFuncSetAttribute(tridiag_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(tridiag_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) ==
+          cudaSuccess) {
+    for (int C : {16, 8}) {
+      if (tri_cluster_smem(n, C) + 2048 > (size_t)max_smem || n < 2 * C) continue;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)C);
+      cfg.blockDim = dim3(kTriThreads);
+      cfg.dynamicSmemBytes = tri_cluster_smem(n, C);
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, tridiag_cluster_kernel, &cfg) == cudaSuccess && nclusters > 0) {
+        best = C;
+        break;
+      }
+    }
+  }
+  cudaGetLastError();
+  cached_n = n;
+  cached_c = best;
+  return best;
+}
+
 // Launch the three phases; returns the number of kernels launched (0 on failure).
 int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_R,
                          int64_t off_d, int64_t off_e, int64_t off_beta, int64_t off_vhead,
@@ -353,12 +541,30 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
   const int want = d.s - 1;                     // at least one trailing column per block
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
-  cudaMemsetAsync(bar_mem, 0, 4 * sizeof(unsigned int), st);
-  GridBar gb{bar_mem, bar_mem + 1, d.err, (int*)(bar_mem + 2)};
-  Dev dd = d;
-  void* args[] = {&dd, &A, &R, &dv, &ev, &bt, &vh, &pg, &gb};
-  if (cudaLaunchCooperativeKernel((void*)tridiag_coop_kernel, grid, kCoopThreads, args, shm, st) != cudaSuccess)
-    return 0;
+  const int C = tri_cluster_size(d.s);
+  if (C > 0) {
+    const int ncl = (d.s + C - 1) / C;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kTriThreads);
+    cfg.dynamicSmemBytes = tri_cluster_smem(d.s, C);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel, d, R, dv, ev, bt, vh, ncl) != cudaSuccess) return 0;
+  } else {
+    cudaMemsetAsync(bar_mem, 0, 4 * sizeof(unsigned int), st);
+    GridBar gb{bar_mem, bar_mem + 1, d.err, (int*)(bar_mem + 2)};
+    Dev dd = d;
+    void* args[] = {&dd, &A, &R, &dv, &ev, &bt, &vh, &pg, &gb};
+    if (cudaLaunchCooperativeKernel((void*)tridiag_coop_kernel, grid, kCoopThreads, args, shm, st) != cudaSuccess)
+      return 0;
+  }
   int nk = 2;
   const int k = d.t;
   if (d.lambda_mode == 0) {
