@@ -71,17 +71,19 @@ __global__ void uniforms_kernel(Dev d, double* unif, int count, int batch) {
   unif[idx] = sample_uniform(d.seed, (uint32_t)batch, (uint32_t)i, (uint32_t)r);
 }
 
-// The sequential scan of Algorithm 3 over the slots (one thread).  A buffered column
-// has a larger index than every column of the previous basis, so it can only be in C
-// already if an earlier slot of this scan took it (the taken[] flags).
 // Prune / refill of the basis slots (Algorithm 3) and the bookkeeping of the later kernels.
 // One CTA: the slot state, the refill probabilities and (when they fit) the uniforms are
 // staged in shared memory by all threads; warp 0 then takes the decisions slot by slot in
 // slot order (a refill tests 32 buffered columns at a time and takes the first success in
-// column order), and thread 0 writes the index lists.
-__global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, int count, int stage_u) {
+// column order), and thread 0 writes the index lists.  A buffered column has a larger index
+// than every column of the previous basis, so it can only be in C already if an earlier slot
+// of this scan took it (the taken[] flags).  Buffered column q has global index jd0 + q.
+// Pool slots: the next-but-one batch's columns go to the first t of the 3t slots that hold
+// neither the new basis nor the next batch (d.dslot_nxt), written over this batch's list.
+__global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, int count, int stage_u,
+                                                     int64_t jd0) {
   extern __shared__ double ssm[];
-  const int t = d.t, two_t = 2 * t, per = count + 1;
+  const int t = d.t, np = d.npool, per = count + 1;
   const int tid = threadIdx.x, lane = tid & 31;
   double* s_told = ssm;                                  // t
   double* s_tauC = s_told + t;                           // t
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
   int* s_slotp = s_slot + t;                             // t
   int* s_dslot = s_slotp + t;                            // count
   int* s_taken = s_dslot + count;                        // count
-  int* s_used = s_taken + count;                         // 2t
+  int* s_used = s_taken + count;                         // npool
   for (int i = tid; i < t; i += blockDim.x) {
     s_told[i] = d.tau_old[i]; s_tauC[i] = d.tauC[i];
     s_JC[i] = d.JC[i]; s_JCp[i] = d.JC_prev[i];
@@ -105,9 +107,9 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
     const double td = d.tauD[r];
     s_tauD[r] = td;
     s_p[r] = fmin(fmax(td * d.refill_scale, 0.0), 1.0);
-    s_JD[r] = d.JD[r]; s_dslot[r] = d.dslot[r]; s_taken[r] = 0;
+    s_JD[r] = jd0 + r; s_dslot[r] = d.dslot[r]; s_taken[r] = 0;
   }
-  for (int i = tid; i < two_t; i += blockDim.x) s_used[i] = 0;
+  for (int i = tid; i < np; i += blockDim.x) s_used[i] = 0;
   if (stage_u)
     for (int i = tid; i < t * per; i += blockDim.x) s_u[i] = unif[i];
   __syncthreads();
@@ -162,10 +164,12 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
     }
     d.meta[META_NACT] = na; d.meta[META_NPACT] = npa; d.meta[META_NNEW] = nn;
     d.meta[META_NTGT] = nt; d.meta[META_NKEPT] = nk;
-    // buffer slots for the next batch: the first t pool slots not used by the new basis
+    // buffer slots of the next-but-one batch: the first t pool slots holding neither the
+    // new basis (flag 1) nor the next batch's columns (flag 3)
+    for (int q = 0; q < t; ++q) s_used[d.dslot_nxt[q]] = 3;
     int q = 0;
-    for (int ps = 0; ps < two_t && q < t; ++ps)
-      if (s_used[ps] != 1) d.dslot[q++] = ps;
+    for (int ps = 0; ps < np && q < t; ++ps)
+      if (s_used[ps] != 1 && s_used[ps] != 3) d.dslot[q++] = ps;
   }
   for (int i = tid; i < t; i += blockDim.x) {
     d.JC[i] = s_JC[i]; d.slotC[i] = s_slot[i]; d.tau_old[i] = s_told[i];
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
 
 size_t select_smem_bytes(int t, int count, bool stage_u) {
   return (size_t)8 * (2 * t + 2 * count + (stage_u ? (size_t)t * (count + 1) : 0)) + (size_t)8 * (2 * t + count) +
-         (size_t)4 * (2 * t + 2 * count + 2 * t);
+         (size_t)4 * (2 * t + 2 * count + 3 * t);
 }
 
 // ---------------------------------------------------------------- basis Gram
@@ -254,20 +258,21 @@ __global__ void gram_reduce_kernel(Dev d, int nsplit) {
   double v = 0.0;
   for (int z = 0; z < nsplit; ++z) v += d.gpart[((size_t)z * d.t + x) * two_t + y];
   const int a = d.gnew[x], b = d.gtgt[y];
+  const int np = d.npool;
   // a pair of two new columns is computed twice; only the one with a <= b writes it, so
   // that the stored Gram is symmetric and independent of the order of the writes
   bool b_new = false;
   for (int z = 0; z < nnew; ++z) b_new |= d.gnew[z] == b;
   if (b_new && a > b) return;
-  d.Gp[a + (size_t)b * two_t] = v;
-  d.Gp[b + (size_t)a * two_t] = v;
+  d.Gp[a + (size_t)b * np] = v;
+  d.Gp[b + (size_t)a * np] = v;
 }
 
 // ---------------------------------------------------------------- gather + factorizations
 // Gather Omega A_J (scaled), the probe rows of the basis, G = A_J^T A_J and A_J^T A_Jprev from
 // the pool Gram, and the new-element columns for Algorithm 6 (grid-stride, many blocks).
 __global__ void gather_kernel(Dev d, WorkLayout w) {
-  const int s = d.s, two_t = 2 * d.t, hh = d.h1 + d.h2 + d.h3;
+  const int s = d.s, np = d.npool, hh = d.h1 + d.h2 + d.h3;
   const int na = d.meta[META_NACT], npa = d.meta[META_NPACT], nn = d.meta[META_NNEW];
   const double rs = 1.0 / sqrt((double)s);
   double* SJ = d.work + w.SJ;
@@ -294,13 +299,13 @@ __global__ void gather_kernel(Dev d, WorkLayout w) {
   }
   for (int64_t idx = g0; idx < (int64_t)na * na; idx += gs) {
     const int a = (int)(idx % na), b = (int)(idx / na);
-    const double g = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC[d.act[b]] * two_t];
+    const double g = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC[d.act[b]] * np];
     G[a + (size_t)b * na] = g;
     Gc[a + (size_t)b * na] = g;
   }
   for (int64_t idx = g0; idx < (int64_t)na * npa; idx += gs) {
     const int a = (int)(idx % na), b = (int)(idx / na);
-    Gq[a + (size_t)b * na] = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC_prev[d.pact[b]] * two_t];
+    Gq[a + (size_t)b * na] = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC_prev[d.pact[b]] * np];
   }
 }
 
@@ -472,71 +477,119 @@ __global__ void __launch_bounds__(256) hutch_partial_kernel(Dev d, WorkLayout w,
   if (threadIdx.x == 0) out[(size_t)hh * t] = tot;
 }
 
-// Pseudo-inverse of the small p x q matrix X (p <= q, row-major in Y) by one-sided Jacobi
-// on its rows; writes Xp (q x p, row-major).  Single warp.
-__device__ void warp_pinv_rows(double* Y, double* J, int p, int q, double* Xp, double rcond) {
-  const int lane = threadIdx.x & 31;
-  for (int idx = lane; idx < p * p; idx += 32) J[idx] = (idx % (p + 1) == 0) ? 1.0 : 0.0;
-  __syncwarp();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0;
-    for (int a = 0; a < p; ++a)
-      for (int c = a + 1; c < p; ++c) {
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int k = lane; k < q; k += 32) {
-          const double ya = Y[a * q + k], yc = Y[c * q + k];
-          al += ya * ya; be += yc * yc; ga += ya * yc;
-        }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (al == 0.0 || be == 0.0) continue;
-        const double rel = fabs(ga) / sqrt(al * be);
-        off = fmax(off, rel);
-        if (rel < 1e-15) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double tt = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-        __syncwarp();
-        for (int k = lane; k < q; k += 32) {
-          const double ya = Y[a * q + k], yc = Y[c * q + k];
-          Y[a * q + k] = cs * ya - sn * yc;
-          Y[c * q + k] = sn * ya + cs * yc;
-        }
-        for (int k = lane; k < p; k += 32) {
-          const double ja = J[k * p + a], jc = J[k * p + c];
-          J[k * p + a] = cs * ja - sn * jc;
-          J[k * p + c] = sn * ja + cs * jc;
-        }
-        __syncwarp();
-      }
-    if (off < 1e-15) break;
+// sum_{c < n} a[c sa] b[c sb] with four independent partial sums: a dependent FP64 FMA chain
+// costs about 64 cycles per step on this GPU.
+__device__ __forceinline__ double dot4(const double* a, int64_t sa, const double* b, int64_t sb, int n) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int c = 0;
+  for (; c + 4 <= n; c += 4) {
+    s0 += a[c * sa] * b[c * sb];
+    s1 += a[(c + 1) * sa] * b[(c + 1) * sb];
+    s2 += a[(c + 2) * sa] * b[(c + 2) * sb];
+    s3 += a[(c + 3) * sa] * b[(c + 3) * sb];
   }
-  // sigma_i = ||Y_i||; X^+ = Y^T diag(1/sigma^2) J^T for sigma_i > rcond * sigma_max
-  double smax = 0.0;
-  for (int a = 0; a < p; ++a) {
-    double nr = 0.0;
-    for (int k = lane; k < q; k += 32) nr += Y[a * q + k] * Y[a * q + k];
-    nr = warp_sum(nr);
-    smax = fmax(smax, sqrt(nr));
-  }
-  for (int idx = lane; idx < q * p; idx += 32) Xp[idx] = 0.0;
-  __syncwarp();
-  for (int a = 0; a < p; ++a) {
-    double nr = 0.0;
-    for (int k = lane; k < q; k += 32) nr += Y[a * q + k] * Y[a * q + k];
-    nr = warp_sum(nr);
-    const double sg = sqrt(nr);
-    if (!(sg > rcond * smax) || sg == 0.0) continue;
-    const double inv = 1.0 / nr;
-    for (int idx = lane; idx < q * p; idx += 32) {
-      const int k = idx / p, c = idx % p;      // Xp[k][c] += Y[a][k] / sigma^2 * J[c][a]
-      Xp[idx] += Y[a * q + k] * inv * J[c * p + a];
-    }
-    __syncwarp();
-  }
+  for (; c < n; ++c) s0 += a[c * sa] * b[c * sb];
+  return (s0 + s1) + (s2 + s3);
 }
 
+// Pseudo-inverse of the small p x q matrix X (p <= q, row-major in Y) by one-sided Jacobi on
+// its rows, all warps of the CTA: each sweep visits every row pair once in p' - 1 rounds of
+// disjoint pairs (round-robin order, p' = p rounded up to even; warp w rotates pair w of the
+// round).  Writes Xp (q x p, row-major); J (p x p), nr2 (p) and wred (>= 33 doubles) are scratch.
+// Singular values below rcond * sigma_max are dropped, as in an SVD-based pseudo-inverse.
+__device__ void cta_pinv_rows(double* Y, double* J, int p, int q, double* Xp, double rcond, double* nr2,
+                              double* wred) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (int idx = tid; idx < p * p; idx += blockDim.x) J[idx] = (idx % (p + 1) == 0) ? 1.0 : 0.0;
+  const int pe = p + (p & 1);
+  const int npair = pe / 2;
+  __syncthreads();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int r = 0; r < pe - 1; ++r) {
+      for (int pr = wid; pr < npair; pr += nw) {
+        // circle method: pair 0 is (r, pe - 1); pair i is ((r + i) mod (pe-1), (r - i) mod (pe-1))
+        int a, c;
+        if (pr == 0) { a = r; c = pe - 1; }
+        else { a = (r + pr) % (pe - 1); c = (r - pr + (pe - 1)) % (pe - 1); }
+        if (a > c) { const int tmp = a; a = c; c = tmp; }
+        if (c >= p) continue;                     // the dummy row of an odd p
+        double al0 = 0.0, be0 = 0.0, ga0 = 0.0, al1 = 0.0, be1 = 0.0, ga1 = 0.0;
+        int k = lane;
+        for (; k + 32 < q; k += 64) {
+          const double ya = Y[a * q + k], yc = Y[c * q + k];
+          const double yb = Y[a * q + k + 32], yd = Y[c * q + k + 32];
+          al0 += ya * ya; be0 += yc * yc; ga0 += ya * yc;
+          al1 += yb * yb; be1 += yd * yd; ga1 += yb * yd;
+        }
+        if (k < q) { const double ya = Y[a * q + k], yc = Y[c * q + k]; al0 += ya * ya; be0 += yc * yc; ga0 += ya * yc; }
+        const double al = warp_sum(al0 + al1), be = warp_sum(be0 + be1), ga = warp_sum(ga0 + ga1);
+        if (al == 0.0 || be == 0.0) continue;
+        const double rel = fabs(ga) * rsqrt(al * be);
+        off = fmax(off, rel);
+        if (rel < 1e-15) continue;
+        // rotation annihilating ga: t = ga / (d + sign(d) sqrt(d^2 + ga^2)), d = (be - al) / 2
+        const double dd = 0.5 * (be - al);
+        const double tt = ga / (dd + copysign(sqrt(dd * dd + ga * ga), dd));
+        const double cs = rsqrt(1.0 + tt * tt), sn = cs * tt;
+        for (int kk = lane; kk < q; kk += 32) {
+          const double ya = Y[a * q + kk], yc = Y[c * q + kk];
+          Y[a * q + kk] = cs * ya - sn * yc;
+          Y[c * q + kk] = sn * ya + cs * yc;
+        }
+        for (int kk = lane; kk < p; kk += 32) {
+          const double ja = J[kk * p + a], jc = J[kk * p + c];
+          J[kk * p + a] = cs * ja - sn * jc;
+          J[kk * p + c] = sn * ja + cs * jc;
+        }
+      }
+      __syncthreads();
+    }
+    // largest off-diagonal measure of the sweep over the CTA
+    if (lane == 0) wred[wid] = off;
+    __syncthreads();
+    if (tid == 0) {
+      double m = 0.0;
+      for (int i = 0; i < nw; ++i) m = fmax(m, wred[i]);
+      wred[32] = m;
+    }
+    __syncthreads();
+    const bool done = wred[32] < 1e-15;
+    __syncthreads();
+    if (done) break;
+  }
+  // sigma_a^2 = ||Y_a||^2 (one warp per row); X^+ = Y^T diag(1/sigma^2) J^T over sigma > rcond sigma_max
+  for (int a = wid; a < p; a += nw) {
+    double v = 0.0;
+    for (int k = lane; k < q; k += 32) v += Y[a * q + k] * Y[a * q + k];
+    v = warp_sum(v);
+    if (lane == 0) nr2[a] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int a = 0; a < p; ++a) m = fmax(m, nr2[a]);
+    wred[32] = sqrt(m);
+  }
+  __syncthreads();
+  const double smax = wred[32];
+  for (int idx = tid; idx < q * p; idx += blockDim.x) {
+    const int k = idx / p, c = idx % p;          // Xp[k][c] = sum_a Y[a][k] / sigma_a^2 * J[c][a]
+    double acc = 0.0;
+    for (int a = 0; a < p; ++a) {
+      const double sg = sqrt(nr2[a]);
+      if (!(sg > rcond * smax) || sg == 0.0) continue;
+      acc += Y[a * q + k] / nr2[a] * J[c * p + a];
+    }
+    Xp[idx] = acc;
+  }
+  __syncthreads();
+}
+
+
 // One CTA per candidate: reduce the partials and evaluate Eqs. 36-37.
-__global__ void __launch_bounds__(512) hutch_finish_kernel(Dev d, WorkLayout w, int nchunk, int staged) {
+__global__ void __launch_bounds__(512) hutch_finish_kernel(Dev d, WorkLayout w, int nchunk, int staged,
+                                                           int fro_slot) {
   extern __shared__ double hsm[];
   __shared__ double sh[33];
   const int q = blockIdx.x;
@@ -577,42 +630,31 @@ __global__ void __launch_bounds__(512) hutch_finish_kernel(Dev d, WorkLayout w, 
   if (h1 > 0 && h2 > 0) {
     for (int idx = threadIdx.x; idx < h1 * h2; idx += blockDim.x) {
       const int a = idx / h2, b = idx % h2;
-      double acc = 0.0;
-      for (int c = 0; c < na; ++c) acc += Zs[(o1 + a) + (size_t)c * hh] * HJs[(o2 + b) + (size_t)c * hh];
-      X[idx] = acc;
+      X[idx] = dot4(Zs + (o1 + a), hh, HJs + (o2 + b), hh, na);
     }
     for (int idx = threadIdx.x; idx < h1 * na; idx += blockDim.x) {
       const int a = idx / na, c = idx % na;
-      double acc = 0.0;
       // G is symmetric: G[e][c] read as G[c][e], consecutive c at consecutive addresses
-      for (int e = 0; e < na; ++e) acc += Zs[(o1 + a) + (size_t)e * hh] * G[c + (size_t)e * na];
-      ZG[idx] = acc;
+      ZG[idx] = dot4(Zs + (o1 + a), hh, G + c, na, na);
     }
     for (int idx = threadIdx.x; idx < h1 * h3; idx += blockDim.x) {
       const int a = idx / h3, r = idx % h3;
-      double acc = 0.0;
-      for (int c = 0; c < na; ++c) acc += Zs[(o1 + a) + (size_t)c * hh] * HJs[(o3 + r) + (size_t)c * hh];
-      M1[idx] = acc;
+      M1[idx] = dot4(Zs + (o1 + a), hh, HJs + (o3 + r), hh, na);
     }
     for (int idx = threadIdx.x; idx < h3 * h2; idx += blockDim.x) {
       const int r = idx / h2, b = idx % h2;
-      double acc = 0.0;
-      for (int c = 0; c < na; ++c) acc += HJs[(o3 + r) + (size_t)c * hh] * Zs[(o2 + b) + (size_t)c * hh];
-      F[idx] = acc;
+      F[idx] = dot4(HJs + (o3 + r), hh, Zs + (o2 + b), hh, na);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < h1 * h2; idx += blockDim.x) {
       const int a = idx / h2, b = idx % h2;
-      double acc = 0.0;
-      for (int c = 0; c < na; ++c) acc += ZG[a * na + c] * Zs[(o2 + b) + (size_t)c * hh];
-      W[idx] = acc;
+      W[idx] = dot4(ZG + a * na, 1, Zs + (o2 + b), hh, na);
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
+    {
       const int mx = (h1 > h2) ? h1 : h2;
-      warp_pinv_rows(X, Jm, h1, h2, Xp, (double)mx * 2.220446049250313e-16);
+      cta_pinv_rows(X, Jm, h1, h2, Xp, (double)mx * 2.220446049250313e-16, ZG /* free after W */, sh);
     }
-    __syncthreads();
     for (int idx = threadIdx.x; idx < h2 * h3; idx += blockDim.x) {
       const int a = idx / h3, r = idx % h3;
       double acc = 0.0;
@@ -641,7 +683,7 @@ __global__ void __launch_bounds__(512) hutch_finish_kernel(Dev d, WorkLayout w, 
   const double direct = block_sum(p3, sh);
   if (threadIdx.x == 0) {
     const double cross = term1 + (direct - corr) / (double)h3;
-    d.scal[SCAL_EST + q] = d.fro2[0] - 2.0 * cross + trg;
+    d.scal[SCAL_EST + q] = d.scal[fro_slot] - 2.0 * cross + trg;
   }
 }
 
@@ -677,7 +719,7 @@ __global__ void reset_kernel(Dev d) {
   const int t = d.t;
   for (int i = threadIdx.x; i < t; i += blockDim.x) {
     d.JC[i] = -1; d.JC_prev[i] = -1; d.slotC[i] = -1; d.slotC_prev[i] = -1;
-    d.dslot[i] = i; d.tau_old[i] = 1.0; d.JD[i] = -1;
+    d.dslot[i] = i; d.dslot_nxt[i] = t + i; d.tau_old[i] = 1.0; d.JD[i] = -1;
   }
   if (threadIdx.x == 0) {
     d.fro2[0] = 0.0; d.fro2[1] = 0.0;
@@ -687,29 +729,28 @@ __global__ void reset_kernel(Dev d) {
   }
 }
 
-__global__ void set_jd_kernel(Dev d, int count, int nb, int64_t n_obs) {
-  const int q = threadIdx.x;
-  if (q < nb) d.JD[count + q] = n_obs + q;
-}
 
-int launch_set_jd(const Dev& d, int count, int nb, int64_t n_obs, cudaStream_t st) {
-  set_jd_kernel<<<1, 32, 0, st>>>(d, count, nb, n_obs);
-  return 1;
-}
 
 int launch_reset_state(const Dev& d, cudaStream_t st) {
   reset_kernel<<<1, 256, 0, st>>>(d);
   cudaMemsetAsync(d.SSt, 0, sizeof(double) * (size_t)d.s * d.s, st);
-  cudaMemsetAsync(d.Gp, 0, sizeof(double) * (size_t)4 * d.t * d.t, st);
+  cudaMemsetAsync(d.Gp, 0, sizeof(double) * (size_t)d.npool * d.npool, st);
   return 1;
 }
 
-int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
-                      cudaStream_t st) {
+int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st) {
   const WorkLayout w = layout(d);
-  int nk = launch_lambda_scores(d, count, d.work, w.eigA, w.eigR, w.eigD, w.eigE, w.beta, w.vhead, w.eigP,
-                                w.mu, w.ldld, w.ldll, w.vec, (d.s > d.t ? d.s : d.t), d.gbar, d.n_sm, st);
-  if (nk == 0) return 0;
+  return launch_lambda(d, batch, d.work, w.eigA, w.eigR, w.eigD, w.eigE, w.beta, w.vhead, w.eigP, w.mu, w.ldld,
+                       w.ldll, d.gbar, d.n_sm, st);
+}
+
+int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
+                      cudaStream_t st, cudaEvent_t ev_scores) {
+  const WorkLayout w = layout(d);
+  const int64_t jd0 = n_obs - count;
+  int nk = launch_scores(d, count, jd0, d.work, w.eigR, w.beta, w.vhead, w.ldld, w.ldll, w.vec,
+                         (d.s > d.t ? d.s : d.t), st);
+  if (ev_scores) cudaEventRecord(ev_scores, st);
   const int nu = d.t * (count + 1);
   uniforms_kernel<<<(nu + 255) / 256, 256, 0, st>>>(d, d.work + w.unif, count, batch);
   {
@@ -720,11 +761,11 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
     }
     const bool stage_u = select_smem_bytes(d.t, count, true) <= 160 * 1024;
     select_kernel<<<1, 256, select_smem_bytes(d.t, count, stage_u), st>>>(d, d.work + w.unif, count,
-                                                                         stage_u ? 1 : 0);
+                                                                         stage_u ? 1 : 0, jd0);
   }
   int ngk = 2;
   if (d.dtype == 1 && d.tc_part) {
-    ngk = launch_tc_gram(d, d.tc_blocks, d.tc_part, st);
+    ngk = launch_tc_gram(d, d.tc_blocks, d.tg_part, st);
     if (ngk < 0) return 0;
   } else {
     dim3 gg((d.t + 63) / 64, (2 * d.t + 63) / 64, d.gram_split);
@@ -734,7 +775,7 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   }
   gather_kernel<<<d.n_sm, 256, 0, st>>>(d, w);
   if (!launch_qr_coop(d, d.work + w.QR4, d.work + w.b4, d.work + w.h4, d.work + w.r4, d.work + w.QR6,
-                      d.work + w.b6, d.work + w.h6, d.work + w.r6, d.gbar, st))
+                      d.work + w.b6, d.work + w.h6, d.work + w.r6, d.gbar2, st))
     return 0;
   {
     static int staged = -1;
@@ -752,7 +793,8 @@ int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
     if (staged < 0)
       staged = cudaFuncSetAttribute(hutch_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kHutchSmemBytes) == cudaSuccess ? 1 : 0;
-    hutch_finish_kernel<<<4, 512, staged ? kHutchSmemBytes : 0, st>>>(d, w, nchunk, staged);
+    hutch_finish_kernel<<<4, 512, staged ? kHutchSmemBytes : 0, st>>>(d, w, nchunk, staged,
+                                                                      SCAL_FRO0 + (batch & 1));
   }
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);

@@ -315,6 +315,13 @@ __device__ __forceinline__ int sign_flip(double a, double b) {
 __device__ __forceinline__ bool is_zero(double a) {
   return ((__double2hiint(a) & 0x7FFFFFFF) | __double2loint(a)) == 0;
 }
+__device__ __forceinline__ void rescale_pair(double& p, double& pm) {
+  const int ea = (__double2hiint(p) >> 20) & 0x7FF, eb = (__double2hiint(pm) >> 20) & 0x7FF;
+  const int em = ea > eb ? ea : eb;
+  const double f = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em)
+  p *= f;
+  pm *= f;
+}
 __device__ int sturm_count_minors(const double* ds, const double* e2s, int n, double x) {
   double pm = 1.0, p = ds[0] - x;
   if (is_zero(p)) p = -0x1p-600;
@@ -325,19 +332,15 @@ __device__ int sturm_count_minors(const double* ds, const double* e2s, int n, do
     cnt += sign_flip(pn, p);
     pm = p;
     p = pn;
-    if ((i & 3) == 0) {
-      const int ea = (__double2hiint(p) >> 20) & 0x7FF, eb = (__double2hiint(pm) >> 20) & 0x7FF;
-      const int em = ea > eb ? ea : eb;
-      const double f = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em)
-      p *= f;
-      pm *= f;
-    }
+    if ((i & 3) == 0) rescale_pair(p, pm);
   }
   return cnt;
 }
 
-// One warp per requested eigenvalue index j (ascending order): 32-point multisection
-// of the Sturm count until the bracket reaches the count's resolution eps * ||T||.
+// One warp per requested eigenvalue index j (ascending order): 32-point multisection of the
+// Sturm count until the bracket reaches the count's resolution eps * ||T||.  (A warp issues
+// about one FP64 instruction per 64 cycles on this GPU, dependent or not, so more shifts per
+// lane only add time.)
 __global__ void __launch_bounds__(32) topk_eig_kernel(Dev d, const double* dvec, const double* evec, int k,
                                                       double* mu) {
   extern __shared__ double tsm[];
@@ -346,32 +349,41 @@ __global__ void __launch_bounds__(32) topk_eig_kernel(Dev d, const double* dvec,
   const int n = d.s;
   if (gw >= k || gw >= n) return;
   const int j = n - 1 - gw;                    // the gw-th largest
-  double lo = dvec[0], hi = dvec[0];
-  for (int i = 0; i < n; ++i) {
+  double* ds = tsm;
+  double* e2s = tsm + n;
+  // Gershgorin interval, lane-parallel
+  double lo = 1e300, hi = -1e300;
+  for (int i = lane; i < n; i += 32) {
+    const double di = dvec[i];
     const double r = ((i > 0) ? fabs(evec[i - 1]) : 0.0) + ((i + 1 < n) ? fabs(evec[i]) : 0.0);
-    lo = fmin(lo, dvec[i] - r);
-    hi = fmax(hi, dvec[i] + r);
+    ds[i] = di;
+    if (i + 1 < n) e2s[i] = evec[i];
+    lo = fmin(lo, di - r);
+    hi = fmax(hi, di + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
   const double sc = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
   const double inv = 1.0 / sc;
-  double* ds = tsm;
-  double* e2s = tsm + n;
+  __syncwarp();
   for (int i = lane; i < n; i += 32) {
-    ds[i] = dvec[i] * inv;
-    if (i + 1 < n) { const double e = evec[i] * inv; e2s[i] = e * e; }
+    ds[i] *= inv;
+    if (i + 1 < n) { const double e = e2s[i] * inv; e2s[i] = e * e; }
   }
   __syncwarp();
   const double tol = 4.440892098500626e-16;    // in units of sc
   lo = lo * inv - 2.0 * tol;
   hi = hi * inv + 2.0 * tol;
+  const double step = 1.0 / 33.0;
   for (int it = 0; it < 64; ++it) {
-    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const bool above = sturm_count_minors(ds, e2s, n, x) > j;   // eigenvalue j < x
-    const unsigned msk = __ballot_sync(0xffffffffu, above);
+    const double x = lo + (hi - lo) * ((double)(lane + 1) * step);
+    const unsigned msk = __ballot_sync(0xffffffffu, sturm_count_minors(ds, e2s, n, x) > j);  // eig j < x
     // first lane whose point lies above eigenvalue j
     const int a = msk ? __ffs(msk) - 1 : 32;
-    const double nlo = (a == 0) ? lo : lo + (hi - lo) * (double)a / 33.0;
-    const double nhi = (a == 32) ? hi : lo + (hi - lo) * (double)(a + 1) / 33.0;
+    const double nlo = (a == 0) ? lo : lo + (hi - lo) * ((double)a * step);
+    const double nhi = (a == 32) ? hi : lo + (hi - lo) * ((double)(a + 1) * step);
     if (!(nhi - nlo < hi - lo)) break;
     lo = nlo;
     hi = nhi;
@@ -385,7 +397,8 @@ __global__ void __launch_bounds__(32) topk_eig_kernel(Dev d, const double* dvec,
 // One warp stages the tridiagonal and the eigenvalues in shared memory; lane 0 then runs
 // the two sequential recurrences.
 __global__ void __launch_bounds__(32) lambda_ldl_kernel(Dev d, const double* mu, int k, const double* dvec,
-                                                        const double* evec, double* ldl_d, double* ldl_l) {
+                                                        const double* evec, double* ldl_d, double* ldl_l,
+                                                        int fro_slot) {
   extern __shared__ double lsm[];
   const int n = d.s, lane = threadIdx.x;
   const int kk = k < n ? k : n;
@@ -408,6 +421,7 @@ __global__ void __launch_bounds__(32) lambda_ldl_kernel(Dev d, const double* mu,
     lam = fmax(lam, 1e-12 * fro / (double)k);
   }
   d.scal[SCAL_LAMBDA] = lam;
+  d.scal[fro_slot] = d.fro2[0];         // the step's ||A_obs||^2: later ingest may add to fro2
   double del = sd[0] + lam;
   ldl_d[0] = del;
   for (int i = 1; i < n; ++i) {
@@ -421,7 +435,8 @@ __global__ void __launch_bounds__(32) lambda_ldl_kernel(Dev d, const double* mu,
 // One warp per vector: occupied C slots (v < t) and buffered D columns (t <= v < t + count).
 __global__ void __launch_bounds__(32)
 tri_scores_kernel(Dev d, const double* R, const double* beta, const double* vhead,
-                  const double* ldl_d, const double* ldl_l, double* vecbuf, int vstride, int count) {
+                  const double* ldl_d, const double* ldl_l, double* vecbuf, int vstride, int count,
+                  int64_t jd0) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -431,7 +446,7 @@ tri_scores_kernel(Dev d, const double* R, const double* beta, const double* vhea
   for (int vi = gw; vi < d.t + count; vi += nwarps) {
     int64_t col;
     if (vi < d.t) { col = d.JC[vi]; if (col < 0) { if (lane == 0) d.tauC[vi] = 1.0; continue; } }
-    else col = d.JD[vi - d.t];
+    else col = jd0 + (vi - d.t);            // buffered column q of the batch is jd0 + q
     const double* l = d.Slev + (size_t)col * d.lev_ld;
     for (int i = lane; i < n; i += 32) y[i] = l[i] * rs;
     __syncwarp();
@@ -511,12 +526,11 @@ int tri_cluster_size(int n) {
   return best;
 }
 
-// Launch the three phases; returns the number of kernels launched (0 on failure).
-int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_R,
-                         int64_t off_d, int64_t off_e, int64_t off_beta, int64_t off_vhead,
-                         int64_t off_p, int64_t off_mu, int64_t off_ldld, int64_t off_ldll,
-                         int64_t off_vec, int vstride, unsigned int* bar_mem, int n_sm,
-                         cudaStream_t st) {
+// Tridiagonalization, top-k eigenvalues and lambda / LDL^T; returns the number of kernels
+// launched (0 on failure).
+int launch_lambda(const Dev& d, int batch, double* work_base, int64_t off_A, int64_t off_R, int64_t off_d,
+                  int64_t off_e, int64_t off_beta, int64_t off_vhead, int64_t off_p, int64_t off_mu,
+                  int64_t off_ldld, int64_t off_ldll, unsigned int* bar_mem, int n_sm, cudaStream_t st) {
   double* A = work_base + off_A;
   double* R = work_base + off_R;
   double* dv = work_base + off_d;
@@ -571,11 +585,20 @@ int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off
     topk_eig_kernel<<<k, 32, (size_t)2 * d.s * sizeof(double), st>>>(d, dv, ev, k, mu);   // FP64-bound
     ++nk;
   }
-  lambda_ldl_kernel<<<1, 32, (size_t)(2 * d.s + (k < d.s ? k : d.s)) * sizeof(double), st>>>(d, mu, k, dv, ev,
-                                                                                            ld, ll);
+  lambda_ldl_kernel<<<1, 32, (size_t)(2 * d.s + (k < d.s ? k : d.s)) * sizeof(double), st>>>(
+      d, mu, k, dv, ev, ld, ll, SCAL_FRO0 + (batch & 1));
+  return nk + 1;
+}
+
+// Sketched ridge scores of the occupied C slots and the count buffered columns.
+int launch_scores(const Dev& d, int count, int64_t jd0, double* work_base, int64_t off_R, int64_t off_beta,
+                  int64_t off_vhead, int64_t off_ldld, int64_t off_ldll, int64_t off_vec, int vstride,
+                  cudaStream_t st) {
   const int nvec = d.t + count;
-  tri_scores_kernel<<<nvec, 32, 0, st>>>(d, R, bt, vh, ld, ll, work_base + off_vec, vstride, count);
-  return nk + 2;
+  tri_scores_kernel<<<nvec, 32, 0, st>>>(d, work_base + off_R, work_base + off_beta, work_base + off_vhead,
+                                         work_base + off_ldld, work_base + off_ldll, work_base + off_vec,
+                                         vstride, count, jd0);
+  return 1;
 }
 
 }  // namespace rid

@@ -20,7 +20,11 @@ using rid::Dev;
 struct rid_handle {
   rid_config cfg;
   Dev d;
-  cudaStream_t st;
+  cudaStream_t st;        // the caller's stream: ingest and the lambda part of each batch step
+  cudaStream_t stb;       // the batch stream: the tail of each batch step (scores .. commit)
+  cudaEvent_t ev_lambda;  // lambda part of the latest step done (stream st)
+  cudaEvent_t ev_scores[2], ev_tail[2];   // per batch parity, recorded on stb
+  int* dslot_buf;         // 2 x t: buffer-slot lists of consecutive batches
   int count;          // columns buffered since the last batch step
   int64_t n_obs;      // columns ingested
   int64_t n_prev;     // columns covered by the last batch step
@@ -42,6 +46,7 @@ struct rid_handle {
   size_t evused;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[3];
   int64_t kernels[3];
+  float* tg_part;
 };
 
 static thread_local std::string g_init_err;
@@ -74,11 +79,33 @@ cudaError_t dalloc(T** p, size_t n) {
 
 void free_all(Dev& d, void* staging) {
   void* ptrs[] = {d.pool, d.omegaT, d.omegagT, d.S, d.SSt, d.fro2, d.JC, d.JC_prev, d.slotC,
-                  d.slotC_prev, d.dslot, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
+                  d.slotC_prev, d.dslot /* 2t: both batch lists */, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
                   d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
                   d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, staging};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
+}
+
+void destroy_sync_objects(rid_handle* h) {
+  if (h->stb) cudaStreamDestroy(h->stb);
+  cudaEvent_t evs[] = {h->ev_lambda, h->ev_scores[0], h->ev_scores[1], h->ev_tail[0], h->ev_tail[1]};
+  for (cudaEvent_t e : evs) if (e) cudaEventDestroy(e);
+  h->stb = nullptr;
+}
+
+// The device view for batch b: its buffer-slot list and the next batch's.
+Dev dev_for(const rid_handle* h, int b) {
+  Dev d = h->d;
+  const int t = d.t;
+  d.dslot = h->dslot_buf + (size_t)(b & 1) * t;
+  d.dslot_nxt = h->dslot_buf + (size_t)((b + 1) & 1) * t;
+  return d;
+}
+
+// Make the caller's stream wait for the tail of the latest batch step (after this, work on
+// h->st and a synchronization of h->st cover everything the handle has launched).
+void join(rid_handle* h) {
+  if (h->batch >= 1) cudaStreamWaitEvent(h->st, h->ev_tail[(h->batch - 1) & 1], 0);
 }
 
 int64_t hpart_len(const Dev& d, int64_t ncap) {
@@ -92,6 +119,7 @@ int grow(rid_handle* h, int64_t need) {
   if (need <= d.n_cap && d.S) return RID_OK;
   int64_t cap = d.n_cap > 0 ? d.n_cap : 1;
   while (cap < need) cap *= 2;
+  join(h);
   CK(cudaStreamSynchronize(h->st));
   double *S, *Slev = nullptr, *P, *cand, *hpart;
   CK(dalloc(&S, (size_t)d.rows * cap));
@@ -130,16 +158,26 @@ cudaEvent_t next_event(rid_handle* h) {
   return h->evpool[h->evused++];
 }
 
+// Batch step b: the lambda part on the caller's stream (after the previous step's scores
+// have read the previous lambda part's outputs), the tail on the batch stream after it.
 int run_batch(rid_handle* h) {
+  const int b = h->batch;
+  const Dev db = dev_for(h, b);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->prof) { e0 = next_event(h); e1 = next_event(h); cudaEventRecord(e0, h->st); }
-  const int nk = rid::launch_batch_step(h->d, h->count, h->n_obs, h->n_prev, h->batch, h->st);
-  if (nk == 0) {
+  if (b >= 1) CK(cudaStreamWaitEvent(h->st, h->ev_scores[(b - 1) & 1], 0));
+  const int nl = rid::launch_batch_lambda(db, b, h->st);
+  CK(cudaEventRecord(h->ev_lambda, h->st));
+  CK(cudaStreamWaitEvent(h->stb, h->ev_lambda, 0));
+  const int nt = nl ? rid::launch_batch_tail(db, h->count, h->n_obs, h->n_prev, b, h->stb, h->ev_scores[b & 1]) : 0;
+  if (nl == 0 || nt == 0) {
     cudaGetLastError();
-    return fail(h, RID_ECUDA, "batch step launch failed (cooperative launch refused)");
+    return fail(h, RID_ECUDA, "batch step launch failed (cooperative or cluster launch refused)");
   }
+  CK(cudaEventRecord(h->ev_tail[b & 1], h->stb));
+  const int nk = nl + nt;
   if (h->prof) {
-    cudaEventRecord(e1, h->st);
+    cudaEventRecord(e1, h->stb);
     h->spans[2].push_back({e0, e1});
     h->kernels[2] += nk;
   }
@@ -151,6 +189,7 @@ int run_batch(rid_handle* h) {
 }
 
 int check_device_error(rid_handle* h) {
+  join(h);
   int e = 0;
   CK(cudaMemcpyAsync(&e, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -166,24 +205,27 @@ int flush(rid_handle* h) {
   if (G == 0) return RID_OK;
   int rc = grow(h, h->n_obs + G);
   if (rc != RID_OK) return rc;
-  const int nj = rid::launch_set_jd(h->d, h->count, G, h->n_obs, h->st);
+  // The batch's buffer slots were chosen by step batch-2, and step batch-1 (which may still
+  // run on the batch stream) reads none of them.
+  if (h->count == 0 && h->batch >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_tail[(h->batch - 2) & 1], 0));
+  const Dev db = dev_for(h, h->batch);
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (h->prof) for (auto& e : ev) e = next_event(h);
-  int nk0 = 0, nk1 = nj;
+  int nk0 = 0, nk1 = 0;
   if (h->tc) {
     const int split = h->cfg.sketch_prec == RID_SKETCH_BF16X2 ? 1 : 0;
-    if (rid::launch_tc_ingest(h->d, h->pend.data(), G, split, h->count, h->n_obs, h->tc_blocks,
+    if (rid::launch_tc_ingest(db, h->pend.data(), G, split, h->count, h->n_obs, h->tc_blocks,
                               h->tc_part, h->tc_npart, h->st, h->prof ? ev : nullptr) != 0)
       return fail(h, RID_ECUDA, "tensor-core ingest launch failed");
-    rid::launch_gram_update(h->d, G, h->n_obs, h->st);
+    rid::launch_gram_update(db, G, h->n_obs, h->st);
     nk0 = 1;
     nk1 += 2;
   } else {
     for (int q0 = 0; q0 < G; q0 += rid::kMaxB) {
       const int nb = G - q0 < rid::kMaxB ? G - q0 : rid::kMaxB;
       cudaEvent_t* e = (h->prof && q0 == 0) ? ev : nullptr;
-      nk1 += rid::launch_ingest(h->d, h->pend.data() + q0, nb, h->count + q0, h->n_obs + q0, h->st, e) - 1;
-      rid::launch_gram_update(h->d, nb, h->n_obs + q0, h->st);
+      nk1 += rid::launch_ingest(db, h->pend.data() + q0, nb, h->count + q0, h->n_obs + q0, h->st, e) - 1;
+      rid::launch_gram_update(db, nb, h->n_obs + q0, h->st);
       nk0 += 1;
       nk1 += 1;
     }
@@ -307,31 +349,36 @@ int rid_init(rid_handle** out, const rid_config* c) {
     const int nrows16 = (d.rows + 15) / 16 * 16;
     const int prow = nrows16 > 256 ? nrows16 : 256;     // ingest partials or Gram partials
     AL(h->tc_part, (size_t)h->tc_blocks * prow * 128);
+    AL(h->tg_part, (size_t)h->tc_blocks * 256 * 128);
     AL(h->tc_npart, (size_t)h->tc_blocks * 128);
     d.tc_blocks = h->tc_blocks;
     d.tc_part = h->tc_part;
+    d.tg_part = h->tg_part;
   }
   {
     char* pool = nullptr;
-    AL(pool, (size_t)2 * t * d.m_pad * h->esize);
+    // 3t slots: the basis (t), the batch in its step (t), the next batch being ingested (t)
+    d.npool = 3 * t;
+    AL(pool, (size_t)d.npool * d.m_pad * h->esize);
     d.pool = pool;
-    if (cudaMemset(d.pool, 0, (size_t)2 * t * d.m_pad * h->esize) != cudaSuccess) { rc = RID_ECUDA; goto fail_alloc; }
+    if (cudaMemset(d.pool, 0, (size_t)d.npool * d.m_pad * h->esize) != cudaSuccess) { rc = RID_ECUDA; goto fail_alloc; }
   }
   if (d.omega_kind == 0) AL(d.omegaT, (size_t)d.m_pad * d.rows);
   AL(d.SSt, (size_t)d.s * d.s);
   AL(d.fro2, 2);
   AL(d.JC, t); AL(d.JC_prev, t); AL(d.JD, t);
-  AL(d.slotC, t); AL(d.slotC_prev, t); AL(d.dslot, t);
+  AL(d.slotC, t); AL(d.slotC_prev, t); AL(d.dslot, 2 * t);
   AL(d.tau_old, t); AL(d.tauC, t); AL(d.tauD, t);
   AL(d.meta, rid::META_LEN); AL(d.scal, rid::SCAL_LEN);
   AL(d.act, t); AL(d.pact, t); AL(d.isnew, t); AL(d.posof, t); AL(d.newpos, t);
   AL(d.gnew, t); AL(d.gtgt, 2 * t);
-  AL(d.Gp, (size_t)4 * t * t);
+  AL(d.Gp, (size_t)d.npool * d.npool);
   AL(d.gpart, (size_t)d.gram_split * t * 2 * t);
   AL(d.spart, (size_t)d.n_sketch_blocks * rid::kMaxB * d.rows);
   AL(d.npart, (size_t)d.n_sketch_blocks * rid::kMaxB);
   AL(d.err, 1);
-  AL(d.gbar, 4);
+  AL(d.gbar, 8);
+  d.gbar2 = d.gbar + 4;
   d.n_sm = h->n_sm;
   d.work_len = rid::work_doubles(d);
   AL(d.work, d.work_len);
@@ -346,6 +393,17 @@ int rid_init(rid_handle** out, const rid_config* c) {
     rc = grow(h, want);
     if (rc != RID_OK) goto fail_alloc;
   }
+  h->dslot_buf = d.dslot;
+  d.dslot_nxt = d.dslot + t;
+  if (cudaStreamCreateWithFlags(&h->stb, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_lambda, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_scores[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_scores[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_tail[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_tail[1], cudaEventDisableTiming) != cudaSuccess) {
+    rc = RID_ECUDA;
+    goto fail_alloc;
+  }
   if (d.omega_kind == 0) rid::launch_materialize_omega(d, h->st);
   rid::launch_reset_state(d, h->st);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->st) != cudaSuccess) {
@@ -359,7 +417,9 @@ fail_alloc:
     std::string msg = rc == RID_ENOMEM ? "device allocation failed" : (h->err.empty() ? "CUDA error during init" : h->err);
     free_all(h->d, h->staging);
     if (h->tc_part) cudaFree(h->tc_part);
+    if (h->tg_part) cudaFree(h->tg_part);
     if (h->tc_npart) cudaFree(h->tc_npart);
+    destroy_sync_objects(h);
     delete h;
     return fail(nullptr, rc, msg);
   }
@@ -424,6 +484,7 @@ int rid_error_estimate(rid_handle* h, double est_sq[5], double est_fro[5], int32
     if (rc != RID_OK) return rc;
   }
   if (h->batch == 0) return fail(h, RID_ESTATE, "no batch step has run yet");
+  join(h);
   double e[4];
   int meta[rid::META_LEN];
   CK(cudaMemcpyAsync(e, h->d.scal + rid::SCAL_EST, sizeof(e), cudaMemcpyDeviceToHost, h->st));
@@ -448,6 +509,7 @@ int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device) {
     const int rc = flush(h);
     if (rc != RID_OK) return rc;
   }
+  join(h);
   const int t = h->d.t;
   std::vector<int> slot(t);
   std::vector<int64_t> jc(t);
@@ -476,6 +538,7 @@ int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
     const int rc = flush(h);
     if (rc != RID_OK) return rc;
   }
+  join(h);
   const Dev& d = h->d;
   const int64_t n = h->n_obs;
   const void* src = nullptr;
@@ -522,6 +585,7 @@ int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
 
 int rid_profile(rid_handle* h, int32_t enable) {
   if (!h) return RID_EINVAL;
+  join(h);
   CK(cudaStreamSynchronize(h->st));
   h->prof = enable != 0;
   h->evused = 0;
@@ -532,6 +596,7 @@ int rid_profile(rid_handle* h, int32_t enable) {
 
 int rid_profile_read(rid_handle* h, double ms[3], int64_t kernels[3], int64_t groups[3]) {
   if (!h) return RID_EINVAL;
+  join(h);
   CK(cudaStreamSynchronize(h->st));
   for (int p = 0; p < 3; ++p) {
     double tot = 0.0;
@@ -556,6 +621,7 @@ int rid_sync(rid_handle* h) {
 
 int rid_reset(rid_handle* h) {
   if (!h) return RID_EINVAL;
+  join(h);
   const int nk = rid::launch_reset_state(h->d, h->st);
   if (h->prof) h->kernels[1] += nk;
   CK(cudaGetLastError());
@@ -574,11 +640,15 @@ const char* rid_last_error(const rid_handle* h) {
 
 void rid_destroy(rid_handle* h) {
   if (!h) return;
+  join(h);
   cudaStreamSynchronize(h->st);
+  if (h->stb) cudaStreamSynchronize(h->stb);
   for (auto e : h->evpool) cudaEventDestroy(e);
   free_all(h->d, h->staging);
   if (h->tc_part) cudaFree(h->tc_part);
+  if (h->tg_part) cudaFree(h->tg_part);
   if (h->tc_npart) cudaFree(h->tc_npart);
+  destroy_sync_objects(h);
   delete h;
 }
 

@@ -49,7 +49,9 @@ struct Dev {
   // selection state (device)
   int64_t* JC; int64_t* JC_prev;  // t
   int* slotC; int* slotC_prev;    // t, pool slot of each basis slot (-1 empty)
-  int* dslot;                     // t, pool slot receiving the q-th buffered column
+  int* dslot;                     // t, pool slot receiving the q-th buffered column of this batch
+  int* dslot_nxt;                 // t, the same for the next batch (chosen one batch ahead)
+  int npool;                      // pool slots: 3t (basis, this batch, next batch)
   int64_t* JD;                    // t, global index of the q-th buffered column
   double* tau_old;                // t
   double* tauC; double* tauD;     // t each
@@ -73,7 +75,9 @@ struct Dev {
   unsigned int* gbar;             // grid-barrier words of the cooperative kernels
   int n_sm;
   int tc_blocks;                  // CTAs of the tensor-core kernels
-  float* tc_part;                 // their partial accumulators (>= tc_blocks x 512 x 128 floats)
+  float* tc_part;                 // ingest partial accumulators (tc_blocks x max(rows16, 256) x 128 floats)
+  float* tg_part;                 // basis-Gram partial accumulators (tc_blocks x 256 x 128 floats)
+  unsigned int* gbar2;            // grid-barrier words of the batch-step stream's cooperative kernels
   int n_sketch_blocks;
   int gram_split;
   int64_t work_len;
@@ -85,7 +89,9 @@ enum {
   META_NOBS = 5, META_NPREV = 6, META_BATCH = 7, META_QSTAR = 8, META_NKEPT = 9, META_LEN = 16
 };
 // scal[] indices
-enum { SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_LEN = 8 };
+// SCAL_FRO0 + (batch & 1): ||A_obs||^2 as the batch's step saw it (two slots: the next step's
+// lambda part may run while this step's tail still reads it)
+enum { SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_FRO0 = 5, SCAL_LEN = 8 };
 
 // device error bits
 enum { ERR_NONFINITE = 1, ERR_CHOL = 2, ERR_EIG = 4, ERR_TIMEOUT = 8 };
@@ -111,19 +117,26 @@ int tc_smem_bytes();
 int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st);
 void launch_materialize_omega(const Dev& d, cudaStream_t st);
 
-// batch.cu
-int launch_batch_step(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
-                      cudaStream_t st);
+// batch.cu.  A batch step runs in two parts on two streams.  The lambda part
+// (tridiagonalization of the sketch Gram, its top-k eigenvalues, lambda and the LDL^T of
+// T + lambda I; it also snapshots ||A_obs||^2) reads only the sketch and runs on the ingest
+// stream.  The tail (ridge scores, prune/refill, basis Gram, Algorithms 4-8, commit) runs on
+// the batch stream; ev_scores (may be null) is recorded after the scores, once the tail no
+// longer needs the lambda part's outputs.  jd0 = global index of the batch's first column.
+// Both return the number of kernels launched (0 on failure).
+int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st);
+int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
+                      cudaStream_t st, cudaEvent_t ev_scores);
 int launch_reset_state(const Dev& d, cudaStream_t st);
-int launch_set_jd(const Dev& d, int count, int nb, int64_t n_obs, cudaStream_t st);
 
-// coop.cu: lambda (Eq. 23) and the sketched ridge scores of C and D through a
-// multi-SM tridiagonalization; returns the number of kernels launched (0 on failure).
-int launch_lambda_scores(const Dev& d, int count, double* work_base, int64_t off_A, int64_t off_R,
-                         int64_t off_d, int64_t off_e, int64_t off_beta, int64_t off_vhead,
-                         int64_t off_p, int64_t off_mu, int64_t off_ldld, int64_t off_ldll,
-                         int64_t off_vec, int vstride, unsigned int* bar_mem, int n_sm,
-                         cudaStream_t st);
+// coop.cu: lambda (Eq. 23) through a tridiagonalization of the sketch Gram (cluster or
+// grid), and the sketched ridge scores of C and D from its reflectors; 0 on failure.
+int launch_lambda(const Dev& d, int batch, double* work_base, int64_t off_A, int64_t off_R, int64_t off_d,
+                  int64_t off_e, int64_t off_beta, int64_t off_vhead, int64_t off_p, int64_t off_mu,
+                  int64_t off_ldld, int64_t off_ldll, unsigned int* bar_mem, int n_sm, cudaStream_t st);
+int launch_scores(const Dev& d, int count, int64_t jd0, double* work_base, int64_t off_R, int64_t off_beta,
+                  int64_t off_vhead, int64_t off_ldld, int64_t off_ldll, int64_t off_vec, int vstride,
+                  cudaStream_t st);
 // coop.cu: Householder QR of Omega A_J (s x n_act) and of its new-element columns
 // (s x n_new) on every SM; R's diagonal goes to r4 / r6.  Returns 1, or 0 on failure.
 int launch_qr_coop(const Dev& d, double* Q4, double* b4, double* h4, double* r4, double* Q6,

@@ -591,7 +591,7 @@ __global__ void tc_gram_reduce_kernel(Dev d, const float* __restrict__ part, int
     v += (double)p[(size_t)y * 128 + x] + (double)p[(size_t)y * 128 + 64 + x] +
          (double)p[(size_t)(128 + y) * 128 + x] + (double)p[(size_t)(128 + y) * 128 + 64 + x];
   }
-  const int two_t = 2 * d.t;
+  const int np = d.npool;
   const int a = d.gnew[x0 + x], bb = d.gtgt[y0 + y];
   // a pair of two new columns is computed twice; only the one with a <= bb writes it, so
   // that the stored Gram is symmetric and independent of the order of the writes
@@ -599,8 +599,8 @@ __global__ void tc_gram_reduce_kernel(Dev d, const float* __restrict__ part, int
   bool b_new = false;
   for (int z = 0; z < nnew; ++z) b_new |= d.gnew[z] == bb;
   if (b_new && a > bb) return;
-  d.Gp[a + (size_t)bb * two_t] = v;
-  d.Gp[bb + (size_t)a * two_t] = v;
+  d.Gp[a + (size_t)bb * np] = v;
+  d.Gp[bb + (size_t)a * np] = v;
 }
 
 // Gram of every (new, target) pool-slot pair, in tiles of 64 x 128.  The counts live on the
