@@ -242,6 +242,22 @@ def main():
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         e2e_val = world * n / e2e_s
 
+    # The ingest kernel alone (no batch step running beside it): one group of G columns per
+    # launch, G < t so that no batch step is triggered.  Reported beside the in-step figure.
+    G = max(1, min(args.group, cfg["k"] - 1, n))
+    h.reset()
+    h.ingest(X[:G])
+    h.sync()
+    h.reset()
+    h.profile(True)
+    for _ in range(5):
+        h.ingest(X[:G])
+        h.sync()
+        h.reset()
+    iso_ms_tot, _, iso_grp = h.profile_read()
+    h.profile(False)
+    iso_ms = iso_ms_tot[0] / max(int(iso_grp[0]), 1)
+
     pk = peaks()
     groups = max(int(prof_grp[0]), 1)
     avg_ms = prof_ms[0] / groups
@@ -273,6 +289,10 @@ def main():
                      "frac": achieved / pk.get("hbm_gbs"), "traffic": traffic,
                      "kernel": "tc_ingest_kernel" if args.sketch != "native" else "ingest_sketch_kernel",
                      "avg_launch_ms": avg_ms, "cols_per_launch": cols_per_launch,
+                     "isolated": {"cols_per_launch": G, "avg_launch_ms": iso_ms,
+                                  "achieved": 2.0 * G * m * 4 / (iso_ms / 1e3) / 1e9,
+                                  "frac": 2.0 * G * m * 4 / (iso_ms / 1e3) / 1e9 / pk.get("hbm_gbs"),
+                                  "note": "same kernel timed alone (no batch step beside it)"},
                      "phase_ms_per_step": {"ingest_sketch": prof_ms[0] / args.steps,
                                            "ingest_reduce": prof_ms[1] / args.steps,
                                            "batch_step": prof_ms[2] / args.steps},

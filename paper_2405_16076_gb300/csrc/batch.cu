@@ -78,8 +78,9 @@ __global__ void uniforms_kernel(Dev d, double* unif, int count, int batch) {
 // column order), and thread 0 writes the index lists.  A buffered column has a larger index
 // than every column of the previous basis, so it can only be in C already if an earlier slot
 // of this scan took it (the taken[] flags).  Buffered column q has global index jd0 + q.
-// Pool slots: the next-but-one batch's columns go to the first t of the 3t slots that hold
-// neither the new basis nor the next batch (d.dslot_nxt), written over this batch's list.
+// Pool slots: the next-but-one batch's columns go to the first t of the 4t slots that hold
+// neither the previous nor the new basis nor the next batch (d.dslot_nxt), written over this
+// batch's list; so that batch's ingest may overlap this step's Gram and the next step.
 __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, int count, int stage_u,
                                                      int64_t jd0) {
   extern __shared__ double ssm[];
@@ -164,12 +165,12 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
     }
     d.meta[META_NACT] = na; d.meta[META_NPACT] = npa; d.meta[META_NNEW] = nn;
     d.meta[META_NTGT] = nt; d.meta[META_NKEPT] = nk;
-    // buffer slots of the next-but-one batch: the first t pool slots holding neither the
-    // new basis (flag 1) nor the next batch's columns (flag 3)
+    // buffer slots of the next-but-one batch: the first t pool slots holding none of the new
+    // basis (flag 1), the previous basis (flag 2) and the next batch's columns (flag 3)
     for (int q = 0; q < t; ++q) s_used[d.dslot_nxt[q]] = 3;
     int q = 0;
     for (int ps = 0; ps < np && q < t; ++ps)
-      if (s_used[ps] != 1 && s_used[ps] != 3) d.dslot[q++] = ps;
+      if (s_used[ps] == 0) d.dslot[q++] = ps;
   }
   for (int i = tid; i < t; i += blockDim.x) {
     d.JC[i] = s_JC[i]; d.slotC[i] = s_slot[i]; d.tau_old[i] = s_told[i];
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
 
 size_t select_smem_bytes(int t, int count, bool stage_u) {
   return (size_t)8 * (2 * t + 2 * count + (stage_u ? (size_t)t * (count + 1) : 0)) + (size_t)8 * (2 * t + count) +
-         (size_t)4 * (2 * t + 2 * count + 3 * t);
+         (size_t)4 * (2 * t + 2 * count + 4 * t);
 }
 
 // ---------------------------------------------------------------- basis Gram
@@ -745,7 +746,7 @@ int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st) {
 }
 
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
-                      cudaStream_t st, cudaEvent_t ev_scores) {
+                      cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select) {
   const WorkLayout w = layout(d);
   const int64_t jd0 = n_obs - count;
   int nk = launch_scores(d, count, jd0, d.work, w.eigR, w.beta, w.vhead, w.ldld, w.ldll, w.vec,
@@ -763,6 +764,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
     select_kernel<<<1, 256, select_smem_bytes(d.t, count, stage_u), st>>>(d, d.work + w.unif, count,
                                                                          stage_u ? 1 : 0, jd0);
   }
+  if (ev_select) cudaEventRecord(ev_select, st);
   int ngk = 2;
   if (d.dtype == 1 && d.tc_part) {
     ngk = launch_tc_gram(d, d.tc_blocks, d.tg_part, st);

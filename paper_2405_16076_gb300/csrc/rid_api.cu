@@ -20,11 +20,14 @@ using rid::Dev;
 struct rid_handle {
   rid_config cfg;
   Dev d;
-  cudaStream_t st;        // the caller's stream: ingest and the lambda part of each batch step
+  cudaStream_t st;        // the caller's stream: ingest, and a snapshot of SS^T and ||A||^2 per batch
+  cudaStream_t stl;       // the lambda stream: the lambda part of each batch step, from the snapshot
   cudaStream_t stb;       // the batch stream: the tail of each batch step (scores .. commit)
-  cudaEvent_t ev_lambda;  // lambda part of the latest step done (stream st)
-  cudaEvent_t ev_scores[2], ev_tail[2];   // per batch parity, recorded on stb
+  cudaEvent_t ev_snap;    // snapshot of the latest batch taken (stream st)
+  cudaEvent_t ev_lambda[2];   // per batch parity, recorded on stl
+  cudaEvent_t ev_scores[2], ev_select[2], ev_tail[2];   // per batch parity, recorded on stb
   int* dslot_buf;         // 2 x t: buffer-slot lists of consecutive batches
+  double* snap;           // 2 x (s*s + 2): SS^T and ||A||^2 as of the end of a batch, by parity
   int count;          // columns buffered since the last batch step
   int64_t n_obs;      // columns ingested
   int64_t n_prev;     // columns covered by the last batch step
@@ -88,9 +91,12 @@ void free_all(Dev& d, void* staging) {
 
 void destroy_sync_objects(rid_handle* h) {
   if (h->stb) cudaStreamDestroy(h->stb);
-  cudaEvent_t evs[] = {h->ev_lambda, h->ev_scores[0], h->ev_scores[1], h->ev_tail[0], h->ev_tail[1]};
+  if (h->stl) cudaStreamDestroy(h->stl);
+  cudaEvent_t evs[] = {h->ev_snap, h->ev_lambda[0], h->ev_lambda[1], h->ev_scores[0], h->ev_scores[1],
+                       h->ev_select[0], h->ev_select[1], h->ev_tail[0], h->ev_tail[1]};
   for (cudaEvent_t e : evs) if (e) cudaEventDestroy(e);
   h->stb = nullptr;
+  h->stl = nullptr;
 }
 
 // The device view for batch b: its buffer-slot list and the next batch's.
@@ -158,18 +164,32 @@ cudaEvent_t next_event(rid_handle* h) {
   return h->evpool[h->evused++];
 }
 
-// Batch step b: the lambda part on the caller's stream (after the previous step's scores
-// have read the previous lambda part's outputs), the tail on the batch stream after it.
+// Batch step b.  The caller's stream snapshots SS^T and ||A||^2 (buffer b % 2, free once
+// the lambda part of step b-2 has run) and goes on ingesting; the lambda part runs on the
+// lambda stream from the snapshot (after step b-1's scores have read the previous lambda
+// part's outputs); the tail runs on the batch stream after it.
 int run_batch(rid_handle* h) {
   const int b = h->batch;
   const Dev db = dev_for(h, b);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->prof) { e0 = next_event(h); e1 = next_event(h); cudaEventRecord(e0, h->st); }
-  if (b >= 1) CK(cudaStreamWaitEvent(h->st, h->ev_scores[(b - 1) & 1], 0));
-  const int nl = rid::launch_batch_lambda(db, b, h->st);
-  CK(cudaEventRecord(h->ev_lambda, h->st));
-  CK(cudaStreamWaitEvent(h->stb, h->ev_lambda, 0));
-  const int nt = nl ? rid::launch_batch_tail(db, h->count, h->n_obs, h->n_prev, b, h->stb, h->ev_scores[b & 1]) : 0;
+  const size_t ss = (size_t)db.s * db.s;
+  double* snap = h->snap + (size_t)(b & 1) * (ss + 2);
+  if (b >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_lambda[b & 1], 0));
+  CK(cudaMemcpyAsync(snap, db.SSt, ss * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(snap + ss, db.fro2, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaEventRecord(h->ev_snap, h->st));
+  CK(cudaStreamWaitEvent(h->stl, h->ev_snap, 0));
+  if (b >= 1) CK(cudaStreamWaitEvent(h->stl, h->ev_scores[(b - 1) & 1], 0));
+  Dev dl = db;
+  dl.SSt = snap;
+  dl.fro2 = snap + ss;
+  const int nl = rid::launch_batch_lambda(dl, b, h->stl);
+  CK(cudaEventRecord(h->ev_lambda[b & 1], h->stl));
+  CK(cudaStreamWaitEvent(h->stb, h->ev_lambda[b & 1], 0));
+  const int nt = nl ? rid::launch_batch_tail(db, h->count, h->n_obs, h->n_prev, b, h->stb, h->ev_scores[b & 1],
+                                             h->ev_select[b & 1])
+                    : 0;
   if (nl == 0 || nt == 0) {
     cudaGetLastError();
     return fail(h, RID_ECUDA, "batch step launch failed (cooperative or cluster launch refused)");
@@ -205,9 +225,9 @@ int flush(rid_handle* h) {
   if (G == 0) return RID_OK;
   int rc = grow(h, h->n_obs + G);
   if (rc != RID_OK) return rc;
-  // The batch's buffer slots were chosen by step batch-2, and step batch-1 (which may still
-  // run on the batch stream) reads none of them.
-  if (h->count == 0 && h->batch >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_tail[(h->batch - 2) & 1], 0));
+  // The batch's buffer slots were chosen by the select of step batch-2; steps batch-2 and
+  // batch-1 (which may still run on the batch stream) read none of them.
+  if (h->count == 0 && h->batch >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_select[(h->batch - 2) & 1], 0));
   const Dev db = dev_for(h, h->batch);
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (h->prof) for (auto& e : ev) e = next_event(h);
@@ -340,7 +360,9 @@ int rid_init(rid_handle** out, const rid_config* c) {
   {
     const int64_t tc_chunks = (d.m + 63) / 64;
     const int64_t want_blocks = (tc_chunks + 1) / 2;
-    h->tc_blocks = (int)(want_blocks < h->n_sm ? want_blocks : h->n_sm);
+    // leave 16 SMs to the lambda part's 16-CTA cluster, which runs beside the ingest
+    const int avail = h->n_sm >= 64 ? h->n_sm - 16 : h->n_sm;
+    h->tc_blocks = (int)(want_blocks < avail ? want_blocks : avail);
     if (h->tc_blocks < 1) h->tc_blocks = 1;
   }
   int rc = RID_OK;
@@ -357,14 +379,16 @@ int rid_init(rid_handle** out, const rid_config* c) {
   }
   {
     char* pool = nullptr;
-    // 3t slots: the basis (t), the batch in its step (t), the next batch being ingested (t)
-    d.npool = 3 * t;
+    // 4t slots: the previous and the new basis of the step in flight (at most 2t together with
+    // its batch), and the next batch being ingested (t)
+    d.npool = 4 * t;
     AL(pool, (size_t)d.npool * d.m_pad * h->esize);
     d.pool = pool;
     if (cudaMemset(d.pool, 0, (size_t)d.npool * d.m_pad * h->esize) != cudaSuccess) { rc = RID_ECUDA; goto fail_alloc; }
   }
   if (d.omega_kind == 0) AL(d.omegaT, (size_t)d.m_pad * d.rows);
   AL(d.SSt, (size_t)d.s * d.s);
+  AL(h->snap, (size_t)2 * ((size_t)d.s * d.s + 2));
   AL(d.fro2, 2);
   AL(d.JC, t); AL(d.JC_prev, t); AL(d.JD, t);
   AL(d.slotC, t); AL(d.slotC_prev, t); AL(d.dslot, 2 * t);
@@ -396,9 +420,14 @@ int rid_init(rid_handle** out, const rid_config* c) {
   h->dslot_buf = d.dslot;
   d.dslot_nxt = d.dslot + t;
   if (cudaStreamCreateWithFlags(&h->stb, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_lambda, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->stl, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_lambda[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_lambda[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_scores[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_scores[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_select[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_select[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_tail[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_tail[1], cudaEventDisableTiming) != cudaSuccess) {
     rc = RID_ECUDA;
@@ -419,6 +448,7 @@ fail_alloc:
     if (h->tc_part) cudaFree(h->tc_part);
     if (h->tg_part) cudaFree(h->tg_part);
     if (h->tc_npart) cudaFree(h->tc_npart);
+    if (h->snap) cudaFree(h->snap);
     destroy_sync_objects(h);
     delete h;
     return fail(nullptr, rc, msg);
@@ -643,11 +673,13 @@ void rid_destroy(rid_handle* h) {
   join(h);
   cudaStreamSynchronize(h->st);
   if (h->stb) cudaStreamSynchronize(h->stb);
+  if (h->stl) cudaStreamSynchronize(h->stl);
   for (auto e : h->evpool) cudaEventDestroy(e);
   free_all(h->d, h->staging);
   if (h->tc_part) cudaFree(h->tc_part);
   if (h->tg_part) cudaFree(h->tg_part);
   if (h->tc_npart) cudaFree(h->tc_npart);
+  if (h->snap) cudaFree(h->snap);
   destroy_sync_objects(h);
   delete h;
 }

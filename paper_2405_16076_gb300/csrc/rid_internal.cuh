@@ -51,7 +51,7 @@ struct Dev {
   int* slotC; int* slotC_prev;    // t, pool slot of each basis slot (-1 empty)
   int* dslot;                     // t, pool slot receiving the q-th buffered column of this batch
   int* dslot_nxt;                 // t, the same for the next batch (chosen one batch ahead)
-  int npool;                      // pool slots: 3t (basis, this batch, next batch)
+  int npool;                      // pool slots: 4t (previous and new basis, this batch, next batch)
   int64_t* JD;                    // t, global index of the q-th buffered column
   double* tau_old;                // t
   double* tauC; double* tauD;     // t each
@@ -122,11 +122,11 @@ void launch_materialize_omega(const Dev& d, cudaStream_t st);
 // T + lambda I; it also snapshots ||A_obs||^2) reads only the sketch and runs on the ingest
 // stream.  The tail (ridge scores, prune/refill, basis Gram, Algorithms 4-8, commit) runs on
 // the batch stream; ev_scores (may be null) is recorded after the scores, once the tail no
-// longer needs the lambda part's outputs.  jd0 = global index of the batch's first column.
-// Both return the number of kernels launched (0 on failure).
+// longer needs the lambda part's outputs, and ev_select (may be null) once the buffer slots of
+// the next-but-one batch are chosen.  Both return the number of kernels launched (0 on failure).
 int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st);
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
-                      cudaStream_t st, cudaEvent_t ev_scores);
+                      cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select);
 int launch_reset_state(const Dev& d, cudaStream_t st);
 
 // coop.cu: lambda (Eq. 23) through a tridiagonalization of the sketch Gram (cluster or
