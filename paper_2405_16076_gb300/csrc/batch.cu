@@ -154,10 +154,13 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
     }
     int npa = 0;
     for (int i = 0; i < t; ++i) if (s_JCp[i] >= 0) d.pact[npa++] = i;
-    // Gram targets: pool slots of the current and the previous basis (distinct)
+    // Gram targets: pool slots of the current and the previous basis (distinct); the new
+    // elements first, in the order of gnew, so that target x < nnew is new element x
     int nt = 0;
     for (int i = 0; i < t; ++i)
-      if (s_JC[i] >= 0) { const int ps = s_slot[i]; d.gtgt[nt++] = ps; s_used[ps] = 1; }
+      if (s_JC[i] >= 0 && s_JC[i] != s_JCp[i]) { const int ps = s_slot[i]; d.gtgt[nt++] = ps; s_used[ps] = 1; }
+    for (int i = 0; i < t; ++i)
+      if (s_JC[i] >= 0 && s_JC[i] == s_JCp[i]) { const int ps = s_slot[i]; d.gtgt[nt++] = ps; s_used[ps] = 1; }
     for (int i = 0; i < t; ++i) {
       if (s_JCp[i] < 0) continue;
       const int ps = s_slotp[i];

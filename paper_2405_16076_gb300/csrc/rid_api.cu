@@ -371,7 +371,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
     const int nrows16 = (d.rows + 15) / 16 * 16;
     const int prow = nrows16 > 256 ? nrows16 : 256;     // ingest partials or Gram partials
     AL(h->tc_part, (size_t)h->tc_blocks * prow * 128);
-    AL(h->tg_part, (size_t)h->tc_blocks * 256 * 128);
+    AL(h->tg_part, (size_t)h->tc_blocks * 512 * 128);     // basis-Gram partials: 512 rows per CTA
     AL(h->tc_npart, (size_t)h->tc_blocks * 128);
     d.tc_blocks = h->tc_blocks;
     d.tc_part = h->tc_part;

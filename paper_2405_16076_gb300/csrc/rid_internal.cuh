@@ -76,7 +76,7 @@ struct Dev {
   int n_sm;
   int tc_blocks;                  // CTAs of the tensor-core kernels
   float* tc_part;                 // ingest partial accumulators (tc_blocks x max(rows16, 256) x 128 floats)
-  float* tg_part;                 // basis-Gram partial accumulators (tc_blocks x 256 x 128 floats)
+  float* tg_part;                 // basis-Gram partial accumulators (tc_blocks x 512 x 128 floats)
   unsigned int* gbar2;            // grid-barrier words of the batch-step stream's cooperative kernels
   int n_sketch_blocks;
   int gram_split;
@@ -113,7 +113,7 @@ int launch_tc_ingest(const Dev& d, const void* const* cols, int ncols, int split
                      cudaEvent_t* ev);
 int tc_smem_bytes();
 // Basis Gram of the new x target pool slots on tensor cores (FP32 pool); returns the
-// number of kernels launched, or -1.  part holds nblk x 256 x 128 floats.
+// number of kernels launched, or -1.  part holds nblk x 512 x 128 floats.
 int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st);
 void launch_materialize_omega(const Dev& d, cudaStream_t st);
 

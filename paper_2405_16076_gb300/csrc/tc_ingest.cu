@@ -605,6 +605,206 @@ __global__ void tc_gram_reduce_kernel(Dev d, const float* __restrict__ part, int
 
 // Gram of every (new, target) pool-slot pair, in tiles of 64 x 128.  The counts live on the
 // device, so every tile is launched for the largest possible counts and exits early.
+// Basis Gram of every new element against every target in one pass over the pool.  The
+// targets (new elements first) are staged per chunk as one B tile of 64-target blocks (64 hi
+// rows, then the 64 lo rows of the same targets); the A operand of the MMA is the 128-row
+// block holding new elements x0 .. x0+63, read from the same tile.  D[L][c] accumulates in
+// TMEM over this CTA's chunks; the reduction adds the split-K partials and the four
+// hi/lo products.  Requires ntgt <= 256 (2t <= 256).
+constexpr int kGramRowsMax = 512;            // 4 blocks x (64 hi + 64 lo) rows
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ part, int nstage) {
+  extern __shared__ uint8_t smem_raw[];
+  const int nnew = d.meta[META_NNEW], ntgt = d.meta[META_NTGT];
+  if (x0 >= nnew || ntgt <= 0) return;                  // uniform over the CTA, before any TMEM use
+  const int nbrows = 128 * ((ntgt + 63) / 64);            // B rows in use (multiple of 128, <= 512)
+  const uint32_t btile = (uint32_t)kGramRowsMax * 128u;
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t sB = base;
+  const uint32_t sBar = sB + (uint32_t)nstage * btile;  // full[4], empty[4], done
+  uint8_t* gbar = gbase + (sBar - base);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 96);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 104);
+  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 32, bar_done = sBar + 64;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
+  const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
+  int64_t c1 = c0 + chunks_per_cta;
+  if (c1 > nchunks) c1 = nchunks;
+  const int64_t nch = c1 > c0 ? c1 - c0 : 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nstage; ++i) {
+      mbar_init(bar_full0 + 8 * i, 32 * kProducerWarps);
+      mbar_init(bar_empty0 + 8 * i, 1);
+    }
+    mbar_init(bar_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 0) {
+    if (lane == 0) {
+      const int n1 = nbrows < 256 ? nbrows : 256, n2 = nbrows - n1;
+      const uint32_t id1 = idesc_bf16(128, n1);
+      const uint32_t id2 = idesc_bf16(128, n2 > 0 ? n2 : 16);
+      const uint32_t aoff = (uint32_t)(x0 / 64) * 128u * 128u;   // A = rows of the x0 block
+      int st = 0;
+      uint32_t par = 0;
+      for (int64_t c = 0; c < nch; ++c) {
+        if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err)) break;
+        tc_fence_after();
+        const uint32_t bst = sB + st * btile;
+        const uint64_t da = desc_sw128(bst + aoff);
+        const uint64_t db1 = desc_sw128(bst);
+        const uint64_t db2 = desc_sw128(bst + 256 * 128);
+#pragma unroll
+        for (int kk = 0; kk < kChunkK / 16; ++kk) {
+          const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t adv = (uint64_t)(kk * 2);
+          tc_mma(tmem, da + adv, db1 + adv, id1, acc);
+          if (n2 > 0) tc_mma(tmem + (uint32_t)n1, da + adv, db2 + adv, id2, acc);
+        }
+        tc_commit(bar_empty0 + 8 * st);
+        if (++st == nstage) { st = 0; par ^= 1u; }
+      }
+      tc_commit(bar_done);
+    }
+    __syncwarp();
+  } else {
+    // producer thread pt moves, for u = 0..3, coordinates 8g..8g+7 of target y = (pt + 512u) / 8
+    const int pt = threadIdx.x - 32;
+    const float* pool = (const float*)d.pool;
+    const int g = pt & 7;
+    const int y0t = pt >> 3;                              // target of round u: y0t + 64 u
+    int slot[4];                                          // pool slot, or -1 past the targets
+#pragma unroll
+    for (int u = 0; u < 4; ++u) slot[u] = (y0t + 64 * u < ntgt) ? d.gtgt[y0t + 64 * u] : -1;
+#define GSRC(u) (pool + (int64_t)slot[u] * d.m_pad)
+    float4 bufA[4][2], bufB[4][2];
+    auto load_chunk = [&](int64_t c, float4 (&v)[4][2]) {
+      if (c >= nch) return;
+      const int64_t i = (c0 + c) * kChunkK + 8 * g;        // < m_pad: the slot tail beyond m is zero
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (slot[u] < 0) continue;
+        const float4* s4 = reinterpret_cast<const float4*>(GSRC(u) + i);
+        v[u][0] = __ldcs(s4);
+        v[u][1] = __ldcs(s4 + 1);
+        if (g == 0 && c + kL2Ahead < nch) prefetch_l2(GSRC(u) + (c0 + c + kL2Ahead) * kChunkK, kChunkK * 4);
+      }
+    };
+    int pst = 0;
+    uint32_t ppar = 1u;
+    auto process = [&](const float4 (&v)[4][2]) -> bool {
+      const int st = pst;
+      if (!mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err)) return false;
+      if (++pst == nstage) { pst = 0; ppar ^= 1u; }
+      const uint32_t bst = sB + st * btile;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (slot[u] < 0) continue;
+        const int rhi = 128 * u + y0t;                    // hi row of target y0t + 64 u
+        const float x[8] = {v[u][0].x, v[u][0].y, v[u][0].z, v[u][0].w, v[u][1].x, v[u][1].y, v[u][1].z, v[u][1].w};
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+          const uint32_t hv = *reinterpret_cast<const uint32_t*>(&h2);
+          hw[j] = hv;
+          const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * j] - __uint_as_float(hv << 16),
+                                                          x[2 * j + 1] - __uint_as_float(hv & 0xFFFF0000u));
+          lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
+        }
+        sts128(bst + sw128_off(rhi, g), hw[0], hw[1], hw[2], hw[3]);
+        sts128(bst + sw128_off(rhi + 64, g), lw[0], lw[1], lw[2], lw[3]);
+      }
+      fence_async_smem();
+      mbar_arrive(bar_full0 + 8 * st);
+      return true;
+    };
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (slot[u] >= 0 && g == 0)
+        for (int64_t c = 2; c < kL2Ahead && c < nch; ++c) prefetch_l2(GSRC(u) + (c0 + c) * kChunkK, kChunkK * 4);
+    load_chunk(0, bufA);
+    load_chunk(1, bufB);
+    for (int64_t c = 0; c < nch; c += 2) {
+      if (!process(bufA)) break;
+      load_chunk(c + 2, bufA);
+      if (c + 1 < nch) {
+        if (!process(bufB)) break;
+        load_chunk(c + 3, bufB);
+      }
+    }
+#undef GSRC
+    if (warp <= 4) {
+      const bool ok = mbar_wait(bar_done, 0, abort_flag, d.err);
+      tc_fence_after();
+      if (ok && !*abort_flag) {
+        const int quarter = warp & 3;
+        const int L = 32 * quarter + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
+        for (int cb = 0; cb < nbrows; cb += 32) {
+          uint32_t r[32];
+          tc_ld32(taddr + (uint32_t)cb, r);
+          tc_wait_ld();
+          float* o = part + ((size_t)blockIdx.x * kGramRowsMax + cb) * 128 + L;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) o[(size_t)j * 128] = (nch > 0) ? __uint_as_float(r[j]) : 0.f;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// One CTA per target y, 256 threads: thread (j, x) adds the partials of blocks b = j (mod 4) in
+// order; the four sums are combined in the fixed order j = 0..3.  G(new x0 + x, target y).
+__global__ void __launch_bounds__(256) tc_gram_all_reduce_kernel(Dev d, const float* __restrict__ part, int nblk,
+                                                                 int x0) {
+  __shared__ double red[4][64];
+  const int nnew = d.meta[META_NNEW], ntgt = d.meta[META_NTGT];
+  const int y = blockIdx.x;
+  if (x0 >= nnew || y >= ntgt) return;
+  const int nx = min(64, nnew - x0);
+  const int x = threadIdx.x & 63, j = threadIdx.x >> 6;
+  const int chi = 128 * (y >> 6) + (y & 63), clo = chi + 64;
+  double v = 0.0;
+  if (x < nx) {
+    for (int b = j; b < nblk; b += 4) {
+      const float* p = part + (size_t)b * kGramRowsMax * 128;
+      v += (double)p[(size_t)chi * 128 + x] + (double)p[(size_t)clo * 128 + x] +
+           (double)p[(size_t)chi * 128 + 64 + x] + (double)p[(size_t)clo * 128 + 64 + x];
+    }
+  }
+  red[j][x] = v;
+  __syncthreads();
+  if (j != 0 || x >= nx) return;
+  const double g = ((red[0][x] + red[1][x]) + red[2][x]) + red[3][x];
+  const int np = d.npool;
+  const int a = d.gnew[x0 + x], bb = d.gtgt[y];
+  // target y < nnew is a new element: its pair with x0 + x is computed twice; the smaller
+  // new-element index writes it, so the stored Gram is symmetric and deterministic
+  if (y < nnew && x0 + x > y) return;
+  d.Gp[a + (size_t)bb * np] = g;
+  d.Gp[bb + (size_t)a * np] = g;
+}
+
 int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
@@ -616,6 +816,29 @@ int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st) {
   const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
   int64_t per = (nchunks + nblk - 1) / nblk;
   int nk = 0;
+  if (2 * d.t <= 256) {
+    // one pass over the targets per 64 new elements
+    static int max_smem = 0;
+    if (max_smem == 0) {
+      int dev = 0, v = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+          cudaFuncSetAttribute(tc_gram_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, v) != cudaSuccess)
+        return -1;
+      max_smem = v;
+    }
+    const int stage_bytes = kGramRowsMax * 128;
+    int nstage = (max_smem - 1024 - 128) / stage_bytes;
+    if (nstage > kMaxStages) nstage = kMaxStages;
+    if (nstage < 2) return -1;
+    const size_t smem = 1024 + 128 + (size_t)nstage * stage_bytes;
+    for (int x0 = 0; x0 < d.t; x0 += 64) {
+      tc_gram_all_kernel<<<nblk, kThreads, smem, st>>>(d, x0, per, part, nstage);
+      tc_gram_all_reduce_kernel<<<2 * d.t, 256, 0, st>>>(d, part, nblk, x0);
+      nk += 2;
+    }
+    return nk;
+  }
   for (int x0 = 0; x0 < d.t; x0 += 64)
     for (int y0 = 0; y0 < 2 * d.t; y0 += 128) {
       tc_gram_kernel<<<nblk, kGramThreads, kSmemBytes, st>>>(d, x0, y0, per, part);
