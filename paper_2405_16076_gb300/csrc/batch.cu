@@ -273,8 +273,10 @@ __global__ void gram_reduce_kernel(Dev d, int nsplit) {
 }
 
 // ---------------------------------------------------------------- gather + factorizations
-// Gather Omega A_J (scaled), the probe rows of the basis, G = A_J^T A_J and A_J^T A_Jprev from
-// the pool Gram, and the new-element columns for Algorithm 6 (grid-stride, many blocks).
+// Gather Omega A_J (scaled), the probe rows of the basis and the new-element columns for
+// Algorithm 6 (sketch side), or G = A_J^T A_J and A_J^T A_Jprev from the pool Gram (Gram side);
+// grid-stride, many blocks.
+template <bool kSketch>
 __global__ void gather_kernel(Dev d, WorkLayout w) {
   const int s = d.s, np = d.npool, hh = d.h1 + d.h2 + d.h3;
   const int na = d.meta[META_NACT], npa = d.meta[META_NPACT], nn = d.meta[META_NNEW];
@@ -287,6 +289,19 @@ __global__ void gather_kernel(Dev d, WorkLayout w) {
   double* QR4 = d.work + w.QR4;
   double* QR6 = d.work + w.QR6;
   const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+  if (!kSketch) {
+    for (int64_t idx = g0; idx < (int64_t)na * na; idx += gs) {
+      const int a = (int)(idx % na), b = (int)(idx / na);
+      const double g = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC[d.act[b]] * np];
+      G[a + (size_t)b * na] = g;
+      Gc[a + (size_t)b * na] = g;
+    }
+    for (int64_t idx = g0; idx < (int64_t)na * npa; idx += gs) {
+      const int a = (int)(idx % na), b = (int)(idx / na);
+      Gq[a + (size_t)b * na] = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC_prev[d.pact[b]] * np];
+    }
+    return;
+  }
   for (int64_t idx = g0; idx < (int64_t)s * na; idx += gs) {
     const int i = (int)(idx % s), a = (int)(idx / s);
     const double v = d.S[(size_t)d.JC[d.act[a]] * d.rows + i] * rs;
@@ -300,16 +315,6 @@ __global__ void gather_kernel(Dev d, WorkLayout w) {
   for (int64_t idx = g0; idx < (int64_t)hh * na; idx += gs) {
     const int r = (int)(idx % hh), a = (int)(idx / hh);
     HJ[r + (size_t)a * hh] = d.S[(size_t)d.JC[d.act[a]] * d.rows + d.hbase + r];
-  }
-  for (int64_t idx = g0; idx < (int64_t)na * na; idx += gs) {
-    const int a = (int)(idx % na), b = (int)(idx / na);
-    const double g = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC[d.act[b]] * np];
-    G[a + (size_t)b * na] = g;
-    Gc[a + (size_t)b * na] = g;
-  }
-  for (int64_t idx = g0; idx < (int64_t)na * npa; idx += gs) {
-    const int a = (int)(idx % na), b = (int)(idx / na);
-    Gq[a + (size_t)b * na] = d.Gp[d.slotC[d.act[a]] + (size_t)d.slotC_prev[d.pact[b]] * np];
   }
 }
 
@@ -749,7 +754,8 @@ int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st) {
 }
 
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
-                      cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select) {
+                      cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select, cudaStream_t stg,
+                      cudaEvent_t ev_fork, cudaEvent_t ev_gram) {
   const WorkLayout w = layout(d);
   const int64_t jd0 = n_obs - count;
   int nk = launch_scores(d, count, jd0, d.work, w.eigR, w.beta, w.vhead, w.ldld, w.ldll, w.vec,
@@ -768,28 +774,35 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
                                                                          stage_u ? 1 : 0, jd0);
   }
   if (ev_select) cudaEventRecord(ev_select, st);
+  // Gram side on stg (basis Gram, G, its Cholesky factor, T of Algorithm 7), sketch side
+  // (gather, Householder QRs) on st; they join before the coefficient kernel.
+  cudaEventRecord(ev_fork, st);
+  cudaStreamWaitEvent(stg, ev_fork, 0);
   int ngk = 2;
   if (d.dtype == 1 && d.tc_part) {
-    ngk = launch_tc_gram(d, d.tc_blocks, d.tg_part, st);
+    ngk = launch_tc_gram(d, d.tc_blocks, d.tg_part, stg);
     if (ngk < 0) return 0;
   } else {
     dim3 gg((d.t + 63) / 64, (2 * d.t + 63) / 64, d.gram_split);
-    if (d.dtype == 0) basis_gram_kernel<double><<<gg, 256, 0, st>>>(d);
-    else basis_gram_kernel<float><<<gg, 256, 0, st>>>(d);
-    gram_reduce_kernel<<<(d.t * 2 * d.t + 255) / 256, 256, 0, st>>>(d, d.gram_split);
+    if (d.dtype == 0) basis_gram_kernel<double><<<gg, 256, 0, stg>>>(d);
+    else basis_gram_kernel<float><<<gg, 256, 0, stg>>>(d);
+    gram_reduce_kernel<<<(d.t * 2 * d.t + 255) / 256, 256, 0, stg>>>(d, d.gram_split);
   }
-  gather_kernel<<<d.n_sm, 256, 0, st>>>(d, w);
-  if (!launch_qr_coop(d, d.work + w.QR4, d.work + w.b4, d.work + w.h4, d.work + w.r4, d.work + w.QR6,
-                      d.work + w.b6, d.work + w.h6, d.work + w.r6, d.gbar2, st))
-    return 0;
+  gather_kernel<false><<<d.n_sm, 256, 0, stg>>>(d, w);
   {
     static int staged = -1;
     if (staged < 0)
       staged = cudaFuncSetAttribute(gram_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kCholSmemBytes) == cudaSuccess ? 1 : 0;
-    gram_chol_kernel<<<1, 1024, staged ? kCholSmemBytes : 0, st>>>(d, w, staged);
+    gram_chol_kernel<<<1, 1024, staged ? kCholSmemBytes : 0, stg>>>(d, w, staged);
   }
-  tsolve_kernel<<<(d.t + 7) / 8, 256, 0, st>>>(d, w);
+  tsolve_kernel<<<(d.t + 7) / 8, 256, 0, stg>>>(d, w);
+  cudaEventRecord(ev_gram, stg);
+  gather_kernel<true><<<d.n_sm, 256, 0, st>>>(d, w);
+  if (!launch_qr_coop(d, d.work + w.QR4, d.work + w.b4, d.work + w.h4, d.work + w.r4, d.work + w.QR6,
+                      d.work + w.b6, d.work + w.h6, d.work + w.r6, d.gbar2, st))
+    return 0;
+  cudaStreamWaitEvent(st, ev_gram, 0);
   coeff_kernel<<<kApplyBlocks, kApplyThreads, 0, st>>>(d, w, n_obs, n_prev);
   const int nchunk = (int)((n_obs + kHutChunk - 1) / kHutChunk);
   hutch_partial_kernel<<<dim3(nchunk, 4), 256, 0, st>>>(d, w, n_obs);
@@ -803,7 +816,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   }
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
-  return nk + 12 + ngk;
+  return nk + 13 + ngk;
 }
 
 }  // namespace rid

@@ -23,6 +23,8 @@ struct rid_handle {
   cudaStream_t st;        // the caller's stream: ingest, and a snapshot of SS^T and ||A||^2 per batch
   cudaStream_t stl;       // the lambda stream: the lambda part of each batch step, from the snapshot
   cudaStream_t stb;       // the batch stream: the tail of each batch step (scores .. commit)
+  cudaStream_t stg;       // the tail's Gram side, forked from and joined to stb within a step
+  cudaEvent_t ev_fork, ev_gram;
   cudaEvent_t ev_snap;    // snapshot of the latest batch taken (stream st)
   cudaEvent_t ev_lambda[2];   // per batch parity, recorded on stl
   cudaEvent_t ev_scores[2], ev_select[2], ev_tail[2];   // per batch parity, recorded on stb
@@ -92,11 +94,13 @@ void free_all(Dev& d, void* staging) {
 void destroy_sync_objects(rid_handle* h) {
   if (h->stb) cudaStreamDestroy(h->stb);
   if (h->stl) cudaStreamDestroy(h->stl);
-  cudaEvent_t evs[] = {h->ev_snap, h->ev_lambda[0], h->ev_lambda[1], h->ev_scores[0], h->ev_scores[1],
+  if (h->stg) cudaStreamDestroy(h->stg);
+  cudaEvent_t evs[] = {h->ev_fork, h->ev_gram, h->ev_snap, h->ev_lambda[0], h->ev_lambda[1], h->ev_scores[0], h->ev_scores[1],
                        h->ev_select[0], h->ev_select[1], h->ev_tail[0], h->ev_tail[1]};
   for (cudaEvent_t e : evs) if (e) cudaEventDestroy(e);
   h->stb = nullptr;
   h->stl = nullptr;
+  h->stg = nullptr;
 }
 
 // The device view for batch b: its buffer-slot list and the next batch's.
@@ -188,7 +192,7 @@ int run_batch(rid_handle* h) {
   CK(cudaEventRecord(h->ev_lambda[b & 1], h->stl));
   CK(cudaStreamWaitEvent(h->stb, h->ev_lambda[b & 1], 0));
   const int nt = nl ? rid::launch_batch_tail(db, h->count, h->n_obs, h->n_prev, b, h->stb, h->ev_scores[b & 1],
-                                             h->ev_select[b & 1])
+                                             h->ev_select[b & 1], h->stg, h->ev_fork, h->ev_gram)
                     : 0;
   if (nl == 0 || nt == 0) {
     cudaGetLastError();
@@ -421,6 +425,9 @@ int rid_init(rid_handle** out, const rid_config* c) {
   d.dslot_nxt = d.dslot + t;
   if (cudaStreamCreateWithFlags(&h->stb, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->stl, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->stg, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_gram, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_lambda[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_lambda[1], cudaEventDisableTiming) != cudaSuccess ||
@@ -674,6 +681,7 @@ void rid_destroy(rid_handle* h) {
   cudaStreamSynchronize(h->st);
   if (h->stb) cudaStreamSynchronize(h->stb);
   if (h->stl) cudaStreamSynchronize(h->stl);
+  if (h->stg) cudaStreamSynchronize(h->stg);
   for (auto e : h->evpool) cudaEventDestroy(e);
   free_all(h->d, h->staging);
   if (h->tc_part) cudaFree(h->tc_part);

@@ -123,10 +123,13 @@ void launch_materialize_omega(const Dev& d, cudaStream_t st);
 // stream.  The tail (ridge scores, prune/refill, basis Gram, Algorithms 4-8, commit) runs on
 // the batch stream; ev_scores (may be null) is recorded after the scores, once the tail no
 // longer needs the lambda part's outputs, and ev_select (may be null) once the buffer slots of
-// the next-but-one batch are chosen.  Both return the number of kernels launched (0 on failure).
+// the next-but-one batch are chosen.  The tail's Gram side (basis Gram, G and its factor, T)
+// runs on stg between ev_fork and ev_gram, beside the sketch side's QRs on st.  Both return
+// the number of kernels launched (0 on failure).
 int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st);
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
-                      cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select);
+                      cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select, cudaStream_t stg,
+                      cudaEvent_t ev_fork, cudaEvent_t ev_gram);
 int launch_reset_state(const Dev& d, cudaStream_t st);
 
 // coop.cu: lambda (Eq. 23) through a tridiagonalization of the sketch Gram (cluster or
