@@ -259,7 +259,11 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
     float* dstp = has_col ? (float*)d.pool + (int64_t)d.dslot[count + q] * d.m_pad : nullptr;
     const int r0 = pt;                        // Omega row of this thread
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    // squared norm: compensated FP32 sum (Kahan) over 16 chunks, then folded into FP64 (this
+    // GPU issues about one FP64 instruction per warp per 64 cycles)
     double nrm = 0.0;
+    float ks = 0.f, kc = 0.f;
+    int kn = 0;
     uint32_t keep[2] = {0u, 0u};
     float4 bufA[2], bufB[2];
     // Loads run two chunks ahead in registers; one lane per column also asks L2 for the
@@ -304,7 +308,13 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
         float s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) s2 = fmaf(x[j], x[j], s2);
-        nrm += (double)s2;
+        {
+          const float y = s2 - kc;
+          const float tsum = ks + y;
+          kc = (tsum - ks) - y;
+          ks = tsum;
+          if (++kn == 16) { nrm += (double)ks - (double)kc; ks = 0.f; kc = 0.f; kn = 0; }
+        }
         // a = hi + lo with hi = bf16(a) and lo = bf16(a - hi), two coordinates per 32-bit word
         uint32_t hw[4], lw[4];
 #pragma unroll
@@ -357,6 +367,7 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
         load_chunk(c + 3, bufB);
       }
     }
+    nrm += (double)ks - (double)kc;
     // squared norms: the eight segment threads of a column are adjacent lanes
     nrm += __shfl_xor_sync(0xffffffffu, nrm, 1);
     nrm += __shfl_xor_sync(0xffffffffu, nrm, 2);
