@@ -259,11 +259,10 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
     float* dstp = has_col ? (float*)d.pool + (int64_t)d.dslot[count + q] * d.m_pad : nullptr;
     const int r0 = pt;                        // Omega row of this thread
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
-    // squared norm: compensated FP32 sum (Kahan) over 16 chunks, then folded into FP64 (this
-    // GPU issues about one FP64 instruction per warp per 64 cycles)
-    double nrm = 0.0;
+    // squared norm: compensated FP32 sum (Kahan) over this CTA's coordinates, converted to FP64
+    // at the end: its error stays at a few FP32 roundings of the total, and the loop issues no
+    // FP64 instruction (this GPU issues about one per warp per 64 cycles)
     float ks = 0.f, kc = 0.f;
-    int kn = 0;
     uint32_t keep[2] = {0u, 0u};
     float4 bufA[2], bufB[2];
     // Loads run two chunks ahead in registers; one lane per column also asks L2 for the
@@ -313,7 +312,6 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
           const float tsum = ks + y;
           kc = (tsum - ks) - y;
           ks = tsum;
-          if (++kn == 16) { nrm += (double)ks - (double)kc; ks = 0.f; kc = 0.f; kn = 0; }
         }
         // a = hi + lo with hi = bf16(a) and lo = bf16(a - hi), two coordinates per 32-bit word
         uint32_t hw[4], lw[4];
@@ -367,7 +365,7 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
         load_chunk(c + 3, bufB);
       }
     }
-    nrm += (double)ks - (double)kc;
+    double nrm = (double)ks - (double)kc;
     // squared norms: the eight segment threads of a column are adjacent lanes
     nrm += __shfl_xor_sync(0xffffffffu, nrm, 1);
     nrm += __shfl_xor_sync(0xffffffffu, nrm, 2);
