@@ -17,6 +17,7 @@ the same workload.  Under torchrun every rank runs its own independent stream
 (weak scaling, no collective on the data path).
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -264,11 +265,17 @@ def main():
     cols_per_launch = int(prof_kern[0] and (n * args.steps) / max(int(prof_grp[0]), 1))
     bytes_per_launch = 2.0 * cols_per_launch * m * 4    # read each column once + write it to its slot
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    # DRAM bytes per launch from the committed ncu counters, scaled by the columns and coordinates
+    # of a launch; null unless the counters were taken on this very kernel source
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "ingest_traffic.json")
-    if os.path.exists(tr_path):
+    src_path = os.path.join(ROOT, "paper_2405_16076_gb300", "csrc", "tc_ingest.cu")
+    if args.sketch != "native" and os.path.exists(tr_path):
         try:
-            traffic = json.load(open(tr_path)).get(args.config)
+            tr = json.load(open(tr_path))
+            src_hash = hashlib.sha256(open(src_path, "rb").read()).hexdigest()
+            if tr.get("tc_ingest_cu_sha256") == src_hash:
+                traffic = tr["dram_bytes_per_column_coordinate"] * cols_per_launch * m
         except Exception:
             traffic = None
     line = {
