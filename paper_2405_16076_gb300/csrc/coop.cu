@@ -652,8 +652,147 @@ qr_coop_kernel(Dev d, double* Q4, double* b4, double* h4, double* r4, double* Q6
   qr_coop(Q6, d.s, nn, b6, h6, r6, bar, sh);
 }
 
+// Householder QR of the m x n matrix A (column-major, lda = m), with the same outputs as
+// qr_coop, on one thread-block cluster: CTA r holds the columns l with l % C == r in shared
+// memory.  At step j every CTA reads column j (rows j..m-1) from its owner -- final since
+// step j-1, and never written again -- forms reflector j (scalars on one thread), and applies
+// it to its own columns l > j; one cluster barrier per step.  n is read on the device
+// (meta[n_item]); control flow is uniform over the cluster.
+__global__ void __launch_bounds__(kTriThreads, 1)
+qr_cluster_kernel(Dev d, double* A, int n_item, double* beta, double* vhead, double* rdiag, int ncl) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int m = d.s, n = d.meta[n_item];
+  if (n <= 0) return;                          // uniform over the cluster
+  const int ldc = m | 1;
+  extern __shared__ double qsm[];
+  double* cols = qsm;                          // ncl x ldc
+  double* x = cols + (size_t)ncl * ldc;        // column j, rows j..m-1
+  __shared__ double sh[33];
+  __shared__ double scal[2];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int nown = (n - rank + C - 1) / C;
+  for (int lc = wid; lc < nown; lc += nw) {
+    const double* src = A + (size_t)(lc * C + rank) * m;
+    for (int i = lane; i < m; i += 32) cols[(size_t)lc * ldc + i] = src[i];
+  }
+  cl.sync();
+  for (int j = 0; j < n; ++j) {
+    const int mj = m - j;
+    {
+      const double* src = cl.map_shared_rank(cols, j % C) + (size_t)(j / C) * ldc + j;
+      for (int i = tid; i < mj; i += blockDim.x) x[i] = src[i];
+    }
+    __syncthreads();
+    if (wid < kRedWarps) {
+      double part = 0.0;
+      for (int i = tid; i < mj; i += 32 * kRedWarps) part += x[i] * x[i];
+      part = warp_sum(part);
+      if (lane == 0) sh[wid] = part;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double nrm2 = 0.0;
+      for (int i = 0; i < kRedWarps; ++i) nrm2 += sh[i];
+      const double x0 = x[0];
+      const double nrm = sqrt(nrm2);
+      const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = nrm2 - x0 * x0 + v0 * v0;
+      const double bt = (nrm2 > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
+      scal[0] = bt;
+      scal[1] = v0;
+      if (rank == 0) { beta[j] = bt; vhead[j] = v0; rdiag[j] = (bt > 0.0) ? alpha : x0; }
+    }
+    __syncthreads();
+    const double bt = scal[0], v0 = scal[1];
+    if (bt > 0.0) {
+      const int lc0 = (j + 1 - rank + C - 1) / C;   // first owned column > j
+      for (int lc = lc0 + wid; lc < nown; lc += nw) {
+        double* a = cols + (size_t)lc * ldc;
+        double dot = (lane == 0) ? v0 * a[j] : 0.0;
+        for (int i = 1 + lane; i < mj; i += 32) dot += x[i] * a[j + i];
+        dot = warp_sum(dot);
+        const double f = bt * dot;
+        if (lane == 0) a[j] -= f * v0;
+        for (int i = 1 + lane; i < mj; i += 32) a[j + i] -= f * x[i];
+      }
+    }
+    cl.sync();                                  // column j+1 is final; x may be overwritten
+  }
+  for (int lc = wid; lc < nown; lc += nw) {
+    double* dst = A + (size_t)(lc * C + rank) * m;
+    for (int i = lane; i < m; i += 32) dst[i] = cols[(size_t)lc * ldc + i];
+  }
+  cl.sync();                                    // no CTA leaves while its shared memory may be read
+}
+
+// Cluster size for qr_cluster_kernel with up to t columns of length m (0: not available).
+int qr_cluster_size(int m, int t) {
+  static int cached_m = -1, cached_t = -1, cached_c = 0;
+  if (m == cached_m && t == cached_t) return cached_c;
+  int dev = 0, max_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  int best = 0;
+  if (cudaFuncGetAttributes(&fa, qr_cluster_kernel) == cudaSuccess) {
+    max_smem -= (int)fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) ==
+            cudaSuccess) {
+      for (int C : {16, 8}) {
+        const size_t smem = ((size_t)((t + C - 1) / C) * (m | 1) + m) * sizeof(double);
+        if (smem + 1024 > (size_t)max_smem) continue;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3(kTriThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, qr_cluster_kernel, &cfg) == cudaSuccess && nclusters > 0) {
+          best = C;
+          break;
+        }
+      }
+    }
+  }
+  cudaGetLastError();
+  cached_m = m;
+  cached_t = t;
+  cached_c = best;
+  return best;
+}
+
 int launch_qr_coop(const Dev& d, double* Q4, double* b4, double* h4, double* r4, double* Q6,
                    double* b6, double* h6, double* r6, unsigned int* bar_mem, cudaStream_t st) {
+  const int C = qr_cluster_size(d.s, d.t);
+  if (C > 0) {
+    // one small cluster: unlike the grid version it needs no co-residency of ~t CTAs, which
+    // the long-lived ingest CTAs running beside the batch step would delay
+    const int ncl = (d.t + C - 1) / C;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kTriThreads);
+    cfg.dynamicSmemBytes = ((size_t)ncl * (d.s | 1) + d.s) * sizeof(double);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, qr_cluster_kernel, d, Q4, (int)META_NACT, b4, h4, r4, ncl) != cudaSuccess) return 0;
+    if (cudaLaunchKernelEx(&cfg, qr_cluster_kernel, d, Q6, (int)META_NNEW, b6, h6, r6, ncl) != cudaSuccess) return 0;
+    return 1;
+  }
   int grid = d.n_sm < d.t ? d.n_sm : d.t;
   if (grid < 1) grid = 1;
   cudaMemsetAsync(bar_mem, 0, 4 * sizeof(unsigned int), st);

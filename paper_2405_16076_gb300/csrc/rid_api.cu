@@ -40,7 +40,8 @@ struct rid_handle {
   std::vector<const void*> pend;   // columns recorded but not yet sketched
   int group_max;
   bool tc;                // tensor-core ingest (FP32 data, BF16 / BF16x2 sketch)
-  int tc_blocks;
+  int tc_blocks;          // CTAs of the basis Gram (and the bound of the partial buffers)
+  int ingest_blocks;      // CTAs of the tensor-core ingest
   float* tc_part;
   double* tc_npart;
   std::string err;
@@ -238,7 +239,9 @@ int flush(rid_handle* h) {
   int nk0 = 0, nk1 = 0;
   if (h->tc) {
     const int split = h->cfg.sketch_prec == RID_SKETCH_BF16X2 ? 1 : 0;
-    if (rid::launch_tc_ingest(db, h->pend.data(), G, split, h->count, h->n_obs, h->tc_blocks,
+    // no batch step can run beside the first batch's ingest: it takes the whole grid
+    const int nblk = h->batch >= 1 ? h->ingest_blocks : h->tc_blocks;
+    if (rid::launch_tc_ingest(db, h->pend.data(), G, split, h->count, h->n_obs, nblk,
                               h->tc_part, h->tc_npart, h->st, h->prof ? ev : nullptr) != 0)
       return fail(h, RID_ECUDA, "tensor-core ingest launch failed");
     rid::launch_gram_update(db, G, h->n_obs, h->st);
@@ -368,7 +371,14 @@ int rid_init(rid_handle** out, const rid_config* c) {
     const int avail = h->n_sm >= 64 ? h->n_sm - 16 : h->n_sm;
     h->tc_blocks = (int)(want_blocks < avail ? want_blocks : avail);
     if (h->tc_blocks < 1) h->tc_blocks = 1;
+    // The ingest is off the critical path (it runs a batch ahead of the batch step), and each of
+    // its CTAs holds a whole SM for its chunk range: it leaves a third of the SMs to the batch
+    // step's kernels, which run beside it.
+    const int ingest_avail = h->n_sm >= 96 ? h->n_sm - h->n_sm / 3 : avail;
+    h->ingest_blocks = (int)(want_blocks < ingest_avail ? want_blocks : ingest_avail);
+    if (h->ingest_blocks < 1) h->ingest_blocks = 1;
   }
+  int prio_lo = 0, prio_hi = 0;
   int rc = RID_OK;
 #define AL(ptr, n) do { if (dalloc(&(ptr), (size_t)(n)) != cudaSuccess) { rc = RID_ENOMEM; goto fail_alloc; } } while (0)
   if (h->tc) {
@@ -423,9 +433,13 @@ int rid_init(rid_handle** out, const rid_config* c) {
   }
   h->dslot_buf = d.dslot;
   d.dslot_nxt = d.dslot + t;
-  if (cudaStreamCreateWithFlags(&h->stb, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->stl, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->stg, cudaStreamNonBlocking) != cudaSuccess ||
+  // The batch-step streams get the device's highest priority: their kernels are short and on
+  // the critical path, and each of the ingest's CTAs holds a whole SM for its chunk range, so
+  // freed SMs should go to them first.
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&h->stb, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&h->stl, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&h->stg, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_gram, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming) != cudaSuccess ||
