@@ -422,14 +422,16 @@ __global__ void __launch_bounds__(32) lambda_ldl_kernel(Dev d, const double* mu,
   }
   d.scal[SCAL_LAMBDA] = lam;
   d.scal[fro_slot] = d.fro2[0];         // the step's ||A_obs||^2: later ingest may add to fro2
+  // T + lambda I = L D L^T; ldl_d holds the inverse pivots 1/D_i (0 for a non-positive pivot)
   double del = sd[0] + lam;
-  ldl_d[0] = del;
   for (int i = 1; i < n; ++i) {
-    const double l = (del != 0.0) ? se[i - 1] / del : 0.0;
+    const double inv = (del != 0.0) ? 1.0 / del : 0.0;
+    ldl_d[i - 1] = (del > 0.0) ? inv : 0.0;
+    const double l = se[i - 1] * inv;
     ldl_l[i - 1] = l;
     del = sd[i] + lam - l * se[i - 1];
-    ldl_d[i] = del;
   }
+  ldl_d[n - 1] = (del > 0.0) ? 1.0 / del : 0.0;
 }
 
 // One warp per vector: occupied C slots (v < t) and buffered D columns (t <= v < t + count).
@@ -467,10 +469,10 @@ tri_scores_kernel(Dev d, const double* R, const double* beta, const double* vhea
     if (lane == 0) {
       // tau = y^T (L D L^T)^{-1} y = sum_i z_i^2 / D_i with L z = y
       double z = y[0];
-      double tau = (ldl_d[0] > 0.0) ? z * z / ldl_d[0] : 0.0;
+      double tau = z * z * ldl_d[0];            // ldl_d: inverse pivots, 0 where D_i <= 0
       for (int i = 1; i < n; ++i) {
         z = y[i] - ldl_l[i - 1] * z;
-        if (ldl_d[i] > 0.0) tau += z * z / ldl_d[i];
+        tau += z * z * ldl_d[i];
       }
       if (vi < d.t) d.tauC[vi] = tau; else d.tauD[vi - d.t] = tau;
     }
@@ -524,6 +526,127 @@ int tri_cluster_size(int n) {
   cached_n = n;
   cached_c = best;
   return best;
+}
+
+// The same scores with one 128-thread CTA per vector (n <= 512): thread t holds rows t + 128 q
+// (q < 4) of y in registers; each reflector costs one CTA reduction (warp sums added in a fixed
+// order) and the next reflector's entries are loaded while the current one is applied.  Then
+// z = L^{-1} y is a first-order linear recurrence, solved as a scan of affine maps over
+// contiguous 4-row segments, and tau = sum_i z_i^2 / D_i.
+constexpr int kScThreads = 128, kScRows = 4;
+
+__global__ void __launch_bounds__(kScThreads)
+tri_scores_cta_kernel(Dev d, const double* __restrict__ R, const double* __restrict__ beta,
+                      const double* __restrict__ vhead, const double* __restrict__ inv_d,
+                      const double* __restrict__ ldl_l, int count, int64_t jd0) {
+  __shared__ double red[kScThreads / 32];
+  __shared__ double fsh;
+  __shared__ double ys[kScThreads * kScRows];
+  __shared__ double wa[kScThreads / 32], wb[kScThreads / 32], wz[kScThreads / 32];
+  const int vi = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = d.s;
+  int64_t col;
+  if (vi < d.t) {
+    col = d.JC[vi];
+    if (col < 0) { if (tid == 0) d.tauC[vi] = 1.0; return; }   // uniform over the CTA
+  } else {
+    col = jd0 + (vi - d.t);                 // buffered column q of the batch is jd0 + q
+  }
+  const double rs = 1.0 / sqrt((double)n);
+  const double* l = d.Slev + (size_t)col * d.lev_ld;
+  double y[kScRows], un[kScRows];
+#pragma unroll
+  for (int q = 0; q < kScRows; ++q) {
+    const int r = tid + kScThreads * q;
+    y[q] = (r < n) ? l[r] * rs : 0.0;
+  }
+  auto load_u = [&](int k) {
+#pragma unroll
+    for (int q = 0; q < kScRows; ++q) {
+      const int r = tid + kScThreads * q;
+      un[q] = (r >= k + 2 && r < n) ? R[(size_t)r + (size_t)k * n] : 0.0;
+    }
+  };
+  double bn = 0.0, vn = 0.0;
+  if (n > 2) { load_u(0); bn = beta[0]; vn = vhead[0]; }
+  for (int k = 0; k + 2 < n; ++k) {          // y <- H_{n-3} ... H_0 y
+    double u[kScRows];
+#pragma unroll
+    for (int q = 0; q < kScRows; ++q) u[q] = un[q];
+    const double bt = bn, vh = vn;
+    if (k + 3 < n) { load_u(k + 1); bn = beta[k + 1]; vn = vhead[k + 1]; }
+    if (bt == 0.0) continue;                 // uniform
+    double dot = 0.0;
+#pragma unroll
+    for (int q = 0; q < kScRows; ++q) {
+      const int r = tid + kScThreads * q;
+      dot = fma(u[q], y[q], dot);
+      if (r == k + 1) dot = fma(vh, y[q], dot);
+    }
+    dot = warp_sum(dot);
+    if (lane == 0) red[wid] = dot;
+    __syncthreads();
+    if (tid == 0) fsh = bt * ((red[0] + red[1]) + (red[2] + red[3]));
+    __syncthreads();
+    const double f = fsh;
+#pragma unroll
+    for (int q = 0; q < kScRows; ++q) {
+      const int r = tid + kScThreads * q;
+      y[q] = fma(-f, u[q], y[q]);
+      if (r == k + 1) y[q] = fma(-f, vh, y[q]);
+    }
+  }
+  // L z = y: z_0 = y_0, z_i = y_i - l_{i-1} z_{i-1}; thread t takes rows 4t .. 4t+3
+#pragma unroll
+  for (int q = 0; q < kScRows; ++q) ys[tid + kScThreads * q] = y[q];
+  __syncthreads();
+  const int r0 = kScRows * tid;
+  double A = 1.0, B = 0.0;                   // z_out = A z_in + B over this segment
+#pragma unroll
+  for (int q = 0; q < kScRows; ++q) {
+    const int r = r0 + q;
+    if (r < n) {
+      const double a = (r == 0) ? 0.0 : -ldl_l[r - 1];
+      B = fma(a, B, ys[r]);
+      A = a * A;
+    }
+  }
+  // inclusive scan of the maps over the lanes (earlier lanes applied first)
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double Ap = __shfl_up_sync(0xffffffffu, A, o), Bp = __shfl_up_sync(0xffffffffu, B, o);
+    if (lane >= o) { B = fma(A, Bp, B); A = A * Ap; }
+  }
+  if (lane == 31) { wa[wid] = A; wb[wid] = B; }
+  __syncthreads();
+  if (tid == 0) {
+    double z = 0.0;                           // z entering warp 0 (none before row 0)
+    for (int w = 0; w < kScThreads / 32; ++w) { wz[w] = z; z = fma(wa[w], z, wb[w]); }
+  }
+  __syncthreads();
+  // exclusive prefix of this lane = inclusive prefix of the previous lane
+  double Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+  if (lane == 0) { Ae = 1.0; Be = 0.0; }
+  double z = fma(Ae, wz[wid], Be);          // z_{r0 - 1}
+  double tau = 0.0;
+#pragma unroll
+  for (int q = 0; q < kScRows; ++q) {
+    const int r = r0 + q;
+    if (r < n) {
+      const double a = (r == 0) ? 0.0 : -ldl_l[r - 1];
+      z = fma(a, z, ys[r]);
+      tau = fma(z * z, inv_d[r], tau);
+    }
+  }
+  tau = warp_sum(tau);
+  __syncthreads();
+  if (lane == 0) red[wid] = tau;
+  __syncthreads();
+  if (tid == 0) {
+    const double tt = (red[0] + red[1]) + (red[2] + red[3]);
+    if (vi < d.t) d.tauC[vi] = tt; else d.tauD[vi - d.t] = tt;
+  }
 }
 
 // Tridiagonalization, top-k eigenvalues and lambda / LDL^T; returns the number of kernels
@@ -595,6 +718,12 @@ int launch_scores(const Dev& d, int count, int64_t jd0, double* work_base, int64
                   int64_t off_vhead, int64_t off_ldld, int64_t off_ldll, int64_t off_vec, int vstride,
                   cudaStream_t st) {
   const int nvec = d.t + count;
+  if (d.s <= kScThreads * kScRows) {
+    tri_scores_cta_kernel<<<nvec, kScThreads, 0, st>>>(d, work_base + off_R, work_base + off_beta,
+                                                      work_base + off_vhead, work_base + off_ldld,
+                                                      work_base + off_ldll, count, jd0);
+    return 1;
+  }
   tri_scores_kernel<<<nvec, 32, 0, st>>>(d, work_base + off_R, work_base + off_beta, work_base + off_vhead,
                                          work_base + off_ldld, work_base + off_ldll, work_base + off_vec,
                                          vstride, count, jd0);
