@@ -93,7 +93,14 @@ int rid_config_default(rid_config* cfg);
 /* Validate *cfg and allocate the device state (Algorithm 3, initialisation).
  * On success *out receives a new handle.  Errors: RID_EINVAL (sizes: m >= 1,
  * 1 <= k <= 1024, k < s <= 4096, 0 <= h <= 1024, h == 0 or h >= 3,
- * 0 < c1 < c2, c1 + c2 < 1, unknown enum values), RID_ENOMEM, RID_ENOLIB. */
+ * 0 < c1 < c2, c1 + c2 < 1, unknown enum values; gradient mode: grad_dims
+ * must be 0 or 2, and with 2: nx, ny >= 2, nfields >= 1, m = nx ny nfields,
+ * sketch_prec NATIVE), RID_ENOMEM, RID_ENOLIB.
+ * Gradient mode (Sec. 3.4, Eqs. 38-43): the ridge scores and lambda use the
+ * sketch of [a; G a], i.e. Omega a + Omega_g (G a) with an independent Omega_g
+ * (s x 2m), and ||a||^2 + ||G a||^2; G is the least-squares gradient on each
+ * field's nx x ny grid graph (central differences inside, one-sided at the
+ * boundary, unit spacing). */
 int rid_init(rid_handle** out, const rid_config* cfg);
 
 /* Ingest ncols >= 0 columns (Algorithm 3, the loop body for each column):

@@ -179,6 +179,146 @@ __global__ void materialize_omega_kernel(Dev d) {
   }
 }
 
+// ---------------------------------------------------------------- gradient mode (Sec. 3.4)
+// Entry j = p * m + i of G a (Eq. 42) for component p (0: along x, the fastest axis; 1: along
+// y) at coordinate i of field f = i / (nx ny): the least-squares gradient of Eqs. 39-43 on the
+// grid graph, i.e. the central difference along axis p where both axis neighbours exist and
+// the one-sided difference at the boundary (spacing 1; fields independent).
+template <typename T>
+__device__ __forceinline__ double grad_entry(const T* a, int64_t j, int64_t m, int nx, int ny) {
+  const int p = (int)(j / m);
+  const int64_t i = j - (int64_t)p * m;
+  const int64_t ql = i % ((int64_t)nx * ny);
+  const int c = p == 0 ? (int)(ql % nx) : (int)(ql / nx);
+  const int len = p == 0 ? nx : ny;
+  const int64_t st = p == 0 ? 1 : nx;
+  if (c == 0) return (double)a[i + st] - (double)a[i];
+  if (c == len - 1) return (double)a[i] - (double)a[i - st];
+  return 0.5 * ((double)a[i + st] - (double)a[i - st]);
+}
+
+// Omega_g (G a_q) for the s leverage rows and ||G a_q||^2, split-K over the d m gradient
+// entries like the ingest sketch: grid (n_sketch_blocks, ceil(s / 256)), 256 threads, thread
+// tid of row group y owns row r = 256 y + tid; partials to d.spart / d.npart.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kSketchThreads)
+grad_sketch_kernel(Dev d, SimtCols cols, int nb) {
+  __shared__ double X[NB][kChunk];
+  __shared__ double red[kSketchThreads / 32][NB];
+  const int tid = threadIdx.x;
+  const int r = blockIdx.y * kSketchThreads + tid;
+  const bool row_ok = r < d.s;
+  const bool lead = blockIdx.y == 0;
+  const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+  const int64_t dm = 2 * d.m;
+  double acc[NB], nrm[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) { acc[q] = 0.0; nrm[q] = 0.0; }
+  const int64_t nchunks = (dm + kChunk - 1) / kChunk;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int64_t j0 = c * kChunk;
+    const int64_t j = j0 + tid;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      if (q < nb) {
+        const double g = (j < dm) ? grad_entry((const T*)cols.p[q], j, d.m, d.nx, d.ny) : 0.0;
+        X[q][tid] = g;
+        nrm[q] += g * g;
+      }
+    }
+    __syncthreads();
+    if (row_ok) {
+      if (d.omega_kind == 1) {
+#pragma unroll 1
+        for (int half = 0; half < kChunk / 128; ++half) {
+          const u32x4 w = philox4x32_10((uint32_t)((j0 >> 7) + half), (uint32_t)r, kTagGradRademacher, 0, k0, k1);
+          const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int wi = 0; wi < 4; ++wi) {
+#pragma unroll 8
+            for (int e = 0; e < 32; ++e) {
+              const int bpos = (e & 1) ? 31 - (e >> 1) : 15 - (e >> 1);
+              const uint32_t bit = (words[wi] >> bpos) & 1u;
+              const int ii = half * 128 + wi * 32 + e;
+#pragma unroll
+              for (int q = 0; q < NB; ++q)
+                if (q < nb) acc[q] += flip_sign(X[q][ii], bit);
+            }
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int ii = 0; ii < kChunk; ++ii) {
+          if (j0 + ii >= dm) break;
+          const double w = gauss_entry(d.seed, kTagGradGauss, (uint32_t)r, (uint64_t)(j0 + ii));
+#pragma unroll
+          for (int q = 0; q < NB; ++q)
+            if (q < nb) acc[q] += w * X[q][ii];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (row_ok) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (q < nb) d.spart[((size_t)blockIdx.x * nb + q) * d.rows + r] = acc[q];
+  }
+  if (lead) {
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      double v = nrm[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid][q] = v;
+    }
+    __syncthreads();
+    if (tid < nb) {
+      double v = 0.0;
+      for (int w = 0; w < kSketchThreads / 32; ++w) v += red[w][tid];
+      d.npart[(size_t)blockIdx.x * nb + tid] = v;
+    }
+  }
+}
+
+// Leverage sketch column n_obs + q: the s left rows of Omega a_q plus Omega_g (G a_q), and
+// ||G a_q||^2 added to the leverage norm, in column order.
+__global__ void grad_reduce_kernel(Dev d, int nb, int64_t n_obs, int nblk) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < nb * d.s) {
+    const int q = idx / d.s, r = idx % d.s;
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += d.spart[((size_t)b * nb + q) * d.rows + r];
+    d.Slev[(size_t)(n_obs + q) * d.lev_ld + r] = d.S[(size_t)(n_obs + q) * d.rows + r] + v;
+  }
+  if (idx == 0) {
+    for (int q = 0; q < nb; ++q) {
+      double v = 0.0;
+      for (int b = 0; b < nblk; ++b) v += d.npart[(size_t)b * nb + q];
+      if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
+      d.fro2[1] += v;
+    }
+  }
+}
+
+int launch_grad(const Dev& d, const void* const* colp, int nb, int64_t n_obs, cudaStream_t st) {
+  SimtCols cols;
+  for (int q = 0; q < kMaxB; ++q) cols.p[q] = q < nb ? colp[q] : nullptr;
+  const int64_t nchunks = (2 * d.m + kChunk - 1) / kChunk;
+  const int nblk = (int)(nchunks < d.n_sketch_blocks ? nchunks : d.n_sketch_blocks);
+  dim3 grid(nblk, (d.s + kSketchThreads - 1) / kSketchThreads);
+  if (d.dtype == 0) {
+    if (nb == 1) grad_sketch_kernel<double, 1><<<grid, kSketchThreads, 0, st>>>(d, cols, nb);
+    else grad_sketch_kernel<double, kMaxB><<<grid, kSketchThreads, 0, st>>>(d, cols, nb);
+  } else {
+    if (nb == 1) grad_sketch_kernel<float, 1><<<grid, kSketchThreads, 0, st>>>(d, cols, nb);
+    else grad_sketch_kernel<float, kMaxB><<<grid, kSketchThreads, 0, st>>>(d, cols, nb);
+  }
+  const int n = nb * d.s;
+  grad_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, nb, n_obs, nblk);
+  return 2;
+}
+
 void launch_materialize_omega(const Dev& d, cudaStream_t st) {
   materialize_omega_kernel<<<4 * 152, 256, 0, st>>>(d);
 }

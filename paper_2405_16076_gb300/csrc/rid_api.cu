@@ -252,6 +252,7 @@ int flush(rid_handle* h) {
       const int nb = G - q0 < rid::kMaxB ? G - q0 : rid::kMaxB;
       cudaEvent_t* e = (h->prof && q0 == 0) ? ev : nullptr;
       nk1 += rid::launch_ingest(db, h->pend.data() + q0, nb, h->count + q0, h->n_obs + q0, h->st, e) - 1;
+      if (db.grad) nk1 += rid::launch_grad(db, h->pend.data() + q0, nb, h->n_obs + q0, h->st);
       rid::launch_gram_update(db, nb, h->n_obs + q0, h->st);
       nk0 += 1;
       nk1 += 1;
@@ -320,7 +321,14 @@ int rid_init(rid_handle** out, const rid_config* c) {
     if (c->s + c->h > 512) return fail(h, RID_EINVAL, "BF16 sketches support s + h <= 512");
   }
   if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
-  if (c->grad_dims != 0) return fail(h, RID_EINVAL, "this build supports grad_dims = 0");
+  if (c->grad_dims != 0) {
+    if (c->grad_dims != 2) return fail(h, RID_EINVAL, "grad_dims must be 0 or 2 (2-D grids)");
+    if (c->nx < 2 || c->ny < 2 || c->nfields < 1)
+      return fail(h, RID_EINVAL, "gradient mode needs nx >= 2, ny >= 2, nfields >= 1");
+    if ((int64_t)c->nx * c->ny * c->nfields != c->m) return fail(h, RID_EINVAL, "gradient mode needs m = nx ny nfields");
+    if (c->sketch_prec != RID_SKETCH_NATIVE)
+      return fail(h, RID_EINVAL, "gradient mode runs the native-precision sketch (sketch_prec NATIVE)");
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -355,8 +363,11 @@ int rid_init(rid_handle** out, const rid_config* c) {
   const double k = (double)c->k;
   d.refill_scale = c->c_const * (k * log(k) + k * log(1.0 / c->delta) / c->eps) / (double)c->k;
   d.seed = c->seed;
-  d.grad = 0;
-  d.lev_ld = d.rows;
+  d.grad = c->grad_dims != 0 ? 1 : 0;
+  d.nx = c->nx;
+  d.ny = c->ny;
+  d.nfields = c->nfields;
+  d.lev_ld = d.grad ? d.s : d.rows;     // gradient mode: a separate s x n leverage sketch
   const int64_t nchunks = (d.m + rid::kChunk - 1) / rid::kChunk;
   d.n_sketch_blocks = (int)(nchunks < 4 * h->n_sm ? nchunks : 4 * h->n_sm);
   int64_t gs = (d.m + 16383) / 16384;

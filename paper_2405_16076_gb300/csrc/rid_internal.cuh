@@ -103,6 +103,9 @@ constexpr int kMaxGroup = 64;      // columns per tensor-core ingest launch
 // before the sketch kernel, after it, and after the reductions.
 int launch_ingest(const Dev& d, const void* const* cols, int nb, int count, int64_t n_obs,
                   cudaStream_t st, cudaEvent_t* ev);
+// Gradient mode (Sec. 3.4): the leverage sketch of nb columns given by pointer, after their
+// sketch has been reduced; returns the number of kernels launched.
+int launch_grad(const Dev& d, const void* const* cols, int nb, int64_t n_obs, cudaStream_t st);
 // SS^T update for nb new columns (shared by both ingest paths).
 void launch_gram_update(const Dev& d, int nb, int64_t n_obs, cudaStream_t st);
 

@@ -112,7 +112,8 @@ class OnlineRID:
 
     def __init__(self, m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
                  lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
-                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False):
+                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
+                 grad_dims=0, nx=0, ny=0, nfields=1):
         cfg = rid_config()
         _check(rid_config_default(ctypes.byref(cfg)))
         cfg.m, cfg.k, cfg.s, cfg.h = int(m), int(k), int(s), int(h)
@@ -126,6 +127,7 @@ class OnlineRID:
         cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         cfg.group_max = int(group_max)
         cfg.defer_device_input = 1 if defer else 0
+        cfg.grad_dims, cfg.nx, cfg.ny, cfg.nfields = int(grad_dims), int(nx), int(ny), int(nfields)
         cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         self.cfg = cfg
         self.t = int(k)
