@@ -121,6 +121,18 @@ int rid_init(rid_handle** out, const rid_config* cfg);
  * RID_ESTATE (after rid_finalize), RID_ECUDA. */
 int rid_ingest(rid_handle* h, const void* cols, int64_t ld, int32_t ncols, int32_t on_device);
 
+/* Ingest into several independent streams in one call (configuration C5:
+ * many small streams): for i < nh, ncols[i] columns for handle hs[i], given
+ * as in rid_ingest by cols[i] (leading dimension ld[i]).  Equivalent to nh
+ * rid_ingest calls, enqueued in order i = 0, 1, ...; every handle runs on its
+ * own streams, so handles created with distinct cuda_stream values proceed
+ * concurrently on the device.  Stops at the first failing handle and returns
+ * its status (its message in rid_last_error of that handle); handles before it
+ * have ingested their columns.  Errors: RID_EINVAL (NULL arrays, nh < 0, a
+ * NULL handle), and those of rid_ingest. */
+int rid_batch_ingest(rid_handle* const* hs, int32_t nh, const void* const* cols, const int64_t* ld,
+                     const int32_t* ncols, int32_t on_device);
+
 /* End the stream: run the batch step over the count < t buffered columns, if
  * any (tail batch).  Then, if J_out != NULL, write the t basis indices
  * (int64, -1 = empty slot) and, if P_out != NULL, the t x n coefficient matrix

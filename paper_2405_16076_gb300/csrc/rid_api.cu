@@ -515,6 +515,18 @@ int rid_ingest(rid_handle* h, const void* cols, int64_t ld, int32_t ncols, int32
   return RID_OK;
 }
 
+int rid_batch_ingest(rid_handle* const* hs, int32_t nh, const void* const* cols, const int64_t* ld,
+                     const int32_t* ncols, int32_t on_device) {
+  if (nh < 0 || (nh > 0 && (!hs || !cols || !ld || !ncols))) return fail(nullptr, RID_EINVAL, "rid_batch_ingest: NULL array or nh < 0");
+  for (int32_t i = 0; i < nh; ++i)
+    if (!hs[i]) return fail(nullptr, RID_EINVAL, "rid_batch_ingest: NULL handle");
+  for (int32_t i = 0; i < nh; ++i) {
+    const int rc = rid_ingest(hs[i], cols[i], ld[i], ncols[i], on_device);
+    if (rc != RID_OK) return rc;
+  }
+  return RID_OK;
+}
+
 int rid_finalize(rid_handle* h, int64_t* J_out, double* P_out, int64_t ldp, int32_t on_device) {
   if (!h) return RID_EINVAL;
   const int t = h->d.t;

@@ -64,6 +64,7 @@ def _load():
         "rid_reset": (ctypes.c_int, [H]),
         "rid_last_error": (ctypes.c_char_p, [H]),
         "rid_destroy": (None, [H]),
+        "rid_batch_ingest": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, ctypes.c_int32]),
         "rid_sketch_noalloc": (ctypes.c_int, [ctypes.POINTER(rid_config), P, ctypes.c_int64, ctypes.c_int32,
                                               P, ctypes.c_int64, P]),
     }
@@ -91,6 +92,29 @@ rid_reset = lib.rid_reset
 rid_last_error = lib.rid_last_error
 rid_destroy = lib.rid_destroy
 rid_sketch_noalloc = lib.rid_sketch_noalloc
+rid_batch_ingest = lib.rid_batch_ingest
+
+
+def batch_ingest(handles, blocks):
+    """rid_batch_ingest: blocks[i] (b_i x m_i rows = columns, torch on the GPU or numpy on the
+    host, all on the same side) into handles[i] (OnlineRID objects), in one call."""
+    nh = len(handles)
+    if nh == 0:
+        return
+    on_dev = hasattr(blocks[0], "data_ptr") and bool(blocks[0].is_cuda)
+    arrs = [b if on_dev else np.ascontiguousarray(b, dtype=hd.np_dtype) for hd, b in zip(handles, blocks)]
+    hs = (ctypes.c_void_p * nh)(*[hd.h.value for hd in handles])
+    cols = (ctypes.c_void_p * nh)(*[(a.data_ptr() if on_dev else a.ctypes.data) for a in arrs])
+    ld = (ctypes.c_int64 * nh)(*[hd.m for hd in handles])
+    nc = (ctypes.c_int32 * nh)(*[int(a.shape[0]) for a in arrs])
+    rc = rid_batch_ingest(hs, nh, cols, ld, nc, 1 if on_dev else 0)
+    if rc != RID_OK:
+        msg = None
+        for hd in handles:
+            m = rid_last_error(hd.h)
+            if m:
+                msg = m
+        raise RIDError(rc, (msg or rid_last_error(None) or b"").decode())
 
 
 def _check(rc, h=None):
