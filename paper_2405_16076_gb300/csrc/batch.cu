@@ -22,6 +22,7 @@ struct WorkLayout {
   int64_t vec;                            // per-warp vectors (scores / applies)
   int64_t SJ, HJ, G, Gq, Gc, T;           // gathered sketch data and Grams
   int64_t QR4, b4, h4, r4, QR6, b6, h6, r6;   // Householder factors (r: diagonal of R)
+  int64_t Lcinv, r4inv, r6inv;            // reciprocal diagonals of the triangular factors
   int64_t Z, trgpp, hut, hut_stride;      // Hutch++
   int64_t total;
 };
@@ -52,6 +53,7 @@ static WorkLayout layout(const Dev& d) {
   w.Gc = take(t * t); w.T = take(t * t);
   w.QR4 = take(s * t); w.b4 = take(t); w.h4 = take(t); w.r4 = take(t);
   w.QR6 = take(s * t); w.b6 = take(t); w.h6 = take(t); w.r6 = take(t);
+  w.Lcinv = take(t); w.r4inv = take(t); w.r6inv = take(t);
   w.Z = take(4 * hh * t); w.trgpp = take(4);
   w.hut_stride = hut_stride(d);
   w.hut = take(4 * w.hut_stride);
@@ -342,8 +344,39 @@ __global__ void __launch_bounds__(1024) gram_chol_kernel(Dev d, WorkLayout w, in
   }
   __syncthreads();
   cta_cholesky(A, na, na, 1e-13 * gm, &fail);
+  double* linv = d.work + w.Lcinv;
+  for (int a = threadIdx.x; a < na; a += blockDim.x) {
+    const double ljj = A[a + (size_t)a * na];
+    linv[a] = (ljj != 0.0) ? 1.0 / ljj : 0.0;
+  }
   if (use_smem)
     for (int i = threadIdx.x; i < na * na; i += blockDim.x) Gc[i] = gsm[i];
+}
+
+// Reciprocal diagonals of the two QR factors, with the rank tolerance of each:
+// |R_jj| <= max(s, n) eps max|R_ii| gives 0 (the component is dropped).
+__global__ void __launch_bounds__(256) qr_prep_kernel(Dev d, WorkLayout w) {
+  __shared__ double sm[2][8];
+  const int na = d.meta[META_NACT], nn = d.meta[META_NNEW], s = d.s;
+  const double* r4 = d.work + w.r4;
+  const double* r6 = d.work + w.r6;
+  double m4 = 0.0, m6 = 0.0;
+  for (int a = threadIdx.x; a < na; a += blockDim.x) m4 = fmax(m4, fabs(r4[a]));
+  for (int c = threadIdx.x; c < nn; c += blockDim.x) m6 = fmax(m6, fabs(r6[c]));
+  for (int o = 16; o > 0; o >>= 1) {
+    m4 = fmax(m4, __shfl_xor_sync(0xffffffffu, m4, o));
+    m6 = fmax(m6, __shfl_xor_sync(0xffffffffu, m6, o));
+  }
+  if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = m4; sm[1][threadIdx.x >> 5] = m6; }
+  __syncthreads();
+  m4 = 0.0; m6 = 0.0;
+  for (int i = 0; i < 8; ++i) { m4 = fmax(m4, sm[0][i]); m6 = fmax(m6, sm[1][i]); }
+  const double tol4 = (double)(s > na ? s : na) * 2.220446049250313e-16 * m4;
+  const double tol6 = (double)(s > nn ? s : nn) * 2.220446049250313e-16 * m6;
+  for (int a = threadIdx.x; a < na; a += blockDim.x)
+    d.work[w.r4inv + a] = (fabs(r4[a]) > tol4) ? 1.0 / r4[a] : 0.0;
+  for (int c = threadIdx.x; c < nn; c += blockDim.x)
+    d.work[w.r6inv + c] = (fabs(r6[c]) > tol6) ? 1.0 / r6[c] : 0.0;
 }
 
 // T = G^{-1} Gq, one warp per column (Algorithm 7 through the Gram:
@@ -360,8 +393,8 @@ __global__ void tsolve_kernel(Dev d, WorkLayout w) {
     double* x = T + (size_t)b * na;
     for (int a = lane; a < na; a += 32) x[a] = Gq[a + (size_t)b * na];
     __syncwarp();
-    warp_trsv_lower(Gc, na, na, x);
-    warp_trsv_lower_t(Gc, na, na, x);
+    warp_trsv_lower_r(Gc, d.work + w.Lcinv, na, na, x);
+    warp_trsv_lower_t_r(Gc, d.work + w.Lcinv, na, na, x);
   }
 }
 
@@ -384,23 +417,18 @@ __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout 
   double* P5 = d.cand + (size_t)t * d.n_cap;
   double* P6 = d.cand + 2 * (size_t)t * d.n_cap;
   double* P7 = d.cand + 3 * (size_t)t * d.n_cap;
-  // rank tolerance of R: max(s, na) * eps * |largest diagonal|
-  double rmax = 0.0;
-  const double* r4 = d.work + w.r4;
-  const double* r6 = d.work + w.r6;
-  for (int a = 0; a < na; ++a) rmax = fmax(rmax, fabs(r4[a]));
-  const double tol4 = (double)(s > na ? s : na) * 2.220446049250313e-16 * rmax;
+  // reciprocal diagonals (0 below the rank tolerance) from qr_prep_kernel and gram_chol_kernel
+  const double* r4inv = d.work + w.r4inv;
+  const double* r6inv = d.work + w.r6inv;
+  const double* lcinv = d.work + w.Lcinv;
   const int nn = d.meta[META_NNEW];
-  double rmax6 = 0.0;
-  for (int c = 0; c < nn; ++c) rmax6 = fmax(rmax6, fabs(r6[c]));
-  const double tol6 = (double)(s > nn ? s : nn) * 2.220446049250313e-16 * rmax6;
   for (int64_t j = gw; j < n_obs; j += nwarps) {
     const double* sa = d.S + (size_t)j * d.rows;
     // Algorithm 4 (Eq. 24): P4(:, j) = (Omega A_J)^+ Omega a_j via Householder QR
     for (int i = lane; i < s; i += 32) b[i] = sa[i] * rs;
     __syncwarp();
     warp_apply_qt(QR4, s, na, s, d.work + w.b4, d.work + w.h4, b);
-    warp_trsv_upper_d(QR4, r4, na, s, b, tol4);
+    warp_trsv_upper_r(QR4, r4inv, na, s, b);
     for (int a = lane; a < na; a += 32) P4[a + (size_t)j * t] = b[a];
     __syncwarp();
     // Algorithm 5: P5(:, j) = G^{-1} (Omega A_J)^T Omega a_j
@@ -411,8 +439,8 @@ __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout 
       if (lane == 0) b[a] = acc;
     }
     __syncwarp();
-    warp_trsv_lower(Gc, na, na, b);
-    warp_trsv_lower_t(Gc, na, na, b);
+    warp_trsv_lower_r(Gc, lcinv, na, na, b);
+    warp_trsv_lower_t_r(Gc, lcinv, na, na, b);
     for (int a = lane; a < na; a += 32) P5[a + (size_t)j * t] = b[a];
     __syncwarp();
     // Algorithm 6 (Eqs. 27-30): keep the rows of unchanged basis elements, refit the new
@@ -429,7 +457,7 @@ __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout 
     }
     __syncwarp();
     warp_apply_qt(QR6, s, nn, s, d.work + w.b6, d.work + w.h6, b);
-    warp_trsv_upper_d(QR6, r6, nn, s, b, tol6);
+    warp_trsv_upper_r(QR6, r6inv, nn, s, b);
     if (lane == 0) {
       int c = 0;
       for (int a = 0; a < na; ++a) {
@@ -802,6 +830,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   if (!launch_qr_coop(d, d.work + w.QR4, d.work + w.b4, d.work + w.h4, d.work + w.r4, d.work + w.QR6,
                       d.work + w.b6, d.work + w.h6, d.work + w.r6, d.gbar2, st))
     return 0;
+  qr_prep_kernel<<<1, 256, 0, st>>>(d, w);
   cudaStreamWaitEvent(st, ev_gram, 0);
   coeff_kernel<<<kApplyBlocks, kApplyThreads, 0, st>>>(d, w, n_obs, n_prev);
   const int nchunk = (int)((n_obs + kHutChunk - 1) / kHutChunk);
@@ -816,7 +845,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   }
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
-  return nk + 13 + ngk;
+  return nk + 14 + ngk;
 }
 
 }  // namespace rid

@@ -163,6 +163,39 @@ static __device__ void warp_trsv_upper_d(const double* R, const double* rdiag, i
   }
 }
 
+// The same three triangular solves with precomputed reciprocal diagonals (0 where the
+// division is skipped): this GPU's FP64 division is a long multi-instruction sequence.
+static __device__ void warp_trsv_lower_r(const double* L, const double* linv, int n, int lda, double* b) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {
+    const double yj = b[j] * linv[j];
+    __syncwarp();
+    for (int i = j + 1 + lane; i < n; i += 32) b[i] -= L[i + (size_t)j * lda] * yj;
+    if (lane == 0) b[j] = yj;
+    __syncwarp();
+  }
+}
+static __device__ void warp_trsv_lower_t_r(const double* L, const double* linv, int n, int lda, double* b) {
+  const int lane = threadIdx.x & 31;
+  for (int j = n - 1; j >= 0; --j) {
+    const double xj = b[j] * linv[j];
+    __syncwarp();
+    for (int i = lane; i < j; i += 32) b[i] -= L[j + (size_t)i * lda] * xj;
+    if (lane == 0) b[j] = xj;
+    __syncwarp();
+  }
+}
+static __device__ void warp_trsv_upper_r(const double* R, const double* rinv, int n, int lda, double* c) {
+  const int lane = threadIdx.x & 31;
+  for (int j = n - 1; j >= 0; --j) {
+    const double xj = c[j] * rinv[j];
+    __syncwarp();
+    for (int i = lane; i < j; i += 32) c[i] -= R[i + (size_t)j * lda] * xj;
+    if (lane == 0) c[j] = xj;
+    __syncwarp();
+  }
+}
+
 // Householder tridiagonalization of the symmetric n x n matrix A (full
 // storage, destroyed); diagonal to dvec, off-diagonal to evec.  v, p: n doubles each.
 static __device__ void cta_tridiagonalize(double* A, int n, int lda, double* dvec, double* evec,
