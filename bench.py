@@ -38,6 +38,9 @@ CONFIGS = {
                         nx=96, ny=65, nz=96, n=200, b=8, k=100, s=403, h=50),
     "channel_small": dict(workload="channel-flow-shaped stream, 3 x 48 x 33 x 48 FP32, n=200, blocks of 8",
                           nx=48, ny=33, nz=48, n=200, b=8, k=20, s=83, h=30),
+    # gradient mode (Sec. 3.4) on 11 fields of 1024 x 1024: the native-precision FP32 path
+    "ignition": dict(workload="ignition-shaped stream, 11 fields x 1024 x 1024 FP32, gradient mode, n=2000, "
+                              "blocks of 8", kind="ignition", N=1024, nfields=11, n=2000, b=8, k=150, s=603, h=50),
 }
 
 
@@ -106,12 +109,25 @@ def cpu_baseline(cfg, seconds_target=15.0, m_sample=1 << 17):
     b snapshots of the same stream; throughput extrapolated linearly in m (ingest is linear in m)."""
     import torch
     from oracle.rid import OnlineRID as Oracle, RIDConfig
-    from workloads import ChannelFlowStream
-    st = ChannelFlowStream(seed=0, nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=cfg["n"], device="cpu")
-    m = st.m
-    ms = min(m_sample, m)
-    blk = st.block(0, cfg["b"]).double().numpy()[:, :ms]
-    o = Oracle(RIDConfig(m=ms, k=cfg["k"], s=cfg["s"], h=cfg["h"], seed=0))
+    from workloads import ChannelFlowStream, IgnitionStream
+    if cfg.get("kind") == "ignition":
+        # gradient mode: the sample is the first rows of field 0, a 1024-wide grid of its own
+        # (s = 603 rows of Omega and Omega_g make the oracle slow: 32 rows keep it to ~30 s)
+        m_sample = min(m_sample, 1 << 15)
+        from oracle.gradient import grid_gradient_operator
+        st = IgnitionStream(seed=0, N=cfg["N"], nfields=cfg["nfields"], n=cfg["n"], device="cpu")
+        m = st.m
+        rows_s = max(2, min(m_sample, m) // cfg["N"])
+        ms = rows_s * cfg["N"]
+        blk = st.block(0, cfg["b"]).double().numpy()[:, :ms]
+        o = Oracle(RIDConfig(m=ms, k=cfg["k"], s=cfg["s"], h=cfg["h"], seed=0,
+                             grad_op=grid_gradient_operator((cfg["N"], rows_s))))
+    else:
+        st = ChannelFlowStream(seed=0, nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=cfg["n"], device="cpu")
+        m = st.m
+        ms = min(m_sample, m)
+        blk = st.block(0, cfg["b"]).double().numpy()[:, :ms]
+        o = Oracle(RIDConfig(m=ms, k=cfg["k"], s=cfg["s"], h=cfg["h"], seed=0))
     t0 = time.perf_counter()
     o.ingest(blk.T)
     dt = time.perf_counter() - t0
@@ -160,7 +176,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2405_16076_gb300 import rid
-    from workloads import ChannelFlowStream
+    from workloads import ChannelFlowStream, IgnitionStream
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -171,7 +187,12 @@ def main():
     dev = torch.device("cuda", local)
 
     n, b = cfg["n"], cfg["b"]
-    gen = ChannelFlowStream(seed=1000 + rank, nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=n, device=dev)
+    grad = cfg.get("kind") == "ignition"
+    if grad:
+        gen = IgnitionStream(seed=1000 + rank, N=cfg["N"], nfields=cfg["nfields"], n=n, device=dev)
+        args.sketch = "native"                      # gradient mode runs the native-precision sketch
+    else:
+        gen = ChannelFlowStream(seed=1000 + rank, nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=n, device=dev)
     m = gen.m
     X = torch.empty((n, m), dtype=torch.float32, device=dev)     # row j = snapshot j, resident in HBM
     for j0 in range(0, n, 50):
@@ -179,8 +200,9 @@ def main():
     torch.cuda.synchronize()
 
     st = torch.cuda.Stream(device=dev)
+    gkw = dict(grad_dims=2, nx=cfg["N"], ny=cfg["N"], nfields=cfg["nfields"]) if grad else {}
     h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=args.sketch, n_max=n,
-                      seed=7 + rank, stream=st, defer=True, group_max=args.group)
+                      seed=7 + rank, stream=st, defer=True, group_max=args.group, **gkw)
     Jd = torch.empty(cfg["k"], dtype=torch.int64, device=dev)
     Pd = torch.empty((n, cfg["k"]), dtype=torch.float64, device=dev)
 
@@ -246,6 +268,8 @@ def main():
     # The ingest kernel alone (no batch step running beside it): one group of G columns per
     # launch, G < t so that no batch step is triggered.  Reported beside the in-step figure.
     G = max(1, min(args.group, cfg["k"] - 1, n))
+    if args.sketch == "native":
+        G = min(G, 16)                              # one SIMT sketch launch takes up to 16 columns
     h.reset()
     h.ingest(X[:G])
     h.sync()
@@ -263,6 +287,8 @@ def main():
     groups = max(int(prof_grp[0]), 1)
     avg_ms = prof_ms[0] / groups
     cols_per_launch = int(prof_kern[0] and (n * args.steps) / max(int(prof_grp[0]), 1))
+    if args.sketch == "native":
+        cols_per_launch = min(cols_per_launch, 16)  # the timed launch is the group's first (16 columns)
     bytes_per_launch = 2.0 * cols_per_launch * m * 4    # read each column once + write it to its slot
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     # DRAM bytes per launch from the committed ncu counters, scaled by the columns and coordinates
@@ -306,6 +332,18 @@ def main():
                      "peak_source": "measured (MEASURED_PEAKS.json)" if "fallback" not in pk else "fallback"},
         "clocks": clk.summary(),
     }
+    if args.sketch == "native":
+        # The native-precision sketch runs on the FP32 pipe: one signed add per (row, coordinate,
+        # column) of the s + h sketch rows.  Peak: SMs x 128 FP32 lanes x the maximum SM clock.
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_t = nsm * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        rows = cfg["s"] + cfg["h"]
+        ach = cols_per_launch * m * rows / (avg_ms / 1e3) / 1e12
+        iso = G * m * rows / (iso_ms / 1e3) / 1e12
+        line["roofline"].update({"bound": "alu", "achieved": ach, "peak": peak_t, "unit": "Tadd/s",
+                                 "frac": ach / peak_t, "traffic": None,
+                                 "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x {pk.get('sm_max_mhz', 2070.0)} MHz"})
+        line["roofline"]["isolated"].update({"achieved": iso, "frac": iso / peak_t})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:

@@ -183,27 +183,34 @@ __global__ void materialize_omega_kernel(Dev d) {
 // Entry j = p * m + i of G a (Eq. 42) for component p (0: along x, the fastest axis; 1: along
 // y) at coordinate i of field f = i / (nx ny): the least-squares gradient of Eqs. 39-43 on the
 // grid graph, i.e. the central difference along axis p where both axis neighbours exist and
-// the one-sided difference at the boundary (spacing 1; fields independent).
-template <typename T>
-__device__ __forceinline__ double grad_entry(const T* a, int64_t j, int64_t m, int nx, int ny) {
-  const int p = (int)(j / m);
-  const int64_t i = j - (int64_t)p * m;
-  const int64_t ql = i % ((int64_t)nx * ny);
+// the one-sided difference at the boundary (spacing 1; fields independent).  The stencil
+// (offset and the weights of a[i - st], a[i], a[i + st]) depends only on j.
+struct GradStencil {
+  int64_t i, st;
+  double wm, wc, wp;
+};
+__device__ __forceinline__ GradStencil grad_stencil(int64_t j, int64_t m, int nx, int ny) {
+  GradStencil g;
+  const int p = j >= m ? 1 : 0;                // d = 2
+  g.i = j - (p ? m : 0);
+  const int64_t ql = g.i % ((int64_t)nx * ny);
   const int c = p == 0 ? (int)(ql % nx) : (int)(ql / nx);
   const int len = p == 0 ? nx : ny;
-  const int64_t st = p == 0 ? 1 : nx;
-  if (c == 0) return (double)a[i + st] - (double)a[i];
-  if (c == len - 1) return (double)a[i] - (double)a[i - st];
-  return 0.5 * ((double)a[i + st] - (double)a[i - st]);
+  g.st = p == 0 ? 1 : nx;
+  if (c == 0) { g.wm = 0.0; g.wc = -1.0; g.wp = 1.0; }
+  else if (c == len - 1) { g.wm = -1.0; g.wc = 1.0; g.wp = 0.0; }
+  else { g.wm = -0.5; g.wc = 0.0; g.wp = 0.5; }
+  return g;
 }
 
 // Omega_g (G a_q) for the s leverage rows and ||G a_q||^2, split-K over the d m gradient
-// entries like the ingest sketch: grid (n_sketch_blocks, ceil(s / 256)), 256 threads, thread
-// tid of row group y owns row r = 256 y + tid; partials to d.spart / d.npart.
+// entries like the ingest sketch (working-precision sums over four chunks, then FP64): grid
+// (nblk, ceil(s / 256)), 256 threads, thread tid of row group y owns row r = 256 y + tid;
+// partials to d.spart / d.npart.
 template <typename T, int NB>
 __global__ void __launch_bounds__(kSketchThreads)
 grad_sketch_kernel(Dev d, SimtCols cols, int nb) {
-  __shared__ double X[NB][kChunk];
+  __shared__ T X[NB][kChunk];
   __shared__ double red[kSketchThreads / 32][NB];
   const int tid = threadIdx.x;
   const int r = blockIdx.y * kSketchThreads + tid;
@@ -211,20 +218,32 @@ grad_sketch_kernel(Dev d, SimtCols cols, int nb) {
   const bool lead = blockIdx.y == 0;
   const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
   const int64_t dm = 2 * d.m;
-  double acc[NB], nrm[NB];
+  double acc64[NB], nrm[NB];
+  T acc[NB];
 #pragma unroll
-  for (int q = 0; q < NB; ++q) { acc[q] = 0.0; nrm[q] = 0.0; }
+  for (int q = 0; q < NB; ++q) { acc64[q] = 0.0; acc[q] = T(0); nrm[q] = 0.0; }
   const int64_t nchunks = (dm + kChunk - 1) / kChunk;
+  int pending = 0;
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const int64_t j0 = c * kChunk;
     const int64_t j = j0 + tid;
+    if (j < dm) {
+      const GradStencil g = grad_stencil(j, d.m, d.nx, d.ny);
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      if (q < nb) {
-        const double g = (j < dm) ? grad_entry((const T*)cols.p[q], j, d.m, d.nx, d.ny) : 0.0;
-        X[q][tid] = g;
-        nrm[q] += g * g;
+      for (int q = 0; q < NB; ++q) {
+        if (q < nb) {
+          const T* a = (const T*)cols.p[q];
+          T v = (T)g.wc * a[g.i];
+          if (g.wm != 0.0) v += (T)g.wm * a[g.i - g.st];
+          if (g.wp != 0.0) v += (T)g.wp * a[g.i + g.st];
+          X[q][tid] = v;
+          nrm[q] += (double)v * (double)v;
+        }
       }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < nb) X[q][tid] = T(0);
     }
     __syncthreads();
     if (row_ok) {
@@ -250,19 +269,24 @@ grad_sketch_kernel(Dev d, SimtCols cols, int nb) {
 #pragma unroll 1
         for (int ii = 0; ii < kChunk; ++ii) {
           if (j0 + ii >= dm) break;
-          const double w = gauss_entry(d.seed, kTagGradGauss, (uint32_t)r, (uint64_t)(j0 + ii));
+          const T w = (T)gauss_entry(d.seed, kTagGradGauss, (uint32_t)r, (uint64_t)(j0 + ii));
 #pragma unroll
           for (int q = 0; q < NB; ++q)
             if (q < nb) acc[q] += w * X[q][ii];
         }
       }
     }
+    if (++pending == 4) {
+#pragma unroll
+      for (int q = 0; q < NB; ++q) { acc64[q] += (double)acc[q]; acc[q] = T(0); }
+      pending = 0;
+    }
     __syncthreads();
   }
   if (row_ok) {
 #pragma unroll
     for (int q = 0; q < NB; ++q)
-      if (q < nb) d.spart[((size_t)blockIdx.x * nb + q) * d.rows + r] = acc[q];
+      if (q < nb) d.spart[((size_t)blockIdx.x * nb + q) * d.rows + r] = acc64[q] + (double)acc[q];
   }
   if (lead) {
     const int lane = tid & 31, wid = tid >> 5;
