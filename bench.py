@@ -38,6 +38,10 @@ CONFIGS = {
                         nx=96, ny=65, nz=96, n=200, b=8, k=100, s=403, h=50),
     "channel_small": dict(workload="channel-flow-shaped stream, 3 x 48 x 33 x 48 FP32, n=200, blocks of 8",
                           nx=48, ny=33, nz=48, n=200, b=8, k=20, s=83, h=30),
+    # configuration C5: 64 independent streams through rid_batch_ingest (m log-uniform in
+    # [2^16, 2^21], n in [100, 1000], k in {10, 30, 60}, h = 30, blocks of 8, BF16x2 sketches)
+    "streams64": dict(workload="64 independent streams (half imaging-, half low-rank-shaped), FP32, blocks of 8",
+                      kind="streams", nstreams=64, b=8, h=30),
     # gradient mode (Sec. 3.4) on 11 fields of 1024 x 1024: the native-precision FP32 path
     "ignition": dict(workload="ignition-shaped stream, 11 fields x 1024 x 1024 FP32, gradient mode, n=2000, "
                               "blocks of 8", kind="ignition", N=1024, nfields=11, n=2000, b=8, k=150, s=603, h=50),
@@ -138,6 +142,86 @@ def cpu_baseline(cfg, seconds_target=15.0, m_sample=1 << 17):
                       f"({dt:.1f} s), extrapolated linearly in m; batch steps not included"}
 
 
+def run_streams(args, cfg):
+    """Configuration C5: all streams stepped together through rid_batch_ingest (each handle on its
+    own CUDA stream), against the same streams run one after another."""
+    import torch
+    from paper_2405_16076_gb300 import rid
+    from workloads import ImagingStream, LowRankStream, batched_streams_spec
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    spec = batched_streams_spec(seed=0, nstreams=cfg["nstreams"])
+    data = []
+    for sp in spec:
+        gen = (ImagingStream(seed=sp["seed"], m=sp["m"], n=sp["n"], device=dev) if sp["kind"] == "imaging"
+               else LowRankStream(seed=sp["seed"], m=sp["m"], n=sp["n"], device=dev))
+        X = torch.empty((sp["n"], sp["m"]), dtype=torch.float32, device=dev)
+        for j0 in range(0, sp["n"], 100):
+            gen.block(j0, min(100, sp["n"] - j0), out=X[j0:j0 + 100])
+        data.append(X)
+    torch.cuda.synchronize()
+    b = cfg["b"]
+    streams = [torch.cuda.Stream(device=dev) for _ in spec]
+    hs = [rid.OnlineRID(m=sp["m"], k=sp["k"], s=4 * sp["k"] + 3, h=cfg["h"], dtype="f32", sketch="bf16x2",
+                        n_max=sp["n"], seed=sp["seed"], stream=st, defer=True, group_max=64)
+          for sp, st in zip(spec, streams)]
+    outs = [(torch.empty(sp["k"], dtype=torch.int64, device=dev),
+             torch.empty((sp["n"], sp["k"]), dtype=torch.float64, device=dev)) for sp in spec]
+    nmax = max(sp["n"] for sp in spec)
+    total = sum(sp["n"] for sp in spec)
+
+    def batched():
+        for hd in hs:
+            hd.reset()
+        for j0 in range(0, nmax, b):
+            sel = [(hd, X[j0:j0 + b]) for hd, X, sp in zip(hs, data, spec) if j0 < sp["n"]]
+            rid.batch_ingest([x[0] for x in sel], [x[1] for x in sel])
+        for hd, (J, P) in zip(hs, outs):
+            hd.finalize_device(J, P)
+
+    def sequential():
+        for hd, X, sp, (J, P) in zip(hs, data, spec, outs):
+            hd.reset()
+            for j0 in range(0, sp["n"], b):
+                hd.ingest(X[j0:j0 + b])
+            hd.finalize_device(J, P)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    with ClockSampler(0) as clk:
+        tb = timed(batched, args.steps)
+    ts = timed(sequential, 1)
+    pk = peaks()
+    algo = sum(8.0 * sp["m"] * sp["n"] for sp in spec)     # read + slot write of every snapshot
+    line = {
+        "metric": "snapshots/s", "value": total / tb, "unit": "snapshots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 data, bf16x2 sketch", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "streams": len(spec), "snapshots": total,
+                   "m_range": [min(sp["m"] for sp in spec), max(sp["m"] for sp in spec)],
+                   "k": sorted({sp["k"] for sp in spec}), "h": cfg["h"], "block": b,
+                   "timing": "host clock around whole steps, synchronized on both sides"},
+        "sequential": {"value": total / ts, "unit": "snapshots/s", "ms_per_step": ts * 1e3,
+                       "note": "the same 64 streams run one after another"},
+        "e2e": None,
+        "roofline": {"bound": "hbm", "achieved": algo / tb / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": algo / tb / 1e9 / pk.get("hbm_gbs"), "traffic": None, "kernel": "whole step",
+                     "note": "algorithmic bytes of every ingest (8 m per snapshot) over the whole batched step"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    for hd in hs:
+        hd.close()
+
+
 def run_reference(args, cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -172,6 +256,8 @@ def main():
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
         return run_reference(args, cfg)
+    if cfg.get("kind") == "streams":
+        return run_streams(args, cfg)
 
     import torch
     import torch.distributed as dist

@@ -7,7 +7,7 @@ ignition run, NSTX GPI) are not available; these generators stand in for them
 with the shapes, sizes and value ranges the paper describes (Sec. 4).
 """
 from .synth import (config1_matrix, ChannelFlowStream, IgnitionStream,
-                    ImagingStream, batched_streams_spec)
+                    ImagingStream, LowRankStream, batched_streams_spec)
 
 __all__ = ["config1_matrix", "ChannelFlowStream", "IgnitionStream",
-           "ImagingStream", "batched_streams_spec"]
+           "ImagingStream", "LowRankStream", "batched_streams_spec"]

@@ -172,6 +172,32 @@ class ImagingStream:
         return out
 
 
+class LowRankStream:
+    """Configuration-1-style stream with m rows: U diag(sigma) V^T + noise, built on ``device``.
+
+    U: m x r Gaussian columns scaled to unit norm; sigma_j = 10^(-j/8); V(t, j) = cos(pi j t / n);
+    noise variance 1e-8.  ``block(j0, b)`` returns b x m (row q = snapshot j0 + q)."""
+
+    def __init__(self, seed=0, m=65536, n=200, r=64, dtype=torch.float32, device="cpu"):
+        self.m, self.n, self.r = m, n, r
+        self.dtype, self.device = dtype, torch.device(device)
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        U = torch.randn(m, r, generator=g, dtype=torch.float32)
+        self.U = (U / U.norm(dim=0, keepdim=True)).to(self.device)
+        self.sigma = (10.0 ** (-torch.arange(r, dtype=torch.float32) / 8.0)).to(self.device)
+        self.g = torch.Generator(device=self.device).manual_seed(seed + 1)
+
+    def block(self, j0, b, out=None):
+        t = torch.arange(j0, j0 + b, dtype=torch.float32)[:, None]
+        V = torch.cos(math.pi * t * torch.arange(self.r, dtype=torch.float32)[None, :] / self.n).to(self.device)
+        X = (V * self.sigma[None, :]) @ self.U.T
+        X += 1e-4 * torch.randn(b, self.m, generator=self.g, dtype=torch.float32, device=self.device)
+        if out is None:
+            return X.to(self.dtype)
+        out.copy_(X)
+        return out
+
+
 def batched_streams_spec(seed=0, nstreams=64):
     """Per-stream (kind, m, n, k) for the batched form: m log-uniform in [2^16, 2^21],
     n uniform in [100, 1000], k in {10, 30, 60}, half imaging- and half flow-shaped."""
