@@ -174,6 +174,22 @@ enum rid_state_item {
 };
 int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count);
 
+/* Checkpoint / resume of a stream (not in the paper: a library service for long
+ * streams).  rid_checkpoint_size gives the bytes rid_checkpoint needs;
+ * rid_checkpoint sketches any pending columns, waits for the device, and writes
+ * the stream state to the caller's host buffer: the configuration, the counters,
+ * the sketch, SS^T, the norms, the basis and buffer slot tables, tau, P, the
+ * pool Gram and the data columns still in use (the basis and the columns of
+ * the current batch).  rid_restore puts such a state into a handle created
+ * with the same configuration (any state it held is discarded); the stream
+ * then continues exactly as the checkpointed one would have.  Errors:
+ * RID_EINVAL (buffer too small or truncated, another configuration, not a
+ * checkpoint), RID_ECUDA; the restored handle is in the reset state after a
+ * failed rid_restore that got past the configuration check. */
+int rid_checkpoint_size(rid_handle* h, int64_t* bytes);
+int rid_checkpoint(rid_handle* h, void* buf, int64_t bytes);
+int rid_restore(rid_handle* h, const void* buf, int64_t bytes);
+
 /* Measurement hooks (used by the benchmark).  While enabled, the library
  * brackets its launches with CUDA events on the handle's stream, per phase:
  * [0] the fused ingest/sketch kernel, [1] the ingest reductions (sketch

@@ -657,6 +657,172 @@ int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
   return RID_OK;
 }
 
+// ---------------------------------------------------------------- checkpoint / resume
+// Layout (host bytes): header | config | counters | arrays, each array as stored on the device.
+// Between batch steps the previous basis equals the current one, so the pool slots still in
+// use are the basis slots and the buffer slots of the count columns buffered so far.
+namespace {
+
+constexpr uint64_t kCkptMagic = 0x31545043444952ull;   // "RIDCPT1"
+
+struct CkptCounters {
+  int64_t n_obs, n_prev;
+  int32_t count, batch, finalized, nslots;
+};
+
+bool same_config(const rid_config& a, const rid_config& b) {
+  return a.m == b.m && a.k == b.k && a.s == b.s && a.h == b.h && a.lambda_mode == b.lambda_mode &&
+         a.c1 == b.c1 && a.c2 == b.c2 && a.eps == b.eps && a.delta == b.delta && a.c_const == b.c_const &&
+         a.lambda_fixed == b.lambda_fixed && a.omega_kind == b.omega_kind && a.data_dtype == b.data_dtype &&
+         a.sketch_prec == b.sketch_prec && a.grad_dims == b.grad_dims && a.nx == b.nx && a.ny == b.ny &&
+         a.nfields == b.nfields && a.seed == b.seed;
+}
+
+struct CkptPlan {
+  std::vector<std::pair<void*, size_t>> arrays;   // device pointer, bytes
+  std::vector<int> slots;                         // pool slots saved, in order
+  size_t total;
+};
+
+// The device arrays of the stream state (fixed order) and the pool slots in use.
+int ckpt_plan(rid_handle* h, CkptPlan& pl) {
+  Dev& d = h->d;
+  const int t = d.t;
+  const int64_t n = h->n_obs;
+  pl.arrays = {
+      {d.S, sizeof(double) * (size_t)d.rows * n},
+      {d.SSt, sizeof(double) * (size_t)d.s * d.s},
+      {d.fro2, 2 * sizeof(double)},
+      {d.JC, sizeof(int64_t) * t}, {d.JC_prev, sizeof(int64_t) * t},
+      {d.slotC, sizeof(int) * t}, {d.slotC_prev, sizeof(int) * t},
+      {h->dslot_buf, sizeof(int) * 2 * (size_t)t},
+      {d.tau_old, sizeof(double) * t},
+      {d.meta, sizeof(int) * rid::META_LEN}, {d.scal, sizeof(double) * rid::SCAL_LEN},
+      {d.P, sizeof(double) * (size_t)t * n},
+      {d.Gp, sizeof(double) * (size_t)d.npool * d.npool},
+  };
+  if (d.grad) pl.arrays.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
+  std::vector<int> slotc(t), dsl(2 * (size_t)t);
+  CK(cudaMemcpyAsync(slotc.data(), d.slotC, sizeof(int) * t, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(dsl.data(), h->dslot_buf, sizeof(int) * 2 * t, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  pl.slots.clear();
+  for (int i = 0; i < t; ++i) if (slotc[i] >= 0) pl.slots.push_back(slotc[i]);
+  const int* cur = dsl.data() + (size_t)(h->batch & 1) * t;
+  for (int q = 0; q < h->count; ++q) pl.slots.push_back(cur[q]);
+  size_t tot = sizeof(uint64_t) + sizeof(rid_config) + sizeof(CkptCounters);
+  for (auto& a : pl.arrays) tot += a.second;
+  tot += sizeof(int) * pl.slots.size() + pl.slots.size() * (size_t)d.m * h->esize;
+  pl.total = tot;
+  return RID_OK;
+}
+
+}  // namespace
+
+int rid_checkpoint_size(rid_handle* h, int64_t* bytes) {
+  if (!h || !bytes) return RID_EINVAL;
+  int rc = flush(h);
+  if (rc != RID_OK) return rc;
+  join(h);
+  CkptPlan pl;
+  rc = ckpt_plan(h, pl);
+  if (rc != RID_OK) return rc;
+  *bytes = (int64_t)pl.total;
+  return RID_OK;
+}
+
+int rid_checkpoint(rid_handle* h, void* buf, int64_t bytes) {
+  if (!h || !buf) return RID_EINVAL;
+  int rc = flush(h);
+  if (rc != RID_OK) return rc;
+  rc = check_device_error(h);                   // joins the batch streams and synchronizes
+  if (rc != RID_OK) return rc;
+  CkptPlan pl;
+  rc = ckpt_plan(h, pl);
+  if (rc != RID_OK) return rc;
+  if ((size_t)bytes < pl.total) return fail(h, RID_EINVAL, "checkpoint buffer too small (see rid_checkpoint_size)");
+  char* p = (char*)buf;
+  const uint64_t magic = kCkptMagic;
+  memcpy(p, &magic, sizeof(magic)); p += sizeof(magic);
+  memcpy(p, &h->cfg, sizeof(rid_config)); p += sizeof(rid_config);
+  CkptCounters cn{h->n_obs, h->n_prev, h->count, h->batch, h->finalized ? 1 : 0, (int32_t)pl.slots.size()};
+  memcpy(p, &cn, sizeof(cn)); p += sizeof(cn);
+  for (auto& a : pl.arrays) {
+    if (a.second) CK(cudaMemcpyAsync(p, a.first, a.second, cudaMemcpyDeviceToHost, h->st));
+    p += a.second;
+  }
+  memcpy(p, pl.slots.data(), sizeof(int) * pl.slots.size()); p += sizeof(int) * pl.slots.size();
+  const size_t cb = (size_t)h->d.m * h->esize;
+  for (int sl : pl.slots) {
+    CK(cudaMemcpyAsync(p, (const char*)h->d.pool + (size_t)sl * h->d.m_pad * h->esize, cb, cudaMemcpyDeviceToHost, h->st));
+    p += cb;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return RID_OK;
+}
+
+int rid_restore(rid_handle* h, const void* buf, int64_t bytes) {
+  if (!h || !buf) return RID_EINVAL;
+  const char* p = (const char*)buf;
+  const size_t head = sizeof(uint64_t) + sizeof(rid_config) + sizeof(CkptCounters);
+  if ((size_t)bytes < head) return fail(h, RID_EINVAL, "checkpoint truncated");
+  uint64_t magic;
+  memcpy(&magic, p, sizeof(magic)); p += sizeof(magic);
+  if (magic != kCkptMagic) return fail(h, RID_EINVAL, "not a checkpoint of this library");
+  rid_config cf;
+  memcpy(&cf, p, sizeof(cf)); p += sizeof(cf);
+  if (!same_config(cf, h->cfg)) return fail(h, RID_EINVAL, "checkpoint of a different configuration");
+  CkptCounters cn;
+  memcpy(&cn, p, sizeof(cn)); p += sizeof(cn);
+  int rc = rid_reset(h);                       // joins, clears pending columns and counters
+  if (rc != RID_OK) return rc;
+  rc = grow(h, cn.n_obs > 0 ? cn.n_obs : 1);
+  if (rc != RID_OK) return rc;
+  h->n_obs = cn.n_obs;
+  h->n_prev = cn.n_prev;
+  h->count = cn.count;
+  h->batch = cn.batch;
+  h->finalized = cn.finalized != 0;
+  CkptPlan pl;
+  {
+    // the array list depends only on the configuration and n_obs
+    Dev& d = h->d;
+    const int t = d.t;
+    const int64_t n = h->n_obs;
+    pl.arrays = {
+        {d.S, sizeof(double) * (size_t)d.rows * n},
+        {d.SSt, sizeof(double) * (size_t)d.s * d.s},
+        {d.fro2, 2 * sizeof(double)},
+        {d.JC, sizeof(int64_t) * t}, {d.JC_prev, sizeof(int64_t) * t},
+        {d.slotC, sizeof(int) * t}, {d.slotC_prev, sizeof(int) * t},
+        {h->dslot_buf, sizeof(int) * 2 * (size_t)t},
+        {d.tau_old, sizeof(double) * t},
+        {d.meta, sizeof(int) * rid::META_LEN}, {d.scal, sizeof(double) * rid::SCAL_LEN},
+        {d.P, sizeof(double) * (size_t)t * n},
+        {d.Gp, sizeof(double) * (size_t)d.npool * d.npool},
+    };
+    if (d.grad) pl.arrays.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
+  }
+  size_t need = head;
+  for (auto& a : pl.arrays) need += a.second;
+  const size_t cb = (size_t)h->d.m * h->esize;
+  need += (size_t)cn.nslots * (sizeof(int) + cb);
+  if ((size_t)bytes < need) return fail(h, RID_EINVAL, "checkpoint truncated");
+  for (auto& a : pl.arrays) {
+    if (a.second) CK(cudaMemcpyAsync(a.first, p, a.second, cudaMemcpyHostToDevice, h->st));
+    p += a.second;
+  }
+  std::vector<int> slots(cn.nslots);
+  memcpy(slots.data(), p, sizeof(int) * slots.size()); p += sizeof(int) * slots.size();
+  for (int sl : slots) {
+    if (sl < 0 || sl >= h->d.npool) return fail(h, RID_EINVAL, "checkpoint holds an invalid pool slot");
+    CK(cudaMemcpyAsync((char*)h->d.pool + (size_t)sl * h->d.m_pad * h->esize, p, cb, cudaMemcpyHostToDevice, h->st));
+    p += cb;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return RID_OK;
+}
+
 int rid_profile(rid_handle* h, int32_t enable) {
   if (!h) return RID_EINVAL;
   join(h);

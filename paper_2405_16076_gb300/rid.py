@@ -64,6 +64,9 @@ def _load():
         "rid_reset": (ctypes.c_int, [H]),
         "rid_last_error": (ctypes.c_char_p, [H]),
         "rid_destroy": (None, [H]),
+        "rid_checkpoint_size": (ctypes.c_int, [H, P]),
+        "rid_checkpoint": (ctypes.c_int, [H, P, ctypes.c_int64]),
+        "rid_restore": (ctypes.c_int, [H, P, ctypes.c_int64]),
         "rid_batch_ingest": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, ctypes.c_int32]),
         "rid_sketch_noalloc": (ctypes.c_int, [ctypes.POINTER(rid_config), P, ctypes.c_int64, ctypes.c_int32,
                                               P, ctypes.c_int64, P]),
@@ -93,6 +96,9 @@ rid_last_error = lib.rid_last_error
 rid_destroy = lib.rid_destroy
 rid_sketch_noalloc = lib.rid_sketch_noalloc
 rid_batch_ingest = lib.rid_batch_ingest
+rid_checkpoint_size = lib.rid_checkpoint_size
+rid_checkpoint = lib.rid_checkpoint
+rid_restore = lib.rid_restore
 
 
 def batch_ingest(handles, blocks):
@@ -275,6 +281,19 @@ class OnlineRID:
         _check(rid_profile_read(self.h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(kern.ctypes.data),
                                 ctypes.c_void_p(grp.ctypes.data)), self.h)
         return ms, kern, grp
+
+    def checkpoint(self):
+        """The stream state as bytes (rid_checkpoint)."""
+        n = ctypes.c_int64()
+        _check(rid_checkpoint_size(self.h, ctypes.byref(n)), self.h)
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(rid_checkpoint(self.h, ctypes.c_void_p(buf.ctypes.data), n.value), self.h)
+        return buf.tobytes()
+
+    def restore(self, state):
+        """Continue the stream saved by checkpoint() (same configuration)."""
+        buf = np.frombuffer(state, dtype=np.uint8)
+        _check(rid_restore(self.h, ctypes.c_void_p(buf.ctypes.data), buf.size), self.h)
 
     def sync(self):
         _check(rid_sync(self.h), self.h)
