@@ -142,6 +142,27 @@ def cpu_baseline(cfg, seconds_target=15.0, m_sample=1 << 17):
                       f"({dt:.1f} s), extrapolated linearly in m; batch steps not included"}
 
 
+def rank_seeds(rank):
+    """Seeds of rank r's independent stream (data generator, sketch): every rank has its own."""
+    return 1000 + rank, 7 + rank
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (all ranks take part; a no-op for one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(world, units_per_rank, t_max_ms):
+    """Units all ranks processed divided by the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / (t_max_ms / 1e3)
+
+
 def run_streams(args, cfg):
     """Configuration C5: all streams stepped together through rid_batch_ingest (each handle on its
     own CUDA stream), against the same streams run one after another."""
@@ -275,10 +296,10 @@ def main():
     n, b = cfg["n"], cfg["b"]
     grad = cfg.get("kind") == "ignition"
     if grad:
-        gen = IgnitionStream(seed=1000 + rank, N=cfg["N"], nfields=cfg["nfields"], n=n, device=dev)
+        gen = IgnitionStream(seed=rank_seeds(rank)[0], N=cfg["N"], nfields=cfg["nfields"], n=n, device=dev)
         args.sketch = "native"                      # gradient mode runs the native-precision sketch
     else:
-        gen = ChannelFlowStream(seed=1000 + rank, nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=n, device=dev)
+        gen = ChannelFlowStream(seed=rank_seeds(rank)[0], nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=n, device=dev)
     m = gen.m
     X = torch.empty((n, m), dtype=torch.float32, device=dev)     # row j = snapshot j, resident in HBM
     for j0 in range(0, n, 50):
@@ -288,7 +309,7 @@ def main():
     st = torch.cuda.Stream(device=dev)
     gkw = dict(grad_dims=2, nx=cfg["N"], ny=cfg["N"], nfields=cfg["nfields"]) if grad else {}
     h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=args.sketch, n_max=n,
-                      seed=7 + rank, stream=st, defer=True, group_max=args.group, **gkw)
+                      seed=rank_seeds(rank)[1], stream=st, defer=True, group_max=args.group, **gkw)
     Jd = torch.empty(cfg["k"], dtype=torch.int64, device=dev)
     Pd = torch.empty((n, cfg["k"]), dtype=torch.float64, device=dev)
 
@@ -318,12 +339,8 @@ def main():
     ms_total = e0.elapsed_time(e1)
     prof_ms, prof_kern, prof_grp = h.profile_read()
     h.profile(False)
-    t_max = ms_total
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * n * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(ms_total, world, dev)
+    value = whole_job_rate(world, n * args.steps, t_max)
 
     # e2e: same metric through rid_ingest with pinned host buffers and a host read of P
     ring = max(1, min(32, n // b))
