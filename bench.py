@@ -43,6 +43,11 @@ CONFIGS = {
     "streams64": dict(workload="64 independent streams (half imaging-, half low-rank-shaped), FP32, blocks of 8",
                       kind="streams", nstreams=64, b=8, h=30),
     # gradient mode (Sec. 3.4) on 11 fields of 1024 x 1024: the native-precision FP32 path
+    # configuration C4: the small FP64 stream (m = 4096, n = 256, k = 20, s = 83, h = 30, columns one
+    # at a time, fixed lambda) in FP32 with BF16x2 / BF16 tensor-core sketches, beside FP32 and FP64
+    "precision": dict(workload="precision forms of the 4096 x 256 low-rank stream (k=20, s=83, h=30, "
+                               "columns one at a time, fixed lambda), seeds 0..9",
+                      kind="precision", m=4096, n=256, k=20, s=83, h=30, seeds=10),
     "ignition": dict(workload="ignition-shaped stream, 11 fields x 1024 x 1024 FP32, gradient mode, n=2000, "
                               "blocks of 8", kind="ignition", N=1024, nfields=11, n=2000, b=8, k=150, s=603, h=50),
 }
@@ -108,12 +113,62 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def low_rank_inputs(cfg):
+    """The small stream for seeds 0.. with its fixed lambda = ||A - A_k||_F^2 / k (from the SVD)."""
+    from workloads import config1_matrix
+    out = []
+    for seed in range(cfg["seeds"]):
+        A = config1_matrix(seed, m=cfg["m"], n=cfg["n"])
+        sv = np.linalg.svd(A, compute_uv=False)
+        out.append((seed, A, float((sv[cfg["k"]:] ** 2).sum() / cfg["k"])))
+    return out
+
+
+def rel_id_error(A, J, P):
+    """||A - A_J P||_F / ||A||_F on the host (P is t x n; empty slots have J < 0)."""
+    act = J >= 0
+    return float(np.linalg.norm(A - A[:, J[act]] @ P[act]) / np.linalg.norm(A))
+
+
 def cpu_baseline(cfg, seconds_target=15.0, m_sample=1 << 17):
     """The oracle as it stands on a bounded sample: the first m_sample coordinates of one block of
     b snapshots of the same stream; throughput extrapolated linearly in m (ingest is linear in m)."""
     import torch
     from oracle.rid import OnlineRID as Oracle, RIDConfig
     from workloads import ChannelFlowStream, IgnitionStream
+    if cfg.get("kind") == "precision":
+        # the whole workload: every seed's stream, one column at a time, in FP64
+        errs, dt = [], 0.0
+        for seed, A, lam in low_rank_inputs(cfg):
+            o = Oracle(RIDConfig(m=cfg["m"], k=cfg["k"], s=cfg["s"], h=cfg["h"], lambda_mode="fixed",
+                                 lambda_fixed=lam, seed=seed))
+            t0 = time.perf_counter()
+            for j in range(cfg["n"]):
+                o.ingest(A[:, j:j + 1])
+            J, P = o.finalize()
+            dt += time.perf_counter() - t0
+            errs.append(rel_id_error(A, J, P))
+        return {"value": cfg["seeds"] * cfg["n"] / dt, "unit": "snapshots/s", "cores": torch.get_num_threads(),
+                "kind": "oracle", "rel_fro_err": errs,
+                "sample": f"the whole workload: {cfg['seeds']} streams of {cfg['n']} columns ({dt:.1f} s)"}
+    if cfg.get("kind") == "streams":
+        # the first 4 of the 64 streams, their first m_sample coordinates, one block of b snapshots
+        from workloads import ImagingStream, LowRankStream, batched_streams_spec
+        spec = batched_streams_spec(seed=0, nstreams=cfg["nstreams"])[:4]
+        dt_full, nsnap = 0.0, 0
+        for sp in spec:
+            gen = (ImagingStream(seed=sp["seed"], m=sp["m"], n=sp["n"], device="cpu") if sp["kind"] == "imaging"
+                   else LowRankStream(seed=sp["seed"], m=sp["m"], n=sp["n"], device="cpu"))
+            ms = min(m_sample, sp["m"])
+            blk = gen.block(0, cfg["b"]).double().numpy()[:, :ms]
+            o = Oracle(RIDConfig(m=ms, k=sp["k"], s=4 * sp["k"] + 3, h=cfg["h"], seed=sp["seed"]))
+            t0 = time.perf_counter()
+            o.ingest(blk.T)
+            dt_full += (time.perf_counter() - t0) * sp["m"] / ms
+            nsnap += cfg["b"]
+        return {"value": nsnap / dt_full, "unit": "snapshots/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                "sample": f"oracle ingest of {cfg['b']} snapshots of each of the first 4 streams, restricted to "
+                          f"their first {m_sample} coordinates, extrapolated linearly in m; batch steps not included"}
     if cfg.get("kind") == "ignition":
         # gradient mode: the sample is the first rows of field 0, a 1024-wide grid of its own
         # (s = 603 rows of Omega and Omega_g make the oracle slow: 32 rows keep it to ~30 s)
@@ -140,6 +195,34 @@ def cpu_baseline(cfg, seconds_target=15.0, m_sample=1 << 17):
     return {"value": 1.0 / per_snap_full, "unit": "snapshots/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle ingest of {cfg['b']} snapshots restricted to the first {ms} of m={m} coordinates "
                       f"({dt:.1f} s), extrapolated linearly in m; batch steps not included"}
+
+
+def id_error_device(X, J, P, chunk=1 << 17):
+    """Relative Frobenius error ||A - A_J P||_F / ||A||_F of a finished stream, for the report only.
+
+    X (n, m) FP32 on the device, row j = snapshot j; J (t,) int64 (-1 = empty slot); P (n, t)
+    FP64, row j = coefficients of snapshot j.  Coordinates are taken in chunks and everything
+    runs in FP64: coefficients of ill-conditioned bases reach 1e6 and more, and their
+    cancellation must not be lost to the evaluation's own rounding."""
+    import torch
+    act = (J >= 0).nonzero().flatten()
+    Jv = J[act]
+    Pv = P[:, act]
+    num = torch.zeros((), dtype=torch.float64, device=X.device)
+    den = torch.zeros((), dtype=torch.float64, device=X.device)
+    for c0 in range(0, X.shape[1], chunk):
+        Xc = X[:, c0:c0 + chunk].double()
+        R = torch.addmm(Xc, Pv, X[Jv, c0:c0 + chunk].double(), alpha=-1.0)
+        num += R.square().sum()
+        den += Xc.square().sum()
+    return float((num / den).sqrt().item()), float(den.item())
+
+
+def accuracy_report(h, X, Jd, Pd):
+    """Exact relative error of the result and the NA-Hutch++ estimate of it (Algorithm 8)."""
+    err, fro2 = id_error_device(X, Jd, Pd)
+    est_sq, est_fro, q = h.error_estimate()
+    return {"rel_fro_err": err, "est_rel_fro_err": float(est_fro[0] / np.sqrt(fro2)), "q_star": q}
 
 
 def rank_seeds(rank):
@@ -220,6 +303,12 @@ def run_streams(args, cfg):
     with ClockSampler(0) as clk:
         tb = timed(batched, args.steps)
     ts = timed(sequential, 1)
+    errs = [id_error_device(X, J, P, chunk=1 << 20)[0] for X, (J, P) in zip(data, outs)]
+    accuracy = {"rel_fro_err_mean": float(np.mean(errs)), "rel_fro_err_max": float(np.max(errs)),
+                "rel_fro_err": [float(e) for e in errs],
+                "sketch": "bf16x2",
+                "note": "||A - A_J P||_F / ||A||_F per stream after the timed region (the batched and the "
+                        "one-after-another runs give identical J and P)"}
     pk = peaks()
     algo = sum(8.0 * sp["m"] * sp["n"] for sp in spec)     # read + slot write of every snapshot
     line = {
@@ -237,10 +326,104 @@ def run_streams(args, cfg):
                      "frac": algo / tb / 1e9 / pk.get("hbm_gbs"), "traffic": None, "kernel": "whole step",
                      "note": "algorithmic bytes of every ingest (8 m per snapshot) over the whole batched step"},
         "clocks": clk.summary(),
+        "accuracy": accuracy,
     }
     print(json.dumps(line), flush=True)
     for hd in hs:
         hd.close()
+
+
+def run_precision(args, cfg):
+    """Configuration C4: the same seeded streams through FP64, plain FP32, BF16x2 and BF16 sketches.
+
+    Every form runs every seed (columns one at a time, fixed lambda); the line reports the relative
+    Frobenius error of each form's result and of the oracle's (its cpu_baseline leg), and the
+    throughput of each form on seed 0 (W warm-up and K timed passes, CUDA events).  The headline
+    value is the BF16x2 form."""
+    import torch
+    from paper_2405_16076_gb300 import rid
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    k, n, m = cfg["k"], cfg["n"], cfg["m"]
+    inputs = low_rank_inputs(cfg)
+    st = torch.cuda.Stream(device=dev)
+    Jd = torch.empty(k, dtype=torch.int64, device=dev)
+    Pd = torch.empty((n, k), dtype=torch.float64, device=dev)
+    forms = {"f64": ("f64", "native"), "f32": ("f32", "native"), "bf16x2": ("f32", "bf16x2"), "bf16": ("f32", "bf16")}
+    res, clk_summary, launches = {}, None, 0
+    for name, (dtype, sk) in forms.items():
+        errs, ests = [], []
+        for seed, A, lam in inputs:
+            hd = rid.OnlineRID(m=m, k=k, s=cfg["s"], h=cfg["h"], dtype=dtype, sketch=sk, lambda_mode="fixed",
+                               lambda_fixed=lam, seed=seed, n_max=n, stream=st, defer=True)
+            X = torch.from_numpy(np.ascontiguousarray(A.T, dtype=np.float64 if dtype == "f64" else np.float32)).to(dev)
+
+            def step():
+                hd.reset()
+                for j in range(n):
+                    hd.ingest(X[j:j + 1])
+                hd.finalize_device(Jd, Pd)
+            step()
+            torch.cuda.synchronize()
+            if seed == 0:
+                for _ in range(args.warmup):
+                    step()
+                torch.cuda.synchronize()
+                hd.profile(True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                with ClockSampler(0) as clk:
+                    e0.record(st)
+                    for _ in range(args.steps):
+                        step()
+                    e1.record(st)
+                    torch.cuda.synchronize()
+                prof_ms, prof_kern, prof_grp = hd.profile_read()
+                hd.profile(False)
+                ms = e0.elapsed_time(e1) / args.steps
+                res[name] = {"value": n / (ms / 1e3), "unit": "snapshots/s", "ms_per_step": ms,
+                             "ingest_ms_per_launch": prof_ms[0] / max(int(prof_grp[0]), 1)}
+                if name == "bf16x2":
+                    clk_summary = clk.summary()
+                    launches = int(prof_kern.sum())
+            J = Jd.cpu().numpy()
+            P = Pd.cpu().numpy().T
+            errs.append(rel_id_error(A, J, P))
+            ests.append(float(hd.error_estimate()[1][0] / np.linalg.norm(A)))
+            hd.close()
+        res[name].update({"rel_fro_err": errs, "rel_fro_err_mean": float(np.mean(errs)),
+                          "est_rel_fro_err_mean": float(np.mean(ests))})
+    accuracy = {"forms": res, "err_ratio_bf16x2_vs_f64": res["bf16x2"]["rel_fro_err_mean"] / res["f64"]["rel_fro_err_mean"],
+                "err_ratio_bf16_vs_f64": res["bf16"]["rel_fro_err_mean"] / res["f64"]["rel_fro_err_mean"],
+                "note": "||A - A_J P||_F / ||A||_F per seed (0..9) for each form; est = the NA-Hutch++ estimate"}
+    pk = peaks()
+    per_launch = res["bf16x2"]["ingest_ms_per_launch"]
+    ach = 2.0 * m * 4 / (per_launch / 1e3) / 1e9
+    line = {
+        "metric": "snapshots/s", "value": res["bf16x2"]["value"], "unit": "snapshots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["bf16x2"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 data, bf16x2 sketch",
+        "data": "synthetic",
+        "config": {"workload": cfg["workload"], "m": m, "n": n, "block": 1, "k": k, "s": cfg["s"], "h": cfg["h"],
+                   "omega": "rademacher", "lambda": "fixed, ||A - A_k||_F^2 / k",
+                   "l2": "small inputs (the stream is 4 MB): latency-bound, L2-resident"},
+        "e2e": None,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": ach / pk.get("hbm_gbs"), "traffic": None, "kernel": "tc_ingest_kernel",
+                     "avg_launch_ms": per_launch, "cols_per_launch": 1,
+                     "note": "one 4096-coordinate column per launch: launch- and latency-bound, far from HBM",
+                     "peak_source": "measured (MEASURED_PEAKS.json)" if "fallback" not in pk else "fallback"},
+        "clocks": clk_summary,
+        "accuracy": accuracy,
+    }
+    if not args.no_cpu_baseline:
+        cb = cpu_baseline(cfg)
+        line["cpu_baseline"] = {key: v for key, v in cb.items() if key != "rel_fro_err"}
+        oe = float(np.mean(cb["rel_fro_err"]))
+        accuracy["oracle_f64"] = {"rel_fro_err": cb["rel_fro_err"], "rel_fro_err_mean": oe}
+        accuracy["err_ratio_bf16x2_vs_oracle"] = res["bf16x2"]["rel_fro_err_mean"] / oe
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args, cfg):
@@ -273,12 +456,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sketch", default="bf16x2", choices=["bf16x2", "bf16", "native"])
     ap.add_argument("--group", type=int, default=64)
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="skip the accuracy comparison with the other sketch precisions")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
         return run_reference(args, cfg)
     if cfg.get("kind") == "streams":
         return run_streams(args, cfg)
+    if cfg.get("kind") == "precision":
+        return run_precision(args, cfg)
 
     import torch
     import torch.distributed as dist
@@ -339,6 +526,7 @@ def main():
     ms_total = e0.elapsed_time(e1)
     prof_ms, prof_kern, prof_grp = h.profile_read()
     h.profile(False)
+    accuracy = accuracy_report(h, X, Jd, Pd)
     t_max = max_over_ranks(ms_total, world, dev)
     value = whole_job_rate(world, n * args.steps, t_max)
 
@@ -385,6 +573,44 @@ def main():
     iso_ms_tot, _, iso_grp = h.profile_read()
     h.profile(False)
     iso_ms = iso_ms_tot[0] / max(int(iso_grp[0]), 1)
+
+    h.close()
+
+    # The same stream through the other sketch precisions, for the accuracy-throughput comparison
+    # (one warm-up and one timed pass each; the plain FP32 form runs on the FP32 pipe)
+    forms = {}
+    if not grad and args.forms:
+        for form in ("bf16x2", "bf16", "native"):
+            if form == args.sketch:
+                continue
+            hf = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=form, n_max=n,
+                               seed=rank_seeds(rank)[1], stream=st, defer=True, group_max=args.group)
+
+            def step_f():
+                hf.reset()
+                for j0 in range(0, n, b):
+                    hf.ingest(X[j0:j0 + b])
+                hf.finalize_device(Jd, Pd)
+            step_f()
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(st)
+            step_f()
+            f1.record(st)
+            torch.cuda.synchronize()
+            forms[form] = {"value": n / (f0.elapsed_time(f1) / 1e3), "unit": "snapshots/s",
+                           **accuracy_report(hf, X, Jd, Pd)}
+            hf.close()
+    accuracy["sketch"] = args.sketch
+    if forms:
+        accuracy["forms"] = forms
+        if "native" in forms:
+            accuracy["err_ratio_vs_plain_f32"] = accuracy["rel_fro_err"] / forms["native"]["rel_fro_err"]
+    accuracy["note"] = ("rel_fro_err = ||A - A_J P||_F / ||A||_F over the whole stream (evaluated in FP64 after the "
+                        "timed region); est_rel_fro_err = the NA-Hutch++ estimate of the "
+                        "chosen candidate; forms = the same stream with the other sketch precisions "
+                        "('native' = plain FP32 on the FP32 pipe)")
 
     pk = peaks()
     groups = max(int(prof_grp[0]), 1)
@@ -434,6 +660,7 @@ def main():
                                            "batch_step": prof_ms[2] / args.steps},
                      "peak_source": "measured (MEASURED_PEAKS.json)" if "fallback" not in pk else "fallback"},
         "clocks": clk.summary(),
+        "accuracy": accuracy,
     }
     if args.sketch == "native":
         # The native-precision sketch runs on the FP32 pipe: one signed add per (row, coordinate,
@@ -451,7 +678,6 @@ def main():
         line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         dist.destroy_process_group()
 

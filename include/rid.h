@@ -166,11 +166,20 @@ int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device);
  *  RID_STATE_CAND     : 4 x t x n_obs doubles, candidates P_4..P_7 of the last
  *                       batch step (rows of empty slots are 0)
  *  RID_STATE_BATCHES  : 1 int64, number of batch steps run
+ *  RID_STATE_GRAM_SHIFT: 1 double, the Tikhonov shift that the last batch step
+ *                       added to the basis Gram of Algorithms 5 and 7, relative
+ *                       to its largest diagonal entry; 0 when G = A_J^T A_J was
+ *                       factored as is.  The shift is taken only when the
+ *                       smallest Cholesky pivot falls below that same fraction
+ *                       of the largest diagonal entry (1e-11 for FP64 sums,
+ *                       3e-5 for the tensor-core Gram of FP32 data): the basis
+ *                       is then so nearly dependent that the Gram's rounding
+ *                       would dominate the solve.
  * count is the number of elements the caller's buffer holds. */
 enum rid_state_item {
   RID_STATE_SKETCH = 0, RID_STATE_SKETCH_LEV = 1, RID_STATE_SST = 2, RID_STATE_FRO2 = 3,
   RID_STATE_JC = 4, RID_STATE_TAU_OLD = 5, RID_STATE_LAMBDA = 6, RID_STATE_CAND = 7,
-  RID_STATE_BATCHES = 8
+  RID_STATE_BATCHES = 8, RID_STATE_GRAM_SHIFT = 9
 };
 int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count);
 

@@ -325,12 +325,20 @@ constexpr size_t kCholSmemBytes = 160 * 1024;
 constexpr size_t kHutchSmemBytes = 160 * 1024;
 
 // Cholesky factor of the basis Gram (in place in Gc); staged in shared memory when it fits.
-__global__ void __launch_bounds__(1024) gram_chol_kernel(Dev d, WorkLayout w, int staged) {
+//
+// Algorithms 5 and 7 go through G = A_J^T A_J, whose condition number is kappa(A_J)^2.  When
+// the smallest pivot falls below rho0 x the largest diagonal entry -- the basis is so nearly
+// dependent that the Gram's own rounding (rho0 is ten times its relative accuracy: FP64 sums,
+// or the BF16x2 split on tensor cores) would dominate the solve -- G is factored again with the
+// Tikhonov shift rho0 max_a G_aa on its diagonal: directions of A_J below the shift are damped
+// instead of amplified, so the coefficients stay bounded and the residual near its minimum.
+__global__ void __launch_bounds__(1024) gram_chol_kernel(Dev d, WorkLayout w, int staged, double rho0) {
   extern __shared__ double gsm[];
   __shared__ int fail;
-  __shared__ double gm;
+  __shared__ double gm, pmin;
   const int na = d.meta[META_NACT];
   double* Gc = d.work + w.Gc;
+  const double* G = d.work + w.G;
   const bool use_smem = staged && (size_t)na * na * sizeof(double) <= kCholSmemBytes;
   double* A = use_smem ? gsm : Gc;
   if (use_smem)
@@ -338,12 +346,25 @@ __global__ void __launch_bounds__(1024) gram_chol_kernel(Dev d, WorkLayout w, in
   __syncthreads();
   if (threadIdx.x == 0) {
     fail = 0;
+    pmin = 0.0;
     double m = 0.0;
     for (int a = 0; a < na; ++a) m = fmax(m, A[a + (size_t)a * na]);
     gm = m;
   }
   __syncthreads();
-  cta_cholesky(A, na, na, 1e-13 * gm, &fail);
+  cta_cholesky(A, na, na, 1e-13 * gm, &fail, &pmin);
+  __syncthreads();
+  const bool shift = na > 0 && pmin < rho0 * gm;
+  if (shift) {
+    for (int i = threadIdx.x; i < na * na; i += blockDim.x) {
+      const int a = i % na, b = i / na;
+      A[i] = G[i] + (a == b ? rho0 * gm : 0.0);
+    }
+    if (threadIdx.x == 0) fail = 0;
+    __syncthreads();
+    cta_cholesky(A, na, na, 1e-13 * gm, &fail);
+  }
+  if (threadIdx.x == 0) d.scal[SCAL_GSHIFT] = shift ? rho0 : 0.0;
   double* linv = d.work + w.Lcinv;
   for (int a = threadIdx.x; a < na; a += blockDim.x) {
     const double ljj = A[a + (size_t)a * na];
@@ -354,7 +375,8 @@ __global__ void __launch_bounds__(1024) gram_chol_kernel(Dev d, WorkLayout w, in
 }
 
 // Reciprocal diagonals of the two QR factors, with the rank tolerance of each:
-// |R_jj| <= max(s, n) eps max|R_ii| gives 0 (the component is dropped).
+// |R_jj| <= max(max(s, n) eps, sk_rel) max|R_ii| gives 0 (the component is dropped; sk_rel is
+// the relative accuracy of a reduced-precision sketch, 0 for FP64).
 __global__ void __launch_bounds__(256) qr_prep_kernel(Dev d, WorkLayout w) {
   __shared__ double sm[2][8];
   const int na = d.meta[META_NACT], nn = d.meta[META_NNEW], s = d.s;
@@ -371,8 +393,8 @@ __global__ void __launch_bounds__(256) qr_prep_kernel(Dev d, WorkLayout w) {
   __syncthreads();
   m4 = 0.0; m6 = 0.0;
   for (int i = 0; i < 8; ++i) { m4 = fmax(m4, sm[0][i]); m6 = fmax(m6, sm[1][i]); }
-  const double tol4 = (double)(s > na ? s : na) * 2.220446049250313e-16 * m4;
-  const double tol6 = (double)(s > nn ? s : nn) * 2.220446049250313e-16 * m6;
+  const double tol4 = fmax((double)(s > na ? s : na) * 2.220446049250313e-16, d.sk_rel) * m4;
+  const double tol6 = fmax((double)(s > nn ? s : nn) * 2.220446049250313e-16, d.sk_rel) * m6;
   for (int a = threadIdx.x; a < na; a += blockDim.x)
     d.work[w.r4inv + a] = (fabs(r4[a]) > tol4) ? 1.0 / r4[a] : 0.0;
   for (int c = threadIdx.x; c < nn; c += blockDim.x)
@@ -494,7 +516,7 @@ __global__ void __launch_bounds__(256) hutch_partial_kernel(Dev d, WorkLayout w,
   const double* Pq = d.cand + (size_t)q * t * d.n_cap;
   const int64_t j0 = (int64_t)blockIdx.x * kHutChunk;
   const int64_t j1 = (j0 + kHutChunk < n_obs) ? j0 + kHutChunk : n_obs;
-  double* out = d.hpart + ((size_t)q * gridDim.x + blockIdx.x) * ((size_t)hh * t + 1);
+  double* out = d.hpart + ((size_t)q * gridDim.x + blockIdx.x) * hpart_stride(hh, t);
   for (int idx = threadIdx.x; idx < hh * na; idx += blockDim.x) {
     const int r = idx % hh, a = idx / hh;
     double acc = 0.0;
@@ -502,16 +524,22 @@ __global__ void __launch_bounds__(256) hutch_partial_kernel(Dev d, WorkLayout w,
     out[idx] = acc;
   }
   const double* G = d.work + w.G;
-  double part = 0.0;
+  double part = 0.0, part_e = 0.0;
   for (int idx = threadIdx.x; idx < na * (int)(j1 - j0); idx += blockDim.x) {
     const int a = idx % na;
     const int64_t j = j0 + idx / na;
     double gp = 0.0;
     for (int c = 0; c < na; ++c) gp += G[a + (size_t)c * na] * Pq[c + (size_t)j * t];
-    part += gp * Pq[a + (size_t)j * t];
+    const double p = Pq[a + (size_t)j * t];
+    part += gp * p;
+    part_e += G[a + (size_t)a * na] * p * p;
   }
   const double tot = block_sum(part, sh);
-  if (threadIdx.x == 0) out[(size_t)hh * t] = tot;
+  const double tot_e = block_sum(part_e, sh);
+  if (threadIdx.x == 0) {
+    out[(size_t)hh * t] = tot;
+    out[(size_t)hh * t + 1] = tot_e;
+  }
 }
 
 // sum_{c < n} a[c sa] b[c sb] with four independent partial sums: a dependent FP64 FMA chain
@@ -643,15 +671,19 @@ __global__ void __launch_bounds__(512) hutch_finish_kernel(Dev d, WorkLayout w, 
   const double* HJs = use_smem ? hsm + (size_t)hh * na : HJ;
   for (int idx = threadIdx.x; idx < hh * na; idx += blockDim.x) {
     double v = 0.0;
-    for (int c = 0; c < nchunk; ++c) v += d.hpart[((size_t)q * nchunk + c) * ((size_t)hh * t + 1) + idx];
+    for (int c = 0; c < nchunk; ++c) v += d.hpart[((size_t)q * nchunk + c) * hpart_stride(hh, t) + idx];
     Z[idx] = v;                                   // Z[r + a*hh] = (Omega A_obs P^T)[r][a]
     if (use_smem) Zs[idx] = v;
   }
   if (use_smem)
     for (int idx = threadIdx.x; idx < hh * na; idx += blockDim.x) hsm[(size_t)hh * na + idx] = HJ[idx];
-  double trg = 0.0;
+  double trg = 0.0, ener = 0.0;
   if (threadIdx.x == 0)
-    for (int c = 0; c < nchunk; ++c) trg += d.hpart[((size_t)q * nchunk + c) * ((size_t)hh * t + 1) + (size_t)hh * t];
+    for (int c = 0; c < nchunk; ++c) {
+      const double* pc = d.hpart + ((size_t)q * nchunk + c) * hpart_stride(hh, t) + (size_t)hh * t;
+      trg += pc[0];
+      ener += pc[1];
+    }
   __syncthreads();
   // views: Zi rows [o_i, o_i + h_i) of Z and HJ
   const int o1 = 0, o2 = h1, o3 = h1 + h2;
@@ -690,7 +722,8 @@ __global__ void __launch_bounds__(512) hutch_finish_kernel(Dev d, WorkLayout w, 
     __syncthreads();
     {
       const int mx = (h1 > h2) ? h1 : h2;
-      cta_pinv_rows(X, Jm, h1, h2, Xp, (double)mx * 2.220446049250313e-16, ZG /* free after W */, sh);
+      cta_pinv_rows(X, Jm, h1, h2, Xp, fmax((double)mx * 2.220446049250313e-16, d.sk_rel), ZG /* free after W */,
+                    sh);
     }
     for (int idx = threadIdx.x; idx < h2 * h3; idx += blockDim.x) {
       const int a = idx / h3, r = idx % h3;
@@ -720,20 +753,36 @@ __global__ void __launch_bounds__(512) hutch_finish_kernel(Dev d, WorkLayout w, 
   const double direct = block_sum(p3, sh);
   if (threadIdx.x == 0) {
     const double cross = term1 + (direct - corr) / (double)h3;
-    d.scal[SCAL_EST + q] = d.scal[fro_slot] - 2.0 * cross + trg;
+    const double fro = d.scal[fro_slot];
+    d.scal[SCAL_EST + q] = fro - 2.0 * cross + trg;
+    // Every term of the estimate is a sum over the basis expansion A_J P; with reduced-
+    // precision sketches and Gram (relative accuracy sk_rel) each carries a rounding error of
+    // about sk_rel x sum_j sum_a G_aa P_aj^2, the energy of the expansion before cancellation.
+    d.scal[SCAL_UNC + q] = fro > 0.0 ? d.sk_rel * ener / fro : 0.0;
   }
 }
 
 // ---------------------------------------------------------------- commit P = P_{q*}
-__device__ __forceinline__ int argmin4(const double* e) {
-  int q = 0;
-  for (int i = 1; i < 4; ++i) if (e[i] < e[q]) q = i;
+// q* = argmin of the estimates (Algorithm 8), over the candidates whose estimate the rounding
+// of a reduced-precision sketch cannot overturn (uncertainty <= 0.1 ||A_obs||^2): a candidate
+// whose coefficients cancel far beyond that precision can have an estimate of any sign and
+// size.  If no candidate qualifies, the one with the smallest uncertainty.  With FP64 sketches
+// every uncertainty is 0 and this is the plain argmin.
+__device__ __forceinline__ int choose_q(const double* scal) {
+  const double* e = scal + SCAL_EST;
+  const double* u = scal + SCAL_UNC;
+  int q = -1;
+  for (int i = 0; i < 4; ++i)
+    if (u[i] <= 0.1 && (q < 0 || e[i] < e[q])) q = i;
+  if (q >= 0) return q;
+  q = 0;
+  for (int i = 1; i < 4; ++i) if (u[i] < u[q]) q = i;
   return q;
 }
 
 __global__ void commit_kernel(Dev d, int64_t n_obs) {
   const int t = d.t;
-  const int q = argmin4(d.scal + SCAL_EST);
+  const int q = choose_q(d.scal);
   const double* Pq = d.cand + (size_t)q * t * d.n_cap;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)t * n_obs;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -746,7 +795,7 @@ __global__ void commit_kernel(Dev d, int64_t n_obs) {
 
 __global__ void finish_kernel(Dev d, int batch, int64_t n_obs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  d.meta[META_QSTAR] = 4 + argmin4(d.scal + SCAL_EST);
+  d.meta[META_QSTAR] = 4 + choose_q(d.scal);
   for (int i = 0; i < d.t; ++i) { d.JC_prev[i] = d.JC[i]; d.slotC_prev[i] = d.slotC[i]; }
   d.meta[META_BATCH] = batch + 1;
   d.meta[META_NPREV] = (int)n_obs;
@@ -822,7 +871,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
     if (staged < 0)
       staged = cudaFuncSetAttribute(gram_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kCholSmemBytes) == cudaSuccess ? 1 : 0;
-    gram_chol_kernel<<<1, 1024, staged ? kCholSmemBytes : 0, stg>>>(d, w, staged);
+    gram_chol_kernel<<<1, 1024, staged ? kCholSmemBytes : 0, stg>>>(d, w, staged, d.gram_rho0);
   }
   tsolve_kernel<<<(d.t + 7) / 8, 256, 0, stg>>>(d, w);
   cudaEventRecord(ev_gram, stg);

@@ -33,13 +33,15 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // In-place lower Cholesky of the n x n SPD matrix A (lower triangle used).
 // A non-positive pivot (relative to tol) zeroes its column; returns via *fail.
-static __device__ void cta_cholesky(double* A, int n, int lda, double tol, int* fail) {
+// pmin (shared, may be null) receives the smallest pivot, before its square root.
+static __device__ void cta_cholesky(double* A, int n, int lda, double tol, int* fail, double* pmin = nullptr) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int j = 0; j < n; ++j) {
     __syncthreads();
     double djj = A[j + (size_t)j * lda];
     const bool ok = djj > tol;
     if (!ok && tid == 0) *fail = 1;
+    if (pmin && tid == 0) *pmin = (j == 0 || djj < *pmin) ? djj : *pmin;
     djj = ok ? sqrt(djj) : 0.0;
     __syncthreads();
     if (tid == 0) A[j + (size_t)j * lda] = djj;

@@ -121,7 +121,7 @@ void join(rid_handle* h) {
 
 int64_t hpart_len(const Dev& d, int64_t ncap) {
   const int64_t hh = d.h1 + d.h2 + d.h3;
-  return 4 * ((ncap + 31) / 32) * (hh * d.t + 1);
+  return 4 * ((ncap + 31) / 32) * rid::hpart_stride(hh, d.t);
 }
 
 // (Re)allocate the arrays whose size follows the column capacity, keeping S, Slev and P.
@@ -374,6 +374,19 @@ int rid_init(rid_handle** out, const rid_config* c) {
   d.gram_split = (int)(gs < 1 ? 1 : (gs > 256 ? 256 : gs));
   const int t = d.t;
   h->tc = c->sketch_prec != RID_SKETCH_NATIVE;
+  // Accuracy of the sketch entries and of the basis Gram (about ten times their relative
+  // rounding): no rank tolerance of the coefficient solves or of the Hutch++ pseudo-inverse
+  // goes below them, so that directions the rounding decides are dropped, not amplified.
+  if (d.dtype == 0) {                       // FP64 sums
+    d.sk_rel = 0.0;
+    d.gram_rho0 = 1e-11;
+  } else if (!h->tc) {                      // FP32 products summed in FP32 over short runs
+    d.sk_rel = 1e-6;
+    d.gram_rho0 = 1e-6;
+  } else {                                  // tensor cores; the Gram always takes the BF16x2 split
+    d.sk_rel = c->sketch_prec == RID_SKETCH_BF16X2 ? 2e-5 : 4e-3;
+    d.gram_rho0 = 3e-5;
+  }
   h->group_max = c->group_max > 0 ? c->group_max : (h->tc ? rid::kMaxGroup : rid::kMaxB);
   {
     const int64_t tc_chunks = (d.m + 63) / 64;
@@ -635,6 +648,7 @@ int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
     case RID_STATE_JC: src = d.JC; bytes = sizeof(int64_t) * d.t; break;
     case RID_STATE_TAU_OLD: src = d.tau_old; bytes = sizeof(double) * d.t; break;
     case RID_STATE_LAMBDA: src = d.scal + rid::SCAL_LAMBDA; bytes = sizeof(double); break;
+    case RID_STATE_GRAM_SHIFT: src = d.scal + rid::SCAL_GSHIFT; bytes = sizeof(double); break;
     case RID_STATE_CAND: {
       if (count < 4 * (int64_t)d.t * h->n_prev) return fail(h, RID_EINVAL, "buffer too small");
       for (int q = 0; q < 4; ++q)

@@ -30,6 +30,8 @@ struct Dev {
   int hbase, h1, h2, h3;          // probe rows [hbase, hbase+h1+h2+h3) split into Omega_1/2/3
   int64_t n_cap;
   int dtype;                      // 0 f64, 1 f32
+  double sk_rel;                  // relative accuracy of a sketch entry (0 for FP64 sketches)
+  double gram_rho0;               // pivot threshold and Tikhonov shift of the basis Gram
   int omega_kind;                 // 0 gaussian, 1 rademacher
   int lambda_mode;
   double lambda_fixed;
@@ -91,7 +93,18 @@ enum {
 // scal[] indices
 // SCAL_FRO0 + (batch & 1): ||A_obs||^2 as the batch's step saw it (two slots: the next step's
 // lambda part may run while this step's tail still reads it)
-enum { SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_FRO0 = 5, SCAL_LEN = 8 };
+// SCAL_GSHIFT: the Tikhonov shift of the basis Gram in the last batch step, relative to its
+// largest diagonal entry (0 when the Gram was factored as is).
+// SCAL_UNC + q: rounding uncertainty of candidate q's estimate relative to ||A_obs||^2 (see
+// hutch_finish_kernel); 0 for FP64 sketches.
+enum {
+  SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_FRO0 = 5, SCAL_GSHIFT = 7,
+  SCAL_UNC = 8 /* 4 values */, SCAL_LEN = 16
+};
+
+// Per (candidate, column chunk) partials of the Hutch++ step: H P_q^T (hh x t), tr(G P P^T) and
+// sum_j sum_a G_aa P_aj^2.
+inline __host__ __device__ int64_t hpart_stride(int64_t hh, int64_t t) { return hh * t + 2; }
 
 // device error bits
 enum { ERR_NONFINITE = 1, ERR_CHOL = 2, ERR_EIG = 4, ERR_TIMEOUT = 8 };

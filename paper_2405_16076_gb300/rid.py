@@ -21,7 +21,7 @@ RID_OMEGA_GAUSSIAN, RID_OMEGA_RADEMACHER = 0, 1
 RID_F64, RID_F32 = 0, 1
 RID_SKETCH_NATIVE, RID_SKETCH_BF16, RID_SKETCH_BF16X2 = 0, 1, 2
 (RID_STATE_SKETCH, RID_STATE_SKETCH_LEV, RID_STATE_SST, RID_STATE_FRO2, RID_STATE_JC,
- RID_STATE_TAU_OLD, RID_STATE_LAMBDA, RID_STATE_CAND, RID_STATE_BATCHES) = range(9)
+ RID_STATE_TAU_OLD, RID_STATE_LAMBDA, RID_STATE_CAND, RID_STATE_BATCHES, RID_STATE_GRAM_SHIFT) = range(10)
 
 
 class rid_config(ctypes.Structure):
@@ -242,7 +242,7 @@ class OnlineRID:
             out = np.empty(t, dtype=np.int64)
         elif item == RID_STATE_TAU_OLD:
             out = np.empty(t)
-        elif item == RID_STATE_LAMBDA:
+        elif item in (RID_STATE_LAMBDA, RID_STATE_GRAM_SHIFT):
             out = np.empty(1)
         elif item == RID_STATE_BATCHES:
             out = np.empty(1, dtype=np.int64)
