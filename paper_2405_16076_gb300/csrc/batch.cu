@@ -634,18 +634,19 @@ __device__ void cta_pinv_rows(double* Y, double* J, int p, int q, double* Xp, do
   if (tid == 0) {
     double m = 0.0;
     for (int a = 0; a < p; ++a) m = fmax(m, nr2[a]);
-    wred[32] = sqrt(m);
+    // nr2[a] <- 1 / sigma_a^2 for the kept rows, 0 for the dropped ones (one thread: this
+    // GPU's FP64 square root and division are long instruction sequences)
+    const double cut = rcond * sqrt(m);
+    for (int a = 0; a < p; ++a) {
+      const double sg = sqrt(nr2[a]);
+      nr2[a] = (sg > cut && sg != 0.0) ? 1.0 / nr2[a] : 0.0;
+    }
   }
   __syncthreads();
-  const double smax = wred[32];
   for (int idx = tid; idx < q * p; idx += blockDim.x) {
     const int k = idx / p, c = idx % p;          // Xp[k][c] = sum_a Y[a][k] / sigma_a^2 * J[c][a]
     double acc = 0.0;
-    for (int a = 0; a < p; ++a) {
-      const double sg = sqrt(nr2[a]);
-      if (!(sg > rcond * smax) || sg == 0.0) continue;
-      acc += Y[a * q + k] / nr2[a] * J[c * p + a];
-    }
+    for (int a = 0; a < p; ++a) acc += Y[a * q + k] * nr2[a] * J[c * p + a];
     Xp[idx] = acc;
   }
   __syncthreads();

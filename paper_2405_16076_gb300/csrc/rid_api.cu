@@ -42,6 +42,7 @@ struct rid_handle {
   bool tc;                // tensor-core ingest (FP32 data, BF16 / BF16x2 sketch)
   int tc_blocks;          // CTAs of the basis Gram (and the bound of the partial buffers)
   int ingest_blocks;      // CTAs of the tensor-core ingest
+  int first_blocks;       // CTAs of the first batch's ingest (no batch step beside it)
   float* tc_part;
   double* tc_npart;
   std::string err;
@@ -240,7 +241,7 @@ int flush(rid_handle* h) {
   if (h->tc) {
     const int split = h->cfg.sketch_prec == RID_SKETCH_BF16X2 ? 1 : 0;
     // no batch step can run beside the first batch's ingest: it takes the whole grid
-    const int nblk = h->batch >= 1 ? h->ingest_blocks : h->tc_blocks;
+    const int nblk = h->batch >= 1 ? h->ingest_blocks : h->first_blocks;
     if (rid::launch_tc_ingest(db, h->pend.data(), G, split, h->count, h->n_obs, nblk,
                               h->tc_part, h->tc_npart, h->st, h->prof ? ev : nullptr) != 0)
       return fail(h, RID_ECUDA, "tensor-core ingest launch failed");
@@ -401,6 +402,9 @@ int rid_init(rid_handle** out, const rid_config* c) {
     const int ingest_avail = h->n_sm >= 96 ? h->n_sm - h->n_sm / 3 : avail;
     h->ingest_blocks = (int)(want_blocks < ingest_avail ? want_blocks : ingest_avail);
     if (h->ingest_blocks < 1) h->ingest_blocks = 1;
+    // nothing runs beside the first batch's ingest: it takes every SM
+    h->first_blocks = (int)(want_blocks < h->n_sm ? want_blocks : h->n_sm);
+    if (h->first_blocks < 1) h->first_blocks = 1;
   }
   int prio_lo = 0, prio_hi = 0;
   int rc = RID_OK;
@@ -408,9 +412,10 @@ int rid_init(rid_handle** out, const rid_config* c) {
   if (h->tc) {
     const int nrows16 = (d.rows + 15) / 16 * 16;
     const int prow = nrows16 > 256 ? nrows16 : 256;     // ingest partials or Gram partials
-    AL(h->tc_part, (size_t)h->tc_blocks * prow * 128);
+    const int pblk = h->first_blocks > h->tc_blocks ? h->first_blocks : h->tc_blocks;
+    AL(h->tc_part, (size_t)pblk * prow * 128);
     AL(h->tg_part, (size_t)h->tc_blocks * 512 * 128);     // basis-Gram partials: 512 rows per CTA
-    AL(h->tc_npart, (size_t)h->tc_blocks * 128);
+    AL(h->tc_npart, (size_t)pblk * 128);
     d.tc_blocks = h->tc_blocks;
     d.tc_part = h->tc_part;
     d.tg_part = h->tg_part;

@@ -622,11 +622,26 @@ __global__ void tc_gram_reduce_kernel(Dev d, const float* __restrict__ part, int
 // hi/lo products.  Requires ntgt <= 256 (2t <= 256).
 constexpr int kGramRowsMax = 512;            // 4 blocks x (64 hi + 64 lo) rows
 
+// Both 64-blocks of new elements (nnew > 64) in one pass over the targets: their two
+// accumulators, 128 lanes x nbrows columns each, fit the 512 TMEM columns together when
+// nbrows = 128 ceil(ntgt / 64) <= 256.
+__device__ __forceinline__ bool gram_merged(int nnew, int ntgt) {
+  return nnew > 64 && nnew <= 128 && ntgt <= 128;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ part, int nstage) {
   extern __shared__ uint8_t smem_raw[];
-  const int nnew = d.meta[META_NNEW], ntgt = d.meta[META_NTGT];
-  if (x0 >= nnew || ntgt <= 0) return;                  // uniform over the CTA, before any TMEM use
+  const int nnew = d.meta[META_NNEW], ntgt_all = d.meta[META_NTGT];
+  if (x0 >= nnew || ntgt_all <= 0) return;              // uniform over the CTA, before any TMEM use
+  // both 64-blocks of new elements in one pass when their accumulators fit TMEM together
+  const bool merged = gram_merged(nnew, ntgt_all);
+  if (merged && x0 > 0) return;                           // done by the x0 = 0 pass
+  const int nablk = (merged && x0 == 0) ? 2 : 1;
+  // targets before x0 are new elements of earlier blocks, whose pairs with this block those
+  // blocks' passes computed: the tile starts at target x0 (the A block is its first 128 rows)
+  const int ybase = merged ? 0 : x0;
+  const int ntgt = ntgt_all - ybase;
   const int nbrows = 128 * ((ntgt + 63) / 64);            // B rows in use (multiple of 128, <= 512)
   const uint32_t btile = (uint32_t)kGramRowsMax * 128u;
   const uint32_t raw = smem_u32(smem_raw);
@@ -666,22 +681,26 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
       const int n1 = nbrows < 256 ? nbrows : 256, n2 = nbrows - n1;
       const uint32_t id1 = idesc_bf16(128, n1);
       const uint32_t id2 = idesc_bf16(128, n2 > 0 ? n2 : 16);
-      const uint32_t aoff = (uint32_t)(x0 / 64) * 128u * 128u;   // A = rows of the x0 block
       int st = 0;
       uint32_t par = 0;
       for (int64_t c = 0; c < nch; ++c) {
         if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err)) break;
         tc_fence_after();
         const uint32_t bst = sB + st * btile;
-        const uint64_t da = desc_sw128(bst + aoff);
         const uint64_t db1 = desc_sw128(bst);
         const uint64_t db2 = desc_sw128(bst + 256 * 128);
+        for (int ab = 0; ab < nablk; ++ab) {
+          // A block ab: the 128 tile rows of new elements x0 + 64 ab .. (hi, then lo); its
+          // accumulator at TMEM columns ab nbrows
+          const uint64_t da = desc_sw128(bst + (uint32_t)ab * 128u * 128u);
+          const uint32_t dcol = tmem + (uint32_t)(ab * nbrows);
 #pragma unroll
-        for (int kk = 0; kk < kChunkK / 16; ++kk) {
-          const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-          const uint64_t adv = (uint64_t)(kk * 2);
-          tc_mma(tmem, da + adv, db1 + adv, id1, acc);
-          if (n2 > 0) tc_mma(tmem + (uint32_t)n1, da + adv, db2 + adv, id2, acc);
+          for (int kk = 0; kk < kChunkK / 16; ++kk) {
+            const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+            const uint64_t adv = (uint64_t)(kk * 2);
+            tc_mma(dcol, da + adv, db1 + adv, id1, acc);
+            if (n2 > 0) tc_mma(dcol + (uint32_t)n1, da + adv, db2 + adv, id2, acc);
+          }
         }
         tc_commit(bar_empty0 + 8 * st);
         if (++st == nstage) { st = 0; par ^= 1u; }
@@ -697,7 +716,7 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
     const int y0t = pt >> 3;                              // target of round u: y0t + 64 u
     int slot[4];                                          // pool slot, or -1 past the targets
 #pragma unroll
-    for (int u = 0; u < 4; ++u) slot[u] = (y0t + 64 * u < ntgt) ? d.gtgt[y0t + 64 * u] : -1;
+    for (int u = 0; u < 4; ++u) slot[u] = (y0t + 64 * u < ntgt) ? d.gtgt[ybase + y0t + 64 * u] : -1;
 #define GSRC(u) (pool + (int64_t)slot[u] * d.m_pad)
     float4 bufA[4][2], bufB[4][2];
     auto load_chunk = [&](int64_t c, float4 (&v)[4][2]) {
@@ -763,7 +782,7 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
         const int quarter = warp & 3;
         const int L = 32 * quarter + lane;
         const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16);
-        for (int cb = 0; cb < nbrows; cb += 32) {
+        for (int cb = 0; cb < nablk * nbrows; cb += 32) {
           uint32_t r[32];
           tc_ld32(taddr + (uint32_t)cb, r);
           tc_wait_ld();
@@ -790,9 +809,16 @@ __global__ void __launch_bounds__(256) tc_gram_all_reduce_kernel(Dev d, const fl
   const int nnew = d.meta[META_NNEW], ntgt = d.meta[META_NTGT];
   const int y = blockIdx.x;
   if (x0 >= nnew || y >= ntgt) return;
+  const bool merged = gram_merged(nnew, ntgt);
+  // a separate pass of block x0 starts its tile at target x0; in a merged pass the
+  // accumulators of the second 64-block follow those of the first
+  const int ybase = merged ? 0 : x0;
+  if (y < ybase) return;                                  // pair computed by an earlier block's pass
   const int nx = min(64, nnew - x0);
   const int x = threadIdx.x & 63, j = threadIdx.x >> 6;
-  const int chi = 128 * (y >> 6) + (y & 63), clo = chi + 64;
+  const int cofs = (merged && x0 > 0) ? 128 * ((ntgt + 63) / 64) : 0;
+  const int yl = y - ybase;
+  const int chi = cofs + 128 * (yl >> 6) + (yl & 63), clo = chi + 64;
   double v = 0.0;
   if (x < nx) {
     for (int b = j; b < nblk; b += 4) {
