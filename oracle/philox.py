@@ -26,6 +26,9 @@ library:
   Philox((i, r, TAG_UNIFORM, batch)).
 * Gradient-sketch Omega_g[r, q]: as Rademacher/Gaussian with TAG_GRAD_* and
   q = p*m + i the index into the stacked gradient vector (Sec. 3.4).
+* Right-sketch omega_j[r] (the optional m x l right sketch Y = sum_j a_j omega_j^T; not part
+  of the paper's method): as Rademacher/Gaussian with TAG_RIGHT_*, row r in 0..l-1 and
+  i = j the global index of the snapshot.
 
 Keys are (seed & 0xffffffff, seed >> 32).
 """
@@ -42,6 +45,8 @@ TAG_GAUSS = 0x47415531        # 'GAU1'
 TAG_UNIFORM = 0x554E4931      # 'UNI1'
 TAG_GRAD_RADEMACHER = 0x47524431  # 'GRD1'
 TAG_GRAD_GAUSS = 0x47524731       # 'GRG1'
+TAG_RIGHT_RADEMACHER = 0x52534B31  # 'RSK1'
+TAG_RIGHT_GAUSS = 0x52534731       # 'RSG1'
 
 TWO_M53 = 1.0 / 9007199254740992.0   # 2**-53
 
@@ -120,11 +125,13 @@ def gauss_block(seed, rows, i0, i1, tag=TAG_GAUSS):
     return np.where(even, rad * np.cos(ang), rad * np.sin(ang))
 
 
-def omega_block(kind, seed, rows, i0, i1, grad=False):
-    """Omega[rows, i0:i1] for ``kind`` in {'gaussian', 'rademacher'}."""
+def omega_block(kind, seed, rows, i0, i1, grad=False, right=False):
+    """Omega[rows, i0:i1] for ``kind`` in {'gaussian', 'rademacher'} (``grad``: Omega_g of the
+    gradient sketch; ``right``: the right-sketch vectors, row r, column i = snapshot index)."""
     if kind == "rademacher":
-        return rademacher_block(seed, rows, i0, i1,
-                                TAG_GRAD_RADEMACHER if grad else TAG_RADEMACHER)
+        tag = TAG_RIGHT_RADEMACHER if right else (TAG_GRAD_RADEMACHER if grad else TAG_RADEMACHER)
+        return rademacher_block(seed, rows, i0, i1, tag)
     if kind == "gaussian":
-        return gauss_block(seed, rows, i0, i1, TAG_GRAD_GAUSS if grad else TAG_GAUSS)
+        tag = TAG_RIGHT_GAUSS if right else (TAG_GRAD_GAUSS if grad else TAG_GAUSS)
+        return gauss_block(seed, rows, i0, i1, tag)
     raise ValueError(kind)

@@ -50,6 +50,10 @@ R16 Gradient mode (Sec. 3.4): the ridge scores use the sketch of [a; G a],
     squared norm ||a||^2 + ||G a||^2; coefficients and the error estimate use
     the plain sketch Omega a.
 R19 Indices are 0-based; -1 marks an empty slot.
+
+The optional right sketch Y = sum_j a_j omega_j^T (m x l, unit-variance omega_j of l entries
+keyed by the snapshot index j) is not part of the paper's method; it is kept beside the
+stream when ``right_l`` > 0 (``right_sketch`` gives it for a whole matrix).
 """
 from dataclasses import dataclass, field
 import math
@@ -77,6 +81,7 @@ class RIDConfig:
     omega_kind: str = "rademacher"     # or "gaussian"
     seed: int = 0
     grad_op: object = None             # sparse (d*m) x m simplex-gradient operator, Eq. 42
+    right_l: int = 0                   # columns of the optional right sketch Y (0: off)
 
     @property
     def t(self):
@@ -97,6 +102,13 @@ def refill_scale(cfg):
     """c (k log k + k log(1/delta)/eps) / t, the factor of tau^D in Algorithm 3's refill."""
     k = cfg.k
     return cfg.c_const * (k * math.log(k) + k * math.log(1.0 / cfg.delta) / cfg.eps) / cfg.t
+
+
+def right_sketch(A, l, kind, seed):
+    """Y = A W, W[j, r] = omega_j[r]: the right sketch of the m x n matrix A (all columns)."""
+    n = A.shape[1]
+    W = philox.omega_block(kind, seed, np.arange(l), 0, n, right=True).T     # n x l
+    return A @ W
 
 
 def streaming_lambda(SSt_scaled, fro2, k):
@@ -246,6 +258,7 @@ class OnlineRID:
         self._omega = None
         self._omega_g = None
         self.margins = []
+        self.Y = np.zeros((cfg.m, cfg.right_l)) if cfg.right_l > 0 else None
 
     # Omega is materialized once: this is the slow, obviously correct form.
     def omega(self):
@@ -282,6 +295,9 @@ class OnlineRID:
             fro_lev += ga @ ga
         self.S_lev = np.concatenate([self.S_lev, lev[:, None]], axis=1)
         self.SSt += np.outer(lev, lev)                       # SS^T <- SS^T + s_j s_j^T
+        if c.right_l > 0:                                    # Y <- Y + a_j omega_j^T
+            w = philox.omega_block(c.omega_kind, c.seed, np.arange(c.right_l), j, j + 1, right=True)[:, 0]
+            self.Y += np.outer(a, w)
         self.cols[j] = a                                     # d_count = a_j (R6)
         self.JD.append(j)
         self.fro2 += a @ a

@@ -345,3 +345,47 @@ def test_gradient_interior_is_central_difference_and_linear_exact():
     assert G2.shape == (2 * 2 * nx * ny, 2 * nx * ny)
     np.testing.assert_allclose(G2 @ np.concatenate([f, lin]),
                                np.concatenate([gx.ravel(), lin * 0 + 2.0, gy.ravel(), lin * 0 - 3.0]), atol=1e-12)
+
+
+# ---------------------------------------------------------------- optional right sketch
+@pytest.mark.parametrize("kind", ["rademacher", "gaussian"])
+def test_right_sketch_is_unbiased_for_the_column_gram(kind):
+    """E[Y Y^T] = l A A^T for unit-variance i.i.d. omega_j (JL-type sketch): the mean over
+    independent seeds lies within 5 standard errors entrywise; a dropped or doubled scale, or
+    omega vectors shared between snapshots, break it."""
+    from oracle.rid import right_sketch
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((6, 5))
+    l, nseed = 8, 1500
+    acc = np.zeros((6, 6))
+    acc2 = np.zeros((6, 6))
+    for seed in range(nseed):
+        Y = right_sketch(A, l, kind, 1000 + seed)
+        g = Y @ Y.T / l
+        acc += g
+        acc2 += g * g
+    mean = acc / nseed
+    se = np.sqrt(np.maximum(acc2 / nseed - mean ** 2, 1e-30) / nseed)
+    assert np.all(np.abs(mean - A @ A.T) <= 5 * se + 1e-12)
+
+
+def test_right_sketch_captures_the_range_and_is_block_invariant():
+    """With l >= rank(A) Gaussian omega_j, range(Y) = range(A) (A = Q Q^T A for the
+    orthonormal basis Q of Y), and streaming the columns in any blocks gives the same Y as
+    the whole matrix (omega_j is keyed by the global snapshot index j)."""
+    from oracle.rid import right_sketch
+    rng = np.random.default_rng(5)
+    m, n, r = 40, 30, 4
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    Y = right_sketch(A, 7, "gaussian", 11)
+    U, sv, _ = np.linalg.svd(Y, full_matrices=False)
+    Q = U[:, sv > 1e-10 * sv[0]]
+    assert np.linalg.norm(A - Q @ (Q.T @ A)) <= 1e-12 * np.linalg.norm(A)
+    o = OnlineRID(RIDConfig(m=m, k=5, s=23, h=12, omega_kind="gaussian", seed=11, right_l=7))
+    o.ingest(A[:, :3])
+    o.ingest(A[:, 3:4])
+    o.ingest(A[:, 4:])
+    assert np.allclose(o.Y, Y, rtol=0, atol=1e-12 * np.abs(Y).max())
+    L = philox.omega_block("gaussian", 11, np.arange(7), 0, n)           # the left-sketch stream
+    R = philox.omega_block("gaussian", 11, np.arange(7), 0, n, right=True)
+    assert not np.allclose(L, R)                                         # independent streams
