@@ -34,6 +34,10 @@ sys.path.insert(0, ROOT)
 CONFIGS = {
     "channel": dict(workload="channel-flow-shaped stream, 3 x 192 x 129 x 192 FP32, n=1000, blocks of 8",
                     nx=192, ny=129, nz=192, n=1000, b=8, k=100, s=403, h=50),
+    # the same stream with the optional m x l right sketch (l = 2k + 1; not part of the paper)
+    "channel_right": dict(workload="channel-flow-shaped stream, 3 x 192 x 129 x 192 FP32, n=1000, blocks of 8, "
+                                   "with the m x 201 right sketch", nx=192, ny=129, nz=192, n=1000, b=8, k=100,
+                          s=403, h=50, right_l=201),
     "channel_mid": dict(workload="channel-flow-shaped stream, 3 x 96 x 65 x 96 FP32, n=200, blocks of 8",
                         nx=96, ny=65, nz=96, n=200, b=8, k=100, s=403, h=50),
     "channel_small": dict(workload="channel-flow-shaped stream, 3 x 48 x 33 x 48 FP32, n=200, blocks of 8",
@@ -496,7 +500,8 @@ def main():
     st = torch.cuda.Stream(device=dev)
     gkw = dict(grad_dims=2, nx=cfg["N"], ny=cfg["N"], nfields=cfg["nfields"]) if grad else {}
     h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=args.sketch, n_max=n,
-                      seed=rank_seeds(rank)[1], stream=st, defer=True, group_max=args.group, **gkw)
+                      seed=rank_seeds(rank)[1], stream=st, defer=True, group_max=args.group,
+                      right_l=cfg.get("right_l", 0), **gkw)
     Jd = torch.empty(cfg["k"], dtype=torch.int64, device=dev)
     Pd = torch.empty((n, cfg["k"]), dtype=torch.float64, device=dev)
 
@@ -575,6 +580,48 @@ def main():
     iso_ms = iso_ms_tot[0] / max(int(iso_grp[0]), 1)
 
     h.close()
+
+    # The optional right sketch: its kernels timed alone, as the difference between ingesting one
+    # group of G columns with and without it (CUDA events on the handle's stream, 5 repetitions)
+    right = None
+    if cfg.get("right_l", 0) > 0:
+        rl = cfg["right_l"]
+
+        def group_ms(l):
+            hr = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=args.sketch, n_max=n,
+                               seed=rank_seeds(rank)[1], stream=st, defer=True, group_max=args.group, right_l=l)
+            hr.ingest(X[:G])
+            hr.sync()
+            tot = 0.0
+            for _ in range(5):
+                hr.reset()
+                torch.cuda.synchronize()
+                r0 = torch.cuda.Event(enable_timing=True)
+                r1 = torch.cuda.Event(enable_timing=True)
+                r0.record(st)
+                hr.ingest(X[:G])
+                hr.sync()
+                r1.record(st)
+                torch.cuda.synchronize()
+                tot += r0.elapsed_time(r1)
+            hr.close()
+            return tot / 5
+        r_ms = group_ms(rl) - group_ms(0)
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        pk0 = peaks()
+        fma_peak = nsm * 128 * float(pk0.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12     # FP32 TFMA/s
+        r_bytes = 2.0 * 4 * m * rl + 4.0 * m * G                                       # Y read + write, A read
+        r_fma = float(m) * rl * G
+        right = {"bound": "alu", "kernel": "right_sketch_kernel", "cols_per_launch": G, "l": rl,
+                 "avg_launch_ms": r_ms, "achieved": r_fma / (r_ms / 1e3) / 1e12, "peak": fma_peak,
+                 "unit": "TFMA/s", "frac": r_fma / (r_ms / 1e3) / 1e12 / fma_peak,
+                 "hbm": {"achieved": r_bytes / (r_ms / 1e3) / 1e9, "peak": pk0.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": r_bytes / (r_ms / 1e3) / 1e9 / pk0.get("hbm_gbs")},
+                 "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x {pk0.get('sm_max_mhz', 2070.0)} MHz "
+                                "(FP32 FMA); HBM: measured (MEASURED_PEAKS.json)",
+                 "note": "Y += A_group W over m x l: l FMAs per coordinate and column (FP32 pipe) against "
+                         "2 x 4 m l bytes of Y per group; timed alone as the difference between one group "
+                         "ingested with and without the right sketch"}
 
     # The same stream through the other sketch precisions, for the accuracy-throughput comparison
     # (one warm-up and one timed pass each; the plain FP32 form runs on the FP32 pipe)
@@ -662,6 +709,10 @@ def main():
         "clocks": clk.summary(),
         "accuracy": accuracy,
     }
+    if right is not None:
+        line["ingest_roofline"] = line["roofline"]
+        line["roofline"] = right
+        line["config"]["right_l"] = cfg["right_l"]
     if args.sketch == "native":
         # The native-precision sketch runs on the FP32 pipe: one signed add per (row, coordinate,
         # column) of the s + h sketch rows.  Peak: SMs x 128 FP32 lanes x the maximum SM clock.

@@ -81,6 +81,8 @@ typedef struct rid_config {
   int32_t group_max;     /* columns sketched per launch (1..64; 0 = 64 on tensor cores, 16 otherwise) */
   int32_t defer_device_input; /* 1: device columns are read later, in groups (see rid_ingest) */
   void* cuda_stream;     /* cudaStream_t to run on; NULL = default stream */
+  int32_t right_l;       /* columns l of the optional right sketch Y = sum_j a_j omega_j^T
+                            (m x l, data dtype; not part of the paper's method); 0 = off */
 } rid_config;
 
 typedef struct rid_handle rid_handle;
@@ -95,7 +97,7 @@ int rid_config_default(rid_config* cfg);
  * 1 <= k <= 1024, k < s <= 4096, 0 <= h <= 1024, h == 0 or h >= 3,
  * 0 < c1 < c2, c1 + c2 < 1, unknown enum values; gradient mode: grad_dims
  * must be 0 or 2, and with 2: nx, ny >= 2, nfields >= 1, m = nx ny nfields,
- * sketch_prec NATIVE), RID_ENOMEM, RID_ENOLIB.
+ * sketch_prec NATIVE; 0 <= right_l <= 4096), RID_ENOMEM, RID_ENOLIB.
  * Gradient mode (Sec. 3.4, Eqs. 38-43): the ridge scores and lambda use the
  * sketch of [a; G a], i.e. Omega a + Omega_g (G a) with an independent Omega_g
  * (s x 2m), and ||a||^2 + ||G a||^2; G is the least-squares gradient on each
@@ -154,6 +156,14 @@ int64_t rid_n_obs(const rid_handle* h);
 /* Copy the current basis columns A(:,J) (m x t, data dtype, ld >= m; empty
  * slots are written as zeros) to out (device or host).  Synchronizes. */
 int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device);
+
+/* Copy the optional right sketch Y = sum_{j < n_obs} a_j omega_j^T (m x right_l, data dtype,
+ * column-major, ld >= m) to out (device or host).  omega_j holds right_l unit-variance entries
+ * of the configured kind (Rademacher or Gaussian) drawn from their own Philox stream keyed by
+ * the snapshot index j; Y is updated once per group of ingested columns.  Not part of the
+ * paper's method (a running sketch of the stream's range).  Synchronizes.  Errors:
+ * RID_EINVAL (NULL out, ld < m), RID_ESTATE (right_l = 0), RID_ECUDA. */
+int rid_get_right_sketch(rid_handle* h, void* out, int64_t ld, int32_t on_device);
 
 /* Internal state for tests (host output, synchronizes):
  *  RID_STATE_SKETCH   : (s+h) x n_obs doubles, Omega A_obs (unit-variance rows)

@@ -88,7 +88,7 @@ void free_all(Dev& d, void* staging) {
   void* ptrs[] = {d.pool, d.omegaT, d.omegagT, d.S, d.SSt, d.fro2, d.JC, d.JC_prev, d.slotC,
                   d.slotC_prev, d.dslot /* 2t: both batch lists */, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
                   d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
-                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, staging};
+                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, d.Y, d.Wr, staging};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
 }
@@ -259,6 +259,12 @@ int flush(rid_handle* h) {
       nk1 += 1;
     }
   }
+  // the optional right sketch over the same columns (not part of the paper's method)
+  if (db.right_l > 0) {
+    const int nr = rid::launch_right_sketch(db, h->pend.data(), G, h->n_obs, h->st);
+    if (nr < 0) return fail(h, RID_ECUDA, "right-sketch launch failed");
+    nk1 += nr;
+  }
   if (h->prof) {
     cudaEventRecord(ev[2], h->st);
     h->spans[0].push_back({ev[0], ev[1]});
@@ -322,6 +328,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
     if (c->s + c->h > 512) return fail(h, RID_EINVAL, "BF16 sketches support s + h <= 512");
   }
   if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
+  if (c->right_l < 0 || c->right_l > 4096) return fail(h, RID_EINVAL, "right_l must be in [0, 4096]");
   if (c->grad_dims != 0) {
     if (c->grad_dims != 2) return fail(h, RID_EINVAL, "grad_dims must be 0 or 2 (2-D grids)");
     if (c->nx < 2 || c->ny < 2 || c->nfields < 1)
@@ -369,6 +376,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
   d.ny = c->ny;
   d.nfields = c->nfields;
   d.lev_ld = d.grad ? d.s : d.rows;     // gradient mode: a separate s x n leverage sketch
+  d.right_l = c->right_l;
   const int64_t nchunks = (d.m + rid::kChunk - 1) / rid::kChunk;
   d.n_sketch_blocks = (int)(nchunks < 4 * h->n_sm ? nchunks : 4 * h->n_sm);
   int64_t gs = (d.m + 16383) / 16384;
@@ -445,6 +453,15 @@ int rid_init(rid_handle** out, const rid_config* c) {
   AL(d.npart, (size_t)d.n_sketch_blocks * rid::kMaxB);
   AL(d.err, 1);
   AL(d.gbar, 8);
+  if (d.right_l > 0) {
+    char* y = nullptr;
+    char* wr = nullptr;
+    AL(y, (size_t)d.m_pad * d.right_l * h->esize);
+    AL(wr, rid::right_w_bytes(d));
+    d.Y = y;
+    d.Wr = wr;
+    if (cudaMemset(d.Y, 0, (size_t)d.m_pad * d.right_l * h->esize) != cudaSuccess) { rc = RID_ECUDA; goto fail_alloc; }
+  }
   d.gbar2 = d.gbar + 4;
   d.n_sm = h->n_sm;
   d.work_len = rid::work_doubles(d);
@@ -624,6 +641,22 @@ int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device) {
   return RID_OK;
 }
 
+int rid_get_right_sketch(rid_handle* h, void* out, int64_t ld, int32_t on_device) {
+  if (!h || !out) return RID_EINVAL;
+  if (h->d.right_l <= 0) return fail(h, RID_ESTATE, "no right sketch (right_l = 0)");
+  if (ld < h->d.m) return fail(h, RID_EINVAL, "ld < m");
+  {
+    const int rc = flush(h);
+    if (rc != RID_OK) return rc;
+  }
+  join(h);
+  const size_t es = h->esize;
+  CK(cudaMemcpy2DAsync(out, es * (size_t)ld, h->d.Y, es * (size_t)h->d.m_pad, es * (size_t)h->d.m,
+                       (size_t)h->d.right_l, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RID_OK;
+}
+
 int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
   if (!h || !out) return RID_EINVAL;
   {
@@ -694,7 +727,7 @@ bool same_config(const rid_config& a, const rid_config& b) {
          a.c1 == b.c1 && a.c2 == b.c2 && a.eps == b.eps && a.delta == b.delta && a.c_const == b.c_const &&
          a.lambda_fixed == b.lambda_fixed && a.omega_kind == b.omega_kind && a.data_dtype == b.data_dtype &&
          a.sketch_prec == b.sketch_prec && a.grad_dims == b.grad_dims && a.nx == b.nx && a.ny == b.ny &&
-         a.nfields == b.nfields && a.seed == b.seed;
+         a.nfields == b.nfields && a.seed == b.seed && a.right_l == b.right_l;
 }
 
 struct CkptPlan {
@@ -721,6 +754,7 @@ int ckpt_plan(rid_handle* h, CkptPlan& pl) {
       {d.Gp, sizeof(double) * (size_t)d.npool * d.npool},
   };
   if (d.grad) pl.arrays.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
+  if (d.right_l > 0) pl.arrays.push_back({d.Y, (size_t)d.m_pad * d.right_l * h->esize});
   std::vector<int> slotc(t), dsl(2 * (size_t)t);
   CK(cudaMemcpyAsync(slotc.data(), d.slotC, sizeof(int) * t, cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(dsl.data(), h->dslot_buf, sizeof(int) * 2 * t, cudaMemcpyDeviceToHost, h->st));
@@ -821,6 +855,7 @@ int rid_restore(rid_handle* h, const void* buf, int64_t bytes) {
         {d.Gp, sizeof(double) * (size_t)d.npool * d.npool},
     };
     if (d.grad) pl.arrays.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
+    if (d.right_l > 0) pl.arrays.push_back({d.Y, (size_t)d.m_pad * d.right_l * h->esize});
   }
   size_t need = head;
   for (auto& a : pl.arrays) need += a.second;
@@ -883,6 +918,7 @@ int rid_reset(rid_handle* h) {
   join(h);
   const int nk = rid::launch_reset_state(h->d, h->st);
   if (h->prof) h->kernels[1] += nk;
+  if (h->d.right_l > 0) CK(cudaMemsetAsync(h->d.Y, 0, (size_t)h->d.m_pad * h->d.right_l * h->esize, h->st));
   CK(cudaGetLastError());
   h->pend.clear();
   h->count = 0;

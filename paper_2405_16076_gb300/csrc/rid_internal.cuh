@@ -83,6 +83,9 @@ struct Dev {
   int n_sketch_blocks;
   int gram_split;
   int64_t work_len;
+  int right_l;                    // columns of the optional right sketch (0: off)
+  void* Y;                        // right sketch, m_pad x right_l, data dtype
+  void* Wr;                       // the group's right-sketch vectors (see right.cu)
 };
 
 // meta[] indices
@@ -119,6 +122,9 @@ int launch_ingest(const Dev& d, const void* const* cols, int nb, int count, int6
 // Gradient mode (Sec. 3.4): the leverage sketch of nb columns given by pointer, after their
 // sketch has been reduced; returns the number of kernels launched.
 int launch_grad(const Dev& d, const void* const* cols, int nb, int64_t n_obs, cudaStream_t st);
+// Optional right sketch Y += sum_q a_q omega_{j0+q}^T over ncols ingested columns (right.cu).
+int launch_right_sketch(const Dev& d, const void* const* cols, int ncols, int64_t j0, cudaStream_t st);
+size_t right_w_bytes(const Dev& d);
 // SS^T update for nb new columns (shared by both ingest paths).
 void launch_gram_update(const Dev& d, int nb, int64_t n_obs, cudaStream_t st);
 

@@ -33,7 +33,7 @@ class rid_config(ctypes.Structure):
         ("sketch_prec", ctypes.c_int32), ("grad_dims", ctypes.c_int32), ("nx", ctypes.c_int32),
         ("ny", ctypes.c_int32), ("nfields", ctypes.c_int32), ("n_max", ctypes.c_int64),
         ("seed", ctypes.c_uint64), ("group_max", ctypes.c_int32), ("defer_device_input", ctypes.c_int32),
-        ("cuda_stream", ctypes.c_void_p),
+        ("cuda_stream", ctypes.c_void_p), ("right_l", ctypes.c_int32),
     ]
 
 
@@ -57,6 +57,7 @@ def _load():
         "rid_error_estimate": (ctypes.c_int, [H, P, P, P]),
         "rid_n_obs": (ctypes.c_int64, [H]),
         "rid_get_basis": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32]),
+        "rid_get_right_sketch": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32]),
         "rid_get_state": (ctypes.c_int, [H, ctypes.c_int32, P, ctypes.c_int64]),
         "rid_sync": (ctypes.c_int, [H]),
         "rid_profile": (ctypes.c_int, [H, ctypes.c_int32]),
@@ -87,6 +88,7 @@ rid_finalize = lib.rid_finalize
 rid_error_estimate = lib.rid_error_estimate
 rid_n_obs = lib.rid_n_obs
 rid_get_basis = lib.rid_get_basis
+rid_get_right_sketch = lib.rid_get_right_sketch
 rid_get_state = lib.rid_get_state
 rid_sync = lib.rid_sync
 rid_profile = lib.rid_profile
@@ -143,7 +145,7 @@ class OnlineRID:
     def __init__(self, m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
                  lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
                  sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
-                 grad_dims=0, nx=0, ny=0, nfields=1):
+                 grad_dims=0, nx=0, ny=0, nfields=1, right_l=0):
         cfg = rid_config()
         _check(rid_config_default(ctypes.byref(cfg)))
         cfg.m, cfg.k, cfg.s, cfg.h = int(m), int(k), int(s), int(h)
@@ -158,6 +160,7 @@ class OnlineRID:
         cfg.group_max = int(group_max)
         cfg.defer_device_input = 1 if defer else 0
         cfg.grad_dims, cfg.nx, cfg.ny, cfg.nfields = int(grad_dims), int(nx), int(ny), int(nfields)
+        cfg.right_l = int(right_l)
         cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         self.cfg = cfg
         self.t = int(k)
@@ -266,6 +269,17 @@ class OnlineRID:
         out = np.zeros((self.t, self.m), dtype=self.np_dtype)
         _check(rid_get_basis(self.h, ctypes.c_void_p(out.ctypes.data), self.m, 0), self.h)
         return out.T.copy()
+
+    def right_sketch(self):
+        """The optional right sketch Y (m x right_l, data dtype) on the host."""
+        l = int(self.cfg.right_l)
+        out = np.zeros((l, self.m), dtype=self.np_dtype)      # row r = column r of Y
+        _check(rid_get_right_sketch(self.h, ctypes.c_void_p(out.ctypes.data), self.m, 0), self.h)
+        return out.T.copy()
+
+    def right_sketch_device(self, out):
+        """Copy Y into a device tensor of shape (right_l, m) (row r = column r of Y)."""
+        _check(rid_get_right_sketch(self.h, ctypes.c_void_p(out.data_ptr()), out.stride(0), 1), self.h)
 
     def finalize_device(self, J, P):
         """Finalize into device tensors: J (t,) int64 and P (n, t) float64 (row j = column j)."""
