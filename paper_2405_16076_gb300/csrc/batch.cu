@@ -23,9 +23,13 @@ struct WorkLayout {
   int64_t SJ, HJ, G, Gq, Gc, T;           // gathered sketch data and Grams
   int64_t QR4, b4, h4, r4, QR6, b6, h6, r6;   // Householder factors (r: diagonal of R)
   int64_t Lcinv, r4inv, r6inv;            // reciprocal diagonals of the triangular factors
+  int64_t Q4x, Q6x, M6;                   // explicit thin Q factors (s x t) and Q6^T (Omega A_J) (t x t)
   int64_t Z, trgpp, hut, hut_stride;      // Hutch++
   int64_t total;
 };
+
+// Per-warp scratch of the apply / coefficient kernels: an s-vector, or two t-vectors.
+__host__ __device__ inline int64_t vec_stride(int64_t s, int64_t t) { return s > 2 * t ? s : 2 * t; }
 
 static constexpr int kApplyBlocks = 2 * 152;
 static constexpr int kApplyThreads = 256;
@@ -48,12 +52,13 @@ static WorkLayout layout(const Dev& d) {
   w.eigP = take(2 * s);
   w.beta = take(s); w.vhead = take(s); w.mu = take(t); w.ldld = take(s); w.ldll = take(s);
   w.unif = take(t * (t + 1));
-  w.vec = take(nw * (s > t ? s : t));
+  w.vec = take(nw * vec_stride(s, t));
   w.SJ = take(s * t); w.HJ = take(hh * t); w.G = take(t * t); w.Gq = take(t * t);
   w.Gc = take(t * t); w.T = take(t * t);
   w.QR4 = take(s * t); w.b4 = take(t); w.h4 = take(t); w.r4 = take(t);
   w.QR6 = take(s * t); w.b6 = take(t); w.h6 = take(t); w.r6 = take(t);
   w.Lcinv = take(t); w.r4inv = take(t); w.r6inv = take(t);
+  w.Q4x = take(s * t); w.Q6x = take(s * t); w.M6 = take(t * t);
   w.Z = take(4 * hh * t); w.trgpp = take(4);
   w.hut_stride = hut_stride(d);
   w.hut = take(4 * w.hut_stride);
@@ -420,7 +425,100 @@ __global__ void tsolve_kernel(Dev d, WorkLayout w) {
   }
 }
 
-// ---------------------------------------------------------------- Algorithms 4-7, one warp per column
+// ---------------------------------------------------------------- Algorithms 4-7
+// The Householder QR factors of Omega A_J (QR4) and of its new columns (QR6) are turned into
+// explicit thin Q factors once per batch step, so that the per-column work is two small GEMMs
+// over all observed columns plus triangular arithmetic:
+//   Z4 = Q4^T S~, Z6 = Q6^T S~ (S~ = Omega A_obs / sqrt(s)), M6 = Q6^T (Omega A_J) / sqrt(s);
+//   Algorithm 4: P4(:, j) = R4^{-1} Z4(:, j);
+//   Algorithm 5: (Omega A_J)^T s~_j = R4^T Q4^T s~_j = R4^T Z4(:, j), then G^{-1} (Cholesky);
+//   Algorithm 6: Q6^T (s~_j - (Omega A_J)_kept p_j) = Z6(:, j) - M6_kept p_j, then R6^{-1}.
+// Equal in exact arithmetic to applying the reflectors to every column (the products carry the
+// same rounding order of magnitude), with about half of the FP64 operations.
+
+// Explicit thin Q (s x n) of a Householder factorization: column c = H_0 ... H_c e_c (the
+// reflectors after c leave e_c unchanged), one warp per column; Q4 columns first, then Q6.
+__global__ void __launch_bounds__(256) qform_kernel(Dev d, WorkLayout w) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int s = d.s, t = d.t;
+  const int na = d.meta[META_NACT], nn = d.meta[META_NNEW];
+  if (gw >= na + nn) return;
+  const bool six = gw >= na;
+  const int c = six ? gw - na : gw;
+  const double* QR = d.work + (six ? w.QR6 : w.QR4);
+  const double* beta = d.work + (six ? w.b6 : w.b4);
+  const double* vhead = d.work + (six ? w.h6 : w.h4);
+  double* x = d.work + w.vec + (size_t)gw * vec_stride(s, t);
+  for (int i = lane; i < s; i += 32) x[i] = (i == c) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int j = c; j >= 0; --j) {
+    const double bj = beta[j];
+    if (bj == 0.0) continue;
+    const double* v = QR + (size_t)j * s;
+    const double vh = vhead[j];
+    double dot = (lane == 0) ? vh * x[j] : 0.0;
+    for (int i = j + 1 + lane; i < s; i += 32) dot += v[i] * x[i];
+    dot = warp_sum(dot);
+    const double f = bj * dot;
+    __syncwarp();
+    if (lane == 0) x[j] -= f * vh;
+    for (int i = j + 1 + lane; i < s; i += 32) x[i] -= f * v[i];
+    __syncwarp();
+  }
+  double* Q = d.work + (six ? w.Q6x : w.Q4x) + (size_t)c * s;
+  for (int i = lane; i < s; i += 32) Q[i] = x[i];
+}
+
+// C(0:M, 0:N) = Q^T B over K = s rows, in 32 x 32 output tiles (256 threads, 4 outputs each):
+//   mode 0: Q = Q4 (M = n_act), B = S~ (N = n_obs), C = Z4;  mode 1: Q = Q6 (M = n_new),
+//   B = S~, C = Z6;  mode 2: Q = Q6, B = Omega A_J / sqrt(s) (N = n_act), C = M6.
+// Each output is one dot product in row order, i = 0 .. s-1.
+__global__ void __launch_bounds__(256) proj_gemm_kernel(Dev d, WorkLayout w, int mode, int64_t n_obs) {
+  __shared__ double Qs[32][33];
+  __shared__ double Bs[32][33];
+  const int s = d.s, t = d.t;
+  const int na = d.meta[META_NACT], nn = d.meta[META_NNEW];
+  const int M = mode == 0 ? na : nn;
+  const int64_t N = mode == 2 ? (int64_t)na : n_obs;
+  const int m0 = blockIdx.x * 32;
+  const int64_t n0 = (int64_t)blockIdx.y * 32;
+  if (m0 >= M || n0 >= N) return;
+  const double* Q = d.work + (mode == 0 ? w.Q4x : w.Q6x);
+  const double rs = 1.0 / sqrt((double)s);
+  double* C = mode == 0 ? d.zq : mode == 1 ? d.zq + (size_t)t * d.n_cap : d.work + w.M6;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;         // output column n0 + tx, rows m0 + ty + 8 u
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k0 = 0; k0 < s; k0 += 32) {
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
+      const int kk = idx & 31, cc = idx >> 5;
+      const int k = k0 + kk;
+      const int mq = m0 + cc;
+      const int64_t nb = n0 + cc;
+      Qs[cc][kk] = (k < s && mq < M) ? Q[k + (size_t)mq * s] : 0.0;
+      double bv = 0.0;
+      if (k < s && nb < N)
+        bv = mode == 2 ? d.work[w.SJ + k + (size_t)nb * s] : d.S[(size_t)nb * d.rows + k] * rs;
+      Bs[cc][kk] = bv;
+    }
+    __syncthreads();
+    const int kmax = (s - k0) < 32 ? (s - k0) : 32;
+    for (int kk = 0; kk < kmax; ++kk) {
+      const double bv = Bs[tx][kk];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(Qs[ty + 8 * u][kk], bv, acc[u]);
+    }
+    __syncthreads();
+  }
+  const int64_t nb = n0 + tx;
+  if (nb < N)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int mq = m0 + ty + 8 * u;
+      if (mq < M) C[mq + (size_t)nb * t] = acc[u];
+    }
+}
+
 __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout w, int64_t n_obs,
                                                               int64_t n_prev) {
   const int lane = threadIdx.x & 31;
@@ -428,13 +526,14 @@ __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout 
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int s = d.s, t = d.t;
   const int na = d.meta[META_NACT], npa = d.meta[META_NPACT];
-  const double rs = 1.0 / sqrt((double)s);
-  const double* SJ = d.work + w.SJ;
   const double* QR4 = d.work + w.QR4;
   const double* QR6 = d.work + w.QR6;
+  const double* r4 = d.work + w.r4;
+  const double* M6 = d.work + w.M6;
   const double* Gc = d.work + w.Gc;
   const double* T = d.work + w.T;
-  double* b = d.work + w.vec + (size_t)gw * (s > t ? s : t);
+  double* b = d.work + w.vec + (size_t)gw * vec_stride(s, t);
+  double* y = b + t;                                   // a second t-vector
   double* P4 = d.cand;
   double* P5 = d.cand + (size_t)t * d.n_cap;
   double* P6 = d.cand + 2 * (size_t)t * d.n_cap;
@@ -445,40 +544,55 @@ __global__ void __launch_bounds__(kApplyThreads) coeff_kernel(Dev d, WorkLayout 
   const double* lcinv = d.work + w.Lcinv;
   const int nn = d.meta[META_NNEW];
   for (int64_t j = gw; j < n_obs; j += nwarps) {
-    const double* sa = d.S + (size_t)j * d.rows;
-    // Algorithm 4 (Eq. 24): P4(:, j) = (Omega A_J)^+ Omega a_j via Householder QR
-    for (int i = lane; i < s; i += 32) b[i] = sa[i] * rs;
+    const double* z4 = d.zq + (size_t)j * t;
+    const double* z6 = d.zq + (size_t)t * d.n_cap + (size_t)j * t;
+    // Algorithm 5's right-hand side (Omega A_J)^T s~_j = R4^T z4 (lane per row, four partial sums)
+    for (int a = lane; a < na; a += 32) {
+      double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+      int c = 0;
+      for (; c + 4 <= a; c += 4) {
+        p0 += QR4[c + (size_t)a * s] * z4[c];
+        p1 += QR4[c + 1 + (size_t)a * s] * z4[c + 1];
+        p2 += QR4[c + 2 + (size_t)a * s] * z4[c + 2];
+        p3 += QR4[c + 3 + (size_t)a * s] * z4[c + 3];
+      }
+      for (; c < a; ++c) p0 += QR4[c + (size_t)a * s] * z4[c];
+      y[a] = ((p0 + p1) + (p2 + p3)) + r4[a] * z4[a];
+      b[a] = z4[a];
+    }
     __syncwarp();
-    warp_apply_qt(QR4, s, na, s, d.work + w.b4, d.work + w.h4, b);
+    // Algorithm 4 (Eq. 24): P4(:, j) = R4^{-1} Q4^T s~_j
     warp_trsv_upper_r(QR4, r4inv, na, s, b);
     for (int a = lane; a < na; a += 32) P4[a + (size_t)j * t] = b[a];
     __syncwarp();
-    // Algorithm 5: P5(:, j) = G^{-1} (Omega A_J)^T Omega a_j
-    for (int a = 0; a < na; ++a) {
-      double acc = 0.0;
-      for (int i = lane; i < s; i += 32) acc += SJ[i + (size_t)a * s] * sa[i] * rs;
-      acc = warp_sum(acc);
-      if (lane == 0) b[a] = acc;
-    }
-    __syncwarp();
-    warp_trsv_lower_r(Gc, lcinv, na, na, b);
-    warp_trsv_lower_t_r(Gc, lcinv, na, na, b);
-    for (int a = lane; a < na; a += 32) P5[a + (size_t)j * t] = b[a];
+    // Algorithm 5: P5(:, j) = G^{-1} (Omega A_J)^T s~_j
+    warp_trsv_lower_r(Gc, lcinv, na, na, y);
+    warp_trsv_lower_t_r(Gc, lcinv, na, na, y);
+    for (int a = lane; a < na; a += 32) P5[a + (size_t)j * t] = y[a];
     __syncwarp();
     // Algorithm 6 (Eqs. 27-30): keep the rows of unchanged basis elements, refit the new
-    // ones on the sketched residual.  Previous coefficients of columns observed since the
-    // last batch step are the preliminary estimate P4.
-    for (int i = lane; i < s; i += 32) {
-      double r = sa[i] * rs;
-      for (int a = 0; a < na; ++a) {
-        if (d.isnew[a]) continue;
-        const double pp = (j < n_prev) ? d.P[d.act[a] + (size_t)j * t] : P4[a + (size_t)j * t];
-        r -= SJ[i + (size_t)a * s] * pp;
+    // ones on the sketched residual, Q6^T r = z6 - M6_kept p.  Previous coefficients of
+    // columns observed since the last batch step are the preliminary estimate P4.
+    for (int c = lane; c < nn; c += 32) {
+      double p0 = 0.0, p1 = 0.0;
+      int a = 0;
+      for (; a + 2 <= na; a += 2) {
+        if (!d.isnew[a]) {
+          const double pp = (j < n_prev) ? d.P[d.act[a] + (size_t)j * t] : P4[a + (size_t)j * t];
+          p0 += M6[c + (size_t)a * t] * pp;
+        }
+        if (!d.isnew[a + 1]) {
+          const double pp = (j < n_prev) ? d.P[d.act[a + 1] + (size_t)j * t] : P4[a + 1 + (size_t)j * t];
+          p1 += M6[c + (size_t)(a + 1) * t] * pp;
+        }
       }
-      b[i] = r;
+      if (a < na && !d.isnew[a]) {
+        const double pp = (j < n_prev) ? d.P[d.act[a] + (size_t)j * t] : P4[a + (size_t)j * t];
+        p0 += M6[c + (size_t)a * t] * pp;
+      }
+      b[c] = z6[c] - (p0 + p1);
     }
     __syncwarp();
-    warp_apply_qt(QR6, s, nn, s, d.work + w.b6, d.work + w.h6, b);
     warp_trsv_upper_r(QR6, r6inv, nn, s, b);
     if (lane == 0) {
       int c = 0;
@@ -837,7 +951,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   const WorkLayout w = layout(d);
   const int64_t jd0 = n_obs - count;
   int nk = launch_scores(d, count, jd0, d.work, w.eigR, w.beta, w.vhead, w.ldld, w.ldll, w.vec,
-                         (d.s > d.t ? d.s : d.t), st);
+                         (int)vec_stride(d.s, d.t), st);
   if (ev_scores) cudaEventRecord(ev_scores, st);
   const int nu = d.t * (count + 1);
   uniforms_kernel<<<(nu + 255) / 256, 256, 0, st>>>(d, d.work + w.unif, count, batch);
@@ -881,6 +995,13 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
                       d.work + w.b6, d.work + w.h6, d.work + w.r6, d.gbar2, st))
     return 0;
   qr_prep_kernel<<<1, 256, 0, st>>>(d, w);
+  qform_kernel<<<(2 * d.t + 7) / 8, 256, 0, st>>>(d, w);
+  {
+    const unsigned gm = (unsigned)((d.t + 31) / 32);
+    proj_gemm_kernel<<<dim3(gm, (unsigned)((n_obs + 31) / 32)), 256, 0, st>>>(d, w, 0, n_obs);
+    proj_gemm_kernel<<<dim3(gm, (unsigned)((n_obs + 31) / 32)), 256, 0, st>>>(d, w, 1, n_obs);
+    proj_gemm_kernel<<<dim3(gm, gm), 256, 0, st>>>(d, w, 2, n_obs);
+  }
   cudaStreamWaitEvent(st, ev_gram, 0);
   coeff_kernel<<<kApplyBlocks, kApplyThreads, 0, st>>>(d, w, n_obs, n_prev);
   const int nchunk = (int)((n_obs + kHutChunk - 1) / kHutChunk);
@@ -895,7 +1016,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   }
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
-  return nk + 14 + ngk;
+  return nk + 18 + ngk;
 }
 
 }  // namespace rid

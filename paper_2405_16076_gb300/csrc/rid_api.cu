@@ -88,7 +88,7 @@ void free_all(Dev& d, void* staging) {
   void* ptrs[] = {d.pool, d.omegaT, d.omegagT, d.S, d.SSt, d.fro2, d.JC, d.JC_prev, d.slotC,
                   d.slotC_prev, d.dslot /* 2t: both batch lists */, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
                   d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
-                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, d.Y, d.Wr, staging};
+                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, d.Y, d.Wr, d.zq, staging};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
 }
@@ -133,12 +133,13 @@ int grow(rid_handle* h, int64_t need) {
   while (cap < need) cap *= 2;
   join(h);
   CK(cudaStreamSynchronize(h->st));
-  double *S, *Slev = nullptr, *P, *cand, *hpart;
+  double *S, *Slev = nullptr, *P, *cand, *hpart, *zq;
   CK(dalloc(&S, (size_t)d.rows * cap));
   if (d.grad) CK(dalloc(&Slev, (size_t)d.s * cap));
   CK(dalloc(&P, (size_t)d.t * cap));
   CK(dalloc(&cand, (size_t)4 * d.t * cap));
   CK(dalloc(&hpart, (size_t)hpart_len(d, cap)));
+  CK(dalloc(&zq, (size_t)2 * d.t * cap));
   CK(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)d.t * cap, h->st));
   CK(cudaMemsetAsync(cand, 0, sizeof(double) * (size_t)4 * d.t * cap, h->st));
   if (d.S) {
@@ -151,12 +152,14 @@ int grow(rid_handle* h, int64_t need) {
     cudaFree(d.P);
     cudaFree(d.cand);
     cudaFree(d.hpart);
+    cudaFree(d.zq);
   }
   d.S = S;
   d.Slev = d.grad ? Slev : S;
   d.P = P;
   d.cand = cand;
   d.hpart = hpart;
+  d.zq = zq;
   d.n_cap = cap;
   return RID_OK;
 }

@@ -69,6 +69,7 @@ struct Dev {
   double* gpart;                  // gram split-K partials
   double* P;                      // t x n_cap
   double* cand;                   // 4 x t x n_cap
+  double* zq;                     // 2 x t x n_cap: Q4^T (Omega A_obs) and Q6^T (Omega A_obs) / sqrt(s)
   double* work;                   // linear-algebra scratch
   double* hpart;                  // Hutch++ partials
   double* spart;                  // sketch partials
