@@ -18,6 +18,9 @@ namespace rid {
 struct WorkLayout {
   int64_t eigA, eigR, eigD, eigE, eigV, eigP;   // tridiagonalization of the sketch Gram
   int64_t beta, vhead, mu, ldld, ldll;    // reflectors, top-k eigenvalues, LDL^T of T + lambda I
+  // what the scores read (reflectors, LDL^T) has a second copy: batch b uses copy b % 2, so
+  // that the lambda part of batch b+1 may run while the scores of batch b still read theirs
+  int64_t eigR2, beta2, vhead2, ldld2, ldll2;
   int64_t unif;                           // uniforms of the prune/refill decisions
   int64_t vec;                            // per-warp vectors (scores / applies)
   int64_t SJ, HJ, G, Gq, Gc, T;           // gathered sketch data and Grams
@@ -51,6 +54,7 @@ static WorkLayout layout(const Dev& d) {
   w.eigA = take(s * s); w.eigR = take(s * s); w.eigD = take(s); w.eigE = take(s); w.eigV = take(s);
   w.eigP = take(2 * s);
   w.beta = take(s); w.vhead = take(s); w.mu = take(t); w.ldld = take(s); w.ldll = take(s);
+  w.eigR2 = take(s * s); w.beta2 = take(s); w.vhead2 = take(s); w.ldld2 = take(s); w.ldll2 = take(s);
   w.unif = take(t * (t + 1));
   w.vec = take(nw * vec_stride(s, t));
   w.SJ = take(s * t); w.HJ = take(hh * t); w.G = take(t * t); w.Gq = take(t * t);
@@ -941,8 +945,10 @@ int launch_reset_state(const Dev& d, cudaStream_t st) {
 
 int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st) {
   const WorkLayout w = layout(d);
-  return launch_lambda(d, batch, d.work, w.eigA, w.eigR, w.eigD, w.eigE, w.beta, w.vhead, w.eigP, w.mu, w.ldld,
-                       w.ldll, d.gbar, d.n_sm, st);
+  const bool odd = batch & 1;
+  return launch_lambda(d, batch, d.work, w.eigA, odd ? w.eigR2 : w.eigR, w.eigD, w.eigE, odd ? w.beta2 : w.beta,
+                       odd ? w.vhead2 : w.vhead, w.eigP, w.mu, odd ? w.ldld2 : w.ldld, odd ? w.ldll2 : w.ldll,
+                       d.gbar, d.n_sm, st);
 }
 
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
@@ -950,7 +956,9 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
                       cudaEvent_t ev_fork, cudaEvent_t ev_gram) {
   const WorkLayout w = layout(d);
   const int64_t jd0 = n_obs - count;
-  int nk = launch_scores(d, count, jd0, d.work, w.eigR, w.beta, w.vhead, w.ldld, w.ldll, w.vec,
+  const bool odd = batch & 1;
+  int nk = launch_scores(d, count, jd0, d.work, odd ? w.eigR2 : w.eigR, odd ? w.beta2 : w.beta,
+                         odd ? w.vhead2 : w.vhead, odd ? w.ldld2 : w.ldld, odd ? w.ldll2 : w.ldll, w.vec,
                          (int)vec_stride(d.s, d.t), st);
   if (ev_scores) cudaEventRecord(ev_scores, st);
   const int nu = d.t * (count + 1);

@@ -175,8 +175,8 @@ cudaEvent_t next_event(rid_handle* h) {
 
 // Batch step b.  The caller's stream snapshots SS^T and ||A||^2 (buffer b % 2, free once
 // the lambda part of step b-2 has run) and goes on ingesting; the lambda part runs on the
-// lambda stream from the snapshot (after step b-1's scores have read the previous lambda
-// part's outputs); the tail runs on the batch stream after it.
+// lambda stream from the snapshot into output copy b % 2 (after step b-2's scores have read
+// that copy); the tail runs on the batch stream after it.
 int run_batch(rid_handle* h) {
   const int b = h->batch;
   const Dev db = dev_for(h, b);
@@ -189,7 +189,8 @@ int run_batch(rid_handle* h) {
   CK(cudaMemcpyAsync(snap + ss, db.fro2, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   CK(cudaEventRecord(h->ev_snap, h->st));
   CK(cudaStreamWaitEvent(h->stl, h->ev_snap, 0));
-  if (b >= 1) CK(cudaStreamWaitEvent(h->stl, h->ev_scores[(b - 1) & 1], 0));
+  // the lambda outputs of batch b share their copy (b % 2) with the scores of batch b-2
+  if (b >= 2) CK(cudaStreamWaitEvent(h->stl, h->ev_scores[b & 1], 0));
   Dev dl = db;
   dl.SSt = snap;
   dl.fro2 = snap + ss;
