@@ -138,9 +138,16 @@ int rid_batch_ingest(rid_handle* const* hs, int32_t nh, const void* const* cols,
 /* End the stream: run the batch step over the count < t buffered columns, if
  * any (tail batch).  Then, if J_out != NULL, write the t basis indices
  * (int64, -1 = empty slot) and, if P_out != NULL, the t x n coefficient matrix
- * (double, column-major, ldp >= t).  on_device selects device or host output
- * pointers.  Synchronizes the stream.  May be called again to re-read the
- * result.  Errors: RID_EINVAL (ldp < t), RID_ENONFINITE, RID_ECUDA. */
+ * (double, column-major, ldp >= t).  on_device: 0 = host output pointers,
+ * 1 = device output pointers; both synchronize the stream and report device
+ * errors.  RID_OUT_DEVICE_ASYNC = device output pointers without any host
+ * synchronization: the copies are queued on the handle's stream, device errors
+ * surface at the next synchronizing call (rid_sync), and the call may be
+ * captured into a CUDA graph together with rid_reset and rid_ingest of device
+ * columns (with n_max large enough that no capacity growth is needed).  May be
+ * called again to re-read the result.  Errors: RID_EINVAL (ldp < t),
+ * RID_ENONFINITE, RID_ECUDA. */
+enum { RID_OUT_HOST = 0, RID_OUT_DEVICE = 1, RID_OUT_DEVICE_ASYNC = 2 };
 int rid_finalize(rid_handle* h, int64_t* J_out, double* P_out, int64_t ldp, int32_t on_device);
 
 /* Estimates from the last batch step (Algorithm 8): est_sq[0] = chosen

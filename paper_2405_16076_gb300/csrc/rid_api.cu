@@ -35,6 +35,7 @@ struct rid_handle {
   int64_t n_prev;     // columns covered by the last batch step
   int batch;          // batch steps run
   bool finalized;
+  bool joined;            // the caller's stream already waits for every batch step issued
   size_t esize;
   void* staging;          // host-input staging area: group_max columns of m_pad
   std::vector<const void*> pend;   // columns recorded but not yet sketched
@@ -116,8 +117,12 @@ Dev dev_for(const rid_handle* h, int b) {
 
 // Make the caller's stream wait for the tail of the latest batch step (after this, work on
 // h->st and a synchronization of h->st cover everything the handle has launched).
+// Make the caller's stream wait for the last batch step (once per batch step issued: a handle
+// whose stream already waits -- e.g. after an asynchronous finalize captured into a CUDA graph,
+// whose events must not be waited on outside the graph -- adds no second wait).
 void join(rid_handle* h) {
-  if (h->batch >= 1) cudaStreamWaitEvent(h->st, h->ev_tail[(h->batch - 1) & 1], 0);
+  if (h->batch >= 1 && !h->joined) cudaStreamWaitEvent(h->st, h->ev_tail[(h->batch - 1) & 1], 0);
+  h->joined = true;
 }
 
 int64_t hpart_len(const Dev& d, int64_t ncap) {
@@ -179,6 +184,7 @@ cudaEvent_t next_event(rid_handle* h) {
 // that copy); the tail runs on the batch stream after it.
 int run_batch(rid_handle* h) {
   const int b = h->batch;
+  h->joined = false;
   const Dev db = dev_for(h, b);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->prof) { e0 = next_event(h); e1 = next_event(h); cudaEventRecord(e0, h->st); }
@@ -308,6 +314,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
   rid_handle* h = nullptr;
   if (!out || !c) return fail(h, RID_EINVAL, "NULL argument");
   *out = nullptr;
+  cudaGetLastError();                          // an error left by other code is not this handle's
   if (c->m < 1) return fail(h, RID_EINVAL, "m must be >= 1");
   if (c->k < 1 || c->k > 1024) return fail(h, RID_EINVAL, "k must be in [1, 1024]");
   if (c->s <= c->k || c->s > 4096) return fail(h, RID_EINVAL, "s must satisfy k < s <= 4096");
@@ -579,14 +586,19 @@ int rid_finalize(rid_handle* h, int64_t* J_out, double* P_out, int64_t ldp, int3
     }
   }
   h->finalized = true;
-  int rc = check_device_error(h);
-  if (rc != RID_OK) return rc;
+  const bool async = on_device == RID_OUT_DEVICE_ASYNC;
+  if (async) {
+    join(h);                                     // the batch streams rejoin the caller's stream
+  } else {
+    const int rc = check_device_error(h);
+    if (rc != RID_OK) return rc;
+  }
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (J_out) CK(cudaMemcpyAsync(J_out, h->d.JC, sizeof(int64_t) * t, kind, h->st));
   if (P_out && h->n_obs > 0)
     CK(cudaMemcpy2DAsync(P_out, sizeof(double) * ldp, h->d.P, sizeof(double) * t, sizeof(double) * t,
                          (size_t)h->n_obs, kind, h->st));
-  CK(cudaStreamSynchronize(h->st));
+  if (!async) CK(cudaStreamSynchronize(h->st));
   return RID_OK;
 }
 

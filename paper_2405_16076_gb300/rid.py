@@ -281,9 +281,13 @@ class OnlineRID:
         """Copy Y into a device tensor of shape (right_l, m) (row r = column r of Y)."""
         _check(rid_get_right_sketch(self.h, ctypes.c_void_p(out.data_ptr()), out.stride(0), 1), self.h)
 
-    def finalize_device(self, J, P):
-        """Finalize into device tensors: J (t,) int64 and P (n, t) float64 (row j = column j)."""
-        _check(rid_finalize(self.h, ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(P.data_ptr()), self.t, 1), self.h)
+    def finalize_device(self, J, P, sync=True):
+        """Finalize into device tensors: J (t,) int64 and P (n, t) float64 (row j = column j).
+
+        sync=False queues the copies without a host synchronization (RID_OUT_DEVICE_ASYNC), so
+        that reset / ingest / finalize can be captured into a CUDA graph."""
+        _check(rid_finalize(self.h, ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(P.data_ptr()), self.t,
+                            1 if sync else 2), self.h)
 
     def profile(self, enable=True):
         _check(rid_profile(self.h, 1 if enable else 0), self.h)

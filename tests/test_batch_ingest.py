@@ -67,3 +67,62 @@ def test_batch_ingest_rejects_null_handle():
     nc = (ctypes.c_int32 * 1)(1)
     hs = (ctypes.c_void_p * 1)(None)
     assert rid.rid_batch_ingest(hs, 1, cols, ld, nc, 1) == rid.RID_EINVAL
+
+
+@pytest.mark.gpu
+def test_graph_captured_streams_match_eager_runs():
+    """rid_reset, rid_batch_ingest of device columns and the asynchronous device finalize of
+    several streams, captured into one CUDA graph: every replay reproduces the eager run's J and
+    P exactly."""
+    import torch
+    from paper_2405_16076_gb300 import rid
+    specs = [(20000, 10, 70, 200), (35001, 5, 45, 201), (16384, 15, 61, 202)]
+    data = [ImagingStream(seed=seed, m=m, n=n, device="cuda").block(0, n) for (m, k, n, seed) in specs]
+    streams = [torch.cuda.Stream() for _ in specs]
+    hs = [rid.OnlineRID(m=m, k=k, s=4 * k + 3, h=30, dtype="f32", sketch="bf16x2", n_max=n, seed=seed,
+                        stream=st, defer=True) for (m, k, n, seed), st in zip(specs, streams)]
+    outs = [(torch.zeros(k, dtype=torch.int64, device="cuda"), torch.zeros((n, k), dtype=torch.float64, device="cuda"))
+            for (m, k, n, seed) in specs]
+    b = 8
+    nmax = max(n for (_, _, n, _) in specs)
+
+    def run(sync):
+        for hd in hs:
+            hd.reset()
+        for j0 in range(0, nmax, b):
+            sel = [(hd, X[j0:j0 + b]) for hd, X, (m, k, n, seed) in zip(hs, data, specs) if j0 < n]
+            rid.batch_ingest([x[0] for x in sel], [x[1] for x in sel])
+        for hd, (J, P) in zip(hs, outs):
+            hd.finalize_device(J, P, sync=sync)
+
+    run(True)
+    torch.cuda.synchronize()
+    ref = [(J.clone(), P.clone()) for J, P in outs]
+    for hd in hs:
+        hd.reset()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=cap, capture_error_mode="relaxed"):
+        fork = torch.cuda.Event()
+        fork.record(cap)
+        for st in streams:
+            st.wait_event(fork)
+        run(False)
+        for st in streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            cap.wait_event(e)
+    for _ in range(2):
+        for J, P in outs:
+            J.zero_()
+            P.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        for (J, P), (Jr, Pr) in zip(outs, ref):
+            assert torch.equal(J, Jr)
+            assert torch.equal(P, Pr)
+    for hd in hs:
+        hd.sync()                                  # no device error behind the replays
+        hd.close()
