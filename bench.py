@@ -334,17 +334,18 @@ def run_streams(args, cfg):
                 ev = torch.cuda.Event()
                 ev.record(st)
                 cap.wait_event(ev)
-        for _ in range(args.warmup):
-            graph.replay()
-        torch.cuda.synchronize()
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        with ClockSampler(0) as clk:
-            g0.record(cap)
-            for _ in range(args.steps):
+        with torch.cuda.stream(cap):                # replays run on the current stream
+            for _ in range(args.warmup):
                 graph.replay()
-            g1.record(cap)
             torch.cuda.synchronize()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            with ClockSampler(0) as clk:
+                g0.record(cap)
+                for _ in range(args.steps):
+                    graph.replay()
+                g1.record(cap)
+                torch.cuda.synchronize()
         tg = g0.elapsed_time(g1) / 1e3 / args.steps
         for hd in hs:
             hd.sync()                               # device errors behind the replays
