@@ -387,6 +387,8 @@ def run_streams(args, cfg):
     }
     if graph_note:
         line["graph_note"] = graph_note
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, m_sample=1 << 15)
     print(json.dumps(line), flush=True)
     for hd in hs:
         hd.close()
