@@ -1,0 +1,24 @@
+"""The accuracy-table harness: every row is consistent with the library's own outputs.
+
+The chosen update's exact error equals the error of the returned P; the offline references
+order as they must (the truncated SVD is optimal, so no rank-k ID beats it); estimates are
+non-negative errors of the same magnitude as the exact ones."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_table_rows_are_consistent():
+    from paper_2405_16076_gb300 import tables
+    from workloads import config1_matrix
+    A = config1_matrix(3, m=2048, n=120)
+    for k in (8, 16):
+        r = tables.table_row(A, k, block=4, seed=3)
+        assert r["q_star"] in (4, 5, 6, 7)
+        assert abs(r["chosen_exact"] - r["exact"][r["q_star"] - 4]) <= 1e-12
+        assert r["svd"] <= r["cpqr"] + 1e-12
+        assert r["svd"] <= min(r["exact"]) + 1e-12
+        assert all(e >= 0.0 for e in r["estimated"])
+    md = tables.markdown([r], "check")
+    assert md.count("|") > 10
