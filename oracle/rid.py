@@ -60,6 +60,7 @@ import math
 
 import numpy as np
 
+from . import gcv as gcv_mod
 from . import philox
 
 EPS64 = np.finfo(np.float64).eps
@@ -82,6 +83,7 @@ class RIDConfig:
     seed: int = 0
     grad_op: object = None             # sparse (d*m) x m simplex-gradient operator, Eq. 42
     right_l: int = 0                   # columns of the optional right sketch Y (0: off)
+    grad_coeff: bool = False           # keep Omega G^p a for the gradient-augmented coefficients
 
     @property
     def t(self):
@@ -259,6 +261,7 @@ class OnlineRID:
         self._omega_g = None
         self.margins = []
         self.Y = np.zeros((cfg.m, cfg.right_l)) if cfg.right_l > 0 else None
+        self.SG = None                              # d x s x n_obs: Omega G^p A_obs (unit variance)
 
     # Omega is materialized once: this is the slow, obviously correct form.
     def omega(self):
@@ -295,6 +298,10 @@ class OnlineRID:
             fro_lev += ga @ ga
         self.S_lev = np.concatenate([self.S_lev, lev[:, None]], axis=1)
         self.SSt += np.outer(lev, lev)                       # SS^T <- SS^T + s_j s_j^T
+        if c.grad_coeff:                                     # Omega G^p a_j for Sec. 3.4's coefficients
+            Gs = gcv_mod.split_gradient(c.grad_op, c.m)
+            col = np.stack([self.omega()[: c.s] @ (Gp @ a) for Gp in Gs])[:, :, None]
+            self.SG = col if self.SG is None else np.concatenate([self.SG, col], axis=2)
         if c.right_l > 0:                                    # Y <- Y + a_j omega_j^T
             w = philox.omega_block(c.omega_kind, c.seed, np.arange(c.right_l), j, j + 1, right=True)[:, 0]
             self.Y += np.outer(a, w)
@@ -311,6 +318,23 @@ class OnlineRID:
         if self.JD:
             self.batch_step()
         return self.JC.copy(), self.P.copy()
+
+    def gradient_coefficients(self, lo=-3.0, hi=3.0, tol=1e-3):
+        """Sec. 3.4's gradient-augmented coefficients for the final basis, lambda by the
+        sketched GCV (``oracle.gcv``): returns (lambda*, P (t x n, rows of empty slots 0),
+        GCV(lambda*))."""
+        c = self.cfg
+        s = c.s
+        act = np.nonzero(self.JC >= 0)[0]
+        Jact = self.JC[act]
+        S = self.S[:s] / math.sqrt(s)
+        G = [self.SG[p] / math.sqrt(s) for p in range(self.SG.shape[0])]
+        Om = self.omega()[:s]
+        K = [Om @ (Gp @ Om.T) / s for Gp in gcv_mod.split_gradient(c.grad_op, c.m)]
+        lam, Pa, g = gcv_mod.gradient_coefficients(S[:, Jact], S, [x[:, Jact] for x in G], G, K, lo, hi, tol)
+        P = np.zeros((c.t, self.n_obs))
+        P[act] = Pa
+        return lam, P, g
 
     def batch_step(self):
         c = self.cfg

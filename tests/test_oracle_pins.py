@@ -389,3 +389,70 @@ def test_right_sketch_captures_the_range_and_is_block_invariant():
     L = philox.omega_block("gaussian", 11, np.arange(7), 0, n)           # the left-sketch stream
     R = philox.omega_block("gaussian", 11, np.arange(7), 0, n, right=True)
     assert not np.allclose(L, R)                                         # independent streams
+
+
+# ---------------------------------------------------------------- gradient-augmented coefficients (Sec. 3.4)
+def _grid_case(seed=0, nx=6, ny=5, n=12):
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx)[None, :] / nx
+    y = np.arange(ny)[:, None] / ny
+    A = np.stack([(np.cos(2 * np.pi * (rng.integers(1, 3) * x + rng.integers(0, 2) * y) + rng.uniform(0, 6))
+                   + 0.1 * rng.standard_normal((ny, nx))).reshape(-1) for _ in range(n)], axis=1)
+    G = grid_gradient_operator((nx, ny))
+    return A, G
+
+
+def test_gradient_coefficients_with_identity_sketch_solve_the_augmented_problem():
+    """With Omega = sqrt(s) I the sketched quantities are the exact ones: P(lam) is the least-
+    squares solution of the stacked system [A_J; sqrt(lam) G^p A_J] X = [A; sqrt(lam) G^p A]
+    (lstsq, another route), C(lam) A = A_J P(lam) (the identity the paper states for C), and at
+    lam -> 0 C is the orthogonal projector onto range(A_J): tr(I - C) = m - |J|."""
+    from oracle import gcv
+    A, Gop = _grid_case()
+    m = A.shape[0]
+    Gs = gcv.split_gradient(Gop, m)
+    J = [0, 3, 7, 9]
+    SJ, GJ, G = A[:, J], [Gp @ A[:, J] for Gp in Gs], [Gp @ A for Gp in Gs]
+    K = [Gp.toarray() for Gp in Gs]
+    for lam in (1e-3, 0.3, 7.0):
+        P = gcv.p_of_lambda(SJ, A, GJ, G, lam)
+        stack_l = np.vstack([SJ] + [math.sqrt(lam) * g for g in GJ])
+        stack_r = np.vstack([A] + [math.sqrt(lam) * g for g in G])
+        P_ls = np.linalg.lstsq(stack_l, stack_r, rcond=None)[0]
+        assert np.allclose(P, P_ls, rtol=1e-9, atol=1e-11)
+        C = gcv.c_matrix(SJ, GJ, K, lam)
+        assert np.allclose(C @ A, SJ @ P, rtol=1e-9, atol=1e-11)
+    C0 = gcv.c_matrix(SJ, GJ, K, 1e-14)
+    assert abs(np.trace(C0) - len(J)) < 1e-8
+    Q, _ = np.linalg.qr(SJ)
+    proj_res = np.sum((A - Q @ (Q.T @ A)) ** 2)
+    assert abs(gcv.gcv(SJ, A, GJ, K, 1e-14) - proj_res / (m - len(J)) ** 2) < 1e-8 * proj_res
+
+
+def test_golden_section_finds_known_minima():
+    from oracle import gcv
+    assert abs(gcv.golden_section(lambda t: (t - 0.7) ** 2 + 1.0) - 0.7) < 1e-3
+    assert abs(gcv.golden_section(lambda t: math.exp(t) - 2.0 * t) - math.log(2.0)) < 1e-3
+    assert abs(gcv.golden_section(lambda t: abs(t + 2.5)) + 2.5) < 1e-3
+
+
+def test_stream_keeps_gradient_sketches_and_small_lambda_gives_algorithm_4():
+    """The streamed Omega G^p a_j equal Omega G^p A column by column, and with lam -> 0 the
+    augmented solution is the plain sketched least squares of Algorithm 4 (Eq. 24)."""
+    from oracle import gcv
+    A, Gop = _grid_case(1, n=20)
+    m = A.shape[0]
+    o = OnlineRID(RIDConfig(m=m, k=4, s=19, h=12, seed=2, grad_op=Gop, grad_coeff=True))
+    o.ingest(A[:, :7])
+    o.ingest(A[:, 7:])
+    Om = o.omega()[:19]
+    for p, Gp in enumerate(gcv.split_gradient(Gop, m)):
+        assert np.allclose(o.SG[p], Om @ (Gp @ A), rtol=1e-12, atol=1e-12)
+    J, P = o.finalize()
+    act = J >= 0
+    S = o.S[:19] / math.sqrt(19)
+    G = [o.SG[p] / math.sqrt(19) for p in range(2)]
+    Pz = gcv.p_of_lambda(S[:, J[act]], S, [g[:, J[act]] for g in G], G, 1e-13)
+    assert np.allclose(Pz, coeff_alg4(S[:, J[act]], S), rtol=1e-7, atol=1e-9)
+    lam, Pg, g = o.gradient_coefficients()
+    assert 1e-3 <= lam <= 1e3 and np.isfinite(g) and Pg.shape == (4, 20)
