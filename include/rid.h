@@ -83,6 +83,9 @@ typedef struct rid_config {
   void* cuda_stream;     /* cudaStream_t to run on; NULL = default stream */
   int32_t right_l;       /* columns l of the optional right sketch Y = sum_j a_j omega_j^T
                             (m x l, data dtype; not part of the paper's method); 0 = off */
+  int32_t grad_coeff;    /* 1 = keep Omega G^p a_j (p = 1, 2) during the ingest for the
+                            gradient-augmented coefficients of Sec. 3.4 (needs grad_dims = 2;
+                            see rid_gradient_coefficients) */
 } rid_config;
 
 typedef struct rid_handle rid_handle;
@@ -97,7 +100,8 @@ int rid_config_default(rid_config* cfg);
  * 1 <= k <= 1024, k < s <= 4096, 0 <= h <= 1024, h == 0 or h >= 3,
  * 0 < c1 < c2, c1 + c2 < 1, unknown enum values; gradient mode: grad_dims
  * must be 0 or 2, and with 2: nx, ny >= 2, nfields >= 1, m = nx ny nfields,
- * sketch_prec NATIVE; 0 <= right_l <= 4096), RID_ENOMEM, RID_ENOLIB.
+ * sketch_prec NATIVE; 0 <= right_l <= 4096; grad_coeff needs grad_dims = 2), RID_ENOMEM,
+ * RID_ENOLIB.
  * Gradient mode (Sec. 3.4, Eqs. 38-43): the ridge scores and lambda use the
  * sketch of [a; G a], i.e. Omega a + Omega_g (G a) with an independent Omega_g
  * (s x 2m), and ||a||^2 + ||G a||^2; G is the least-squares gradient on each
@@ -172,6 +176,21 @@ int rid_get_basis(rid_handle* h, void* out, int64_t ld, int32_t on_device);
  * RID_EINVAL (NULL out, ld < m), RID_ESTATE (right_l = 0), RID_ECUDA. */
 int rid_get_right_sketch(rid_handle* h, void* out, int64_t ld, int32_t on_device);
 
+/* Gradient-augmented coefficients of Sec. 3.4 for the final basis (the stream is finalized
+ * first if it was not): P(lambda) = argmin_X ||Omega (A_J X - A)||_F^2
+ * + lambda sum_p ||Omega (G^p A_J X - G^p A)||_F^2 from the sketches, with lambda chosen by
+ * golden-section search of the sketched GCV function GCV(lambda) = ||(I - C(lambda)) Omega A||^2
+ * / tr(I - C(lambda))^2 over log10(lambda) in [-3, 3] (bracket narrower than 1e-3; the midpoint
+ * of the last bracket).  C(lambda) = Omega A_J M^{-1} (Omega A_J + lambda sum_p (Omega G^p
+ * Omega^T)^T Omega G^p A_J)^T, M = (Omega A_J)^T Omega A_J + lambda sum_p (Omega G^p A_J)^T
+ * Omega G^p A_J, every sketch scaled by 1/sqrt(s).  Writes P (t x n, double, column-major,
+ * ldp >= t, rows of empty slots 0; device or host per on_device), *lambda_out and *gcv_out
+ * (may be NULL).  The first call forms Omega G^p Omega^T / s (s^2 m work per direction).
+ * Allocates device scratch; synchronizes.  Errors: RID_ESTATE (grad_coeff = 0), RID_EINVAL
+ * (ldp < t, NULL P_out), RID_ENOMEM / RID_ECUDA. */
+int rid_gradient_coefficients(rid_handle* h, double* P_out, int64_t ldp, int32_t on_device, double* lambda_out,
+                              double* gcv_out);
+
 /* Internal state for tests (host output, synchronizes):
  *  RID_STATE_SKETCH   : (s+h) x n_obs doubles, Omega A_obs (unit-variance rows)
  *  RID_STATE_SKETCH_LEV: s x n_obs doubles, the sketch used by the ridge scores
@@ -183,6 +202,8 @@ int rid_get_right_sketch(rid_handle* h, void* out, int64_t ld, int32_t on_device
  *  RID_STATE_CAND     : 4 x t x n_obs doubles, candidates P_4..P_7 of the last
  *                       batch step (rows of empty slots are 0)
  *  RID_STATE_BATCHES  : 1 int64, number of batch steps run
+ *  RID_STATE_GRAD_SKETCH: 2 s x n_obs doubles, column j = [Omega G^1 a_j; Omega G^2 a_j]
+ *                       (unit-variance rows; grad_coeff = 1 only)
  *  RID_STATE_GRAM_SHIFT: 1 double, the Tikhonov shift that the last batch step
  *                       added to the basis Gram of Algorithms 5 and 7, relative
  *                       to its largest diagonal entry; 0 when G = A_J^T A_J was
@@ -196,7 +217,7 @@ int rid_get_right_sketch(rid_handle* h, void* out, int64_t ld, int32_t on_device
 enum rid_state_item {
   RID_STATE_SKETCH = 0, RID_STATE_SKETCH_LEV = 1, RID_STATE_SST = 2, RID_STATE_FRO2 = 3,
   RID_STATE_JC = 4, RID_STATE_TAU_OLD = 5, RID_STATE_LAMBDA = 6, RID_STATE_CAND = 7,
-  RID_STATE_BATCHES = 8, RID_STATE_GRAM_SHIFT = 9
+  RID_STATE_BATCHES = 8, RID_STATE_GRAM_SHIFT = 9, RID_STATE_GRAD_SKETCH = 10
 };
 int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count);
 

@@ -180,29 +180,8 @@ __global__ void materialize_omega_kernel(Dev d) {
 }
 
 // ---------------------------------------------------------------- gradient mode (Sec. 3.4)
-// Entry j = p * m + i of G a (Eq. 42) for component p (0: along x, the fastest axis; 1: along
-// y) at coordinate i of field f = i / (nx ny): the least-squares gradient of Eqs. 39-43 on the
-// grid graph, i.e. the central difference along axis p where both axis neighbours exist and
-// the one-sided difference at the boundary (spacing 1; fields independent).  The stencil
-// (offset and the weights of a[i - st], a[i], a[i + st]) depends only on j.
-struct GradStencil {
-  int64_t i, st;
-  double wm, wc, wp;
-};
-__device__ __forceinline__ GradStencil grad_stencil(int64_t j, int64_t m, int nx, int ny) {
-  GradStencil g;
-  const int p = j >= m ? 1 : 0;                // d = 2
-  g.i = j - (p ? m : 0);
-  const int64_t ql = g.i % ((int64_t)nx * ny);
-  const int c = p == 0 ? (int)(ql % nx) : (int)(ql / nx);
-  const int len = p == 0 ? nx : ny;
-  g.st = p == 0 ? 1 : nx;
-  if (c == 0) { g.wm = 0.0; g.wc = -1.0; g.wp = 1.0; }
-  else if (c == len - 1) { g.wm = -1.0; g.wc = 1.0; g.wp = 0.0; }
-  else { g.wm = -0.5; g.wc = 0.0; g.wp = 0.5; }
-  return g;
-}
-
+// G a (Eq. 42) by grad_stencil (rid_internal.cuh): the least-squares gradient of Eqs. 39-43 on
+// the grid graph, central inside and one-sided at the boundary.
 // Omega_g (G a_q) for the s leverage rows and ||G a_q||^2, split-K over the d m gradient
 // entries like the ingest sketch (working-precision sums over four chunks, then FP64): grid
 // (nblk, ceil(s / 256)), 256 threads, thread tid of row group y owns row r = 256 y + tid;
@@ -325,6 +304,98 @@ __global__ void grad_reduce_kernel(Dev d, int nb, int64_t n_obs, int nblk) {
   }
 }
 
+// Omega (G^p a_q) for the s left rows of Omega (the main stream) and direction p: the sketches
+// of Sec. 3.4's gradient-augmented coefficient problem.  Split-K over the m coordinates like the
+// ingest sketch (working-precision sums over four chunks, then FP64); partials to d.spart.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kSketchThreads)
+gradc_sketch_kernel(Dev d, SimtCols cols, int nb, int p) {
+  __shared__ T X[NB][kChunk];
+  const int tid = threadIdx.x;
+  const int r = blockIdx.y * kSketchThreads + tid;
+  const bool row_ok = r < d.s;
+  const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+  double acc64[NB];
+  T acc[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) { acc64[q] = 0.0; acc[q] = T(0); }
+  const int64_t nchunks = (d.m + kChunk - 1) / kChunk;
+  int pending = 0;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int64_t i0 = c * kChunk;
+    const int64_t i = i0 + tid;
+    if (i < d.m) {
+      const GradStencil g = grad_stencil((int64_t)p * d.m + i, d.m, d.nx, d.ny);
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < nb) {
+          const T* a = (const T*)cols.p[q];
+          T v = (T)g.wc * a[g.i];
+          if (g.wm != 0.0) v += (T)g.wm * a[g.i - g.st];
+          if (g.wp != 0.0) v += (T)g.wp * a[g.i + g.st];
+          X[q][tid] = v;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < nb) X[q][tid] = T(0);
+    }
+    __syncthreads();
+    if (row_ok) {
+      if (d.omega_kind == 1) {
+#pragma unroll 1
+        for (int half = 0; half < kChunk / 128; ++half) {
+          const u32x4 w = philox4x32_10((uint32_t)((i0 >> 7) + half), (uint32_t)r, kTagRademacher, 0, k0, k1);
+          const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int wi = 0; wi < 4; ++wi) {
+#pragma unroll 8
+            for (int e = 0; e < 32; ++e) {
+              const int bpos = (e & 1) ? 31 - (e >> 1) : 15 - (e >> 1);
+              const uint32_t bit = (words[wi] >> bpos) & 1u;
+              const int ii = half * 128 + wi * 32 + e;
+#pragma unroll
+              for (int q = 0; q < NB; ++q)
+                if (q < nb) acc[q] += flip_sign(X[q][ii], bit);
+            }
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int ii = 0; ii < kChunk; ++ii) {
+          if (i0 + ii >= d.m) break;
+          const T w = (T)gauss_entry(d.seed, kTagGauss, (uint32_t)r, (uint64_t)(i0 + ii));
+#pragma unroll
+          for (int q = 0; q < NB; ++q)
+            if (q < nb) acc[q] += w * X[q][ii];
+        }
+      }
+    }
+    if (++pending == 4) {
+#pragma unroll
+      for (int q = 0; q < NB; ++q) { acc64[q] += (double)acc[q]; acc[q] = T(0); }
+      pending = 0;
+    }
+    __syncthreads();
+  }
+  if (row_ok) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (q < nb) d.spart[((size_t)blockIdx.x * nb + q) * d.rows + r] = acc64[q] + (double)acc[q];
+  }
+}
+
+// Coefficient sketch column n_obs + q, direction p: Sg[((n_obs + q) 2 + p) s + r].
+__global__ void gradc_reduce_kernel(Dev d, int nb, int64_t n_obs, int nblk, int p) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb * d.s) return;
+  const int q = idx / d.s, r = idx % d.s;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += d.spart[((size_t)b * nb + q) * d.rows + r];
+  d.Sg[((size_t)(n_obs + q) * 2 + p) * d.s + r] = v;
+}
+
 int launch_grad(const Dev& d, const void* const* colp, int nb, int64_t n_obs, cudaStream_t st) {
   SimtCols cols;
   for (int q = 0; q < kMaxB; ++q) cols.p[q] = q < nb ? colp[q] : nullptr;
@@ -340,7 +411,22 @@ int launch_grad(const Dev& d, const void* const* colp, int nb, int64_t n_obs, cu
   }
   const int n = nb * d.s;
   grad_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, nb, n_obs, nblk);
-  return 2;
+  if (!d.grad_coeff) return 2;
+  // the coefficient sketches Omega G^p a (the partial buffer is free again after the reduce)
+  const int64_t mchunks = (d.m + kChunk - 1) / kChunk;
+  const int mblk = (int)(mchunks < d.n_sketch_blocks ? mchunks : d.n_sketch_blocks);
+  dim3 gm(mblk, (d.s + kSketchThreads - 1) / kSketchThreads);
+  for (int p = 0; p < 2; ++p) {
+    if (d.dtype == 0) {
+      if (nb == 1) gradc_sketch_kernel<double, 1><<<gm, kSketchThreads, 0, st>>>(d, cols, nb, p);
+      else gradc_sketch_kernel<double, kMaxB><<<gm, kSketchThreads, 0, st>>>(d, cols, nb, p);
+    } else {
+      if (nb == 1) gradc_sketch_kernel<float, 1><<<gm, kSketchThreads, 0, st>>>(d, cols, nb, p);
+      else gradc_sketch_kernel<float, kMaxB><<<gm, kSketchThreads, 0, st>>>(d, cols, nb, p);
+    }
+    gradc_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, nb, n_obs, mblk, p);
+  }
+  return 6;
 }
 
 void launch_materialize_omega(const Dev& d, cudaStream_t st) {

@@ -36,6 +36,7 @@ struct rid_handle {
   int batch;          // batch steps run
   bool finalized;
   bool joined;            // the caller's stream already waits for every batch step issued
+  bool kg_ready;          // d.Kg holds Omega G^p Omega^T / s
   size_t esize;
   void* staging;          // host-input staging area: group_max columns of m_pad
   std::vector<const void*> pend;   // columns recorded but not yet sketched
@@ -89,7 +90,8 @@ void free_all(Dev& d, void* staging) {
   void* ptrs[] = {d.pool, d.omegaT, d.omegagT, d.S, d.SSt, d.fro2, d.JC, d.JC_prev, d.slotC,
                   d.slotC_prev, d.dslot /* 2t: both batch lists */, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
                   d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
-                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, d.Y, d.Wr, d.zq, staging};
+                  d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, d.Y, d.Wr, d.zq, d.Sg,
+                  d.Kg, staging};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
 }
@@ -138,18 +140,21 @@ int grow(rid_handle* h, int64_t need) {
   while (cap < need) cap *= 2;
   join(h);
   CK(cudaStreamSynchronize(h->st));
-  double *S, *Slev = nullptr, *P, *cand, *hpart, *zq;
+  double *S, *Slev = nullptr, *P, *cand, *hpart, *zq, *Sg = nullptr;
   CK(dalloc(&S, (size_t)d.rows * cap));
   if (d.grad) CK(dalloc(&Slev, (size_t)d.s * cap));
   CK(dalloc(&P, (size_t)d.t * cap));
   CK(dalloc(&cand, (size_t)4 * d.t * cap));
   CK(dalloc(&hpart, (size_t)hpart_len(d, cap)));
   CK(dalloc(&zq, (size_t)2 * d.t * cap));
+  if (d.grad_coeff) CK(dalloc(&Sg, (size_t)2 * d.s * cap));
   CK(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)d.t * cap, h->st));
   CK(cudaMemsetAsync(cand, 0, sizeof(double) * (size_t)4 * d.t * cap, h->st));
   if (d.S) {
     CK(cudaMemcpyAsync(S, d.S, sizeof(double) * (size_t)d.rows * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
     if (d.grad) CK(cudaMemcpyAsync(Slev, d.Slev, sizeof(double) * (size_t)d.s * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
+    if (d.grad_coeff)
+      CK(cudaMemcpyAsync(Sg, d.Sg, sizeof(double) * 2 * (size_t)d.s * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(P, d.P, sizeof(double) * (size_t)d.t * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
     cudaFree(d.S);
@@ -158,6 +163,7 @@ int grow(rid_handle* h, int64_t need) {
     cudaFree(d.cand);
     cudaFree(d.hpart);
     cudaFree(d.zq);
+    if (d.Sg) cudaFree(d.Sg);
   }
   d.S = S;
   d.Slev = d.grad ? Slev : S;
@@ -165,6 +171,7 @@ int grow(rid_handle* h, int64_t need) {
   d.cand = cand;
   d.hpart = hpart;
   d.zq = zq;
+  d.Sg = Sg;
   d.n_cap = cap;
   return RID_OK;
 }
@@ -340,6 +347,8 @@ int rid_init(rid_handle** out, const rid_config* c) {
   }
   if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
   if (c->right_l < 0 || c->right_l > 4096) return fail(h, RID_EINVAL, "right_l must be in [0, 4096]");
+  if (c->grad_coeff != 0 && c->grad_dims != 2)
+    return fail(h, RID_EINVAL, "grad_coeff needs gradient mode (grad_dims = 2)");
   if (c->grad_dims != 0) {
     if (c->grad_dims != 2) return fail(h, RID_EINVAL, "grad_dims must be 0 or 2 (2-D grids)");
     if (c->nx < 2 || c->ny < 2 || c->nfields < 1)
@@ -388,6 +397,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
   d.nfields = c->nfields;
   d.lev_ld = d.grad ? d.s : d.rows;     // gradient mode: a separate s x n leverage sketch
   d.right_l = c->right_l;
+  d.grad_coeff = c->grad_coeff != 0 ? 1 : 0;
   const int64_t nchunks = (d.m + rid::kChunk - 1) / rid::kChunk;
   d.n_sketch_blocks = (int)(nchunks < 4 * h->n_sm ? nchunks : 4 * h->n_sm);
   int64_t gs = (d.m + 16383) / 16384;
@@ -464,6 +474,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
   AL(d.npart, (size_t)d.n_sketch_blocks * rid::kMaxB);
   AL(d.err, 1);
   AL(d.gbar, 8);
+  if (d.grad_coeff) AL(d.Kg, (size_t)2 * d.s * d.s);
   if (d.right_l > 0) {
     char* y = nullptr;
     char* wr = nullptr;
@@ -673,6 +684,31 @@ int rid_get_right_sketch(rid_handle* h, void* out, int64_t ld, int32_t on_device
   return RID_OK;
 }
 
+int rid_gradient_coefficients(rid_handle* h, double* P_out, int64_t ldp, int32_t on_device, double* lambda_out,
+                              double* gcv_out) {
+  if (!h || !P_out) return RID_EINVAL;
+  if (!h->d.grad_coeff) return fail(h, RID_ESTATE, "gradient sketches were not kept (grad_coeff = 0)");
+  if (ldp < h->d.t) return fail(h, RID_EINVAL, "ldp < t");
+  if (!h->finalized) {
+    const int rc = rid_finalize(h, nullptr, nullptr, h->d.t, RID_OUT_DEVICE);
+    if (rc != RID_OK) return rc;
+  }
+  join(h);
+  const int t = h->d.t;
+  std::vector<int64_t> jc(t);
+  CK(cudaMemcpyAsync(jc.data(), h->d.JC, sizeof(int64_t) * t, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  std::vector<int64_t> jact;
+  std::vector<int> slot;
+  for (int i = 0; i < t; ++i)
+    if (jc[i] >= 0) { jact.push_back(jc[i]); slot.push_back(i); }
+  if (jact.empty()) return fail(h, RID_ESTATE, "empty basis");
+  if (rid::gradient_coefficients(h->d, h->st, h->n_obs, jact.data(), slot.data(), (int)jact.size(), -3.0, 3.0, 1e-3,
+                                 P_out, ldp, on_device, &h->kg_ready, lambda_out, gcv_out) != 0)
+    return fail(h, RID_ECUDA, "gradient-coefficient computation failed");
+  return RID_OK;
+}
+
 int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
   if (!h || !out) return RID_EINVAL;
   {
@@ -703,6 +739,11 @@ int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
     case RID_STATE_TAU_OLD: src = d.tau_old; bytes = sizeof(double) * d.t; break;
     case RID_STATE_LAMBDA: src = d.scal + rid::SCAL_LAMBDA; bytes = sizeof(double); break;
     case RID_STATE_GRAM_SHIFT: src = d.scal + rid::SCAL_GSHIFT; bytes = sizeof(double); break;
+    case RID_STATE_GRAD_SKETCH:
+      if (!d.grad_coeff) return fail(h, RID_ESTATE, "no gradient sketches (grad_coeff = 0)");
+      src = d.Sg;
+      bytes = sizeof(double) * 2 * (size_t)d.s * n;
+      break;
     case RID_STATE_CAND: {
       if (count < 4 * (int64_t)d.t * h->n_prev) return fail(h, RID_EINVAL, "buffer too small");
       for (int q = 0; q < 4; ++q)
@@ -743,7 +784,7 @@ bool same_config(const rid_config& a, const rid_config& b) {
          a.c1 == b.c1 && a.c2 == b.c2 && a.eps == b.eps && a.delta == b.delta && a.c_const == b.c_const &&
          a.lambda_fixed == b.lambda_fixed && a.omega_kind == b.omega_kind && a.data_dtype == b.data_dtype &&
          a.sketch_prec == b.sketch_prec && a.grad_dims == b.grad_dims && a.nx == b.nx && a.ny == b.ny &&
-         a.nfields == b.nfields && a.seed == b.seed && a.right_l == b.right_l;
+         a.nfields == b.nfields && a.seed == b.seed && a.right_l == b.right_l && a.grad_coeff == b.grad_coeff;
 }
 
 struct CkptPlan {
@@ -771,6 +812,7 @@ int ckpt_plan(rid_handle* h, CkptPlan& pl) {
   };
   if (d.grad) pl.arrays.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
   if (d.right_l > 0) pl.arrays.push_back({d.Y, (size_t)d.m_pad * d.right_l * h->esize});
+  if (d.grad_coeff) pl.arrays.push_back({d.Sg, sizeof(double) * 2 * (size_t)d.s * n});
   std::vector<int> slotc(t), dsl(2 * (size_t)t);
   CK(cudaMemcpyAsync(slotc.data(), d.slotC, sizeof(int) * t, cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(dsl.data(), h->dslot_buf, sizeof(int) * 2 * t, cudaMemcpyDeviceToHost, h->st));
@@ -872,6 +914,7 @@ int rid_restore(rid_handle* h, const void* buf, int64_t bytes) {
     };
     if (d.grad) pl.arrays.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
     if (d.right_l > 0) pl.arrays.push_back({d.Y, (size_t)d.m_pad * d.right_l * h->esize});
+    if (d.grad_coeff) pl.arrays.push_back({d.Sg, sizeof(double) * 2 * (size_t)d.s * n});
   }
   size_t need = head;
   for (auto& a : pl.arrays) need += a.second;

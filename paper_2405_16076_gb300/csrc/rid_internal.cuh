@@ -84,6 +84,9 @@ struct Dev {
   int n_sketch_blocks;
   int gram_split;
   int64_t work_len;
+  int grad_coeff;                 // keep Omega G^p a (Sec. 3.4's gradient-augmented coefficients)
+  double* Sg;                     // 2 s x n_cap: column j = [Omega G^1 a_j; Omega G^2 a_j] (unit variance)
+  double* Kg;                     // 2 s x s: Omega G^p Omega^T / s, formed on first use (gcv.cu)
   int right_l;                    // columns of the optional right sketch (0: off)
   void* Y;                        // right sketch, m_pad x right_l, data dtype
   void* Wr;                       // the group's right-sketch vectors (see right.cu)
@@ -123,9 +126,39 @@ int launch_ingest(const Dev& d, const void* const* cols, int nb, int count, int6
 // Gradient mode (Sec. 3.4): the leverage sketch of nb columns given by pointer, after their
 // sketch has been reduced; returns the number of kernels launched.
 int launch_grad(const Dev& d, const void* const* cols, int nb, int64_t n_obs, cudaStream_t st);
+// Gradient stencil of Sec. 3.4 on each field's nx x ny grid (x fastest): entry j of the
+// stacked d m = 2 m gradient vector, direction p = j / m at coordinate i = j mod m, is
+// wm a[i - st] + wc a[i] + wp a[i + st]: central difference inside, one-sided at the boundary
+// (spacing 1; fields independent).
+struct GradStencil {
+  int64_t i, st;
+  double wm, wc, wp;
+};
+__device__ __forceinline__ GradStencil grad_stencil(int64_t j, int64_t m, int nx, int ny) {
+  GradStencil g;
+  const int p = j >= m ? 1 : 0;                // d = 2
+  g.i = j - (p ? m : 0);
+  const int64_t ql = g.i % ((int64_t)nx * ny);
+  const int c = p == 0 ? (int)(ql % nx) : (int)(ql / nx);
+  const int len = p == 0 ? nx : ny;
+  g.st = p == 0 ? 1 : nx;
+  if (c == 0) { g.wm = 0.0; g.wc = -1.0; g.wp = 1.0; }
+  else if (c == len - 1) { g.wm = -1.0; g.wc = 1.0; g.wp = 0.0; }
+  else { g.wm = -0.5; g.wc = 0.0; g.wp = 0.5; }
+  return g;
+}
+
 // Optional right sketch Y += sum_q a_q omega_{j0+q}^T over ncols ingested columns (right.cu).
 int launch_right_sketch(const Dev& d, const void* const* cols, int ncols, int64_t j0, cudaStream_t st);
 size_t right_w_bytes(const Dev& d);
+
+// Sec. 3.4's gradient-augmented coefficients for the final basis with lambda chosen by the
+// sketched GCV function (gcv.cu).  jact: the na active basis columns (global indices, slot
+// order) and slot: their slots; P_out rows are slots (ldp >= t), empty slots zero.  kg_ready:
+// whether d.Kg already holds Omega G^p Omega^T / s (set on return).  Returns 0 or a CUDA error.
+int gradient_coefficients(const Dev& d, cudaStream_t st, int64_t n, const int64_t* jact, const int* slot, int na,
+                          double lo, double hi, double tol, double* P_out, int64_t ldp, int on_device,
+                          bool* kg_ready, double* lambda_out, double* gcv_out);
 // SS^T update for nb new columns (shared by both ingest paths).
 void launch_gram_update(const Dev& d, int nb, int64_t n_obs, cudaStream_t st);
 

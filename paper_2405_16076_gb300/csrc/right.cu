@@ -34,17 +34,6 @@ struct RCols {
   const void* p[64];
 };
 
-// Rademacher entry (r, i) of a +-1 stream with the layout of the left sketch: bit 15 - p (even
-// e) or 31 - p (odd e) of word (i mod 128) / 32 of Philox(i / 128, r, tag, 0), e = i mod 32,
-// p = e / 2; a set bit is -1.
-__device__ __forceinline__ double rademacher_entry(uint64_t seed, uint32_t tag, uint32_t r, uint64_t i) {
-  const u32x4 w = philox4x32_10((uint32_t)(i >> 7), r, tag, 0, (uint32_t)seed, (uint32_t)(seed >> 32));
-  const uint32_t j = (uint32_t)(i & 127), e = j & 31, p = e >> 1;
-  const uint32_t word = (j >> 5) == 0 ? w.x : (j >> 5) == 1 ? w.y : (j >> 5) == 2 ? w.z : w.w;
-  const uint32_t bit = (e & 1) ? 31 - p : 15 - p;
-  return ((word >> bit) & 1u) ? -1.0 : 1.0;
-}
-
 template <typename T>
 __global__ void right_w_kernel(Dev d, int64_t j0, int G, int lw, T* __restrict__ W) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;

@@ -21,7 +21,8 @@ RID_OMEGA_GAUSSIAN, RID_OMEGA_RADEMACHER = 0, 1
 RID_F64, RID_F32 = 0, 1
 RID_SKETCH_NATIVE, RID_SKETCH_BF16, RID_SKETCH_BF16X2 = 0, 1, 2
 (RID_STATE_SKETCH, RID_STATE_SKETCH_LEV, RID_STATE_SST, RID_STATE_FRO2, RID_STATE_JC,
- RID_STATE_TAU_OLD, RID_STATE_LAMBDA, RID_STATE_CAND, RID_STATE_BATCHES, RID_STATE_GRAM_SHIFT) = range(10)
+ RID_STATE_TAU_OLD, RID_STATE_LAMBDA, RID_STATE_CAND, RID_STATE_BATCHES, RID_STATE_GRAM_SHIFT,
+ RID_STATE_GRAD_SKETCH) = range(11)
 
 
 class rid_config(ctypes.Structure):
@@ -33,7 +34,7 @@ class rid_config(ctypes.Structure):
         ("sketch_prec", ctypes.c_int32), ("grad_dims", ctypes.c_int32), ("nx", ctypes.c_int32),
         ("ny", ctypes.c_int32), ("nfields", ctypes.c_int32), ("n_max", ctypes.c_int64),
         ("seed", ctypes.c_uint64), ("group_max", ctypes.c_int32), ("defer_device_input", ctypes.c_int32),
-        ("cuda_stream", ctypes.c_void_p), ("right_l", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p), ("right_l", ctypes.c_int32), ("grad_coeff", ctypes.c_int32),
     ]
 
 
@@ -58,6 +59,7 @@ def _load():
         "rid_n_obs": (ctypes.c_int64, [H]),
         "rid_get_basis": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32]),
         "rid_get_right_sketch": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32]),
+        "rid_gradient_coefficients": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32, P, P]),
         "rid_get_state": (ctypes.c_int, [H, ctypes.c_int32, P, ctypes.c_int64]),
         "rid_sync": (ctypes.c_int, [H]),
         "rid_profile": (ctypes.c_int, [H, ctypes.c_int32]),
@@ -89,6 +91,7 @@ rid_error_estimate = lib.rid_error_estimate
 rid_n_obs = lib.rid_n_obs
 rid_get_basis = lib.rid_get_basis
 rid_get_right_sketch = lib.rid_get_right_sketch
+rid_gradient_coefficients = lib.rid_gradient_coefficients
 rid_get_state = lib.rid_get_state
 rid_sync = lib.rid_sync
 rid_profile = lib.rid_profile
@@ -145,7 +148,7 @@ class OnlineRID:
     def __init__(self, m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
                  lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
                  sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
-                 grad_dims=0, nx=0, ny=0, nfields=1, right_l=0):
+                 grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False):
         cfg = rid_config()
         _check(rid_config_default(ctypes.byref(cfg)))
         cfg.m, cfg.k, cfg.s, cfg.h = int(m), int(k), int(s), int(h)
@@ -161,6 +164,7 @@ class OnlineRID:
         cfg.defer_device_input = 1 if defer else 0
         cfg.grad_dims, cfg.nx, cfg.ny, cfg.nfields = int(grad_dims), int(nx), int(ny), int(nfields)
         cfg.right_l = int(right_l)
+        cfg.grad_coeff = 1 if grad_coeff else 0
         cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         self.cfg = cfg
         self.t = int(k)
@@ -247,6 +251,10 @@ class OnlineRID:
             out = np.empty(t)
         elif item in (RID_STATE_LAMBDA, RID_STATE_GRAM_SHIFT):
             out = np.empty(1)
+        elif item == RID_STATE_GRAD_SKETCH:
+            out = np.empty((n, 2, s))
+            _check(rid_get_state(self.h, item, ctypes.c_void_p(out.ctypes.data), out.size), self.h)
+            return out.transpose(1, 2, 0).copy()           # (2, s, n)
         elif item == RID_STATE_BATCHES:
             out = np.empty(1, dtype=np.int64)
         elif item == RID_STATE_CAND:
@@ -269,6 +277,17 @@ class OnlineRID:
         out = np.zeros((self.t, self.m), dtype=self.np_dtype)
         _check(rid_get_basis(self.h, ctypes.c_void_p(out.ctypes.data), self.m, 0), self.h)
         return out.T.copy()
+
+    def gradient_coefficients(self):
+        """Sec. 3.4's gradient-augmented coefficients, lambda by the sketched GCV:
+        (lambda*, P (t x n), GCV(lambda*))."""
+        n = self.n_obs()
+        P = np.zeros((n, self.t))                      # row j = column j of the t x n matrix
+        lam = ctypes.c_double()
+        g = ctypes.c_double()
+        _check(rid_gradient_coefficients(self.h, ctypes.c_void_p(P.ctypes.data), self.t, 0, ctypes.byref(lam),
+                                         ctypes.byref(g)), self.h)
+        return lam.value, P.T.copy(), g.value
 
     def right_sketch(self):
         """The optional right sketch Y (m x right_l, data dtype) on the host."""
