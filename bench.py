@@ -222,6 +222,41 @@ def id_error_device(X, J, P, chunk=1 << 17):
     return float((num / den).sqrt().item()), float(den.item())
 
 
+def grad_field_error(X, J, P, cfg, chunk=64):
+    """||G (A - A_J P)||_F / ||G A||_F for the stacked fields of the ignition stream (central
+    differences along x and y inside, one-sided at the boundary), in FP64 on the device."""
+    import torch
+    N, nf = cfg["N"], cfg["nfields"]
+    act = (J >= 0).nonzero().flatten()
+    Jv = J[act]
+    Pv = P[:, act]
+    B = X[Jv].double()                                   # t x m basis
+    num = torch.zeros((), dtype=torch.float64, device=X.device)
+    den = torch.zeros((), dtype=torch.float64, device=X.device)
+
+    def grad2(F):                                        # F: (c, nf, N, N) -> list of (c, nf, N, N)
+        gx = torch.empty_like(F)
+        gx[..., 1:-1] = 0.5 * (F[..., 2:] - F[..., :-2])
+        gx[..., 0] = F[..., 1] - F[..., 0]
+        gx[..., -1] = F[..., -1] - F[..., -2]
+        gy = torch.empty_like(F)
+        gy[..., 1:-1, :] = 0.5 * (F[..., 2:, :] - F[..., :-2, :])
+        gy[..., 0, :] = F[..., 1, :] - F[..., 0, :]
+        gy[..., -1, :] = F[..., -1, :] - F[..., -2, :]
+        return gx, gy
+    for j0 in range(0, X.shape[0], chunk):
+        Xc = X[j0:j0 + chunk].double()
+        R = Xc - Pv[j0:j0 + chunk] @ B
+        for F, acc in ((R, "num"), (Xc, "den")):
+            gx, gy = grad2(F.view(-1, nf, N, N))
+            v = gx.square().sum() + gy.square().sum()
+            if acc == "num":
+                num += v
+            else:
+                den += v
+    return float((num / den).sqrt().item())
+
+
 def accuracy_report(h, X, Jd, Pd):
     """Exact relative error of the result and the NA-Hutch++ estimate of it (Algorithm 8)."""
     err, fro2 = id_error_device(X, Jd, Pd)
@@ -517,6 +552,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sketch", default="bf16x2", choices=["bf16x2", "bf16", "native"])
     ap.add_argument("--group", type=int, default=64)
+    ap.add_argument("--grad-coeff", action="store_true",
+                    help="gradient mode: keep Omega G^p a and report Sec. 3.4's gradient-augmented coefficients")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the accuracy comparison with the other sketch precisions")
     args = ap.parse_args()
@@ -556,6 +593,8 @@ def main():
 
     st = torch.cuda.Stream(device=dev)
     gkw = dict(grad_dims=2, nx=cfg["N"], ny=cfg["N"], nfields=cfg["nfields"]) if grad else {}
+    if grad and args.grad_coeff:
+        gkw["grad_coeff"] = True
     h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=args.sketch, n_max=n,
                       seed=rank_seeds(rank)[1], stream=st, defer=True, group_max=args.group,
                       right_l=cfg.get("right_l", 0), **gkw)
@@ -589,6 +628,24 @@ def main():
     prof_ms, prof_kern, prof_grp = h.profile_read()
     h.profile(False)
     accuracy = accuracy_report(h, X, Jd, Pd)
+    gradc = None
+    if grad and args.grad_coeff:
+        # Sec. 3.4's gradient-augmented coefficients for the final basis (lambda by sketched GCV),
+        # timed once after the stream; errors of the data and of its gradient field
+        Pg = torch.empty((n, cfg["k"]), dtype=torch.float64, device=dev)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(st)
+        lam, _, gval = h.gradient_coefficients(out=Pg)
+        c1.record(st)
+        torch.cuda.synchronize()
+        e_g = id_error_device(X, Jd, Pg)[0]
+        gradc = {"lambda": lam, "gcv": gval, "ms": c0.elapsed_time(c1), "rel_fro_err": e_g,
+                 "grad_rel_fro_err": grad_field_error(X, Jd, Pg, cfg), "streaming_grad_rel_fro_err":
+                 grad_field_error(X, Jd, Pd, cfg),
+                 "note": "P(lambda*) of the augmented sketched least squares (Sec. 3.4) after the stream, "
+                         "the first call including Omega G^p Omega^T / s; errors of A and of its x/y "
+                         "differences, against the streaming P of Algorithms 4-8"}
     t_max = max_over_ranks(ms_total, world, dev)
     value = whole_job_rate(world, n * args.steps, t_max)
 
@@ -766,6 +823,8 @@ def main():
         "clocks": clk.summary(),
         "accuracy": accuracy,
     }
+    if gradc is not None:
+        line["gradient_coefficients"] = gradc
     if right is not None:
         line["ingest_roofline"] = line["roofline"]
         line["roofline"] = right

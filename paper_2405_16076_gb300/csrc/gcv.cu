@@ -38,10 +38,11 @@ __global__ void omega_rows_kernel(Dev d, T* __restrict__ Om) {
   }
 }
 
-// K^p[r + c s] = sum_i Om[r][i] (G^p Om[c])[i] / s in 64 x 64 tiles, chunks of 32 coordinates;
-// 256 threads, 4 x 4 outputs each; working-precision sums flushed to FP64 every 64 chunks.
+// Partial K^p over coordinate slice z of gridDim.z: Kp[z][r + c s] = sum_{i in slice} Om[r][i]
+// (G^p Om[c])[i] in 64 x 64 tiles, chunks of 32 coordinates; 256 threads, 4 x 4 outputs each;
+// working-precision sums flushed to FP64 every 64 chunks.
 template <typename T>
-__global__ void __launch_bounds__(256) kgram_kernel(Dev d, const T* __restrict__ Om, int p, double* __restrict__ K) {
+__global__ void __launch_bounds__(256) kgram_kernel(Dev d, const T* __restrict__ Om, int p, double* __restrict__ Kp) {
   __shared__ T As[32][65];
   __shared__ T Bs[32][65];
   const int s = d.s;
@@ -54,7 +55,11 @@ __global__ void __launch_bounds__(256) kgram_kernel(Dev d, const T* __restrict__
 #pragma unroll
     for (int v = 0; v < 4; ++v) { acc[u][v] = T(0); acc64[u][v] = 0.0; }
   int pending = 0;
-  for (int64_t i0 = 0; i0 < d.m; i0 += 32) {
+  const int64_t nch = (d.m + 31) / 32;
+  const int64_t per = (nch + gridDim.z - 1) / gridDim.z;
+  const int64_t ib = (int64_t)blockIdx.z * per * 32;
+  const int64_t ie = ib + per * 32 < d.m ? ib + per * 32 : d.m;
+  for (int64_t i0 = ib; i0 < ie; i0 += 32) {
     for (int idx = threadIdx.x; idx < 32 * 64; idx += 256) {
       const int kk = idx & 31, rr = idx >> 5;
       const int64_t i = i0 + kk;
@@ -90,14 +95,23 @@ __global__ void __launch_bounds__(256) kgram_kernel(Dev d, const T* __restrict__
       pending = 0;
     }
   }
-  const double inv_s = 1.0 / (double)s;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int r = r0 + ty * 4 + u, c = c0 + tx * 4 + v;
-      if (r < s && c < s) K[(size_t)p * s * s + r + (size_t)c * s] = (acc64[u][v] + (double)acc[u][v]) * inv_s;
+      if (r < s && c < s) Kp[(size_t)blockIdx.z * s * s + r + (size_t)c * s] = acc64[u][v] + (double)acc[u][v];
     }
+}
+
+// K^p = (sum of the slices in order) / s.
+__global__ void kgram_reduce_kernel(const double* Kp, int nz, int s, int p, double* K) {
+  const int64_t ss = (int64_t)s * s;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < ss; idx += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int z = 0; z < nz; ++z) v += Kp[z * ss + idx];
+    K[p * ss + idx] = v / (double)s;
+  }
 }
 
 // C (M x N, ldc) = alpha A^T B (+ C when acc), A: K x M (lda), B: K x N (ldb), column-major.
@@ -249,15 +263,28 @@ int gradient_coefficients(const Dev& d, cudaStream_t st, int64_t n, const int64_
 #define GA(ptr, type, count) type* ptr = (type*)alloc(sizeof(type) * (size_t)(count)); if (!ptr) { release(); return -1; }
   if (!*kg_ready) {
     // K^p = Omega G^p Omega^T / s from the materialised left rows of Omega
-    const dim3 gk((unsigned)((s + 63) / 64), (unsigned)((s + 63) / 64));
+    // enough coordinate slices that the tiles fill the GPU a few times over
+    const int tiles = ((s + 63) / 64) * ((s + 63) / 64);
+    int nz = (4 * d.n_sm + tiles - 1) / tiles;
+    const int64_t nch = (d.m + 31) / 32;
+    if (nz > nch) nz = (int)nch;
+    if (nz < 1) nz = 1;
+    const dim3 gk((unsigned)((s + 63) / 64), (unsigned)((s + 63) / 64), (unsigned)nz);
+    GA(Kp, double, (size_t)nz * s * s);
     if (d.omega_kind == 1) {                 // +-1 entries: FP32 products and sums are exact
       GA(Om, float, (size_t)s * d.m_pad);
       omega_rows_kernel<float><<<4 * d.n_sm, 256, 0, st>>>(d, Om);
-      for (int p = 0; p < 2; ++p) kgram_kernel<float><<<gk, 256, 0, st>>>(d, Om, p, d.Kg);
+      for (int p = 0; p < 2; ++p) {
+        kgram_kernel<float><<<gk, 256, 0, st>>>(d, Om, p, Kp);
+        kgram_reduce_kernel<<<2 * d.n_sm, 256, 0, st>>>(Kp, nz, s, p, d.Kg);
+      }
     } else {
       GA(Om, double, (size_t)s * d.m_pad);
       omega_rows_kernel<double><<<4 * d.n_sm, 256, 0, st>>>(d, Om);
-      for (int p = 0; p < 2; ++p) kgram_kernel<double><<<gk, 256, 0, st>>>(d, Om, p, d.Kg);
+      for (int p = 0; p < 2; ++p) {
+        kgram_kernel<double><<<gk, 256, 0, st>>>(d, Om, p, Kp);
+        kgram_reduce_kernel<<<2 * d.n_sm, 256, 0, st>>>(Kp, nz, s, p, d.Kg);
+      }
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) { release(); return -1; }
     release();

@@ -278,13 +278,18 @@ class OnlineRID:
         _check(rid_get_basis(self.h, ctypes.c_void_p(out.ctypes.data), self.m, 0), self.h)
         return out.T.copy()
 
-    def gradient_coefficients(self):
+    def gradient_coefficients(self, out=None):
         """Sec. 3.4's gradient-augmented coefficients, lambda by the sketched GCV:
-        (lambda*, P (t x n), GCV(lambda*))."""
-        n = self.n_obs()
-        P = np.zeros((n, self.t))                      # row j = column j of the t x n matrix
+        (lambda*, P (t x n) on the host, GCV(lambda*)); with ``out`` (a device tensor (n, t),
+        row j = column j) P is written there instead and None is returned in its place."""
         lam = ctypes.c_double()
         g = ctypes.c_double()
+        if out is not None:
+            _check(rid_gradient_coefficients(self.h, ctypes.c_void_p(out.data_ptr()), self.t, 1, ctypes.byref(lam),
+                                             ctypes.byref(g)), self.h)
+            return lam.value, None, g.value
+        n = self.n_obs()
+        P = np.zeros((n, self.t))                      # row j = column j of the t x n matrix
         _check(rid_gradient_coefficients(self.h, ctypes.c_void_p(P.ctypes.data), self.t, 0, ctypes.byref(lam),
                                          ctypes.byref(g)), self.h)
         return lam.value, P.T.copy(), g.value
