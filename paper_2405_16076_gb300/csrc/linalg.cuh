@@ -65,27 +65,6 @@ static __device__ void cta_cholesky(double* A, int n, int lda, double tol, int* 
   __syncthreads();
 }
 
-// b <- Q^T b for the Householder reflectors of an m x n QR factor (reflector j is
-// v = [vhead[j]; QR(j+1:m, j)], H_j = I - beta[j] v v^T); warp cooperative.
-static __device__ void warp_apply_qt(const double* QR, int m, int n, int lda, const double* beta,
-                              const double* vhead, double* b) {
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < n; ++j) {
-    const double bj = beta[j];
-    if (bj == 0.0) continue;
-    const double* v = QR + (size_t)j * lda;
-    const double vh = vhead[j];
-    double dot = (lane == 0) ? vh * b[j] : 0.0;
-    for (int i = j + 1 + lane; i < m; i += 32) dot += v[i] * b[i];
-    dot = warp_sum(dot);
-    const double f = bj * dot;
-    __syncwarp();
-    if (lane == 0) b[j] -= f * vh;
-    for (int i = j + 1 + lane; i < m; i += 32) b[i] -= f * v[i];
-    __syncwarp();
-  }
-}
-
 // Triangular solves with precomputed reciprocal diagonals (0 where the component is
 // dropped), warp cooperative: L y = b, L^T x = y (L lower from cta_cholesky), R x = c (R upper).
 static __device__ void warp_trsv_lower_r(const double* L, const double* linv, int n, int lda, double* b) {
