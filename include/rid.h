@@ -112,9 +112,11 @@ int rid_init(rid_handle** out, const rid_config* cfg);
 /* Ingest ncols >= 0 columns (Algorithm 3, the loop body for each column):
  * column q starts at cols + q*ld elements of the configured dtype.
  * on_device != 0: cols is a device pointer, read in place; otherwise a host
- * pointer (preferably pinned), copied to a device staging area first.  The
- * library copies what it keeps; the caller may reuse a host buffer when the
- * call returns and a device buffer once the handle's stream has passed this
+ * pointer, copied to a device staging area on the handle's stream first.  The
+ * library copies what it keeps.  A pageable host buffer may be reused
+ * when the call returns; a page-locked (pinned) one is read asynchronously and
+ * may be reused after the next synchronizing call (rid_sync, rid_finalize);
+ * a device buffer once the handle's stream has passed this
  * call -- except with defer_device_input = 1, where device columns are only
  * recorded and read later, in groups of up to group_max columns (one read of
  * each column sketches the whole group); the caller must then keep them
