@@ -1020,7 +1020,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
       staged = cudaFuncSetAttribute(hutch_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kHutchSmemBytes) == cudaSuccess ? 1 : 0;
     hutch_finish_kernel<<<4, 512, staged ? kHutchSmemBytes : 0, st>>>(d, w, nchunk, staged,
-                                                                      SCAL_FRO0 + (batch & 1));
+                                                                      SCAL_FRO0 + (batch & 3));
   }
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);

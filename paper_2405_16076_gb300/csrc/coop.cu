@@ -709,7 +709,7 @@ int launch_lambda(const Dev& d, int batch, double* work_base, int64_t off_A, int
     ++nk;
   }
   lambda_ldl_kernel<<<1, 32, (size_t)(2 * d.s + (k < d.s ? k : d.s)) * sizeof(double), st>>>(
-      d, mu, k, dv, ev, ld, ll, SCAL_FRO0 + (batch & 1));
+      d, mu, k, dv, ev, ld, ll, SCAL_FRO0 + (batch & 3));
   return nk + 1;
 }
 

@@ -187,8 +187,8 @@ cudaEvent_t next_event(rid_handle* h) {
 
 // Batch step b.  The caller's stream snapshots SS^T and ||A||^2 (buffer b % 2, free once
 // the lambda part of step b-2 has run) and goes on ingesting; the lambda part runs on the
-// lambda stream from the snapshot into output copy b % 2 (after step b-2's tail, the last
-// reader of that copy, has ended); the tail runs on the batch stream after it.
+// lambda stream from the snapshot into output copy b % 2 (after step b-2's scores, the last
+// reader of that copy); the tail runs on the batch stream after it.
 int run_batch(rid_handle* h) {
   const int b = h->batch;
   h->joined = false;
@@ -202,9 +202,10 @@ int run_batch(rid_handle* h) {
   CK(cudaMemcpyAsync(snap + ss, db.fro2, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   CK(cudaEventRecord(h->ev_snap, h->st));
   CK(cudaStreamWaitEvent(h->stl, h->ev_snap, 0));
-  // the lambda outputs of batch b share their copy (b % 2) with batch b-2, whose tail reads
-  // them (the scores) and the step's ||A_obs||^2 slot (NA-Hutch++) until it ends
-  if (b >= 2) CK(cudaStreamWaitEvent(h->stl, h->ev_tail[b & 1], 0));
+  // the lambda outputs of batch b share their copy (b % 2) with the scores of batch b-2; its
+  // ||A_obs||^2 slot (b % 4) was last read by the tail of batch b-4, which ended before the
+  // scores of batch b-2 ran (one batch stream)
+  if (b >= 2) CK(cudaStreamWaitEvent(h->stl, h->ev_scores[b & 1], 0));
   Dev dl = db;
   dl.SSt = snap;
   dl.fro2 = snap + ss;

@@ -98,14 +98,15 @@ enum {
   META_NOBS = 5, META_NPREV = 6, META_BATCH = 7, META_QSTAR = 8, META_NKEPT = 9, META_LEN = 16
 };
 // scal[] indices
-// SCAL_FRO0 + (batch & 1): ||A_obs||^2 as the batch's step saw it (two slots: the next step's
-// lambda part may run while this step's tail still reads it)
+// SCAL_FRO0 + (batch & 3): ||A_obs||^2 as the batch's step saw it, written by its lambda part and
+// read at the end of its tail (four slots: the lambda parts of the next two steps may run while
+// this step's tail still reads it)
 // SCAL_GSHIFT: the Tikhonov shift of the basis Gram in the last batch step, relative to its
 // largest diagonal entry (0 when the Gram was factored as is).
 // SCAL_UNC + q: rounding uncertainty of candidate q's estimate relative to ||A_obs||^2 (see
 // hutch_finish_kernel); 0 for FP64 sketches.
 enum {
-  SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_FRO0 = 5, SCAL_GSHIFT = 7,
+  SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_FRO0 = 12 /* 4 slots */, SCAL_GSHIFT = 7,
   SCAL_UNC = 8 /* 4 values */, SCAL_LEN = 16
 };
 
