@@ -13,7 +13,7 @@ every round after the first.  Pinned by the published known-answer vectors
 The method draws three kinds of random numbers (Algorithm 3): the entries of
 the test matrix Omega (Gaussian in the paper, Rademacher as the sub-Gaussian
 alternative allowed by the NA-Hutch++ analysis of Sec. 3.3), and the uniforms
-behind every "with probability p" decision of the column subset selection.
+behind every random keep / drop decision of the column subset selection.
 Their counter layout is fixed here and restated independently by the CUDA
 library:
 

@@ -34,8 +34,8 @@ R10 Algorithms 6 and 7 need P_prev for columns observed since the last batch
     Algorithm 4 every batch for exactly this use).  For Algorithm 7 the new
     columns are copied after the transform.
 R10b Algorithm 6 solves the residual least-squares problem for the rows of the
-    new basis elements only (the text of Sec. 3.2.3: "update coefficients for
-    new basis elements ... on the residual").  Solving over all of A_J, as the
+    new basis elements only, as the prose of Sec. 3.2.3 describes it (old rows
+    keep their coefficients, new rows are fitted to the residual).  Solving over all of A_J, as the
     listing reads, gives P_prev + (Omega A_J)^+(Omega A - Omega A_J P_prev)
     = (Omega A_J)^+ Omega A, i.e. Algorithm 4 again whenever Omega A_J has full
     column rank, whereas the paper's tables report different errors for the two.
