@@ -1,0 +1,42 @@
+"""The benchmark's accuracy evaluation, on the CPU, against independent routes.
+
+id_error_device (chunked FP64 residual norm on torch tensors) against numpy's norm of the
+explicit residual; grad_field_error (x / y differences of the stacked fields by slicing)
+against the gradient operator of Sec. 3.4 built from the grid graph (oracle.gradient)."""
+import numpy as np
+import torch
+
+import bench
+from oracle.gradient import grid_gradient_operator
+
+
+def _case(seed, n, m, t):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)).astype(np.float32).astype(np.float64)
+    J = np.array(list(rng.choice(n, size=t - 1, replace=False)) + [-1])     # one empty slot
+    P = rng.standard_normal((t, n))
+    P[-1] = 0.0
+    return A, J, P
+
+
+def test_id_error_matches_explicit_residual():
+    A, J, P = _case(0, n=23, m=1000, t=6)
+    X = torch.from_numpy(np.ascontiguousarray(A.T)).float()
+    err, fro2 = bench.id_error_device(X, torch.from_numpy(J), torch.from_numpy(np.ascontiguousarray(P.T)), chunk=97)
+    act = J >= 0
+    ref = np.linalg.norm(A - A[:, J[act]] @ P[act]) / np.linalg.norm(A)
+    assert abs(err - ref) <= 1e-12 * ref
+    assert abs(fro2 - np.sum(A * A)) <= 1e-12 * np.sum(A * A)
+
+
+def test_gradient_field_error_matches_grid_operator():
+    N, nf, n, t = 7, 3, 9, 4
+    A, J, P = _case(1, n=n, m=nf * N * N, t=t)
+    X = torch.from_numpy(np.ascontiguousarray(A.T)).float()
+    got = bench.grad_field_error(X, torch.from_numpy(J), torch.from_numpy(np.ascontiguousarray(P.T)),
+                                 {"N": N, "nfields": nf}, chunk=4)
+    G = grid_gradient_operator((N, N), nfields=nf)
+    act = J >= 0
+    R = A - A[:, J[act]] @ P[act]
+    ref = np.linalg.norm(G @ R) / np.linalg.norm(G @ A)
+    assert abs(got - ref) <= 1e-10 * ref
