@@ -551,7 +551,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sketch", default="bf16x2", choices=["bf16x2", "bf16", "native"])
-    ap.add_argument("--group", type=int, default=64)
+    ap.add_argument("--group", type=int, default=64,
+                    help="columns per sketch launch (1..64); 0 = measure it with rid_autotune on the "
+                         "first 2k snapshots before the timed region")
     ap.add_argument("--grad-coeff", action="store_true",
                     help="gradient mode: keep Omega G^p a and report Sec. 3.4's gradient-augmented coefficients")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
@@ -595,6 +597,14 @@ def main():
     gkw = dict(grad_dims=2, nx=cfg["N"], ny=cfg["N"], nfields=cfg["nfields"]) if grad else {}
     if grad and args.grad_coeff:
         gkw["grad_coeff"] = True
+    tune = None
+    if args.group == 0:
+        # the group size measured on this stream's first two batches, outside the timed region
+        ntune = min(n, 2 * cfg["k"])
+        gbest, us = rid.autotune_group(X[:ntune], m, cfg["k"], cfg["s"], cfg["h"], dtype="f32", sketch=args.sketch,
+                                       seed=rank_seeds(rank)[1], stream=st, right_l=cfg.get("right_l", 0), **gkw)
+        args.group = gbest
+        tune = {"group_max": gbest, "us_per_column": us, "columns": ntune}
     h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=args.sketch, n_max=n,
                       seed=rank_seeds(rank)[1], stream=st, defer=True, group_max=args.group,
                       right_l=cfg.get("right_l", 0), **gkw)
@@ -802,7 +812,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": cfg["workload"], "m": m, "n": n, "block": b, "k": cfg["k"], "s": cfg["s"],
                    "h": cfg["h"], "omega": "rademacher", "lambda": "streaming", "sketch": args.sketch,
-                   "group": args.group,
+                   "group": args.group, "autotune": tune,
                    "l2": "inputs larger than L2 (57 MB per snapshot, whole stream resident in HBM)",
                    "parallelism": f"{world} independent streams"},
         "e2e": {"value": e2e_val, "unit": "snapshots/s", "h2d_bytes_per_step": int(n * m * 4),

@@ -95,6 +95,10 @@ typedef struct rid_handle rid_handle;
  * n_max = 1024.  m, k, s, h must still be set.  Returns RID_EINVAL on NULL. */
 int rid_config_default(rid_config* cfg);
 
+/* Check *cfg as rid_init does (the same conditions and messages), without creating a handle
+ * or touching a device.  Returns RID_OK or RID_EINVAL (message in rid_last_error(NULL)). */
+int rid_config_check(const rid_config* cfg);
+
 /* Validate *cfg and allocate the device state (Algorithm 3, initialisation).
  * On success *out receives a new handle.  Errors: RID_EINVAL (sizes: m >= 1,
  * 1 <= k <= 1024, k < s <= 4096, 0 <= h <= 1024, h == 0 or h >= 3,
@@ -256,8 +260,27 @@ int rid_sync(rid_handle* h);
 int rid_reset(rid_handle* h);
 
 /* Text of the last error on h (or, when h is NULL, of the last failed
- * rid_init or rid_sketch_noalloc of the calling thread). */
+ * rid_init, rid_config_check, rid_autotune or rid_sketch_noalloc of the calling thread). */
 const char* rid_last_error(const rid_handle* h);
+
+/* Pick cfg->group_max -- the ingest's group size, i.e. how many device columns one sketch
+ * launch reads (no counterpart in the paper: a tuning of this library's ingest) -- by
+ * measurement on the current device.  cols: ncols >= 1 representative columns of the stream
+ * (device memory, m x ncols column-major, ld >= m), read and not modified.  Candidates are the
+ * powers of two from 1 to 64 (tensor-core sketches) or 16 (native precision), up to the first
+ * one >= min(ncols, k), since groups never span a batch of k columns; each runs the columns
+ * through a temporary handle of *cfg with that group size and defer_device_input = 1: one
+ * untimed pass, then one timed by CUDA events around the ingest's launches (batch steps are
+ * not counted).  The largest group within 2 % of the fastest time per column is written to
+ * cfg->group_max and its time (microseconds per column) to *us_per_col (may be NULL); no other
+ * field of *cfg changes.  If the environment variable RID_AUTOTUNE_CACHE names a file, a stored
+ * result for the same device and configuration (m, k, s, h, data dtype, sketch precision, Omega
+ * kind, gradient mode, right_l) is returned without measuring, and a new result is appended to
+ * the file as a line "<key> <group> <microseconds>".  Needs device memory for one handle at a
+ * time besides the caller's columns.  Errors: RID_EINVAL (NULL cfg or cols, an invalid
+ * configuration, ncols < 1, ld < m, cols not in device memory), RID_ENOLIB (no device), and
+ * those of rid_init / rid_ingest; messages in rid_last_error(NULL). */
+int rid_autotune(rid_config* cfg, const void* cols, int64_t ld, int32_t ncols, double* us_per_col);
 
 /* Sketch of a block of columns that allocates nothing.  The paper has no
  * counterpart: this is a library service for callers that cannot allocate

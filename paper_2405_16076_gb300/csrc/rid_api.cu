@@ -299,31 +299,10 @@ int flush(rid_handle* h) {
   return RID_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int rid_config_default(rid_config* cfg) {
-  if (!cfg) return RID_EINVAL;
-  memset(cfg, 0, sizeof(*cfg));
-  cfg->c1 = 1.0 / 6.0;
-  cfg->c2 = 1.0 / 3.0;
-  cfg->eps = 0.5;
-  cfg->delta = 0.05;
-  cfg->c_const = 1.0;
-  cfg->lambda_mode = RID_LAMBDA_STREAMING;
-  cfg->omega_kind = RID_OMEGA_RADEMACHER;
-  cfg->data_dtype = RID_F32;
-  cfg->sketch_prec = RID_SKETCH_NATIVE;
-  cfg->n_max = 1024;
-  return RID_OK;
-}
-
-int rid_init(rid_handle** out, const rid_config* c) {
+// Host-side checks of a configuration, before any device call (the message goes to the calling
+// thread's error text).
+int check_config(const rid_config* c) {
   rid_handle* h = nullptr;
-  if (!out || !c) return fail(h, RID_EINVAL, "NULL argument");
-  *out = nullptr;
-  cudaGetLastError();                          // an error left by other code is not this handle's
   if (c->m < 1) return fail(h, RID_EINVAL, "m must be >= 1");
   if (c->k < 1 || c->k > 1024) return fail(h, RID_EINVAL, "k must be in [1, 1024]");
   if (c->s <= c->k || c->s > 4096) return fail(h, RID_EINVAL, "s must satisfy k < s <= 4096");
@@ -358,6 +337,48 @@ int rid_init(rid_handle** out, const rid_config* c) {
     if ((int64_t)c->nx * c->ny * c->nfields != c->m) return fail(h, RID_EINVAL, "gradient mode needs m = nx ny nfields");
     if (c->sketch_prec != RID_SKETCH_NATIVE)
       return fail(h, RID_EINVAL, "gradient mode runs the native-precision sketch (sketch_prec NATIVE)");
+  }
+  {
+    const int nprobe = c->h > 0 ? c->h : c->s;
+    if (nprobe - (int)floor(c->c1 * nprobe) - (int)floor(c->c2 * nprobe) < 1)
+      return fail(h, RID_EINVAL, "empty Omega_3 split");
+  }
+  return RID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rid_config_default(rid_config* cfg) {
+  if (!cfg) return RID_EINVAL;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->c1 = 1.0 / 6.0;
+  cfg->c2 = 1.0 / 3.0;
+  cfg->eps = 0.5;
+  cfg->delta = 0.05;
+  cfg->c_const = 1.0;
+  cfg->lambda_mode = RID_LAMBDA_STREAMING;
+  cfg->omega_kind = RID_OMEGA_RADEMACHER;
+  cfg->data_dtype = RID_F32;
+  cfg->sketch_prec = RID_SKETCH_NATIVE;
+  cfg->n_max = 1024;
+  return RID_OK;
+}
+
+int rid_config_check(const rid_config* cfg) {
+  if (!cfg) return fail(nullptr, RID_EINVAL, "NULL argument");
+  return check_config(cfg);
+}
+
+int rid_init(rid_handle** out, const rid_config* c) {
+  rid_handle* h = nullptr;
+  if (!out || !c) return fail(h, RID_EINVAL, "NULL argument");
+  *out = nullptr;
+  cudaGetLastError();                          // an error left by other code is not this handle's
+  {
+    const int vrc = check_config(c);
+    if (vrc != RID_OK) return vrc;
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {

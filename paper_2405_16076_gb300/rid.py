@@ -73,6 +73,8 @@ def _load():
         "rid_batch_ingest": (ctypes.c_int, [P, ctypes.c_int32, P, P, P, ctypes.c_int32]),
         "rid_sketch_noalloc": (ctypes.c_int, [ctypes.POINTER(rid_config), P, ctypes.c_int64, ctypes.c_int32,
                                               P, ctypes.c_int64, P]),
+        "rid_config_check": (ctypes.c_int, [ctypes.POINTER(rid_config)]),
+        "rid_autotune": (ctypes.c_int, [ctypes.POINTER(rid_config), P, ctypes.c_int64, ctypes.c_int32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -104,6 +106,8 @@ rid_batch_ingest = lib.rid_batch_ingest
 rid_checkpoint_size = lib.rid_checkpoint_size
 rid_checkpoint = lib.rid_checkpoint
 rid_restore = lib.rid_restore
+rid_config_check = lib.rid_config_check
+rid_autotune = lib.rid_autotune
 
 
 def batch_ingest(handles, blocks):
@@ -142,30 +146,55 @@ def _ptr(x):
     return ctypes.c_void_p(arr.ctypes.data), False
 
 
+def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
+                lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
+                sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
+                grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False):
+    """An rid_config from keyword arguments (the defaults of rid_config_default otherwise)."""
+    cfg = rid_config()
+    _check(rid_config_default(ctypes.byref(cfg)))
+    cfg.m, cfg.k, cfg.s, cfg.h = int(m), int(k), int(s), int(h)
+    cfg.c1, cfg.c2, cfg.eps, cfg.delta, cfg.c_const = c1, c2, eps, delta, c_const
+    cfg.lambda_mode = RID_LAMBDA_FIXED if lambda_mode == "fixed" else RID_LAMBDA_STREAMING
+    cfg.lambda_fixed = float(lambda_fixed)
+    cfg.omega_kind = RID_OMEGA_GAUSSIAN if omega == "gaussian" else RID_OMEGA_RADEMACHER
+    cfg.data_dtype = RID_F64 if dtype == "f64" else RID_F32
+    cfg.sketch_prec = {"native": RID_SKETCH_NATIVE, "bf16": RID_SKETCH_BF16, "bf16x2": RID_SKETCH_BF16X2}[sketch]
+    cfg.n_max = int(n_max)
+    cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    cfg.group_max = int(group_max)
+    cfg.defer_device_input = 1 if defer else 0
+    cfg.grad_dims, cfg.nx, cfg.ny, cfg.nfields = int(grad_dims), int(nx), int(ny), int(nfields)
+    cfg.right_l = int(right_l)
+    cfg.grad_coeff = 1 if grad_coeff else 0
+    cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    return cfg
+
+
+def autotune_group(cols, m, k, s, h=0, **kw):
+    """rid_autotune: the ingest group size (columns per sketch launch) measured for the
+    configuration ``make_config(m, k, s, h, **kw)`` on representative device columns ``cols``
+    (a torch tensor (b, m), row q = snapshot q).  Returns (group_max, microseconds per column);
+    RID_AUTOTUNE_CACHE in the environment names an optional cache file."""
+    cfg = make_config(m, k, s, h, **kw)
+    if not (hasattr(cols, "data_ptr") and cols.is_cuda) or cols.dim() != 2 or cols.shape[1] != int(m) \
+            or cols.stride(1) != 1:
+        raise ValueError("cols must be a device tensor (b, m) with contiguous rows")
+    us = ctypes.c_double()
+    _check(rid_autotune(ctypes.byref(cfg), ctypes.c_void_p(cols.data_ptr()), int(cols.stride(0)),
+                        int(cols.shape[0]), ctypes.byref(us)))
+    return int(cfg.group_max), float(us.value)
+
+
 class OnlineRID:
     """One streaming decomposition handle (see include/rid.h)."""
 
-    def __init__(self, m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
-                 lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
-                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
-                 grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False):
-        cfg = rid_config()
-        _check(rid_config_default(ctypes.byref(cfg)))
-        cfg.m, cfg.k, cfg.s, cfg.h = int(m), int(k), int(s), int(h)
-        cfg.c1, cfg.c2, cfg.eps, cfg.delta, cfg.c_const = c1, c2, eps, delta, c_const
-        cfg.lambda_mode = RID_LAMBDA_FIXED if lambda_mode == "fixed" else RID_LAMBDA_STREAMING
-        cfg.lambda_fixed = float(lambda_fixed)
-        cfg.omega_kind = RID_OMEGA_GAUSSIAN if omega == "gaussian" else RID_OMEGA_RADEMACHER
-        cfg.data_dtype = RID_F64 if dtype == "f64" else RID_F32
-        cfg.sketch_prec = {"native": RID_SKETCH_NATIVE, "bf16": RID_SKETCH_BF16, "bf16x2": RID_SKETCH_BF16X2}[sketch]
-        cfg.n_max = int(n_max)
-        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
-        cfg.group_max = int(group_max)
-        cfg.defer_device_input = 1 if defer else 0
-        cfg.grad_dims, cfg.nx, cfg.ny, cfg.nfields = int(grad_dims), int(nx), int(ny), int(nfields)
-        cfg.right_l = int(right_l)
-        cfg.grad_coeff = 1 if grad_coeff else 0
-        cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    def __init__(self, m, k, s, h=0, **kw):
+        """Keyword arguments as make_config: c1, c2, eps, delta, c_const, lambda_mode,
+        lambda_fixed, omega, dtype, sketch, n_max, seed, stream, group_max, defer, grad_dims,
+        nx, ny, nfields, right_l, grad_coeff."""
+        cfg = make_config(m, k, s, h, **kw)
+        dtype = kw.get("dtype", "f32")
         self.cfg = cfg
         self.t = int(k)
         self.m = int(m)

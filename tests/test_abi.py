@@ -84,3 +84,40 @@ def test_no_cpu_fallback_without_device(lib):
     with pytest.raises(rid.RIDError) as e:
         rid.OnlineRID(m=1000, k=5, s=23, h=12)
     assert e.value.code == rid.RID_ENOLIB
+
+
+def test_config_check_matches_init_validation(lib):
+    from paper_2405_16076_gb300 import rid
+    assert rid.rid_config_check(None) == rid.RID_EINVAL
+    cfg = rid.make_config(100, 10, 43, 12)
+    assert rid.rid_config_check(ctypes.byref(cfg)) == rid.RID_OK
+    cfg.s = 10                                           # s <= k
+    assert rid.rid_config_check(ctypes.byref(cfg)) == rid.RID_EINVAL
+    assert b"s must" in rid.rid_last_error(None)
+    cfg = rid.make_config(100, 10, 43, 12, dtype="f64", sketch="bf16x2")
+    assert rid.rid_config_check(ctypes.byref(cfg)) == rid.RID_EINVAL
+    assert b"FP32" in rid.rid_last_error(None)
+    cfg = rid.make_config(100, 10, 43, 12, group_max=65)
+    assert rid.rid_config_check(ctypes.byref(cfg)) == rid.RID_EINVAL
+
+
+def test_autotune_argument_checks_without_device(lib):
+    import torch
+    from paper_2405_16076_gb300 import rid
+    dummy = ctypes.c_void_p(16)                          # never dereferenced: every check fails first
+    us = ctypes.c_double()
+    cfg = rid.make_config(1000, 10, 43, 12)
+    assert rid.rid_autotune(None, dummy, 1000, 8, ctypes.byref(us)) == rid.RID_EINVAL
+    assert rid.rid_autotune(ctypes.byref(cfg), None, 1000, 8, ctypes.byref(us)) == rid.RID_EINVAL
+    assert rid.rid_autotune(ctypes.byref(cfg), dummy, 1000, 0, ctypes.byref(us)) == rid.RID_EINVAL
+    assert b"ncols" in rid.rid_last_error(None)
+    assert rid.rid_autotune(ctypes.byref(cfg), dummy, 999, 8, ctypes.byref(us)) == rid.RID_EINVAL
+    bad = rid.make_config(1000, 10, 9, 12)
+    assert rid.rid_autotune(ctypes.byref(bad), dummy, 1000, 8, ctypes.byref(us)) == rid.RID_EINVAL
+    assert b"s must" in rid.rid_last_error(None)
+    rc = rid.rid_autotune(ctypes.byref(cfg), dummy, 1000, 8, ctypes.byref(us))
+    if torch.cuda.is_available():
+        assert rc == rid.RID_EINVAL                      # a host address is refused before any launch
+    else:
+        assert rc == rid.RID_ENOLIB
+    assert cfg.group_max == 0                            # nothing written on failure
