@@ -813,7 +813,7 @@ def main():
         "config": {"workload": cfg["workload"], "m": m, "n": n, "block": b, "k": cfg["k"], "s": cfg["s"],
                    "h": cfg["h"], "omega": "rademacher", "lambda": "streaming", "sketch": args.sketch,
                    "group": args.group, "autotune": tune,
-                   "l2": "inputs larger than L2 (57 MB per snapshot, whole stream resident in HBM)",
+                   "l2": f"inputs larger than L2 ({m * 4 / 1e6:.0f} MB per snapshot, whole stream resident in HBM)",
                    "parallelism": f"{world} independent streams"},
         "e2e": {"value": e2e_val, "unit": "snapshots/s", "h2d_bytes_per_step": int(n * m * 4),
                 "d2h_bytes_per_step": int(cfg["k"] * n * 8 + cfg["k"] * 8)},
