@@ -140,23 +140,36 @@ int grow(rid_handle* h, int64_t need) {
   while (cap < need) cap *= 2;
   join(h);
   CK(cudaStreamSynchronize(h->st));
-  double *S, *Slev = nullptr, *P, *cand, *hpart, *zq, *Sg = nullptr;
-  CK(dalloc(&S, (size_t)d.rows * cap));
-  if (d.grad) CK(dalloc(&Slev, (size_t)d.s * cap));
-  CK(dalloc(&P, (size_t)d.t * cap));
-  CK(dalloc(&cand, (size_t)4 * d.t * cap));
-  CK(dalloc(&hpart, (size_t)hpart_len(d, cap)));
-  CK(dalloc(&zq, (size_t)2 * d.t * cap));
-  if (d.grad_coeff) CK(dalloc(&Sg, (size_t)2 * d.s * cap));
-  CK(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)d.t * cap, h->st));
-  CK(cudaMemsetAsync(cand, 0, sizeof(double) * (size_t)4 * d.t * cap, h->st));
+  // New arrays first; on any failure they are released and the handle keeps its current ones.
+  double *S = nullptr, *Slev = nullptr, *P = nullptr, *cand = nullptr, *hpart = nullptr, *zq = nullptr,
+         *Sg = nullptr;
+  cudaError_t e = dalloc(&S, (size_t)d.rows * cap);
+  if (e == cudaSuccess && d.grad) e = dalloc(&Slev, (size_t)d.s * cap);
+  if (e == cudaSuccess) e = dalloc(&P, (size_t)d.t * cap);
+  if (e == cudaSuccess) e = dalloc(&cand, (size_t)4 * d.t * cap);
+  if (e == cudaSuccess) e = dalloc(&hpart, (size_t)hpart_len(d, cap));
+  if (e == cudaSuccess) e = dalloc(&zq, (size_t)2 * d.t * cap);
+  if (e == cudaSuccess && d.grad_coeff) e = dalloc(&Sg, (size_t)2 * d.s * cap);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P, 0, sizeof(double) * (size_t)d.t * cap, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cand, 0, sizeof(double) * (size_t)4 * d.t * cap, h->st);
+  if (e == cudaSuccess && d.S) {
+    e = cudaMemcpyAsync(S, d.S, sizeof(double) * (size_t)d.rows * d.n_cap, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess && d.grad)
+      e = cudaMemcpyAsync(Slev, d.Slev, sizeof(double) * (size_t)d.s * d.n_cap, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess && d.grad_coeff)
+      e = cudaMemcpyAsync(Sg, d.Sg, sizeof(double) * 2 * (size_t)d.s * d.n_cap, cudaMemcpyDeviceToDevice, h->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P, d.P, sizeof(double) * (size_t)d.t * d.n_cap, cudaMemcpyDeviceToDevice, h->st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(h->st);
+    for (double* p : {S, Slev, P, cand, hpart, zq, Sg})
+      if (p) cudaFree(p);
+    return fail(h, e == cudaErrorMemoryAllocation ? RID_ENOMEM : RID_ECUDA,
+                std::string("capacity growth: ") + cudaGetErrorString(e));
+  }
   if (d.S) {
-    CK(cudaMemcpyAsync(S, d.S, sizeof(double) * (size_t)d.rows * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
-    if (d.grad) CK(cudaMemcpyAsync(Slev, d.Slev, sizeof(double) * (size_t)d.s * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
-    if (d.grad_coeff)
-      CK(cudaMemcpyAsync(Sg, d.Sg, sizeof(double) * 2 * (size_t)d.s * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(P, d.P, sizeof(double) * (size_t)d.t * d.n_cap, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaStreamSynchronize(h->st));
     cudaFree(d.S);
     if (d.grad) cudaFree(d.Slev);
     cudaFree(d.P);
