@@ -110,7 +110,12 @@ int rid_config_check(const rid_config* cfg);
  * sketch of [a; G a], i.e. Omega a + Omega_g (G a) with an independent Omega_g
  * (s x 2m), and ||a||^2 + ||G a||^2; G is the least-squares gradient on each
  * field's nx x ny grid graph (central differences inside, one-sided at the
- * boundary, unit spacing). */
+ * boundary, unit spacing).
+ * On any failure every device allocation made so far is released and *out is NULL.  For tests
+ * of these paths, RID_FAULT_INJECT=alloc:<n> in the environment when rid_init starts makes the
+ * n-th device allocation from then on -- in this rid_init or in a later capacity growth of a
+ * handle -- fail as if the device were out of memory (RID_ENOMEM); a growth that fails leaves
+ * its handle as it was, with the recorded columns still pending. */
 int rid_init(rid_handle** out, const rid_config* cfg);
 
 /* Ingest ncols >= 0 columns (Algorithm 3, the loop body for each column):

@@ -7,8 +7,10 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -79,10 +81,26 @@ int fail(rid_handle* h, int code, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                 \
   } while (0)
 
+// Allocation-failure injection, for tests of the error paths (no device fault is involved): with
+// RID_FAULT_INJECT=alloc:<n> in the environment when rid_init starts, the n-th device allocation
+// of the handles from then on -- inside that rid_init or in a later capacity growth -- reports
+// cudaErrorMemoryAllocation without calling cudaMalloc.  Every rid_init re-reads the variable
+// (unset: off).
+std::atomic<int64_t> g_alloc_countdown{0};
+
+void arm_fault_injection() {
+  const char* v = getenv("RID_FAULT_INJECT");
+  int64_t n = 0;
+  if (v && strncmp(v, "alloc:", 6) == 0) n = strtoll(v + 6, nullptr, 10);
+  g_alloc_countdown.store(n > 0 ? n : 0);
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
+  if (g_alloc_countdown.load(std::memory_order_relaxed) > 0 && g_alloc_countdown.fetch_sub(1) == 1)
+    return cudaErrorMemoryAllocation;
   return cudaMalloc((void**)p, n * sizeof(T));
 }
 
@@ -393,6 +411,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
     const int vrc = check_config(c);
     if (vrc != RID_OK) return vrc;
   }
+  arm_fault_injection();
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -515,8 +534,8 @@ int rid_init(rid_handle** out, const rid_config* c) {
     char* y = nullptr;
     char* wr = nullptr;
     AL(y, (size_t)d.m_pad * d.right_l * h->esize);
-    AL(wr, rid::right_w_bytes(d));
     d.Y = y;
+    AL(wr, rid::right_w_bytes(d));
     d.Wr = wr;
     if (cudaMemset(d.Y, 0, (size_t)d.m_pad * d.right_l * h->esize) != cudaSuccess) { rc = RID_ECUDA; goto fail_alloc; }
   }
