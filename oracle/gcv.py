@@ -13,7 +13,7 @@ Test infrastructure (see ``oracle/__init__``).  Plain numpy, following the paper
   evaluated from its definition (the s x s matrix C is formed).
 * lam* = the golden-section minimiser of GCV over [1e-3, 1e3] at the end of the stream.
 
-Readings (also in the design doc): the search runs on log10(lam) in [-3, 3] (the range spans six
+Readings: the search runs on log10(lam) in [-3, 3] (the range spans six
 decades) with golden ratio steps until the bracket is narrower than 1e-3 in log10(lam), and
 returns the midpoint of the last bracket; GCV of a candidate is compared with plain "<" (ties
 keep the left probe); the gradient operators G^p are those of ``oracle.gradient`` (one-sided at

@@ -4,8 +4,7 @@ Test infrastructure (see ``oracle/__init__``).  Plain numpy, no blocking, no
 fusion; each step follows the paper's order and notation.  Library primitives
 used as single steps: ``solve``, ``lstsq``, ``pinv``, ``qr``, ``eigvalsh``.
 
-Readings where the paper is silent, ambiguous or at odds with itself (each is
-repeated in DESIGN.md):
+Readings where the paper is silent, ambiguous or at odds with itself:
 
 R1  Omega scale.  Omega has unit-variance entries (``randn`` in Algorithm 3);
     every quantity that meets unsketched data uses the scaled sketch
