@@ -258,6 +258,35 @@ int rid_restore(rid_handle* h, const void* buf, int64_t bytes);
 int rid_profile(rid_handle* h, int32_t enable);
 int rid_profile_read(rid_handle* h, double ms[3], int64_t kernels[3], int64_t groups[3]);
 
+/* One record of the per-batch log: what a batch step decided (the quantities of the paper's
+ * "update decision" rows, Algorithm 8 with Eqs. 23 and 36-37). */
+typedef struct {
+  int64_t batch;        /* 0-based index of the batch step */
+  int64_t n_obs;        /* columns observed when it ran (its P covers them) */
+  double lambda;        /* its ridge parameter (Eq. 23's streaming value, or the fixed one) */
+  double fro2;          /* ||A_obs||_F^2 it used */
+  double est_sq[4];     /* signed NA-Hutch++ estimates of ||A_obs - A_J P_q||_F^2, q = 4..7 */
+  double est_unc[4];    /* rounding uncertainty of each estimate relative to fro2 (0 for FP64 sketches) */
+  double gram_shift;    /* Tikhonov shift of the basis Gram relative to its largest diagonal entry */
+  int32_t q_star;       /* the candidate committed to P (4..7) */
+  int32_t n_active;     /* occupied basis slots after the step */
+  int32_t n_kept;       /* of those, slots that held the same column before the step */
+  int32_t n_new;        /* of those, slots filled by the step */
+} rid_log_record;
+
+/* Keep a log of the last `capacity` batch steps on the device (0 turns it off and frees it);
+ * the log starts empty with the next batch step.  Each step adds two small device-to-device
+ * copies on the handle's own streams (none while the log is off), so logging also works inside a
+ * captured CUDA graph.  Synchronizes.  Errors: RID_EINVAL (capacity outside [0, 2^20]),
+ * RID_ENOMEM, RID_ECUDA. */
+int rid_log_enable(rid_handle* h, int32_t capacity);
+
+/* Copy the most recent min(max_records, steps logged, capacity) records, oldest first, to out
+ * (host) and their number to *n_out (may be NULL).  Synchronizes; pending columns are not
+ * flushed.  rid_reset and rid_restore start the log afresh.  Errors: RID_EINVAL (max_records < 0,
+ * NULL out with max_records > 0), RID_ESTATE (the log is off), RID_ECUDA. */
+int rid_get_log(rid_handle* h, rid_log_record* out, int32_t max_records, int32_t* n_out);
+
 /* Wait for the handle's stream; report deferred device errors. */
 int rid_sync(rid_handle* h);
 

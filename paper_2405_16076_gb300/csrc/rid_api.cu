@@ -58,7 +58,18 @@ struct rid_handle {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[3];
   int64_t kernels[3];
   float* tg_part;
+  // per-batch log (rid_log_enable): log_cap slots of kLogSlot bytes on the device, batch b in
+  // slot b % log_cap; log_first = the first batch step it covers
+  char* log_dev;
+  int log_cap;
+  int log_first;
 };
+
+// A log slot: the step's scal[] at 0 (after its tail), lambda and ||A_obs||^2 at 128 (after its
+// lambda part, before the next step's lambda part overwrites them), meta[] at 144.
+constexpr size_t kLogSlot = 256;
+static_assert(144 + sizeof(int) * rid::META_LEN <= kLogSlot && sizeof(double) * rid::SCAL_LEN <= 128,
+              "log slot layout");
 
 static thread_local std::string g_init_err;
 
@@ -241,6 +252,12 @@ int run_batch(rid_handle* h) {
   dl.SSt = snap;
   dl.fro2 = snap + ss;
   const int nl = rid::launch_batch_lambda(dl, b, h->stl);
+  if (nl && h->log_cap > 0) {
+    char* slot = h->log_dev + (size_t)(b % h->log_cap) * kLogSlot;
+    CK(cudaMemcpyAsync(slot + 128, dl.scal + rid::SCAL_LAMBDA, sizeof(double), cudaMemcpyDeviceToDevice, h->stl));
+    CK(cudaMemcpyAsync(slot + 136, dl.scal + rid::SCAL_FRO0 + (b & 3), sizeof(double), cudaMemcpyDeviceToDevice,
+                       h->stl));
+  }
   CK(cudaEventRecord(h->ev_lambda[b & 1], h->stl));
   CK(cudaStreamWaitEvent(h->stb, h->ev_lambda[b & 1], 0));
   const int nt = nl ? rid::launch_batch_tail(db, h->count, h->n_obs, h->n_prev, b, h->stb, h->ev_scores[b & 1],
@@ -249,6 +266,11 @@ int run_batch(rid_handle* h) {
   if (nl == 0 || nt == 0) {
     cudaGetLastError();
     return fail(h, RID_ECUDA, "batch step launch failed (cooperative or cluster launch refused)");
+  }
+  if (h->log_cap > 0) {
+    char* slot = h->log_dev + (size_t)(b % h->log_cap) * kLogSlot;
+    CK(cudaMemcpyAsync(slot, db.scal, sizeof(double) * rid::SCAL_LEN, cudaMemcpyDeviceToDevice, h->stb));
+    CK(cudaMemcpyAsync(slot + 144, db.meta, sizeof(int) * rid::META_LEN, cudaMemcpyDeviceToDevice, h->stb));
   }
   CK(cudaEventRecord(h->ev_tail[b & 1], h->stb));
   const int nk = nl + nt;
@@ -950,6 +972,7 @@ int rid_restore(rid_handle* h, const void* buf, int64_t bytes) {
   h->n_prev = cn.n_prev;
   h->count = cn.count;
   h->batch = cn.batch;
+  h->log_first = h->batch;
   h->finalized = cn.finalized != 0;
   CkptPlan pl;
   {
@@ -1041,7 +1064,67 @@ int rid_reset(rid_handle* h) {
   h->n_obs = 0;
   h->n_prev = 0;
   h->batch = 0;
+  h->log_first = 0;
   h->finalized = false;
+  return RID_OK;
+}
+
+int rid_log_enable(rid_handle* h, int32_t capacity) {
+  if (!h) return RID_EINVAL;
+  if (capacity < 0 || capacity > (1 << 20)) return fail(h, RID_EINVAL, "capacity must be in [0, 1048576]");
+  join(h);
+  CK(cudaStreamSynchronize(h->st));
+  if (h->log_dev) cudaFree(h->log_dev);
+  h->log_dev = nullptr;
+  h->log_cap = 0;
+  h->log_first = h->batch;
+  if (capacity > 0) {
+    char* p = nullptr;
+    CK(dalloc(&p, (size_t)capacity * kLogSlot));
+    h->log_dev = p;
+    CK(cudaMemsetAsync(p, 0, (size_t)capacity * kLogSlot, h->st));
+    h->log_cap = capacity;
+  }
+  return RID_OK;
+}
+
+int rid_get_log(rid_handle* h, rid_log_record* out, int32_t max_records, int32_t* n_out) {
+  if (!h) return RID_EINVAL;
+  if (n_out) *n_out = 0;
+  if (max_records < 0 || (max_records > 0 && !out)) return fail(h, RID_EINVAL, "bad output buffer");
+  if (h->log_cap == 0) return fail(h, RID_ESTATE, "the log is off (rid_log_enable)");
+  join(h);
+  int64_t nrec = h->batch - h->log_first;
+  if (nrec > h->log_cap) nrec = h->log_cap;
+  if (nrec > max_records) nrec = max_records;
+  if (nrec < 0) nrec = 0;
+  std::vector<char> buf((size_t)h->log_cap * kLogSlot);
+  CK(cudaMemcpyAsync(buf.data(), h->log_dev, buf.size(), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  for (int64_t i = 0; i < nrec; ++i) {
+    const int64_t b = h->batch - nrec + i;
+    const char* slot = buf.data() + (size_t)(b % h->log_cap) * kLogSlot;
+    double sc[rid::SCAL_LEN], lf[2];
+    int mt[rid::META_LEN];
+    memcpy(sc, slot, sizeof(sc));
+    memcpy(lf, slot + 128, sizeof(lf));
+    memcpy(mt, slot + 144, sizeof(mt));
+    rid_log_record& r = out[i];
+    r.batch = mt[rid::META_BATCH] - 1;
+    r.n_obs = mt[rid::META_NPREV];
+    r.lambda = lf[0];
+    r.fro2 = lf[1];
+    for (int q = 0; q < 4; ++q) {
+      r.est_sq[q] = sc[rid::SCAL_EST + q];
+      r.est_unc[q] = sc[rid::SCAL_UNC + q];
+    }
+    r.gram_shift = sc[rid::SCAL_GSHIFT];
+    r.q_star = mt[rid::META_QSTAR];
+    r.n_active = mt[rid::META_NACT];
+    r.n_kept = mt[rid::META_NKEPT];
+    r.n_new = mt[rid::META_NNEW];
+  }
+  if (n_out) *n_out = (int32_t)nrec;
   return RID_OK;
 }
 
@@ -1062,6 +1145,7 @@ void rid_destroy(rid_handle* h) {
   if (h->tg_part) cudaFree(h->tg_part);
   if (h->tc_npart) cudaFree(h->tc_npart);
   if (h->snap) cudaFree(h->snap);
+  if (h->log_dev) cudaFree(h->log_dev);
   destroy_sync_objects(h);
   delete h;
 }

@@ -38,6 +38,15 @@ class rid_config(ctypes.Structure):
     ]
 
 
+class rid_log_record(ctypes.Structure):
+    _fields_ = [
+        ("batch", ctypes.c_int64), ("n_obs", ctypes.c_int64), ("lambda_", ctypes.c_double),
+        ("fro2", ctypes.c_double), ("est_sq", ctypes.c_double * 4), ("est_unc", ctypes.c_double * 4),
+        ("gram_shift", ctypes.c_double), ("q_star", ctypes.c_int32), ("n_active", ctypes.c_int32),
+        ("n_kept", ctypes.c_int32), ("n_new", ctypes.c_int32),
+    ]
+
+
 class RIDError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"rid error {code}: {msg}")
@@ -75,6 +84,8 @@ def _load():
                                               P, ctypes.c_int64, P]),
         "rid_config_check": (ctypes.c_int, [ctypes.POINTER(rid_config)]),
         "rid_autotune": (ctypes.c_int, [ctypes.POINTER(rid_config), P, ctypes.c_int64, ctypes.c_int32, P]),
+        "rid_log_enable": (ctypes.c_int, [H, ctypes.c_int32]),
+        "rid_get_log": (ctypes.c_int, [H, P, ctypes.c_int32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -108,6 +119,8 @@ rid_checkpoint = lib.rid_checkpoint
 rid_restore = lib.rid_restore
 rid_config_check = lib.rid_config_check
 rid_autotune = lib.rid_autotune
+rid_log_enable = lib.rid_log_enable
+rid_get_log = lib.rid_get_log
 
 
 def batch_ingest(handles, blocks):
@@ -368,6 +381,23 @@ class OnlineRID:
 
     def sync(self):
         _check(rid_sync(self.h), self.h)
+
+    def log_enable(self, capacity=1024):
+        """Keep the last ``capacity`` batch steps' decisions on the device (0: off)."""
+        _check(rid_log_enable(self.h, int(capacity)), self.h)
+
+    def log(self, max_records=1 << 20):
+        """The logged batch steps, oldest first, as dicts (see rid_log_record in include/rid.h)."""
+        cap = max(0, int(max_records))
+        buf = (rid_log_record * max(cap, 1))()
+        n = ctypes.c_int32()
+        _check(rid_get_log(self.h, ctypes.cast(buf, ctypes.c_void_p), cap, ctypes.byref(n)), self.h)
+        out = []
+        for r in buf[:n.value]:
+            out.append({"batch": r.batch, "n_obs": r.n_obs, "lambda": r.lambda_, "fro2": r.fro2,
+                        "est_sq": list(r.est_sq), "est_unc": list(r.est_unc), "gram_shift": r.gram_shift,
+                        "q_star": r.q_star, "n_active": r.n_active, "n_kept": r.n_kept, "n_new": r.n_new})
+        return out
 
     def reset(self):
         _check(rid_reset(self.h), self.h)

@@ -43,13 +43,16 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared_functions()) <= exported
 
 
-def test_ctypes_layout_matches_c(lib):
-    from paper_2405_16076_gb300.rid import rid_config
-    fields = [f for f, _ in rid_config._fields_]
+@pytest.mark.parametrize("struct", ["rid_config", "rid_log_record"])
+def test_ctypes_layout_matches_c(lib, struct):
+    from paper_2405_16076_gb300 import rid
+    cls = getattr(rid, struct)
+    fields = [f for f, _ in cls._fields_]
+    cname = {"lambda_": "lambda"}                   # a Python keyword, renamed in the binding
     src = "#include <stdio.h>\n#include <stddef.h>\n#include \"rid.h\"\nint main(void){\n"
-    src += 'printf("%zu\\n", sizeof(rid_config));\n'
+    src += f'printf("%zu\\n", sizeof({struct}));\n'
     for f in fields:
-        src += f'printf("%zu\\n", offsetof(rid_config, {f}));\n'
+        src += f'printf("%zu\\n", offsetof({struct}, {cname.get(f, f)}));\n'
     src += "return 0;}\n"
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
@@ -57,9 +60,9 @@ def test_ctypes_layout_matches_c(lib):
         open(c, "w").write(src)
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
-    assert vals[0] == ctypes.sizeof(rid_config)
+    assert vals[0] == ctypes.sizeof(cls)
     for f, off in zip(fields, vals[1:]):
-        assert getattr(rid_config, f).offset == off, f
+        assert getattr(cls, f).offset == off, f
 
 
 def test_defaults_and_validation_without_device(lib):
@@ -121,3 +124,9 @@ def test_autotune_argument_checks_without_device(lib):
     else:
         assert rc == rid.RID_ENOLIB
     assert cfg.group_max == 0                            # nothing written on failure
+
+
+def test_log_calls_reject_null_handles(lib):
+    from paper_2405_16076_gb300 import rid
+    assert rid.rid_log_enable(None, 4) == rid.RID_EINVAL
+    assert rid.rid_get_log(None, None, 0, None) == rid.RID_EINVAL
