@@ -130,3 +130,39 @@ def test_log_calls_reject_null_handles(lib):
     from paper_2405_16076_gb300 import rid
     assert rid.rid_log_enable(None, 4) == rid.RID_EINVAL
     assert rid.rid_get_log(None, None, 0, None) == rid.RID_EINVAL
+
+
+def test_plain_c_client_links_and_validates(lib):
+    """The boundary is usable from C alone: a C program includes rid.h, links librid.so, checks
+    a configuration and reads the error text; rid_init reports RID_ENOLIB without a device (or
+    succeeds with one)."""
+    src = r'''
+#include <stdio.h>
+#include "rid.h"
+int main(void) {
+  rid_config c;
+  if (rid_config_default(&c) != RID_OK) return 10;
+  c.m = 4096; c.k = 20; c.s = 83; c.h = 30;
+  if (rid_config_check(&c) != RID_OK) return 11;
+  c.s = 20;
+  if (rid_config_check(&c) != RID_EINVAL) return 12;
+  if (!rid_last_error(NULL) || !rid_last_error(NULL)[0]) return 13;
+  c.s = 83;
+  rid_handle* h = 0;
+  int rc = rid_init(&h, &c);
+  if (rc == RID_OK) { rid_destroy(h); printf("device\n"); return 0; }
+  if (rc != RID_ENOLIB || h != 0) return 14;
+  printf("no device\n");
+  return 0;
+}
+'''
+    libdir = os.path.dirname(LIB)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "client.c")
+        exe = os.path.join(d, "client")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), c,
+                        "-L", libdir, "-lrid", f"-Wl,-rpath,{libdir}", "-o", exe], check=True)
+        r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() in ("device", "no device")
