@@ -552,8 +552,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sketch", default="bf16x2", choices=["bf16x2", "bf16", "native"])
     ap.add_argument("--group", type=int, default=64,
-                    help="columns per sketch launch (1..64); 0 = measure it with rid_autotune on the "
-                         "first 2k snapshots before the timed region")
+                    help="columns per sketch launch (1..64); 0 = measure it and the CTAs per launch "
+                         "with rid_autotune on the first 2k snapshots before the timed region")
     ap.add_argument("--grad-coeff", action="store_true",
                     help="gradient mode: keep Omega G^p a and report Sec. 3.4's gradient-augmented coefficients")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
@@ -601,13 +601,14 @@ def main():
     if args.group == 0:
         # the group size measured on this stream's first two batches, outside the timed region
         ntune = min(n, 2 * cfg["k"])
-        gbest, us = rid.autotune_group(X[:ntune], m, cfg["k"], cfg["s"], cfg["h"], dtype="f32", sketch=args.sketch,
-                                       seed=rank_seeds(rank)[1], stream=st, right_l=cfg.get("right_l", 0), **gkw)
+        gbest, cbest, us = rid.autotune_group(X[:ntune], m, cfg["k"], cfg["s"], cfg["h"], dtype="f32",
+                                              sketch=args.sketch, seed=rank_seeds(rank)[1], stream=st,
+                                              right_l=cfg.get("right_l", 0), **gkw)
         args.group = gbest
-        tune = {"group_max": gbest, "us_per_column": us, "columns": ntune}
+        tune = {"group_max": gbest, "ingest_ctas": cbest, "us_per_column": us, "columns": ntune}
     h = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=args.sketch, n_max=n,
                       seed=rank_seeds(rank)[1], stream=st, defer=True, group_max=args.group,
-                      right_l=cfg.get("right_l", 0), **gkw)
+                      right_l=cfg.get("right_l", 0), ingest_ctas=tune["ingest_ctas"] if tune else 0, **gkw)
     Jd = torch.empty(cfg["k"], dtype=torch.int64, device=dev)
     Pd = torch.empty((n, cfg["k"]), dtype=torch.float64, device=dev)
 

@@ -86,6 +86,11 @@ typedef struct rid_config {
   int32_t grad_coeff;    /* 1 = keep Omega G^p a_j (p = 1, 2) during the ingest for the
                             gradient-augmented coefficients of Sec. 3.4 (needs grad_dims = 2;
                             see rid_gradient_coefficients) */
+  int32_t ingest_ctas;   /* CTAs per sketch launch; 0 = automatic (tensor cores: every SM for the
+                            first batch, two thirds of them beside the batch steps afterwards;
+                            native path: up to four per SM).  A positive value replaces the
+                            tensor-core ingest's count after the first batch, or caps the native
+                            one, and is clamped to the automatic maximum (see rid_autotune) */
 } rid_config;
 
 typedef struct rid_handle rid_handle;
@@ -297,23 +302,27 @@ int rid_reset(rid_handle* h);
  * rid_init, rid_config_check, rid_autotune or rid_sketch_noalloc of the calling thread). */
 const char* rid_last_error(const rid_handle* h);
 
-/* Pick cfg->group_max -- the ingest's group size, i.e. how many device columns one sketch
- * launch reads (no counterpart in the paper: a tuning of this library's ingest) -- by
- * measurement on the current device.  cols: ncols >= 1 representative columns of the stream
- * (device memory, m x ncols column-major, ld >= m), read and not modified.  Candidates are the
- * powers of two from 1 to 64 (tensor-core sketches) or 16 (native precision), up to the first
- * one >= min(ncols, k), since groups never span a batch of k columns; each runs the columns
- * through a temporary handle of *cfg with that group size and defer_device_input = 1: one
- * untimed pass, then one timed by CUDA events around the ingest's launches (batch steps are
- * not counted).  The largest group within 2 % of the fastest time per column is written to
- * cfg->group_max and its time (microseconds per column) to *us_per_col (may be NULL); no other
- * field of *cfg changes.  If the environment variable RID_AUTOTUNE_CACHE names a file, a stored
- * result for the same device and configuration (m, k, s, h, data dtype, sketch precision, Omega
- * kind, gradient mode, right_l) is returned without measuring, and a new result is appended to
- * the file as a line "<key> <group> <microseconds>".  Needs device memory for one handle at a
- * time besides the caller's columns.  Errors: RID_EINVAL (NULL cfg or cols, an invalid
- * configuration, ncols < 1, ld < m, cols not in device memory), RID_ENOLIB (no device), and
- * those of rid_init / rid_ingest; messages in rid_last_error(NULL). */
+/* Pick the ingest's launch shape for *cfg on the current device by measurement (no counterpart
+ * in the paper: a tuning of this library's ingest): cfg->group_max, how many device columns one
+ * sketch launch reads, and cfg->ingest_ctas, the CTAs per sketch launch.  cols: ncols >= 1
+ * representative columns of the stream (device memory, m x ncols column-major, ld >= m), read
+ * and not modified; 2k columns cover two batch steps.  Each candidate runs the columns through a
+ * temporary handle of *cfg with defer_device_input = 1: one untimed pass, then three passes
+ * timed on the host clock from the first rid_ingest to the end of rid_sync -- the ingest and
+ * the batch steps it triggers -- of which the fastest counts.  First the group size, with the
+ * automatic CTA count: the powers of two from 1 to 64 (tensor-core sketches) or 16 (native
+ * precision), up to the first one >= min(ncols, k) since groups never span a batch of k columns;
+ * the largest group within 2 % of the fastest time wins.  Then, for that group, the CTA count:
+ * automatic (0), then 1/6 .. 6/6 of the SMs (tensor cores) or 1, 2, 3 per SM (native path); the
+ * first within 2 % of the fastest wins.  No other field of *cfg changes; *us_per_col (may be
+ * NULL) receives the winner's time per column in microseconds.  If the environment variable
+ * RID_AUTOTUNE_CACHE names a file, a stored result for the same device and configuration (m,
+ * k, s, h, data dtype, sketch precision, Omega kind, gradient mode and coefficients, right_l) is
+ * returned without measuring, and a new result is appended to the file as a line
+ * "<key> <group> <ctas> <microseconds>".  Needs device memory for one handle at a time besides
+ * the caller's columns.  Errors: RID_EINVAL (NULL cfg or cols, an invalid configuration,
+ * ncols < 1, ld < m, cols not in device memory), RID_ENOLIB (no device), and those of rid_init /
+ * rid_ingest; messages in rid_last_error(NULL). */
 int rid_autotune(rid_config* cfg, const void* cols, int64_t ld, int32_t ncols, double* us_per_col);
 
 /* Sketch of a block of columns that allocates nothing.  The paper has no

@@ -1,16 +1,19 @@
-// Autotuning of the ingest's group size: the number of device columns that one sketch launch
-// reads (one HBM read of each column sketches all s + h rows for the whole group).  Larger groups
-// spread the on-chip generation of Omega and the fill of each launch's pipeline over more
-// columns; smaller groups start earlier and, beside a batch step running on its own streams,
-// hold the SMs for shorter stretches.  Which wins depends on m, s + h, the precision and the
-// device, so it is measured: each candidate runs the caller's columns through a handle of its own
-// (public entry points only, nothing here touches device memory directly) and the device time of
-// the ingest phases per column is compared.  Host code only.
+// Autotuning of the ingest's launch shape: the group size (how many device columns one sketch
+// launch reads; one HBM read of each column sketches all s + h rows for the whole group) and the
+// number of CTAs per sketch launch.  Larger groups spread the on-chip generation of Omega and the
+// fill of each launch's pipeline over more columns; smaller groups start earlier.  Fewer CTAs
+// leave more SMs to the batch step that runs beside the ingest on its own streams; more CTAs
+// read faster.  Which wins depends on m, s + h, k, the precision and the device, so it is
+// measured: each candidate runs the caller's columns through a handle of its own (public entry
+// points only; nothing here touches device memory directly), and the wall time of a whole pass
+// -- the ingest and the batch steps it triggers, up to the synchronization -- is compared.
+// Host code only.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -24,33 +27,36 @@ int fail_global(int code, const char* msg) {
   return code;
 }
 
-// Cache key: the device and every configuration field the ingest's cost depends on.
-std::string tune_key(const rid_config* c, int dev) {
+// Cache key: the device and every configuration field the pass's cost depends on.
+std::string tune_key(const rid_config* c, int dev, int* n_sm) {
   cudaDeviceProp p;
   memset(&p, 0, sizeof(p));
   cudaGetDeviceProperties(&p, dev);
+  *n_sm = p.multiProcessorCount;
   std::string name(p.name);
   for (char& ch : name)
     if (ch == ' ' || ch == '\t' || ch == '|') ch = '_';
   char buf[512];
-  snprintf(buf, sizeof(buf), "%s|sm%d|cc%d.%d|m%lld|k%d|s%d|h%d|dt%d|sp%d|om%d|gd%d|rl%d",
+  snprintf(buf, sizeof(buf), "%s|sm%d|cc%d.%d|m%lld|k%d|s%d|h%d|dt%d|sp%d|om%d|gd%d|rl%d|gc%d",
            name.c_str(), p.multiProcessorCount, p.major, p.minor, (long long)c->m, c->k, c->s, c->h,
-           c->data_dtype, c->sketch_prec, c->omega_kind, c->grad_dims, c->right_l);
+           c->data_dtype, c->sketch_prec, c->omega_kind, c->grad_dims, c->right_l, c->grad_coeff);
   return std::string(buf);
 }
 
-// The last entry of the cache file for this key, if any.  Lines: "<key> <group> <us per column>".
-bool cache_lookup(const char* path, const std::string& key, int gmax, int* g, double* us) {
+// The last entry of the cache file for this key, if any.
+// Lines: "<key> <group> <ctas> <microseconds per column>".
+bool cache_lookup(const char* path, const std::string& key, int gmax, int* g, int* ctas, double* us) {
   FILE* f = fopen(path, "r");
   if (!f) return false;
   char line[1024];
   char k[1024];
   bool found = false;
   while (fgets(line, sizeof(line), f)) {
-    int gv = 0;
+    int gv = 0, cv = 0;
     double uv = 0.0;
-    if (sscanf(line, "%1023s %d %lf", k, &gv, &uv) == 3 && key == k && gv >= 1 && gv <= gmax) {
+    if (sscanf(line, "%1023s %d %d %lf", k, &gv, &cv, &uv) == 4 && key == k && gv >= 1 && gv <= gmax && cv >= 0) {
       *g = gv;
+      *ctas = cv;
       *us = uv;
       found = true;
     }
@@ -59,40 +65,57 @@ bool cache_lookup(const char* path, const std::string& key, int gmax, int* g, do
   return found;
 }
 
-void cache_store(const char* path, const std::string& key, int g, double us) {
+void cache_store(const char* path, const std::string& key, int g, int ctas, double us) {
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %.6g\n", key.c_str(), g, us);
+  fprintf(f, "%s %d %d %.6g\n", key.c_str(), g, ctas, us);
   fclose(f);
 }
 
-// Device time (microseconds per column) of the ingest phases -- sketch launch, reduction, copy
-// into the buffer slots, norms, SS^T -- for groups of at most g columns: one untimed pass, then
-// one pass bracketed by the handle's own event pairs.  Batch steps that the columns trigger run
-// on their own streams and are not counted.
-int time_group(const rid_config* base, int g, const void* cols, int64_t ld, int32_t ncols, double* us) {
+// Wall time (microseconds per column) of a whole pass over the columns -- reset, ingest with
+// groups of at most g columns and `ctas` CTAs per sketch launch (0: automatic), the batch steps
+// the columns trigger, synchronization -- the fastest of three passes after one untimed pass.
+int time_config(const rid_config* base, int g, int ctas, const void* cols, int64_t ld, int32_t ncols,
+                double* us) {
   rid_config c = *base;
   c.group_max = g;
+  c.ingest_ctas = ctas;
   c.defer_device_input = 1;
   if (c.n_max < ncols) c.n_max = ncols;
   rid_handle* h = nullptr;
   int rc = rid_init(&h, &c);
   if (rc != RID_OK) return rc;
-  for (int pass = 0; pass < 2 && rc == RID_OK; ++pass) {
+  double best = 0.0;
+  for (int pass = 0; pass < 4 && rc == RID_OK; ++pass) {
     rc = rid_reset(h);
-    if (rc == RID_OK) rc = rid_profile(h, pass);
+    if (rc == RID_OK) rc = rid_sync(h);
+    const auto t0 = std::chrono::steady_clock::now();
     if (rc == RID_OK) rc = rid_ingest(h, cols, ld, ncols, 1);
     if (rc == RID_OK) rc = rid_sync(h);
+    const double dt = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    if (pass > 0 && (best == 0.0 || dt < best)) best = dt;
   }
-  double ms[3] = {0.0, 0.0, 0.0};
-  if (rc == RID_OK) rc = rid_profile_read(h, ms, nullptr, nullptr);
   if (rc != RID_OK) {
     const char* e = rid_last_error(h);
     rid::set_global_error(e ? e : "autotune measurement failed");
   }
   rid_destroy(h);
-  if (rc == RID_OK) *us = (ms[0] + ms[1]) * 1e3 / ncols;
+  if (rc == RID_OK) *us = best / ncols;
   return rc;
+}
+
+// The index of the fastest time, preferring earlier entries within 2 % of it.
+size_t pick(const std::vector<double>& ts, bool prefer_last) {
+  double lo = ts[0];
+  for (double t : ts) lo = t < lo ? t : lo;
+  size_t best = 0;
+  bool found = false;
+  for (size_t i = 0; i < ts.size(); ++i)
+    if (ts[i] <= 1.02 * lo && (prefer_last || !found)) {
+      best = i;
+      found = true;
+    }
+  return best;
 }
 
 }  // namespace
@@ -114,43 +137,60 @@ extern "C" int rid_autotune(rid_config* cfg, const void* cols, int64_t ld, int32
     cudaGetLastError();
     return fail_global(RID_EINVAL, "cols must be device memory");
   }
-  int dev = 0;
+  int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
-  const std::string key = tune_key(cfg, dev);
-  const int gmax = cfg->sketch_prec != RID_SKETCH_NATIVE ? rid::kMaxGroup : rid::kMaxB;
+  const std::string key = tune_key(cfg, dev, &n_sm);
+  const bool tc = cfg->sketch_prec != RID_SKETCH_NATIVE;
+  const int gmax = tc ? rid::kMaxGroup : rid::kMaxB;
   const char* path = getenv("RID_AUTOTUNE_CACHE");
-  int g_hit = 0;
-  double us_hit = 0.0;
-  if (path && *path && cache_lookup(path, key, gmax, &g_hit, &us_hit)) {
-    cfg->group_max = g_hit;
-    if (us_per_col) *us_per_col = us_hit;
-    return RID_OK;
+  {
+    int g = 0, ctas = 0;
+    double us = 0.0;
+    if (path && *path && cache_lookup(path, key, gmax, &g, &ctas, &us)) {
+      cfg->group_max = g;
+      cfg->ingest_ctas = ctas;
+      if (us_per_col) *us_per_col = us;
+      return RID_OK;
+    }
   }
-  // Groups never span a batch boundary (t = k columns) nor exceed the columns given, so every
-  // candidate above the first power of two >= min(ncols, k) forms the same groups.
+  // 1. Group size, with the automatic CTA count.  Groups never span a batch (t = k columns) nor
+  // exceed the columns given, so every candidate above the first power of two >= min(ncols, k)
+  // forms the same groups.  Ties go to the larger group (fewer launches, less host work).
   const int cap = ncols < cfg->k ? ncols : cfg->k;
   std::vector<int> gs;
   std::vector<double> ts;
   for (int g = 1; g <= gmax; g *= 2) {
     double us = 0.0;
-    rc = time_group(cfg, g, cols, ld, ncols, &us);
+    rc = time_config(cfg, g, 0, cols, ld, ncols, &us);
     if (rc != RID_OK) return rc;
     gs.push_back(g);
     ts.push_back(us);
     if (g >= cap) break;
   }
-  // the largest group within 2 % of the fastest: fewer launches and less host work per column
-  double best_us = ts[0];
-  for (double t : ts) best_us = t < best_us ? t : best_us;
-  int best = gs[0];
-  double chosen_us = ts[0];
-  for (size_t i = 0; i < gs.size(); ++i)
-    if (ts[i] <= 1.02 * best_us) {
-      best = gs[i];
-      chosen_us = ts[i];
-    }
-  cfg->group_max = best;
-  if (us_per_col) *us_per_col = chosen_us;
-  if (path && *path) cache_store(path, key, best, chosen_us);
+  size_t ib = pick(ts, true);
+  const int gbest = gs[ib];
+  double us_best = ts[ib];
+  // 2. CTAs per sketch launch for that group size: the automatic count first (kept on a tie),
+  // then fractions of the SMs (tensor cores; clamped by rid_init to the buffers it sizes) or
+  // multiples of them (native path, at most its automatic four per SM).
+  std::vector<int> cs = {0};
+  if (tc) {
+    for (int num : {1, 2, 3, 4, 5, 6}) cs.push_back(n_sm * num / 6 > 0 ? n_sm * num / 6 : 1);
+  } else {
+    for (int mul : {1, 2, 3}) cs.push_back(n_sm * mul);
+  }
+  std::vector<double> tc_times = {us_best};
+  for (size_t i = 1; i < cs.size(); ++i) {
+    double us = 0.0;
+    rc = time_config(cfg, gbest, cs[i], cols, ld, ncols, &us);
+    if (rc != RID_OK) return rc;
+    tc_times.push_back(us);
+  }
+  const size_t ic = pick(tc_times, false);
+  cfg->group_max = gbest;
+  cfg->ingest_ctas = cs[ic];
+  us_best = tc_times[ic];
+  if (us_per_col) *us_per_col = us_best;
+  if (path && *path) cache_store(path, key, gbest, cs[ic], us_best);
   return RID_OK;
 }

@@ -381,6 +381,7 @@ int check_config(const rid_config* c) {
   }
   if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
   if (c->right_l < 0 || c->right_l > 4096) return fail(h, RID_EINVAL, "right_l must be in [0, 4096]");
+  if (c->ingest_ctas < 0) return fail(h, RID_EINVAL, "ingest_ctas must be >= 0");
   if (c->grad_coeff != 0 && c->grad_dims != 2)
     return fail(h, RID_EINVAL, "grad_coeff needs gradient mode (grad_dims = 2)");
   if (c->grad_dims != 0) {
@@ -477,6 +478,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
   d.grad_coeff = c->grad_coeff != 0 ? 1 : 0;
   const int64_t nchunks = (d.m + rid::kChunk - 1) / rid::kChunk;
   d.n_sketch_blocks = (int)(nchunks < 4 * h->n_sm ? nchunks : 4 * h->n_sm);
+  if (c->ingest_ctas > 0 && c->ingest_ctas < d.n_sketch_blocks) d.n_sketch_blocks = c->ingest_ctas;
   int64_t gs = (d.m + 16383) / 16384;
   d.gram_split = (int)(gs < 1 ? 1 : (gs > 256 ? 256 : gs));
   const int t = d.t;
@@ -511,6 +513,8 @@ int rid_init(rid_handle** out, const rid_config* c) {
     // nothing runs beside the first batch's ingest: it takes every SM
     h->first_blocks = (int)(want_blocks < h->n_sm ? want_blocks : h->n_sm);
     if (h->first_blocks < 1) h->first_blocks = 1;
+    // a chosen count (rid_autotune) stays within the partial buffers sized below
+    if (c->ingest_ctas > 0) h->ingest_blocks = c->ingest_ctas < h->first_blocks ? c->ingest_ctas : h->first_blocks;
   }
   int prio_lo = 0, prio_hi = 0;
   int rc = RID_OK;

@@ -35,6 +35,7 @@ class rid_config(ctypes.Structure):
         ("ny", ctypes.c_int32), ("nfields", ctypes.c_int32), ("n_max", ctypes.c_int64),
         ("seed", ctypes.c_uint64), ("group_max", ctypes.c_int32), ("defer_device_input", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p), ("right_l", ctypes.c_int32), ("grad_coeff", ctypes.c_int32),
+        ("ingest_ctas", ctypes.c_int32),
     ]
 
 
@@ -162,7 +163,7 @@ def _ptr(x):
 def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
                 lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
-                grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False):
+                grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False, ingest_ctas=0):
     """An rid_config from keyword arguments (the defaults of rid_config_default otherwise)."""
     cfg = rid_config()
     _check(rid_config_default(ctypes.byref(cfg)))
@@ -180,15 +181,17 @@ def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_cons
     cfg.grad_dims, cfg.nx, cfg.ny, cfg.nfields = int(grad_dims), int(nx), int(ny), int(nfields)
     cfg.right_l = int(right_l)
     cfg.grad_coeff = 1 if grad_coeff else 0
+    cfg.ingest_ctas = int(ingest_ctas)
     cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return cfg
 
 
 def autotune_group(cols, m, k, s, h=0, **kw):
-    """rid_autotune: the ingest group size (columns per sketch launch) measured for the
-    configuration ``make_config(m, k, s, h, **kw)`` on representative device columns ``cols``
-    (a torch tensor (b, m), row q = snapshot q).  Returns (group_max, microseconds per column);
-    RID_AUTOTUNE_CACHE in the environment names an optional cache file."""
+    """rid_autotune: the ingest's launch shape -- group size (columns per sketch launch) and
+    CTAs per sketch launch -- measured for the configuration ``make_config(m, k, s, h, **kw)``
+    on representative device columns ``cols`` (a torch tensor (b, m), row q = snapshot q).
+    Returns (group_max, ingest_ctas, microseconds per column of a whole pass); pass both to
+    OnlineRID.  RID_AUTOTUNE_CACHE in the environment names an optional cache file."""
     cfg = make_config(m, k, s, h, **kw)
     if not (hasattr(cols, "data_ptr") and cols.is_cuda) or cols.dim() != 2 or cols.shape[1] != int(m) \
             or cols.stride(1) != 1:
@@ -196,7 +199,7 @@ def autotune_group(cols, m, k, s, h=0, **kw):
     us = ctypes.c_double()
     _check(rid_autotune(ctypes.byref(cfg), ctypes.c_void_p(cols.data_ptr()), int(cols.stride(0)),
                         int(cols.shape[0]), ctypes.byref(us)))
-    return int(cfg.group_max), float(us.value)
+    return int(cfg.group_max), int(cfg.ingest_ctas), float(us.value)
 
 
 class OnlineRID:
@@ -205,7 +208,7 @@ class OnlineRID:
     def __init__(self, m, k, s, h=0, **kw):
         """Keyword arguments as make_config: c1, c2, eps, delta, c_const, lambda_mode,
         lambda_fixed, omega, dtype, sketch, n_max, seed, stream, group_max, defer, grad_dims,
-        nx, ny, nfields, right_l, grad_coeff."""
+        nx, ny, nfields, right_l, grad_coeff, ingest_ctas."""
         cfg = make_config(m, k, s, h, **kw)
         dtype = kw.get("dtype", "f32")
         self.cfg = cfg
