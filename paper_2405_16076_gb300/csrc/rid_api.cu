@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rid.h"
 #include "rid_internal.cuh"
 
@@ -78,6 +80,16 @@ void set_global_error(const char* msg) { g_init_err = msg ? msg : ""; }
 }  // namespace rid
 
 namespace {
+
+// NVTX range over a host-side phase (the enqueue of an ingest call, a sketch group or a batch
+// step), so that profilers can attribute and filter the kernels it launches; a no-op unless a
+// tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int fail(rid_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg; else g_init_err = msg;
@@ -232,6 +244,7 @@ cudaEvent_t next_event(rid_handle* h) {
 // lambda stream from the snapshot into output copy b % 2 (after step b-2's scores, the last
 // reader of that copy); the tail runs on the batch stream after it.
 int run_batch(rid_handle* h) {
+  NvtxRange nvtx("rid_batch_step");
   const int b = h->batch;
   h->joined = false;
   const Dev db = dev_for(h, b);
@@ -299,6 +312,7 @@ int check_device_error(rid_handle* h) {
 // Sketch the pending columns (one read of each), append them, and run the batch step
 // when the t-th buffered column has arrived.
 int flush(rid_handle* h) {
+  NvtxRange nvtx("rid_sketch_group");
   const int G = (int)h->pend.size();
   if (G == 0) return RID_OK;
   int rc = grow(h, h->n_obs + G);
@@ -626,6 +640,7 @@ fail_alloc:
 }
 
 int rid_ingest(rid_handle* h, const void* cols, int64_t ld, int32_t ncols, int32_t on_device) {
+  NvtxRange nvtx("rid_ingest");
   if (!h) return RID_EINVAL;
   if (h->finalized) return fail(h, RID_ESTATE, "rid_ingest after rid_finalize (call rid_reset first)");
   if (ncols < 0) return fail(h, RID_EINVAL, "ncols < 0");
@@ -668,6 +683,7 @@ int rid_batch_ingest(rid_handle* const* hs, int32_t nh, const void* const* cols,
 }
 
 int rid_finalize(rid_handle* h, int64_t* J_out, double* P_out, int64_t ldp, int32_t on_device) {
+  NvtxRange nvtx("rid_finalize");
   if (!h) return RID_EINVAL;
   const int t = h->d.t;
   if (P_out && ldp < t) return fail(h, RID_EINVAL, "ldp < t");
