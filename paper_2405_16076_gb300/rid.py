@@ -130,12 +130,14 @@ def batch_ingest(handles, blocks):
     nh = len(handles)
     if nh == 0:
         return
-    on_dev = hasattr(blocks[0], "data_ptr") and bool(blocks[0].is_cuda)
-    arrs = [b if on_dev else np.ascontiguousarray(b, dtype=hd.np_dtype) for hd, b in zip(handles, blocks)]
+    marsh = [_columns(b, hd.m, hd.esize) for hd, b in zip(handles, blocks)]
+    on_dev = marsh[0][1]
+    if any(x[1] != on_dev for x in marsh):
+        raise ValueError("all blocks must be on the device, or all on the host")
     hs = (ctypes.c_void_p * nh)(*[hd.h.value for hd in handles])
-    cols = (ctypes.c_void_p * nh)(*[(a.data_ptr() if on_dev else a.ctypes.data) for a in arrs])
-    ld = (ctypes.c_int64 * nh)(*[hd.m for hd in handles])
-    nc = (ctypes.c_int32 * nh)(*[int(a.shape[0]) for a in arrs])
+    cols = (ctypes.c_void_p * nh)(*[x[0].value for x in marsh])
+    ld = (ctypes.c_int64 * nh)(*[x[2] for x in marsh])
+    nc = (ctypes.c_int32 * nh)(*[x[3] for x in marsh])
     rc = rid_batch_ingest(hs, nh, cols, ld, nc, 1 if on_dev else 0)
     if rc != RID_OK:
         msg = None
@@ -152,12 +154,50 @@ def _check(rc, h=None):
         raise RIDError(rc, msg.decode() if msg else "")
 
 
-def _ptr(x):
-    """Device pointer of a torch tensor or host pointer of a numpy array."""
-    if hasattr(x, "data_ptr"):
-        return ctypes.c_void_p(x.data_ptr()), bool(x.is_cuda)
-    arr = np.asarray(x)
-    return ctypes.c_void_p(arr.ctypes.data), False
+def _columns(cols, m, esize):
+    """(pointer, on_device, ld, ncols, owner) of a block of m-long columns in the data dtype.
+
+    Accepted: a torch tensor (device or host) of shape (m,), (m, b) with unit stride down each
+    column, or (b, m) with unit stride along each row (row q = column q), of the data dtype; or
+    anything numpy reads as such an array (converted to the data dtype, and copied to contiguous
+    columns when needed).  Anything else raises TypeError or ValueError, so that the library never
+    reads outside the caller's buffer.  ``owner`` must stay referenced until the call returns."""
+    if hasattr(cols, "data_ptr"):
+        want = "torch.float64" if esize == 8 else "torch.float32"
+        if str(cols.dtype) != want:
+            raise TypeError(f"columns must be {want}, not {cols.dtype}")
+        shp, st = tuple(cols.shape), tuple(cols.stride())
+        if len(shp) == 1 and st[0] == 1:
+            ncols, ld = 1, shp[0]
+        elif len(shp) == 2 and shp[0] == m and st[0] == 1:
+            ncols, ld = shp[1], st[1]
+        elif len(shp) == 2 and shp[1] == m and st[1] == 1:
+            ncols, ld = shp[0], st[0]
+        else:
+            raise ValueError("tensor must hold contiguous m-long columns")
+        return ctypes.c_void_p(cols.data_ptr()), bool(cols.is_cuda), int(ld), int(ncols), cols
+    want = np.float64 if esize == 8 else np.float32
+    a = np.asarray(cols)
+    if a.ndim == 1:
+        a = np.ascontiguousarray(a, dtype=want)
+        return ctypes.c_void_p(a.ctypes.data), False, int(a.shape[0]), 1, a
+    if a.ndim != 2:
+        raise ValueError("array must hold m-long columns")
+    if a.shape[0] == m and a.flags.f_contiguous:
+        a = np.asfortranarray(a, dtype=want)
+        ncols = a.shape[1]
+    elif a.shape[1] == m and a.flags.c_contiguous:
+        a = np.ascontiguousarray(a, dtype=want)
+        ncols = a.shape[0]
+    elif a.shape[0] == m:
+        a = np.asfortranarray(a, dtype=want)
+        ncols = a.shape[1]
+    elif a.shape[1] == m:
+        a = np.ascontiguousarray(a, dtype=want)
+        ncols = a.shape[0]
+    else:
+        raise ValueError("array must hold m-long columns")
+    return ctypes.c_void_p(a.ctypes.data), False, int(m), int(ncols), a
 
 
 def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
@@ -233,32 +273,13 @@ class OnlineRID:
         except Exception:
             pass
 
-    def ingest(self, cols, ld=None, ncols=None):
-        """cols: m x b column-major block (torch tensor on the GPU, or numpy array on the host).
-
-        A torch tensor of shape (b, m) (row q = snapshot q) is accepted as well."""
-        p, on_dev = _ptr(cols)
-        if ncols is None or ld is None:
-            shp = tuple(cols.shape)
-            if len(shp) == 1:
-                ncols, ld = 1, shp[0]
-            elif hasattr(cols, "stride") and not isinstance(cols, np.ndarray):
-                st = cols.stride()
-                if shp[0] == self.m and st[0] == 1:
-                    ncols, ld = shp[1], st[1]
-                elif shp[1] == self.m and st[1] == 1:
-                    ncols, ld = shp[0], st[0]
-                else:
-                    raise ValueError("tensor must hold contiguous m-long columns")
-            else:
-                a = np.asarray(cols)
-                if a.flags.f_contiguous and a.shape[0] == self.m:
-                    ncols, ld = a.shape[1], a.shape[0]
-                elif a.flags.c_contiguous and a.shape[1] == self.m:
-                    ncols, ld = a.shape[0], a.shape[1]
-                else:
-                    raise ValueError("array must hold contiguous m-long columns")
-        _check(rid_ingest(self.h, p, int(ld), int(ncols), int(on_dev)), self.h)
+    def ingest(self, cols):
+        """cols: a block of m-long columns -- a torch tensor on the GPU (device input) or on the
+        host, of shape (m, b) column-major or (b, m) with row q = snapshot q, in the data dtype;
+        or a numpy array of either shape (converted to the data dtype)."""
+        p, on_dev, ld, ncols, owner = _columns(cols, self.m, self.esize)
+        _check(rid_ingest(self.h, p, ld, ncols, int(on_dev)), self.h)
+        del owner
 
     def finalize(self):
         t = self.t
