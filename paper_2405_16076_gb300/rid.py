@@ -200,6 +200,23 @@ def _columns(cols, m, esize):
     return ctypes.c_void_p(a.ctypes.data), False, int(m), int(ncols), a
 
 
+def _device_out(x, dtype, numel, what):
+    """Check a caller's output tensor before the library writes ``numel`` elements of ``dtype``
+    (a torch dtype name) into it from the device: right dtype, contiguous, large enough, on a
+    CUDA device.  Raises TypeError or ValueError otherwise."""
+    if not hasattr(x, "data_ptr"):
+        raise TypeError(f"{what} must be a torch tensor")
+    if str(x.dtype) != dtype:
+        raise TypeError(f"{what} must be {dtype}, not {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if x.numel() < numel:
+        raise ValueError(f"{what} holds {x.numel()} elements; {numel} are written")
+    if not x.is_cuda:
+        raise TypeError(f"{what} must be on a CUDA device")
+    return ctypes.c_void_p(x.data_ptr())
+
+
 def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
                 lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
@@ -351,8 +368,8 @@ class OnlineRID:
         lam = ctypes.c_double()
         g = ctypes.c_double()
         if out is not None:
-            _check(rid_gradient_coefficients(self.h, ctypes.c_void_p(out.data_ptr()), self.t, 1, ctypes.byref(lam),
-                                             ctypes.byref(g)), self.h)
+            po = _device_out(out, "torch.float64", self.n_obs() * self.t, "out")
+            _check(rid_gradient_coefficients(self.h, po, self.t, 1, ctypes.byref(lam), ctypes.byref(g)), self.h)
             return lam.value, None, g.value
         n = self.n_obs()
         P = np.zeros((n, self.t))                      # row j = column j of the t x n matrix
@@ -368,16 +385,22 @@ class OnlineRID:
         return out.T.copy()
 
     def right_sketch_device(self, out):
-        """Copy Y into a device tensor of shape (right_l, m) (row r = column r of Y)."""
-        _check(rid_get_right_sketch(self.h, ctypes.c_void_p(out.data_ptr()), out.stride(0), 1), self.h)
+        """Copy Y into a contiguous device tensor of shape (right_l, m) (row r = column r of Y)."""
+        l = int(self.cfg.right_l)
+        want = "torch.float64" if self.esize == 8 else "torch.float32"
+        if out.dim() != 2 or tuple(out.shape) != (l, self.m):
+            raise ValueError(f"out must have shape ({l}, {self.m})")
+        po = _device_out(out, want, l * self.m, "out")
+        _check(rid_get_right_sketch(self.h, po, self.m, 1), self.h)
 
     def finalize_device(self, J, P, sync=True):
         """Finalize into device tensors: J (t,) int64 and P (n, t) float64 (row j = column j).
 
         sync=False queues the copies without a host synchronization (RID_OUT_DEVICE_ASYNC), so
         that reset / ingest / finalize can be captured into a CUDA graph."""
-        _check(rid_finalize(self.h, ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(P.data_ptr()), self.t,
-                            1 if sync else 2), self.h)
+        pj = _device_out(J, "torch.int64", self.t, "J")
+        pp = _device_out(P, "torch.float64", self.n_obs() * self.t, "P")
+        _check(rid_finalize(self.h, pj, pp, self.t, 1 if sync else 2), self.h)
 
     def profile(self, enable=True):
         _check(rid_profile(self.h, 1 if enable else 0), self.h)

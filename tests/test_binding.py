@@ -68,3 +68,17 @@ def test_numpy_layouts_and_conversion(esize, npd):
         _columns(np.zeros((b, m + 1)), m, esize)
     with pytest.raises(ValueError):
         _columns(np.zeros((2, b, m)), m, esize)
+
+
+def test_device_outputs_are_checked_before_any_write():
+    from paper_2405_16076_gb300.rid import _device_out
+    with pytest.raises(TypeError, match="torch tensor"):
+        _device_out(np.zeros(8), "torch.float64", 8, "P")
+    with pytest.raises(TypeError, match="float64"):
+        _device_out(torch.zeros(8, dtype=torch.float32), "torch.float64", 8, "P")
+    with pytest.raises(ValueError, match="contiguous"):
+        _device_out(torch.zeros((4, 4), dtype=torch.float64).T, "torch.float64", 8, "P")
+    with pytest.raises(ValueError, match="elements"):
+        _device_out(torch.zeros(7, dtype=torch.float64), "torch.float64", 8, "P")
+    with pytest.raises(TypeError, match="CUDA"):
+        _device_out(torch.zeros(8, dtype=torch.float64), "torch.float64", 8, "P")
