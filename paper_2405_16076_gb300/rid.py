@@ -175,6 +175,8 @@ def _columns(cols, m, esize):
             ncols, ld = shp[0], st[0]
         else:
             raise ValueError("tensor must hold contiguous m-long columns")
+        if ncols == 1:
+            ld = max(ld, m)                  # one column: its stride to a next one is irrelevant
         return ctypes.c_void_p(cols.data_ptr()), bool(cols.is_cuda), int(ld), int(ncols), cols
     want = np.float64 if esize == 8 else np.float32
     a = np.asarray(cols)

@@ -82,3 +82,13 @@ def test_device_outputs_are_checked_before_any_write():
         _device_out(torch.zeros(7, dtype=torch.float64), "torch.float64", 8, "P")
     with pytest.raises(TypeError, match="CUDA"):
         _device_out(torch.zeros(8, dtype=torch.float64), "torch.float64", 8, "P")
+
+
+def test_single_column_views_of_any_stride():
+    from paper_2405_16076_gb300.rid import _columns
+    m = 9
+    v = torch.arange(m, dtype=torch.float32)
+    for X in (v, v.unsqueeze(0), v.unsqueeze(1)):
+        ptr, _, ld, ncols, _ = _columns(X, m, 4)
+        assert ncols == 1 and ld >= m
+        assert np.array_equal(_read(ptr.value, ld, 1, m, np.float32)[:, 0], v.numpy())
