@@ -198,7 +198,9 @@ def cpu_baseline(cfg, seconds_target=15.0, m_sample=1 << 17):
     per_snap_full = dt / cfg["b"] * (m / ms)
     return {"value": 1.0 / per_snap_full, "unit": "snapshots/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle ingest of {cfg['b']} snapshots restricted to the first {ms} of m={m} coordinates "
-                      f"({dt:.1f} s), extrapolated linearly in m; batch steps not included"}
+                      f"({dt:.1f} s), extrapolated linearly in m; batch steps not included",
+            "note": "cores = the BLAS threads of the matrix products; numpy's elementwise work (the Philox "
+                    "draws of Omega, most of the time) runs on one core"}
 
 
 def id_error_device(X, J, P, chunk=1 << 17):
