@@ -135,10 +135,11 @@ def test_log_calls_reject_null_handles(lib):
     assert rid.rid_get_log(None, None, 0, None) == rid.RID_EINVAL
 
 
-def test_plain_c_client_links_and_validates(lib):
-    """The boundary is usable from C alone: a C program includes rid.h, links librid.so, checks
-    a configuration and reads the error text; rid_init reports RID_ENOLIB without a device (or
-    succeeds with one)."""
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_plain_c_client_links_and_validates(lib, compiler, std):
+    """The boundary is usable from C (and C++) alone: a program includes rid.h, links
+    librid.so, checks a configuration and reads the error text; rid_init reports RID_ENOLIB
+    without a device (or succeeds with one)."""
     src = r'''
 #include <stdio.h>
 #include "rid.h"
@@ -151,10 +152,10 @@ int main(void) {
   if (rid_config_check(&c) != RID_EINVAL) return 12;
   if (!rid_last_error(NULL) || !rid_last_error(NULL)[0]) return 13;
   c.s = 83;
-  rid_handle* h = 0;
+  rid_handle* h = NULL;
   int rc = rid_init(&h, &c);
   if (rc == RID_OK) { rid_destroy(h); printf("device\n"); return 0; }
-  if (rc != RID_ENOLIB || h != 0) return 14;
+  if (rc != RID_ENOLIB || h != NULL) return 14;
   printf("no device\n");
   return 0;
 }
@@ -164,7 +165,8 @@ int main(void) {
         c = os.path.join(d, "client.c")
         exe = os.path.join(d, "client")
         open(c, "w").write(src)
-        subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), c,
+        lang = ["-x", "c++"] if compiler == "g++" else []
+        subprocess.run([compiler, std, "-Wall", "-Werror", *lang, "-I", os.path.join(ROOT, "include"), c,
                         "-L", libdir, "-lrid", f"-Wl,-rpath,{libdir}", "-o", exe], check=True)
         r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
