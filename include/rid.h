@@ -280,7 +280,7 @@ typedef struct {
 } rid_log_record;
 
 /* Keep a log of the last `capacity` batch steps on the device (0 turns it off and frees it);
- * the log starts empty with the next batch step.  Each step adds two small device-to-device
+ * the log starts empty with the next batch step.  Each step adds four small device-to-device
  * copies on the handle's own streams (none while the log is off), so logging also works inside a
  * captured CUDA graph.  Synchronizes.  Errors: RID_EINVAL (capacity outside [0, 2^20]),
  * RID_ENOMEM, RID_ECUDA. */
