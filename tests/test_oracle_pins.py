@@ -456,3 +456,17 @@ def test_stream_keeps_gradient_sketches_and_small_lambda_gives_algorithm_4():
     assert np.allclose(Pz, coeff_alg4(S[:, J[act]], S), rtol=1e-7, atol=1e-9)
     lam, Pg, g = o.gradient_coefficients()
     assert 1e-3 <= lam <= 1e3 and np.isfinite(g) and Pg.shape == (4, 20)
+
+
+def test_truncated_svd_error_closed_form():
+    """Eckart-Young: with A = U diag(sigma) V^T (orthonormal U, V) the best rank-k error is the
+    norm of the trailing singular values."""
+    from oracle.offline import truncated_svd_error
+    rng = np.random.default_rng(21)
+    U, _ = np.linalg.qr(rng.standard_normal((40, 9)))
+    V, _ = np.linalg.qr(rng.standard_normal((15, 9)))
+    sig = np.array([9.0, 5.0, 4.0, 2.0, 1.0, 0.5, 0.25, 0.125, 0.0625])
+    A = U @ np.diag(sig) @ V.T
+    for k in (0, 1, 4, 9):
+        want = math.sqrt(np.sum(sig[k:] ** 2) / np.sum(sig ** 2))
+        assert abs(truncated_svd_error(A, k) - want) <= 1e-13
