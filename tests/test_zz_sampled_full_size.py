@@ -24,7 +24,8 @@ oracle computes them one by one, and by properties that hold at any size:
 * the NA-Hutch++ estimate (Algorithm 8) of the committed result lies within 15 % of its exact
   error ||A - A_J P||_F / ||A||_F, evaluated in FP64.
 
-The module runs last (file order): it holds about 90 GB of device memory while it runs.
+The module runs after the earlier GPU modules (file order): it holds about 90 GB of device memory
+while it runs.
 """
 import ctypes
 import math
@@ -150,7 +151,7 @@ def test_full_size_algorithm4_commit_and_estimate(channel_run):
         # in directions the sketch does not determine; their residuals still agree
         res_g = np.linalg.norm(SJ @ got - SA)
         res_o = np.linalg.norm(SJ @ P4 - SA)
-        assert res_g <= res_o * (1.0 + 1e-3), (kap, res_g, res_o)
+        assert res_g <= res_o * (1.0 + 1e-2) + 1e-12 * np.linalg.norm(SA), (kap, res_g, res_o)
     sq, fro_est, q = g.error_estimate()
     assert 4 <= q <= 7
     assert P.shape == (r["k"], n)
