@@ -287,7 +287,8 @@ typedef struct {
 int rid_log_enable(rid_handle* h, int32_t capacity);
 
 /* Copy the most recent min(max_records, steps logged, capacity) records, oldest first, to out
- * (host) and their number to *n_out (may be NULL).  Synchronizes; pending columns are not
+ * (host) and their number to *n_out (may be NULL); with max_records = 0 nothing is copied and
+ * *n_out receives the number of records available.  Synchronizes; pending columns are not
  * flushed.  rid_reset and rid_restore start the log afresh.  Errors: RID_EINVAL (max_records < 0,
  * NULL out with max_records > 0), RID_ESTATE (the log is off), RID_ECUDA. */
 int rid_get_log(rid_handle* h, rid_log_record* out, int32_t max_records, int32_t* n_out);

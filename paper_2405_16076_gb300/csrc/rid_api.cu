@@ -1116,8 +1116,12 @@ int rid_get_log(rid_handle* h, rid_log_record* out, int32_t max_records, int32_t
   join(h);
   int64_t nrec = h->batch - h->log_first;
   if (nrec > h->log_cap) nrec = h->log_cap;
-  if (nrec > max_records) nrec = max_records;
   if (nrec < 0) nrec = 0;
+  if (max_records == 0) {                      // a size query
+    if (n_out) *n_out = (int32_t)nrec;
+    return RID_OK;
+  }
+  if (nrec > max_records) nrec = max_records;
   std::vector<char> buf((size_t)h->log_cap * kLogSlot);
   CK(cudaMemcpyAsync(buf.data(), h->log_dev, buf.size(), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));

@@ -435,11 +435,15 @@ class OnlineRID:
         """Keep the last ``capacity`` batch steps' decisions on the device (0: off)."""
         _check(rid_log_enable(self.h, int(capacity)), self.h)
 
-    def log(self, max_records=1 << 20):
-        """The logged batch steps, oldest first, as dicts (see rid_log_record in include/rid.h)."""
-        cap = max(0, int(max_records))
-        buf = (rid_log_record * max(cap, 1))()
+    def log(self, max_records=None):
+        """The logged batch steps (the newest ``max_records``, all by default), oldest first, as
+        dicts (see rid_log_record in include/rid.h)."""
         n = ctypes.c_int32()
+        _check(rid_get_log(self.h, None, 0, ctypes.byref(n)), self.h)         # records available
+        cap = n.value if max_records is None else min(n.value, max(0, int(max_records)))
+        if cap == 0:
+            return []
+        buf = (rid_log_record * cap)()
         _check(rid_get_log(self.h, ctypes.cast(buf, ctypes.c_void_p), cap, ctypes.byref(n)), self.h)
         out = []
         for r in buf[:n.value]:
