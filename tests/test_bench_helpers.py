@@ -40,3 +40,24 @@ def test_gradient_field_error_matches_grid_operator():
     R = A - A[:, J[act]] @ P[act]
     ref = np.linalg.norm(G @ R) / np.linalg.norm(G @ A)
     assert abs(got - ref) <= 1e-10 * ref
+
+
+def test_reference_arm_prints_its_contract_line():
+    """bench.py --impl reference (the oracle on the host cores, a bounded sample of the workload)
+    prints one JSON line with the keys the benchmark contract asks of the reference arm."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--config",
+                        "channel_small", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       cwd=root, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["metric"] == "snapshots/s" and line["unit"] == "snapshots/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
