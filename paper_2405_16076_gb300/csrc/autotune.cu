@@ -19,6 +19,7 @@
 
 #include "rid.h"
 #include "rid_internal.cuh"
+#include "tune_cache.h"
 
 namespace {
 
@@ -41,35 +42,6 @@ std::string tune_key(const rid_config* c, int dev, int* n_sm) {
            name.c_str(), p.multiProcessorCount, p.major, p.minor, (long long)c->m, c->k, c->s, c->h,
            c->data_dtype, c->sketch_prec, c->omega_kind, c->grad_dims, c->right_l, c->grad_coeff);
   return std::string(buf);
-}
-
-// The last entry of the cache file for this key, if any.
-// Lines: "<key> <group> <ctas> <microseconds per column>".
-bool cache_lookup(const char* path, const std::string& key, int gmax, int* g, int* ctas, double* us) {
-  FILE* f = fopen(path, "r");
-  if (!f) return false;
-  char line[1024];
-  char k[1024];
-  bool found = false;
-  while (fgets(line, sizeof(line), f)) {
-    int gv = 0, cv = 0;
-    double uv = 0.0;
-    if (sscanf(line, "%1023s %d %d %lf", k, &gv, &cv, &uv) == 4 && key == k && gv >= 1 && gv <= gmax && cv >= 0) {
-      *g = gv;
-      *ctas = cv;
-      *us = uv;
-      found = true;
-    }
-  }
-  fclose(f);
-  return found;
-}
-
-void cache_store(const char* path, const std::string& key, int g, int ctas, double us) {
-  FILE* f = fopen(path, "a");
-  if (!f) return;
-  fprintf(f, "%s %d %d %.6g\n", key.c_str(), g, ctas, us);
-  fclose(f);
 }
 
 // Wall time (microseconds per column) of a whole pass over the columns -- reset, ingest with
@@ -104,7 +76,7 @@ int time_config(const rid_config* base, int g, int ctas, const void* cols, int64
   return rc;
 }
 
-// The index of the fastest time, preferring earlier entries within 2 % of it.
+// The index of the last (prefer_last) or the first entry within 2 % of the fastest time.
 size_t pick(const std::vector<double>& ts, bool prefer_last) {
   double lo = ts[0];
   for (double t : ts) lo = t < lo ? t : lo;
@@ -146,7 +118,7 @@ extern "C" int rid_autotune(rid_config* cfg, const void* cols, int64_t ld, int32
   {
     int g = 0, ctas = 0;
     double us = 0.0;
-    if (path && *path && cache_lookup(path, key, gmax, &g, &ctas, &us)) {
+    if (path && *path && rid::tune_cache_lookup(path, key, gmax, &g, &ctas, &us)) {
       cfg->group_max = g;
       cfg->ingest_ctas = ctas;
       if (us_per_col) *us_per_col = us;
@@ -191,6 +163,6 @@ extern "C" int rid_autotune(rid_config* cfg, const void* cols, int64_t ld, int32
   cfg->ingest_ctas = cs[ic];
   us_best = tc_times[ic];
   if (us_per_col) *us_per_col = us_best;
-  if (path && *path) cache_store(path, key, gbest, cs[ic], us_best);
+  if (path && *path) rid::tune_cache_store(path, key, gbest, cs[ic], us_best);
   return RID_OK;
 }

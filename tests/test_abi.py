@@ -171,3 +171,44 @@ int main(void) {
         r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert r.stdout.strip() in ("device", "no device")
+
+
+def test_tuning_cache_file_parsing():
+    """The autotuner's cache (csrc/tune_cache.h, host C++ only): the last valid line of a key wins;
+    other keys, malformed lines and out-of-range values are skipped; stores append a line."""
+    src = r'''
+#include <stdio.h>
+#include "tune_cache.h"
+int main(int argc, char** argv) {
+  const char* path = argv[1];
+  int g = -1, c = -1; double us = 0;
+  if (rid::tune_cache_lookup(path, "missing", 64, &g, &c, &us)) return 10;
+  if (!rid::tune_cache_lookup(path, "devA|m5", 64, &g, &c, &us)) return 11;
+  printf("%d %d %.3f\n", g, c, us);
+  if (rid::tune_cache_lookup(path, "devB|m5", 16, &g, &c, &us)) return 12;   // its group 32 > 16
+  rid::tune_cache_store(path, "devC|m7", 8, 101, 12.5);
+  if (!rid::tune_cache_lookup(path, "devC|m7", 64, &g, &c, &us)) return 13;
+  printf("%d %d %.3f\n", g, c, us);
+  if (rid::tune_cache_lookup("/nonexistent/dir/cache", "devA|m5", 64, &g, &c, &us)) return 14;
+  return 0;
+}
+'''
+    csrc = os.path.join(ROOT, "paper_2405_16076_gb300", "csrc")
+    with tempfile.TemporaryDirectory() as d:
+        cache = os.path.join(d, "cache.txt")
+        with open(cache, "w") as f:
+            f.write("devA|m5 16 0 3.5\n"
+                    "devB|m5 32 50 2.0\n"
+                    "garbage line\n"
+                    "devA|m5 0 0 1.0\n"            # group out of range: skipped
+                    "devA|m5 64 -3 1.0\n"          # negative CTA count: skipped
+                    "devA|m5 32 76 2.25\n"         # the last valid line for devA
+                    "devA|m5 8 0 -1\n")            # non-positive time: skipped
+        c = os.path.join(d, "t.cpp")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-I", csrc, c, "-o", exe], check=True)
+        r = subprocess.run([exe, cache], capture_output=True, text=True)
+        assert r.returncode == 0, (r.returncode, r.stdout)
+        assert r.stdout.split("\n")[:2] == ["32 76 2.250", "8 101 12.500"]
+        assert open(cache).read().splitlines()[-1] == "devC|m7 8 101 12.5"
