@@ -16,6 +16,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "fault_inject.h"
 #include "rid.h"
 #include "rid_internal.cuh"
 
@@ -109,21 +110,15 @@ int fail(rid_handle* h, int code, const std::string& msg) {
 // of the handles from then on -- inside that rid_init or in a later capacity growth -- reports
 // cudaErrorMemoryAllocation without calling cudaMalloc.  Every rid_init re-reads the variable
 // (unset: off).
-std::atomic<int64_t> g_alloc_countdown{0};
+rid::AllocCountdown g_alloc_countdown;
 
-void arm_fault_injection() {
-  const char* v = getenv("RID_FAULT_INJECT");
-  int64_t n = 0;
-  if (v && strncmp(v, "alloc:", 6) == 0) n = strtoll(v + 6, nullptr, 10);
-  g_alloc_countdown.store(n > 0 ? n : 0);
-}
+void arm_fault_injection() { g_alloc_countdown.arm(rid::parse_fault_inject(getenv("RID_FAULT_INJECT"))); }
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
-  if (g_alloc_countdown.load(std::memory_order_relaxed) > 0 && g_alloc_countdown.fetch_sub(1) == 1)
-    return cudaErrorMemoryAllocation;
+  if (g_alloc_countdown.next_fails()) return cudaErrorMemoryAllocation;
   return cudaMalloc((void**)p, n * sizeof(T));
 }
 

@@ -212,3 +212,36 @@ int main(int argc, char** argv) {
         assert r.returncode == 0, (r.returncode, r.stdout)
         assert r.stdout.split("\n")[:2] == ["32 76 2.250", "8 101 12.500"]
         assert open(cache).read().splitlines()[-1] == "devC|m7 8 101 12.5"
+
+
+def test_fault_injection_parsing_and_countdown():
+    """RID_FAULT_INJECT (csrc/fault_inject.h, host C++ only): only "alloc:<n>" with n >= 1 arms
+    it, and then exactly the n-th allocation fails, once."""
+    src = r'''
+#include <stdio.h>
+#include "fault_inject.h"
+int main(void) {
+  const char* off[] = {0, "", "alloc:", "alloc:0", "alloc:-2", "alloc:3x", "free:3", "ALLOC:3"};
+  for (const char* v : off)
+    if (rid::parse_fault_inject(v) != 0) return 10;
+  if (rid::parse_fault_inject("alloc:1") != 1 || rid::parse_fault_inject("alloc:37") != 37) return 11;
+  rid::AllocCountdown c;
+  for (int i = 0; i < 5; ++i) if (c.next_fails()) return 12;          // disarmed
+  c.arm(3);
+  const bool seq[6] = {c.next_fails(), c.next_fails(), c.next_fails(), c.next_fails(), c.next_fails(),
+                       c.next_fails()};
+  if (seq[0] || seq[1] || !seq[2] || seq[3] || seq[4] || seq[5]) return 13;
+  c.arm(0);
+  if (c.next_fails()) return 14;
+  printf("ok\n");
+  return 0;
+}
+'''
+    csrc = os.path.join(ROOT, "paper_2405_16076_gb300", "csrc")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.cpp")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-I", csrc, c, "-o", exe], check=True)
+        r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout)
