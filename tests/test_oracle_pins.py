@@ -470,3 +470,20 @@ def test_truncated_svd_error_closed_form():
     for k in (0, 1, 4, 9):
         want = math.sqrt(np.sum(sig[k:] ** 2) / np.sum(sig ** 2))
         assert abs(truncated_svd_error(A, k) - want) <= 1e-13
+
+
+def test_stream_exact_rank_r_with_shared_probe_rows():
+    """The paper-literal probe mode (h = 0: NA-Hutch++ draws its rows from the left sketch itself,
+    split c1 s / c2 s / rest): with rank r < t data Algorithm 4 reproduces A and the chosen
+    estimate is ~0, as with independent probe rows."""
+    rng = np.random.default_rng(19)
+    m, n, r, k = 400, 70, 5, 8
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    o = OnlineRID(RIDConfig(m=m, k=k, s=4 * k + 3, h=0, seed=6))
+    assert o.cfg.probe_split() == ((0, 5), (5, 16), (16, 35))
+    o.ingest(A)
+    J, P = o.finalize()
+    act = o._last_active
+    assert np.linalg.norm(A - A[:, J[act]] @ o._last_candidates[0]) < 1e-11 * np.linalg.norm(A)
+    est, q = o.error_estimates()
+    assert abs(est.min()) < 1e-9 * np.sum(A * A)
