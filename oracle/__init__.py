@@ -10,7 +10,9 @@ reduction" (arXiv 2405.16076), written from the paper's text:
 * Algorithms 4-7 (the four coefficient updates),
 * Algorithm 8 with Eqs. 35-37 (NA-Hutch++ error estimate per candidate),
 * Sec. 2.1, Eqs. 5-11 (offline CPQR-based ID), Eq. 16 (exact ridge leverage
-  score), Sec. 3.4, Eqs. 38-43 (simplex-gradient operator).
+  score), Sec. 3.4, Eqs. 38-43 (simplex-gradient operator),
+* and, for the reduced-precision sketch forms (not in the paper), the E4M3
+  block-scaled operands of an FP8 sketch (``oracle.fp8``).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  It shares no code with the CUDA library: the two

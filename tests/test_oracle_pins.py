@@ -487,3 +487,75 @@ def test_stream_exact_rank_r_with_shared_probe_rows():
     assert np.linalg.norm(A - A[:, J[act]] @ o._last_candidates[0]) < 1e-11 * np.linalg.norm(A)
     est, q = o.error_estimates()
     assert abs(est.min()) < 1e-9 * np.sum(A * A)
+
+
+# ---------------------------------------------------------------- FP8 (E4M3) block-scaled operands
+def test_e4m3_grid_from_the_bit_definition():
+    from oracle import fp8
+    g = fp8.e4m3_grid()
+    pos = g[g > 0]
+    assert len(pos) == 126                              # 7 subnormals, 14 x 8 normals, 7 in the top binade
+    assert pos.min() == 2.0 ** -9 and pos.max() == 448.0
+    assert 2.0 ** -6 in pos and (1 + 7 / 8) * 2.0 ** 7 in pos and 480.0 not in pos
+    assert np.all(np.diff(g) > 0)
+
+
+def test_e4m3_rounding_is_nearest_with_ties_to_even_and_saturates():
+    from oracle import fp8
+    g = fp8.e4m3_grid()
+    assert np.array_equal(fp8.e4m3_round(g), g) and np.array_equal(fp8.e4m3_round(-g), -g)
+    # brute force: the nearest grid value; at a midpoint, the one whose mantissa (index) is even
+    rng = np.random.default_rng(8)
+    mids = (g[1:] + g[:-1]) / 2
+    x = np.concatenate([rng.uniform(0, 448, 4000), 2.0 ** rng.uniform(-12, 8.8, 4000), mids])
+    got = fp8.e4m3_round(x)
+    for xi, gi in zip(x, got):
+        d = np.abs(g - min(xi, 448.0))
+        cand = np.nonzero(d == d.min())[0]
+        want = g[cand[0]] if len(cand) == 1 else g[[c for c in cand if c % 2 == 0][0]]
+        assert gi == want, (xi, gi, want)
+    assert fp8.e4m3_round(0.1) == 0.1015625                   # 1.625 x 2^-4
+    assert fp8.e4m3_round(1.0625) == 1.0 and fp8.e4m3_round(1.1875) == 1.25   # ties to even
+    assert fp8.e4m3_round(2.0 ** -10) == 0.0 and fp8.e4m3_round(3 * 2.0 ** -11) == 2.0 ** -9
+    assert fp8.e4m3_round(500.0) == 448.0 and fp8.e4m3_round(-1e6) == -448.0
+
+
+def test_block_scales_are_the_smallest_powers_of_two_that_avoid_saturation():
+    from oracle import fp8
+    rng = np.random.default_rng(9)
+    a = rng.standard_normal((100, 5)) * 10.0 ** rng.uniform(-6, 6, 5)
+    a[32:64, 2] = 0.0                                   # an all-zero block
+    a[5, 4] = 448.0 * 2.0 ** -20                        # a block maximum exactly on the bound
+    s = fp8.block_scales(a, 32)
+    for b0 in range(0, 100, 32):
+        blk, sb = a[b0:b0 + 32], s[b0:b0 + 32]
+        assert np.all(sb == sb[0])                      # one scale per block and column
+        amax = np.abs(blk).max(axis=0)
+        x = np.log2(sb[0])
+        assert np.all(x == np.round(x))                 # powers of two
+        nz = amax > 0
+        assert np.all(amax[nz] / sb[0][nz] <= 448.0) and np.all(amax[nz] / (sb[0][nz] / 2) > 448.0)
+        assert np.all(sb[0][~nz] == 1.0)
+
+
+def test_fp8x2_split_error_bound_and_sketch():
+    """Each stage rounds to 3 fraction bits (relative error <= 2^-4 for normal values), so
+    |a - hi - lo| <= 2^-8 |a| plus the subnormal spacing of the second stage; the split's
+    sketch is the sketch of hi + lo, and its error is the sketch of that residual."""
+    from oracle import fp8
+    rng = np.random.default_rng(10)
+    m, n, block = 1000, 6, 32
+    a = rng.standard_normal((m, n)) * np.exp(rng.standard_normal((m, n)))
+    hi, lo = fp8.split_x2(a, block)
+    s1, s2 = fp8.block_scales(a, block), fp8.block_scales(a - hi, block)
+    g = fp8.e4m3_grid()
+    assert np.isin(np.abs(hi / s1), g).all() and np.isin(np.abs(lo / s2), g).all()   # block-scaled E4M3 terms
+    err = np.abs(a - hi - lo)
+    assert np.all(err <= 2.0 ** -8 * np.abs(a) + 2.0 ** -10 * s2 + 1e-300)
+    r = a - hi                                          # each stage: 3 fraction bits at its own scale
+    assert np.all(np.abs(r - lo) <= 2.0 ** -4 * np.abs(r) + 2.0 ** -10 * s2)
+    assert np.all(np.abs(a - hi) <= 2.0 ** -4 * np.abs(a) + 2.0 ** -10 * fp8.block_scales(a, block))
+    om = philox.rademacher_block(3, np.arange(20), 0, m)
+    S = fp8.sketch_fp8x2(om, a, block)
+    assert np.allclose(S, om @ (hi + lo), rtol=0, atol=1e-12 * np.abs(om @ a).max())
+    assert np.abs(S - om @ a).max() <= 2.0 ** -8 * np.abs(om).max() * np.abs(a).sum(axis=0).max() * 1.01
