@@ -203,6 +203,27 @@ def cpu_baseline(cfg, seconds_target=15.0, m_sample=1 << 17):
                     "draws of Omega, most of the time) runs on one core"}
 
 
+def cpu_baseline_single_thread(config, timeout=300):
+    """The oracle's rate on one host core: the reference arm of this script in a child process with
+    every thread pool limited to one thread (its own bounded sample of the workload).  A failure is
+    reported in the result, never raised."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--config", config, "--steps", "1",
+           "--warmup", "0"]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not lines:
+            return {"error": f"exit {r.returncode}: {r.stderr.strip()[-200:]}"}
+        ref = json.loads(lines[-1])
+        cb = ref.get("cpu_baseline", {})
+        return {"value": ref["value"], "unit": ref["unit"], "cores": cb.get("cores"), "sample": cb.get("sample")}
+    except Exception as exc:                            # the baseline is a report, not the product
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
 def id_error_device(X, J, P, chunk=1 << 17):
     """Relative Frobenius error ||A - A_J P||_F / ||A||_F of a finished stream, for the report only.
 
@@ -856,6 +877,7 @@ def main():
         line["roofline"]["isolated"].update({"achieved": iso, "frac": iso / peak_t})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
+        line["cpu_baseline"]["single_thread"] = cpu_baseline_single_thread(args.config)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

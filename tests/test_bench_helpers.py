@@ -61,3 +61,9 @@ def test_reference_arm_prints_its_contract_line():
     assert line["value"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_single_thread_cpu_baseline_runs_on_one_core():
+    r = bench.cpu_baseline_single_thread("channel_small")
+    assert "error" not in r, r
+    assert r["cores"] == 1 and r["value"] > 0 and r["unit"] == "snapshots/s"
