@@ -308,6 +308,23 @@ def whole_job_rate(world, units_per_rank, t_max_ms):
     return world * units_per_rank / (t_max_ms / 1e3)
 
 
+def write_timeline(path, tl, names, steps):
+    """The per-batch phase records of the timed steps, and per phase the mean duration and the
+    mean gap between consecutive batches' starts (the phase's period)."""
+    recs = [{"batch": int(b), "phase": names[int(p)], "start_ms": float(a), "end_ms": float(e)}
+            for b, p, a, e in tl]
+    summ = {}
+    for pi, name in enumerate(names):
+        rows = tl[tl[:, 1] == pi]
+        if len(rows) == 0:
+            continue
+        dur = rows[:, 3] - rows[:, 2]
+        summ[name] = {"count": int(len(rows)), "mean_ms": float(dur.mean()), "max_ms": float(dur.max()),
+                      "total_ms_per_step": float(dur.sum() / max(steps, 1))}
+    with open(path, "w") as f:
+        json.dump({"summary": summ, "records": recs}, f)
+
+
 def run_streams(args, cfg):
     """Configuration C5: all streams stepped together through rid_batch_ingest (each handle on its
     own CUDA stream), against the same streams run one after another."""
@@ -581,6 +598,8 @@ def main():
                     help="gradient mode: keep Omega G^p a and report Sec. 3.4's gradient-augmented coefficients")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the accuracy comparison with the other sketch precisions")
+    ap.add_argument("--timeline", default=None,
+                    help="write the per-batch phase timeline of the timed steps (JSON) to this file")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
@@ -660,6 +679,8 @@ def main():
         barrier()
     ms_total = e0.elapsed_time(e1)
     prof_ms, prof_kern, prof_grp = h.profile_read()
+    if args.timeline:
+        write_timeline(args.timeline, h.profile_timeline(), h.TIMELINE_PHASES, args.steps)
     h.profile(False)
     accuracy = accuracy_report(h, X, Jd, Pd)
     gradc = None

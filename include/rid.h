@@ -245,10 +245,14 @@ int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count);
  * pool Gram and the data columns still in use (the basis and the columns of
  * the current batch).  rid_restore puts such a state into a handle created
  * with the same configuration (any state it held is discarded); the stream
- * then continues exactly as the checkpointed one would have.  Errors:
- * RID_EINVAL (buffer too small or truncated, another configuration, not a
- * checkpoint), RID_ECUDA; the restored handle is in the reset state after a
- * failed rid_restore that got past the configuration check. */
+ * then continues exactly as the checkpointed one would have.  rid_restore
+ * checks the whole buffer before it changes the handle: the magic number, the
+ * configuration, the counters (0 <= count < t, n_prev = n_obs - count >= 0,
+ * batch >= 0, finalized 0 or 1, 0 <= saved slots <= t + count), the size and
+ * every saved pool slot; a rejected buffer leaves the handle's stream as it
+ * was.  Errors: RID_EINVAL (buffer too small or truncated, another
+ * configuration, inconsistent counters, not a checkpoint), RID_ECUDA (the
+ * handle is then in the reset state). */
 int rid_checkpoint_size(rid_handle* h, int64_t* bytes);
 int rid_checkpoint(rid_handle* h, void* buf, int64_t bytes);
 int rid_restore(rid_handle* h, const void* buf, int64_t bytes);
@@ -262,6 +266,20 @@ int rid_restore(rid_handle* h, const void* buf, int64_t bytes);
  * launch groups per phase since then (any pointer may be NULL). */
 int rid_profile(rid_handle* h, int32_t enable);
 int rid_profile_read(rid_handle* h, double ms[3], int64_t kernels[3], int64_t groups[3]);
+
+/* Per-batch phase timeline of the launches made while profiling was on (a benchmark hook; the
+ * paper has no counterpart).  Each record is four doubles: the batch index, the phase, and its
+ * start and end in milliseconds from the rid_profile(h, 1) call, measured with CUDA events on
+ * the stream the phase runs on.  Phases: 0 an ingest group (sketch launch and reductions, on the
+ * handle's stream), 1 the lambda part of a batch step (tridiagonalization, top-k eigenvalues,
+ * lambda and LDL^T of Eq. 23), 2 the ridge scores, 3 the uniforms and the prune / refill of
+ * Algorithm 3, 4 the Gram side of the tail (basis Gram, its Cholesky factor, T of
+ * Algorithm 7), 5 the sketch side of the tail (gathers, Householder QRs, projections), 6 the
+ * coefficient candidates, NA-Hutch++ and the commit (Algorithms 4-8).  Writes min(max_records,
+ * available) records to out (4 * max_records doubles) and their number to *n_out; with
+ * max_records = 0 only the number available.  Synchronizes.  Errors: RID_EINVAL (bad buffer),
+ * RID_ESTATE (profiling off), RID_ECUDA. */
+int rid_profile_timeline(rid_handle* h, double* out, int32_t max_records, int32_t* n_out);
 
 /* One record of the per-batch log: what a batch step decided (the quantities of the paper's
  * "update decision" rows, Algorithm 8 with Eqs. 23 and 36-37). */

@@ -953,14 +953,16 @@ int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st) {
 
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
                       cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select, cudaStream_t stg,
-                      cudaEvent_t ev_fork, cudaEvent_t ev_gram) {
+                      cudaEvent_t ev_fork, cudaEvent_t ev_gram, cudaEvent_t* tl) {
   const WorkLayout w = layout(d);
   const int64_t jd0 = n_obs - count;
   const bool odd = batch & 1;
+  if (tl) cudaEventRecord(tl[TL_TAIL0], st);
   int nk = launch_scores(d, count, jd0, d.work, odd ? w.eigR2 : w.eigR, odd ? w.beta2 : w.beta,
                          odd ? w.vhead2 : w.vhead, odd ? w.ldld2 : w.ldld, odd ? w.ldll2 : w.ldll, w.vec,
                          (int)vec_stride(d.s, d.t), st);
   if (ev_scores) cudaEventRecord(ev_scores, st);
+  if (tl) cudaEventRecord(tl[TL_SCORES], st);
   const int nu = d.t * (count + 1);
   uniforms_kernel<<<(nu + 255) / 256, 256, 0, st>>>(d, d.work + w.unif, count, batch);
   {
@@ -974,10 +976,12 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
                                                                          stage_u ? 1 : 0, jd0);
   }
   if (ev_select) cudaEventRecord(ev_select, st);
+  if (tl) cudaEventRecord(tl[TL_SELECT], st);
   // Gram side on stg (basis Gram, G, its Cholesky factor, T of Algorithm 7), sketch side
   // (gather, Householder QRs) on st; they join before the coefficient kernel.
   cudaEventRecord(ev_fork, st);
   cudaStreamWaitEvent(stg, ev_fork, 0);
+  if (tl) cudaEventRecord(tl[TL_GRAM0], stg);
   int ngk = 2;
   if (d.dtype == 1 && d.tc_part) {
     ngk = launch_tc_gram(d, d.tc_blocks, d.tg_part, stg);
@@ -997,6 +1001,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
     gram_chol_kernel<<<1, 1024, staged ? kCholSmemBytes : 0, stg>>>(d, w, staged, d.gram_rho0);
   }
   tsolve_kernel<<<(d.t + 7) / 8, 256, 0, stg>>>(d, w);
+  if (tl) cudaEventRecord(tl[TL_GRAM1], stg);
   cudaEventRecord(ev_gram, stg);
   gather_kernel<true><<<d.n_sm, 256, 0, st>>>(d, w);
   if (!launch_qr_coop(d, d.work + w.QR4, d.work + w.b4, d.work + w.h4, d.work + w.r4, d.work + w.QR6,
@@ -1010,6 +1015,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
     proj_gemm_kernel<<<dim3(gm, (unsigned)((n_obs + 31) / 32)), 256, 0, st>>>(d, w, 1, n_obs);
     proj_gemm_kernel<<<dim3(gm, gm), 256, 0, st>>>(d, w, 2, n_obs);
   }
+  if (tl) cudaEventRecord(tl[TL_QR1], st);
   cudaStreamWaitEvent(st, ev_gram, 0);
   coeff_kernel<<<kApplyBlocks, kApplyThreads, 0, st>>>(d, w, n_obs, n_prev);
   const int nchunk = (int)((n_obs + kHutChunk - 1) / kHutChunk);
@@ -1024,6 +1030,7 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
   }
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
   finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
+  if (tl) cudaEventRecord(tl[TL_TAIL1], st);
   return nk + 18 + ngk;
 }
 

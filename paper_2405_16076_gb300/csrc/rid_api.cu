@@ -60,6 +60,10 @@ struct rid_handle {
   size_t evused;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[3];
   int64_t kernels[3];
+  // per-batch phase timeline (rid_profile_timeline): base event, then (batch, phase, start, end)
+  cudaEvent_t tl_base;
+  struct TlRec { int batch, phase; cudaEvent_t a, b; };
+  std::vector<TlRec> tl;
   float* tg_part;
   // per-batch log (rid_log_enable): log_cap slots of kLogSlot bytes on the device, batch b in
   // slot b % log_cap; log_first = the first batch step it covers
@@ -259,7 +263,14 @@ int run_batch(rid_handle* h) {
   Dev dl = db;
   dl.SSt = snap;
   dl.fro2 = snap + ss;
+  cudaEvent_t tle[rid::kTlEvents] = {};
+  if (h->prof) {
+    for (auto& e : tle) e = next_event(h);
+    cudaEventRecord(tle[rid::TL_SNAP], h->st);
+    cudaEventRecord(tle[rid::TL_LAMBDA0], h->stl);
+  }
   const int nl = rid::launch_batch_lambda(dl, b, h->stl);
+  if (h->prof) cudaEventRecord(tle[rid::TL_LAMBDA1], h->stl);
   if (nl && h->log_cap > 0) {
     char* slot = h->log_dev + (size_t)(b % h->log_cap) * kLogSlot;
     CK(cudaMemcpyAsync(slot + 128, dl.scal + rid::SCAL_LAMBDA, sizeof(double), cudaMemcpyDeviceToDevice, h->stl));
@@ -269,7 +280,8 @@ int run_batch(rid_handle* h) {
   CK(cudaEventRecord(h->ev_lambda[b & 1], h->stl));
   CK(cudaStreamWaitEvent(h->stb, h->ev_lambda[b & 1], 0));
   const int nt = nl ? rid::launch_batch_tail(db, h->count, h->n_obs, h->n_prev, b, h->stb, h->ev_scores[b & 1],
-                                             h->ev_select[b & 1], h->stg, h->ev_fork, h->ev_gram)
+                                             h->ev_select[b & 1], h->stg, h->ev_fork, h->ev_gram,
+                                             h->prof ? tle : nullptr)
                     : 0;
   if (nl == 0 || nt == 0) {
     cudaGetLastError();
@@ -286,6 +298,14 @@ int run_batch(rid_handle* h) {
     cudaEventRecord(e1, h->stb);
     h->spans[2].push_back({e0, e1});
     h->kernels[2] += nk;
+    // phases of the step: lambda part, scores, select, Gram side, QR side, coefficients..commit
+    const int pairs[][3] = {{rid::TLP_LAMBDA, rid::TL_LAMBDA0, rid::TL_LAMBDA1},
+                            {rid::TLP_SCORES, rid::TL_TAIL0, rid::TL_SCORES},
+                            {rid::TLP_SELECT, rid::TL_SCORES, rid::TL_SELECT},
+                            {rid::TLP_GRAM, rid::TL_GRAM0, rid::TL_GRAM1},
+                            {rid::TLP_QR, rid::TL_SELECT, rid::TL_QR1},
+                            {rid::TLP_COEFF, rid::TL_QR1, rid::TL_TAIL1}};
+    for (const auto& pr : pairs) h->tl.push_back({b, pr[0], tle[pr[1]], tle[pr[2]]});
   }
   h->n_prev = h->n_obs;
   h->batch += 1;
@@ -350,6 +370,7 @@ int flush(rid_handle* h) {
     cudaEventRecord(ev[2], h->st);
     h->spans[0].push_back({ev[0], ev[1]});
     h->spans[1].push_back({ev[1], ev[2]});
+    h->tl.push_back({h->batch, rid::TLP_INGEST, ev[0], ev[2]});
     h->kernels[0] += nk0;
     h->kernels[1] += nk1;
   }
@@ -887,12 +908,12 @@ struct CkptPlan {
   size_t total;
 };
 
-// The device arrays of the stream state (fixed order) and the pool slots in use.
-int ckpt_plan(rid_handle* h, CkptPlan& pl) {
+// The device arrays of the stream state for n observed columns, in their fixed order (device
+// pointer, bytes); the list depends only on the configuration and n.
+std::vector<std::pair<void*, size_t>> ckpt_arrays(rid_handle* h, int64_t n) {
   Dev& d = h->d;
   const int t = d.t;
-  const int64_t n = h->n_obs;
-  pl.arrays = {
+  std::vector<std::pair<void*, size_t>> a = {
       {d.S, sizeof(double) * (size_t)d.rows * n},
       {d.SSt, sizeof(double) * (size_t)d.s * d.s},
       {d.fro2, 2 * sizeof(double)},
@@ -904,9 +925,17 @@ int ckpt_plan(rid_handle* h, CkptPlan& pl) {
       {d.P, sizeof(double) * (size_t)t * n},
       {d.Gp, sizeof(double) * (size_t)d.npool * d.npool},
   };
-  if (d.grad) pl.arrays.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
-  if (d.right_l > 0) pl.arrays.push_back({d.Y, (size_t)d.m_pad * d.right_l * h->esize});
-  if (d.grad_coeff) pl.arrays.push_back({d.Sg, sizeof(double) * 2 * (size_t)d.s * n});
+  if (d.grad) a.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
+  if (d.right_l > 0) a.push_back({d.Y, (size_t)d.m_pad * d.right_l * h->esize});
+  if (d.grad_coeff) a.push_back({d.Sg, sizeof(double) * 2 * (size_t)d.s * n});
+  return a;
+}
+
+// The device arrays of the stream state and the pool slots in use.
+int ckpt_plan(rid_handle* h, CkptPlan& pl) {
+  Dev& d = h->d;
+  const int t = d.t;
+  pl.arrays = ckpt_arrays(h, h->n_obs);
   std::vector<int> slotc(t), dsl(2 * (size_t)t);
   CK(cudaMemcpyAsync(slotc.data(), d.slotC, sizeof(int) * t, cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(dsl.data(), h->dslot_buf, sizeof(int) * 2 * t, cudaMemcpyDeviceToHost, h->st));
@@ -920,6 +949,22 @@ int ckpt_plan(rid_handle* h, CkptPlan& pl) {
   tot += sizeof(int) * pl.slots.size() + pl.slots.size() * (size_t)d.m * h->esize;
   pl.total = tot;
   return RID_OK;
+}
+
+// Checks of a checkpoint's counters against the handle's configuration, before anything of the
+// handle changes: between batch steps 0 <= count < t columns are buffered since the last step,
+// which covered n_prev = n_obs - count columns; the saved pool slots are the occupied basis slots
+// and the count buffer slots.  Returns an empty string when the counters are consistent.
+const char* ckpt_counters_invalid(const CkptCounters& cn, int t, int npool) {
+  if (cn.n_obs < 0 || cn.n_obs > ((int64_t)1 << 40)) return "checkpoint counter n_obs out of range";
+  if (cn.count < 0 || cn.count >= t) return "checkpoint counter count out of range (0 <= count < t)";
+  if (cn.n_prev < 0 || cn.n_prev > cn.n_obs || cn.n_obs - cn.n_prev != cn.count)
+    return "checkpoint counters n_prev, n_obs and count disagree";
+  if (cn.batch < 0 || (int64_t)cn.batch > cn.n_obs) return "checkpoint counter batch out of range";
+  if (cn.finalized != 0 && cn.finalized != 1) return "checkpoint flag finalized is not 0 or 1";
+  if (cn.nslots < 0 || cn.nslots > t + cn.count || cn.nslots > npool)
+    return "checkpoint counter nslots out of range";
+  return "";
 }
 
 }  // namespace
@@ -968,6 +1013,7 @@ int rid_checkpoint(rid_handle* h, void* buf, int64_t bytes) {
 
 int rid_restore(rid_handle* h, const void* buf, int64_t bytes) {
   if (!h || !buf) return RID_EINVAL;
+  if (bytes < 0) return fail(h, RID_EINVAL, "checkpoint size < 0");
   const char* p = (const char*)buf;
   const size_t head = sizeof(uint64_t) + sizeof(rid_config) + sizeof(CkptCounters);
   if ((size_t)bytes < head) return fail(h, RID_EINVAL, "checkpoint truncated");
@@ -979,6 +1025,23 @@ int rid_restore(rid_handle* h, const void* buf, int64_t bytes) {
   if (!same_config(cf, h->cfg)) return fail(h, RID_EINVAL, "checkpoint of a different configuration");
   CkptCounters cn;
   memcpy(&cn, p, sizeof(cn)); p += sizeof(cn);
+  // Everything is checked before the handle changes: a rejected checkpoint leaves the handle's
+  // stream as it was.
+  {
+    const char* why = ckpt_counters_invalid(cn, h->d.t, h->d.npool);
+    if (*why) return fail(h, RID_EINVAL, why);
+  }
+  const size_t cb = (size_t)h->d.m * h->esize;
+  size_t need = head;
+  for (auto& a : ckpt_arrays(h, cn.n_obs)) need += a.second;     // sizes only
+  need += (size_t)cn.nslots * (sizeof(int) + cb);
+  if ((size_t)bytes < need) return fail(h, RID_EINVAL, "checkpoint truncated");
+  size_t arr_bytes = 0;
+  for (auto& a : ckpt_arrays(h, cn.n_obs)) arr_bytes += a.second;
+  std::vector<int> slots((size_t)cn.nslots);
+  memcpy(slots.data(), p + arr_bytes, sizeof(int) * slots.size());
+  for (int sl : slots)
+    if (sl < 0 || sl >= h->d.npool) return fail(h, RID_EINVAL, "checkpoint holds an invalid pool slot");
   int rc = rid_reset(h);                       // joins, clears pending columns and counters
   if (rc != RID_OK) return rc;
   rc = grow(h, cn.n_obs > 0 ? cn.n_obs : 1);
@@ -989,41 +1052,12 @@ int rid_restore(rid_handle* h, const void* buf, int64_t bytes) {
   h->batch = cn.batch;
   h->log_first = h->batch;
   h->finalized = cn.finalized != 0;
-  CkptPlan pl;
-  {
-    // the array list depends only on the configuration and n_obs
-    Dev& d = h->d;
-    const int t = d.t;
-    const int64_t n = h->n_obs;
-    pl.arrays = {
-        {d.S, sizeof(double) * (size_t)d.rows * n},
-        {d.SSt, sizeof(double) * (size_t)d.s * d.s},
-        {d.fro2, 2 * sizeof(double)},
-        {d.JC, sizeof(int64_t) * t}, {d.JC_prev, sizeof(int64_t) * t},
-        {d.slotC, sizeof(int) * t}, {d.slotC_prev, sizeof(int) * t},
-        {h->dslot_buf, sizeof(int) * 2 * (size_t)t},
-        {d.tau_old, sizeof(double) * t},
-        {d.meta, sizeof(int) * rid::META_LEN}, {d.scal, sizeof(double) * rid::SCAL_LEN},
-        {d.P, sizeof(double) * (size_t)t * n},
-        {d.Gp, sizeof(double) * (size_t)d.npool * d.npool},
-    };
-    if (d.grad) pl.arrays.push_back({d.Slev, sizeof(double) * (size_t)d.s * n});
-    if (d.right_l > 0) pl.arrays.push_back({d.Y, (size_t)d.m_pad * d.right_l * h->esize});
-    if (d.grad_coeff) pl.arrays.push_back({d.Sg, sizeof(double) * 2 * (size_t)d.s * n});
-  }
-  size_t need = head;
-  for (auto& a : pl.arrays) need += a.second;
-  const size_t cb = (size_t)h->d.m * h->esize;
-  need += (size_t)cn.nslots * (sizeof(int) + cb);
-  if ((size_t)bytes < need) return fail(h, RID_EINVAL, "checkpoint truncated");
-  for (auto& a : pl.arrays) {
+  for (auto& a : ckpt_arrays(h, h->n_obs)) {
     if (a.second) CK(cudaMemcpyAsync(a.first, p, a.second, cudaMemcpyHostToDevice, h->st));
     p += a.second;
   }
-  std::vector<int> slots(cn.nslots);
-  memcpy(slots.data(), p, sizeof(int) * slots.size()); p += sizeof(int) * slots.size();
+  p += sizeof(int) * slots.size();
   for (int sl : slots) {
-    if (sl < 0 || sl >= h->d.npool) return fail(h, RID_EINVAL, "checkpoint holds an invalid pool slot");
     CK(cudaMemcpyAsync((char*)h->d.pool + (size_t)sl * h->d.m_pad * h->esize, p, cb, cudaMemcpyHostToDevice, h->st));
     p += cb;
   }
@@ -1038,6 +1072,11 @@ int rid_profile(rid_handle* h, int32_t enable) {
   h->prof = enable != 0;
   h->evused = 0;
   for (auto& v : h->spans) v.clear();
+  h->tl.clear();
+  if (h->prof) {
+    if (!h->tl_base) CK(cudaEventCreate(&h->tl_base));
+    CK(cudaEventRecord(h->tl_base, h->st));
+  }
   for (auto& k : h->kernels) k = 0;
   return RID_OK;
 }
@@ -1057,6 +1096,28 @@ int rid_profile_read(rid_handle* h, double ms[3], int64_t kernels[3], int64_t gr
     if (kernels) kernels[p] = h->kernels[p];
     if (groups) groups[p] = (int64_t)h->spans[p].size();
   }
+  return RID_OK;
+}
+
+int rid_profile_timeline(rid_handle* h, double* out, int32_t max_records, int32_t* n_out) {
+  if (!h) return RID_EINVAL;
+  if (n_out) *n_out = 0;
+  if (max_records < 0 || (max_records > 0 && !out)) return fail(h, RID_EINVAL, "bad output buffer");
+  if (!h->prof || !h->tl_base) return fail(h, RID_ESTATE, "profiling is off (rid_profile)");
+  join(h);
+  CK(cudaStreamSynchronize(h->st));
+  const int32_t n = (int32_t)h->tl.size() < max_records ? (int32_t)h->tl.size() : max_records;
+  for (int32_t i = 0; i < n; ++i) {
+    const auto& r = h->tl[(size_t)i];
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, h->tl_base, r.a));
+    CK(cudaEventElapsedTime(&b, h->tl_base, r.b));
+    out[4 * (size_t)i + 0] = r.batch;
+    out[4 * (size_t)i + 1] = r.phase;
+    out[4 * (size_t)i + 2] = a;
+    out[4 * (size_t)i + 3] = b;
+  }
+  if (n_out) *n_out = max_records == 0 ? (int32_t)h->tl.size() : n;
   return RID_OK;
 }
 
@@ -1159,6 +1220,7 @@ void rid_destroy(rid_handle* h) {
   if (h->stl) cudaStreamSynchronize(h->stl);
   if (h->stg) cudaStreamSynchronize(h->stg);
   for (auto e : h->evpool) cudaEventDestroy(e);
+  if (h->tl_base) cudaEventDestroy(h->tl_base);
   free_all(h->d, h->staging);
   if (h->tc_part) cudaFree(h->tc_part);
   if (h->tg_part) cudaFree(h->tg_part);

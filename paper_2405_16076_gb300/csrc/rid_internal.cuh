@@ -183,10 +183,15 @@ void launch_materialize_omega(const Dev& d, cudaStream_t st);
 // the next-but-one batch are chosen.  The tail's Gram side (basis Gram, G and its factor, T)
 // runs on stg between ev_fork and ev_gram, beside the sketch side's QRs on st.  Both return
 // the number of kernels launched (0 on failure).
+// Timeline events of one batch step (recorded only while profiling; tl may be null).
+enum { TL_SNAP = 0, TL_LAMBDA0, TL_LAMBDA1, TL_TAIL0, TL_SCORES, TL_SELECT, TL_GRAM0, TL_GRAM1, TL_QR1, TL_TAIL1,
+       kTlEvents };
+// Phases reported by rid_profile_timeline.
+enum { TLP_INGEST = 0, TLP_LAMBDA = 1, TLP_SCORES = 2, TLP_SELECT = 3, TLP_GRAM = 4, TLP_QR = 5, TLP_COEFF = 6 };
 int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st);
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
                       cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select, cudaStream_t stg,
-                      cudaEvent_t ev_fork, cudaEvent_t ev_gram);
+                      cudaEvent_t ev_fork, cudaEvent_t ev_gram, cudaEvent_t* tl);
 int launch_reset_state(const Dev& d, cudaStream_t st);
 
 // coop.cu: lambda (Eq. 23) through a tridiagonalization of the sketch Gram (cluster or

@@ -74,6 +74,7 @@ def _load():
         "rid_sync": (ctypes.c_int, [H]),
         "rid_profile": (ctypes.c_int, [H, ctypes.c_int32]),
         "rid_profile_read": (ctypes.c_int, [H, P, P, P]),
+        "rid_profile_timeline": (ctypes.c_int, [H, P, ctypes.c_int32, P]),
         "rid_reset": (ctypes.c_int, [H]),
         "rid_last_error": (ctypes.c_char_p, [H]),
         "rid_destroy": (None, [H]),
@@ -110,6 +111,7 @@ rid_get_state = lib.rid_get_state
 rid_sync = lib.rid_sync
 rid_profile = lib.rid_profile
 rid_profile_read = lib.rid_profile_read
+rid_profile_timeline = lib.rid_profile_timeline
 rid_reset = lib.rid_reset
 rid_last_error = lib.rid_last_error
 rid_destroy = lib.rid_destroy
@@ -414,6 +416,17 @@ class OnlineRID:
         _check(rid_profile_read(self.h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(kern.ctypes.data),
                                 ctypes.c_void_p(grp.ctypes.data)), self.h)
         return ms, kern, grp
+
+    TIMELINE_PHASES = ("ingest", "lambda", "scores", "select", "gram", "qr", "coeff")
+
+    def profile_timeline(self):
+        """Per-batch phase records since profile(True): an (n, 4) array of (batch, phase, start
+        ms, end ms); phase names in TIMELINE_PHASES."""
+        n = ctypes.c_int32()
+        _check(rid_profile_timeline(self.h, None, 0, ctypes.byref(n)), self.h)
+        out = np.zeros((max(n.value, 1), 4))
+        _check(rid_profile_timeline(self.h, ctypes.c_void_p(out.ctypes.data), n.value, ctypes.byref(n)), self.h)
+        return out[:n.value]
 
     def checkpoint(self):
         """The stream state as bytes (rid_checkpoint)."""

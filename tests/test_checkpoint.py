@@ -74,3 +74,40 @@ def test_restore_rejects_other_configuration():
         a.restore(state[:100])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("field,value", [("nslots", -1), ("count", 21), ("count", -3), ("n_prev", 10 ** 6),
+                                         ("finalized", 2), ("batch", -1), ("nslots", 10 ** 6)])
+def test_restore_rejects_inconsistent_counters(field, value):
+    """A checkpoint whose counters were corrupted is rejected with RID_EINVAL before the handle
+    changes: the live stream it was offered to continues exactly as an untouched one."""
+    import ctypes
+    import torch
+    from paper_2405_16076_gb300 import rid
+    A = config1_matrix(7)
+    m, n = A.shape
+    src = torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
+    ref = rid.OnlineRID(m=m, k=20, s=83, h=30, dtype="f64", seed=8, n_max=n)
+    ref.ingest(src[:n])
+    J0, P0 = ref.finalize()
+    ref.close()
+    a = rid.OnlineRID(m=m, k=20, s=83, h=30, dtype="f64", seed=8, n_max=n)
+    a.ingest(src[:45])
+    state = bytearray(a.checkpoint())
+    # counters follow the magic number and the configuration: int64 n_obs, n_prev, then int32
+    # count, batch, finalized, nslots
+    off = 8 + ctypes.sizeof(rid.rid_config)
+    fields = {"n_obs": (0, "<q"), "n_prev": (8, "<q"), "count": (16, "<i"), "batch": (20, "<i"),
+              "finalized": (24, "<i"), "nslots": (28, "<i")}
+    import struct
+    o, fmt = fields[field]
+    struct.pack_into(fmt, state, off + o, value)
+    with pytest.raises(rid.RIDError) as ei:
+        a.restore(bytes(state))
+    assert ei.value.code == rid.RID_EINVAL
+    assert a.n_obs() == 45
+    a.ingest(src[45:n])
+    J1, P1 = a.finalize()
+    a.close()
+    assert np.array_equal(J0, J1)
+    assert np.array_equal(P0, P1)
