@@ -54,6 +54,18 @@ enum rid_omega_kind {
 
 enum rid_dtype { RID_F64 = 0, RID_F32 = 1 };
 
+/* Refill of an empty basis slot (Algorithm 3's inner loop over the buffered columns r, each
+ * taken with probability p_r = min(1, tau^D_r c (k ln k + k ln(1/delta)/eps) / t)).  Both
+ * readings decide whether the slot is refilled by scanning r in order with one uniform per
+ * (batch, slot, r): the first r with u < p_r whose column is not already in the basis succeeds. */
+enum rid_refill_mode {
+  RID_REFILL_FIRST = 0,       /* the slot takes that first successful column (default) */
+  RID_REFILL_PROPORTIONAL = 1 /* the slot takes a column drawn among those not in the basis with
+                                 probability tau^D_r / sum tau^D (Sec. 2.3's normalized score),
+                                 by one more uniform per slot; differs from FIRST chiefly when
+                                 every p_r is clipped to 1 */
+};
+
 enum rid_sketch_prec {
   RID_SKETCH_NATIVE = 0,     /* sketch accumulated in the data type (FP64 or FP32) */
   RID_SKETCH_BF16 = 1,       /* data rounded to BF16, tensor cores, FP32 accumulation */
@@ -91,6 +103,11 @@ typedef struct rid_config {
                             native path: up to four per SM).  A positive value replaces the
                             tensor-core ingest's count after the first batch, or caps the native
                             one, and is clamped to the automatic maximum (see rid_autotune) */
+  int32_t refill_mode;   /* enum rid_refill_mode: which buffered column refills an empty basis slot */
+  int32_t lookahead;     /* batches the ingest may run ahead of the batch steps, 2..4 (0 = 3): the
+                            select of step b chooses the buffer slots of batch b + lookahead, and
+                            the handle keeps (lookahead + 2) t data columns of m in device memory.
+                            The results do not depend on it */
 } rid_config;
 
 typedef struct rid_handle rid_handle;
@@ -368,12 +385,17 @@ int rid_autotune(rid_config* cfg, const void* cols, int64_t ld, int32_t ncols, d
  * with a message in rid_last_error(NULL) and launches nothing.
  * Set-up: the first call on a device, with that device current, looks up the
  * scratch array's address (cudaGetSymbolAddress) and keeps it; make that
- * first call before any stream capture.  Every later call on the device
+ * first call before any stream capture.  The kept address belongs to that
+ * device's primary context: after a cudaDeviceReset of the device it is stale,
+ * and the entry point must not be called on that device again in the process.
+ * The device is the current one; cfg->cuda_stream must belong to it (else
+ * RID_EINVAL).  Every later call on the device
  * shares the array, which keeps the last call's contents (nothing in it has
  * to start at zero).  Calls whose kernels overlap on the GPU (streams with no
  * ordering between them) race on the scratch; calls on one stream are safe.
- * Errors: RID_EINVAL (NULL or non-device pointer, sizes, Gaussian Omega),
- * RID_ENOLIB (no GPU), RID_ECUDA (set-up or launch failure). */
+ * Errors: RID_EINVAL (NULL or non-device pointer, sizes, Gaussian Omega, a
+ * stream of another device), RID_ENOLIB (no GPU), RID_ECUDA (set-up or launch
+ * failure). */
 int rid_sketch_noalloc(const rid_config* cfg, const void* cols, int64_t ld, int32_t ncols,
                        double* S_out, int64_t lds, double* norms_out);
 

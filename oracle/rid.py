@@ -25,6 +25,14 @@ R7  Refill: candidates r = 1..count are scanned in order; the first success
     whose column is not already in C fills the slot; probabilities are
     clipped to [0, 1]; a slot dropped in iteration i is refilled in the same
     iteration.  u < p means success.
+R7p (alternative, ``refill="proportional"``): the same scan decides whether
+    slot i is refilled; the column it takes is then drawn among the buffered
+    columns not already in C with probability tau^D_r / sum tau^D (Sec. 2.3
+    reads the normalized ridge score as the selection probability): one more
+    uniform u(batch, i, count + 1) is compared with the running sums of the
+    scores, added in column order.  With the refill probabilities of R8 every
+    p is clipped to 1 on the benchmark streams, so R7 takes the first columns
+    of each batch while R7p spreads the choice by score.
 R8  c = 1 and natural logarithms in the refill probability.
 R9  After the last column, a batch step runs over the count < t buffered
     columns (finalize).
@@ -83,6 +91,7 @@ class RIDConfig:
     grad_op: object = None             # sparse (d*m) x m simplex-gradient operator, Eq. 42
     right_l: int = 0                   # columns of the optional right sketch Y (0: off)
     grad_coeff: bool = False           # keep Omega G^p a for the gradient-augmented coefficients
+    refill: str = "first"              # R7 ("first") or R7p ("proportional")
 
     @property
     def t(self):
@@ -151,16 +160,42 @@ def css_update(cfg, batch, JC, tau_old, tau_C, JD, tau_D, margins=None):
             else:
                 tau_old[i] = tau_C[i]
         if JC[i] < 0:
+            hit = None
             for r in range(len(JD)):
                 p = min(max(tau_D[r] * scale, 0.0), 1.0)
                 u = float(philox.uniform(cfg.seed, batch, i, 1 + r))
                 if margins is not None and p < 1.0 and tau_D[r] > 0:
                     margins.append(abs(u - p) / p)
                 if u < p and JD[r] not in JC:
-                    JC[i] = JD[r]
-                    tau_old[i] = tau_D[r]
+                    hit = r
                     break
+            if hit is not None and cfg.refill == "proportional":
+                hit = proportional_draw(cfg, batch, i, JC, JD, tau_D, hit, margins)
+            if hit is not None:
+                JC[i] = JD[hit]
+                tau_old[i] = tau_D[hit]
     return JC, tau_old
+
+
+def proportional_draw(cfg, batch, i, JC, JD, tau_D, fallback, margins=None):
+    """R7p: the buffered column r (not already in C) with probability tau^D_r / sum tau^D,
+    by inverse CDF on u(batch, i, count + 1) over the scores summed in column order."""
+    cand = [r for r in range(len(JD)) if JD[r] not in JC]
+    total = 0.0
+    for r in cand:
+        total += max(float(tau_D[r]), 0.0)
+    if not total > 0.0:
+        return fallback
+    x = float(philox.uniform(cfg.seed, batch, i, 1 + len(JD))) * total
+    run = 0.0
+    pick = None
+    for r in cand:
+        run += max(float(tau_D[r]), 0.0)
+        if margins is not None:
+            margins.append(abs(x - run) / total)
+        if pick is None and x < run:
+            pick = r
+    return pick if pick is not None else cand[-1]
 
 
 def coeff_alg4(SJ, SA):

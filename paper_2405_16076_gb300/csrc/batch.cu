@@ -18,9 +18,12 @@ namespace rid {
 struct WorkLayout {
   int64_t eigA, eigR, eigD, eigE, eigV, eigP;   // tridiagonalization of the sketch Gram
   int64_t beta, vhead, mu, ldld, ldll;    // reflectors, top-k eigenvalues, LDL^T of T + lambda I
-  // what the scores read (reflectors, LDL^T) has a second copy: batch b uses copy b % 2, so
-  // that the lambda part of batch b+1 may run while the scores of batch b still read theirs
+  // every array of the lambda part has a second copy: batch b uses copy b % 2, so that the
+  // lambda parts of consecutive batches run concurrently (two lambda streams) and the lambda
+  // part of batch b+1 may run while the scores of batch b still read theirs
   int64_t eigR2, beta2, vhead2, ldld2, ldll2;
+  int64_t eigA2, eigD2, eigE2, eigP2, mu2;
+  int64_t svec;                           // per-warp vectors of the scores (their own stream)
   int64_t unif;                           // uniforms of the prune/refill decisions
   int64_t vec;                            // per-warp vectors (scores / applies)
   int64_t SJ, HJ, G, Gq, Gc, T;           // gathered sketch data and Grams
@@ -55,7 +58,9 @@ static WorkLayout layout(const Dev& d) {
   w.eigP = take(2 * s);
   w.beta = take(s); w.vhead = take(s); w.mu = take(t); w.ldld = take(s); w.ldll = take(s);
   w.eigR2 = take(s * s); w.beta2 = take(s); w.vhead2 = take(s); w.ldld2 = take(s); w.ldll2 = take(s);
-  w.unif = take(t * (t + 1));
+  w.eigA2 = take(s * s); w.eigD2 = take(s); w.eigE2 = take(s); w.eigP2 = take(2 * s); w.mu2 = take(t);
+  w.svec = take(2 * t * vec_stride(s, t));
+  w.unif = take(t * (t + 2));
   w.vec = take(nw * vec_stride(s, t));
   w.SJ = take(s * t); w.HJ = take(hh * t); w.G = take(t * t); w.Gq = take(t * t);
   w.Gc = take(t * t); w.T = take(t * t);
@@ -73,10 +78,11 @@ static WorkLayout layout(const Dev& d) {
 int64_t work_doubles(const Dev& d) { return layout(d).total; }
 
 // ---------------------------------------------------------------- prune / refill
-// The uniforms of every possible decision, u(batch, i, r), drawn in parallel.
+// The uniforms of every possible decision, u(batch, i, r), drawn in parallel: r = 0 the drop of
+// slot i, r = 1..count the refill scan, r = count + 1 the proportional draw (R7p).
 __global__ void uniforms_kernel(Dev d, double* unif, int count, int batch) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int per = count + 1;
+  const int per = count + 2;
   if (idx >= d.t * per) return;
   const int i = idx / per, r = idx % per;
   unif[idx] = sample_uniform(d.seed, (uint32_t)batch, (uint32_t)i, (uint32_t)r);
@@ -89,13 +95,18 @@ __global__ void uniforms_kernel(Dev d, double* unif, int count, int batch) {
 // column order), and thread 0 writes the index lists.  A buffered column has a larger index
 // than every column of the previous basis, so it can only be in C already if an earlier slot
 // of this scan took it (the taken[] flags).  Buffered column q has global index jd0 + q.
-// Pool slots: the next-but-one batch's columns go to the first t of the 4t slots that hold
-// neither the previous nor the new basis nor the next batch (d.dslot_nxt), written over this
-// batch's list; so that batch's ingest may overlap this step's Gram and the next step.
-__global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, int count, int stage_u,
-                                                     int64_t jd0) {
+// d holds the live selection state (JC, slotC, tau_old: read, then updated to the new basis);
+// the step's record r receives the previous and the new basis (r.JC_prev / r.slotC_prev and
+// r.JC / r.slotC) and the index lists its tail reads, so that the next step's scores and select
+// may run while this step's tail still reads its record.
+// Pool slots: the columns of batch + la go to the first t of the (la + 2) t slots that hold
+// neither the previous nor the new basis nor the batches batch + 1 .. batch + la - 1 (their
+// lists in d.dslot_all), written over this batch's list; so that batch's ingest may run while
+// this step and the next la - 1 steps are in flight.
+__global__ void __launch_bounds__(256) select_kernel(Dev d, Dev r, const double* unif, int count, int stage_u,
+                                                     int64_t jd0, int batch) {
   extern __shared__ double ssm[];
-  const int t = d.t, np = d.npool, per = count + 1;
+  const int t = d.t, np = d.npool, per = count + 2;
   const int tid = threadIdx.x, lane = tid & 31;
   double* s_told = ssm;                                  // t
   double* s_tauC = s_told + t;                           // t
@@ -112,14 +123,14 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
   int* s_used = s_taken + count;                         // npool
   for (int i = tid; i < t; i += blockDim.x) {
     s_told[i] = d.tau_old[i]; s_tauC[i] = d.tauC[i];
-    s_JC[i] = d.JC[i]; s_JCp[i] = d.JC_prev[i];
-    s_slot[i] = d.slotC[i]; s_slotp[i] = d.slotC_prev[i];
+    s_JC[i] = d.JC[i]; s_JCp[i] = d.JC[i];              // the previous basis is the live one
+    s_slot[i] = d.slotC[i]; s_slotp[i] = d.slotC[i];
   }
-  for (int r = tid; r < count; r += blockDim.x) {
-    const double td = d.tauD[r];
-    s_tauD[r] = td;
-    s_p[r] = fmin(fmax(td * d.refill_scale, 0.0), 1.0);
-    s_JD[r] = jd0 + r; s_dslot[r] = d.dslot[r]; s_taken[r] = 0;
+  for (int q = tid; q < count; q += blockDim.x) {
+    const double td = d.tauD[q];
+    s_tauD[q] = td;
+    s_p[q] = fmin(fmax(td * d.refill_scale, 0.0), 1.0);
+    s_JD[q] = jd0 + q; s_dslot[q] = d.dslot[q]; s_taken[q] = 0;
   }
   for (int i = tid; i < np; i += blockDim.x) s_used[i] = 0;
   if (stage_u)
@@ -136,12 +147,33 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
       __syncwarp();
       if (s_JC[i] < 0) {
         for (int r0 = 0; r0 < count; r0 += 32) {
-          const int r = r0 + lane;
-          const bool ok = r < count && u[1 + r] < s_p[r] && !s_taken[r];
+          const int rr0 = r0 + lane;
+          const bool ok = rr0 < count && u[1 + rr0] < s_p[rr0] && !s_taken[rr0];
           const unsigned msk = __ballot_sync(0xffffffffu, ok);
           if (msk) {
-            const int rr = r0 + __ffs(msk) - 1;
-            if (lane == 0) { s_taken[rr] = 1; s_JC[i] = s_JD[rr]; s_slot[i] = s_dslot[rr]; s_told[i] = s_tauD[rr]; }
+            int rr = r0 + __ffs(msk) - 1;
+            if (lane == 0) {
+              if (d.refill_mode == 1) {
+                // R7p: the column is drawn among those not yet taken with probability proportional
+                // to its score, by inverse CDF over the scores summed in column order (one lane, a
+                // fixed order of the additions)
+                double tot = 0.0;
+                for (int q = 0; q < count; ++q) if (!s_taken[q]) tot += fmax(s_tauD[q], 0.0);
+                if (tot > 0.0) {
+                  const double x = u[1 + count] * tot;
+                  double run = 0.0;
+                  int pick = -1, last = -1;
+                  for (int q = 0; q < count; ++q) {
+                    if (s_taken[q]) continue;
+                    run += fmax(s_tauD[q], 0.0);
+                    last = q;
+                    if (x < run) { pick = q; break; }
+                  }
+                  rr = pick >= 0 ? pick : last;
+                }
+              }
+              s_taken[rr] = 1; s_JC[i] = s_JD[rr]; s_slot[i] = s_dslot[rr]; s_told[i] = s_tauD[rr];
+            }
             break;
           }
         }
@@ -153,47 +185,56 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, const double* unif, 
   if (tid == 0) {
     int na = 0, nn = 0, nk = 0;
     for (int i = 0; i < t; ++i) {
-      d.posof[i] = -1;
+      r.posof[i] = -1;
       if (s_JC[i] >= 0) {
         const int is_new = !(s_JC[i] == s_JCp[i]);
-        d.act[na] = i;
-        d.posof[i] = na;
-        d.isnew[na] = is_new;
-        if (is_new) { d.newpos[nn] = na; d.gnew[nn++] = s_slot[i]; } else ++nk;
+        r.act[na] = i;
+        r.posof[i] = na;
+        r.isnew[na] = is_new;
+        if (is_new) { r.newpos[nn] = na; r.gnew[nn++] = s_slot[i]; } else ++nk;
         ++na;
       }
     }
     int npa = 0;
-    for (int i = 0; i < t; ++i) if (s_JCp[i] >= 0) d.pact[npa++] = i;
+    for (int i = 0; i < t; ++i) if (s_JCp[i] >= 0) r.pact[npa++] = i;
     // Gram targets: pool slots of the current and the previous basis (distinct); the new
     // elements first, in the order of gnew, so that target x < nnew is new element x
     int nt = 0;
     for (int i = 0; i < t; ++i)
-      if (s_JC[i] >= 0 && s_JC[i] != s_JCp[i]) { const int ps = s_slot[i]; d.gtgt[nt++] = ps; s_used[ps] = 1; }
+      if (s_JC[i] >= 0 && s_JC[i] != s_JCp[i]) { const int ps = s_slot[i]; r.gtgt[nt++] = ps; s_used[ps] = 1; }
     for (int i = 0; i < t; ++i)
-      if (s_JC[i] >= 0 && s_JC[i] == s_JCp[i]) { const int ps = s_slot[i]; d.gtgt[nt++] = ps; s_used[ps] = 1; }
+      if (s_JC[i] >= 0 && s_JC[i] == s_JCp[i]) { const int ps = s_slot[i]; r.gtgt[nt++] = ps; s_used[ps] = 1; }
     for (int i = 0; i < t; ++i) {
       if (s_JCp[i] < 0) continue;
       const int ps = s_slotp[i];
-      if (!s_used[ps]) { d.gtgt[nt++] = ps; s_used[ps] = 2; }
+      if (!s_used[ps]) { r.gtgt[nt++] = ps; s_used[ps] = 2; }
     }
-    d.meta[META_NACT] = na; d.meta[META_NPACT] = npa; d.meta[META_NNEW] = nn;
-    d.meta[META_NTGT] = nt; d.meta[META_NKEPT] = nk;
-    // buffer slots of the next-but-one batch: the first t pool slots holding none of the new
-    // basis (flag 1), the previous basis (flag 2) and the next batch's columns (flag 3)
-    for (int q = 0; q < t; ++q) s_used[d.dslot_nxt[q]] = 3;
+    for (int i = 0; i < META_LEN; ++i) r.meta[i] = 0;
+    r.meta[META_NACT] = na; r.meta[META_NPACT] = npa; r.meta[META_NNEW] = nn;
+    r.meta[META_NTGT] = nt; r.meta[META_NKEPT] = nk;
+    // buffer slots of batch + la: the first t pool slots holding none of the new basis (flag 1),
+    // the previous basis (flag 2) and the columns of the batches in between (flag 3)
+    for (int k = 1; k < d.la; ++k) {
+      const int* lst = d.dslot_all + (size_t)((batch + k) % d.la) * t;
+      for (int q = 0; q < t; ++q) s_used[lst[q]] = 3;
+    }
     int q = 0;
     for (int ps = 0; ps < np && q < t; ++ps)
       if (s_used[ps] == 0) d.dslot[q++] = ps;
   }
   for (int i = tid; i < t; i += blockDim.x) {
     d.JC[i] = s_JC[i]; d.slotC[i] = s_slot[i]; d.tau_old[i] = s_told[i];
+    r.JC[i] = s_JC[i]; r.slotC[i] = s_slot[i];
+    r.JC_prev[i] = s_JCp[i]; r.slotC_prev[i] = s_slotp[i];
   }
 }
 
-size_t select_smem_bytes(int t, int count, bool stage_u) {
-  return (size_t)8 * (2 * t + 2 * count + (stage_u ? (size_t)t * (count + 1) : 0)) + (size_t)8 * (2 * t + count) +
-         (size_t)4 * (2 * t + 2 * count + 4 * t);
+// Dynamic shared memory of select_kernel: doubles s_told, s_tauC (t), s_p, s_tauD (count) and the
+// staged uniforms (t x (count + 2)); int64 s_JC, s_JCp (t), s_JD (count); ints s_slot, s_slotp
+// (t), s_dslot, s_taken (count) and s_used (npool).
+size_t select_smem_bytes(int t, int count, bool stage_u, int npool) {
+  return (size_t)8 * (2 * t + 2 * count + (stage_u ? (size_t)t * (count + 2) : 0)) + (size_t)8 * (2 * t + count) +
+         (size_t)4 * (2 * t + 2 * count + npool);
 }
 
 // ---------------------------------------------------------------- basis Gram
@@ -912,19 +953,24 @@ __global__ void commit_kernel(Dev d, int64_t n_obs) {
   }
 }
 
-__global__ void finish_kernel(Dev d, int batch, int64_t n_obs) {
+// The end of a step's tail: its decision and counts go to the handle's reporting state (gmeta,
+// and the basis it leaves as gjcp / gslotp, which equal the live basis once no step is in
+// flight).
+__global__ void finish_kernel(Dev d, int batch, int64_t n_obs, int* gmeta, int64_t* gjcp, int* gslotp) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   d.meta[META_QSTAR] = 4 + choose_q(d.scal);
-  for (int i = 0; i < d.t; ++i) { d.JC_prev[i] = d.JC[i]; d.slotC_prev[i] = d.slotC[i]; }
   d.meta[META_BATCH] = batch + 1;
   d.meta[META_NPREV] = (int)n_obs;
+  for (int i = 0; i < META_LEN; ++i) gmeta[i] = d.meta[i];
+  for (int i = 0; i < d.t; ++i) { gjcp[i] = d.JC[i]; gslotp[i] = d.slotC[i]; }
 }
 
 __global__ void reset_kernel(Dev d) {
   const int t = d.t;
   for (int i = threadIdx.x; i < t; i += blockDim.x) {
     d.JC[i] = -1; d.JC_prev[i] = -1; d.slotC[i] = -1; d.slotC_prev[i] = -1;
-    d.dslot[i] = i; d.dslot_nxt[i] = t + i; d.tau_old[i] = 1.0; d.JD[i] = -1;
+    for (int k = 0; k < d.la; ++k) d.dslot_all[(size_t)k * t + i] = k * t + i;
+    d.tau_old[i] = 1.0; d.JD[i] = -1;
   }
   if (threadIdx.x == 0) {
     d.fro2[0] = 0.0; d.fro2[1] = 0.0;
@@ -946,37 +992,47 @@ int launch_reset_state(const Dev& d, cudaStream_t st) {
 int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st) {
   const WorkLayout w = layout(d);
   const bool odd = batch & 1;
-  return launch_lambda(d, batch, d.work, w.eigA, odd ? w.eigR2 : w.eigR, w.eigD, w.eigE, odd ? w.beta2 : w.beta,
-                       odd ? w.vhead2 : w.vhead, w.eigP, w.mu, odd ? w.ldld2 : w.ldld, odd ? w.ldll2 : w.ldll,
-                       d.gbar, d.n_sm, st);
+  return launch_lambda(d, batch, d.work, odd ? w.eigA2 : w.eigA, odd ? w.eigR2 : w.eigR, odd ? w.eigD2 : w.eigD,
+                       odd ? w.eigE2 : w.eigE, odd ? w.beta2 : w.beta, odd ? w.vhead2 : w.vhead,
+                       odd ? w.eigP2 : w.eigP, odd ? w.mu2 : w.mu, odd ? w.ldld2 : w.ldld, odd ? w.ldll2 : w.ldll,
+                       odd ? d.gbar + 8 : d.gbar, d.n_sm, st);
 }
 
-int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
-                      cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select, cudaStream_t stg,
-                      cudaEvent_t ev_fork, cudaEvent_t ev_gram, cudaEvent_t* tl) {
+int launch_batch_select(const Dev& d, const Dev& r, int count, int64_t n_obs, int batch, cudaStream_t st,
+                        cudaEvent_t ev_scores, cudaEvent_t ev_wait_rec, cudaEvent_t* tl) {
   const WorkLayout w = layout(d);
   const int64_t jd0 = n_obs - count;
   const bool odd = batch & 1;
   if (tl) cudaEventRecord(tl[TL_TAIL0], st);
   int nk = launch_scores(d, count, jd0, d.work, odd ? w.eigR2 : w.eigR, odd ? w.beta2 : w.beta,
-                         odd ? w.vhead2 : w.vhead, odd ? w.ldld2 : w.ldld, odd ? w.ldll2 : w.ldll, w.vec,
+                         odd ? w.vhead2 : w.vhead, odd ? w.ldld2 : w.ldld, odd ? w.ldll2 : w.ldll, w.svec,
                          (int)vec_stride(d.s, d.t), st);
   if (ev_scores) cudaEventRecord(ev_scores, st);
   if (tl) cudaEventRecord(tl[TL_SCORES], st);
-  const int nu = d.t * (count + 1);
+  const int nu = d.t * (count + 2);
   uniforms_kernel<<<(nu + 255) / 256, 256, 0, st>>>(d, d.work + w.unif, count, batch);
+  // the record this step writes was last read by the tail of step batch - 2
+  if (ev_wait_rec) cudaStreamWaitEvent(st, ev_wait_rec, 0);
   {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
       attr = true;
     }
-    const bool stage_u = select_smem_bytes(d.t, count, true) <= 160 * 1024;
-    select_kernel<<<1, 256, select_smem_bytes(d.t, count, stage_u), st>>>(d, d.work + w.unif, count,
-                                                                         stage_u ? 1 : 0, jd0);
+    const bool stage_u = select_smem_bytes(d.t, count, true, d.npool) <= 160 * 1024;
+    select_kernel<<<1, 256, select_smem_bytes(d.t, count, stage_u, d.npool), st>>>(d, r, d.work + w.unif, count,
+                                                                         stage_u ? 1 : 0, jd0, batch);
   }
-  if (ev_select) cudaEventRecord(ev_select, st);
   if (tl) cudaEventRecord(tl[TL_SELECT], st);
+  return nk + 2;
+}
+
+int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
+                      cudaStream_t st, cudaStream_t stg, cudaEvent_t ev_fork, cudaEvent_t ev_gram,
+                      int* gmeta, int64_t* gjcp, int* gslotp, cudaEvent_t* tl) {
+  (void)count;
+  const WorkLayout w = layout(d);
+  if (tl) cudaEventRecord(tl[TL_QR0], st);
   // Gram side on stg (basis Gram, G, its Cholesky factor, T of Algorithm 7), sketch side
   // (gather, Householder QRs) on st; they join before the coefficient kernel.
   cudaEventRecord(ev_fork, st);
@@ -1026,12 +1082,12 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
       staged = cudaFuncSetAttribute(hutch_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kHutchSmemBytes) == cudaSuccess ? 1 : 0;
     hutch_finish_kernel<<<4, 512, staged ? kHutchSmemBytes : 0, st>>>(d, w, nchunk, staged,
-                                                                      SCAL_FRO0 + (batch & 3));
+                                                                      SCAL_FRO0 + (batch & 7));
   }
   commit_kernel<<<kApplyBlocks, 256, 0, st>>>(d, n_obs);
-  finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs);
+  finish_kernel<<<1, 32, 0, st>>>(d, batch, n_obs, gmeta, gjcp, gslotp);
   if (tl) cudaEventRecord(tl[TL_TAIL1], st);
-  return nk + 18 + ngk;
+  return 16 + ngk;
 }
 
 }  // namespace rid

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(32) topk_eig_kernel(Dev d, const double* dvec,
 // the two sequential recurrences.
 __global__ void __launch_bounds__(32) lambda_ldl_kernel(Dev d, const double* mu, int k, const double* dvec,
                                                         const double* evec, double* ldl_d, double* ldl_l,
-                                                        int fro_slot) {
+                                                        int fro_slot, int lam_slot) {
   extern __shared__ double lsm[];
   const int n = d.s, lane = threadIdx.x;
   const int kk = k < n ? k : n;
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(32) lambda_ldl_kernel(Dev d, const double* mu,
     lam = (fro - top) / (double)k;
     lam = fmax(lam, 1e-12 * fro / (double)k);
   }
-  d.scal[SCAL_LAMBDA] = lam;
+  d.scal[lam_slot] = lam;
   d.scal[fro_slot] = d.fro2[0];         // the step's ||A_obs||^2: later ingest may add to fro2
   // T + lambda I = L D L^T; ldl_d holds the inverse pivots 1/D_i (0 for a non-positive pivot)
   double del = sd[0] + lam;
@@ -709,7 +709,7 @@ int launch_lambda(const Dev& d, int batch, double* work_base, int64_t off_A, int
     ++nk;
   }
   lambda_ldl_kernel<<<1, 32, (size_t)(2 * d.s + (k < d.s ? k : d.s)) * sizeof(double), st>>>(
-      d, mu, k, dv, ev, ld, ll, SCAL_FRO0 + (batch & 3));
+      d, mu, k, dv, ev, ld, ll, SCAL_FRO0 + (batch & 7), SCAL_LAMBDA + (batch & 1));
   return nk + 1;
 }
 

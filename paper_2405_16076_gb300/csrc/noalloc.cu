@@ -233,6 +233,19 @@ extern "C" int rid_sketch_noalloc(const rid_config* cfg, const void* cols, int64
   }
 
   cudaStream_t st = (cudaStream_t)cfg->cuda_stream;
+  // The scratch address above is the current device's; the kernels run on cfg->cuda_stream, which
+  // must therefore belong to that device (the legacy default stream always does).
+  if (st != nullptr) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return na_fail(RID_EINVAL, "rid_sketch_noalloc: cannot query the device of cfg->cuda_stream");
+    }
+    if (sdev != dev)
+      return na_fail(RID_EINVAL,
+                     "rid_sketch_noalloc: cfg->cuda_stream belongs to another device than the current one "
+                     "(make the stream's device current first)");
+  }
   const int64_t nchunks = (cfg->m + kNaChunk - 1) / kNaChunk;
   const int nblk = (int)(nchunks < kNaBlocks ? nchunks : kNaBlocks);
   double* part = scratch;

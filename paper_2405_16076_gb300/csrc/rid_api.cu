@@ -26,15 +26,21 @@ struct rid_handle {
   rid_config cfg;
   Dev d;
   cudaStream_t st;        // the caller's stream: ingest, and a snapshot of SS^T and ||A||^2 per batch
-  cudaStream_t stl;       // the lambda stream: the lambda part of each batch step, from the snapshot
-  cudaStream_t stb;       // the batch stream: the tail of each batch step (scores .. commit)
+  cudaStream_t stl[2];    // lambda streams: the lambda part of batch b on stl[b % 2], from the snapshot
+  cudaStream_t sts;       // the select stream: ridge scores, uniforms and prune/refill of each step
+  cudaStream_t stb;       // the batch stream: the tail of each batch step (basis Gram .. commit)
   cudaStream_t stg;       // the tail's Gram side, forked from and joined to stb within a step
-  cudaEvent_t ev_fork, ev_gram;
-  cudaEvent_t ev_snap;    // snapshot of the latest batch taken (stream st)
-  cudaEvent_t ev_lambda[2];   // per batch parity, recorded on stl
-  cudaEvent_t ev_scores[2], ev_select[2], ev_tail[2];   // per batch parity, recorded on stb
-  int* dslot_buf;         // 2 x t: buffer-slot lists of consecutive batches
+  cudaEvent_t ev_fork;
+  // per batch b, slot b % kEv (recorded once per step; the slot of step b is reused by step
+  // b + kEv, long after every wait on it was enqueued)
+  static constexpr int kEv = 8;
+  cudaEvent_t ev_snap[kEv], ev_lambda[kEv], ev_scores[kEv], ev_select[kEv], ev_gram[kEv], ev_tail[kEv];
+  int* dslot_buf;         // la x t: buffer-slot lists of the batches b .. b + la - 1 (batch b at b % la)
   double* snap;           // 2 x (s*s + 2): SS^T and ||A||^2 as of the end of a batch, by parity
+  // selection records of the steps in flight, by batch parity: the previous and the new basis
+  // (indices and pool slots) and the index lists of the tail
+  int64_t* rec_i64;       // 2 x 2t
+  int* rec_i32;           // 2 x (10t + META_LEN)
   int count;          // columns buffered since the last batch step
   int64_t n_obs;      // columns ingested
   int64_t n_prev;     // columns covered by the last batch step
@@ -43,7 +49,13 @@ struct rid_handle {
   bool joined;            // the caller's stream already waits for every batch step issued
   bool kg_ready;          // d.Kg holds Omega G^p Omega^T / s
   size_t esize;
-  void* staging;          // host-input staging area: group_max columns of m_pad
+  void* staging;          // host-input staging: two areas of group_max columns of m_pad
+  cudaStream_t stc;       // host-to-device copies of host columns into the staging areas
+  cudaEvent_t ev_cfork;   // on st: the ingest of the previous group has been enqueued before this point
+  cudaEvent_t ev_cfull;   // on stc: the copies of the group being flushed are complete
+  bool cfork_valid;       // ev_cfork has been recorded
+  int stage_area;         // staging area the current group's host columns go to
+  int pend_host;          // host columns in the pending group
   std::vector<const void*> pend;   // columns recorded but not yet sketched
   int group_max;
   bool tc;                // tensor-core ingest (FP32 data, BF16 / BF16x2 sketch)
@@ -75,7 +87,7 @@ struct rid_handle {
 // A log slot: the step's scal[] at 0 (after its tail), lambda and ||A_obs||^2 at 128 (after its
 // lambda part, before the next step's lambda part overwrites them), meta[] at 144.
 constexpr size_t kLogSlot = 256;
-static_assert(144 + sizeof(int) * rid::META_LEN <= kLogSlot && sizeof(double) * rid::SCAL_LEN <= 128,
+static_assert(144 + sizeof(int) * rid::META_LEN <= kLogSlot && sizeof(double) * rid::SCAL_LOG <= 128,
               "log slot layout");
 
 static thread_local std::string g_init_err;
@@ -128,7 +140,7 @@ cudaError_t dalloc(T** p, size_t n) {
 
 void free_all(Dev& d, void* staging) {
   void* ptrs[] = {d.pool, d.omegaT, d.omegagT, d.S, d.SSt, d.fro2, d.JC, d.JC_prev, d.slotC,
-                  d.slotC_prev, d.dslot /* 2t: both batch lists */, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
+                  d.slotC_prev, d.dslot_all, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
                   d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
                   d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, d.Y, d.Wr, d.zq, d.Sg,
                   d.Kg, staging};
@@ -137,24 +149,68 @@ void free_all(Dev& d, void* staging) {
 }
 
 void destroy_sync_objects(rid_handle* h) {
-  if (h->stb) cudaStreamDestroy(h->stb);
-  if (h->stl) cudaStreamDestroy(h->stl);
-  if (h->stg) cudaStreamDestroy(h->stg);
-  cudaEvent_t evs[] = {h->ev_fork, h->ev_gram, h->ev_snap, h->ev_lambda[0], h->ev_lambda[1], h->ev_scores[0], h->ev_scores[1],
-                       h->ev_select[0], h->ev_select[1], h->ev_tail[0], h->ev_tail[1]};
-  for (cudaEvent_t e : evs) if (e) cudaEventDestroy(e);
-  h->stb = nullptr;
-  h->stl = nullptr;
-  h->stg = nullptr;
+  for (cudaStream_t* sp : {&h->stb, &h->stl[0], &h->stl[1], &h->sts, &h->stg, &h->stc}) {
+    if (*sp) cudaStreamDestroy(*sp);
+    *sp = nullptr;
+  }
+  for (cudaEvent_t* e : {&h->ev_fork, &h->ev_cfork, &h->ev_cfull}) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
+  }
+  for (int i = 0; i < rid_handle::kEv; ++i)
+    for (cudaEvent_t* e : {&h->ev_snap[i], &h->ev_lambda[i], &h->ev_scores[i], &h->ev_select[i], &h->ev_gram[i],
+                           &h->ev_tail[i]}) {
+      if (*e) cudaEventDestroy(*e);
+      *e = nullptr;
+    }
+}
+
+int create_sync_objects(rid_handle* h) {
+  int prio_lo = 0, prio_hi = 0;
+  // The batch-step streams get the device's highest priority: their kernels are short and on
+  // the critical path, and each of the ingest's CTAs holds a whole SM for its chunk range, so
+  // freed SMs should go to them first.
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  for (cudaStream_t* sp : {&h->stb, &h->stl[0], &h->stl[1], &h->sts, &h->stg})
+    if (cudaStreamCreateWithPriority(sp, cudaStreamNonBlocking, prio_hi) != cudaSuccess) return RID_ECUDA;
+  if (cudaStreamCreateWithFlags(&h->stc, cudaStreamNonBlocking) != cudaSuccess) return RID_ECUDA;
+  for (cudaEvent_t* e : {&h->ev_fork, &h->ev_cfork, &h->ev_cfull})
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return RID_ECUDA;
+  for (int i = 0; i < rid_handle::kEv; ++i)
+    for (cudaEvent_t* e : {&h->ev_snap[i], &h->ev_lambda[i], &h->ev_scores[i], &h->ev_select[i], &h->ev_gram[i],
+                           &h->ev_tail[i]})
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return RID_ECUDA;
+  return RID_OK;
 }
 
 // The device view for batch b: its buffer-slot list and the next batch's.
 Dev dev_for(const rid_handle* h, int b) {
   Dev d = h->d;
   const int t = d.t;
-  d.dslot = h->dslot_buf + (size_t)(b & 1) * t;
-  d.dslot_nxt = h->dslot_buf + (size_t)((b + 1) & 1) * t;
+  d.dslot = h->dslot_buf + (size_t)(b % d.la) * t;
   return d;
+}
+
+// The selection record of step b (copy b % 2) as the device view its tail reads: JC / slotC the
+// new basis, JC_prev / slotC_prev the previous one, the index lists and the step's counts.
+Dev rec_view(const rid_handle* h, int b) {
+  Dev r = dev_for(h, b);
+  const int t = r.t;
+  int64_t* i64 = h->rec_i64 + (size_t)(b & 1) * 2 * t;
+  int* i32 = h->rec_i32 + (size_t)(b & 1) * (10 * (size_t)t + rid::META_LEN);
+  r.JC = i64;
+  r.JC_prev = i64 + t;
+  r.slotC = i32;
+  r.slotC_prev = i32 + t;
+  r.act = i32 + 2 * t;
+  r.pact = i32 + 3 * t;
+  r.isnew = i32 + 4 * t;
+  r.posof = i32 + 5 * t;
+  r.newpos = i32 + 6 * t;
+  r.gnew = i32 + 7 * t;
+  r.gtgt = i32 + 8 * t;                 // 2t
+  r.meta = i32 + 10 * t;
+  return r;
 }
 
 // Make the caller's stream wait for the tail of the latest batch step (after this, work on
@@ -163,7 +219,7 @@ Dev dev_for(const rid_handle* h, int b) {
 // whose stream already waits -- e.g. after an asynchronous finalize captured into a CUDA graph,
 // whose events must not be waited on outside the graph -- adds no second wait).
 void join(rid_handle* h) {
-  if (h->batch >= 1 && !h->joined) cudaStreamWaitEvent(h->st, h->ev_tail[(h->batch - 1) & 1], 0);
+  if (h->batch >= 1 && !h->joined) cudaStreamWaitEvent(h->st, h->ev_tail[(h->batch - 1) % rid_handle::kEv], 0);
   h->joined = true;
 }
 
@@ -239,27 +295,32 @@ cudaEvent_t next_event(rid_handle* h) {
 }
 
 // Batch step b.  The caller's stream snapshots SS^T and ||A||^2 (buffer b % 2, free once
-// the lambda part of step b-2 has run) and goes on ingesting; the lambda part runs on the
-// lambda stream from the snapshot into output copy b % 2 (after step b-2's scores, the last
-// reader of that copy); the tail runs on the batch stream after it.
+// the lambda part of step b-2 has run) and goes on ingesting; the lambda part runs on lambda
+// stream b % 2 from the snapshot into output copy b % 2 (after step b-2's scores, the last
+// reader of that copy); the select part runs on the select stream after it (writing selection
+// record b % 2 once the tail of step b-2, its last reader, has ended); the tail runs on the
+// batch stream after the select.
 int run_batch(rid_handle* h) {
   NvtxRange nvtx("rid_batch_step");
   const int b = h->batch;
+  constexpr int E = rid_handle::kEv;
   h->joined = false;
   const Dev db = dev_for(h, b);
+  const Dev rv = rec_view(h, b);
+  cudaStream_t stl = h->stl[b & 1];
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->prof) { e0 = next_event(h); e1 = next_event(h); cudaEventRecord(e0, h->st); }
   const size_t ss = (size_t)db.s * db.s;
   double* snap = h->snap + (size_t)(b & 1) * (ss + 2);
-  if (b >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_lambda[b & 1], 0));
+  if (b >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_lambda[(b - 2) % E], 0));
   CK(cudaMemcpyAsync(snap, db.SSt, ss * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   CK(cudaMemcpyAsync(snap + ss, db.fro2, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-  CK(cudaEventRecord(h->ev_snap, h->st));
-  CK(cudaStreamWaitEvent(h->stl, h->ev_snap, 0));
+  CK(cudaEventRecord(h->ev_snap[b % E], h->st));
+  CK(cudaStreamWaitEvent(stl, h->ev_snap[b % E], 0));
   // the lambda outputs of batch b share their copy (b % 2) with the scores of batch b-2; its
   // ||A_obs||^2 slot (b % 4) was last read by the tail of batch b-4, which ended before the
-  // scores of batch b-2 ran (one batch stream)
-  if (b >= 2) CK(cudaStreamWaitEvent(h->stl, h->ev_scores[b & 1], 0));
+  // select of batch b-2 wrote the buffer slots of this batch (whose ingest preceded the snapshot)
+  if (b >= 2) CK(cudaStreamWaitEvent(stl, h->ev_scores[(b - 2) % E], 0));
   Dev dl = db;
   dl.SSt = snap;
   dl.fro2 = snap + ss;
@@ -267,33 +328,39 @@ int run_batch(rid_handle* h) {
   if (h->prof) {
     for (auto& e : tle) e = next_event(h);
     cudaEventRecord(tle[rid::TL_SNAP], h->st);
-    cudaEventRecord(tle[rid::TL_LAMBDA0], h->stl);
+    cudaEventRecord(tle[rid::TL_LAMBDA0], stl);
   }
-  const int nl = rid::launch_batch_lambda(dl, b, h->stl);
-  if (h->prof) cudaEventRecord(tle[rid::TL_LAMBDA1], h->stl);
+  const int nl = rid::launch_batch_lambda(dl, b, stl);
+  if (h->prof) cudaEventRecord(tle[rid::TL_LAMBDA1], stl);
   if (nl && h->log_cap > 0) {
     char* slot = h->log_dev + (size_t)(b % h->log_cap) * kLogSlot;
-    CK(cudaMemcpyAsync(slot + 128, dl.scal + rid::SCAL_LAMBDA, sizeof(double), cudaMemcpyDeviceToDevice, h->stl));
-    CK(cudaMemcpyAsync(slot + 136, dl.scal + rid::SCAL_FRO0 + (b & 3), sizeof(double), cudaMemcpyDeviceToDevice,
-                       h->stl));
+    CK(cudaMemcpyAsync(slot + 128, dl.scal + rid::SCAL_LAMBDA + (b & 1), sizeof(double), cudaMemcpyDeviceToDevice,
+                       stl));
+    CK(cudaMemcpyAsync(slot + 136, dl.scal + rid::SCAL_FRO0 + (b & 7), sizeof(double), cudaMemcpyDeviceToDevice,
+                       stl));
   }
-  CK(cudaEventRecord(h->ev_lambda[b & 1], h->stl));
-  CK(cudaStreamWaitEvent(h->stb, h->ev_lambda[b & 1], 0));
-  const int nt = nl ? rid::launch_batch_tail(db, h->count, h->n_obs, h->n_prev, b, h->stb, h->ev_scores[b & 1],
-                                             h->ev_select[b & 1], h->stg, h->ev_fork, h->ev_gram,
+  CK(cudaEventRecord(h->ev_lambda[b % E], stl));
+  CK(cudaStreamWaitEvent(h->sts, h->ev_lambda[b % E], 0));
+  const int ns = nl ? rid::launch_batch_select(db, rv, h->count, h->n_obs, b, h->sts, h->ev_scores[b % E],
+                                               b >= 2 ? h->ev_tail[(b - 2) % E] : nullptr, h->prof ? tle : nullptr)
+                    : 0;
+  CK(cudaEventRecord(h->ev_select[b % E], h->sts));
+  CK(cudaStreamWaitEvent(h->stb, h->ev_select[b % E], 0));
+  const int nt = ns ? rid::launch_batch_tail(rv, h->count, h->n_obs, h->n_prev, b, h->stb, h->stg, h->ev_fork,
+                                             h->ev_gram[b % E], db.meta, db.JC_prev, db.slotC_prev,
                                              h->prof ? tle : nullptr)
                     : 0;
-  if (nl == 0 || nt == 0) {
+  if (nl == 0 || ns == 0 || nt == 0) {
     cudaGetLastError();
     return fail(h, RID_ECUDA, "batch step launch failed (cooperative or cluster launch refused)");
   }
   if (h->log_cap > 0) {
     char* slot = h->log_dev + (size_t)(b % h->log_cap) * kLogSlot;
-    CK(cudaMemcpyAsync(slot, db.scal, sizeof(double) * rid::SCAL_LEN, cudaMemcpyDeviceToDevice, h->stb));
+    CK(cudaMemcpyAsync(slot, db.scal, sizeof(double) * rid::SCAL_LOG, cudaMemcpyDeviceToDevice, h->stb));
     CK(cudaMemcpyAsync(slot + 144, db.meta, sizeof(int) * rid::META_LEN, cudaMemcpyDeviceToDevice, h->stb));
   }
-  CK(cudaEventRecord(h->ev_tail[b & 1], h->stb));
-  const int nk = nl + nt;
+  CK(cudaEventRecord(h->ev_tail[b % E], h->stb));
+  const int nk = nl + ns + nt;
   if (h->prof) {
     cudaEventRecord(e1, h->stb);
     h->spans[2].push_back({e0, e1});
@@ -303,7 +370,7 @@ int run_batch(rid_handle* h) {
                             {rid::TLP_SCORES, rid::TL_TAIL0, rid::TL_SCORES},
                             {rid::TLP_SELECT, rid::TL_SCORES, rid::TL_SELECT},
                             {rid::TLP_GRAM, rid::TL_GRAM0, rid::TL_GRAM1},
-                            {rid::TLP_QR, rid::TL_SELECT, rid::TL_QR1},
+                            {rid::TLP_QR, rid::TL_QR0, rid::TL_QR1},
                             {rid::TLP_COEFF, rid::TL_QR1, rid::TL_TAIL1}};
     for (const auto& pr : pairs) h->tl.push_back({b, pr[0], tle[pr[1]], tle[pr[2]]});
   }
@@ -332,9 +399,29 @@ int flush(rid_handle* h) {
   if (G == 0) return RID_OK;
   int rc = grow(h, h->n_obs + G);
   if (rc != RID_OK) return rc;
-  // The batch's buffer slots were chosen by the select of step batch-2; steps batch-2 and
-  // batch-1 (which may still run on the batch stream) read none of them.
-  if (h->count == 0 && h->batch >= 2) CK(cudaStreamWaitEvent(h->st, h->ev_select[(h->batch - 2) & 1], 0));
+  // Host columns of this group were copied into staging area stage_area on the copy stream; the
+  // copies of the next group (into the other area) may start once the caller's stream has passed
+  // the ingest of the previous group, the last reader of that area: ev_cfork marks that point,
+  // before the waits below, so that the copies overlap this group's ingest.
+  if (h->pend_host > 0) CK(cudaEventRecord(h->ev_cfull, h->stc));
+  CK(cudaEventRecord(h->ev_cfork, h->st));
+  h->cfork_valid = true;
+  // The batch's buffer slots were chosen by the select of step batch - la among the slots holding
+  // neither its previous nor its new basis nor the columns of the batches in between; they may
+  // still hold basis columns of step batch - la - 1, which the Gram side of that step's tail
+  // reads (it may still run).
+  {
+    const int la = h->d.la;
+    if (h->count == 0 && h->batch >= la) {
+      CK(cudaStreamWaitEvent(h->st, h->ev_select[(h->batch - la) % rid_handle::kEv], 0));
+      if (h->batch >= la + 1) CK(cudaStreamWaitEvent(h->st, h->ev_gram[(h->batch - la - 1) % rid_handle::kEv], 0));
+    }
+  }
+  if (h->pend_host > 0) {
+    CK(cudaStreamWaitEvent(h->st, h->ev_cfull, 0));
+    h->pend_host = 0;
+    h->stage_area ^= 1;
+  }
   const Dev db = dev_for(h, h->batch);
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (h->prof) for (auto& e : ev) e = next_event(h);
@@ -412,6 +499,10 @@ int check_config(const rid_config* c) {
   if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
   if (c->right_l < 0 || c->right_l > 4096) return fail(h, RID_EINVAL, "right_l must be in [0, 4096]");
   if (c->ingest_ctas < 0) return fail(h, RID_EINVAL, "ingest_ctas must be >= 0");
+  if (c->refill_mode != RID_REFILL_FIRST && c->refill_mode != RID_REFILL_PROPORTIONAL)
+    return fail(h, RID_EINVAL, "unknown refill_mode");
+  if (c->lookahead != 0 && (c->lookahead < 2 || c->lookahead > 4))
+    return fail(h, RID_EINVAL, "lookahead must be 0 (default 3) or in [2, 4]");
   if (c->grad_coeff != 0 && c->grad_dims != 2)
     return fail(h, RID_EINVAL, "grad_coeff needs gradient mode (grad_dims = 2)");
   if (c->grad_dims != 0) {
@@ -498,6 +589,8 @@ int rid_init(rid_handle** out, const rid_config* c) {
   d.lambda_fixed = c->lambda_fixed;
   const double k = (double)c->k;
   d.refill_scale = c->c_const * (k * log(k) + k * log(1.0 / c->delta) / c->eps) / (double)c->k;
+  d.refill_mode = c->refill_mode;
+  d.la = c->lookahead > 0 ? c->lookahead : 3;
   d.seed = c->seed;
   d.grad = c->grad_dims != 0 ? 1 : 0;
   d.nx = c->nx;
@@ -546,7 +639,6 @@ int rid_init(rid_handle** out, const rid_config* c) {
     // a chosen count (rid_autotune) stays within the partial buffers sized below
     if (c->ingest_ctas > 0) h->ingest_blocks = c->ingest_ctas < h->first_blocks ? c->ingest_ctas : h->first_blocks;
   }
-  int prio_lo = 0, prio_hi = 0;
   int rc = RID_OK;
 #define AL(ptr, n) do { if (dalloc(&(ptr), (size_t)(n)) != cudaSuccess) { rc = RID_ENOMEM; goto fail_alloc; } } while (0)
   if (h->tc) {
@@ -562,9 +654,9 @@ int rid_init(rid_handle** out, const rid_config* c) {
   }
   {
     char* pool = nullptr;
-    // 4t slots: the previous and the new basis of the step in flight (at most 2t together with
-    // its batch), and the next batch being ingested (t)
-    d.npool = 4 * t;
+    // (la + 2) t slots: the previous and the new basis of the latest step (at most 2t together
+    // with its batch), and the la batches after it, ingested while steps are in flight (t each)
+    d.npool = (d.la + 2) * t;
     AL(pool, (size_t)d.npool * d.m_pad * h->esize);
     d.pool = pool;
     if (cudaMemset(d.pool, 0, (size_t)d.npool * d.m_pad * h->esize) != cudaSuccess) { rc = RID_ECUDA; goto fail_alloc; }
@@ -574,17 +666,19 @@ int rid_init(rid_handle** out, const rid_config* c) {
   AL(h->snap, (size_t)2 * ((size_t)d.s * d.s + 2));
   AL(d.fro2, 2);
   AL(d.JC, t); AL(d.JC_prev, t); AL(d.JD, t);
-  AL(d.slotC, t); AL(d.slotC_prev, t); AL(d.dslot, 2 * t);
+  AL(d.slotC, t); AL(d.slotC_prev, t); AL(d.dslot_all, (size_t)d.la * t);
   AL(d.tau_old, t); AL(d.tauC, t); AL(d.tauD, t);
   AL(d.meta, rid::META_LEN); AL(d.scal, rid::SCAL_LEN);
   AL(d.act, t); AL(d.pact, t); AL(d.isnew, t); AL(d.posof, t); AL(d.newpos, t);
   AL(d.gnew, t); AL(d.gtgt, 2 * t);
+  AL(h->rec_i64, 4 * (size_t)t);
+  AL(h->rec_i32, 2 * (10 * (size_t)t + rid::META_LEN));
   AL(d.Gp, (size_t)d.npool * d.npool);
   AL(d.gpart, (size_t)d.gram_split * t * 2 * t);
   AL(d.spart, (size_t)d.n_sketch_blocks * rid::kMaxB * d.rows);
   AL(d.npart, (size_t)d.n_sketch_blocks * rid::kMaxB);
   AL(d.err, 1);
-  AL(d.gbar, 8);
+  AL(d.gbar, 12);                      // [0, 4) lambda part of even batches, [4, 8) QRs, [8, 12) odd batches
   if (d.grad_coeff) AL(d.Kg, (size_t)2 * d.s * d.s);
   if (d.right_l > 0) {
     char* y = nullptr;
@@ -601,7 +695,7 @@ int rid_init(rid_handle** out, const rid_config* c) {
   AL(d.work, d.work_len);
   {
     char* stg = nullptr;
-    AL(stg, (size_t)h->group_max * d.m_pad * h->esize);
+    AL(stg, 2 * (size_t)h->group_max * d.m_pad * h->esize);
     h->staging = stg;
   }
 #undef AL
@@ -610,26 +704,9 @@ int rid_init(rid_handle** out, const rid_config* c) {
     rc = grow(h, want);
     if (rc != RID_OK) goto fail_alloc;
   }
-  h->dslot_buf = d.dslot;
-  d.dslot_nxt = d.dslot + t;
-  // The batch-step streams get the device's highest priority: their kernels are short and on
-  // the critical path, and each of the ingest's CTAs holds a whole SM for its chunk range, so
-  // freed SMs should go to them first.
-  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-  if (cudaStreamCreateWithPriority(&h->stb, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&h->stl, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&h->stg, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_gram, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_lambda[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_lambda[1], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_scores[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_scores[1], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_select[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_select[1], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_tail[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_tail[1], cudaEventDisableTiming) != cudaSuccess) {
+  h->dslot_buf = d.dslot_all;
+  d.dslot = d.dslot_all;
+  if (create_sync_objects(h) != RID_OK) {
     rc = RID_ECUDA;
     goto fail_alloc;
   }
@@ -649,6 +726,8 @@ fail_alloc:
     if (h->tg_part) cudaFree(h->tg_part);
     if (h->tc_npart) cudaFree(h->tc_npart);
     if (h->snap) cudaFree(h->snap);
+    if (h->rec_i64) cudaFree(h->rec_i64);
+    if (h->rec_i32) cudaFree(h->rec_i32);
     destroy_sync_objects(h);
     delete h;
     return fail(nullptr, rc, msg);
@@ -667,10 +746,22 @@ int rid_ingest(rid_handle* h, const void* cols, int64_t ld, int32_t ncols, int32
   for (int32_t q = 0; q < ncols; ++q) {
     const char* src = (const char*)cols + (size_t)q * ld * h->esize;
     if (!on_device) {
-      // host columns go through the staging area, in stream order with the ingest that reads
-      // them (a copy stream with two areas overlapping the two was slower on GB300)
-      char* dst = (char*)h->staging + h->pend.size() * (size_t)h->d.m_pad * h->esize;
-      CK(cudaMemcpyAsync(dst, src, cbytes, cudaMemcpyHostToDevice, h->st));
+      // Host columns go through a staging area on the copy stream: the group's columns into area
+      // stage_area, while the caller's stream ingests the previous group from the other area.
+      // (The pool slot a column lands in is chosen on the device, so the copy cannot go there
+      // directly.)  The first copy of a group waits until the ingest that last read the area has
+      // been passed (ev_cfork, recorded by the previous flush, or here when none was).
+      if (h->pend_host == 0) {
+        if (!h->cfork_valid) {
+          CK(cudaEventRecord(h->ev_cfork, h->st));
+          h->cfork_valid = true;
+        }
+        CK(cudaStreamWaitEvent(h->stc, h->ev_cfork, 0));
+      }
+      char* dst = (char*)h->staging + ((size_t)h->stage_area * h->group_max + h->pend.size()) *
+                                           (size_t)h->d.m_pad * h->esize;
+      CK(cudaMemcpyAsync(dst, src, cbytes, cudaMemcpyHostToDevice, h->stc));
+      h->pend_host += 1;
       src = dst;
     }
     h->pend.push_back(src);
@@ -852,7 +943,11 @@ int rid_get_state(rid_handle* h, int32_t item, void* out, int64_t count) {
     case RID_STATE_FRO2: src = d.fro2; bytes = sizeof(double) * 2; break;
     case RID_STATE_JC: src = d.JC; bytes = sizeof(int64_t) * d.t; break;
     case RID_STATE_TAU_OLD: src = d.tau_old; bytes = sizeof(double) * d.t; break;
-    case RID_STATE_LAMBDA: src = d.scal + rid::SCAL_LAMBDA; bytes = sizeof(double); break;
+    case RID_STATE_LAMBDA:
+      if (h->batch < 1) return fail(h, RID_ESTATE, "no batch step has run yet");
+      src = d.scal + rid::SCAL_LAMBDA + ((h->batch - 1) & 1);
+      bytes = sizeof(double);
+      break;
     case RID_STATE_GRAM_SHIFT: src = d.scal + rid::SCAL_GSHIFT; bytes = sizeof(double); break;
     case RID_STATE_GRAD_SKETCH:
       if (!d.grad_coeff) return fail(h, RID_ESTATE, "no gradient sketches (grad_coeff = 0)");
@@ -899,7 +994,8 @@ bool same_config(const rid_config& a, const rid_config& b) {
          a.c1 == b.c1 && a.c2 == b.c2 && a.eps == b.eps && a.delta == b.delta && a.c_const == b.c_const &&
          a.lambda_fixed == b.lambda_fixed && a.omega_kind == b.omega_kind && a.data_dtype == b.data_dtype &&
          a.sketch_prec == b.sketch_prec && a.grad_dims == b.grad_dims && a.nx == b.nx && a.ny == b.ny &&
-         a.nfields == b.nfields && a.seed == b.seed && a.right_l == b.right_l && a.grad_coeff == b.grad_coeff;
+         a.nfields == b.nfields && a.seed == b.seed && a.right_l == b.right_l && a.grad_coeff == b.grad_coeff &&
+         a.refill_mode == b.refill_mode && a.lookahead == b.lookahead;
 }
 
 struct CkptPlan {
@@ -919,7 +1015,7 @@ std::vector<std::pair<void*, size_t>> ckpt_arrays(rid_handle* h, int64_t n) {
       {d.fro2, 2 * sizeof(double)},
       {d.JC, sizeof(int64_t) * t}, {d.JC_prev, sizeof(int64_t) * t},
       {d.slotC, sizeof(int) * t}, {d.slotC_prev, sizeof(int) * t},
-      {h->dslot_buf, sizeof(int) * 2 * (size_t)t},
+      {h->dslot_buf, sizeof(int) * (size_t)d.la * t},
       {d.tau_old, sizeof(double) * t},
       {d.meta, sizeof(int) * rid::META_LEN}, {d.scal, sizeof(double) * rid::SCAL_LEN},
       {d.P, sizeof(double) * (size_t)t * n},
@@ -936,13 +1032,13 @@ int ckpt_plan(rid_handle* h, CkptPlan& pl) {
   Dev& d = h->d;
   const int t = d.t;
   pl.arrays = ckpt_arrays(h, h->n_obs);
-  std::vector<int> slotc(t), dsl(2 * (size_t)t);
+  std::vector<int> slotc(t), dsl((size_t)d.la * t);
   CK(cudaMemcpyAsync(slotc.data(), d.slotC, sizeof(int) * t, cudaMemcpyDeviceToHost, h->st));
-  CK(cudaMemcpyAsync(dsl.data(), h->dslot_buf, sizeof(int) * 2 * t, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(dsl.data(), h->dslot_buf, sizeof(int) * (size_t)d.la * t, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   pl.slots.clear();
   for (int i = 0; i < t; ++i) if (slotc[i] >= 0) pl.slots.push_back(slotc[i]);
-  const int* cur = dsl.data() + (size_t)(h->batch & 1) * t;
+  const int* cur = dsl.data() + (size_t)(h->batch % d.la) * t;
   for (int q = 0; q < h->count; ++q) pl.slots.push_back(cur[q]);
   size_t tot = sizeof(uint64_t) + sizeof(rid_config) + sizeof(CkptCounters);
   for (auto& a : pl.arrays) tot += a.second;
@@ -1136,6 +1232,7 @@ int rid_reset(rid_handle* h) {
   if (h->d.right_l > 0) CK(cudaMemsetAsync(h->d.Y, 0, (size_t)h->d.m_pad * h->d.right_l * h->esize, h->st));
   CK(cudaGetLastError());
   h->pend.clear();
+  h->pend_host = 0;
   h->count = 0;
   h->n_obs = 0;
   h->n_prev = 0;
@@ -1184,7 +1281,7 @@ int rid_get_log(rid_handle* h, rid_log_record* out, int32_t max_records, int32_t
   for (int64_t i = 0; i < nrec; ++i) {
     const int64_t b = h->batch - nrec + i;
     const char* slot = buf.data() + (size_t)(b % h->log_cap) * kLogSlot;
-    double sc[rid::SCAL_LEN], lf[2];
+    double sc[rid::SCAL_LOG], lf[2];
     int mt[rid::META_LEN];
     memcpy(sc, slot, sizeof(sc));
     memcpy(lf, slot + 128, sizeof(lf));
@@ -1216,9 +1313,8 @@ void rid_destroy(rid_handle* h) {
   if (!h) return;
   join(h);
   cudaStreamSynchronize(h->st);
-  if (h->stb) cudaStreamSynchronize(h->stb);
-  if (h->stl) cudaStreamSynchronize(h->stl);
-  if (h->stg) cudaStreamSynchronize(h->stg);
+  for (cudaStream_t x : {h->stb, h->stl[0], h->stl[1], h->sts, h->stg, h->stc})
+    if (x) cudaStreamSynchronize(x);
   for (auto e : h->evpool) cudaEventDestroy(e);
   if (h->tl_base) cudaEventDestroy(h->tl_base);
   free_all(h->d, h->staging);
@@ -1226,6 +1322,8 @@ void rid_destroy(rid_handle* h) {
   if (h->tg_part) cudaFree(h->tg_part);
   if (h->tc_npart) cudaFree(h->tc_npart);
   if (h->snap) cudaFree(h->snap);
+  if (h->rec_i64) cudaFree(h->rec_i64);
+  if (h->rec_i32) cudaFree(h->rec_i32);
   if (h->log_dev) cudaFree(h->log_dev);
   destroy_sync_objects(h);
   delete h;

@@ -36,6 +36,7 @@ struct Dev {
   int lambda_mode;
   double lambda_fixed;
   double refill_scale;            // c (k ln k + k ln(1/delta)/eps) / t
+  int refill_mode;                // 0 first success (R7), 1 proportional draw (R7p)
   uint64_t seed;
   int grad;                       // gradient mode
   int nx, ny, nfields;
@@ -52,8 +53,9 @@ struct Dev {
   int64_t* JC; int64_t* JC_prev;  // t
   int* slotC; int* slotC_prev;    // t, pool slot of each basis slot (-1 empty)
   int* dslot;                     // t, pool slot receiving the q-th buffered column of this batch
-  int* dslot_nxt;                 // t, the same for the next batch (chosen one batch ahead)
-  int npool;                      // pool slots: 4t (previous and new basis, this batch, next batch)
+  int* dslot_all;                 // la x t: the lists of batches b .. b + la - 1, batch b at (b % la) t
+  int la;                         // lookahead: the select of step b picks the slots of batch b + la
+  int npool;                      // pool slots: (la + 2) t (previous and new basis, la batches)
   int64_t* JD;                    // t, global index of the q-th buffered column
   double* tau_old;                // t
   double* tauC; double* tauD;     // t each
@@ -98,16 +100,20 @@ enum {
   META_NOBS = 5, META_NPREV = 6, META_BATCH = 7, META_QSTAR = 8, META_NKEPT = 9, META_LEN = 16
 };
 // scal[] indices
-// SCAL_FRO0 + (batch & 3): ||A_obs||^2 as the batch's step saw it, written by its lambda part and
-// read at the end of its tail (four slots: the lambda parts of the next two steps may run while
-// this step's tail still reads it)
+// SCAL_FRO0 + (batch & 7): ||A_obs||^2 as the batch's step saw it, written by its lambda part and
+// read at the end of its tail (eight slots: the lambda parts of the next steps may run while this
+// step's tail still reads it; the lambda part of step b + 8 follows the ingest of its batch, which
+// follows the select of step b + 8 - la, which follows the tail of step b + 6 - la >= b)
 // SCAL_GSHIFT: the Tikhonov shift of the basis Gram in the last batch step, relative to its
 // largest diagonal entry (0 when the Gram was factored as is).
 // SCAL_UNC + q: rounding uncertainty of candidate q's estimate relative to ||A_obs||^2 (see
 // hutch_finish_kernel); 0 for FP64 sketches.
+// SCAL_LAMBDA + (batch & 1): lambda of the step (two slots: consecutive steps' lambda parts run
+// concurrently on two streams).
+// Entries [0, SCAL_LOG) are the step's decision quantities copied into the per-batch log.
 enum {
-  SCAL_LAMBDA = 0, SCAL_EST = 1 /* 4 signed estimates */, SCAL_FRO0 = 12 /* 4 slots */, SCAL_GSHIFT = 7,
-  SCAL_UNC = 8 /* 4 values */, SCAL_LEN = 16
+  SCAL_LAMBDA = 5 /* 2 slots */, SCAL_EST = 1 /* 4 signed estimates */, SCAL_FRO0 = 16 /* 8 slots */,
+  SCAL_GSHIFT = 7, SCAL_UNC = 8 /* 4 values */, SCAL_LOG = 16, SCAL_LEN = 24
 };
 
 // Per (candidate, column chunk) partials of the Hutch++ step: H P_q^T (hh x t), tr(G P P^T) and
@@ -174,24 +180,30 @@ int tc_smem_bytes();
 int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st);
 void launch_materialize_omega(const Dev& d, cudaStream_t st);
 
-// batch.cu.  A batch step runs in two parts on two streams.  The lambda part
-// (tridiagonalization of the sketch Gram, its top-k eigenvalues, lambda and the LDL^T of
-// T + lambda I; it also snapshots ||A_obs||^2) reads only the sketch and runs on the ingest
-// stream.  The tail (ridge scores, prune/refill, basis Gram, Algorithms 4-8, commit) runs on
-// the batch stream; ev_scores (may be null) is recorded after the scores, once the tail no
-// longer needs the lambda part's outputs, and ev_select (may be null) once the buffer slots of
-// the next-but-one batch are chosen.  The tail's Gram side (basis Gram, G and its factor, T)
-// runs on stg between ev_fork and ev_gram, beside the sketch side's QRs on st.  Both return
-// the number of kernels launched (0 on failure).
 // Timeline events of one batch step (recorded only while profiling; tl may be null).
-enum { TL_SNAP = 0, TL_LAMBDA0, TL_LAMBDA1, TL_TAIL0, TL_SCORES, TL_SELECT, TL_GRAM0, TL_GRAM1, TL_QR1, TL_TAIL1,
-       kTlEvents };
+enum { TL_SNAP = 0, TL_LAMBDA0, TL_LAMBDA1, TL_TAIL0, TL_SCORES, TL_SELECT, TL_GRAM0, TL_GRAM1, TL_QR0, TL_QR1,
+       TL_TAIL1, kTlEvents };
 // Phases reported by rid_profile_timeline.
 enum { TLP_INGEST = 0, TLP_LAMBDA = 1, TLP_SCORES = 2, TLP_SELECT = 3, TLP_GRAM = 4, TLP_QR = 5, TLP_COEFF = 6 };
+// A batch step runs in three parts on their own streams; events order them and the host never
+// waits.  The lambda part (tridiagonalization of the sketch Gram, its top-k eigenvalues, lambda
+// and the LDL^T of T + lambda I; it also snapshots ||A_obs||^2) reads only the sketch: batch b's
+// runs on lambda stream b % 2 with scratch copy b % 2, so that consecutive batches' lambda parts
+// overlap.  The select part (ridge scores, uniforms, prune/refill) runs on the select stream:
+// it reads and updates the live selection state of d and writes the step's selection record r
+// (previous and new basis, index lists); ev_scores (may be null) is recorded after the scores,
+// and the select waits for ev_wait_rec (the end of the tail that last read the record).  The
+// tail (basis Gram, Algorithms 4-8, commit) reads only the record (d of launch_batch_tail is
+// the record view): its Gram side (basis Gram, G and its factor, T) runs on stg between ev_fork
+// and ev_gram, beside the sketch side's QRs on st; finish_kernel copies its counts and basis to
+// the reporting state (gmeta, gjcp, gslotp).  Each returns the number of kernels launched (0 on
+// failure).
 int launch_batch_lambda(const Dev& d, int batch, cudaStream_t st);
+int launch_batch_select(const Dev& d, const Dev& r, int count, int64_t n_obs, int batch, cudaStream_t st,
+                        cudaEvent_t ev_scores, cudaEvent_t ev_wait_rec, cudaEvent_t* tl);
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
-                      cudaStream_t st, cudaEvent_t ev_scores, cudaEvent_t ev_select, cudaStream_t stg,
-                      cudaEvent_t ev_fork, cudaEvent_t ev_gram, cudaEvent_t* tl);
+                      cudaStream_t st, cudaStream_t stg, cudaEvent_t ev_fork, cudaEvent_t ev_gram,
+                      int* gmeta, int64_t* gjcp, int* gslotp, cudaEvent_t* tl);
 int launch_reset_state(const Dev& d, cudaStream_t st);
 
 // coop.cu: lambda (Eq. 23) through a tridiagonalization of the sketch Gram (cluster or

@@ -19,6 +19,7 @@ RID_OK, RID_EINVAL, RID_ENOMEM, RID_ECUDA, RID_ESTATE, RID_ENONFINITE, RID_ENOLI
 RID_LAMBDA_STREAMING, RID_LAMBDA_FIXED = 0, 1
 RID_OMEGA_GAUSSIAN, RID_OMEGA_RADEMACHER = 0, 1
 RID_F64, RID_F32 = 0, 1
+RID_REFILL_FIRST, RID_REFILL_PROPORTIONAL = 0, 1
 RID_SKETCH_NATIVE, RID_SKETCH_BF16, RID_SKETCH_BF16X2 = 0, 1, 2
 (RID_STATE_SKETCH, RID_STATE_SKETCH_LEV, RID_STATE_SST, RID_STATE_FRO2, RID_STATE_JC,
  RID_STATE_TAU_OLD, RID_STATE_LAMBDA, RID_STATE_CAND, RID_STATE_BATCHES, RID_STATE_GRAM_SHIFT,
@@ -35,7 +36,7 @@ class rid_config(ctypes.Structure):
         ("ny", ctypes.c_int32), ("nfields", ctypes.c_int32), ("n_max", ctypes.c_int64),
         ("seed", ctypes.c_uint64), ("group_max", ctypes.c_int32), ("defer_device_input", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p), ("right_l", ctypes.c_int32), ("grad_coeff", ctypes.c_int32),
-        ("ingest_ctas", ctypes.c_int32),
+        ("ingest_ctas", ctypes.c_int32), ("refill_mode", ctypes.c_int32), ("lookahead", ctypes.c_int32),
     ]
 
 
@@ -224,7 +225,8 @@ def _device_out(x, dtype, numel, what):
 def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_const=1.0,
                 lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
-                grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False, ingest_ctas=0):
+                grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False, ingest_ctas=0, refill="first",
+                lookahead=0):
     """An rid_config from keyword arguments (the defaults of rid_config_default otherwise)."""
     cfg = rid_config()
     _check(rid_config_default(ctypes.byref(cfg)))
@@ -243,6 +245,8 @@ def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_cons
     cfg.right_l = int(right_l)
     cfg.grad_coeff = 1 if grad_coeff else 0
     cfg.ingest_ctas = int(ingest_ctas)
+    cfg.refill_mode = {"first": RID_REFILL_FIRST, "proportional": RID_REFILL_PROPORTIONAL}[refill]
+    cfg.lookahead = int(lookahead)
     cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return cfg
 
@@ -269,7 +273,7 @@ class OnlineRID:
     def __init__(self, m, k, s, h=0, **kw):
         """Keyword arguments as make_config: c1, c2, eps, delta, c_const, lambda_mode,
         lambda_fixed, omega, dtype, sketch, n_max, seed, stream, group_max, defer, grad_dims,
-        nx, ny, nfields, right_l, grad_coeff, ingest_ctas."""
+        nx, ny, nfields, right_l, grad_coeff, ingest_ctas, refill ("first" or "proportional"), lookahead."""
         cfg = make_config(m, k, s, h, **kw)
         dtype = kw.get("dtype", "f32")
         self.cfg = cfg

@@ -249,6 +249,44 @@ def test_css_update_probabilities():
     assert abs(first[3] / N - q) < 4 * math.sqrt(q * (1 - q) / N)
 
 
+def test_css_update_proportional_refill():
+    """R7p: a refilled slot takes buffered column r with probability tau^D_r / sum tau^D over the
+    columns not already in C (here every refill probability is clipped to 1, the case in which
+    R7 would always take the first column); the refill decision itself is R7's."""
+    cfg = RIDConfig(m=10, k=4, s=7, seed=0, refill="proportional")
+    scale = refill_scale(cfg)
+    JC = np.array([10, -1, 12, 13])                  # slot 1 empty: always refilled
+    tau_old = np.array([0.5, 1.0, 0.5, 0.5])
+    tau_C = np.array([0.5, 1.0, 0.5, 0.5])           # no drops
+    JD = [20, 21, 22, 23]
+    w = np.array([1.0, 2.0, 3.0, 4.0])
+    tau_D = w * (2.0 / scale)                        # p = min(2 w, 1) = 1 for every candidate
+    N = 6000
+    counts = np.zeros(4)
+    for seed in range(N):
+        cfg.seed = seed
+        newJ, newtau = css_update(cfg, 0, JC, tau_old, tau_C, JD, tau_D)
+        r = JD.index(int(newJ[1]))
+        counts[r] += 1
+        assert newtau[1] == tau_D[r]
+        np.testing.assert_array_equal(newJ[[0, 2, 3]], JC[[0, 2, 3]])
+    p = w / w.sum()
+    chi2 = float((((counts - N * p) ** 2) / (N * p)).sum())
+    assert chi2 < 16.3, (counts, chi2)               # chi-square, 3 degrees of freedom, p ~ 0.001
+    # the first-success reading on the same draws always takes the first column
+    cfg.refill = "first"
+    for seed in range(50):
+        cfg.seed = seed
+        assert css_update(cfg, 0, JC, tau_old, tau_C, JD, tau_D)[0][1] == 20
+    # a column already in C is never drawn again: two empty slots receive distinct columns
+    cfg.refill = "proportional"
+    JC2 = np.array([-1, -1, 12, 13])
+    for seed in range(300):
+        cfg.seed = seed
+        newJ = css_update(cfg, 0, JC2, tau_old, tau_C, JD, tau_D)[0]
+        assert newJ[0] != newJ[1] and newJ[0] in JD and newJ[1] in JD
+
+
 def test_refill_scale_formula():
     cfg = RIDConfig(m=10, k=20, s=83, eps=0.5, delta=0.05)
     assert abs(refill_scale(cfg) - (20 * math.log(20) + 20 * math.log(20.0) / 0.5) / 20) < 1e-12

@@ -38,7 +38,8 @@ def run_gpu(A, block=1, host=False, dtype="f64", n_max=1024, **kw):
     g = rid.OnlineRID(m=m, k=kw["k"], s=kw["s"], h=kw.get("h", 0), dtype=dtype,
                       omega=kw.get("omega_kind", "rademacher"), lambda_mode=kw.get("lambda_mode", "streaming"),
                       lambda_fixed=kw.get("lambda_fixed", 0.0), seed=kw.get("seed", 0), n_max=n_max,
-                      c1=kw.get("c1", 1 / 6), c2=kw.get("c2", 1 / 3))
+                      c1=kw.get("c1", 1 / 6), c2=kw.get("c2", 1 / 3), refill=kw.get("refill", "first"),
+                      lookahead=kw.get("lookahead", 0))
     npd = np.float64 if dtype == "f64" else np.float32
     rows = np.ascontiguousarray(A.T.astype(npd))          # row q = column q
     if host:
@@ -102,6 +103,40 @@ def test_config1_streaming_lambda(seed, omega):
     if assert_parity(o, Jo, Po, g, Jg, Pg, A):
         lam_g = g.state(6)[0]
         assert abs(lam_g - o.history[-1].lam) <= 1e-9 * abs(o.history[-1].lam) + 1e-13 * o.fro2
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+@pytest.mark.parametrize("lambda_mode", ["fixed", "streaming"])
+def test_config1_proportional_refill(seed, lambda_mode):
+    """The alternative refill reading (a refilled slot draws its column with probability
+    proportional to the ridge score) on the GPU against the oracle's."""
+    A = config1_matrix(seed)
+    k = 20
+    lam = offline.tail_energy(A, k) / k
+    kw = dict(k=k, s=4 * k + 3, h=30, lambda_mode=lambda_mode, lambda_fixed=lam, seed=seed, refill="proportional")
+    o, Jo, Po = run_oracle(A, **kw)
+    g, Jg, Pg = run_gpu(A, **kw)
+    assert_parity(o, Jo, Po, g, Jg, Pg, A)
+    # the reading changes the selection: the first-success run of the same stream differs
+    o1, J1, _ = run_oracle(A, **{**kw, "refill": "first"})
+    assert not np.array_equal(J1, Jo)
+
+
+@pytest.mark.parametrize("lookahead", [2, 3, 4])
+def test_lookahead_does_not_change_results(lookahead):
+    """How far the ingest runs ahead of the batch steps (and so the pool slots each batch lands
+    in) changes the schedule only: J, P and the estimates are bit-identical to the default's."""
+    A = config1_matrix(5)
+    k = 20
+    kw = dict(k=k, s=83, h=30, seed=5)
+    g0, J0, P0 = run_gpu(A, block=7, **kw)
+    e0 = g0.error_estimate()[0]
+    g, J, P = run_gpu(A, block=7, lookahead=lookahead, **kw)
+    assert np.array_equal(J, J0)
+    assert np.array_equal(P, P0)
+    assert np.array_equal(g.error_estimate()[0], e0)
+    o, Jo, Po = run_oracle(A, **kw)
+    assert_parity(o, Jo, Po, g, J, P, A)
 
 
 def test_last_batch_candidates_match():

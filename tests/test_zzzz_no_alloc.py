@@ -1,5 +1,8 @@
 """rid_sketch_noalloc against the handle's own ingest sketch.
 
+This file is named to be collected after every other test module, so that a run that stops at
+its first failure has run everything else when it reaches these tests.
+
 The allocation-free entry point must give the sketch and squared norms that
 a handle (rid_init + rid_ingest + rid_get_state) records for the same
 columns, within the bars the parity tests use for the sketch: 1e-12 of the
@@ -96,3 +99,43 @@ def test_noalloc_sketch_matches_handle_on_two_calls(dtype):
     assert np.abs(S_na[:, 16:] - S_ref[:, 16:]).max() <= bar
     Xd = np.concatenate([X1.double().cpu().numpy(), X2.double().cpu().numpy()])
     np.testing.assert_allclose(norms, (Xd * Xd).sum(axis=1), rtol=1e-12 if dtype == "f64" else 1e-6)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("m", [1, 255, 257, 40_000])
+@pytest.mark.parametrize("ncols", [1, 16])
+@pytest.mark.parametrize("rows", [256, 257, 512])
+def test_noalloc_edge_sizes_against_exact_sketch(m, ncols, rows):
+    """The short paths of the fixed-scratch sketch: fewer split-K blocks than the maximum (m below
+    32768), a single partial chunk (m < 256), one column, and s + h on both sides of the 256-row
+    boundary of the second row group.  Every output entry is compared with the exact FP64 sketch
+    Omega a (the Rademacher entries of the counter-based generator); the outputs start as NaN, so
+    an entry the kernels never wrote, or a partial sum read before it was written, fails."""
+    import torch
+    from oracle import philox
+    rid = _lib()
+    s = rows - 30
+    h = 30
+    seed = 7 + m + ncols
+    gen = torch.Generator(device="cpu").manual_seed(m * 31 + ncols)
+    X = (torch.rand(ncols, m, generator=gen, dtype=torch.float64) * 2.0 - 1.0).cuda()   # row q = column q
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    cfg = _cfg(rid, m, s, h, seed, "f64", stream.cuda_stream)
+    for call in range(2):                                  # twice: the shared scratch keeps the first call's partials
+        S = torch.full((ncols, rows + 1), float("nan"), dtype=torch.float64, device="cuda")
+        nrm = torch.full((ncols,), float("nan"), dtype=torch.float64, device="cuda")
+        rc = rid.rid_sketch_noalloc(ctypes.byref(cfg), ctypes.c_void_p(X.data_ptr()), m, ncols,
+                                    ctypes.c_void_p(S.data_ptr()), rows + 1, ctypes.c_void_p(nrm.data_ptr()))
+        assert rc == rid.RID_OK, rid.rid_last_error(None)
+        stream.synchronize()
+        A = X.cpu().numpy().T                              # m x ncols
+        Om = philox.omega_block("rademacher", seed, np.arange(rows), 0, m)
+        S_ref = Om @ A
+        S_na = S[:, :rows].cpu().numpy().T
+        assert np.isfinite(S_na).all() and np.isfinite(nrm.cpu().numpy()).all()
+        assert torch.isnan(S[:, rows:]).all().item()
+        assert np.abs(S_na - S_ref).max() <= 1e-12 * max(np.abs(S_ref).max(), 1e-300)
+        np.testing.assert_allclose(nrm.cpu().numpy(), (A * A).sum(axis=0), rtol=1e-12)
+        X = X.flip(1).contiguous() * 0.5                   # other data for the second call
+        torch.cuda.synchronize()
