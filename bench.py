@@ -470,7 +470,8 @@ def run_streams(args, cfg):
 
 
 def run_precision(args, cfg):
-    """Configuration C4: the same seeded streams through FP64, plain FP32, BF16x2 and BF16 sketches.
+    """Configuration C4: the same seeded streams through FP64, plain FP32, BF16x2, BF16 and the
+    block-scaled E4M3 (FP8x2, FP8) sketches.
 
     Every form runs every seed (columns one at a time, fixed lambda); the line reports the relative
     Frobenius error of each form's result and of the oracle's (its cpu_baseline leg), and the
@@ -485,7 +486,8 @@ def run_precision(args, cfg):
     st = torch.cuda.Stream(device=dev)
     Jd = torch.empty(k, dtype=torch.int64, device=dev)
     Pd = torch.empty((n, k), dtype=torch.float64, device=dev)
-    forms = {"f64": ("f64", "native"), "f32": ("f32", "native"), "bf16x2": ("f32", "bf16x2"), "bf16": ("f32", "bf16")}
+    forms = {"f64": ("f64", "native"), "f32": ("f32", "native"), "bf16x2": ("f32", "bf16x2"), "bf16": ("f32", "bf16"),
+             "fp8x2": ("f32", "fp8x2"), "fp8": ("f32", "fp8")}
     res, clk_summary, launches = {}, None, 0
     for name, (dtype, sk) in forms.items():
         errs, ests = [], []
@@ -531,6 +533,8 @@ def run_precision(args, cfg):
                           "est_rel_fro_err_mean": float(np.mean(ests))})
     accuracy = {"forms": res, "err_ratio_bf16x2_vs_f64": res["bf16x2"]["rel_fro_err_mean"] / res["f64"]["rel_fro_err_mean"],
                 "err_ratio_bf16_vs_f64": res["bf16"]["rel_fro_err_mean"] / res["f64"]["rel_fro_err_mean"],
+                "err_ratio_fp8x2_vs_f64": res["fp8x2"]["rel_fro_err_mean"] / res["f64"]["rel_fro_err_mean"],
+                "err_ratio_fp8_vs_f64": res["fp8"]["rel_fro_err_mean"] / res["f64"]["rel_fro_err_mean"],
                 "note": "||A - A_J P||_F / ||A||_F per seed (0..9) for each form; est = the NA-Hutch++ estimate"}
     pk = peaks()
     per_launch = res["bf16x2"]["ingest_ms_per_launch"]
@@ -590,7 +594,7 @@ def main():
     ap.add_argument("--config", default="channel", choices=sorted(CONFIGS))
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sketch", default="bf16x2", choices=["bf16x2", "bf16", "native"])
+    ap.add_argument("--sketch", default="bf16x2", choices=["bf16x2", "bf16", "fp8x2", "fp8", "native"])
     ap.add_argument("--group", type=int, default=64,
                     help="columns per sketch launch (1..64); 0 = measure it and the CTAs per launch "
                          "with rid_autotune on the first 2k snapshots before the timed region")
@@ -796,7 +800,7 @@ def main():
     # (one warm-up and one timed pass each; the plain FP32 form runs on the FP32 pipe)
     forms = {}
     if not grad and args.forms:
-        for form in ("bf16x2", "bf16", "native"):
+        for form in ("bf16x2", "bf16", "fp8x2", "native"):
             if form == args.sketch:
                 continue
             hf = rid.OnlineRID(m=m, k=cfg["k"], s=cfg["s"], h=cfg["h"], dtype="f32", sketch=form, n_max=n,
@@ -853,7 +857,9 @@ def main():
         "metric": "snapshots/s", "value": value, "unit": "snapshots/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16x2": "f32 data, bf16x2 sketch", "bf16": "f32 data, bf16 sketch", "native": "f32"}[args.sketch],
+        "dtype": {"bf16x2": "f32 data, bf16x2 sketch", "bf16": "f32 data, bf16 sketch",
+                  "fp8x2": "f32 data, block-scaled e4m3x2 sketch", "fp8": "f32 data, block-scaled e4m3 sketch",
+                  "native": "f32"}[args.sketch],
         "data": "synthetic",
         "config": {"workload": cfg["workload"], "m": m, "n": n, "block": b, "k": cfg["k"], "s": cfg["s"],
                    "h": cfg["h"], "omega": "rademacher", "lambda": "streaming", "sketch": args.sketch,
@@ -865,7 +871,8 @@ def main():
         "gpu_launches": int(prof_kern.sum()),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                      "frac": achieved / pk.get("hbm_gbs"), "traffic": traffic,
-                     "kernel": "tc_ingest_kernel" if args.sketch != "native" else "ingest_sketch_kernel",
+                     "kernel": {"native": "ingest_sketch_kernel", "fp8x2": "tc_ingest_fp8_kernel",
+                                "fp8": "tc_ingest_fp8_kernel"}.get(args.sketch, "tc_ingest_kernel"),
                      "avg_launch_ms": avg_ms, "cols_per_launch": cols_per_launch,
                      "isolated": {"cols_per_launch": G, "avg_launch_ms": iso_ms,
                                   "achieved": 2.0 * G * m * 4 / (iso_ms / 1e3) / 1e9,

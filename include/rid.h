@@ -69,7 +69,12 @@ enum rid_refill_mode {
 enum rid_sketch_prec {
   RID_SKETCH_NATIVE = 0,     /* sketch accumulated in the data type (FP64 or FP32) */
   RID_SKETCH_BF16 = 1,       /* data rounded to BF16, tensor cores, FP32 accumulation */
-  RID_SKETCH_BF16X2 = 2      /* data split hi+lo in BF16, tensor cores, FP32 accumulation */
+  RID_SKETCH_BF16X2 = 2,     /* data split hi+lo in BF16, tensor cores, FP32 accumulation */
+  RID_SKETCH_FP8 = 3,        /* data in E4M3 with one power-of-two scale per 32 coordinates of a
+                                column (the smallest with no element above 448), tensor cores
+                                (block-scaled MMA), FP32 accumulation */
+  RID_SKETCH_FP8X2 = 4       /* two block-scaled E4M3 terms: a ~ hi + lo, lo quantizing the
+                                residual a - hi with its own block scales */
 };
 
 typedef struct rid_config {

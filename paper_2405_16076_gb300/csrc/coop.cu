@@ -340,24 +340,25 @@ __device__ int sturm_count_minors(const double* ds, const double* e2s, int n, do
 // One warp per requested eigenvalue index j (ascending order): 32-point multisection of the
 // Sturm count until the bracket reaches the count's resolution eps * ||T||.  (A warp issues
 // about one FP64 instruction per 64 cycles on this GPU, dependent or not, so more shifts per
-// lane only add time.)
-__global__ void __launch_bounds__(32) topk_eig_kernel(Dev d, const double* dvec, const double* evec, int k,
-                                                      double* mu) {
+// lane only add time.)  A CTA holds kTopkWarps warps -- one per SM sub-partition, each with its
+// own FP64 pipe -- that share one staged copy of the scaled tridiagonal, so that the kernel
+// occupies few SMs beside the ingest running on the others.
+constexpr int kTopkWarps = 4;
+
+__global__ void __launch_bounds__(32 * kTopkWarps) topk_eig_kernel(Dev d, const double* dvec, const double* evec,
+                                                                   int k, double* mu) {
   extern __shared__ double tsm[];
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x;
+  __shared__ double red[2][kTopkWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kTopkWarps + wid;
   const int n = d.s;
-  if (gw >= k || gw >= n) return;
-  const int j = n - 1 - gw;                    // the gw-th largest
   double* ds = tsm;
   double* e2s = tsm + n;
-  // Gershgorin interval, lane-parallel
+  // Gershgorin interval, CTA-parallel
   double lo = 1e300, hi = -1e300;
-  for (int i = lane; i < n; i += 32) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double di = dvec[i];
     const double r = ((i > 0) ? fabs(evec[i - 1]) : 0.0) + ((i + 1 < n) ? fabs(evec[i]) : 0.0);
-    ds[i] = di;
-    if (i + 1 < n) e2s[i] = evec[i];
     lo = fmin(lo, di - r);
     hi = fmax(hi, di + r);
   }
@@ -365,14 +366,20 @@ __global__ void __launch_bounds__(32) topk_eig_kernel(Dev d, const double* dvec,
     lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
+  if (lane == 0) { red[0][wid] = lo; red[1][wid] = hi; }
+  __syncthreads();
+  lo = red[0][0];
+  hi = red[1][0];
+  for (int w = 1; w < kTopkWarps; ++w) { lo = fmin(lo, red[0][w]); hi = fmax(hi, red[1][w]); }
   const double sc = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
   const double inv = 1.0 / sc;
-  __syncwarp();
-  for (int i = lane; i < n; i += 32) {
-    ds[i] *= inv;
-    if (i + 1 < n) { const double e = e2s[i] * inv; e2s[i] = e * e; }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    ds[i] = dvec[i] * inv;
+    if (i + 1 < n) { const double e = evec[i] * inv; e2s[i] = e * e; }
   }
-  __syncwarp();
+  __syncthreads();
+  if (gw >= k || gw >= n) return;             // after the last CTA-wide barrier
+  const int j = n - 1 - gw;                    // the gw-th largest
   const double tol = 4.440892098500626e-16;    // in units of sc
   lo = lo * inv - 2.0 * tol;
   hi = hi * inv + 2.0 * tol;
@@ -705,7 +712,8 @@ int launch_lambda(const Dev& d, int batch, double* work_base, int64_t off_A, int
   int nk = 2;
   const int k = d.t;
   if (d.lambda_mode == 0) {
-    topk_eig_kernel<<<k, 32, (size_t)2 * d.s * sizeof(double), st>>>(d, dv, ev, k, mu);   // FP64-bound
+    topk_eig_kernel<<<(k + kTopkWarps - 1) / kTopkWarps, 32 * kTopkWarps, (size_t)2 * d.s * sizeof(double), st>>>(
+        d, dv, ev, k, mu);                                                           // FP64-bound
     ++nk;
   }
   lambda_ldl_kernel<<<1, 32, (size_t)(2 * d.s + (k < d.s ? k : d.s)) * sizeof(double), st>>>(

@@ -427,11 +427,12 @@ int flush(rid_handle* h) {
   if (h->prof) for (auto& e : ev) e = next_event(h);
   int nk0 = 0, nk1 = 0;
   if (h->tc) {
-    const int split = h->cfg.sketch_prec == RID_SKETCH_BF16X2 ? 1 : 0;
+    const int split = (h->cfg.sketch_prec == RID_SKETCH_BF16X2 || h->cfg.sketch_prec == RID_SKETCH_FP8X2) ? 1 : 0;
+    const int fp8 = (h->cfg.sketch_prec == RID_SKETCH_FP8 || h->cfg.sketch_prec == RID_SKETCH_FP8X2) ? 1 : 0;
     // no batch step can run beside the first batch's ingest: it takes the whole grid
     const int nblk = h->batch >= 1 ? h->ingest_blocks : h->first_blocks;
     if (rid::launch_tc_ingest(db, h->pend.data(), G, split, h->count, h->n_obs, nblk,
-                              h->tc_part, h->tc_npart, h->st, h->prof ? ev : nullptr) != 0)
+                              h->tc_part, h->tc_npart, h->st, h->prof ? ev : nullptr, fp8) != 0)
       return fail(h, RID_ECUDA, "tensor-core ingest launch failed");
     rid::launch_gram_update(db, G, h->n_obs, h->st);
     nk0 = 1;
@@ -489,11 +490,13 @@ int check_config(const rid_config* c) {
     return fail(h, RID_EINVAL, "unknown omega_kind");
   if (c->data_dtype != RID_F64 && c->data_dtype != RID_F32) return fail(h, RID_EINVAL, "unknown data_dtype");
   if (c->sketch_prec != RID_SKETCH_NATIVE && c->sketch_prec != RID_SKETCH_BF16 &&
-      c->sketch_prec != RID_SKETCH_BF16X2)
+      c->sketch_prec != RID_SKETCH_BF16X2 && c->sketch_prec != RID_SKETCH_FP8 && c->sketch_prec != RID_SKETCH_FP8X2)
     return fail(h, RID_EINVAL, "unknown sketch_prec");
+  if ((c->sketch_prec == RID_SKETCH_FP8 || c->sketch_prec == RID_SKETCH_FP8X2) && c->s + c->h > 480)
+    return fail(h, RID_EINVAL, "FP8 sketches support s + h <= 480 (TMEM holds the block scales beside the sums)");
   if (c->sketch_prec != RID_SKETCH_NATIVE) {
-    if (c->data_dtype != RID_F32) return fail(h, RID_EINVAL, "BF16 sketches need FP32 data");
-    if (c->omega_kind != RID_OMEGA_RADEMACHER) return fail(h, RID_EINVAL, "BF16 sketches need a Rademacher Omega");
+    if (c->data_dtype != RID_F32) return fail(h, RID_EINVAL, "tensor-core sketches need FP32 data");
+    if (c->omega_kind != RID_OMEGA_RADEMACHER) return fail(h, RID_EINVAL, "tensor-core sketches need a Rademacher Omega");
     if (c->s + c->h > 512) return fail(h, RID_EINVAL, "BF16 sketches support s + h <= 512");
   }
   if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
@@ -590,6 +593,10 @@ int rid_init(rid_handle** out, const rid_config* c) {
   const double k = (double)c->k;
   d.refill_scale = c->c_const * (k * log(k) + k * log(1.0 / c->delta) / c->eps) / (double)c->k;
   d.refill_mode = c->refill_mode;
+  {
+    const uint32_t wl = rid::parse_wait_inject(getenv("RID_FAULT_INJECT"));
+    d.ring_wait_limit = wl ? wl : rid::kRingWaitLimit;
+  }
   d.la = c->lookahead > 0 ? c->lookahead : 3;
   d.seed = c->seed;
   d.grad = c->grad_dims != 0 ? 1 : 0;
@@ -616,7 +623,9 @@ int rid_init(rid_handle** out, const rid_config* c) {
     d.sk_rel = 1e-6;
     d.gram_rho0 = 1e-6;
   } else {                                  // tensor cores; the Gram always takes the BF16x2 split
-    d.sk_rel = c->sketch_prec == RID_SKETCH_BF16X2 ? 2e-5 : 4e-3;
+    // relative accuracy of a sketch entry: BF16x2 ~2^-16, BF16 and E4M3x2 ~2^-8, E4M3 ~2^-4
+    d.sk_rel = c->sketch_prec == RID_SKETCH_BF16X2 ? 2e-5
+             : c->sketch_prec == RID_SKETCH_FP8 ? 6e-2 : 4e-3;
     d.gram_rho0 = 3e-5;
   }
   h->group_max = c->group_max > 0 ? c->group_max : (h->tc ? rid::kMaxGroup : rid::kMaxB);

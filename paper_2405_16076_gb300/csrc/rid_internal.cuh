@@ -37,6 +37,7 @@ struct Dev {
   double lambda_fixed;
   double refill_scale;            // c (k ln k + k ln(1/delta)/eps) / t
   int refill_mode;                // 0 first success (R7), 1 proportional draw (R7p)
+  uint32_t ring_wait_limit;       // polls of a tensor-core pipeline wait before it gives up
   uint64_t seed;
   int grad;                       // gradient mode
   int nx, ny, nfields;
@@ -124,6 +125,7 @@ inline __host__ __device__ int64_t hpart_stride(int64_t hh, int64_t t) { return 
 enum { ERR_NONFINITE = 1, ERR_CHOL = 2, ERR_EIG = 4, ERR_TIMEOUT = 8 };
 
 constexpr int kMaxGroup = 64;      // columns per tensor-core ingest launch
+constexpr uint32_t kRingWaitLimit = 1u << 22;   // default polls of a tensor-core pipeline wait
 
 // ingest.cu: SIMT path (FP64 or FP32, native precision), nb <= kMaxB columns given by
 // pointer.  Returns the number of kernels launched; ev[0..2] (may be null) are recorded
@@ -173,7 +175,7 @@ void launch_gram_update(const Dev& d, int nb, int64_t n_obs, cudaStream_t st);
 // around the sketch kernel and launches the reduction.  Returns 0 on success.
 int launch_tc_ingest(const Dev& d, const void* const* cols, int ncols, int split, int count,
                      int64_t n_obs, int nblk, float* part, double* npart, cudaStream_t st,
-                     cudaEvent_t* ev);
+                     cudaEvent_t* ev, int fp8);
 int tc_smem_bytes();
 // Basis Gram of the new x target pool slots on tensor cores (FP32 pool); returns the
 // number of kernels launched, or -1.  part holds nblk x 512 x 128 floats.

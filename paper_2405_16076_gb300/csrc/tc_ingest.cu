@@ -21,6 +21,8 @@
 // then read the accumulators back.  Two SMEM stages, mbarrier hand-off, every
 // wait bounded (on timeout: error flag, drain, free TMEM, return).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -63,11 +65,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after kWaitLimit polls (or when another role gave up),
-// raising the CTA abort flag and the device error word.
+// Bounded wait: gives up after `limit` polls (or when another role gave up), raising the CTA
+// abort flag and the device error word.  Pipeline waits take the handle's limit (d.ring_wait_limit,
+// kRingWaitLimit unless a test shortened it); the final wait for the MMAs in flight always takes
+// kWaitLimit, so that TMEM is freed only once they have completed.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+                                          int* err, uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
     if (it > 32) __nanosleep(128);
@@ -229,7 +233,7 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
       int st = 0;
       uint32_t par = 0;
       for (int64_t c = 0; c < nch; ++c) {
-        if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err)) break;
+        if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err, d.ring_wait_limit)) break;
         tc_fence_after();
         const uint64_t da = desc_sw128(sA + st * kATile);
         const uint64_t db1 = desc_sw128(sB + st * btile);
@@ -289,7 +293,7 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
     uint32_t ppar = 1u;                       // first pass over the ring: stages start empty
     auto process = [&](int64_t c, const float4 (&v)[2]) -> bool {
       const int st = pst;
-      if (!mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err)) return false;
+      if (!mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err, d.ring_wait_limit)) return false;
       if (++pst == nstage) { pst = 0; ppar ^= 1u; }
       const int64_t cg = c0 + c;
       const uint32_t ast = sA + st * kATile;
@@ -496,7 +500,7 @@ tc_gram_kernel(Dev d, int x0, int y0, int64_t chunks_per_cta, float* __restrict_
       const uint32_t id = idesc_bf16(128, kGramN);
       for (int64_t c = 0; c < nch; ++c) {
         const int st = (int)(c & 1);
-        if (!mbar_wait(bar_full0 + 8 * st, (uint32_t)((c >> 1) & 1), abort_flag, d.err)) break;
+        if (!mbar_wait(bar_full0 + 8 * st, (uint32_t)((c >> 1) & 1), abort_flag, d.err, d.ring_wait_limit)) break;
         tc_fence_after();
         const uint64_t da = desc_sw128(sA + st * kATile);
         const uint64_t db = desc_sw128(sB + st * kBTile);
@@ -543,7 +547,7 @@ tc_gram_kernel(Dev d, int x0, int y0, int64_t chunks_per_cta, float* __restrict_
     };
     auto process = [&](int64_t c, const float4 (&va)[4], const float4 (&vb0)[4], const float4 (&vb1)[4]) -> bool {
       const int st = (int)(c & 1);
-      if (!mbar_wait(bar_empty0 + 8 * st, (uint32_t)(((c >> 1) & 1) ^ 1), abort_flag, d.err)) return false;
+      if (!mbar_wait(bar_empty0 + 8 * st, (uint32_t)(((c >> 1) & 1) ^ 1), abort_flag, d.err, d.ring_wait_limit)) return false;
       const uint32_t ast = sA + st * kATile, bst = sB + st * kBTile;
       if (hasA) put(ast, qa, 64 + qa, va);
       if (hasB0) put(bst, qb0, 128 + qb0, vb0);
@@ -684,7 +688,7 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
       int st = 0;
       uint32_t par = 0;
       for (int64_t c = 0; c < nch; ++c) {
-        if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err)) break;
+        if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err, d.ring_wait_limit)) break;
         tc_fence_after();
         const uint32_t bst = sB + st * btile;
         const uint64_t db1 = desc_sw128(bst);
@@ -735,7 +739,7 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
     uint32_t ppar = 1u;
     auto process = [&](const float4 (&v)[4][2]) -> bool {
       const int st = pst;
-      if (!mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err)) return false;
+      if (!mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err, d.ring_wait_limit)) return false;
       if (++pst == nstage) { pst = 0; ppar ^= 1u; }
       const uint32_t bst = sB + st * btile;
 #pragma unroll
@@ -885,17 +889,357 @@ int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st) {
 
 int tc_smem_bytes() { return kSmemBytes; }
 
+// ---------------------------------------------------------------- FP8 (E4M3, block-scaled) ingest
+// The same sketch S(:, q) = Omega a_q with the data quantized to E4M3 with one power-of-two scale
+// per 32 consecutive coordinates of a column (the microscaling layout: UE8M0 exponents), as one
+// term (hi) or two (hi + lo, lo quantizing the residual a - hi with its own block scales).
+// Omega's +-1 entries are exact in E4M3.  MMA: tcgen05.mma kind::mxf8f6f4 with block scaling
+// (scale_vec::1X: one scale per row and 32-element K step), A = the 128 data rows (hi rows
+// 0..63, lo rows 64..127), B = the Omega rows, FP32 accumulation in TMEM.
+// A chunk is 128 coordinates (one 128-byte E4M3 row, four K steps of 32).  The A scales of a
+// chunk live in TMEM: row m's four exponent bytes (one per K step, selected by the
+// instruction's scale-factor id) at lane m, column sfa + m / 32 -- each lane quarter's 32 rows in
+// its own column.  Four scale-writer warps (one per lane quarter, no other work) copy them from
+// the producers' shared-memory staging into TMEM once every producer has staged its column's
+// scales (an mbarrier, so that every wait stays bounded), then release the stage to the MMA;
+// the producers never wait for them, so the ring keeps its overlap.  The B scales are 1.0
+// everywhere, written once.
+constexpr int kChunk8 = 128;                // coordinates per chunk
+constexpr int kSfbCol = 504;                // TMEM columns 504..511: B scales (all 1.0)
+constexpr int kSfaCol0 = 488;               // TMEM columns 488 + 4 st .. + 3: A scales of ring stage st
+constexpr int kMaxStages8 = 3;
+constexpr int kScaleBytes = 128 * 4;        // staged A scale words of one stage
+constexpr int kWriterWarps = 4;             // warps 17..20: the A scales into TMEM
+constexpr int kThreads8 = 32 * (1 + kProducerWarps + kWriterWarps);
+
+__device__ __forceinline__ void tc_st32x1(uint32_t taddr, uint32_t v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma_mx8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t sfa, uint32_t sfb, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accum)
+      : "memory");
+}
+// Instruction descriptor, kind::mxf8f6f4 with block scaling: A and B E4M3 (format 0), K-major,
+// UE8M0 scales (bit 23), N >> 3 at bit 17, M >> 4 at bit 24, scale-factor ids of A (bits 29-30)
+// and B (bits 4-5).
+__host__ __device__ constexpr uint32_t idesc_mx8(int M, int N, int a_sf_id) {
+  return ((uint32_t)(N >> 3) << 17) | (1u << 23) | ((uint32_t)(M >> 4) << 24) | ((uint32_t)a_sf_id << 29);
+}
+// Block exponent X of a 32-coordinate block: the smallest 2^X with amax / 2^X <= 448 (E4M3's
+// largest finite value), 0 for an all-zero block; clamped to [-127, 126] (UE8M0's range; only
+// blocks below 2^-118 in magnitude reach the lower clamp).  amax = (1 + f) 2^e with f the
+// fraction: amax / 448 = (1 + f) / 1.75 * 2^(e - 8), at most 2^(e - 8) iff 1 + f <= 1.75.
+__device__ __forceinline__ int e4m3_block_exp(float amax) {
+  const uint32_t b = __float_as_uint(amax);
+  const int ef = (int)((b >> 23) & 0xFFu);
+  if (!(amax > 0.f)) return 0;
+  int x;
+  if (ef == 0) {
+    x = -127;                                    // subnormal amax: below every representable scale
+  } else {
+    x = ef - 127 - 8 + (((b & 0x7FFFFFu) > 0x600000u) ? 1 : 0);
+  }
+  return x < -127 ? -127 : (x > 126 ? 126 : x);
+}
+// 2^X as a float, X in [-127, 126] (2^-127 is subnormal).
+__device__ __forceinline__ float pow2f(int x) {
+  return x >= -126 ? __uint_as_float((uint32_t)(x + 127) << 23) : __uint_as_float(0x00400000u);
+}
+// Quantize 16 values to E4M3 at scale 2^X (round to nearest even, satfinite): 16 bytes in
+// coordinate order, and the quantized values scaled back (exact in FP32).
+__device__ __forceinline__ void e4m3_quant16(const float (&x)[16], int X, uint32_t (&w)[4], float (&back)[16]) {
+  const float inv = pow2f(-X), sc = pow2f(X);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const __nv_fp8x2_storage_t p =
+        __nv_cvt_float2_to_fp8x2(make_float2(x[2 * j] * inv, x[2 * j + 1] * inv), __NV_SATFINITE, __NV_E4M3);
+    const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(p, __NV_E4M3);
+    __half_raw h0, h1;
+    h0.x = hr.x;
+    h1.x = hr.y;
+    back[2 * j] = __half2float(__half(h0)) * sc;
+    back[2 * j + 1] = __half2float(__half(h1)) * sc;
+    const uint32_t pv = (uint32_t)p;
+    if (j & 1) w[j >> 1] |= pv << 16; else w[j >> 1] = pv;
+  }
+}
+// Four E4M3 +-1 Omega entries (coordinates 4j .. 4j+3 of a 32-coordinate word of the counter-based
+// bits): coordinate e takes bit 15 - e/2 (even e) or 31 - e/2 (odd e), set = -1; after a shift by
+// 2j the four bits sit at 15, 31, 14, 30 and a byte permutation puts them at the sign bits.
+__device__ __forceinline__ uint32_t omega_e4m3x4(uint32_t w, int j) {
+  const uint32_t x = w << (2 * j);
+  const uint32_t y = x & 0x80008000u;
+  const uint32_t z = (x << 1) & 0x80008000u;
+  return __byte_perm(y, z, 0x7531) | 0x38383838u;
+}
+
+__global__ void __launch_bounds__(kThreads8, 1)
+tc_ingest_fp8_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16, int n1, int n2,
+                     int64_t chunks_per_cta, int vec, float* __restrict__ part, double* __restrict__ npart,
+                     int nstage, uint32_t btile) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  // ring stage st: A tile (16 KB) at sA + st * kATile, B tile at sB + st * btile, staged A
+  // scale words at sS + st * kScaleBytes
+  const uint32_t sA = base;
+  const uint32_t sB = base + (uint32_t)nstage * kATile;
+  const uint32_t sS = sB + (uint32_t)nstage * btile;
+  uint32_t* scale_stage = reinterpret_cast<uint32_t*>(gbase + (sS - base));
+  const uint32_t sBar = sS + (uint32_t)nstage * kScaleBytes;   // full[4], empty[4], done, ready[4]
+  uint8_t* gbar = gbase + (sBar - base);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 112);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 120);
+  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 32, bar_done = sBar + 64, bar_ready0 = sBar + 72;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nchunks = (d.m + kChunk8 - 1) / kChunk8;
+  const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
+  int64_t c1 = c0 + chunks_per_cta;
+  if (c1 > nchunks) c1 = nchunks;
+  const int64_t nch = c1 > c0 ? c1 - c0 : 0;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nstage; ++i) {
+      mbar_init(bar_full0 + 8 * i, 32 * (kProducerWarps + kWriterWarps));
+      mbar_init(bar_empty0 + 8 * i, 1);
+      mbar_init(bar_ready0 + 8 * i, 32 * kProducerWarps);
+    }
+    mbar_init(bar_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // the scale writers: warps 17..20 cover the lane quarters 1, 2, 3, 0
+  const bool writer = warp > kProducerWarps;
+  const int quarter = warp & 3;
+  if (writer) {
+    const uint32_t lq = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) tc_st32x1(lq + (uint32_t)(kSfbCol + cc), 0x7F7F7F7Fu);   // 2^0
+    tc_wait_st();
+    tc_fence_before();
+  }
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      int st = 0;
+      uint32_t par = 0;
+      for (int64_t c = 0; c < nch; ++c) {
+        if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err, d.ring_wait_limit)) break;
+        tc_fence_after();
+        const uint64_t da = desc_sw128(sA + st * kATile);
+        const uint64_t db1 = desc_sw128(sB + st * btile);
+        const uint64_t db2 = desc_sw128(sB + st * btile + 256 * 128);
+        const uint32_t sfa = tmem + (uint32_t)(kSfaCol0 + 4 * st);
+        const uint32_t sfb = tmem + (uint32_t)kSfbCol;
+#pragma unroll
+        for (int kk = 0; kk < kChunk8 / 32; ++kk) {
+          const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t adv = (uint64_t)(kk * 2);            // +32 bytes along K
+          tc_mma_mx8(tmem, da + adv, db1 + adv, idesc_mx8(128, n1, kk), sfa, sfb, acc);
+          if (n2 > 0) tc_mma_mx8(tmem + (uint32_t)n1, da + adv, db2 + adv, idesc_mx8(128, n2, kk), sfa, sfb, acc);
+        }
+        tc_commit(bar_empty0 + 8 * st);
+        if (++st == nstage) { st = 0; par ^= 1u; }
+      }
+      tc_commit(bar_done);
+    }
+    __syncwarp();
+  } else if (writer) {
+    // ---------------------------------------------------------------- A scales into TMEM
+    int st = 0;
+    uint32_t par = 0;
+    const uint32_t lq = tmem + ((uint32_t)(32 * quarter) << 16);
+    for (int64_t c = 0; c < nch; ++c) {
+      if (!__all_sync(0xffffffffu, mbar_wait(bar_ready0 + 8 * st, par, abort_flag, d.err, d.ring_wait_limit))) break;
+      const uint32_t v = scale_stage[(size_t)st * 128 + 32 * quarter + lane];
+      tc_st32x1(lq + (uint32_t)(kSfaCol0 + 4 * st + quarter), v);
+      tc_wait_st();
+      tc_fence_before();
+      mbar_arrive(bar_full0 + 8 * st);
+      if (++st == nstage) { st = 0; par ^= 1u; }
+    }
+  } else {
+    // ---------------------------------------------------------------- producers
+    // thread pt moves coordinates 16g .. 16g+15 of every chunk of column q = pt / 8 (g = pt % 8:
+    // one 16-byte E4M3 unit of the 128-byte A row; 32-coordinate block g / 2 shared with the
+    // neighbouring lane) and expands Omega row pt (one counter-based call per chunk).
+    const int pt = threadIdx.x - 32;
+    const int q = pt >> 3, g = pt & 7;
+    const bool has_col = q < ncols;
+    const float* src = has_col ? cols.p[q] : nullptr;
+    float* dstp = has_col ? (float*)d.pool + (int64_t)d.dslot[count + q] * d.m_pad : nullptr;
+    const int r0 = pt;
+    const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
+    float ks = 0.f, kc = 0.f;
+    float bufA[16], bufB[16];
+    auto load_chunk = [&](int64_t c, float (&v)[16]) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      if (has_col && c < nch) {
+        const int64_t i = (c0 + c) * kChunk8 + 16 * g;
+        if (vec && i + 16 <= d.m) {
+          const float4* s4 = reinterpret_cast<const float4*>(src + i);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 t = __ldcs(s4 + j);
+            v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = (i + j < d.m) ? src[i + j] : 0.f;
+        }
+      }
+      if (has_col && g == 0 && vec && c + kL2Ahead < nch && (c0 + c + kL2Ahead + 1) * kChunk8 <= d.m)
+        prefetch_l2(src + (c0 + c + kL2Ahead) * kChunk8, kChunk8 * 4);
+    };
+    int pst = 0;
+    uint32_t ppar = 1u;                       // first pass over the ring: stages start empty
+    auto process = [&](int64_t c, const float (&x)[16]) -> bool {
+      const int st = pst;
+      // warp-uniform outcome of the bounded wait: the shuffles below need every lane
+      if (!__all_sync(0xffffffffu, mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err, d.ring_wait_limit))) return false;
+      const int64_t cg = c0 + c;
+      const uint32_t ast = sA + st * kATile;
+      if (has_col) {
+        const int64_t i0 = cg * kChunk8 + 16 * g;
+        if (i0 + 16 <= d.m && vec) {
+          float4* o = reinterpret_cast<float4*>(dstp + i0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) __stcs(o + j, make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]));
+        } else {
+          for (int j = 0; j < 16; ++j) if (i0 + j < d.m) dstp[i0 + j] = x[j];
+        }
+        float s2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) s2 = fmaf(x[j], x[j], s2);
+        const float y = s2 - kc;
+        const float tsum = ks + y;
+        kc = (tsum - ks) - y;
+        ks = tsum;
+      }
+      // block scales and E4M3 terms (every lane takes part in the shuffles; rows of absent
+      // columns are not stored)
+      float am = 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) am = fmaxf(am, fabsf(x[j]));
+      am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 1));
+      const int Xh = e4m3_block_exp(am);
+      uint32_t wh[4], wl[4];
+      float back[16];
+      e4m3_quant16(x, Xh, wh, back);
+      float rres[16];
+      float amr = 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) { rres[j] = x[j] - back[j]; amr = fmaxf(amr, fabsf(rres[j])); }
+      amr = fmaxf(amr, __shfl_xor_sync(0xffffffffu, amr, 1));
+      const int Xl = e4m3_block_exp(amr);
+      e4m3_quant16(rres, Xl, wl, back);
+      // the four block exponents of the column's row, one byte per K step, gathered over its 8 lanes
+      uint32_t sh = (uint32_t)(Xh + 127) << (8 * (g >> 1));
+      uint32_t sl = split ? (uint32_t)(Xl + 127) << (8 * (g >> 1)) : 0x7Fu << (8 * (g >> 1));
+      sh |= __shfl_xor_sync(0xffffffffu, sh, 2);
+      sh |= __shfl_xor_sync(0xffffffffu, sh, 4);
+      sl |= __shfl_xor_sync(0xffffffffu, sl, 2);
+      sl |= __shfl_xor_sync(0xffffffffu, sl, 4);
+      uint32_t* ss = scale_stage + (size_t)st * 128;
+      if (g == 0) { ss[q] = has_col ? sh : 0x7F7F7F7Fu; ss[64 + q] = has_col ? sl : 0x7F7F7F7Fu; }
+      if (has_col) {
+        sts128(ast + sw128_off(q, g), wh[0], wh[1], wh[2], wh[3]);
+        if (split) sts128(ast + sw128_off(64 + q, g), wl[0], wl[1], wl[2], wl[3]);
+      }
+      if (r0 < nrows16) {
+        const uint32_t bst = sB + st * btile;
+        const u32x4 w = philox4x32_10((uint32_t)cg, (uint32_t)r0, kTagRademacher, 0, k0, k1);
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t ww = words[u >> 1];
+          const int j0 = 4 * (u & 1);             // 4-coordinate groups 4 j0 .. of the 32-bit word
+          sts128(bst + sw128_off(r0, u), omega_e4m3x4(ww, j0), omega_e4m3x4(ww, j0 + 1), omega_e4m3x4(ww, j0 + 2),
+                 omega_e4m3x4(ww, j0 + 3));
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(bar_ready0 + 8 * st);
+      mbar_arrive(bar_full0 + 8 * st);
+      if (++pst == nstage) { pst = 0; ppar ^= 1u; }
+      return true;
+    };
+    load_chunk(0, bufA);
+    load_chunk(1, bufB);
+    for (int64_t c = 0; c < nch; c += 2) {
+      if (!process(c, bufA)) break;
+      load_chunk(c + 2, bufA);
+      if (c + 1 < nch) {
+        if (!process(c + 1, bufB)) break;
+        load_chunk(c + 3, bufB);
+      }
+    }
+    double nrm = (double)ks - (double)kc;
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, 1);
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, 2);
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, 4);
+    if (has_col && g == 0) npart[(size_t)blockIdx.x * 128 + q] = nrm;
+
+    // ---------------------------------------------------------------- epilogue (warps 1..4)
+    if (warp <= 4) {
+      const bool ok = mbar_wait(bar_done, 0, abort_flag, d.err);
+      tc_fence_after();
+      if (ok && !*abort_flag) {
+        const int qtr = warp & 3;
+        const int L = 32 * qtr + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * qtr) << 16);
+        for (int cb = 0; cb < nrows16; cb += 32) {
+          uint32_t r[32];
+          tc_ld32(taddr + (uint32_t)cb, r);
+          tc_wait_ld();
+          float* o = part + ((size_t)blockIdx.x * nrows16 + cb) * 128 + L;
+          const int jn = (nrows16 - cb < 32) ? nrows16 - cb : 32;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < jn) o[(size_t)j * 128] = (nch > 0) ? __uint_as_float(r[j]) : 0.f;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 // Launch the tensor-core sketch of ncols columns; returns 0 on success.
 int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split, int count,
                      int64_t n_obs, int nblk, float* part, double* npart, cudaStream_t st,
-                     cudaEvent_t* ev) {
+                     cudaEvent_t* ev, int fp8) {
   static int max_smem = 0;
   if (max_smem == 0) {
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       return -1;
-    if (cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, v) != cudaSuccess)
+    if (cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, v) != cudaSuccess ||
+        cudaFuncSetAttribute(tc_ingest_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, v) != cudaSuccess)
       return -1;
     max_smem = v;
   }
@@ -908,6 +1252,25 @@ int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split
   const int nrows16 = (d.rows + 15) / 16 * 16;
   const int n1 = nrows16 < 256 ? nrows16 : 256;
   const int n2 = nrows16 - n1;
+  if (fp8) {
+    // E4M3 with block scales: 128-coordinate chunks, the A scales beside each stage, the
+    // accumulator below the scale columns of TMEM
+    if (nrows16 > kSfaCol0) return -1;
+    const int64_t nch8 = (d.m + kChunk8 - 1) / kChunk8;
+    const int64_t per8 = (nch8 + nblk - 1) / nblk;
+    const uint32_t btile8 = (uint32_t)nrows16 * 128u;
+    const int stage8 = kATile + (int)btile8 + kScaleBytes;
+    int ns8 = (max_smem - 1024 - 128) / stage8;
+    if (ns8 > kMaxStages8) ns8 = kMaxStages8;
+    if (ns8 < 2) return -1;
+    const size_t smem8 = 1024 + 128 + (size_t)ns8 * stage8;
+    if (ev) cudaEventRecord(ev[0], st);
+    tc_ingest_fp8_kernel<<<nblk, kThreads8, smem8, st>>>(d, c, ncols, split, count, nrows16, n1, n2, per8,
+                                                        vec ? 1 : 0, part, npart, ns8, btile8);
+    if (ev) cudaEventRecord(ev[1], st);
+    tc_reduce_kernel<<<d.rows + 1, 256, 0, st>>>(d, part, npart, nblk, ncols, split, nrows16, n_obs);
+    return 0;
+  }
   const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
   int64_t per = (nchunks + nblk - 1) / nblk;
   per = (per + 1) / 2 * 2;                      // even: Philox words are shared by chunk pairs

@@ -20,7 +20,7 @@ RID_LAMBDA_STREAMING, RID_LAMBDA_FIXED = 0, 1
 RID_OMEGA_GAUSSIAN, RID_OMEGA_RADEMACHER = 0, 1
 RID_F64, RID_F32 = 0, 1
 RID_REFILL_FIRST, RID_REFILL_PROPORTIONAL = 0, 1
-RID_SKETCH_NATIVE, RID_SKETCH_BF16, RID_SKETCH_BF16X2 = 0, 1, 2
+RID_SKETCH_NATIVE, RID_SKETCH_BF16, RID_SKETCH_BF16X2, RID_SKETCH_FP8, RID_SKETCH_FP8X2 = 0, 1, 2, 3, 4
 (RID_STATE_SKETCH, RID_STATE_SKETCH_LEV, RID_STATE_SST, RID_STATE_FRO2, RID_STATE_JC,
  RID_STATE_TAU_OLD, RID_STATE_LAMBDA, RID_STATE_CAND, RID_STATE_BATCHES, RID_STATE_GRAM_SHIFT,
  RID_STATE_GRAD_SKETCH) = range(11)
@@ -236,7 +236,8 @@ def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_cons
     cfg.lambda_fixed = float(lambda_fixed)
     cfg.omega_kind = RID_OMEGA_GAUSSIAN if omega == "gaussian" else RID_OMEGA_RADEMACHER
     cfg.data_dtype = RID_F64 if dtype == "f64" else RID_F32
-    cfg.sketch_prec = {"native": RID_SKETCH_NATIVE, "bf16": RID_SKETCH_BF16, "bf16x2": RID_SKETCH_BF16X2}[sketch]
+    cfg.sketch_prec = {"native": RID_SKETCH_NATIVE, "bf16": RID_SKETCH_BF16, "bf16x2": RID_SKETCH_BF16X2,
+                       "fp8": RID_SKETCH_FP8, "fp8x2": RID_SKETCH_FP8X2}[sketch]
     cfg.n_max = int(n_max)
     cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     cfg.group_max = int(group_max)

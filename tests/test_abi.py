@@ -216,7 +216,8 @@ int main(int argc, char** argv) {
 
 def test_fault_injection_parsing_and_countdown():
     """RID_FAULT_INJECT (csrc/fault_inject.h, host C++ only): only "alloc:<n>" with n >= 1 arms
-    it, and then exactly the n-th allocation fails, once."""
+    the allocation countdown, and then exactly the n-th allocation fails, once; only "wait:<n>"
+    with 1 <= n <= 2^22 sets a pipeline-wait limit."""
     src = r'''
 #include <stdio.h>
 #include "fault_inject.h"
@@ -233,6 +234,11 @@ int main(void) {
   if (seq[0] || seq[1] || !seq[2] || seq[3] || seq[4] || seq[5]) return 13;
   c.arm(0);
   if (c.next_fails()) return 14;
+  const char* woff[] = {0, "", "wait:", "wait:0", "wait:-1", "wait:4194305", "wait:2x", "alloc:3"};
+  for (const char* v : woff)
+    if (rid::parse_wait_inject(v) != 0) return 15;
+  if (rid::parse_wait_inject("wait:1") != 1 || rid::parse_wait_inject("wait:4194304") != 4194304u) return 16;
+  if (rid::parse_fault_inject("wait:5") != 0) return 17;
   printf("ok\n");
   return 0;
 }

@@ -132,3 +132,61 @@ def test_tc_batch_step_candidates_on_gpu_sketch():
     assert np.linalg.norm(cand[0][:na] - P4) <= 1e-10 * max(1.0, kap) * np.linalg.norm(P4)
     kapG = np.linalg.cond(G)
     assert np.linalg.norm(cand[1][:na] - P5) <= 1e-5 * max(1.0, kapG) * np.linalg.norm(P5)
+
+
+def test_tc_batch_step_alg6_alg7_hutch_on_gpu_state():
+    """Batch-step parity of the rest of the step on identical inputs: the oracle's Algorithms 6 and
+    7 and Algorithm 8's four estimates, evaluated on the GPU's own sketch, basis, previous basis and
+    previous coefficients (read from a second handle stopped after the previous batch step: both
+    run the same deterministic stream).  Algorithm 6 uses only the FP64 sketch (bar 1e-10 x
+    kappa(Omega A_J)); Algorithm 7 goes through the tensor-core basis Gram (bar 1e-5 x kappa(G),
+    as Algorithm 5).  The estimates: the oracle's Eqs. 36-37 on the GPU's candidates, the GPU's
+    ||A_obs||^2 and the pseudo-inverse cutoff of the reduced-precision sketch (sk_rel = 2e-5); the
+    GPU's Gram enters tr(G P P^T), so the bar is 1e-9 ||A_obs||^2 plus 5e-5 x the candidate's energy
+    sum_j sum_a G_aa P_aj^2 (ten times the Gram's relative accuracy)."""
+    import math
+    from oracle.rid import coeff_alg4, coeff_alg6, coeff_alg7, na_hutchpp_sq_error
+    A = _mats(50000, 64, 21)
+    k, s, h = 16, 67, 30
+    n = A.shape[1]
+    gp, Jp, Pp, _ = _run_gpu(A[:, :n - k], k, s, h, "bf16x2", defer=True)   # stops after batch 2
+    g, J, P, _ = _run_gpu(A, k, s, h, "bf16x2", defer=True)
+    n_prev = n - k
+    cand = g.candidates(n)
+    S = g.state(0)
+    fro = g.state(3)[0]
+    est_g = g.error_estimate()[0][1:5]
+    A64 = A.astype(np.float64)
+    act = np.nonzero(J >= 0)[0]
+    Ja = J[act]
+    na = len(act)
+    SA = S[:s] / math.sqrt(s)
+    SJ = SA[:, Ja]
+    AJ = A64[:, Ja]
+    G = AJ.T @ AJ
+    P4a = coeff_alg4(SJ, SA)
+    kept = J[act] == Jp[act]
+    P_prev_ext = np.zeros((na, n))
+    P_prev_ext[:, :n_prev] = Pp[act, :]
+    P_prev_ext[:, n_prev:] = P4a[:, n_prev:]
+    P6 = coeff_alg6(SJ, SA, P_prev_ext, kept)
+    kap = np.linalg.cond(SJ)
+    assert np.linalg.norm(cand[2][:na] - P6) <= 1e-10 * max(1.0, kap) * max(np.linalg.norm(P6), 1e-300)
+    pact = np.nonzero(Jp >= 0)[0]
+    P7 = np.zeros((na, n))
+    P7[:, :n_prev] = coeff_alg7(AJ, A64[:, Jp[pact]], Pp[pact, :])
+    P7[:, n_prev:] = P4a[:, n_prev:]
+    kapG = np.linalg.cond(G)
+    assert np.linalg.norm(cand[3][:na] - P7) <= 1e-5 * max(1.0, kapG) * np.linalg.norm(P7)
+    cfg = RIDConfig(m=A.shape[0], k=k, s=s, h=h, seed=3)
+    split = cfg.probe_split()
+    base = split[0][0]
+    H = S[base: split[2][1]]
+    rel = tuple((a - base, b - base) for a, b in split)
+    n1, n2 = rel[0][1] - rel[0][0], rel[1][1] - rel[1][0]
+    rcond = max(max(n1, n2) * np.finfo(np.float64).eps, 2e-5)
+    for q in range(4):
+        Pq = cand[q][:na]
+        est_o = na_hutchpp_sq_error(H, H[:, Ja], Pq, G, fro, rel, rcond=rcond)
+        ener = float(np.einsum("a,aj->", np.diag(G), Pq * Pq))
+        assert abs(est_g[q] - est_o) <= 1e-9 * fro + 5e-5 * ener, (q, est_g[q], est_o, ener)

@@ -67,3 +67,43 @@ def test_injected_allocation_failures_in_init_and_growth(monkeypatch):
     J, P = g.finalize()
     g.close()
     assert np.array_equal(J, Jr) and np.array_equal(P, Pr)
+
+
+@pytest.mark.parametrize("sketch", ["bf16x2", "fp8x2"])
+def test_bounded_pipeline_wait_gives_up_cleanly(monkeypatch, sketch):
+    """RID_FAULT_INJECT=wait:1 gives the tensor-core kernels' pipeline waits a limit of one poll, so
+    that the MMA issuer's first wait for a staged chunk runs out: the kernel raises the timeout bit
+    of the device error word, every role stops at its next wait, the MMAs already issued are waited
+    for with the full limit, TMEM is freed and the kernel returns.  The host sees RID_ETIMEOUT at
+    the next synchronizing call; the context stays usable, and a handle created without the
+    injection then gives the reference results."""
+    import torch
+    from paper_2405_16076_gb300 import rid
+    m, n = 300_000, 50
+    kw = dict(dtype="f32", sketch=sketch, seed=11, n_max=n)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn((n, m), generator=gen, device="cuda", dtype=torch.float32)
+    monkeypatch.delenv("RID_FAULT_INJECT", raising=False)
+    ref = rid.OnlineRID(m=m, k=K, s=S, h=H, **kw)
+    for j0 in range(0, n, 10):
+        ref.ingest(X[j0:j0 + 10])
+    Jr, Pr = ref.finalize()
+    ref.close()
+
+    monkeypatch.setenv("RID_FAULT_INJECT", "wait:1")
+    g = rid.OnlineRID(m=m, k=K, s=S, h=H, **kw)
+    monkeypatch.delenv("RID_FAULT_INJECT")
+    for j0 in range(0, n, 10):
+        g.ingest(X[j0:j0 + 10])
+    with pytest.raises(rid.RIDError) as e:
+        g.sync()
+    assert e.value.code == rid.RID_ETIMEOUT, e.value
+    g.close()
+    torch.cuda.synchronize()                     # no sticky CUDA error: the kernels returned
+
+    h2 = rid.OnlineRID(m=m, k=K, s=S, h=H, **kw)
+    for j0 in range(0, n, 10):
+        h2.ingest(X[j0:j0 + 10])
+    J, P = h2.finalize()
+    h2.close()
+    assert np.array_equal(J, Jr) and np.array_equal(P, Pr)
