@@ -77,6 +77,13 @@ enum rid_sketch_prec {
                                 residual a - hi with its own block scales */
 };
 
+/* Sum `count` doubles of the device buffer `buf` over every shard of a row-sharded stream (see
+ * rid_config.allreduce), in place, with the same result bits on every shard, ordered on the CUDA
+ * stream `cuda_stream` (for example ncclAllReduce with ncclSum on that stream).  `user` is
+ * rid_config.allreduce_user.  Return 0 on success, nonzero on failure (the calling entry point
+ * then fails with RID_ECUDA). */
+typedef int (*rid_allreduce_fn)(double* buf, int64_t count, void* cuda_stream, void* user);
+
 typedef struct rid_config {
   int64_t m;             /* snapshot length */
   int32_t k;             /* target rank; basis size t = k (Sec. 2.2.2) */
@@ -113,6 +120,21 @@ typedef struct rid_config {
                             select of step b chooses the buffer slots of batch b + lookahead, and
                             the handle keeps (lookahead + 2) t data columns of m in device memory.
                             The results do not depend on it */
+  /* Row sharding (Sec. 5's in-situ parallel use; NULL allreduce = off).  Each shard -- one handle
+   * per GPU or rank -- holds rows [row_offset, row_offset + m) of every snapshot of a stream of
+   * m_global rows; Omega's entries are keyed by the global row, so the shards' partial sketches sum
+   * to the whole one.  The library calls allreduce at the method's two exchange points, on the
+   * handle's own streams: after each sketch group, on the (s + h) x ncols partial sketch and then
+   * on the ncols partial squared norms; in each batch step, on the t x 2t block of partial basis
+   * Gram entries (new elements x targets).  Everything else is replicated on every shard from the
+   * summed values, so all shards return the same J and P; rid_get_basis returns the shard's rows.
+   * Needs row_offset a multiple of 128, m_global >= row_offset + m, no gradient mode; every shard
+   * must make the same calls in the same order with the same configuration apart from m and
+   * row_offset.  Not meant for stream capture unless allreduce is capturable. */
+  int64_t row_offset;
+  int64_t m_global;
+  rid_allreduce_fn allreduce;
+  void* allreduce_user;
 } rid_config;
 
 typedef struct rid_handle rid_handle;

@@ -10,6 +10,7 @@
 
 #include "linalg.cuh"
 #include "philox.cuh"
+#include "rid.h"
 #include "rid_internal.cuh"
 
 namespace rid {
@@ -367,6 +368,26 @@ __global__ void gather_kernel(Dev d, WorkLayout w) {
   for (int64_t idx = g0; idx < (int64_t)hh * na; idx += gs) {
     const int r = (int)(idx % hh), a = (int)(idx / hh);
     HJ[r + (size_t)a * hh] = d.S[(size_t)d.JC[d.act[a]] * d.rows + d.hbase + r];
+  }
+}
+
+// Row sharding: the step's new-element x target block of the pool Gram, packed t x 2t (zeros past
+// the counts) for the exchange, and the summed block written back to both triangles.
+__global__ void gram_pack_kernel(Dev d) {
+  const int t = d.t, nn = d.meta[META_NNEW], nt = d.meta[META_NTGT], np = d.npool;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < t * 2 * t; idx += gridDim.x * blockDim.x) {
+    const int x = idx % t, y = idx / t;
+    d.xbuf[idx] = (x < nn && y < nt) ? d.Gp[d.gnew[x] + (size_t)d.gtgt[y] * np] : 0.0;
+  }
+}
+__global__ void gram_unpack_kernel(Dev d) {
+  const int t = d.t, nn = d.meta[META_NNEW], nt = d.meta[META_NTGT], np = d.npool;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < t * 2 * t; idx += gridDim.x * blockDim.x) {
+    const int x = idx % t, y = idx / t;
+    if (x >= nn || y >= nt) continue;
+    const double v = d.xbuf[idx];
+    d.Gp[d.gnew[x] + (size_t)d.gtgt[y] * np] = v;     // a pair of two new elements: equal values
+    d.Gp[d.gtgt[y] + (size_t)d.gnew[x] * np] = v;
   }
 }
 
@@ -1047,6 +1068,14 @@ int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, in
     if (d.dtype == 0) basis_gram_kernel<double><<<gg, 256, 0, stg>>>(d);
     else basis_gram_kernel<float><<<gg, 256, 0, stg>>>(d);
     gram_reduce_kernel<<<(d.t * 2 * d.t + 255) / 256, 256, 0, stg>>>(d, d.gram_split);
+  }
+  if (d.allreduce) {
+    // row shard: the partial Gram entries of this step summed over the shards
+    const int nb = (2 * d.t * d.t + 255) / 256;
+    gram_pack_kernel<<<nb, 256, 0, stg>>>(d);
+    if (((rid_allreduce_fn)d.allreduce)(d.xbuf, 2 * (int64_t)d.t * d.t, (void*)stg, d.allreduce_user) != 0) return 0;
+    gram_unpack_kernel<<<nb, 256, 0, stg>>>(d);
+    ngk += 2;
   }
   gather_kernel<false><<<d.n_sm, 256, 0, stg>>>(d, w);
   {

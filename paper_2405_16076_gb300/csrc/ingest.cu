@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "philox.cuh"
+#include "rid.h"
 #include "rid_internal.cuh"
 
 namespace rid {
@@ -74,7 +75,7 @@ ingest_sketch_kernel(Dev d, SimtCols cols, int nb, int count) {
         // Rademacher: 2 Philox calls cover the 256 coordinates of the chunk
 #pragma unroll 1
         for (int half = 0; half < kChunk / 128; ++half) {
-          const uint32_t blk = (uint32_t)((i0 >> 7) + half);
+          const uint32_t blk = (uint32_t)(((i0 + d.row_offset) >> 7) + half);   // global row
           const u32x4 w = philox4x32_10(blk, (uint32_t)r, kTagRademacher, 0, k0, k1);
           const uint32_t words[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -148,11 +149,34 @@ __global__ void sketch_reduce_kernel(Dev d, int nb, int64_t n_obs, int nblk) {
     for (int q = 0; q < nb; ++q) {
       double v = 0.0;
       for (int b = 0; b < nblk; ++b) v += d.npart[(size_t)b * nb + q];
+      if (d.gnorm) {                        // row shard: summed over the shards first
+        d.gnorm[q] = v;
+        continue;
+      }
       if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
       d.fro2[0] += v;
       d.fro2[1] += v;
     }
   }
+}
+
+// Row sharding: the group's squared norms, summed over the shards, into ||A_obs||^2 (column order).
+__global__ void add_norms_kernel(Dev d, int nb) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int q = 0; q < nb; ++q) {
+    const double v = d.gnorm[q];
+    if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
+    d.fro2[0] += v;
+    d.fro2[1] += v;
+  }
+}
+
+int shard_exchange_sketch(const Dev& d, int ncols, int64_t n_obs, cudaStream_t st) {
+  const rid_allreduce_fn f = (rid_allreduce_fn)d.allreduce;
+  if (f(d.S + (size_t)n_obs * d.rows, (int64_t)ncols * d.rows, (void*)st, d.allreduce_user) != 0) return -1;
+  if (f(d.gnorm, ncols, (void*)st, d.allreduce_user) != 0) return -1;
+  add_norms_kernel<<<1, 32, 0, st>>>(d, ncols);
+  return 0;
 }
 
 // SS^T += sum_q l_q l_q^T over the new leverage-sketch columns, in column order.
@@ -175,7 +199,7 @@ __global__ void materialize_omega_kernel(Dev d) {
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx / d.rows;
     const int r = (int)(idx % d.rows);
-    d.omegaT[idx] = (i < d.m) ? gauss_entry(d.seed, kTagGauss, (uint32_t)r, (uint64_t)i) : 0.0;
+    d.omegaT[idx] = (i < d.m) ? gauss_entry(d.seed, kTagGauss, (uint32_t)r, (uint64_t)(i + d.row_offset)) : 0.0;
   }
 }
 

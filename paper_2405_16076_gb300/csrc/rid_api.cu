@@ -143,7 +143,7 @@ void free_all(Dev& d, void* staging) {
                   d.slotC_prev, d.dslot_all, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
                   d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
                   d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, d.Y, d.Wr, d.zq, d.Sg,
-                  d.Kg, staging};
+                  d.Kg, d.gnorm, d.xbuf, staging};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
 }
@@ -434,6 +434,8 @@ int flush(rid_handle* h) {
     if (rid::launch_tc_ingest(db, h->pend.data(), G, split, h->count, h->n_obs, nblk,
                               h->tc_part, h->tc_npart, h->st, h->prof ? ev : nullptr, fp8) != 0)
       return fail(h, RID_ECUDA, "tensor-core ingest launch failed");
+    if (db.allreduce && rid::shard_exchange_sketch(db, G, h->n_obs, h->st) != 0)
+      return fail(h, RID_ECUDA, "row-shard exchange (allreduce) of the sketch failed");
     rid::launch_gram_update(db, G, h->n_obs, h->st);
     nk0 = 1;
     nk1 += 2;
@@ -442,6 +444,8 @@ int flush(rid_handle* h) {
       const int nb = G - q0 < rid::kMaxB ? G - q0 : rid::kMaxB;
       cudaEvent_t* e = (h->prof && q0 == 0) ? ev : nullptr;
       nk1 += rid::launch_ingest(db, h->pend.data() + q0, nb, h->count + q0, h->n_obs + q0, h->st, e) - 1;
+      if (db.allreduce && rid::shard_exchange_sketch(db, nb, h->n_obs + q0, h->st) != 0)
+        return fail(h, RID_ECUDA, "row-shard exchange (allreduce) of the sketch failed");
       if (db.grad) nk1 += rid::launch_grad(db, h->pend.data() + q0, nb, h->n_obs + q0, h->st);
       rid::launch_gram_update(db, nb, h->n_obs + q0, h->st);
       nk0 += 1;
@@ -506,6 +510,14 @@ int check_config(const rid_config* c) {
     return fail(h, RID_EINVAL, "unknown refill_mode");
   if (c->lookahead != 0 && (c->lookahead < 2 || c->lookahead > 4))
     return fail(h, RID_EINVAL, "lookahead must be 0 (default 3) or in [2, 4]");
+  if (c->allreduce) {
+    if (c->row_offset < 0 || c->row_offset % 128 != 0)
+      return fail(h, RID_EINVAL, "row sharding needs row_offset >= 0, a multiple of 128");
+    if (c->m_global < c->row_offset + c->m) return fail(h, RID_EINVAL, "row sharding needs m_global >= row_offset + m");
+    if (c->grad_dims != 0 || c->grad_coeff != 0) return fail(h, RID_EINVAL, "row sharding does not support gradient mode");
+  } else if (c->row_offset != 0) {
+    return fail(h, RID_EINVAL, "row_offset needs an allreduce (row sharding)");
+  }
   if (c->grad_coeff != 0 && c->grad_dims != 2)
     return fail(h, RID_EINVAL, "grad_coeff needs gradient mode (grad_dims = 2)");
   if (c->grad_dims != 0) {
@@ -593,6 +605,9 @@ int rid_init(rid_handle** out, const rid_config* c) {
   const double k = (double)c->k;
   d.refill_scale = c->c_const * (k * log(k) + k * log(1.0 / c->delta) / c->eps) / (double)c->k;
   d.refill_mode = c->refill_mode;
+  d.row_offset = c->allreduce ? c->row_offset : 0;
+  d.allreduce = (void*)c->allreduce;
+  d.allreduce_user = c->allreduce_user;
   {
     const uint32_t wl = rid::parse_wait_inject(getenv("RID_FAULT_INJECT"));
     d.ring_wait_limit = wl ? wl : rid::kRingWaitLimit;
@@ -680,6 +695,10 @@ int rid_init(rid_handle** out, const rid_config* c) {
   AL(d.meta, rid::META_LEN); AL(d.scal, rid::SCAL_LEN);
   AL(d.act, t); AL(d.pact, t); AL(d.isnew, t); AL(d.posof, t); AL(d.newpos, t);
   AL(d.gnew, t); AL(d.gtgt, 2 * t);
+  if (d.allreduce) {
+    AL(d.gnorm, rid::kMaxGroup);
+    AL(d.xbuf, 2 * (size_t)t * t);
+  }
   AL(h->rec_i64, 4 * (size_t)t);
   AL(h->rec_i32, 2 * (10 * (size_t)t + rid::META_LEN));
   AL(d.Gp, (size_t)d.npool * d.npool);
@@ -1004,7 +1023,8 @@ bool same_config(const rid_config& a, const rid_config& b) {
          a.lambda_fixed == b.lambda_fixed && a.omega_kind == b.omega_kind && a.data_dtype == b.data_dtype &&
          a.sketch_prec == b.sketch_prec && a.grad_dims == b.grad_dims && a.nx == b.nx && a.ny == b.ny &&
          a.nfields == b.nfields && a.seed == b.seed && a.right_l == b.right_l && a.grad_coeff == b.grad_coeff &&
-         a.refill_mode == b.refill_mode && a.lookahead == b.lookahead;
+         a.refill_mode == b.refill_mode && a.lookahead == b.lookahead && a.row_offset == b.row_offset &&
+         a.m_global == b.m_global;
 }
 
 struct CkptPlan {

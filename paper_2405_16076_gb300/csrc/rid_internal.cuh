@@ -38,6 +38,14 @@ struct Dev {
   double refill_scale;            // c (k ln k + k ln(1/delta)/eps) / t
   int refill_mode;                // 0 first success (R7), 1 proportional draw (R7p)
   uint32_t ring_wait_limit;       // polls of a tensor-core pipeline wait before it gives up
+  // row sharding: global row of local row 0 (a multiple of 128; Omega is keyed by the global row);
+  // with an exchange (allreduce non-null) the sketch reductions leave the group's squared norms in
+  // gnorm instead of adding them to fro2, and xbuf holds a step's partial basis-Gram block
+  int64_t row_offset;
+  void* allreduce;                // rid_allreduce_fn, host-side only
+  void* allreduce_user;
+  double* gnorm;                  // kMaxGroup doubles (sharded only)
+  double* xbuf;                   // t x 2t doubles (sharded only)
   uint64_t seed;
   int grad;                       // gradient mode
   int nx, ny, nfields;
@@ -206,6 +214,10 @@ int launch_batch_select(const Dev& d, const Dev& r, int count, int64_t n_obs, in
 int launch_batch_tail(const Dev& d, int count, int64_t n_obs, int64_t n_prev, int batch,
                       cudaStream_t st, cudaStream_t stg, cudaEvent_t ev_fork, cudaEvent_t ev_gram,
                       int* gmeta, int64_t* gjcp, int* gslotp, cudaEvent_t* tl);
+// Row sharding: sum the group's partial sketch columns (S(:, n_obs .. n_obs + ncols)) and squared
+// norms over the shards with d.allreduce, then add the norms to ||A_obs||^2 in column order.
+// Returns 0, or -1 if the exchange failed.
+int shard_exchange_sketch(const Dev& d, int ncols, int64_t n_obs, cudaStream_t st);
 int launch_reset_state(const Dev& d, cudaStream_t st);
 
 // coop.cu: lambda (Eq. 23) through a tridiagonalization of the sketch Gram (cluster or

@@ -336,7 +336,9 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
         const uint32_t bst = sB + st * btile;
         uint32_t wa, wb;
         if ((cg & 1) == 0) {
-          const u32x4 w = philox4x32_10((uint32_t)(cg >> 1), (uint32_t)r0, kTagRademacher, 0, k0, k1);
+          // counter block of 128 global rows (the shard offset is a multiple of 128)
+          const u32x4 w = philox4x32_10((uint32_t)((cg >> 1) + (d.row_offset >> 7)), (uint32_t)r0, kTagRademacher, 0,
+                                        k0, k1);
           wa = w.x; wb = w.y; keep[0] = w.z; keep[1] = w.w;
         } else {
           wa = keep[0]; wb = keep[1];
@@ -440,6 +442,10 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(Dev d, const float* __re
     if (threadIdx.x == 0) {
       for (int c = 0; c < ncols; ++c) {
         const double v = red[0][c];
+        if (d.gnorm) {                      // row shard: summed over the shards first
+          d.gnorm[c] = v;
+          continue;
+        }
         if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
         d.fro2[0] += v;
         d.fro2[1] += v;
@@ -1167,7 +1173,7 @@ tc_ingest_fp8_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrow
       }
       if (r0 < nrows16) {
         const uint32_t bst = sB + st * btile;
-        const u32x4 w = philox4x32_10((uint32_t)cg, (uint32_t)r0, kTagRademacher, 0, k0, k1);
+        const u32x4 w = philox4x32_10((uint32_t)(cg + (d.row_offset >> 7)), (uint32_t)r0, kTagRademacher, 0, k0, k1);
         const uint32_t words[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int u = 0; u < 8; ++u) {

@@ -37,7 +37,13 @@ class rid_config(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("group_max", ctypes.c_int32), ("defer_device_input", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p), ("right_l", ctypes.c_int32), ("grad_coeff", ctypes.c_int32),
         ("ingest_ctas", ctypes.c_int32), ("refill_mode", ctypes.c_int32), ("lookahead", ctypes.c_int32),
+        ("row_offset", ctypes.c_int64), ("m_global", ctypes.c_int64), ("allreduce", ctypes.c_void_p),
+        ("allreduce_user", ctypes.c_void_p),
     ]
+
+
+# rid_allreduce_fn: int (*)(double* buf, int64_t count, void* cuda_stream, void* user)
+RID_ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class rid_log_record(ctypes.Structure):
@@ -226,7 +232,7 @@ def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_cons
                 lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
                 grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False, ingest_ctas=0, refill="first",
-                lookahead=0):
+                lookahead=0, row_offset=0, m_global=0, allreduce=None):
     """An rid_config from keyword arguments (the defaults of rid_config_default otherwise)."""
     cfg = rid_config()
     _check(rid_config_default(ctypes.byref(cfg)))
@@ -248,6 +254,10 @@ def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_cons
     cfg.ingest_ctas = int(ingest_ctas)
     cfg.refill_mode = {"first": RID_REFILL_FIRST, "proportional": RID_REFILL_PROPORTIONAL}[refill]
     cfg.lookahead = int(lookahead)
+    cfg.row_offset = int(row_offset)
+    cfg.m_global = int(m_global)
+    if allreduce is not None:                 # a RID_ALLREDUCE_FN; the caller keeps it alive
+        cfg.allreduce = ctypes.cast(allreduce, ctypes.c_void_p)
     cfg.cuda_stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
     return cfg
 
@@ -274,8 +284,10 @@ class OnlineRID:
     def __init__(self, m, k, s, h=0, **kw):
         """Keyword arguments as make_config: c1, c2, eps, delta, c_const, lambda_mode,
         lambda_fixed, omega, dtype, sketch, n_max, seed, stream, group_max, defer, grad_dims,
-        nx, ny, nfields, right_l, grad_coeff, ingest_ctas, refill ("first" or "proportional"), lookahead."""
+        nx, ny, nfields, right_l, grad_coeff, ingest_ctas, refill ("first" or "proportional"), lookahead, and for a row shard
+        row_offset, m_global and allreduce (a RID_ALLREDUCE_FN)."""
         cfg = make_config(m, k, s, h, **kw)
+        self._allreduce = kw.get("allreduce")     # the callback must outlive the handle
         dtype = kw.get("dtype", "f32")
         self.cfg = cfg
         self.t = int(k)
