@@ -630,7 +630,8 @@ def main():
     grad = cfg.get("kind") == "ignition"
     if grad:
         gen = IgnitionStream(seed=rank_seeds(rank)[0], N=cfg["N"], nfields=cfg["nfields"], n=n, device=dev)
-        args.sketch = "native"                      # gradient mode runs the native-precision sketch
+        if args.grad_coeff:
+            args.sketch = "native"                  # the coefficient sketches run on the native path
     else:
         gen = ChannelFlowStream(seed=rank_seeds(rank)[0], nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], n=n, device=dev)
     m = gen.m
@@ -891,6 +892,22 @@ def main():
         line["ingest_roofline"] = line["roofline"]
         line["roofline"] = right
         line["config"]["right_l"] = cfg["right_l"]
+    if grad and args.sketch != "native":
+        # Gradient mode on tensor cores: the leverage sketch of [a; G a] needs 2 m (s + h) + 2 (2 m) s
+        # multiply-adds per snapshot (the plain sketch, and Omega_g over the 2 m gradient entries),
+        # taken in row slices of at most 512 rows per pass; tensor-bound.  Achieved: those
+        # algorithmic flops of a group over the group's whole sketch time (every pass, the stencil
+        # and the reductions); BF16x2 issues twice these flops (hi and lo rows).
+        flop_col = 2.0 * m * (cfg["s"] + cfg["h"]) + 2.0 * (2 * m) * cfg["s"]
+        ach = cols_per_launch * flop_col / (avg_ms / 1e3) / 1e12
+        iso = G * flop_col / (iso_ms / 1e3) / 1e12
+        peak_t = float(pk.get("bf16_tflops", 1900.0))
+        line["roofline"].update({"bound": "tensor", "achieved": ach, "peak": peak_t, "unit": "TFLOP/s",
+                                 "frac": ach / peak_t, "traffic": None, "kernel": "tc_ingest_kernel (all passes)",
+                                 "flop_per_snapshot": flop_col,
+                                 "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if "fallback" not in pk
+                                 else "fallback"})
+        line["roofline"]["isolated"].update({"achieved": iso, "frac": iso / peak_t})
     if args.sketch == "native":
         # The native-precision sketch runs on the FP32 pipe: one signed add per (row, coordinate,
         # column) of the s + h sketch rows.  Peak: SMs x 128 FP32 lanes x the maximum SM clock.

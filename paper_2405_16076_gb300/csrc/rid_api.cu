@@ -143,7 +143,7 @@ void free_all(Dev& d, void* staging) {
                   d.slotC_prev, d.dslot_all, d.JD, d.tau_old, d.tauC, d.tauD, d.meta, d.act,
                   d.pact, d.isnew, d.posof, d.newpos, d.gnew, d.gtgt, d.scal, d.Gp, d.gpart,
                   d.P, d.cand, d.work, d.hpart, d.spart, d.npart, d.err, d.gbar, d.Y, d.Wr, d.zq, d.Sg,
-                  d.Kg, d.gnorm, d.xbuf, staging};
+                  d.Kg, d.gnorm, d.xbuf, d.gfield, d.glev, d.gnorm2, staging};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
 }
@@ -501,7 +501,7 @@ int check_config(const rid_config* c) {
   if (c->sketch_prec != RID_SKETCH_NATIVE) {
     if (c->data_dtype != RID_F32) return fail(h, RID_EINVAL, "tensor-core sketches need FP32 data");
     if (c->omega_kind != RID_OMEGA_RADEMACHER) return fail(h, RID_EINVAL, "tensor-core sketches need a Rademacher Omega");
-    if (c->s + c->h > 512) return fail(h, RID_EINVAL, "BF16 sketches support s + h <= 512");
+    if (c->s + c->h > 4096) return fail(h, RID_EINVAL, "tensor-core sketches support s + h <= 4096");
   }
   if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
   if (c->right_l < 0 || c->right_l > 4096) return fail(h, RID_EINVAL, "right_l must be in [0, 4096]");
@@ -525,8 +525,10 @@ int check_config(const rid_config* c) {
     if (c->nx < 2 || c->ny < 2 || c->nfields < 1)
       return fail(h, RID_EINVAL, "gradient mode needs nx >= 2, ny >= 2, nfields >= 1");
     if ((int64_t)c->nx * c->ny * c->nfields != c->m) return fail(h, RID_EINVAL, "gradient mode needs m = nx ny nfields");
-    if (c->sketch_prec != RID_SKETCH_NATIVE)
-      return fail(h, RID_EINVAL, "gradient mode runs the native-precision sketch (sketch_prec NATIVE)");
+    if (c->sketch_prec == RID_SKETCH_FP8 || c->sketch_prec == RID_SKETCH_FP8X2)
+      return fail(h, RID_EINVAL, "gradient mode runs the native or the BF16 sketches");
+    if (c->grad_coeff != 0 && c->sketch_prec != RID_SKETCH_NATIVE)
+      return fail(h, RID_EINVAL, "grad_coeff needs the native-precision sketch (sketch_prec NATIVE)");
   }
   {
     const int nprobe = c->h > 0 ? c->h : c->s;
@@ -667,7 +669,8 @@ int rid_init(rid_handle** out, const rid_config* c) {
 #define AL(ptr, n) do { if (dalloc(&(ptr), (size_t)(n)) != cudaSuccess) { rc = RID_ENOMEM; goto fail_alloc; } } while (0)
   if (h->tc) {
     const int nrows16 = (d.rows + 15) / 16 * 16;
-    const int prow = nrows16 > 256 ? nrows16 : 256;     // ingest partials or Gram partials
+    // ingest partials (one pass: at most 512 rows) or Gram partials (256 rows)
+    const int prow = nrows16 > 256 ? (nrows16 > 512 ? 512 : nrows16) : 256;
     const int pblk = h->first_blocks > h->tc_blocks ? h->first_blocks : h->tc_blocks;
     AL(h->tc_part, (size_t)pblk * prow * 128);
     AL(h->tg_part, (size_t)h->tc_blocks * 512 * 128);     // basis-Gram partials: 512 rows per CTA
@@ -675,6 +678,14 @@ int rid_init(rid_handle** out, const rid_config* c) {
     d.tc_blocks = h->tc_blocks;
     d.tc_part = h->tc_part;
     d.tg_part = h->tg_part;
+    if (d.grad) {
+      // gradient mode on tensor cores: the group's 2m-long gradient fields and their sketches
+      d.gfield_ld = (2 * d.m + 63) / 64 * 64;
+      const int gmax = h->group_max;
+      AL(d.gfield, (size_t)gmax * d.gfield_ld);
+      AL(d.glev, (size_t)gmax * d.s);
+      AL(d.gnorm2, (size_t)gmax);
+    }
   }
   {
     char* pool = nullptr;

@@ -45,6 +45,12 @@ struct Dev {
   void* allreduce;                // rid_allreduce_fn, host-side only
   void* allreduce_user;
   double* gnorm;                  // kMaxGroup doubles (sharded only)
+  // gradient mode on tensor cores: the group's gradient fields (FP32, column q at gfield + q
+  // gfield_ld, 2m entries), the gradient part of its leverage sketch (s x group) and ||G a_q||^2
+  float* gfield;
+  int64_t gfield_ld;
+  double* glev;
+  double* gnorm2;
   double* xbuf;                   // t x 2t doubles (sharded only)
   uint64_t seed;
   int grad;                       // gradient mode

@@ -166,6 +166,22 @@ struct Cols {
   const float* p[128];
 };
 
+}  // namespace
+
+// One pass of the tensor-core sketch: rows [rlo, rlo + rows of the launch) of the test matrix
+// with counter tag `tag`, over `len` coordinates of each column; `copy`: also copy the columns
+// into their buffer slots (the first pass over the data).  The plain sketch of a stream with
+// more than 512 rows takes several passes (the 512 TMEM accumulator columns of one CTA), and
+// gradient mode sketches the 2m-long gradient field with the gradient test matrix.
+struct TcPass {
+  int64_t len;
+  int rlo;
+  uint32_t tag;
+  int copy;
+};
+
+namespace {
+
 // 16 coordinates of one column: 4 float4 (aligned) or guarded scalars.
 __device__ __forceinline__ void load16(const float* src, int64_t i, int64_t m, bool vec, float4 (&v)[4]) {
   if (vec && i + 16 <= m) {
@@ -186,7 +202,7 @@ __device__ __forceinline__ void load16(const float* src, int64_t i, int64_t m, b
 __global__ void __launch_bounds__(kThreads, 1)
 tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16, int n1, int n2,
                  int64_t chunks_per_cta, int vec, float* __restrict__ part, double* __restrict__ npart,
-                 int nstage, uint32_t btile) {
+                 int nstage, uint32_t btile, TcPass ps) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -201,7 +217,7 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
   const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 32, bar_done = sBar + 64;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
+  const int64_t nchunks = (ps.len + kChunkK - 1) / kChunkK;
   const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
   int64_t c1 = c0 + chunks_per_cta;
   if (c1 > nchunks) c1 = nchunks;
@@ -260,7 +276,7 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
     const int q = pt >> 3, g = pt & 7;
     const bool has_col = q < ncols;
     const float* src = has_col ? cols.p[q] : nullptr;
-    float* dstp = has_col ? (float*)d.pool + (int64_t)d.dslot[count + q] * d.m_pad : nullptr;
+    float* dstp = (has_col && ps.copy) ? (float*)d.pool + (int64_t)d.dslot[count + q] * d.m_pad : nullptr;
     const int r0 = pt;                        // Omega row of this thread
     const uint32_t k0 = (uint32_t)d.seed, k1 = (uint32_t)(d.seed >> 32);
     // squared norm: compensated FP32 sum (Kahan) over this CTA's coordinates, converted to FP64
@@ -274,19 +290,19 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
     auto load_chunk = [&](int64_t c, float4 (&v)[2]) {
       if (has_col && c < nch) {
         const int64_t i = (c0 + c) * kChunkK + 8 * g;
-        if (vec && i + 8 <= d.m) {
+        if (vec && i + 8 <= ps.len) {
           const float4* s4 = reinterpret_cast<const float4*>(src + i);
           v[0] = __ldcs(s4);
           v[1] = __ldcs(s4 + 1);
         } else {
           float t[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) t[j] = (i + j < d.m) ? src[i + j] : 0.f;
+          for (int j = 0; j < 8; ++j) t[j] = (i + j < ps.len) ? src[i + j] : 0.f;
           v[0] = make_float4(t[0], t[1], t[2], t[3]);
           v[1] = make_float4(t[4], t[5], t[6], t[7]);
         }
       }
-      if (has_col && g == 0 && vec && c + kL2Ahead < nch && (c0 + c + kL2Ahead + 1) * kChunkK <= d.m)
+      if (has_col && g == 0 && vec && c + kL2Ahead < nch && (c0 + c + kL2Ahead + 1) * kChunkK <= ps.len)
         prefetch_l2(src + (c0 + c + kL2Ahead) * kChunkK, kChunkK * 4);
     };
     int pst = 0;
@@ -300,13 +316,15 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
       if (has_col) {
         const int64_t i0 = cg * kChunkK + 8 * g;
         const float x[8] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w};
-        // copy into the buffer slot
-        if (i0 + 8 <= d.m) {
-          float4* o = reinterpret_cast<float4*>(dstp + i0);
-          __stcs(o, v[0]);
-          __stcs(o + 1, v[1]);
-        } else {
-          for (int j = 0; j < 8; ++j) if (i0 + j < d.m) dstp[i0 + j] = x[j];
+        // copy into the buffer slot (first pass only)
+        if (dstp) {
+          if (i0 + 8 <= d.m) {
+            float4* o = reinterpret_cast<float4*>(dstp + i0);
+            __stcs(o, v[0]);
+            __stcs(o + 1, v[1]);
+          } else {
+            for (int j = 0; j < 8; ++j) if (i0 + j < d.m) dstp[i0 + j] = x[j];
+          }
         }
         float s2 = 0.f;
 #pragma unroll
@@ -337,8 +355,8 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
         uint32_t wa, wb;
         if ((cg & 1) == 0) {
           // counter block of 128 global rows (the shard offset is a multiple of 128)
-          const u32x4 w = philox4x32_10((uint32_t)((cg >> 1) + (d.row_offset >> 7)), (uint32_t)r0, kTagRademacher, 0,
-                                        k0, k1);
+          const u32x4 w = philox4x32_10((uint32_t)((cg >> 1) + (d.row_offset >> 7)), (uint32_t)(ps.rlo + r0), ps.tag,
+                                        0, k0, k1);
           wa = w.x; wb = w.y; keep[0] = w.z; keep[1] = w.w;
         } else {
           wa = keep[0]; wb = keep[1];
@@ -360,7 +378,7 @@ tc_ingest_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrows16,
     };
     if (has_col && g == 0 && vec)
       for (int64_t c = 2; c < kL2Ahead && c < nch; ++c)
-        if ((c0 + c + 1) * kChunkK <= d.m) prefetch_l2(src + (c0 + c) * kChunkK, kChunkK * 4);
+        if ((c0 + c + 1) * kChunkK <= ps.len) prefetch_l2(src + (c0 + c) * kChunkK, kChunkK * 4);
     load_chunk(0, bufA);
     load_chunk(1, bufB);
     for (int64_t c = 0; c < nch; c += 2) {
@@ -1234,6 +1252,110 @@ tc_ingest_fp8_kernel(Dev d, Cols cols, int ncols, int split, int count, int nrow
   }
 }
 
+// ---------------------------------------------------------------- multi-pass sketch (row slices, gradient mode)
+constexpr int kMaxSliceRows = 512;          // TMEM accumulator columns of one CTA
+
+// Rows [rlo, rlo + gridDim.x) of the destination column block: dst(rlo + r, col0 + q) = the sum
+// over the split-K blocks of the hi (and lo) partial rows r of column q, blocks b = j (mod 4)
+// summed in order by thread (j, q) and the four sums added in the fixed order j = 0..3.
+__global__ void __launch_bounds__(256) tc_reduce_rows_kernel(const float* __restrict__ part, int nblk, int ncols,
+                                                             int split, int nrows16, int rlo,
+                                                             double* __restrict__ dst, int64_t ldd, int64_t col0) {
+  __shared__ double red[4][64];
+  const int q = threadIdx.x & 63, j = threadIdx.x >> 6;
+  const int r = blockIdx.x;
+  double v = 0.0;
+  if (q < ncols) {
+    for (int b = j; b < nblk; b += 4) {
+      const float* p = part + ((size_t)b * nrows16 + r) * 128;
+      v += (double)p[q];
+      if (split) v += (double)p[64 + q];
+    }
+  }
+  red[j][q] = v;
+  __syncthreads();
+  if (j == 0 && q < ncols)
+    dst[(size_t)(col0 + q) * ldd + rlo + r] = ((red[0][q] + red[1][q]) + red[2][q]) + red[3][q];
+}
+
+// The group's squared norms (split-K blocks in order): with out == nullptr added to ||A_obs||^2
+// and to the leverage norm in column order, else stored in out.
+__global__ void tc_norms_kernel(Dev d, const double* __restrict__ npart, int nblk, int ncols, double* out) {
+  if (threadIdx.x != 0) return;
+  for (int c = 0; c < ncols; ++c) {
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += npart[(size_t)b * 128 + c];
+    if (out) {
+      out[c] = v;
+      continue;
+    }
+    if (d.gnorm) {                            // row shard: summed over the shards first
+      d.gnorm[c] = v;
+      continue;
+    }
+    if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
+    d.fro2[0] += v;
+    d.fro2[1] += v;
+  }
+}
+
+// Gradient mode (Sec. 3.4, Eqs. 38-43): the stacked gradient fields G a_q (2m entries each, the
+// x then the y differences of every field) into g (column q at g + q ldg), by grad_stencil with
+// the native path's FP32 arithmetic.
+__global__ void grad_field_kernel(Dev d, Cols c, int ncols, float* __restrict__ g, int64_t ldg) {
+  const int64_t dm = 2 * d.m;
+  const int64_t n = (int64_t)ncols * dm;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / dm);
+    const int64_t j = idx - (int64_t)q * dm;
+    const GradStencil gs = grad_stencil(j, d.m, d.nx, d.ny);
+    const float* a = c.p[q];
+    float v = (float)gs.wc * a[gs.i];
+    if (gs.wm != 0.0) v += (float)gs.wm * a[gs.i - gs.st];
+    if (gs.wp != 0.0) v += (float)gs.wp * a[gs.i + gs.st];
+    g[(size_t)q * ldg + j] = v;
+  }
+}
+
+// Leverage sketch columns n_obs + q: the s left rows of the sketch plus Omega_g (G a_q), and
+// ||G a_q||^2 added to the leverage norm in column order.
+__global__ void lev_combine_kernel(Dev d, int ncols, int64_t n_obs) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < ncols * d.s) {
+    const int q = idx / d.s, r = idx % d.s;
+    d.Slev[(size_t)(n_obs + q) * d.lev_ld + r] = d.S[(size_t)(n_obs + q) * d.rows + r] + d.glev[(size_t)q * d.s + r];
+  }
+  if (idx == 0) {
+    for (int q = 0; q < ncols; ++q) {
+      const double v = d.gnorm2[q];
+      if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
+      d.fro2[1] += v;
+    }
+  }
+}
+
+// One pass of the BF16 tensor-core sketch over rows [ps.rlo, ps.rlo + nrows) of the test matrix.
+static int tc_pass(const Dev& d, const Cols& c, int ncols, int split, int count, TcPass ps, int nrows, int vec,
+                   int nblk, float* part, double* npart, int max_smem, cudaStream_t st) {
+  const int nrows16 = (nrows + 15) / 16 * 16;
+  if (nrows16 > kMaxSliceRows) return -1;
+  const int n1 = nrows16 < 256 ? nrows16 : 256;
+  const int n2 = nrows16 - n1;
+  const int64_t nchunks = (ps.len + kChunkK - 1) / kChunkK;
+  int64_t per = (nchunks + nblk - 1) / nblk;
+  per = (per + 1) / 2 * 2;                      // even: Philox words are shared by chunk pairs
+  // as many ring stages as fit (align slack + barrier block + stages)
+  const uint32_t btile = (uint32_t)nrows16 * 128u;
+  const int stage_bytes = kATile + (int)btile;
+  int nstage = (max_smem - 1024 - 128) / stage_bytes;
+  if (nstage > kMaxStages) nstage = kMaxStages;
+  if (nstage < 2) return -1;
+  const size_t smem = 1024 + 128 + (size_t)nstage * stage_bytes;
+  tc_ingest_kernel<<<nblk, kThreads, smem, st>>>(d, c, ncols, split, count, nrows16, n1, n2, per, vec ? 1 : 0, part,
+                                                 npart, nstage, btile, ps);
+  return 0;
+}
+
 // Launch the tensor-core sketch of ncols columns; returns 0 on success.
 int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split, int count,
                      int64_t n_obs, int nblk, float* part, double* npart, cudaStream_t st,
@@ -1277,21 +1399,57 @@ int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split
     tc_reduce_kernel<<<d.rows + 1, 256, 0, st>>>(d, part, npart, nblk, ncols, split, nrows16, n_obs);
     return 0;
   }
-  const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
-  int64_t per = (nchunks + nblk - 1) / nblk;
-  per = (per + 1) / 2 * 2;                      // even: Philox words are shared by chunk pairs
-  // as many ring stages as fit (align slack + barrier block + stages)
-  const uint32_t btile = (uint32_t)nrows16 * 128u;
-  const int stage_bytes = kATile + (int)btile;
-  int nstage = (max_smem - 1024 - 128) / stage_bytes;
-  if (nstage > kMaxStages) nstage = kMaxStages;
-  if (nstage < 2) return -1;
-  const size_t smem = 1024 + 128 + (size_t)nstage * stage_bytes;
+  if (nrows16 <= kMaxSliceRows && !d.grad) {
+    // one pass: the whole test matrix in one CTA's TMEM
+    if (ev) cudaEventRecord(ev[0], st);
+    if (tc_pass(d, c, ncols, split, count, TcPass{d.m, 0, kTagRademacher, 1}, d.rows, vec, nblk, part, npart,
+                max_smem, st) != 0)
+      return -1;
+    if (ev) cudaEventRecord(ev[1], st);
+    tc_reduce_kernel<<<d.rows + 1, 256, 0, st>>>(d, part, npart, nblk, ncols, split, nrows16, n_obs);
+    return 0;
+  }
+  // Several passes over the columns: row slices of the test matrix (at most 512 rows each), then
+  // in gradient mode the gradient field G a (materialized per group) sketched with Omega_g.
   if (ev) cudaEventRecord(ev[0], st);
-  tc_ingest_kernel<<<nblk, kThreads, smem, st>>>(d, c, ncols, split, count, nrows16, n1, n2, per,
-                                                 vec ? 1 : 0, part, npart, nstage, btile);
+  const int nsl = (nrows16 + kMaxSliceRows - 1) / kMaxSliceRows;
+  const int per_sl = ((d.rows + nsl - 1) / nsl + 15) / 16 * 16;
+  for (int sl = 0; sl < nsl; ++sl) {
+    const int rlo = sl * per_sl;
+    const int rc = d.rows - rlo < per_sl ? d.rows - rlo : per_sl;
+    if (rc <= 0) break;
+    if (tc_pass(d, c, ncols, split, count, TcPass{d.m, rlo, kTagRademacher, sl == 0 ? 1 : 0}, rc, vec, nblk, part,
+                npart, max_smem, st) != 0)
+      return -1;
+    tc_reduce_rows_kernel<<<rc, 256, 0, st>>>(part, nblk, ncols, split, (rc + 15) / 16 * 16, rlo, d.S, d.rows,
+                                                n_obs);
+    if (sl == 0) tc_norms_kernel<<<1, 128, 0, st>>>(d, npart, nblk, ncols, nullptr);
+  }
+  if (d.grad) {
+    // Omega_g (G a): the stencil writes the 2m-long gradient fields of the group into gbuf (the
+    // same FP32 arithmetic as the native path), sketched like data with the gradient test matrix
+    const int64_t len = 2 * d.m, ldg = d.gfield_ld;
+    grad_field_kernel<<<2 * d.n_sm, 256, 0, st>>>(d, c, ncols, d.gfield, ldg);
+    Cols gc;
+    for (int q = 0; q < 128; ++q) gc.p[q] = q < ncols ? d.gfield + (size_t)q * ldg : nullptr;
+    const int s16 = (d.s + 15) / 16 * 16;
+    const int gns = (s16 + kMaxSliceRows - 1) / kMaxSliceRows;
+    const int gper = ((d.s + gns - 1) / gns + 15) / 16 * 16;
+    for (int sl = 0; sl < gns; ++sl) {
+      const int rlo = sl * gper;
+      const int rc = d.s - rlo < gper ? d.s - rlo : gper;
+      if (rc <= 0) break;
+      if (tc_pass(d, gc, ncols, split, count, TcPass{len, rlo, kTagGradRademacher, 0}, rc, 1, nblk, part, npart,
+                  max_smem, st) != 0)
+        return -1;
+      tc_reduce_rows_kernel<<<rc, 256, 0, st>>>(part, nblk, ncols, split, (rc + 15) / 16 * 16, rlo, d.glev, d.s,
+                                                  0);
+      if (sl == 0) tc_norms_kernel<<<1, 128, 0, st>>>(d, npart, nblk, ncols, d.gnorm2);
+    }
+    const int n = ncols * d.s;
+    lev_combine_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, ncols, n_obs);
+  }
   if (ev) cudaEventRecord(ev[1], st);
-  tc_reduce_kernel<<<d.rows + 1, 256, 0, st>>>(d, part, npart, nblk, ncols, split, nrows16, n_obs);
   return 0;
 }
 

@@ -75,7 +75,10 @@ def test_gradient_mode_rejects_bad_grids():
     from paper_2405_16076_gb300 import rid
     with pytest.raises(rid.RIDError):
         rid.OnlineRID(m=100, k=5, s=23, h=0, dtype="f64", grad_dims=2, nx=10, ny=9, nfields=1)   # m != nx ny
-    with pytest.raises(rid.RIDError):
-        rid.OnlineRID(m=100, k=5, s=23, h=0, dtype="f32", sketch="bf16x2", grad_dims=2, nx=10, ny=10)
+    with pytest.raises(rid.RIDError):        # E4M3 sketches have no gradient form
+        rid.OnlineRID(m=100, k=5, s=23, h=0, dtype="f32", sketch="fp8x2", grad_dims=2, nx=10, ny=10)
+    with pytest.raises(rid.RIDError):        # the coefficient sketches run on the native path
+        rid.OnlineRID(m=100, k=5, s=23, h=0, dtype="f32", sketch="bf16x2", grad_dims=2, nx=10, ny=10,
+                      grad_coeff=True)
     with pytest.raises(rid.RIDError):
         rid.OnlineRID(m=100, k=5, s=23, h=0, dtype="f64", grad_dims=3, nx=10, ny=10)
