@@ -135,6 +135,15 @@ typedef struct rid_config {
   int64_t m_global;
   rid_allreduce_fn allreduce;
   void* allreduce_user;
+  /* SM partition (0 = off).  With batch_sms > 0 the batch steps' streams run in a CUDA green
+   * context holding at least batch_sms SMs (rounded up to the device's partition granularity),
+   * and the ingest of every batch after the first in a second green context holding the other
+   * SMs, with one CTA per SM of it unless ingest_ctas asks for fewer; the first batch's ingest,
+   * beside which no batch step runs, keeps the whole device.  Neither part then waits for SMs the
+   * other holds.  rid_init fails with RID_ECUDA when the driver offers no green contexts, and with
+   * RID_EINVAL when batch_sms is not below the SM count or the partition cannot co-schedule the
+   * batch step's thread-block clusters.  The results do not depend on it. */
+  int32_t batch_sms;
 } rid_config;
 
 typedef struct rid_handle rid_handle;

@@ -907,6 +907,34 @@ int qr_cluster_size(int m, int t) {
   return best;
 }
 
+// Whether the current context -- a green context's SM partition -- can co-schedule the batch
+// step's thread-block clusters at the sizes tri_cluster_size and qr_cluster_size chose (for s x s
+// sketch Grams and t basis columns).  A partition that cannot would leave their launches waiting.
+bool batch_clusters_fit(int s, int t) {
+  const int ct = tri_cluster_size(s), cq = qr_cluster_size(s, t);
+  if (ct <= 0 || cq <= 0) return false;
+  auto fits = [](const void* fn, int C, size_t smem) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kTriThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0;
+    cudaGetLastError();
+    return ok;
+  };
+  const int ncl = (t + cq - 1) / cq;
+  return fits((const void*)tridiag_cluster_kernel, ct, tri_cluster_smem(s, ct)) &&
+         fits((const void*)qr_cluster_kernel, cq, ((size_t)ncl * (s | 1) + s) * sizeof(double));
+}
+
 int launch_qr_coop(const Dev& d, double* Q4, double* b4, double* h4, double* r4, double* Q6,
                    double* b6, double* h6, double* r6, unsigned int* bar_mem, cudaStream_t st) {
   const int C = qr_cluster_size(d.s, d.t);

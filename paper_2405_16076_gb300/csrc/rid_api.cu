@@ -3,6 +3,7 @@
 // issues the ingest launches and, every t columns, the device batch step.
 // The host never reads device state while ingesting, so a whole stream can
 // be enqueued (or captured) without synchronization.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -77,6 +78,14 @@ struct rid_handle {
   struct TlRec { int batch, phase; cudaEvent_t a, b; };
   std::vector<TlRec> tl;
   float* tg_part;
+  // SM partition (cfg.batch_sms > 0): green contexts of the batch steps' streams (stl, sts, stb,
+  // stg) and of the ingest stream sti, which takes every group after the first batch's
+  CUgreenCtx green_b;
+  CUgreenCtx green_i;
+  cudaStream_t sti;
+  cudaEvent_t ev_ing0;    // on st: the caller's work before an ingest group
+  cudaEvent_t ev_ing1;    // on sti: the ingest group
+  int part_b, part_i;     // SMs of the two partitions
   // per-batch log (rid_log_enable): log_cap slots of kLogSlot bytes on the device, batch b in
   // slot b % log_cap; log_first = the first batch step it covers
   char* log_dev;
@@ -148,12 +157,111 @@ void free_all(Dev& d, void* staging) {
   if (d.Slev && d.Slev != d.S) cudaFree(d.Slev);
 }
 
+// Driver entry points of the green-context calls (SM partition), fetched through the runtime so
+// that the library needs no link against the driver library; ok = all of them were found.
+struct GreenApi {
+  CUresult (*dev_get)(CUdevice*, int) = nullptr;
+  CUresult (*dev_res)(CUdevice, CUdevResource*, CUdevResourceType) = nullptr;
+  CUresult (*split)(CUdevResource*, unsigned int*, const CUdevResource*, CUdevResource*, unsigned int,
+                    unsigned int) = nullptr;
+  CUresult (*gen_desc)(CUdevResourceDesc*, CUdevResource*, unsigned int) = nullptr;
+  CUresult (*create)(CUgreenCtx*, CUdevResourceDesc, CUdevice, unsigned int) = nullptr;
+  CUresult (*destroy)(CUgreenCtx) = nullptr;
+  CUresult (*to_ctx)(CUcontext*, CUgreenCtx) = nullptr;
+  CUresult (*stream_create)(CUstream*, CUgreenCtx, unsigned int, int) = nullptr;
+  CUresult (*stream_destroy)(CUstream) = nullptr;
+  CUresult (*ctx_get)(CUcontext*) = nullptr;
+  CUresult (*ctx_set)(CUcontext) = nullptr;
+  bool ok = false;
+};
+
+const GreenApi& green_api() {
+  static const GreenApi api = [] {
+    GreenApi a;
+    auto get = [](const char* name, void** fn) {
+      cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+      const bool found = cudaGetDriverEntryPointByVersion(name, fn, 13000, cudaEnableDefault, &q) == cudaSuccess &&
+                         q == cudaDriverEntryPointSuccess && *fn != nullptr;
+      cudaGetLastError();
+      return found;
+    };
+    a.ok = get("cuDeviceGet", (void**)&a.dev_get) && get("cuDeviceGetDevResource", (void**)&a.dev_res) &&
+           get("cuDevSmResourceSplitByCount", (void**)&a.split) &&
+           get("cuDevResourceGenerateDesc", (void**)&a.gen_desc) && get("cuGreenCtxCreate", (void**)&a.create) &&
+           get("cuGreenCtxDestroy", (void**)&a.destroy) && get("cuCtxFromGreenCtx", (void**)&a.to_ctx) &&
+           get("cuGreenCtxStreamCreate", (void**)&a.stream_create) &&
+           get("cuStreamDestroy", (void**)&a.stream_destroy) && get("cuCtxGetCurrent", (void**)&a.ctx_get) &&
+           get("cuCtxSetCurrent", (void**)&a.ctx_set);
+    return a;
+  }();
+  return api;
+}
+
+// The SM partition: a green context of at least cfg.batch_sms SMs (a group of the device's SM
+// resource, split so that it keeps the largest thread-block clusters) with the batch steps'
+// streams, and one of the remaining SMs with the ingest stream.  The events stay in the primary
+// context (a green context's stream records them and waits on them like any other).
+int create_partition(rid_handle* h, int prio_hi) {
+  const GreenApi& g = green_api();
+  if (!g.ok) return fail(h, RID_ECUDA, "SM partition: the CUDA driver offers no green contexts");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  CUdevice cd = 0;
+  CUdevResource all = {}, grp = {}, rest = {};
+  unsigned int nb = 1;
+  if (g.dev_get(&cd, dev) != CUDA_SUCCESS || g.dev_res(cd, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS)
+    return fail(h, RID_ECUDA, "SM partition: cannot read the device's SM resource");
+  if ((unsigned int)h->cfg.batch_sms >= all.sm.smCount)
+    return fail(h, RID_EINVAL, "batch_sms must be below the device's SM count");
+  if (g.split(&grp, &nb, &all, &rest, CU_DEV_SM_RESOURCE_SPLIT_MAX_POTENTIAL_CLUSTER_SIZE,
+              (unsigned int)h->cfg.batch_sms) != CUDA_SUCCESS ||
+      nb != 1 || grp.sm.smCount == 0 || rest.sm.smCount == 0)
+    return fail(h, RID_EINVAL, "SM partition: cannot split the SMs at batch_sms");
+  CUdevResourceDesc db = nullptr, di = nullptr;
+  if (g.gen_desc(&db, &grp, 1) != CUDA_SUCCESS || g.gen_desc(&di, &rest, 1) != CUDA_SUCCESS ||
+      g.create(&h->green_b, db, cd, CU_GREEN_CTX_DEFAULT_STREAM) != CUDA_SUCCESS ||
+      g.create(&h->green_i, di, cd, CU_GREEN_CTX_DEFAULT_STREAM) != CUDA_SUCCESS)
+    return fail(h, RID_ECUDA, "SM partition: green-context creation failed");
+  for (cudaStream_t* sp : {&h->stb, &h->stl[0], &h->stl[1], &h->sts, &h->stg}) {
+    CUstream x = nullptr;
+    if (g.stream_create(&x, h->green_b, CU_STREAM_NON_BLOCKING, prio_hi) != CUDA_SUCCESS)
+      return fail(h, RID_ECUDA, "SM partition: stream creation failed");
+    *sp = (cudaStream_t)x;
+  }
+  {
+    CUstream x = nullptr;
+    if (g.stream_create(&x, h->green_i, CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS)
+      return fail(h, RID_ECUDA, "SM partition: stream creation failed");
+    h->sti = (cudaStream_t)x;
+  }
+  h->part_b = (int)grp.sm.smCount;
+  h->part_i = (int)rest.sm.smCount;
+  // the batch step's cluster kernels must be schedulable inside their partition
+  CUcontext prev = nullptr, cb = nullptr;
+  if (g.ctx_get(&prev) != CUDA_SUCCESS || g.to_ctx(&cb, h->green_b) != CUDA_SUCCESS || g.ctx_set(cb) != CUDA_SUCCESS)
+    return fail(h, RID_ECUDA, "SM partition: cannot enter the batch partition's context");
+  const bool fits = rid::batch_clusters_fit(h->d.s, h->d.t);
+  g.ctx_set(prev);
+  if (!fits) return fail(h, RID_EINVAL, "SM partition: batch_sms SMs cannot co-schedule the batch step's clusters");
+  return RID_OK;
+}
+
 void destroy_sync_objects(rid_handle* h) {
-  for (cudaStream_t* sp : {&h->stb, &h->stl[0], &h->stl[1], &h->sts, &h->stg, &h->stc}) {
-    if (*sp) cudaStreamDestroy(*sp);
+  const bool part = h->green_b != nullptr || h->green_i != nullptr;
+  for (cudaStream_t* sp : {&h->stb, &h->stl[0], &h->stl[1], &h->sts, &h->stg, &h->sti}) {
+    if (*sp) {
+      if (part) green_api().stream_destroy((CUstream)*sp);
+      else cudaStreamDestroy(*sp);
+    }
     *sp = nullptr;
   }
-  for (cudaEvent_t* e : {&h->ev_fork, &h->ev_cfork, &h->ev_cfull}) {
+  if (h->stc) cudaStreamDestroy(h->stc);
+  h->stc = nullptr;
+  for (CUgreenCtx* gp : {&h->green_b, &h->green_i}) {
+    if (*gp) green_api().destroy(*gp);
+    *gp = nullptr;
+  }
+  for (cudaEvent_t* e : {&h->ev_fork, &h->ev_cfork, &h->ev_cfull, &h->ev_ing0, &h->ev_ing1}) {
     if (*e) cudaEventDestroy(*e);
     *e = nullptr;
   }
@@ -171,15 +279,24 @@ int create_sync_objects(rid_handle* h) {
   // the critical path, and each of the ingest's CTAs holds a whole SM for its chunk range, so
   // freed SMs should go to them first.
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-  for (cudaStream_t* sp : {&h->stb, &h->stl[0], &h->stl[1], &h->sts, &h->stg})
-    if (cudaStreamCreateWithPriority(sp, cudaStreamNonBlocking, prio_hi) != cudaSuccess) return RID_ECUDA;
-  if (cudaStreamCreateWithFlags(&h->stc, cudaStreamNonBlocking) != cudaSuccess) return RID_ECUDA;
-  for (cudaEvent_t* e : {&h->ev_fork, &h->ev_cfork, &h->ev_cfull})
-    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return RID_ECUDA;
+  if (h->cfg.batch_sms > 0) {
+    const int rc = create_partition(h, prio_hi);
+    if (rc != RID_OK) return rc;
+  } else {
+    for (cudaStream_t* sp : {&h->stb, &h->stl[0], &h->stl[1], &h->sts, &h->stg})
+      if (cudaStreamCreateWithPriority(sp, cudaStreamNonBlocking, prio_hi) != cudaSuccess)
+        return fail(h, RID_ECUDA, "stream creation failed");
+  }
+  if (cudaStreamCreateWithFlags(&h->stc, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(h, RID_ECUDA, "stream creation failed");
+  for (cudaEvent_t* e : {&h->ev_fork, &h->ev_cfork, &h->ev_cfull, &h->ev_ing0, &h->ev_ing1})
+    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(h, RID_ECUDA, "event creation failed");
   for (int i = 0; i < rid_handle::kEv; ++i)
     for (cudaEvent_t* e : {&h->ev_snap[i], &h->ev_lambda[i], &h->ev_scores[i], &h->ev_select[i], &h->ev_gram[i],
                            &h->ev_tail[i]})
-      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return RID_ECUDA;
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess)
+        return fail(h, RID_ECUDA, "event creation failed");
   return RID_OK;
 }
 
@@ -426,40 +543,52 @@ int flush(rid_handle* h) {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (h->prof) for (auto& e : ev) e = next_event(h);
   int nk0 = 0, nk1 = 0;
+  // With an SM partition every group after the first batch's runs on the ingest stream, in the
+  // SMs the batch steps do not use; the caller's stream hands over to it and waits for it.
+  cudaStream_t sg = h->st;
+  if (h->sti && h->batch >= 1) {
+    CK(cudaEventRecord(h->ev_ing0, h->st));
+    CK(cudaStreamWaitEvent(h->sti, h->ev_ing0, 0));
+    sg = h->sti;
+  }
   if (h->tc) {
     const int split = (h->cfg.sketch_prec == RID_SKETCH_BF16X2 || h->cfg.sketch_prec == RID_SKETCH_FP8X2) ? 1 : 0;
     const int fp8 = (h->cfg.sketch_prec == RID_SKETCH_FP8 || h->cfg.sketch_prec == RID_SKETCH_FP8X2) ? 1 : 0;
     // no batch step can run beside the first batch's ingest: it takes the whole grid
     const int nblk = h->batch >= 1 ? h->ingest_blocks : h->first_blocks;
     if (rid::launch_tc_ingest(db, h->pend.data(), G, split, h->count, h->n_obs, nblk,
-                              h->tc_part, h->tc_npart, h->st, h->prof ? ev : nullptr, fp8) != 0)
+                              h->tc_part, h->tc_npart, sg, h->prof ? ev : nullptr, fp8) != 0)
       return fail(h, RID_ECUDA, "tensor-core ingest launch failed");
-    if (db.allreduce && rid::shard_exchange_sketch(db, G, h->n_obs, h->st) != 0)
+    if (db.allreduce && rid::shard_exchange_sketch(db, G, h->n_obs, sg) != 0)
       return fail(h, RID_ECUDA, "row-shard exchange (allreduce) of the sketch failed");
-    rid::launch_gram_update(db, G, h->n_obs, h->st);
+    rid::launch_gram_update(db, G, h->n_obs, sg);
     nk0 = 1;
     nk1 += 2;
   } else {
     for (int q0 = 0; q0 < G; q0 += rid::kMaxB) {
       const int nb = G - q0 < rid::kMaxB ? G - q0 : rid::kMaxB;
       cudaEvent_t* e = (h->prof && q0 == 0) ? ev : nullptr;
-      nk1 += rid::launch_ingest(db, h->pend.data() + q0, nb, h->count + q0, h->n_obs + q0, h->st, e) - 1;
-      if (db.allreduce && rid::shard_exchange_sketch(db, nb, h->n_obs + q0, h->st) != 0)
+      nk1 += rid::launch_ingest(db, h->pend.data() + q0, nb, h->count + q0, h->n_obs + q0, sg, e) - 1;
+      if (db.allreduce && rid::shard_exchange_sketch(db, nb, h->n_obs + q0, sg) != 0)
         return fail(h, RID_ECUDA, "row-shard exchange (allreduce) of the sketch failed");
-      if (db.grad) nk1 += rid::launch_grad(db, h->pend.data() + q0, nb, h->n_obs + q0, h->st);
-      rid::launch_gram_update(db, nb, h->n_obs + q0, h->st);
+      if (db.grad) nk1 += rid::launch_grad(db, h->pend.data() + q0, nb, h->n_obs + q0, sg);
+      rid::launch_gram_update(db, nb, h->n_obs + q0, sg);
       nk0 += 1;
       nk1 += 1;
     }
   }
   // the optional right sketch over the same columns (not part of the paper's method)
   if (db.right_l > 0) {
-    const int nr = rid::launch_right_sketch(db, h->pend.data(), G, h->n_obs, h->st);
+    const int nr = rid::launch_right_sketch(db, h->pend.data(), G, h->n_obs, sg);
     if (nr < 0) return fail(h, RID_ECUDA, "right-sketch launch failed");
     nk1 += nr;
   }
+  if (h->prof) cudaEventRecord(ev[2], sg);
+  if (sg != h->st) {
+    CK(cudaEventRecord(h->ev_ing1, sg));
+    CK(cudaStreamWaitEvent(h->st, h->ev_ing1, 0));
+  }
   if (h->prof) {
-    cudaEventRecord(ev[2], h->st);
     h->spans[0].push_back({ev[0], ev[1]});
     h->spans[1].push_back({ev[1], ev[2]});
     h->tl.push_back({h->batch, rid::TLP_INGEST, ev[0], ev[2]});
@@ -506,6 +635,7 @@ int check_config(const rid_config* c) {
   if (c->group_max < 0 || c->group_max > rid::kMaxGroup) return fail(h, RID_EINVAL, "group_max must be in [0, 64]");
   if (c->right_l < 0 || c->right_l > 4096) return fail(h, RID_EINVAL, "right_l must be in [0, 4096]");
   if (c->ingest_ctas < 0) return fail(h, RID_EINVAL, "ingest_ctas must be >= 0");
+  if (c->batch_sms < 0) return fail(h, RID_EINVAL, "batch_sms must be >= 0");
   if (c->refill_mode != RID_REFILL_FIRST && c->refill_mode != RID_REFILL_PROPORTIONAL)
     return fail(h, RID_EINVAL, "unknown refill_mode");
   if (c->lookahead != 0 && (c->lookahead < 2 || c->lookahead > 4))
@@ -745,9 +875,15 @@ int rid_init(rid_handle** out, const rid_config* c) {
   }
   h->dslot_buf = d.dslot_all;
   d.dslot = d.dslot_all;
-  if (create_sync_objects(h) != RID_OK) {
-    rc = RID_ECUDA;
-    goto fail_alloc;
+  rc = create_sync_objects(h);
+  if (rc != RID_OK) goto fail_alloc;
+  if (h->sti) {
+    // one ingest CTA per SM of its partition (fewer if ingest_ctas asks), the basis Gram on the
+    // batch partition's SMs; the partial buffers were sized for the larger whole-device counts
+    h->ingest_blocks = c->ingest_ctas > 0 && c->ingest_ctas < h->part_i ? c->ingest_ctas : h->part_i;
+    if (h->ingest_blocks > h->first_blocks) h->ingest_blocks = h->first_blocks;
+    if (h->tc_blocks > h->part_b) h->tc_blocks = h->part_b;
+    d.tc_blocks = h->tc_blocks;
   }
   if (d.omega_kind == 0) rid::launch_materialize_omega(d, h->st);
   rid::launch_reset_state(d, h->st);
@@ -1353,7 +1489,7 @@ void rid_destroy(rid_handle* h) {
   if (!h) return;
   join(h);
   cudaStreamSynchronize(h->st);
-  for (cudaStream_t x : {h->stb, h->stl[0], h->stl[1], h->sts, h->stg, h->stc})
+  for (cudaStream_t x : {h->stb, h->stl[0], h->stl[1], h->sts, h->stg, h->stc, h->sti})
     if (x) cudaStreamSynchronize(x);
   for (auto e : h->evpool) cudaEventDestroy(e);
   if (h->tl_base) cudaEventDestroy(h->tl_base);

@@ -194,6 +194,8 @@ int tc_smem_bytes();
 // Basis Gram of the new x target pool slots on tensor cores (FP32 pool); returns the
 // number of kernels launched, or -1.  part holds nblk x 512 x 128 floats.
 int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st);
+// Whether the current context can co-schedule the batch step's cluster kernels (coop.cu).
+bool batch_clusters_fit(int s, int t);
 void launch_materialize_omega(const Dev& d, cudaStream_t st);
 
 // Timeline events of one batch step (recorded only while profiling; tl may be null).

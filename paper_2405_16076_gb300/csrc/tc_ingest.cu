@@ -1278,19 +1278,24 @@ __global__ void __launch_bounds__(256) tc_reduce_rows_kernel(const float* __rest
     dst[(size_t)(col0 + q) * ldd + rlo + r] = ((red[0][q] + red[1][q]) + red[2][q]) + red[3][q];
 }
 
-// The group's squared norms (split-K blocks in order): with out == nullptr added to ||A_obs||^2
-// and to the leverage norm in column order, else stored in out.
-__global__ void tc_norms_kernel(Dev d, const double* __restrict__ npart, int nblk, int ncols, double* out) {
-  if (threadIdx.x != 0) return;
-  for (int c = 0; c < ncols; ++c) {
+// The group's squared norms (split-K blocks in order, one thread per column): with out ==
+// nullptr added to ||A_obs||^2 and to the leverage norm in column order, else stored in out.
+__global__ void __launch_bounds__(128) tc_norms_kernel(Dev d, const double* __restrict__ npart, int nblk, int ncols,
+                                                      double* out) {
+  __shared__ double nv[128];
+  const int c = threadIdx.x;
+  if (c < ncols) {
     double v = 0.0;
     for (int b = 0; b < nblk; ++b) v += npart[(size_t)b * 128 + c];
-    if (out) {
-      out[c] = v;
-      continue;
-    }
+    if (out) out[c] = v;
+    nv[c] = v;
+  }
+  __syncthreads();
+  if (out || c != 0) return;
+  for (int q = 0; q < ncols; ++q) {
+    const double v = nv[q];
     if (d.gnorm) {                            // row shard: summed over the shards first
-      d.gnorm[c] = v;
+      d.gnorm[q] = v;
       continue;
     }
     if (!isfinite(v)) atomicOr(d.err, ERR_NONFINITE);
@@ -1299,21 +1304,47 @@ __global__ void tc_norms_kernel(Dev d, const double* __restrict__ npart, int nbl
   }
 }
 
+// One entry of G a with grad_stencil's weights (central inside, one-sided at either end of the
+// line of length len, position c along it, neighbours st apart) in the native path's FP32
+// arithmetic and order: the centre product first, then the lower and the upper neighbour.
+__device__ __forceinline__ float stencil_fp32(const float* __restrict__ a, int64_t i, int64_t st, int c, int len) {
+  if (c == 0) {
+    float v = -1.0f * a[i];
+    v += 1.0f * a[i + st];
+    return v;
+  }
+  if (c == len - 1) {
+    float v = 1.0f * a[i];
+    v += -1.0f * a[i - st];
+    return v;
+  }
+  float v = 0.0f * a[i];
+  v += -0.5f * a[i - st];
+  v += 0.5f * a[i + st];
+  return v;
+}
+
 // Gradient mode (Sec. 3.4, Eqs. 38-43): the stacked gradient fields G a_q (2m entries each, the
-// x then the y differences of every field) into g (column q at g + q ldg), by grad_stencil with
-// the native path's FP32 arithmetic.
-__global__ void grad_field_kernel(Dev d, Cols c, int ncols, float* __restrict__ g, int64_t ldg) {
-  const int64_t dm = 2 * d.m;
-  const int64_t n = (int64_t)ncols * dm;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(idx / dm);
-    const int64_t j = idx - (int64_t)q * dm;
-    const GradStencil gs = grad_stencil(j, d.m, d.nx, d.ny);
+// x then the y differences of every field) into g (column q at g + q ldg).  A CTA takes one grid
+// line (field f, row y) of one column at a time, so an entry's position along its line (x) and
+// down its field (y) come from the loop indices: no division per entry.  Loads and stores are
+// coalesced along the line; the neighbouring lines' loads hit L1/L2.
+__global__ void __launch_bounds__(256) grad_field_kernel(Dev d, Cols c, int ncols, float* __restrict__ g, int64_t ldg) {
+  const int nx = d.nx, ny = d.ny;
+  const int lines = d.nfields * ny;               // grid lines of one column (m = lines nx)
+  const int64_t nline = (int64_t)lines * ncols;
+  for (int64_t lb = blockIdx.x; lb < nline; lb += gridDim.x) {
+    const int q = (int)(lb / lines);
+    const int line = (int)(lb - (int64_t)q * lines);
+    const int y = line % ny;
     const float* a = c.p[q];
-    float v = (float)gs.wc * a[gs.i];
-    if (gs.wm != 0.0) v += (float)gs.wm * a[gs.i - gs.st];
-    if (gs.wp != 0.0) v += (float)gs.wp * a[gs.i + gs.st];
-    g[(size_t)q * ldg + j] = v;
+    const int64_t i0 = (int64_t)line * nx;
+    float* gx = g + (size_t)q * ldg + i0;         // x differences: entries i0 .. i0 + nx - 1
+    float* gy = gx + d.m;                         // y differences: entries m + i0 ..
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      gx[x] = stencil_fp32(a, i0 + x, 1, x, nx);
+      gy[x] = stencil_fp32(a, i0 + x, nx, y, ny);
+    }
   }
 }
 
@@ -1429,7 +1460,7 @@ int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split
     // Omega_g (G a): the stencil writes the 2m-long gradient fields of the group into gbuf (the
     // same FP32 arithmetic as the native path), sketched like data with the gradient test matrix
     const int64_t len = 2 * d.m, ldg = d.gfield_ld;
-    grad_field_kernel<<<2 * d.n_sm, 256, 0, st>>>(d, c, ncols, d.gfield, ldg);
+    grad_field_kernel<<<8 * d.n_sm, 256, 0, st>>>(d, c, ncols, d.gfield, ldg);
     Cols gc;
     for (int q = 0; q < 128; ++q) gc.p[q] = q < ncols ? d.gfield + (size_t)q * ldg : nullptr;
     const int s16 = (d.s + 15) / 16 * 16;

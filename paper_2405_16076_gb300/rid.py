@@ -38,7 +38,7 @@ class rid_config(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p), ("right_l", ctypes.c_int32), ("grad_coeff", ctypes.c_int32),
         ("ingest_ctas", ctypes.c_int32), ("refill_mode", ctypes.c_int32), ("lookahead", ctypes.c_int32),
         ("row_offset", ctypes.c_int64), ("m_global", ctypes.c_int64), ("allreduce", ctypes.c_void_p),
-        ("allreduce_user", ctypes.c_void_p),
+        ("allreduce_user", ctypes.c_void_p), ("batch_sms", ctypes.c_int32),
     ]
 
 
@@ -232,7 +232,7 @@ def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_cons
                 lambda_mode="streaming", lambda_fixed=0.0, omega="rademacher", dtype="f32",
                 sketch="native", n_max=1024, seed=0, stream=None, group_max=0, defer=False,
                 grad_dims=0, nx=0, ny=0, nfields=1, right_l=0, grad_coeff=False, ingest_ctas=0, refill="first",
-                lookahead=0, row_offset=0, m_global=0, allreduce=None):
+                lookahead=0, row_offset=0, m_global=0, allreduce=None, batch_sms=0):
     """An rid_config from keyword arguments (the defaults of rid_config_default otherwise)."""
     cfg = rid_config()
     _check(rid_config_default(ctypes.byref(cfg)))
@@ -254,6 +254,7 @@ def make_config(m, k, s, h=0, *, c1=1 / 6, c2=1 / 3, eps=0.5, delta=0.05, c_cons
     cfg.ingest_ctas = int(ingest_ctas)
     cfg.refill_mode = {"first": RID_REFILL_FIRST, "proportional": RID_REFILL_PROPORTIONAL}[refill]
     cfg.lookahead = int(lookahead)
+    cfg.batch_sms = int(batch_sms)
     cfg.row_offset = int(row_offset)
     cfg.m_global = int(m_global)
     if allreduce is not None:                 # a RID_ALLREDUCE_FN; the caller keeps it alive
@@ -284,7 +285,8 @@ class OnlineRID:
     def __init__(self, m, k, s, h=0, **kw):
         """Keyword arguments as make_config: c1, c2, eps, delta, c_const, lambda_mode,
         lambda_fixed, omega, dtype, sketch, n_max, seed, stream, group_max, defer, grad_dims,
-        nx, ny, nfields, right_l, grad_coeff, ingest_ctas, refill ("first" or "proportional"), lookahead, and for a row shard
+        nx, ny, nfields, right_l, grad_coeff, ingest_ctas, refill ("first" or "proportional"), lookahead,
+        batch_sms (SMs of the batch steps' partition, 0 = no partition), and for a row shard
         row_offset, m_global and allreduce (a RID_ALLREDUCE_FN)."""
         cfg = make_config(m, k, s, h, **kw)
         self._allreduce = kw.get("allreduce")     # the callback must outlive the handle

@@ -102,6 +102,9 @@ def test_config_check_matches_init_validation(lib):
     assert b"FP32" in rid.rid_last_error(None)
     cfg = rid.make_config(100, 10, 43, 12, group_max=65)
     assert rid.rid_config_check(ctypes.byref(cfg)) == rid.RID_EINVAL
+    cfg = rid.make_config(100, 10, 43, 12, batch_sms=-1)
+    assert rid.rid_config_check(ctypes.byref(cfg)) == rid.RID_EINVAL
+    assert b"batch_sms" in rid.rid_last_error(None)
     cfg = rid.make_config(100, 10, 43, 12, ingest_ctas=-1)
     assert rid.rid_config_check(ctypes.byref(cfg)) == rid.RID_EINVAL
     assert b"ingest_ctas" in rid.rid_last_error(None)
