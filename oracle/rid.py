@@ -138,42 +138,90 @@ def sketched_ridge_scores(SSt_scaled, lam, V):
     return np.einsum("ij,ij->j", V, X)
 
 
-def css_update(cfg, batch, JC, tau_old, tau_C, JD, tau_D, margins=None):
+def css_update(cfg, batch, JC, tau_old, tau_C, JD, tau_D, margins=None, target=None, flips=None):
     """Prune and refill the basis slots (Algorithm 3, following Cohen et al.; R7, R8).
 
     JC, tau_old are updated copies; tau_C are min(tau_old, scores of C) for the
     occupied slots; JD, tau_D the buffered columns and their scores.  If
     ``margins`` is a list, the relative distance of every decision's score
     from the score at which that decision would flip is appended to it.
+
+    Re-synchronisation (test use only): with ``target`` (the slot contents another
+    implementation chose at this step) each slot whose outcome differs from target's
+    takes target's outcome before the next slot is decided, and (slot, kind, margin)
+    of the decision that differed is appended to ``flips`` -- kind "prune" for the
+    keep-or-prune draw, "refill" for the first buffered column whose acceptance draw
+    went the other way, "draw" for R7p's proportional pick.  The decisions of the
+    later slots are then taken on the same state as target's.
     """
     JC = JC.copy()
     tau_old = tau_old.copy()
     scale = refill_scale(cfg)
     for i in range(cfg.t):
+        old = int(JC[i])
+        prune_margin = None
         if JC[i] >= 0:
             u = float(philox.uniform(cfg.seed, batch, i, 0))
-            if margins is not None and tau_C[i] > 0:
-                margins.append(abs(u - (1.0 - tau_C[i] / tau_old[i])) * tau_old[i] / tau_C[i])
+            if tau_C[i] > 0:
+                prune_margin = abs(u - (1.0 - tau_C[i] / tau_old[i])) * tau_old[i] / tau_C[i]
+                if margins is not None:
+                    margins.append(prune_margin)
             if u < 1.0 - tau_C[i] / tau_old[i]:
                 JC[i] = -1
                 tau_old[i] = 1.0
             else:
                 tau_old[i] = tau_C[i]
-        if JC[i] < 0:
+        kept = JC[i] >= 0
+        tgt_kept = target is not None and old >= 0 and int(target[i]) == old
+        if target is not None and old >= 0 and kept != tgt_kept:
+            # the keep-or-prune draw of slot i went the other way in target
+            flips.append((i, "prune", prune_margin if prune_margin is not None else 0.0))
+            if tgt_kept:
+                JC[i] = old
+                tau_old[i] = tau_C[i]
+            else:
+                JC[i] = -1
+                tau_old[i] = 1.0
+                kept = False
+        if not kept:
             hit = None
+            rmargins = []
             for r in range(len(JD)):
                 p = min(max(tau_D[r] * scale, 0.0), 1.0)
                 u = float(philox.uniform(cfg.seed, batch, i, 1 + r))
+                rm = abs(u - p) / p if (p < 1.0 and tau_D[r] > 0) else float("inf")
                 if margins is not None and p < 1.0 and tau_D[r] > 0:
-                    margins.append(abs(u - p) / p)
+                    margins.append(rm)
+                rmargins.append(rm)
                 if u < p and JD[r] not in JC:
                     hit = r
                     break
+            first = hit
+            dmargins = [] if flips is not None else margins
+            cand = [r for r in range(len(JD)) if JD[r] not in JC]      # R7p's candidates, in order
             if hit is not None and cfg.refill == "proportional":
-                hit = proportional_draw(cfg, batch, i, JC, JD, tau_D, hit, margins)
+                hit = proportional_draw(cfg, batch, i, JC, JD, tau_D, hit, dmargins)
+                if margins is not None and dmargins is not margins:
+                    margins.extend(dmargins)
             if hit is not None:
                 JC[i] = JD[hit]
                 tau_old[i] = tau_D[hit]
+            if target is not None and int(JC[i]) != int(target[i]):
+                want = int(target[i])
+                if want >= 0 and want not in JD:
+                    raise ValueError(f"target slot {i} holds column {want}, neither kept nor buffered at step {batch}")
+                rt = JD.index(want) if want in JD else None
+                if cfg.refill == "proportional" and first is not None and rt is not None:
+                    # both accepted a refill; the pick went the other way at the boundary of the
+                    # cumulative scores between the two picks
+                    kb = min(cand.index(hit), cand.index(rt)) if (hit in cand and rt in cand) else 0
+                    flips.append((i, "draw", dmargins[kb] if kb < len(dmargins) else 0.0))
+                else:
+                    # the first buffered column whose acceptance draw differs from target's
+                    cut = min(x for x in (first, rt) if x is not None) if (first is not None or rt is not None) else 0
+                    flips.append((i, "refill", rmargins[cut] if cut < len(rmargins) else 0.0))
+                JC[i] = want
+                tau_old[i] = tau_D[rt] if rt is not None else 1.0
     return JC, tau_old
 
 
@@ -294,6 +342,8 @@ class OnlineRID:
         self._omega = None
         self._omega_g = None
         self.margins = []
+        self.resync = None          # test use: {batch: slot contents to re-synchronise to}
+        self.flips = []             # (batch, slot, kind, margin) of the decisions re-synchronised
         self.Y = np.zeros((cfg.m, cfg.right_l)) if cfg.right_l > 0 else None
         self.SG = None                              # d x s x n_obs: Omega G^p A_obs (unit variance)
 
@@ -391,7 +441,11 @@ class OnlineRID:
         JD = list(self.JD)
         tau_D = sketched_ridge_scores(SSt_scaled, lam, Vlev[:, JD])
         JC_prev = self.JC.copy()
-        JC, tau_old = css_update(c, self.batch, self.JC, self.tau_old, tau_C, JD, tau_D, self.margins)
+        target = self.resync.get(self.batch) if self.resync else None
+        flips = [] if target is not None else None
+        JC, tau_old = css_update(c, self.batch, self.JC, self.tau_old, tau_C, JD, tau_D, self.margins, target, flips)
+        if flips:
+            self.flips.extend((self.batch,) + f for f in flips)
 
         # Coefficient candidates over the active slots (R11)
         act = np.nonzero(JC >= 0)[0]

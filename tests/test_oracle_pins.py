@@ -597,3 +597,68 @@ def test_fp8x2_split_error_bound_and_sketch():
     S = fp8.sketch_fp8x2(om, a, block)
     assert np.allclose(S, om @ (hi + lo), rtol=0, atol=1e-12 * np.abs(om @ a).max())
     assert np.abs(S - om @ a).max() <= 2.0 ** -8 * np.abs(om).max() * np.abs(a).sum(axis=0).max() * 1.01
+
+
+def _stream_with_history(seed, refill="first"):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((300, 8)) @ rng.standard_normal((8, 60)) + 0.05 * rng.standard_normal((300, 60))
+    cfg = RIDConfig(m=300, k=10, s=23, h=9, seed=seed, refill=refill)
+    o = OnlineRID(cfg)
+    o.ingest(A)
+    J, P = o.finalize()
+    return A, cfg, o, J, P
+
+
+@pytest.mark.parametrize("refill", ["first", "proportional"])
+def test_resync_to_own_decisions_changes_nothing(refill):
+    """Re-synchronising the selection to the oracle's own per-step slot contents records no
+    differing decision and reproduces J, P and the estimates exactly."""
+    A, cfg, o, J, P = _stream_with_history(3, refill)
+    o2 = OnlineRID(cfg)
+    o2.resync = {r.batch: r.JC for r in o.history}
+    o2.ingest(A)
+    J2, P2 = o2.finalize()
+    assert o2.flips == []
+    assert np.array_equal(J, J2) and np.array_equal(P, P2)
+    assert np.array_equal(o.error_estimates()[0], o2.error_estimates()[0])
+
+
+def test_resync_reports_the_planted_prune_and_refill_differences():
+    """A planted difference in the target (a kept slot pruned; a refill with another buffered
+    column) is reported as the decision that differs, with that decision's own margin, the step
+    takes the target's slot contents, and the later steps run on them."""
+    A, cfg, o, J, P = _stream_with_history(5)
+    hist = {r.batch: r.JC.copy() for r in o.history}
+    b = 2                                            # a step with earlier basis elements
+    prev = hist[b - 1]
+    kept_slots = [i for i in range(cfg.t) if prev[i] >= 0 and hist[b][i] == prev[i]]
+    assert kept_slots
+    i = kept_slots[0]
+    target = hist[b].copy()
+    target[i] = -1                                   # plant: slot i pruned instead of kept
+    o3 = OnlineRID(cfg)
+    o3.resync = {k: v for k, v in hist.items() if k < b}
+    o3.resync[b] = target                            # the later steps decide on the synced state
+    o3.ingest(A)
+    o3.finalize()
+    # the keep-or-prune draw of slot i differs; the slot's refill scan, which then runs on the
+    # pruned slot, may differ from the planted empty slot too -- nothing else does
+    assert (o3.flips[0][0], o3.flips[0][1], o3.flips[0][2]) == (b, i, "prune")
+    assert all(f[0] == b and f[1] == i for f in o3.flips) and len(o3.flips) <= 2
+    assert o3.history[b].JC[i] == -1
+    assert o3.flips[0][3] > 0.0
+    # a different refill: slot j refilled with another of the step's buffered columns
+    refilled = [j for j in range(cfg.t) if hist[b][j] >= 0 and hist[b][j] != prev[j]]
+    if refilled:
+        j = refilled[0]
+        batch_cols = set(range(b * cfg.t, (b + 1) * cfg.t))
+        others = sorted(batch_cols - set(int(x) for x in hist[b]))
+        target2 = hist[b].copy()
+        target2[j] = others[0]
+        o4 = OnlineRID(cfg)
+        o4.resync = {k: v for k, v in hist.items() if k < b}
+        o4.resync[b] = target2
+        o4.ingest(A)
+        o4.finalize()
+        assert (b, j, "refill") in [(f[0], f[1], f[2]) for f in o4.flips]
+        assert o4.history[b].JC[j] == others[0]

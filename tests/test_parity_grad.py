@@ -48,9 +48,15 @@ def run_both(A, nx, ny, nfields, **kw):
     g = rid.OnlineRID(m=m, k=kw["k"], s=kw["s"], h=kw["h"], dtype="f64", omega=kw["omega_kind"],
                       seed=kw["seed"], n_max=n, grad_dims=2, nx=nx, ny=ny, nfields=nfields)
     src = torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
+    jcs, t = [], kw["k"]
     for j0 in range(0, n, 5):
         g.ingest(src[j0:j0 + 5])
+        while len(jcs) < min(j0 + 5, n) // t:              # selections per batch step, for re-syncs
+            jcs.append(g.state(rid.RID_STATE_JC).copy())
     Jg, Pg = g.finalize()
+    if n % t:
+        jcs.append(Jg.copy())
+    g.jcs, g.okw = jcs, dict(kw, grad_op=G)
     return o, Jo, Po, g, Jg, Pg
 
 
