@@ -3,20 +3,24 @@ launch configuration.
 
 The stream: 11 fields on a 1024 x 1024 grid (m = 11,534,336), n = 2000 snapshots ingested in
 blocks of 8 from device memory (grouped up to 64 columns), k = t = 150, s = 603, h = 50, FP32
-data on the native-precision path, gradient mode (Sec. 3.4: the ridge scores use the sketch of
-[a; G a] with its own Omega_g), the data and sketch seeds of the benchmark's first rank.  As in
-the channel-flow module, the oracle computes sampled outputs one by one and the rest is checked
-by properties that hold at any size:
+data, BF16x2 tensor-core sketches, gradient mode (Sec. 3.4: the ridge scores use the sketch of
+[a; G a] with its own Omega_g; the tensor cores sketch the m data coordinates in two row slices
+of the 653 rows and the 2m entries of G a, formed in FP32 per group, in two slices of the 603),
+the data and sketch seeds of the benchmark's first rank -- the benchmark's launch configuration.
+As in the channel-flow module, the oracle computes sampled outputs one by one and the rest is
+checked by properties that hold at any size:
 
 * sampled entries of the plain sketch (first sketch row, first and last probe rows) and of the
   leverage sketch Omega a + Omega_g (G a) (first and last rows), for snapshots in the first and
   last groups and batches, against the oracle's rows of Omega and Omega_g and its gradient
-  operator, in FP64.  Bar 1e-5 of the column's norm (||a|| or (||a||^2 + ||G a||^2)^(1/2)): the
-  FP32 sketch sums runs of 1024 signed terms in FP32 before FP64 (relative error ~1e-6 of the
-  norm at this m), the bar of the small FP32 parity test;
+  operator, in FP64.  Bar 2e-5 of ||a|| for the plain sketch -- the BF16x2 bar of the channel
+  module (the split leaves at most 2^-16 of each value; the FP32 accumulation in TMEM adds less
+  over the ~110 k coordinates of one CTA's range) -- and 3e-5 of (||a||^2 + ||G a||^2)^(1/2) for
+  the leverage sketch, the sum of two such sketches (2e-5 (||a|| + ||G a||) <= 2e-5 sqrt(2) of
+  that norm), the gradient's accumulating twice as many coordinates per CTA;
 * the same rows for every snapshot at once through a seeded +-1 combination c (linearity:
-  S[R] c = Omega[R] (A c), S_lev[R] c = Omega[R] (A c) + Omega_g[R] G (A c)), bar 1e-5 of the
-  combined norm;
+  S[R] c = Omega[R] (A c), S_lev[R] c = Omega[R] (A c) + Omega_g[R] G (A c)), with the same bars
+  of the combined norms;
 * ||A_obs||^2 within 1e-6 and ||A_obs||^2 + ||G A_obs||^2 within 1e-5 of FP64 sums (the GPU
   forms G a in FP32);
 * bit-exact basis copies and valid indices; the last batch's Algorithm 4 candidate against the
@@ -41,7 +45,8 @@ from oracle import philox
 from oracle.gradient import grid_gradient_operator
 from oracle.rid import coeff_alg4
 
-BAR = 1e-5
+BAR = 2e-5          # plain sketch, of ||a||
+BAR_LEV = 3e-5      # leverage sketch, of (||a||^2 + ||G a||^2)^(1/2)
 
 
 def grad_stencil(F):
@@ -93,7 +98,7 @@ def ignition_run():
         gen.block(j0, min(50, n - j0), out=X[j0:j0 + 50])
     torch.cuda.synchronize()
     st = torch.cuda.Stream(device=dev)
-    g = rid.OnlineRID(m=m, k=k, s=s, h=h, dtype="f32", sketch="native", n_max=n, seed=sketch_seed,
+    g = rid.OnlineRID(m=m, k=k, s=s, h=h, dtype="f32", sketch="bf16x2", n_max=n, seed=sketch_seed,
                       stream=st, defer=True, group_max=64, grad_dims=2, nx=N, ny=N, nfields=nf)
     for j0 in range(0, n, b):
         g.ingest(X[j0:j0 + b])
@@ -175,9 +180,9 @@ def test_ignition_full_size_sampled_sketches_against_oracle(ignition_run):
     assert err.max() <= BAR, err
     ref_lev = ref[:2] + refg                          # rows 0 and s - 1
     err_lev = np.abs(L[np.ix_(lrows, cols)] - ref_lev[:, :-1]) / nrm_lev[None, :]
-    assert err_lev.max() <= BAR, err_lev
+    assert err_lev.max() <= BAR_LEV, err_lev
     assert np.abs(S[rows] @ c - ref[:, -1]).max() <= BAR * math.sqrt(r["fro2"])
-    assert np.abs(L[lrows] @ c - ref_lev[:, -1]).max() <= BAR * math.sqrt(r["fro2_lev"])
+    assert np.abs(L[lrows] @ c - ref_lev[:, -1]).max() <= BAR_LEV * math.sqrt(r["fro2_lev"])
 
 
 @pytest.mark.gpu
