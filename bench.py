@@ -57,6 +57,17 @@ CONFIGS = {
 }
 
 
+def ingest_kernel_hash(src_path):
+    """SHA-256 of the source the ingest kernel's DRAM counters depend on: tc_ingest.cu from its
+    start through the end of tc_ingest_kernel (the helpers it calls come before it) and the
+    counter-based generator it includes.  Later code in the file does not change that kernel."""
+    text = open(src_path, "rb").read()
+    start = text.index(b"tc_ingest_kernel(Dev d,")
+    end = text.index(b"\n}\n", start) + 3
+    gen = open(os.path.join(os.path.dirname(src_path), "philox.cuh"), "rb").read()
+    return hashlib.sha256(text[:end] + gen).hexdigest()
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -849,8 +860,7 @@ def main():
     if args.sketch != "native" and os.path.exists(tr_path):
         try:
             tr = json.load(open(tr_path))
-            src_hash = hashlib.sha256(open(src_path, "rb").read()).hexdigest()
-            if tr.get("tc_ingest_cu_sha256") == src_hash:
+            if tr.get("ingest_kernel_sha256") == ingest_kernel_hash(src_path):
                 traffic = tr["dram_bytes_per_column_coordinate"] * cols_per_launch * m
         except Exception:
             traffic = None

@@ -1327,9 +1327,12 @@ __device__ __forceinline__ float stencil_fp32(const float* __restrict__ a, int64
 // Gradient mode (Sec. 3.4, Eqs. 38-43): the stacked gradient fields G a_q (2m entries each, the
 // x then the y differences of every field) into g (column q at g + q ldg).  A CTA takes one grid
 // line (field f, row y) of one column at a time, so an entry's position along its line (x) and
-// down its field (y) come from the loop indices: no division per entry.  Loads and stores are
-// coalesced along the line; the neighbouring lines' loads hit L1/L2.
-__global__ void __launch_bounds__(256) grad_field_kernel(Dev d, Cols c, int ncols, float* __restrict__ g, int64_t ldg) {
+// down its field (y) come from the loop indices: no division per entry.  With vec (16-byte
+// aligned columns, nx a multiple of 4) a thread takes four consecutive entries of the line: one
+// 16-byte load of the line and of each neighbouring line, the two neighbours along the line from
+// L1, 16-byte stores; otherwise one entry per thread.
+__global__ void __launch_bounds__(256) grad_field_kernel(Dev d, Cols c, int ncols, float* __restrict__ g, int64_t ldg,
+                                                         int vec) {
   const int nx = d.nx, ny = d.ny;
   const int lines = d.nfields * ny;               // grid lines of one column (m = lines nx)
   const int64_t nline = (int64_t)lines * ncols;
@@ -1341,9 +1344,39 @@ __global__ void __launch_bounds__(256) grad_field_kernel(Dev d, Cols c, int ncol
     const int64_t i0 = (int64_t)line * nx;
     float* gx = g + (size_t)q * ldg + i0;         // x differences: entries i0 .. i0 + nx - 1
     float* gy = gx + d.m;                         // y differences: entries m + i0 ..
-    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-      gx[x] = stencil_fp32(a, i0 + x, 1, x, nx);
-      gy[x] = stencil_fp32(a, i0 + x, nx, y, ny);
+    if (vec) {
+      for (int x = 4 * threadIdx.x; x < nx; x += 4 * blockDim.x) {
+        const float4 cv = *reinterpret_cast<const float4*>(a + i0 + x);
+        const float v[4] = {cv.x, cv.y, cv.z, cv.w};
+        const float left = x > 0 ? a[i0 + x - 1] : 0.f;          // read only where used
+        const float right = x + 4 < nx ? a[i0 + x + 4] : 0.f;
+        float ox[4], oy[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int xe = x + e;
+          const float lo = e > 0 ? v[e - 1] : left, hi = e < 3 ? v[e + 1] : right;
+          // grad_stencil's weights in the native path's FP32 order (centre, lower, upper)
+          if (xe == 0) { float t = -1.0f * v[e]; t += 1.0f * hi; ox[e] = t; }
+          else if (xe == nx - 1) { float t = 1.0f * v[e]; t += -1.0f * lo; ox[e] = t; }
+          else { float t = 0.0f * v[e]; t += -0.5f * lo; t += 0.5f * hi; ox[e] = t; }
+        }
+        const float4 dn = y > 0 ? *reinterpret_cast<const float4*>(a + i0 + x - nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 up = y < ny - 1 ? *reinterpret_cast<const float4*>(a + i0 + x + nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float vd[4] = {dn.x, dn.y, dn.z, dn.w}, vu[4] = {up.x, up.y, up.z, up.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (y == 0) { float t = -1.0f * v[e]; t += 1.0f * vu[e]; oy[e] = t; }
+          else if (y == ny - 1) { float t = 1.0f * v[e]; t += -1.0f * vd[e]; oy[e] = t; }
+          else { float t = 0.0f * v[e]; t += -0.5f * vd[e]; t += 0.5f * vu[e]; oy[e] = t; }
+        }
+        *reinterpret_cast<float4*>(gx + x) = make_float4(ox[0], ox[1], ox[2], ox[3]);
+        *reinterpret_cast<float4*>(gy + x) = make_float4(oy[0], oy[1], oy[2], oy[3]);
+      }
+    } else {
+      for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        gx[x] = stencil_fp32(a, i0 + x, 1, x, nx);
+        gy[x] = stencil_fp32(a, i0 + x, nx, y, ny);
+      }
     }
   }
 }
@@ -1460,7 +1493,8 @@ int launch_tc_ingest(const Dev& d, const void* const* colp, int ncols, int split
     // Omega_g (G a): the stencil writes the 2m-long gradient fields of the group into gbuf (the
     // same FP32 arithmetic as the native path), sketched like data with the gradient test matrix
     const int64_t len = 2 * d.m, ldg = d.gfield_ld;
-    grad_field_kernel<<<8 * d.n_sm, 256, 0, st>>>(d, c, ncols, d.gfield, ldg);
+    const int gvec = vec && d.nx % 4 == 0 && ldg % 4 == 0 && d.m % 4 == 0;
+    grad_field_kernel<<<8 * d.n_sm, 256, 0, st>>>(d, c, ncols, d.gfield, ldg, gvec ? 1 : 0);
     Cols gc;
     for (int q = 0; q < 128; ++q) gc.p[q] = q < ncols ? d.gfield + (size_t)q * ldg : nullptr;
     const int s16 = (d.s + 15) / 16 * 16;
