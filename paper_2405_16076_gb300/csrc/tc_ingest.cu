@@ -657,8 +657,22 @@ __device__ __forceinline__ bool gram_merged(int nnew, int ntgt) {
   return nnew > 64 && nnew <= 128 && ntgt <= 128;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ part, int nstage) {
+// Warp roles of the basis Gram: warp 0 issues the MMAs, warps 1..16 convert, warps 17..28 load.
+constexpr int kGramLoadWarp = 1 + kProducerWarps;
+constexpr int kGramLoadWarps = 12;
+constexpr int kGramAllThreads = 32 * (1 + kProducerWarps + kGramLoadWarps);
+constexpr int kGramMaxStages = 8;                       // barrier slots of the staging ring
+constexpr uint32_t kGramStageArea = 3u * kGramRowsMax * 128u;   // 192 KB of stages
+
+// The targets' FP32 chunks are staged by asynchronous copies: warp 17 copies each target's chunk
+// to byte 256 y of the stage (target y), completing on the stage's load barrier, as soon as the
+// MMAs are done with the stage; the converters read the stage, meet at a
+// named barrier, and write the BF16 hi / lo rows of the MMA tile over the same bytes (the FP32
+// chunk of ntgt targets and its hi + lo tile take the same room).  The stage size follows the
+// device-side target count: nbrows x 128 bytes, so that smaller counts keep more chunks in
+// flight (up to kGramMaxStages within kGramStageArea).
+__global__ void __launch_bounds__(kGramAllThreads, 1)
+tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ part) {
   extern __shared__ uint8_t smem_raw[];
   const int nnew = d.meta[META_NNEW], ntgt_all = d.meta[META_NTGT];
   if (x0 >= nnew || ntgt_all <= 0) return;              // uniform over the CTA, before any TMEM use
@@ -671,16 +685,18 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
   const int ybase = merged ? 0 : x0;
   const int ntgt = ntgt_all - ybase;
   const int nbrows = 128 * ((ntgt + 63) / 64);            // B rows in use (multiple of 128, <= 512)
-  const uint32_t btile = (uint32_t)kGramRowsMax * 128u;
+  const uint32_t btile = (uint32_t)nbrows * 128u;         // >= 256 ntgt: the FP32 chunk fits
+  int nstage = (int)(kGramStageArea / btile);
+  if (nstage > kGramMaxStages) nstage = kGramMaxStages;
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t sB = base;
-  const uint32_t sBar = sB + (uint32_t)nstage * btile;  // full[4], empty[4], done
+  const uint32_t sBar = sB + kGramStageArea;              // full[8], empty[8], loaded[8], done; slot offsets
   uint8_t* gbar = gbase + (sBar - base);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 96);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 104);
-  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 32, bar_done = sBar + 64;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 208);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 216);
+  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 64, bar_load0 = sBar + 128, bar_done = sBar + 192;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nchunks = (d.m + kChunkK - 1) / kChunkK;
   const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
@@ -691,6 +707,7 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
     for (int i = 0; i < nstage; ++i) {
       mbar_init(bar_full0 + 8 * i, 32 * kProducerWarps);
       mbar_init(bar_empty0 + 8 * i, 1);
+      mbar_init(bar_load0 + 8 * i, 32 * kGramLoadWarps);   // one arrival per loader thread
     }
     mbar_init(bar_done, 1);
     *abort_flag = 0;
@@ -736,49 +753,86 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
       tc_commit(bar_done);
     }
     __syncwarp();
-  } else {
-    // producer thread pt moves, for u = 0..3, coordinates 8g..8g+7 of target y = (pt + 512u) / 8
-    const int pt = threadIdx.x - 32;
+  } else if (warp >= kGramLoadWarp) {
+    // ---------------------------------------------------------------- loads: 16-byte async copies
+    // (ntgt x 16 of them per chunk, about 13 per lane for 100 targets), each lane's completing on
+    // the stage's load barrier (128 arrivals); 256-byte bulk copies, one per target, were measured
+    // 2.7x slower (the copy engine's cost per transfer dominates at that size), and one loader
+    // warp 1.7x slower (its issue rate).
+    const int lt = threadIdx.x - 32 * kGramLoadWarp;        // loader thread 0..127
     const float* pool = (const float*)d.pool;
-    const int g = pt & 7;
-    const int y0t = pt >> 3;                              // target of round u: y0t + 64 u
-    int slot[4];                                          // pool slot, or -1 past the targets
-#pragma unroll
-    for (int u = 0; u < 4; ++u) slot[u] = (y0t + 64 * u < ntgt) ? d.gtgt[ybase + y0t + 64 * u] : -1;
-#define GSRC(u) (pool + (int64_t)slot[u] * d.m_pad)
-    float4 bufA[4][2], bufB[4][2];
-    auto load_chunk = [&](int64_t c, float4 (&v)[4][2]) {
-      if (c >= nch) return;
-      const int64_t i = (c0 + c) * kChunkK + 8 * g;        // < m_pad: the slot tail beyond m is zero
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (slot[u] < 0) continue;
-        const float4* s4 = reinterpret_cast<const float4*>(GSRC(u) + i);
-        v[u][0] = __ldcs(s4);
-        v[u][1] = __ldcs(s4 + 1);
-        if (g == 0 && c + kL2Ahead < nch) prefetch_l2(GSRC(u) + (c0 + c + kL2Ahead) * kChunkK, kChunkK * 4);
+    int64_t* soff = reinterpret_cast<int64_t*>(gbar + 256);   // element offset of each target's slot
+    for (int y = lt; y < ntgt; y += 32 * kGramLoadWarps) soff[y] = (int64_t)d.gtgt[ybase + y] * d.m_pad;
+    asm volatile("bar.sync 2, %0;" ::"n"(32 * kGramLoadWarps) : "memory");
+    int st = 0;
+    uint32_t epar = 1u;                                   // first pass over the ring: stages start empty
+    for (int64_t c = 0; c < nch; ++c) {
+      // every lane waits (the same barrier and phase), so the warp leaves the loop together
+      const bool okw = mbar_wait(bar_empty0 + 8 * st, epar, abort_flag, d.err, d.ring_wait_limit);
+      if (!__all_sync(0xffffffffu, okw)) break;
+      const uint32_t dst = sB + st * btile;
+      const int64_t off = (c0 + c) * kChunkK;               // < m_pad: the slot tail beyond m is zero
+      for (int idx = lt; idx < ntgt * 16; idx += 32 * kGramLoadWarps) {
+        const int y = idx >> 4, seg = idx & 15;
+        const float* src = pool + soff[y] + off + 4 * seg;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)y * 256u + 16u * seg),
+                     "l"(src)
+                     : "memory");
       }
-    };
-    int pst = 0;
-    uint32_t ppar = 1u;
-    auto process = [&](const float4 (&v)[4][2]) -> bool {
-      const int st = pst;
-      if (!mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err, d.ring_wait_limit)) return false;
-      if (++pst == nstage) { pst = 0; ppar ^= 1u; }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar_load0 + 8 * st) : "memory");
+      if (++st == nstage) { st = 0; epar ^= 1u; }
+    }
+    // no copy may still be landing when the CTA exits
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- converters (warps 1..16)
+    // thread pt converts, for u = 0..3, coordinates 8g..8g+7 of target y = y0t + 64 u
+    const int pt = threadIdx.x - 32;
+    const int g = pt & 7;
+    const int y0t = pt >> 3;
+    int st = 0;
+    uint32_t lpar = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+      const bool okw = mbar_wait(bar_load0 + 8 * st, lpar, abort_flag, d.err, d.ring_wait_limit);
       const uint32_t bst = sB + st * btile;
+      float x[4][8];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (slot[u] < 0) continue;
+        const int y = y0t + 64 * u;
+        if (okw && y < ntgt) {
+          const float* rp = reinterpret_cast<const float*>(gbase + (bst - base) + (uint32_t)y * 256u + 32u * g);
+          const float4 a0 = *reinterpret_cast<const float4*>(rp);
+          const float4 a1 = *reinterpret_cast<const float4*>(rp + 4);
+          x[u][0] = a0.x; x[u][1] = a0.y; x[u][2] = a0.z; x[u][3] = a0.w;
+          x[u][4] = a1.x; x[u][5] = a1.y; x[u][6] = a1.z; x[u][7] = a1.w;
+        }
+      }
+      // every converter has read its FP32 values before any writes the tile over them; the
+      // barrier also takes the AND of the waits, so that all converters leave together
+      uint32_t all_ok;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\t"
+          "setp.ne.u32 q, %1, 0;\n\t"
+          "bar.red.and.pred p, 1, %2, q;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(all_ok)
+          : "r"(okw ? 1u : 0u), "n"(32 * kProducerWarps)
+          : "memory");
+      if (!all_ok) break;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int y = y0t + 64 * u;
+        if (y >= ntgt) continue;
         const int rhi = 128 * u + y0t;                    // hi row of target y0t + 64 u
-        const float x[8] = {v[u][0].x, v[u][0].y, v[u][0].z, v[u][0].w, v[u][1].x, v[u][1].y, v[u][1].z, v[u][1].w};
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[u][2 * j], x[u][2 * j + 1]);
           const uint32_t hv = *reinterpret_cast<const uint32_t*>(&h2);
           hw[j] = hv;
-          const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * j] - __uint_as_float(hv << 16),
-                                                          x[2 * j + 1] - __uint_as_float(hv & 0xFFFF0000u));
+          const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[u][2 * j] - __uint_as_float(hv << 16),
+                                                          x[u][2 * j + 1] - __uint_as_float(hv & 0xFFFF0000u));
           lw[j] = *reinterpret_cast<const uint32_t*>(&l2);
         }
         sts128(bst + sw128_off(rhi, g), hw[0], hw[1], hw[2], hw[3]);
@@ -786,23 +840,8 @@ tc_gram_all_kernel(Dev d, int x0, int64_t chunks_per_cta, float* __restrict__ pa
       }
       fence_async_smem();
       mbar_arrive(bar_full0 + 8 * st);
-      return true;
-    };
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (slot[u] >= 0 && g == 0)
-        for (int64_t c = 2; c < kL2Ahead && c < nch; ++c) prefetch_l2(GSRC(u) + (c0 + c) * kChunkK, kChunkK * 4);
-    load_chunk(0, bufA);
-    load_chunk(1, bufB);
-    for (int64_t c = 0; c < nch; c += 2) {
-      if (!process(bufA)) break;
-      load_chunk(c + 2, bufA);
-      if (c + 1 < nch) {
-        if (!process(bufB)) break;
-        load_chunk(c + 3, bufB);
-      }
+      if (++st == nstage) { st = 0; lpar ^= 1u; }
     }
-#undef GSRC
     if (warp <= 4) {
       const bool ok = mbar_wait(bar_done, 0, abort_flag, d.err);
       tc_fence_after();
@@ -890,13 +929,11 @@ int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st) {
         return -1;
       max_smem = v;
     }
-    const int stage_bytes = kGramRowsMax * 128;
-    int nstage = (max_smem - 1024 - 128) / stage_bytes;
-    if (nstage > kMaxStages) nstage = kMaxStages;
-    if (nstage < 2) return -1;
-    const size_t smem = 1024 + 128 + (size_t)nstage * stage_bytes;
+    // align slack + barriers + the targets' slot offsets (256 x 8 bytes) + stages
+    const size_t smem = 1024 + 256 + 2048 + (size_t)kGramStageArea;
+    if (smem > (size_t)max_smem) return -1;
     for (int x0 = 0; x0 < d.t; x0 += 64) {
-      tc_gram_all_kernel<<<nblk, kThreads, smem, st>>>(d, x0, per, part, nstage);
+      tc_gram_all_kernel<<<nblk, kGramAllThreads, smem, st>>>(d, x0, per, part);
       tc_gram_all_reduce_kernel<<<2 * d.t, 256, 0, st>>>(d, part, nblk, x0);
       nk += 2;
     }
