@@ -797,16 +797,27 @@ def main():
         fma_peak = nsm * 128 * float(pk0.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12     # FP32 TFMA/s
         r_bytes = 2.0 * 4 * m * rl + 4.0 * m * G                                       # Y read + write, A read
         r_fma = float(m) * rl * G
-        right = {"bound": "alu", "kernel": "right_sketch_kernel", "cols_per_launch": G, "l": rl,
-                 "avg_launch_ms": r_ms, "achieved": r_fma / (r_ms / 1e3) / 1e12, "peak": fma_peak,
-                 "unit": "TFMA/s", "frac": r_fma / (r_ms / 1e3) / 1e12 / fma_peak,
-                 "hbm": {"achieved": r_bytes / (r_ms / 1e3) / 1e9, "peak": pk0.get("hbm_gbs"), "unit": "GB/s",
-                         "frac": r_bytes / (r_ms / 1e3) / 1e9 / pk0.get("hbm_gbs")},
-                 "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x {pk0.get('sm_max_mhz', 2070.0)} MHz "
-                                "(FP32 FMA); HBM: measured (MEASURED_PEAKS.json)",
-                 "note": "Y += A_group W over m x l: l FMAs per coordinate and column (FP32 pipe) against "
-                         "2 x 4 m l bytes of Y per group; timed alone as the difference between one group "
-                         "ingested with and without the right sketch"}
+        if args.sketch != "native":
+            # tensor-core handles (a +-1 W) take the BF16x2 tcgen05 form: bound by Y's traffic
+            right = {"bound": "hbm", "kernel": "tc_right_kernel", "cols_per_launch": G, "l": rl,
+                     "avg_launch_ms": r_ms, "achieved": r_bytes / (r_ms / 1e3) / 1e9, "peak": pk0.get("hbm_gbs"),
+                     "unit": "GB/s", "frac": r_bytes / (r_ms / 1e3) / 1e9 / pk0.get("hbm_gbs"),
+                     "fma": {"achieved": r_fma / (r_ms / 1e3) / 1e12, "unit": "TFMA/s"},
+                     "peak_source": "measured (MEASURED_PEAKS.json)",
+                     "note": "Y += A_group W over m x l on tensor cores (BF16x2 split of the data, +-1 W): "
+                             "2 x 4 m l bytes of Y and 4 m G of data per group; timed alone as the difference "
+                             "between one group ingested with and without the right sketch"}
+        else:
+            right = {"bound": "alu", "kernel": "right_sketch_kernel", "cols_per_launch": G, "l": rl,
+                     "avg_launch_ms": r_ms, "achieved": r_fma / (r_ms / 1e3) / 1e12, "peak": fma_peak,
+                     "unit": "TFMA/s", "frac": r_fma / (r_ms / 1e3) / 1e12 / fma_peak,
+                     "hbm": {"achieved": r_bytes / (r_ms / 1e3) / 1e9, "peak": pk0.get("hbm_gbs"), "unit": "GB/s",
+                             "frac": r_bytes / (r_ms / 1e3) / 1e9 / pk0.get("hbm_gbs")},
+                     "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x {pk0.get('sm_max_mhz', 2070.0)} MHz "
+                                    "(FP32 FMA); HBM: measured (MEASURED_PEAKS.json)",
+                     "note": "Y += A_group W over m x l: l FMAs per coordinate and column (FP32 pipe) against "
+                             "2 x 4 m l bytes of Y per group; timed alone as the difference between one group "
+                             "ingested with and without the right sketch"}
 
     # The same stream through the other sketch precisions, for the accuracy-throughput comparison
     # (one warm-up and one timed pass each; the plain FP32 form runs on the FP32 pipe)

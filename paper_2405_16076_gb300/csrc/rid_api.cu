@@ -856,6 +856,9 @@ int rid_init(rid_handle** out, const rid_config* c) {
     d.Y = y;
     AL(wr, rid::right_w_bytes(d));
     d.Wr = wr;
+    // tensor-core handles with FP32 data and a +-1 test matrix take the right sketch on tcgen05
+    // (BF16x2: ~2^-16 of each value, the accuracy of the FP32 sums), the others the FP32/FP64 pipe
+    d.tc_right = (h->tc && d.dtype == 1 && d.omega_kind == 1) ? 1 : 0;
     if (cudaMemset(d.Y, 0, (size_t)d.m_pad * d.right_l * h->esize) != cudaSuccess) { rc = RID_ECUDA; goto fail_alloc; }
   }
   d.gbar2 = d.gbar + 4;

@@ -95,6 +95,7 @@ struct Dev {
   unsigned int* gbar;             // grid-barrier words of the cooperative kernels
   int n_sm;
   int tc_blocks;                  // CTAs of the tensor-core kernels
+  int tc_right;                   // 1: the right sketch runs on tensor cores (FP32 data, +-1 W)
   float* tc_part;                 // ingest partial accumulators (tc_blocks x max(rows16, 256) x 128 floats)
   float* tg_part;                 // basis-Gram partial accumulators (tc_blocks x 512 x 128 floats)
   unsigned int* gbar2;            // grid-barrier words of the batch-step stream's cooperative kernels
@@ -194,6 +195,9 @@ int tc_smem_bytes();
 // Basis Gram of the new x target pool slots on tensor cores (FP32 pool); returns the
 // number of kernels launched, or -1.  part holds nblk x 512 x 128 floats.
 int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st);
+// The optional right sketch of a group of <= 64 FP32 columns on tensor cores (BF16x2, +-1 W given
+// as G x lw FP32 values in W); returns the kernels launched, or -1.
+int launch_tc_right(const Dev& d, const void* const* cols, int ncols, const float* W, int lw, cudaStream_t st);
 // Whether the current context can co-schedule the batch step's cluster kernels (coop.cu).
 bool batch_clusters_fit(int s, int t);
 void launch_materialize_omega(const Dev& d, cudaStream_t st);

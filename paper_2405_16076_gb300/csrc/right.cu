@@ -155,6 +155,14 @@ int launch_right_t(const Dev& d, const void* const* cols, int ncols, int64_t j0,
     T* W = reinterpret_cast<T*>(d.Wr);
     right_w_kernel<T><<<(G * lw + 255) / 256, 256, 0, st>>>(d, j0 + q0, G, lw, W);
     nk += 1;
+    if constexpr (sizeof(T) == 4) {
+      if (d.tc_right) {
+        const int nt = launch_tc_right(d, cols + q0, G, reinterpret_cast<const float*>(W), lw, st);
+        if (nt < 0) return -1;
+        nk += nt;
+        continue;
+      }
+    }
     for (int rb = 0; rb < d.right_l; rb += kRBlock) {
       const int rl = d.right_l - rb < kRBlock ? d.right_l - rb : kRBlock;
       right_sketch_kernel<T><<<grid, kRThreads, smem, st>>>(d, c, G, lw, W, rb, rl, vec);

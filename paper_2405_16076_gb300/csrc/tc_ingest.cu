@@ -126,6 +126,14 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 // Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16).
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -949,6 +957,210 @@ int launch_tc_gram(const Dev& d, int nblk, float* part, cudaStream_t st) {
 }
 
 int tc_smem_bytes() { return kSmemBytes; }
+
+// ---------------------------------------------------------------- right sketch on tensor cores
+// Y(:, rb .. rb + rl - 1) += A_group W(:, rb .. rb + rl - 1) for a group of G <= 64 FP32 columns
+// and a +-1 W (the optional right sketch; not part of the paper's method).  MMA mapping
+// (kind::f16, FP32 accumulation): M = 128 coordinates of a tile, N = nW >= rl sketch columns
+// (a multiple of 16, <= 256), K = the group's columns, split a = hi + lo: one K block of 64
+// columns for the hi parts and one for the lo parts, both against the same B tile (W^T rows,
+// +-1 exact in BF16).  The CTA is persistent over its tiles of 128 coordinates: 16 producer
+// warps transpose each tile into the K-major A tiles (thread: one coordinate, 16 columns; every
+// warp writes 32 consecutive rows of one 16-byte chunk, conflict-free), the MMA warp fills one of
+// two TMEM accumulators, and the same 16 warps then add the accumulator to Y (lane = coordinate:
+// coalesced 128-byte rows of each Y column) -- so Y is read and written once per group, the
+// bound of this update (2 x 4 m l bytes per group against 4 m G of data).
+constexpr int kRtTile = 128;                          // coordinates per tile
+constexpr int kRtStages = 3;
+constexpr uint32_t kRtATile = 128u * 128u;            // 128 rows x 64 BF16
+constexpr uint32_t kRtBTile = 256u * 128u;            // up to 256 W rows x 64 BF16
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_right_kernel(Dev d, Cols cols, int G, const float* __restrict__ Wg, int lw, int rb, int rl, int nW) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t sW = base;                                         // B tile
+  const uint32_t sA = sW + kRtBTile;                                // stages: A hi, A lo
+  const uint32_t sBar = sA + (uint32_t)kRtStages * 2u * kRtATile;   // full[3], empty[3], tfull[2], tempty[2]
+  uint8_t* gbar = gbase + (sBar - base);
+  const float** colptr = reinterpret_cast<const float**>(gbar + 128);   // the group's 64 column pointers
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbar + 96);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbar + 104);
+  const uint32_t bar_full0 = sBar, bar_empty0 = sBar + 24, bar_tfull0 = sBar + 48, bar_tempty0 = sBar + 64;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m = d.m, ldy = d.m_pad;
+  const int64_t ntiles = (m + kRtTile - 1) / kRtTile;
+  const int64_t nmine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kRtStages; ++i) {
+      mbar_init(bar_full0 + 8 * i, 32 * kProducerWarps);
+      mbar_init(bar_empty0 + 8 * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar_tfull0 + 8 * i, 1);
+      mbar_init(bar_tempty0 + 8 * i, 32 * kProducerWarps);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 64) colptr[threadIdx.x] = threadIdx.x < G ? cols.p[threadIdx.x] : nullptr;
+  // the B tile: row n = sketch column rb + n, K entry q = W(q, rb + n), zero past G and rl
+  for (int idx = threadIdx.x; idx < nW * 8; idx += blockDim.x) {
+    const int n = idx >> 3, ch = idx & 7;            // 16-byte chunk ch: columns 8 ch .. 8 ch + 7
+    uint32_t w4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int q0 = 8 * ch + 2 * e;
+      const float v0 = (q0 < G && n < rl) ? Wg[q0 * lw + rb + n] : 0.f;
+      const float v1 = (q0 + 1 < G && n < rl) ? Wg[(q0 + 1) * lw + rb + n] : 0.f;
+      w4[e] = pack_bf16(v0, v1);
+    }
+    sts128(sW + sw128_off(n, ch), w4[0], w4[1], w4[2], w4[3]);
+  }
+  fence_async_smem();
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t id = idesc_bf16(128, nW);
+      const uint64_t db = desc_sw128(sW);
+      int st = 0;
+      uint32_t par = 0;
+      for (int64_t t = 0; t < nmine; ++t) {
+        const int buf = (int)(t & 1);
+        const uint32_t tpar = (uint32_t)(((t >> 1) & 1) ^ 1);   // the buffers start empty
+        if (!mbar_wait(bar_tempty0 + 8 * buf, tpar, abort_flag, d.err, d.ring_wait_limit)) break;
+        if (!mbar_wait(bar_full0 + 8 * st, par, abort_flag, d.err, d.ring_wait_limit)) break;
+        tc_fence_after();
+        const uint32_t sst = sA + (uint32_t)st * 2u * kRtATile;
+        const uint32_t dcol = tmem + (uint32_t)(256 * buf);
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb) {
+          const uint64_t da = desc_sw128(sst + (uint32_t)kb * kRtATile);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 2);            // +32 bytes along K
+            tc_mma(dcol, da + adv, db + adv, id, (kb > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        tc_commit(bar_empty0 + 8 * st);
+        tc_commit(bar_tfull0 + 8 * buf);
+        if (++st == kRtStages) { st = 0; par ^= 1u; }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- producers, then epilogue
+    const int pt = threadIdx.x - 32;                  // 0..511
+    const int rr = pt & 127;                          // coordinate (A row) of this thread
+    const int qb = pt >> 7;                           // columns 16 qb .. 16 qb + 15
+    const int quarter = warp & 3, cq = (warp - 1) >> 2;  // TMEM lanes 32 quarter .., column chunks cq, cq + 4, ..
+    int st = 0;
+    uint32_t ppar = 1u;                               // stages start empty
+    bool ok = true;
+    auto produce = [&](int64_t t) -> bool {
+      if (!mbar_wait(bar_empty0 + 8 * st, ppar, abort_flag, d.err, d.ring_wait_limit)) return false;
+      const int64_t i = (int64_t)(blockIdx.x + t * gridDim.x) * kRtTile + rr;
+      float v[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int q = 16 * qb + e;
+        v[e] = (q < G && i < m) ? __ldcs(colptr[q] + i) : 0.f;
+      }
+      const uint32_t sst = sA + (uint32_t)st * 2u * kRtATile;
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {                // chunk 2 qb + h2: columns 16 qb + 8 h2 ..
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float x0 = v[8 * h2 + 2 * e], x1 = v[8 * h2 + 2 * e + 1];
+          const __nv_bfloat162 hb = __floats2bfloat162_rn(x0, x1);
+          const uint32_t hv = *reinterpret_cast<const uint32_t*>(&hb);
+          hw[e] = hv;
+          const __nv_bfloat162 lb = __floats2bfloat162_rn(x0 - __uint_as_float(hv << 16),
+                                                          x1 - __uint_as_float(hv & 0xFFFF0000u));
+          lw[e] = *reinterpret_cast<const uint32_t*>(&lb);
+        }
+        sts128(sst + sw128_off(rr, 2 * qb + h2), hw[0], hw[1], hw[2], hw[3]);
+        sts128(sst + kRtATile + sw128_off(rr, 2 * qb + h2), lw[0], lw[1], lw[2], lw[3]);
+      }
+      fence_async_smem();
+      mbar_arrive(bar_full0 + 8 * st);
+      if (++st == kRtStages) { st = 0; ppar ^= 1u; }
+      return true;
+    };
+    auto epilogue = [&](int64_t t) -> bool {
+      const int buf = (int)(t & 1);
+      const uint32_t fpar = (uint32_t)((t >> 1) & 1);
+      if (!mbar_wait(bar_tfull0 + 8 * buf, fpar, abort_flag, d.err, d.ring_wait_limit)) return false;
+      tc_fence_after();
+      const int64_t i = (int64_t)(blockIdx.x + t * gridDim.x) * kRtTile + 32 * quarter + lane;
+      const uint32_t taddr = tmem + (uint32_t)(256 * buf) + ((uint32_t)(32 * quarter) << 16);
+      float* __restrict__ Y = reinterpret_cast<float*>(d.Y) + (int64_t)rb * ldy;
+      for (int cb = 16 * cq; cb < nW; cb += 64) {     // 16 columns per load; 4 warps share a lane quarter
+        uint32_t r[16];
+        tc_ld16(taddr + (uint32_t)cb, r);
+        tc_wait_ld();
+        if (i < ldy) {                                 // rows m .. m_pad - 1 of Y stay 0 (the data is 0 there)
+          float y[16];                                 // 16 loads in flight, then their 16 stores
+#pragma unroll
+          for (int j = 0; j < 16; ++j) y[j] = cb + j < rl ? Y[(int64_t)(cb + j) * ldy + i] : 0.f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (cb + j < rl) Y[(int64_t)(cb + j) * ldy + i] = y[j] + __uint_as_float(r[j]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(bar_tempty0 + 8 * buf);
+      return true;
+    };
+    // tile t's epilogue runs after tile t + 1 is staged, so that the MMAs of t + 1 overlap it
+    for (int64_t t = 0; t < nmine && ok; ++t) {
+      ok = produce(t);
+      if (ok && t >= 1) ok = epilogue(t - 1);
+    }
+    if (ok && nmine >= 1) epilogue(nmine - 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+int launch_tc_right(const Dev& d, const void* const* colp, int ncols, const float* W, int lw, cudaStream_t st) {
+  const size_t smem = 1024 + kRtBTile + (size_t)kRtStages * 2 * kRtATile + 128 + 512;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tc_right_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return -1;
+    attr = true;
+  }
+  if (ncols > 64) return -1;
+  Cols c;
+  for (int q = 0; q < 128; ++q) c.p[q] = q < ncols ? (const float*)colp[q] : nullptr;
+  const int64_t ntiles = (d.m + kRtTile - 1) / kRtTile;
+  const int grid = (int)(ntiles < d.n_sm ? ntiles : d.n_sm);
+  int nk = 0;
+  for (int rb = 0; rb < d.right_l; rb += 256) {
+    const int rl = d.right_l - rb < 256 ? d.right_l - rb : 256;
+    const int nW = (rl + 15) / 16 * 16;
+    tc_right_kernel<<<grid, kThreads, smem, st>>>(d, c, ncols, W, lw, rb, rl, nW);
+    ++nk;
+  }
+  return nk;
+}
 
 // ---------------------------------------------------------------- FP8 (E4M3, block-scaled) ingest
 // The same sketch S(:, q) = Omega a_q with the data quantized to E4M3 with one power-of-two scale

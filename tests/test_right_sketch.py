@@ -1,9 +1,11 @@
 """The optional right sketch Y = sum_j a_j omega_j^T (m x l; not part of the paper's method).
 
 GPU against the oracle on the same seeded stream: FP64 within 1e-12 of max|Y| (the same
-additions in the same snapshot order, fused multiply-adds on the GPU); FP32 data (plain and
-tensor-core sketches: Y is always FP32 SIMT) within 1e-5 x (|A| |W|) entrywise, the bound of
-n FP32 roundings of the running sums.  Also: l > 256 (two column blocks), reset, checkpoint and
+additions in the same snapshot order, fused multiply-adds on the GPU); FP32 data within
+1e-5 x (|A| |W|) entrywise: on the native path the bound of n FP32 roundings of the running sums;
+on tensor-core handles (a +-1 W) the BF16x2 split leaves at most 2^-18 of each value per term
+(3.8e-6) and each group's FP32 accumulation and its FP32 addition to Y add rounding of the same
+order, within the same bound.  Also: l > 256 (two column blocks), reset, checkpoint and
 restore, and the error for a handle without a right sketch.
 """
 import numpy as np
