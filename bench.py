@@ -606,9 +606,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sketch", default="bf16x2", choices=["bf16x2", "bf16", "fp8x2", "fp8", "native"])
-    ap.add_argument("--group", type=int, default=64,
+    ap.add_argument("--group", type=int, default=0,
                     help="columns per sketch launch (1..64); 0 = measure it and the CTAs per launch "
-                         "with rid_autotune on the first 2k snapshots before the timed region")
+                         "with rid_autotune on the first 8k snapshots before the timed region")
     ap.add_argument("--grad-coeff", action="store_true",
                     help="gradient mode: keep Omega G^p a and report Sec. 3.4's gradient-augmented coefficients")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
@@ -657,8 +657,10 @@ def main():
         gkw["grad_coeff"] = True
     tune = None
     if args.group == 0:
-        # the group size measured on this stream's first two batches, outside the timed region
-        ntune = min(n, 2 * cfg["k"])
+        # the launch shape measured on this stream's first eight batches, outside the timed region:
+        # enough for the batch steps that run beside the ingest in the steady state to weigh in (on
+        # two batches the ingest runs almost alone and every SM looks best)
+        ntune = min(n, 8 * cfg["k"])
         gbest, cbest, us = rid.autotune_group(X[:ntune], m, cfg["k"], cfg["s"], cfg["h"], dtype="f32",
                                               sketch=args.sketch, seed=rank_seeds(rank)[1], stream=st,
                                               right_l=cfg.get("right_l", 0), **gkw)
