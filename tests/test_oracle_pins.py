@@ -662,3 +662,91 @@ def test_resync_reports_the_planted_prune_and_refill_differences():
         o4.finalize()
         assert (b, j, "refill") in [(f[0], f[1], f[2]) for f in o4.flips]
         assert o4.history[b].JC[j] == others[0]
+
+
+# ---------------------------------------------------------------- Algorithm 1 (residual CSS)
+from oracle.residual_css import ResidualCSS
+
+
+def _rank_stream(m, n, r, seed, dependent_every=3):
+    """Columns that are either a new random direction or a combination of earlier columns."""
+    rng = np.random.default_rng(seed)
+    cols, independent = [], []
+    for j in range(n):
+        if j % dependent_every == dependent_every - 1 and cols:
+            c = np.stack(cols, axis=1) @ rng.standard_normal(len(cols))
+        elif len(independent) < r:
+            c = rng.standard_normal(m)
+            independent.append(j)
+        else:
+            c = np.stack(cols, axis=1) @ rng.standard_normal(len(cols))
+        cols.append(c)
+    return np.stack(cols, axis=1), independent
+
+
+def test_residual_css_tiny_xi_selects_the_greedy_independent_columns():
+    """With xi far below every nonzero residual, p >= 1 for each column outside the span (selected
+    and added at once) and p ~ 0 for the columns inside it: the selection is the first maximal
+    independent set in arrival order, checked by brute-force rank counts."""
+    A, _ = _rank_stream(60, 40, 9, 3)
+    o = ResidualCSS(60, k=5, xi=1e-20 * np.linalg.norm(A) ** 2, seed=1)
+    o.ingest(A)
+    brute = []
+    for j in range(A.shape[1]):
+        if np.linalg.matrix_rank(A[:, brute + [j]], tol=1e-8 * np.linalg.norm(A)) > len(brute):
+            brute.append(j)
+    assert list(o.selection()) == brute
+    assert len(brute) == 9
+
+
+def test_residual_css_huge_xi_selects_nothing_and_never_updates():
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((50, 30))
+    o = ResidualCSS(50, k=4, xi=1e9 * 4 * np.linalg.norm(A) ** 2, seed=3)
+    o.ingest(A)
+    assert len(o.selection()) == 0 and o.steps == []
+    assert abs(o.sigma - sum(o.p)) <= 1e-15 * max(sum(o.p), 1e-300)
+
+
+def test_residual_css_first_column_kept_with_probability_p():
+    """The first column meets an empty C_pre: p = k ||a||^2 / xi, set to 0.3; over 4000 seeds it is
+    kept with frequency 0.3 (4 sigma of the binomial)."""
+    a = np.random.default_rng(5).standard_normal((20, 1))
+    k = 3
+    xi = k * float(a[:, 0] @ a[:, 0]) / 0.3
+    hits = 0
+    for seed in range(4000):
+        o = ResidualCSS(20, k=k, xi=xi, seed=seed)
+        o.ingest(a)
+        assert abs(o.p[0] - 0.3) <= 1e-12
+        hits += len(o.selection())
+    assert abs(hits / 4000 - 0.3) <= 4 * np.sqrt(0.3 * 0.7 / 4000)
+
+
+def test_residual_css_residual_mass_and_forced_updates():
+    """Orthonormal columns with p = 0.4 each: sigma reaches 1.2 at the third, which ends the step;
+    a column with p >= 1 ends a step at once and is always kept."""
+    m = 8
+    E = np.eye(m)
+    k = 2
+    xi = k / 0.4                                   # p = k ||e||^2 / xi = 0.4 outside span(C_pre)
+    o = ResidualCSS(m, k=k, xi=xi, seed=7)
+    o.ingest(E[:, :3])
+    assert o.steps == [2] and o.sigma == 0.0
+    o.ingest(E[:, 3:4])
+    assert abs(o.sigma - 0.4) <= 1e-15
+    o.ingest(3.0 * E[:, 4:5])                      # p = 2 * 9 / 5 = 3.6 >= 1
+    assert o.steps == [2, 4] and 4 in o.selection() and o.sigma == 0.0
+
+
+def test_residual_css_recovers_a_rank_r_stream():
+    """A rank-5 stream with xi far below its energy: every column outside the span ends a step,
+    so span(C) is the stream's range: ||A - Q Q^T A|| at rounding level."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((200, 5)) @ rng.standard_normal((5, 300))
+    o = ResidualCSS(200, k=5, xi=1e-8 * np.linalg.norm(A) ** 2, seed=2)
+    o.ingest(A)
+    Q = o.Q
+    assert Q.shape[1] == 5
+    assert np.linalg.norm(A - Q @ (Q.T @ A)) <= 1e-10 * np.linalg.norm(A)
+    assert np.abs(Q.T @ Q - np.eye(5)).max() <= 1e-12
