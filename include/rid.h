@@ -438,6 +438,58 @@ int rid_sketch_noalloc(const rid_config* cfg, const void* cols, int64_t ld, int3
 /* Free everything.  NULL is ignored. */
 void rid_destroy(rid_handle* h);
 
+/* ---- Online column subset selection by residual-based sampling ----------------------------
+ * The paper's Algorithm 1 (Sec. 2.2.1, after Bhaskara et al.), the online selector the accuracy
+ * tables compare the single-pass ID against; it is not a step of the ID (Algorithm 3).  For each
+ * arriving column a, numbered j = 0, 1, ... over the handle's life:
+ *   p_a = k ||Pi_perp a||^2 / xi, Pi_perp the projector onto the orthogonal complement of the
+ *         span of the previously selected columns C_pre (||a||^2 - ||Q^T a||^2 with Q an
+ *         orthonormal basis of that span, FP64 sums);
+ *   a joins C_cur if u_j < min(p_a, 1), u_j the 53-bit uniform of the Philox4x32-10 block at
+ *         counter (j mod 2^32, j >> 32, 0x52435331, 0) and key (seed mod 2^32, seed >> 32),
+ *         words 0 and 1, as every uniform of this library;
+ *   if p_a < 1 the residual mass sigma grows by p_a; if p_a >= 1 or sigma >= 1, C_pre takes
+ *         C_cur's columns (Q grows by each of them in order, orthogonalized twice against the
+ *         basis so far; a column whose residual norm is at most tol times its norm adds no
+ *         direction, tol = 1e-12 for FP64 data and 1e-4 for FP32) and sigma = 0.
+ * The selection is C_pre followed by C_cur, by arrival.  Products are formed in the data's type
+ * and summed in FP64 over runs of 128 coordinates; the basis is stored in the data's type.
+ * Device memory: 2 cap + 1 columns of m (the basis, a candidate slot and the raw columns of
+ * C_cur), plus 64 columns of staging for host input, allocated at the first host ingest. */
+typedef struct rid_rcss rid_rcss;
+
+/* New selector.  m >= 1 rows, k >= 1 (the target rank), xi > 0, data_dtype RID_F64 or RID_F32,
+ * 1 <= cap <= 4096 the most columns it may select.  stop_at_cap != 0: once cap columns are
+ * selected a later keep decision adds nothing and p, sigma and the steps go on (the treatment of
+ * the experiments, Sec. 4.1, with cap = k); stop_at_cap = 0: a selection beyond cap is an error.
+ * cuda_stream: the stream every call runs on (NULL: the legacy default stream).  Errors:
+ * RID_EINVAL (sizes), RID_ENOMEM, RID_ENOLIB. */
+int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed, int32_t data_dtype,
+                  int32_t cap, int32_t stop_at_cap, void* cuda_stream);
+
+/* Decide ncols columns, column q at cols + q*ld elements (ld >= m), device memory if on_device
+ * else host memory.  Blocks until they are decided.  Errors: RID_EINVAL (arguments; with
+ * stop_at_cap = 0 a selection beyond cap, after which the handle's state is undefined),
+ * RID_ENOMEM, RID_ECUDA. */
+int rid_rcss_ingest(rid_rcss* h, const void* cols, int64_t ld, int32_t ncols, int32_t on_device);
+
+/* The selection so far (C_pre then C_cur; global column numbers), at most max_out of them into
+ * idx (host; NULL to skip), its length into *n_out, sigma into *sigma and the basis size (the
+ * rank of span(C_pre)) into *basis_size; each output pointer may be NULL. */
+int rid_rcss_selection(rid_rcss* h, int64_t* idx, int32_t max_out, int32_t* n_out, double* sigma,
+                       int32_t* basis_size);
+
+/* p_a of every column decided so far, by arrival (host doubles; at most max_out), count into
+ * *n_out (may be NULL). */
+int rid_rcss_probabilities(rid_rcss* h, double* p, int64_t max_out, int64_t* n_out);
+
+/* The orthonormal basis Q of span(C_pre): basis_size columns of m, in the data's type, column i at
+ * out + i*ld (ld >= m), device memory if on_device else host. */
+int rid_rcss_basis(rid_rcss* h, void* out, int64_t ld, int32_t on_device);
+
+/* Free everything.  NULL is ignored. */
+int rid_rcss_destroy(rid_rcss* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,10 @@ For each arriving column a (global index j):
 * if p_a < 1, the residual mass sigma grows by p_a;
 * if p_a >= 1 or sigma >= 1, C_pre takes C_cur's columns, sigma = 0 and C_cur is emptied.
 
-The selection is C_pre followed by C_cur, in order of arrival.  Reading (the paper is silent):
+The selection is C_pre followed by C_cur, in order of arrival.  With ``limit`` set, the selection
+stops growing at ``limit`` columns, the treatment of the experiments (Sec. 4.1: the subset is
+expanded only until k columns are selected); reading: a column whose keep decision comes after
+that is not added, and p, sigma and the steps go on as before.  Reading (the paper is silent):
 the basis Q of span(C_pre) grows by each column of C_cur in order, orthogonalized against the
 basis so far; a column whose residual norm is at most RANK_TOL times its norm adds no direction
 (it lies in the span numerically) but stays in the selection.
@@ -40,10 +43,10 @@ def uniform(seed, j):
 class ResidualCSS:
     """Algorithm 1 over a stream of m-vectors."""
 
-    def __init__(self, m, k, xi, seed=0):
+    def __init__(self, m, k, xi, seed=0, limit=None):
         if not xi > 0:
             raise ValueError("xi must be positive")
-        self.m, self.k, self.xi, self.seed = m, k, float(xi), seed
+        self.m, self.k, self.xi, self.seed, self.limit = m, k, float(xi), seed, limit
         self.Q = np.zeros((m, 0))
         self.pre = []               # indices of C_pre
         self.cur = []               # indices of C_cur
@@ -63,7 +66,8 @@ class ResidualCSS:
         res = a - self.Q @ (self.Q.T @ a)
         p = self.k * float(res @ res) / self.xi
         self.p.append(p)
-        if uniform(self.seed, j) < min(p, 1.0):
+        full = self.limit is not None and len(self.pre) + len(self.cur) >= self.limit
+        if uniform(self.seed, j) < min(p, 1.0) and not full:
             self.cur.append(j)
             self.cur_cols.append(a.copy())
         if p < 1.0:

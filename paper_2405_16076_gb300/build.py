@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librid.so")
-SOURCES = ["rid_api.cu", "ingest.cu", "batch.cu", "tc_ingest.cu", "coop.cu", "noalloc.cu", "right.cu", "gcv.cu", "autotune.cu"]
+SOURCES = ["rid_api.cu", "ingest.cu", "batch.cu", "tc_ingest.cu", "coop.cu", "noalloc.cu", "right.cu", "gcv.cu", "autotune.cu", "rcss.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

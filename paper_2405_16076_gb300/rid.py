@@ -95,6 +95,13 @@ def _load():
         "rid_autotune": (ctypes.c_int, [ctypes.POINTER(rid_config), P, ctypes.c_int64, ctypes.c_int32, P]),
         "rid_log_enable": (ctypes.c_int, [H, ctypes.c_int32]),
         "rid_get_log": (ctypes.c_int, [H, P, ctypes.c_int32, P]),
+        "rid_rcss_init": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                         ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]),
+        "rid_rcss_ingest": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
+        "rid_rcss_selection": (ctypes.c_int, [H, P, ctypes.c_int32, P, P, P]),
+        "rid_rcss_probabilities": (ctypes.c_int, [H, P, ctypes.c_int64, P]),
+        "rid_rcss_basis": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32]),
+        "rid_rcss_destroy": (ctypes.c_int, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -131,6 +138,12 @@ rid_config_check = lib.rid_config_check
 rid_autotune = lib.rid_autotune
 rid_log_enable = lib.rid_log_enable
 rid_get_log = lib.rid_get_log
+rid_rcss_init = lib.rid_rcss_init
+rid_rcss_ingest = lib.rid_rcss_ingest
+rid_rcss_selection = lib.rid_rcss_selection
+rid_rcss_probabilities = lib.rid_rcss_probabilities
+rid_rcss_basis = lib.rid_rcss_basis
+rid_rcss_destroy = lib.rid_rcss_destroy
 
 
 def batch_ingest(handles, blocks):
@@ -486,3 +499,53 @@ class OnlineRID:
 
     def reset(self):
         _check(rid_reset(self.h), self.h)
+
+
+class ResidualCSS:
+    """Owns one rid_rcss handle: online column subset selection by residual-based sampling (the
+    paper's Algorithm 1, Sec. 2.2.1), the selector the accuracy tables compare against."""
+
+    def __init__(self, m, k, xi, *, seed=0, data_dtype=RID_F64, cap=1024, stop_at_cap=False, cuda_stream=None):
+        self.m = int(m)
+        self.esize = 8 if data_dtype == RID_F64 else 4
+        self.data_dtype = data_dtype
+        self.h = ctypes.c_void_p()
+        _check(rid_rcss_init(ctypes.byref(self.h), self.m, int(k), float(xi), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                             int(data_dtype), int(cap), int(bool(stop_at_cap)), ctypes.c_void_p(cuda_stream)))
+
+    def close(self):
+        if self.h:
+            rid_rcss_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ingest(self, cols):
+        ptr, dev, ld, n, _own = _columns(cols, self.m, self.esize)
+        _check(rid_rcss_ingest(self.h, ptr, ld, n, int(dev)))
+
+    def selection(self):
+        """(indices of C_pre then C_cur by arrival, sigma, basis size)."""
+        n, sig, nb = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
+        _check(rid_rcss_selection(self.h, None, 0, ctypes.byref(n), ctypes.byref(sig), ctypes.byref(nb)))
+        idx = np.zeros(max(n.value, 1), dtype=np.int64)
+        _check(rid_rcss_selection(self.h, ctypes.c_void_p(idx.ctypes.data), n.value, None, None, None))
+        return idx[:n.value], sig.value, nb.value
+
+    def probabilities(self):
+        n = ctypes.c_int64()
+        _check(rid_rcss_probabilities(self.h, None, 0, ctypes.byref(n)))
+        p = np.zeros(max(n.value, 1))
+        _check(rid_rcss_probabilities(self.h, ctypes.c_void_p(p.ctypes.data), n.value, None))
+        return p[:n.value]
+
+    def basis(self):
+        nb = self.selection()[2]
+        Q = np.zeros((nb, self.m), dtype=np.float64 if self.esize == 8 else np.float32)
+        if nb:
+            _check(rid_rcss_basis(self.h, ctypes.c_void_p(Q.ctypes.data), self.m, 0))
+        return Q.T

@@ -750,3 +750,23 @@ def test_residual_css_recovers_a_rank_r_stream():
     assert Q.shape[1] == 5
     assert np.linalg.norm(A - Q @ (Q.T @ A)) <= 1e-10 * np.linalg.norm(A)
     assert np.abs(Q.T @ Q - np.eye(5)).max() <= 1e-12
+
+
+def test_residual_css_limit_stops_the_selection_only():
+    """With a limit of k columns (the experiments' treatment), the selection is the unlimited run's
+    first k columns as long as the two runs agree -- they do up to the step that holds the k-th
+    selection, and p is identical up to and including it -- and never more than k."""
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((80, 25)) @ rng.standard_normal((25, 120))
+    xi = 0.2 * 6 * float(np.median(np.einsum("ij,ij->j", A, A)))
+    free = ResidualCSS(80, k=6, xi=xi, seed=4)
+    free.ingest(A)
+    capped = ResidualCSS(80, k=6, xi=xi, seed=4, limit=6)
+    capped.ingest(A)
+    sel = free.selection()
+    assert len(sel) > 6
+    np.testing.assert_array_equal(capped.selection(), sel[:6])
+    # the k-th selection's step: both runs took the same decisions through its end
+    end = min(j for j in free.steps if j >= sel[5])
+    np.testing.assert_array_equal(capped.p[:end + 1], free.p[:end + 1])
+    assert len(capped.selection()) == 6 and len(capped.p) == 120
