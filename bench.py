@@ -298,6 +298,66 @@ def accuracy_report(h, X, Jd, Pd):
     return {"rel_fro_err": err, "est_rel_fro_err": float(est_fro[0] / np.sqrt(fro2)), "q_star": q}
 
 
+def residual_css_comparison(rid, X, k, b, st, seed):
+    """Algorithm 1 (online CSS by residual-based sampling, Sec. 2.2.1) on the same resident stream,
+    as the experiments run it (Sec. 4.1: the subset stops growing at k columns): its throughput,
+    blocks of b snapshots through rid_rcss_ingest, and the relative error of projecting the stream
+    onto its selected columns (the least-squares coefficients P = A_J^+ A of Sec. 3).  xi is the smallest
+    value the algorithm's guarantee allows, ||A - A_k||_F^2, from the eigenvalues of A^T A; the
+    Gram matrices of the set-up and the evaluation take FP32 products over chunks of 2^16
+    coordinates with FP64 sums (cuBLAS, outside the timed region)."""
+    import torch
+    n, m = X.shape
+    dev = X.device
+    G = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    for c0 in range(0, m, 1 << 16):
+        Xc = X[:, c0:c0 + (1 << 16)]
+        G += (Xc @ Xc.T).double()
+    ev = torch.linalg.eigvalsh(G.cpu()).flip(0)
+    total = float(ev.sum())
+    xi = float(ev[k:].sum())
+    # one warm-up pass over the first 64 snapshots, on a handle of its own
+    g = rid.ResidualCSS(m, k, xi, seed=seed, data_dtype=rid.RID_F32, cap=k, stop_at_cap=True,
+                        cuda_stream=st.cuda_stream)
+    g.ingest(X[:min(n, 64)])
+    g.close()
+    torch.cuda.synchronize()
+    g = rid.ResidualCSS(m, k, xi, seed=seed, data_dtype=rid.RID_F32, cap=k, stop_at_cap=True,
+                        cuda_stream=st.cuda_stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for j0 in range(0, n, b):
+        g.ingest(X[j0:j0 + b])
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sel, sigma, nbasis = g.selection()
+    p = g.probabilities()
+    g.close()
+    # ||A - S S^+ A||_F^2 = ||A||_F^2 - tr(B^T Gs^+ B), Gs = S^T S, B = S^T A
+    idx = torch.from_numpy(sel).to(dev)
+    Gs = torch.zeros((len(sel), len(sel)), dtype=torch.float64, device=dev)
+    B = torch.zeros((len(sel), n), dtype=torch.float64, device=dev)
+    for c0 in range(0, m, 1 << 16):
+        Xc = X[:, c0:c0 + (1 << 16)]
+        Sc = Xc[idx]
+        Gs += (Sc @ Sc.T).double()
+        B += (Sc @ Xc.T).double()
+    w, U = torch.linalg.eigh(Gs.cpu())
+    keep = w > w.max() * 1e-12
+    C = (U[:, keep].T @ B.cpu()) / w[keep].sqrt()[:, None]
+    captured = float(C.square().sum())
+    err = max(total - captured, 0.0) / total
+    return {"value": n / (ms / 1e3), "unit": "snapshots/s", "ms": ms, "k": k, "xi": xi,
+            "n_selected": int(len(sel)), "basis_size": int(nbasis), "steps_forced": int((p >= 1).sum()),
+            "rel_fro_err": err ** 0.5, "kernel": "rcss_thin_kernel (basis x block dots)",
+            "note": "Algorithm 1 with the subset capped at k columns (Sec. 4.1); xi = ||A - A_k||_F^2; "
+                    "rel_fro_err = ||A - S S^+ A||_F / ||A||_F, S the selected columns (least-squares "
+                    "coefficients); blocks of the bench's size from the resident stream, decisions in "
+                    "FP64 on the device"}
+
+
 def rank_seeds(rank):
     """Seeds of rank r's independent stream (data generator, sketch): every rank has its own."""
     return 1000 + rank, 7 + rank
@@ -613,6 +673,8 @@ def main():
                     help="gradient mode: keep Omega G^p a and report Sec. 3.4's gradient-augmented coefficients")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the accuracy comparison with the other sketch precisions")
+    ap.add_argument("--no-rcss", dest="rcss", action="store_false",
+                    help="skip the comparison with Algorithm 1 (online CSS by residual-based sampling)")
     ap.add_argument("--timeline", default=None,
                     help="write the per-batch phase timeline of the timed steps (JSON) to this file")
     args = ap.parse_args()
@@ -847,6 +909,9 @@ def main():
             forms[form] = {"value": n / (f0.elapsed_time(f1) / 1e3), "unit": "snapshots/s",
                            **accuracy_report(hf, X, Jd, Pd)}
             hf.close()
+    comparison = None
+    if not grad and args.rcss:
+        comparison = {"residual_css": residual_css_comparison(rid, X, cfg["k"], b, st, rank_seeds(rank)[1])}
     accuracy["sketch"] = args.sketch
     if forms:
         accuracy["forms"] = forms
@@ -911,6 +976,8 @@ def main():
     }
     if gradc is not None:
         line["gradient_coefficients"] = gradc
+    if comparison is not None:
+        line["comparison"] = comparison
     if right is not None:
         line["ingest_roofline"] = line["roofline"]
         line["roofline"] = right

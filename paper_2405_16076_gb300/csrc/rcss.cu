@@ -12,7 +12,8 @@
 //
 // Device state: an orthonormal basis Q of span(C_pre) (cap vectors of m_pad, the data's type),
 // the raw columns of C_cur, and the selection list.  Per block of up to 64 columns:
-//   1. rcss_norms_kernel: ||a||^2 of the block's columns; rcss_dots_kernel: the dot products of
+//   1. rcss_norms_kernel: ||a||^2 of the block's columns; rcss_dots_kernel (rcss_thin_kernel for
+//      blocks of up to 16 columns): the dot products of
 //      the basis with the block's columns (FP32 or FP64 products summed over runs of 128
 //      coordinates, each run's sums added into per-CTA FP64 partials); rcss_reduce_kernel adds the
 //      partials in CTA order into X (basis vector x block column);
@@ -139,6 +140,107 @@ rcss_dots_kernel(const T* const* __restrict__ V, int nv, const T* const* __restr
             if (tv + x < nvt && ta + y < na) P[(size_t)(vt + tv + x) * kRcBlock + ta + y] += (double)acc[x][y];
       }
     }
+  }
+}
+
+// The same products for thin blocks (na <= NA <= 16): thread t of vector group blockIdx.y owns
+// vector v = 256 blockIdx.y + t and streams it with 16-byte loads (8 in flight); the block's
+// columns are staged kThinRuns runs at a time, coordinate-major (As[i * NA + a], zero past na and
+// m), and read as 16-byte broadcasts.  The coordinate partition (CTAs over runs), the per-run sums
+// in the data's type (fma in coordinate order from zero) and their FP64 accumulation in run order
+// are those of rcss_dots_kernel, so both write bit-identical partials.  V must be 16-byte aligned
+// with zeros from m up to the next multiple of kRcRun (the basis slots are).
+constexpr int kThinRuns = 4;
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ T v16_get(const typename Vec16<T>::type& q, int e);
+template <>
+__device__ __forceinline__ float v16_get<float>(const float4& q, int e) {
+  return e == 0 ? q.x : e == 1 ? q.y : e == 2 ? q.z : q.w;
+}
+template <>
+__device__ __forceinline__ double v16_get<double>(const double2& q, int e) { return e == 0 ? q.x : q.y; }
+
+template <typename T, int NA>
+__global__ void __launch_bounds__(kRcThreads)
+rcss_thin_kernel(const T* const* __restrict__ V, int nv, const T* const* __restrict__ A, int na, int64_t m,
+                 int64_t runs_per_cta, int vmax, double* __restrict__ part) {
+  using VT = typename Vec16<T>::type;
+  constexpr int EPV = Vec16<T>::n;                         // elements per 16-byte load
+  constexpr int CH = kThinRuns * kRcRun;                   // coordinates staged at a time
+  constexpr int LPR = kRcRun / EPV;                        // 16-byte loads per run
+  constexpr int B = 8;                                     // loads in flight
+  extern __shared__ __align__(16) unsigned char rsm[];
+  T* As = reinterpret_cast<T*>(rsm);                       // CH x NA
+  const int tid = threadIdx.x;
+  const int v = blockIdx.y * kRcThreads + tid;
+  const bool own = v < nv;
+  const VT* vp = own ? reinterpret_cast<const VT*>(V[v]) : nullptr;
+  double acc64[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) acc64[a] = 0.0;
+  const int64_t nruns = (m + kRcRun - 1) / kRcRun;
+  const int64_t r0 = (int64_t)blockIdx.x * runs_per_cta;
+  const int64_t r1 = r0 + runs_per_cta < nruns ? r0 + runs_per_cta : nruns;
+  for (int64_t rc = r0; rc < r1; rc += kThinRuns) {
+    const int nr = (int)(r1 - rc < kThinRuns ? r1 - rc : kThinRuns);
+    const int64_t c0 = rc * kRcRun;
+    __syncthreads();
+    for (int e0 = 0; e0 < NA * CH; e0 += 8 * kRcThreads) {
+      T val[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * kRcThreads + tid;
+        const int a = e / CH, i = e - a * CH;
+        val[u] = (e < NA * CH && a < na && i < nr * kRcRun && c0 + i < m) ? A[a][c0 + i] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * kRcThreads + tid;
+        const int a = e / CH, i = e - a * CH;
+        if (e < NA * CH) As[i * NA + a] = val[u];
+      }
+    }
+    __syncthreads();
+    if (own) {
+      for (int r = 0; r < nr; ++r) {
+        T acc[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[a] = T(0);
+        const VT* src = vp + ((c0 + (int64_t)r * kRcRun) / EPV);
+        const T* arow = As + (size_t)r * kRcRun * NA;
+        for (int l0 = 0; l0 < LPR; l0 += B) {
+          VT q[B];
+#pragma unroll
+          for (int u = 0; u < B; ++u) q[u] = src[l0 + u];
+#pragma unroll
+          for (int u = 0; u < B; ++u)
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) {
+              const T x = v16_get<T>(q[u], e);
+              const VT* ab = reinterpret_cast<const VT*>(arow + ((l0 + u) * EPV + e) * NA);
+#pragma unroll
+              for (int g = 0; g < NA / EPV; ++g) {
+                const VT y = ab[g];
+#pragma unroll
+                for (int h = 0; h < EPV; ++h) acc[g * EPV + h] = fma(x, v16_get<T>(y, h), acc[g * EPV + h]);
+              }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc64[a] += (double)acc[a];
+      }
+    }
+  }
+  if (own) {
+    double* P = part + ((size_t)blockIdx.x * vmax + v) * kRcBlock;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+      if (a < na) P[a] = acc64[a];
   }
 }
 
@@ -405,6 +507,27 @@ int rc_dots(rid_rcss* h, const std::vector<const void*>& V, const std::vector<co
     return rc_fail(RID_EINVAL, "rcss: too many vectors in one dot pass");
   RCK(cudaMemcpyAsync(h->vptr, V.data(), sizeof(void*) * nv, cudaMemcpyHostToDevice, h->st));
   RCK(cudaMemcpyAsync(h->aptr, A.data(), sizeof(void*) * na, cudaMemcpyHostToDevice, h->st));
+  bool aligned = true;
+  for (const void* p : V) aligned = aligned && ((uintptr_t)p % 16 == 0);
+  if (na <= 16 && aligned) {
+    const int na_t = na <= 4 ? 4 : na <= 8 ? 8 : 16;
+    const size_t smem = h->es * (size_t)rid::kThinRuns * rid::kRcRun * na_t;
+    const dim3 grid(h->nblk, (nv + rid::kRcThreads - 1) / rid::kRcThreads);
+#define RC_THIN(TT, NA)                                                                                           \
+  rid::rcss_thin_kernel<TT, NA><<<grid, rid::kRcThreads, smem, h->st>>>(                                         \
+      reinterpret_cast<const TT* const*>(h->vptr), nv, reinterpret_cast<const TT* const*>(h->aptr), na, h->m,     \
+      h->runs_per_cta, h->vmax, h->part)
+    if (h->dtype == RID_F64) {
+      if (na_t == 4) RC_THIN(double, 4); else if (na_t == 8) RC_THIN(double, 8); else RC_THIN(double, 16);
+    } else {
+      if (na_t == 4) RC_THIN(float, 4); else if (na_t == 8) RC_THIN(float, 8); else RC_THIN(float, 16);
+    }
+#undef RC_THIN
+    rid::rcss_reduce_kernel<<<(nv * na + 255) / 256, 256, 0, h->st>>>(h->part, h->nblk, nv, na, h->vmax, out, row0,
+                                                                     col0);
+    RCK(cudaGetLastError());
+    return RID_OK;
+  }
   const size_t smem = h->es * 2 * (size_t)rid::kRcRun * rid::kRcLd;
   if (h->dtype == RID_F64)
     rid::rcss_dots_kernel<double><<<h->nblk, rid::kRcThreads, smem, h->st>>>(
@@ -551,7 +674,7 @@ int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed
   }
   rid_rcss* h = new rid_rcss();
   h->m = m;
-  h->m_pad = (m + 63) / 64 * 64;
+  h->m_pad = (m + rid::kRcRun - 1) / rid::kRcRun * rid::kRcRun;
   h->k = k;
   h->xi = xi;
   h->seed = seed;
@@ -601,9 +724,12 @@ int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed
   if (ok) {
     const int s64 = 8 * 2 * rid::kRcRun * rid::kRcLd;
     const int s32 = 4 * 2 * rid::kRcRun * rid::kRcLd;
+    const int t64 = 8 * rid::kThinRuns * rid::kRcRun * 16;
     ok = cudaFuncSetAttribute(rid::rcss_dots_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64) ==
              cudaSuccess &&
          cudaFuncSetAttribute(rid::rcss_dots_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(rid::rcss_thin_kernel<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, t64) ==
              cudaSuccess;
   }
   if (ok) {
