@@ -40,6 +40,22 @@ def uniform(seed, j):
     return float(philox.uniform53(w[0], w[1]))
 
 
+def probability(a, Q, k, xi):
+    """p_a = k ||Pi_perp a||^2 / xi with Pi_perp = I - Q Q^T (Q orthonormal columns), the residual
+    a - Q (Q^T a) formed explicitly."""
+    res = a - Q @ (Q.T @ a)
+    return k * float(res @ res) / xi
+
+
+def replay(p, seed, limit=None):
+    """The decisions of Algorithm 1 for a given sequence of p (the bookkeeping alone: keep draws,
+    sigma, steps, the limit): (selection, sigma, steps)."""
+    o = ResidualCSS(1, 1, 1.0, seed, limit)
+    for pj in p:
+        o._decide(float(pj), None)
+    return o.selection(), o.sigma, o.steps
+
+
 class ResidualCSS:
     """Algorithm 1 over a stream of m-vectors."""
 
@@ -62,19 +78,23 @@ class ResidualCSS:
             self._column(A[:, q])
 
     def _column(self, a):
+        self._decide(probability(a, self.Q, self.k, self.xi), a)
+
+    def _decide(self, p, a):
+        """Steps 5-11 of the loop for column j = n_obs with probability p (a = None: bookkeeping
+        only, the basis is not grown)."""
         j = self.n_obs
-        res = a - self.Q @ (self.Q.T @ a)
-        p = self.k * float(res @ res) / self.xi
         self.p.append(p)
         full = self.limit is not None and len(self.pre) + len(self.cur) >= self.limit
         if uniform(self.seed, j) < min(p, 1.0) and not full:
             self.cur.append(j)
-            self.cur_cols.append(a.copy())
+            self.cur_cols.append(None if a is None else a.copy())
         if p < 1.0:
             self.sigma += p
         if p >= 1.0 or self.sigma >= 1.0:
             for c in self.cur_cols:
-                self._extend(c)
+                if c is not None:
+                    self._extend(c)
             self.pre += self.cur
             self.cur, self.cur_cols = [], []
             self.sigma = 0.0
