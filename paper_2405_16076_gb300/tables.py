@@ -3,10 +3,12 @@
 For each target rank k the stream runs through the library (rid_init / rid_ingest /
 rid_finalize); the table reports, for the last batch step, the exact relative error
 ||A - A_J P_q||_F / ||A||_F of each coefficient update q = 4..7 (Algorithms 4-7), its
-single-pass NA-Hutch++ estimate (Algorithm 8), the update chosen (q*), and two offline
-references computed here from the whole matrix: the column-pivoted-QR interpolative
-decomposition of rank k and the truncated SVD of rank k.  The paper's datasets are not
-available; the inputs are the synthetic streams of ``workloads`` (or any m x n array).
+single-pass NA-Hutch++ estimate (Algorithm 8), the update chosen (q*), the least-squares
+coefficients (P = A_J^+ A) on the online selections -- Algorithm 3's J and Algorithm 1's subset
+(rid_rcss_*, capped at k columns with xi = ||A - A_k||_F^2, as the experiments run it, Sec. 4.1)
+-- and two offline references computed here from the whole matrix: the column-pivoted-QR
+interpolative decomposition of rank k and the truncated SVD of rank k.  The paper's datasets are
+not available; the inputs are the synthetic streams of ``workloads`` (or any m x n array).
 
     python -m paper_2405_16076_gb300.tables --workload lowrank --ranks 10 20 30 40
 """
@@ -16,17 +18,38 @@ import json
 import numpy as np
 
 
+def least_squares_error(A, J):
+    """||A - A_J A_J^+ A||_F / ||A||_F: the least-squares coefficients on the columns J."""
+    if len(J) == 0:
+        return 1.0
+    P = np.linalg.lstsq(A[:, J], A, rcond=None)[0]
+    return float(np.linalg.norm(A - A[:, J] @ P) / np.linalg.norm(A))
+
+
 def offline_errors(A, k):
-    """(CPQR ID error, truncated SVD error) of rank k, relative to ||A||_F."""
+    """(CPQR ID error, truncated SVD error, ||A - A_k||_F^2) of rank k, errors relative to ||A||_F."""
     import scipy.linalg
     nA = np.linalg.norm(A)
     _, _, piv = scipy.linalg.qr(A, mode="economic", pivoting=True)
-    Jc = piv[:k]
-    Pc = np.linalg.lstsq(A[:, Jc], A, rcond=None)[0]
-    e_cpqr = np.linalg.norm(A - A[:, Jc] @ Pc) / nA
+    e_cpqr = least_squares_error(A, piv[:k])
     sv = np.linalg.svd(A, compute_uv=False)
-    e_svd = np.sqrt(np.sum(sv[k:] ** 2)) / nA
-    return float(e_cpqr), float(e_svd)
+    tail = float(np.sum(sv[k:] ** 2))
+    return float(e_cpqr), float(np.sqrt(tail) / nA), tail
+
+
+def residual_css(A, k, xi, *, dtype="f64", block=1, seed=0):
+    """Algorithm 1's subset of the stream A (m x n, host array) on the GPU, capped at k columns."""
+    import torch
+    from . import rid
+    m, n = A.shape
+    g = rid.ResidualCSS(m, k, xi, seed=seed, data_dtype=rid.RID_F64 if dtype == "f64" else rid.RID_F32,
+                        cap=k, stop_at_cap=True)
+    X = torch.from_numpy(np.ascontiguousarray(A.T, dtype=np.float64 if dtype == "f64" else np.float32)).cuda()
+    for j0 in range(0, n, block):
+        g.ingest(X[j0:j0 + block])
+    sel = g.selection()[0]
+    g.close()
+    return sel
 
 
 def table_row(A, k, *, h=30, dtype="f64", sketch="native", omega="rademacher", block=1, seed=0,
@@ -49,20 +72,23 @@ def table_row(A, k, *, h=30, dtype="f64", sketch="native", omega="rademacher", b
     AJ = A[:, J[act]]
     na = int(act.sum())
     exact = [float(np.linalg.norm(A - AJ @ cand[q][:na]) / nA) for q in range(4)]
-    e_cpqr, e_svd = offline_errors(A, k)
+    e_cpqr, e_svd, tail = offline_errors(A, k)
+    sel1 = residual_css(A, k, max(tail, 1e-300), dtype=dtype, block=block, seed=seed)
     return {"k": k, "exact": exact, "estimated": [float(e / nA) for e in est_fro[1:5]], "q_star": q_star,
             "chosen_exact": float(np.linalg.norm(A - AJ @ P[act]) / nA), "cpqr": e_cpqr, "svd": e_svd,
-            "n_basis": na}
+            "n_basis": na, "alg3_ls": least_squares_error(A, J[act]),
+            "alg1_ls": least_squares_error(A, sel1), "alg1_n": int(len(sel1))}
 
 
 def markdown(rows, title):
     out = [f"### {title}", "",
            "| k | Alg. 4 exact / est. | Alg. 5 exact / est. | Alg. 6 exact / est. | Alg. 7 exact / est. "
-           "| q* | CPQR ID | truncated SVD |",
-           "|---:|---|---|---|---|---:|---:|---:|"]
+           "| q* | Alg. 3 + LS | Alg. 1 + LS | CPQR ID | truncated SVD |",
+           "|---:|---|---|---|---|---:|---:|---:|---:|---:|"]
     for r in rows:
         cells = [f"{r['exact'][q]:.4f} / {r['estimated'][q]:.4f}" for q in range(4)]
-        out.append(f"| {r['k']} | " + " | ".join(cells) + f" | {r['q_star']} | {r['cpqr']:.4f} | {r['svd']:.4f} |")
+        out.append(f"| {r['k']} | " + " | ".join(cells) + f" | {r['q_star']} | {r['alg3_ls']:.4f} | "
+                   f"{r['alg1_ls']:.4f} | {r['cpqr']:.4f} | {r['svd']:.4f} |")
     return "\n".join(out)
 
 

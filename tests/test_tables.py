@@ -2,7 +2,8 @@
 
 The chosen update's exact error equals the error of the returned P; the offline references
 order as they must (the truncated SVD is optimal, so no rank-k ID beats it); estimates are
-non-negative errors of the same magnitude as the exact ones."""
+non-negative errors of the same magnitude as the exact ones; least squares on Algorithm 3's J is
+no worse than any coefficient update on it; Algorithm 1 selects at most k columns."""
 import numpy as np
 import pytest
 
@@ -20,5 +21,8 @@ def test_table_rows_are_consistent():
         assert r["svd"] <= r["cpqr"] + 1e-12
         assert r["svd"] <= min(r["exact"]) + 1e-12
         assert all(e >= 0.0 for e in r["estimated"])
+        assert r["alg3_ls"] <= r["chosen_exact"] + 1e-12      # least squares is optimal for its J
+        assert r["svd"] <= r["alg1_ls"] + 1e-12 and r["svd"] <= r["alg3_ls"] + 1e-12
+        assert 0 < r["alg1_n"] <= k
     md = tables.markdown([r], "check")
     assert md.count("|") > 10
