@@ -13,6 +13,9 @@
 // The grid barrier is a counter/generation pair with a bounded spin; on timeout
 // the kernel raises ERR_TIMEOUT and every block stops at its next barrier.
 #include <cuda_runtime.h>
+#include <stdlib.h>
+
+#include <array>
 #include <stdint.h>
 
 #include <cooperative_groups.h>
@@ -487,13 +490,24 @@ tri_scores_kernel(Dev d, const double* R, const double* beta, const double* vhea
   }
 }
 
+// Cluster sizes to try in order (the first the device co-schedules is taken), or only the size
+// named by the environment variable (8 or 16).  A smaller cluster leaves SMs to the ingest that
+// runs beside the batch step and makes the step's own kernel slower: on the channel-flow
+// benchmark (GB300) a QR cluster of 8 measured 1.7 % faster than 16 over three alternating runs,
+// a tridiagonalization cluster of 8 5.5 % slower.
+std::array<int, 2> cluster_candidates(const char* var, std::array<int, 2> order) {
+  const char* e = getenv(var);
+  if (e && (atoi(e) == 8 || atoi(e) == 16)) return {atoi(e), 0};
+  return order;
+}
+
 size_t tri_cluster_smem(int n, int C) {
   const int ncl = (n + C - 1) / C;
   return ((size_t)ncl * n + 6 * (size_t)n) * sizeof(double);
 }
 
 // Cluster size for the shared-memory tridiagonalization of an n x n matrix: 16 (non-portable)
-// or 8 CTAs when the columns fit and the device can co-schedule the cluster, else 0.
+// or else 8 CTAs when the columns fit and the device can co-schedule the cluster, else 0.
 int tri_cluster_size(int n) {
   static int cached_n = -1, cached_c = 0;
   if (n == cached_n) return cached_c;
@@ -509,7 +523,8 @@ int tri_cluster_size(int n) {
           cudaSuccess &&
       cudaFuncSetAttribute(tridiag_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) ==
           cudaSuccess) {
-    for (int C : {16, 8}) {
+    for (int C : cluster_candidates("RID_TRI_CLUSTER", {16, 8})) {
+      if (C == 0) continue;
       if (tri_cluster_smem(n, C) + 2048 > (size_t)max_smem || n < 2 * C) continue;
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
@@ -878,7 +893,8 @@ int qr_cluster_size(int m, int t) {
     if (cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
         cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) ==
             cudaSuccess) {
-      for (int C : {16, 8}) {
+      for (int C : cluster_candidates("RID_QR_CLUSTER", {8, 16})) {
+        if (C == 0) continue;
         const size_t smem = ((size_t)((t + C - 1) / C) * (m | 1) + m) * sizeof(double);
         if (smem + 1024 > (size_t)max_smem) continue;
         cudaLaunchConfig_t cfg = {};
