@@ -12,8 +12,8 @@
 //
 // Device state: an orthonormal basis Q of span(C_pre) (cap vectors of m_pad, the data's type),
 // the raw columns of C_cur, and the selection list.  Per block of up to 64 columns:
-//   1. rcss_norms_kernel: ||a||^2 of the block's columns; rcss_dots_kernel (rcss_thin_kernel for
-//      blocks of up to 16 columns): the dot products of
+//   1. rcss_norms_kernel: ||a||^2 of the block's columns; rcss_dots_kernel (for blocks of up to
+//      16 columns rcss_thin_stage_kernel on FP32 data, rcss_thin_kernel on FP64): the dot products of
 //      the basis with the block's columns (FP32 or FP64 products summed over runs of 128
 //      coordinates, each run's sums added into per-CTA FP64 partials); rcss_reduce_kernel adds the
 //      partials in CTA order into X (basis vector x block column);
@@ -238,6 +238,104 @@ rcss_thin_kernel(const T* const* __restrict__ V, int nv, const T* const* __restr
   }
   if (own) {
     double* P = part + ((size_t)blockIdx.x * vmax + v) * kRcBlock;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+      if (a < na) P[a] = acc64[a];
+  }
+}
+
+// FP32 form of the thin-block products with coalesced basis reads: per run, the tile of up to
+// kStTile basis vectors (kRcRun coordinates each) is copied into shared memory by 16-byte
+// cp.async (32 consecutive threads per vector and run), padded to kStLd floats per row so that
+// each thread's 16-byte reads of its own row do not conflict, and the block's columns by 4-byte
+// cp.async (zero past na and m); two stages, the next run's copies in flight while the current one
+// is used.  Thread t owns vector kStTile * blockIdx.y + t.  The arithmetic -- per-run fma in
+// coordinate order from zero, FP64 accumulation in run order, the CTAs' partition of the runs --
+// is rcss_dots_kernel's, so the partials are bit-identical.  Basis rows must be 16-byte aligned
+// and zero from m up to the next multiple of kRcRun.
+constexpr int kStTile = 128;
+constexpr int kStLd = kRcRun + 4;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+template <int NA>
+__global__ void __launch_bounds__(kStTile)
+rcss_thin_stage_kernel(const float* const* __restrict__ V, int nv, const float* const* __restrict__ A, int na,
+                       int64_t m, int64_t runs_per_cta, int vmax, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  float* Vs = reinterpret_cast<float*>(rsm);                         // 2 x kStTile x kStLd
+  float* As = Vs + 2 * kStTile * kStLd;                              // 2 x kRcRun x NA
+  const int tid = threadIdx.x;
+  const int vbase = blockIdx.y * kStTile;
+  const int nvt = nv - vbase < kStTile ? nv - vbase : kStTile;
+  const bool own = tid < nvt;
+  double acc64[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) acc64[a] = 0.0;
+  const int64_t nruns = (m + kRcRun - 1) / kRcRun;
+  const int64_t r0 = (int64_t)blockIdx.x * runs_per_cta;
+  const int64_t r1 = r0 + runs_per_cta < nruns ? r0 + runs_per_cta : nruns;
+  const uint32_t vs0 = (uint32_t)__cvta_generic_to_shared(Vs);
+  const uint32_t as0 = (uint32_t)__cvta_generic_to_shared(As);
+  const float* any = A[0];
+  auto issue = [&](int64_t run, int stage) {
+    const int64_t i0 = run * kRcRun;
+    for (int c = tid; c < nvt * (kRcRun / 4); c += kStTile) {
+      const int row = c / (kRcRun / 4), q = c - row * (kRcRun / 4);
+      cp_async16(vs0 + (uint32_t)(((stage * kStTile + row) * kStLd + 4 * q) * 4), V[vbase + row] + i0 + 4 * q);
+    }
+    for (int e = tid; e < NA * kRcRun; e += kStTile) {
+      const int a = e / kRcRun, ii = e - a * kRcRun;
+      const bool in = a < na && i0 + ii < m;
+      cp_async4(as0 + (uint32_t)(((stage * kRcRun + ii) * NA + a) * 4), in ? A[a] + i0 + ii : any, in ? 4 : 0);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (r0 < r1) issue(r0, 0);
+  for (int64_t run = r0; run < r1; ++run) {
+    const int stage = (int)((run - r0) & 1);
+    if (run + 1 < r1) {
+      issue(run + 1, stage ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    if (own) {
+      float acc[NA];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) acc[a] = 0.f;
+      const float4* vrow = reinterpret_cast<const float4*>(Vs + (stage * kStTile + tid) * kStLd);
+      const float* arow = As + stage * kRcRun * NA;
+#pragma unroll 4
+      for (int l = 0; l < kRcRun / 4; ++l) {
+        const float4 q = vrow[l];
+        const float xs[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float4* ab = reinterpret_cast<const float4*>(arow + (4 * l + e) * NA);
+#pragma unroll
+          for (int g = 0; g < NA / 4; ++g) {
+            const float4 y = ab[g];
+            acc[4 * g + 0] = fmaf(xs[e], y.x, acc[4 * g + 0]);
+            acc[4 * g + 1] = fmaf(xs[e], y.y, acc[4 * g + 1]);
+            acc[4 * g + 2] = fmaf(xs[e], y.z, acc[4 * g + 2]);
+            acc[4 * g + 3] = fmaf(xs[e], y.w, acc[4 * g + 3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < NA; ++a) acc64[a] += (double)acc[a];
+    }
+    __syncthreads();                              // the stage is refilled by the next issue
+  }
+  if (own) {
+    double* P = part + ((size_t)blockIdx.x * vmax + vbase + tid) * kRcBlock;
 #pragma unroll
     for (int a = 0; a < NA; ++a)
       if (a < na) P[a] = acc64[a];
@@ -509,6 +607,21 @@ int rc_dots(rid_rcss* h, const std::vector<const void*>& V, const std::vector<co
   RCK(cudaMemcpyAsync(h->aptr, A.data(), sizeof(void*) * na, cudaMemcpyHostToDevice, h->st));
   bool aligned = true;
   for (const void* p : V) aligned = aligned && ((uintptr_t)p % 16 == 0);
+  if (na <= 16 && aligned && h->dtype == RID_F32) {
+    const int na_t = na <= 4 ? 4 : na <= 8 ? 8 : 16;
+    const size_t smem = sizeof(float) * (2 * (size_t)rid::kStTile * rid::kStLd + 2 * (size_t)rid::kRcRun * na_t);
+    const dim3 grid(h->nblk, (nv + rid::kStTile - 1) / rid::kStTile);
+#define RC_STAGE(NA)                                                                                              \
+  rid::rcss_thin_stage_kernel<NA><<<grid, rid::kStTile, smem, h->st>>>(                                          \
+      reinterpret_cast<const float* const*>(h->vptr), nv, reinterpret_cast<const float* const*>(h->aptr), na,   \
+      h->m, h->runs_per_cta, h->vmax, h->part)
+    if (na_t == 4) RC_STAGE(4); else if (na_t == 8) RC_STAGE(8); else RC_STAGE(16);
+#undef RC_STAGE
+    rid::rcss_reduce_kernel<<<(nv * na + 255) / 256, 256, 0, h->st>>>(h->part, h->nblk, nv, na, h->vmax, out, row0,
+                                                                     col0);
+    RCK(cudaGetLastError());
+    return RID_OK;
+  }
   if (na <= 16 && aligned) {
     const int na_t = na <= 4 ? 4 : na <= 8 ? 8 : 16;
     const size_t smem = h->es * (size_t)rid::kThinRuns * rid::kRcRun * na_t;
@@ -731,6 +844,13 @@ int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed
              cudaSuccess &&
          cudaFuncSetAttribute(rid::rcss_thin_kernel<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, t64) ==
              cudaSuccess;
+    for (int na_t : {4, 8, 16}) {
+      const int st = (int)sizeof(float) * (2 * rid::kStTile * rid::kStLd + 2 * rid::kRcRun * na_t);
+      const void* f = na_t == 4 ? (const void*)rid::rcss_thin_stage_kernel<4>
+                      : na_t == 8 ? (const void*)rid::rcss_thin_stage_kernel<8>
+                                  : (const void*)rid::rcss_thin_stage_kernel<16>;
+      ok = ok && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, st) == cudaSuccess;
+    }
   }
   if (ok) {
     ok = cudaMemsetAsync(h->Q, 0, (size_t)(cap + 1) * h->m_pad * h->es, h->st) == cudaSuccess &&
