@@ -351,7 +351,7 @@ def residual_css_comparison(rid, X, k, b, st, seed):
     err = max(total - captured, 0.0) / total
     return {"value": n / (ms / 1e3), "unit": "snapshots/s", "ms": ms, "k": k, "xi": xi,
             "n_selected": int(len(sel)), "basis_size": int(nbasis), "steps_forced": int((p >= 1).sum()),
-            "rel_fro_err": err ** 0.5, "kernel": "rcss_thin_kernel (basis x block dots)",
+            "rel_fro_err": err ** 0.5, "kernel": "rcss_thin_stage_kernel (basis x block dots)",
             "note": "Algorithm 1 with the subset capped at k columns (Sec. 4.1); xi = ||A - A_k||_F^2; "
                     "rel_fro_err = ||A - S S^+ A||_F / ||A||_F, S the selected columns (least-squares "
                     "coefficients); blocks of the bench's size from the resident stream, decisions in "
