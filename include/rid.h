@@ -490,6 +490,18 @@ int rid_rcss_basis(rid_rcss* h, void* out, int64_t ld, int32_t on_device);
 /* Free everything.  NULL is ignored. */
 int rid_rcss_destroy(rid_rcss* h);
 
+/* Algorithm 1 as the handle's selector: the online rows of the paper's tables for the residual
+ * CSS (Sec. 4.1), where the coefficients are computed with Algorithms 4-7 and Algorithm 8 picks
+ * among them while Algorithm 1 selects.  From then on rid_ingest first passes each block to g
+ * (rid_rcss_ingest), and every batch step puts the columns g kept from its batch into the empty
+ * basis slots in order instead of Algorithm 3's prune / refill (Algorithm 1 never drops a column);
+ * the ridge scores are still computed but decide nothing.  g must have the handle's m, data type
+ * and stream, cap <= t and stop_at_cap != 0, and must outlive the handle's use of it; the handle
+ * must have no row shards and no gradient mode.  Attach before the first rid_ingest; g = NULL
+ * detaches.  rid_reset detaches (a selector serves one stream).  rid_checkpoint does not cover g.
+ * Errors: RID_EINVAL (mismatch), RID_ESTATE (columns already ingested). */
+int rid_attach_rcss(rid_handle* h, rid_rcss* g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,9 @@ class RIDConfig:
     right_l: int = 0                   # columns of the optional right sketch Y (0: off)
     grad_coeff: bool = False           # keep Omega G^p a for the gradient-augmented coefficients
     refill: str = "first"              # R7 ("first") or R7p ("proportional")
+    selector: str = "ridge"            # "ridge" (Algorithm 3) or "residual" (Algorithm 1, below)
+    rcss_xi: float = 1.0               # xi of Algorithm 1 when selector == "residual"
+    rcss_seed: int = 0                 # seed of Algorithm 1's uniforms
 
     @property
     def t(self):
@@ -346,6 +349,14 @@ class OnlineRID:
         self.flips = []             # (batch, slot, kind, margin) of the decisions re-synchronised
         self.Y = np.zeros((cfg.m, cfg.right_l)) if cfg.right_l > 0 else None
         self.SG = None                              # d x s x n_obs: Omega G^p A_obs (unit variance)
+        # The online rows of the paper's tables with Algorithm 1 as the selector (Sec. 4.1):
+        # Algorithm 1 decides each column as it arrives, its subset capped at t columns; each batch
+        # step puts the columns it kept from the batch into the empty slots in order (it never
+        # drops one) and computes Algorithms 4-8 for that basis as for Algorithm 3's.
+        self.rcss = None
+        if cfg.selector == "residual":
+            from .residual_css import ResidualCSS
+            self.rcss = ResidualCSS(cfg.m, cfg.k, cfg.rcss_xi, cfg.rcss_seed, limit=t)
 
     # Omega is materialized once: this is the slow, obviously correct form.
     def omega(self):
@@ -372,6 +383,8 @@ class OnlineRID:
     def _ingest_one(self, a):
         c = self.cfg
         j = self.n_obs
+        if self.rcss is not None:
+            self.rcss.ingest(a[:, None])
         s_j = self.omega() @ a                               # s_j = Omega a_j
         self.S = np.concatenate([self.S, s_j[:, None]], axis=1)
         lev = s_j[: c.s].copy()
@@ -443,7 +456,15 @@ class OnlineRID:
         JC_prev = self.JC.copy()
         target = self.resync.get(self.batch) if self.resync else None
         flips = [] if target is not None else None
-        JC, tau_old = css_update(c, self.batch, self.JC, self.tau_old, tau_C, JD, tau_D, self.margins, target, flips)
+        if self.rcss is not None:
+            JC, tau_old = self.JC.copy(), self.tau_old.copy()
+            new = [int(j) for j in self.rcss.selection() if JD and JD[0] <= j <= JD[-1]]
+            free = [i for i in range(t) if JC[i] < 0]
+            for i, j in zip(free, new):
+                JC[i] = j
+        else:
+            JC, tau_old = css_update(c, self.batch, self.JC, self.tau_old, tau_C, JD, tau_D, self.margins, target,
+                                     flips)
         if flips:
             self.flips.extend((self.batch,) + f for f in flips)
 

@@ -137,7 +137,25 @@ __global__ void __launch_bounds__(256) select_kernel(Dev d, Dev r, const double*
   if (stage_u)
     for (int i = tid; i < t * per; i += blockDim.x) s_u[i] = unif[i];
   __syncthreads();
-  if (tid < 32) {
+  if (d.ext_sel) {
+    // Algorithm 1 as the selector: the columns it kept from this batch fill the empty slots in
+    // order (it never drops a column, and its subset is capped at t).  Entries for later columns
+    // (being appended concurrently) lie past jd0 + count or still read -1: both are skipped.
+    if (tid == 0) {
+      const int ns = *(volatile const int*)d.ext_nsel;
+      int cur = 0;
+      for (int i = 0; i < t; ++i) {
+        if (s_JC[i] >= 0) continue;
+        int rr = -1;
+        while (cur < ns && rr < 0) {
+          const int64_t j = ((volatile const int64_t*)d.ext_sel)[cur++];
+          if (j >= jd0 && j < jd0 + count) rr = (int)(j - jd0);
+        }
+        if (rr < 0) break;
+        s_taken[rr] = 1; s_JC[i] = s_JD[rr]; s_slot[i] = s_dslot[rr]; s_told[i] = 1.0;
+      }
+    }
+  } else if (tid < 32) {
     for (int i = 0; i < t; ++i) {
       const double* u = stage_u ? s_u + (size_t)i * per : unif + (size_t)i * per;
       if (lane == 0 && s_JC[i] >= 0) {

@@ -578,6 +578,21 @@ struct rid_rcss {
   std::vector<double> hp;     // p of every column so far (copied after each pass)
 };
 
+namespace rid {
+
+void rcss_selection_view(const rid_rcss* g, const int64_t** sel, const int** nsel, int64_t* m, int* cap,
+                         int* stop_at_cap, int* dtype, cudaStream_t* st) {
+  *sel = g->sel;
+  *nsel = &g->dst->nsel;
+  *m = g->m;
+  *cap = g->cap;
+  *stop_at_cap = g->stop_at_cap;
+  *dtype = g->dtype;
+  *st = g->st;
+}
+
+}  // namespace rid
+
 namespace {
 
 int rc_fail(int code, const std::string& msg) {
@@ -855,6 +870,7 @@ int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed
   if (ok) {
     ok = cudaMemsetAsync(h->Q, 0, (size_t)(cap + 1) * h->m_pad * h->es, h->st) == cudaSuccess &&
          cudaMemsetAsync(h->dst, 0, sizeof(rid::RcssDevState), h->st) == cudaSuccess &&
+         cudaMemsetAsync(h->sel, 0xFF, sizeof(int64_t) * (size_t)cap, h->st) == cudaSuccess &&   // -1
          cudaStreamSynchronize(h->st) == cudaSuccess;
   }
   if (!ok) {

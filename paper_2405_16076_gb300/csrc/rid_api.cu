@@ -47,6 +47,7 @@ struct rid_handle {
   int64_t n_prev;     // columns covered by the last batch step
   int batch;          // batch steps run
   bool finalized;
+  rid_rcss* rcss = nullptr;       // Algorithm 1 as the selector (rid_attach_rcss), or NULL
   bool joined;            // the caller's stream already waits for every batch step issued
   bool kg_ready;          // d.Kg holds Omega G^p Omega^T / s
   size_t esize;
@@ -920,6 +921,12 @@ int rid_ingest(rid_handle* h, const void* cols, int64_t ld, int32_t ncols, int32
   if (ncols == 0) return RID_OK;
   if (!cols) return fail(h, RID_EINVAL, "cols is NULL");
   if (ld < h->d.m) return fail(h, RID_EINVAL, "ld < m");
+  if (h->rcss) {
+    // the attached selector decides these columns first, on the handle's stream, so that its list
+    // holds them before the batch step that reads it is queued
+    const int rc = rid_rcss_ingest(h->rcss, cols, ld, ncols, on_device);
+    if (rc != RID_OK) return fail(h, rc, std::string("selector: ") + rid_last_error(nullptr));
+  }
   const size_t cbytes = (size_t)h->d.m * h->esize;
   for (int32_t q = 0; q < ncols; ++q) {
     const char* src = (const char*)cols + (size_t)q * ld * h->esize;
@@ -1403,9 +1410,38 @@ int rid_sync(rid_handle* h) {
   return check_device_error(h);
 }
 
+int rid_attach_rcss(rid_handle* h, rid_rcss* g) {
+  if (!h) return RID_EINVAL;
+  if (h->n_obs > 0 || !h->pend.empty()) return fail(h, RID_ESTATE, "attach the selector before the first ingest");
+  if (!g) {
+    h->rcss = nullptr;
+    h->d.ext_sel = nullptr;
+    h->d.ext_nsel = nullptr;
+    return RID_OK;
+  }
+  const int64_t* sel = nullptr;
+  const int* nsel = nullptr;
+  int64_t m = 0;
+  int cap = 0, stop = 0, dtype = 0;
+  cudaStream_t gst = nullptr;
+  rid::rcss_selection_view(g, &sel, &nsel, &m, &cap, &stop, &dtype, &gst);
+  if (m != h->d.m || dtype != h->d.dtype || cap > h->d.t || !stop || gst != h->st || h->d.allreduce ||
+      h->d.grad)
+    return fail(h, RID_EINVAL,
+                "selector: needs the handle's m, data type and stream, cap <= t with stop_at_cap, and a handle "
+                "without row shards or gradient mode");
+  h->rcss = g;
+  h->d.ext_sel = sel;
+  h->d.ext_nsel = nsel;
+  return RID_OK;
+}
+
 int rid_reset(rid_handle* h) {
   if (!h) return RID_EINVAL;
   join(h);
+  h->rcss = nullptr;                      // a selector serves one stream: attach a new one
+  h->d.ext_sel = nullptr;
+  h->d.ext_nsel = nullptr;
   const int nk = rid::launch_reset_state(h->d, h->st);
   if (h->prof) h->kernels[1] += nk;
   if (h->d.right_l > 0) CK(cudaMemsetAsync(h->d.Y, 0, (size_t)h->d.m_pad * h->d.right_l * h->esize, h->st));

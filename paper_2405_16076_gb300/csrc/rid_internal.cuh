@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct rid_rcss;
+
 namespace rid {
 
 constexpr int kMaxB = 16;          // columns per ingest launch
@@ -37,6 +39,8 @@ struct Dev {
   double lambda_fixed;
   double refill_scale;            // c (k ln k + k ln(1/delta)/eps) / t
   int refill_mode;                // 0 first success (R7), 1 proportional draw (R7p)
+  const int64_t* ext_sel;         // Algorithm 1 as the selector: its selection list (NULL: Algorithm 3)
+  const int* ext_nsel;            // and its length, both in the attached selector's device state
   uint32_t ring_wait_limit;       // polls of a tensor-core pipeline wait before it gives up
   // row sharding: global row of local row 0 (a multiple of 128; Omega is keyed by the global row);
   // with an exchange (allreduce non-null) the sketch reductions leave the group's squared norms in
@@ -245,6 +249,11 @@ int launch_scores(const Dev& d, int count, int64_t jd0, double* work_base, int64
 int launch_qr_coop(const Dev& d, double* Q4, double* b4, double* h4, double* r4, double* Q6,
                    double* b6, double* h6, double* r6, unsigned int* bar_mem, cudaStream_t st);
 int64_t work_doubles(const Dev& d);
+
+// The device view of a residual-CSS selector (csrc/rcss.cu): its selection list and length, its
+// sizes, capacity, cap mode, data type and stream.
+void rcss_selection_view(const rid_rcss* g, const int64_t** sel, const int** nsel, int64_t* m, int* cap,
+                         int* stop_at_cap, int* dtype, cudaStream_t* st);
 
 // Message returned by rid_last_error(NULL) for failures outside a handle.
 void set_global_error(const char* msg);

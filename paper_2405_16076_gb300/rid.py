@@ -102,6 +102,7 @@ def _load():
         "rid_rcss_probabilities": (ctypes.c_int, [H, P, ctypes.c_int64, P]),
         "rid_rcss_basis": (ctypes.c_int, [H, P, ctypes.c_int64, ctypes.c_int32]),
         "rid_rcss_destroy": (ctypes.c_int, [H]),
+        "rid_attach_rcss": (ctypes.c_int, [H, H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -144,6 +145,7 @@ rid_rcss_selection = lib.rid_rcss_selection
 rid_rcss_probabilities = lib.rid_rcss_probabilities
 rid_rcss_basis = lib.rid_rcss_basis
 rid_rcss_destroy = lib.rid_rcss_destroy
+rid_attach_rcss = lib.rid_attach_rcss
 
 
 def batch_ingest(handles, blocks):
@@ -499,6 +501,12 @@ class OnlineRID:
 
     def reset(self):
         _check(rid_reset(self.h), self.h)
+
+    def attach_rcss(self, g):
+        """Algorithm 1 (a ``ResidualCSS`` on this handle's stream, cap <= t, stop_at_cap) as the
+        selector; ``None`` detaches.  Keep ``g`` alive while the handle uses it."""
+        _check(rid_attach_rcss(self.h, g.h if g is not None else None), self.h)
+        self._rcss = g
 
 
 class ResidualCSS:

@@ -770,3 +770,25 @@ def test_residual_css_limit_stops_the_selection_only():
     end = min(j for j in free.steps if j >= sel[5])
     np.testing.assert_array_equal(capped.p[:end + 1], free.p[:end + 1])
     assert len(capped.selection()) == 6 and len(capped.p) == 120
+
+
+def test_residual_selector_feeds_algorithm1_subset_to_the_coefficient_updates():
+    """The online rows with Algorithm 1 as the selector: the final basis is Algorithm 1's subset
+    (capped at t columns) in slot order, and on an exact rank-6 stream whose subset spans the range
+    the chosen coefficients reconstruct it to rounding."""
+    from oracle.rid import OnlineRID, RIDConfig
+    rng = np.random.default_rng(3)
+    m, n, r, k = 300, 60, 6, 8
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    xi = 1e-4 * k * float(np.min(np.einsum("ij,ij->j", A, A)))
+    cfg = RIDConfig(m=m, k=k, s=4 * k + 3, h=12, lambda_mode="fixed", lambda_fixed=1e-6, seed=1,
+                    selector="residual", rcss_xi=xi, rcss_seed=5)
+    o = OnlineRID(cfg)
+    o.ingest(A)
+    J, P = o.finalize()
+    ref = ResidualCSS(m, k, xi, 5, limit=k)
+    ref.ingest(A)
+    act = J >= 0
+    np.testing.assert_array_equal(J[act], ref.selection())
+    assert np.all(J[~act] == -1) and act.sum() == 6
+    assert np.linalg.norm(A - A[:, J[act]] @ P[act]) <= 1e-12 * np.linalg.norm(A)
