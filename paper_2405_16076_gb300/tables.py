@@ -6,7 +6,8 @@ rid_finalize); the table reports, for the last batch step, the exact relative er
 single-pass NA-Hutch++ estimate (Algorithm 8), the update chosen (q*), the least-squares
 coefficients (P = A_J^+ A) on the online selections -- Algorithm 3's J and Algorithm 1's subset
 (rid_rcss_*, capped at k columns with xi = ||A - A_k||_F^2, as the experiments run it, Sec. 4.1)
--- and two offline references computed here from the whole matrix: the column-pivoted-QR
+-- the same online columns with Algorithm 1 as the selector (rid_attach_rcss), and two offline
+references computed here from the whole matrix: the column-pivoted-QR
 interpolative decomposition of rank k and the truncated SVD of rank k.  The paper's datasets are
 not available; the inputs are the synthetic streams of ``workloads`` (or any m x n array).
 
@@ -37,6 +38,39 @@ def offline_errors(A, k):
     return float(e_cpqr), float(np.sqrt(tail) / nA), tail
 
 
+def online_run(A, k, *, h=30, dtype="f64", sketch="native", omega="rademacher", block=1, seed=0,
+               lambda_mode="streaming", lambda_fixed=0.0, rcss_xi=None):
+    """The stream A (m x n, host array) through the library at rank k: Algorithm 3 selects, or
+    Algorithm 1 (capped at k, with rcss_xi) when rcss_xi is given.  Returns (exact relative errors
+    of Algorithms 4-7 for the last batch step, their NA-Hutch++ estimates, q*, the chosen P's
+    exact error, the active J)."""
+    import torch
+    from . import rid
+    m, n = A.shape
+    nA = np.linalg.norm(A)
+    g = rid.OnlineRID(m=m, k=k, s=4 * k + 3, h=h, dtype=dtype, sketch=sketch, omega=omega, seed=seed, n_max=n,
+                      lambda_mode=lambda_mode, lambda_fixed=lambda_fixed)
+    sel = None
+    if rcss_xi is not None:
+        sel = rid.ResidualCSS(m, k, rcss_xi, seed=seed, data_dtype=rid.RID_F64 if dtype == "f64" else rid.RID_F32,
+                              cap=k, stop_at_cap=True)
+        g.attach_rcss(sel)
+    X = torch.from_numpy(np.ascontiguousarray(A.T, dtype=np.float64 if dtype == "f64" else np.float32)).cuda()
+    for j0 in range(0, n, block):
+        g.ingest(X[j0:j0 + block])
+    J, P = g.finalize()
+    _, est_fro, q_star = g.error_estimate()
+    cand = g.candidates(n)                     # (4, t, n): rows = active slots in slot order
+    g.close()
+    if sel is not None:
+        sel.close()
+    act = J >= 0
+    AJ = A[:, J[act]]
+    na = int(act.sum())
+    exact = [float(np.linalg.norm(A - AJ @ cand[q][:na]) / nA) for q in range(4)]
+    return exact, [float(e / nA) for e in est_fro[1:5]], q_star, float(np.linalg.norm(A - AJ @ P[act]) / nA), J[act]
+
+
 def residual_css(A, k, xi, *, dtype="f64", block=1, seed=0):
     """Algorithm 1's subset of the stream A (m x n, host array) on the GPU, capped at k columns."""
     import torch
@@ -55,29 +89,17 @@ def residual_css(A, k, xi, *, dtype="f64", block=1, seed=0):
 def table_row(A, k, *, h=30, dtype="f64", sketch="native", omega="rademacher", block=1, seed=0,
               lambda_mode="streaming", lambda_fixed=0.0):
     """One row: run the stream A (m x n, host array) at rank k on the GPU and evaluate it."""
-    import torch
-    from . import rid
-    m, n = A.shape
-    g = rid.OnlineRID(m=m, k=k, s=4 * k + 3, h=h, dtype=dtype, sketch=sketch, omega=omega, seed=seed, n_max=n,
-                      lambda_mode=lambda_mode, lambda_fixed=lambda_fixed)
-    X = torch.from_numpy(np.ascontiguousarray(A.T, dtype=np.float64 if dtype == "f64" else np.float32)).cuda()
-    for j0 in range(0, n, block):
-        g.ingest(X[j0:j0 + block])
-    J, P = g.finalize()
-    _, est_fro, q_star = g.error_estimate()
-    cand = g.candidates(n)                     # (4, t, n): rows = active slots in slot order
-    g.close()
-    nA = np.linalg.norm(A)
-    act = J >= 0
-    AJ = A[:, J[act]]
-    na = int(act.sum())
-    exact = [float(np.linalg.norm(A - AJ @ cand[q][:na]) / nA) for q in range(4)]
+    kw = dict(h=h, dtype=dtype, sketch=sketch, omega=omega, block=block, seed=seed, lambda_mode=lambda_mode,
+              lambda_fixed=lambda_fixed)
+    exact, est, q_star, chosen, Ja = online_run(A, k, **kw)
     e_cpqr, e_svd, tail = offline_errors(A, k)
-    sel1 = residual_css(A, k, max(tail, 1e-300), dtype=dtype, block=block, seed=seed)
-    return {"k": k, "exact": exact, "estimated": [float(e / nA) for e in est_fro[1:5]], "q_star": q_star,
-            "chosen_exact": float(np.linalg.norm(A - AJ @ P[act]) / nA), "cpqr": e_cpqr, "svd": e_svd,
-            "n_basis": na, "alg3_ls": least_squares_error(A, J[act]),
-            "alg1_ls": least_squares_error(A, sel1), "alg1_n": int(len(sel1))}
+    xi = max(tail, 1e-300)
+    sel1 = residual_css(A, k, xi, dtype=dtype, block=block, seed=seed)
+    exact1, est1, q1, chosen1, _ = online_run(A, k, rcss_xi=xi, **kw)
+    return {"k": k, "exact": exact, "estimated": est, "q_star": q_star, "chosen_exact": chosen, "cpqr": e_cpqr,
+            "svd": e_svd, "n_basis": int(len(Ja)), "alg3_ls": least_squares_error(A, Ja),
+            "alg1_ls": least_squares_error(A, sel1), "alg1_n": int(len(sel1)),
+            "alg1_online": {"exact": exact1, "estimated": est1, "q_star": q1, "chosen_exact": chosen1}}
 
 
 def markdown(rows, title):
@@ -89,6 +111,13 @@ def markdown(rows, title):
         cells = [f"{r['exact'][q]:.4f} / {r['estimated'][q]:.4f}" for q in range(4)]
         out.append(f"| {r['k']} | " + " | ".join(cells) + f" | {r['q_star']} | {r['alg3_ls']:.4f} | "
                    f"{r['alg1_ls']:.4f} | {r['cpqr']:.4f} | {r['svd']:.4f} |")
+    out += ["", "Algorithm 1 as the selector, coefficients online (Algorithms 4-7, q* by Algorithm 8):", "",
+            "| k | Alg. 4 exact / est. | Alg. 5 exact / est. | Alg. 6 exact / est. | Alg. 7 exact / est. | q* |",
+            "|---:|---|---|---|---|---:|"]
+    for r in rows:
+        o = r["alg1_online"]
+        cells = [f"{o['exact'][q]:.4f} / {o['estimated'][q]:.4f}" for q in range(4)]
+        out.append(f"| {r['k']} | " + " | ".join(cells) + f" | {o['q_star']} |")
     return "\n".join(out)
 
 

@@ -24,5 +24,9 @@ def test_table_rows_are_consistent():
         assert r["alg3_ls"] <= r["chosen_exact"] + 1e-12      # least squares is optimal for its J
         assert r["svd"] <= r["alg1_ls"] + 1e-12 and r["svd"] <= r["alg3_ls"] + 1e-12
         assert 0 < r["alg1_n"] <= k
+        o = r["alg1_online"]
+        assert o["q_star"] in (4, 5, 6, 7)
+        assert abs(o["chosen_exact"] - o["exact"][o["q_star"] - 4]) <= 1e-12
+        assert r["alg1_ls"] <= o["chosen_exact"] + 1e-12     # same subset: least squares is optimal
     md = tables.markdown([r], "check")
     assert md.count("|") > 10
