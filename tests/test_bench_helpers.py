@@ -67,3 +67,13 @@ def test_single_thread_cpu_baseline_runs_on_one_core():
     r = bench.cpu_baseline_single_thread("channel_small")
     assert "error" not in r, r
     assert r["cores"] == 1 and r["value"] > 0 and r["unit"] == "snapshots/s"
+
+
+def test_least_squares_error_closed_forms():
+    """The tables' least-squares error: 0 when the chosen columns span the matrix, 1 for an empty
+    choice, and the distance of the last column from the line of the first otherwise."""
+    from paper_2405_16076_gb300 import tables
+    A = np.array([[1.0, 2.0, 0.0], [0.0, 0.0, 1.0]])
+    assert tables.least_squares_error(A, [0, 2]) <= 1e-15
+    assert tables.least_squares_error(A, []) == 1.0
+    assert abs(tables.least_squares_error(A, [0]) - 1.0 / np.linalg.norm(A)) <= 1e-15

@@ -792,3 +792,18 @@ def test_residual_selector_feeds_algorithm1_subset_to_the_coefficient_updates():
     np.testing.assert_array_equal(J[act], ref.selection())
     assert np.all(J[~act] == -1) and act.sum() == 6
     assert np.linalg.norm(A - A[:, J[act]] @ P[act]) <= 1e-12 * np.linalg.norm(A)
+
+
+def test_residual_css_replay_reproduces_the_run():
+    """The decision steps replayed on a run's own p give back its selection, sigma and steps (the
+    full-size GPU check relies on this)."""
+    from oracle.residual_css import replay
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((60, 30)) @ rng.standard_normal((30, 150))
+    xi = 0.3 * 5 * float(np.median(np.einsum("ij,ij->j", A, A)))
+    for limit in (None, 7):
+        o = ResidualCSS(60, 5, xi, 2, limit=limit)
+        o.ingest(A)
+        sel, sigma, steps = replay(o.p, 2, limit=limit)
+        np.testing.assert_array_equal(sel, o.selection())
+        assert sigma == o.sigma and steps == o.steps
