@@ -463,7 +463,7 @@ typedef struct rid_rcss rid_rcss;
  * selected a later keep decision adds nothing and p, sigma and the steps go on (the treatment of
  * the experiments, Sec. 4.1, with cap = k); stop_at_cap = 0: a selection beyond cap is an error.
  * cuda_stream: the stream every call runs on (NULL: the legacy default stream).  Errors:
- * RID_EINVAL (sizes), RID_ENOMEM, RID_ENOLIB. */
+ * RID_EINVAL (sizes), RID_ENOMEM, RID_ENOLIB, RID_ECUDA (kernel set-up refused). */
 int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed, int32_t data_dtype,
                   int32_t cap, int32_t stop_at_cap, void* cuda_stream);
 

@@ -849,7 +849,12 @@ int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed
              cudaMallocHost((void**)&h->hflag, sizeof(int)) != cudaSuccess ||
              cudaMallocHost((void**)&h->hp_stage, sizeof(double) * rid::kRcBlock) != cudaSuccess))
     ok = false;
-  if (ok) {
+  if (!ok) {
+    cudaGetLastError();
+    rid_rcss_destroy(h);
+    return rc_fail(RID_ENOMEM, "rcss: device allocation failed");
+  }
+  {
     const int s64 = 8 * 2 * rid::kRcRun * rid::kRcLd;
     const int s32 = 4 * 2 * rid::kRcRun * rid::kRcLd;
     const int t64 = 8 * rid::kThinRuns * rid::kRcRun * 16;
@@ -866,8 +871,13 @@ int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed
                                   : (const void*)rid::rcss_thin_stage_kernel<16>;
       ok = ok && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, st) == cudaSuccess;
     }
+    if (!ok) {
+      cudaGetLastError();
+      rid_rcss_destroy(h);
+      return rc_fail(RID_ECUDA, "rcss: kernel shared-memory attributes refused");
+    }
   }
-  if (ok) {
+  {
     ok = cudaMemsetAsync(h->Q, 0, (size_t)(cap + 1) * h->m_pad * h->es, h->st) == cudaSuccess &&
          cudaMemsetAsync(h->dst, 0, sizeof(rid::RcssDevState), h->st) == cudaSuccess &&
          cudaMemsetAsync(h->sel, 0xFF, sizeof(int64_t) * (size_t)cap, h->st) == cudaSuccess &&   // -1
@@ -876,7 +886,7 @@ int rid_rcss_init(rid_rcss** out, int64_t m, int32_t k, double xi, uint64_t seed
   if (!ok) {
     cudaGetLastError();
     rid_rcss_destroy(h);
-    return rc_fail(RID_ENOMEM, "rcss: device allocation failed");
+    return rc_fail(RID_ECUDA, "rcss: device initialization failed");
   }
   *out = h;
   return RID_OK;
