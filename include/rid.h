@@ -498,8 +498,9 @@ int rid_rcss_destroy(rid_rcss* h);
  * the ridge scores are still computed but decide nothing.  g must have the handle's m, data type
  * and stream, cap <= t and stop_at_cap != 0, and must outlive the handle's use of it; the handle
  * must have no row shards and no gradient mode.  Attach before the first rid_ingest; g = NULL
- * detaches.  rid_reset detaches (a selector serves one stream).  rid_checkpoint does not cover g.
- * Errors: RID_EINVAL (mismatch), RID_ESTATE (columns already ingested). */
+ * detaches.  rid_reset and rid_restore detach (a selector serves one stream); rid_checkpoint and
+ * rid_checkpoint_size fail with RID_ESTATE while g is attached (its state is not in the
+ * checkpoint).  Errors: RID_EINVAL (mismatch), RID_ESTATE (columns already ingested). */
 int rid_attach_rcss(rid_handle* h, rid_rcss* g);
 
 #ifdef __cplusplus

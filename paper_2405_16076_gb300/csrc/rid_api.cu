@@ -1253,6 +1253,7 @@ const char* ckpt_counters_invalid(const CkptCounters& cn, int t, int npool) {
 
 int rid_checkpoint_size(rid_handle* h, int64_t* bytes) {
   if (!h || !bytes) return RID_EINVAL;
+  if (h->rcss) return fail(h, RID_ESTATE, "a checkpoint does not cover an attached selector");
   int rc = flush(h);
   if (rc != RID_OK) return rc;
   join(h);
@@ -1265,6 +1266,7 @@ int rid_checkpoint_size(rid_handle* h, int64_t* bytes) {
 
 int rid_checkpoint(rid_handle* h, void* buf, int64_t bytes) {
   if (!h || !buf) return RID_EINVAL;
+  if (h->rcss) return fail(h, RID_ESTATE, "a checkpoint does not cover an attached selector");
   int rc = flush(h);
   if (rc != RID_OK) return rc;
   rc = check_device_error(h);                   // joins the batch streams and synchronizes

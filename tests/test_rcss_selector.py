@@ -82,6 +82,9 @@ def test_residual_selector_arguments():
     g.attach_rcss(sel)
     g.ingest(np.random.default_rng(0).standard_normal((500, 3)))
     with pytest.raises(rid.RIDError) as e:
+        g.checkpoint()                                                           # not covered
+    assert e.value.code == rid.RID_ESTATE
+    with pytest.raises(rid.RIDError) as e:
         g.attach_rcss(None)                                                      # after an ingest
     assert e.value.code == rid.RID_ESTATE
     g.close()
